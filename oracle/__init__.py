@@ -1,0 +1,252 @@
+"""Python handle on the plain FP64 CPU oracle (``alens_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg
+of the benchmark use it to check and time the CUDA path.  The product
+library never imports it.  Arrays go in and out as float64 / int32 numpy
+arrays; the C side does all arithmetic.
+
+Parity pins: every function here is checked by ``tests/test_oracle_*.py``
+against closed forms, brute force, library routines or invariants; none is
+"parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "alens_oracle.c"
+_LIB = _HERE / "_build" / "liborc.so"
+
+
+class Problem(C.Structure):
+    _fields_ = [("box", C.c_double * 3), ("diameter", C.c_double), ("length", C.c_double),
+                ("viscosity", C.c_double), ("dt", C.c_double), ("delta_c", C.c_double)]
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (-O2 -ffp-contract=off, OpenMP)."""
+    if _LIB.exists() and not force and _LIB.stat().st_mtime >= _SRC.stat().st_mtime:
+        return _LIB
+    _LIB.parent.mkdir(parents=True, exist_ok=True)
+    tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-std=c11", "-fvisibility=hidden", str(_SRC), "-o", str(tmp), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(str(build()))
+        d, i64, vp = C.c_double, C.c_int64, C.c_void_p
+        P = C.POINTER(Problem)
+        sig = {
+            "orc_drag": (None, [d, d, d, vp]),
+            "orc_axis": (None, [i64, vp, vp]),
+            "orc_wrap": (None, [i64, vp, vp, vp]),
+            "orc_segment_closest": (d, [vp, vp, vp, d, vp, vp]),
+            "orc_find_pairs": (i64, [i64, vp, vp, P, vp, i64, vp, i64]),
+            "orc_pair_gaps": (None, [i64, vp, vp, P, i64, vp, vp]),
+            "orc_mobility_apply": (None, [i64, vp, P, vp, vp]),
+            "orc_assemble": (None, [i64, vp, vp, vp, P, i64, vp, vp, vp, vp, vp, vp]),
+            "orc_apply_D": (None, [i64, i64, vp, vp, vp, vp]),
+            "orc_apply_Dt": (None, [i64, vp, vp, vp, vp]),
+            "orc_gradient": (d, [i64, vp, P, i64, vp, vp, vp, vp, vp]),
+            "orc_dense_A": (None, [i64, vp, P, i64, vp, vp, vp]),
+            "orc_solve_enum": (i64, [i64, vp, P, i64, vp, vp, vp, vp]),
+            "orc_solve_apgd": (d, [i64, vp, P, i64, vp, vp, vp, vp, d, i64, vp]),
+            "orc_update": (None, [i64, vp, vp, vp, P, i64, vp, vp, vp, vp, vp, vp]),
+            "orc_step": (i64, [i64, vp, vp, vp, P, d, i64, i64, vp, vp, vp, vp, vp, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def problem(box, diameter=1.0, length=10.0, viscosity=1.0, dt=1e-3, delta_c=None) -> Problem:
+    b = box if np.ndim(box) else (box, box, box)
+    return Problem((C.c_double * 3)(*[float(v) for v in b]), float(diameter), float(length),
+                   float(viscosity), float(dt), float(diameter if delta_c is None else delta_c))
+
+
+def problem_of(sys) -> Problem:
+    """Problem parameters of a ``workloads.RodSystem``."""
+    return problem(sys.box, sys.diameter, sys.length, sys.viscosity, sys.dt, sys.delta_c)
+
+
+def drag(eta, length, diameter):
+    out = np.zeros(4)
+    lib().orc_drag(eta, length, diameter, _p(out))
+    return out  # zeta_perp, zeta_par, zeta_rot, zeta_spin
+
+
+def axis(quat):
+    q = _f64(quat, (-1, 4))
+    out = np.zeros((q.shape[0], 3))
+    lib().orc_axis(q.shape[0], _p(q), _p(out))
+    return out
+
+
+def wrap(x, box):
+    xx = _f64(x, (-1, 3))
+    b = _f64(box if np.ndim(box) else [box] * 3)
+    out = np.zeros_like(xx)
+    lib().orc_wrap(xx.shape[0], _p(xx), _p(b), _p(out))
+    return out
+
+
+def segment_closest(dx, p, q, length):
+    dx, p, q = _f64(dx), _f64(p), _f64(q)
+    s, t = C.c_double(), C.c_double()
+    d = lib().orc_segment_closest(_p(dx), _p(p), _p(q), float(length), C.byref(s), C.byref(t))
+    return d, s.value, t.value
+
+
+def find_pairs(x, quat, pb: Problem, rows=None):
+    x, quat = _f64(x, (-1, 3)), _f64(quat, (-1, 4))
+    n = x.shape[0]
+    r = None if rows is None else np.ascontiguousarray(np.unique(np.asarray(rows, dtype=np.int64)))
+    nr = 0 if r is None else r.shape[0]
+    cnt = lib().orc_find_pairs(n, _p(x), _p(quat), C.byref(pb), _p(r), nr, None, 0)
+    out = np.zeros((max(cnt, 1), 3), dtype=np.int32)
+    cnt2 = lib().orc_find_pairs(n, _p(x), _p(quat), C.byref(pb), _p(r), nr, _p(out), cnt)
+    assert cnt2 == cnt
+    return out[:cnt]
+
+
+def pair_gaps(x, quat, pb: Problem, pairs):
+    x, quat = _f64(x, (-1, 3)), _f64(quat, (-1, 4))
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros(pr.shape[0])
+    lib().orc_pair_gaps(x.shape[0], _p(x), _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(out))
+    return out
+
+
+def mobility_apply(quat, pb: Problem, F):
+    quat, F = _f64(quat, (-1, 4)), _f64(F, (-1, 6))
+    U = np.zeros_like(F)
+    lib().orc_mobility_apply(quat.shape[0], _p(quat), C.byref(pb), _p(F), _p(U))
+    return U
+
+
+def assemble(x, quat, fnc, pb: Problem, pairs):
+    x, quat, fnc = _f64(x, (-1, 3)), _f64(quat, (-1, 4)), _f64(fnc, (-1, 6))
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    m = pr.shape[0]
+    phi, dg, q = np.zeros(m), np.zeros((m, 9)), np.zeros(m)
+    yp, yq = np.zeros((m, 3)), np.zeros((m, 3))
+    lib().orc_assemble(x.shape[0], _p(x), _p(quat), _p(fnc), C.byref(pb), m, _p(pr), _p(phi), _p(dg), _p(q),
+                       _p(yp), _p(yq))
+    return {"phi": phi, "dgeom": dg, "q": q, "yP": yp, "yQ": yq}
+
+
+def apply_D(n, pairs, dgeom, gamma):
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    dg, g = _f64(dgeom, (-1, 9)), _f64(gamma)
+    F = np.zeros((n, 6))
+    lib().orc_apply_D(n, pr.shape[0], _p(pr), _p(dg), _p(g), _p(F))
+    return F
+
+
+def apply_Dt(pairs, dgeom, U):
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    dg, U = _f64(dgeom, (-1, 9)), _f64(U, (-1, 6))
+    out = np.zeros(pr.shape[0])
+    lib().orc_apply_Dt(pr.shape[0], _p(pr), _p(dg), _p(U), _p(out))
+    return out
+
+
+def gradient(quat, pb: Problem, pairs, dgeom, q, gamma):
+    quat = _f64(quat, (-1, 4))
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    dg, q, gm = _f64(dgeom, (-1, 9)), _f64(q), _f64(gamma)
+    g = np.zeros(pr.shape[0])
+    r = lib().orc_gradient(quat.shape[0], _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(q), _p(gm), _p(g))
+    return g, r
+
+
+def dense_A(quat, pb: Problem, pairs, dgeom):
+    quat = _f64(quat, (-1, 4))
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    dg = _f64(dgeom, (-1, 9))
+    m = pr.shape[0]
+    A = np.zeros((m, m))
+    lib().orc_dense_A(quat.shape[0], _p(quat), C.byref(pb), m, _p(pr), _p(dg), _p(A))
+    return A
+
+
+def solve_enum(quat, pb: Problem, pairs, dgeom, q):
+    quat = _f64(quat, (-1, 4))
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    dg, q = _f64(dgeom, (-1, 9)), _f64(q)
+    gm = np.zeros(pr.shape[0])
+    mask = lib().orc_solve_enum(quat.shape[0], _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(q), _p(gm))
+    return gm, mask
+
+
+def solve_apgd(quat, pb: Problem, pairs, dgeom, q, tol=1e-12, max_iter=1_000_000, gamma0=None):
+    quat = _f64(quat, (-1, 4))
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    dg, q = _f64(dgeom, (-1, 9)), _f64(q)
+    gm = np.zeros(pr.shape[0]) if gamma0 is None else _f64(gamma0).copy()
+    it = C.c_int64()
+    r = lib().orc_solve_apgd(quat.shape[0], _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(q), _p(gm),
+                             float(tol), int(max_iter), C.byref(it))
+    return gm, r, it.value
+
+
+def update(x, quat, fnc, pb: Problem, pairs, dgeom, gamma):
+    x, quat, fnc = _f64(x, (-1, 3)), _f64(quat, (-1, 4)), _f64(fnc, (-1, 6))
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
+    dg, gm = _f64(dgeom, (-1, 9)), _f64(gamma)
+    xo, qo, U = np.zeros_like(x), np.zeros_like(quat), np.zeros((x.shape[0], 6))
+    lib().orc_update(x.shape[0], _p(x), _p(quat), _p(fnc), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(gm),
+                     _p(xo), _p(qo), _p(U))
+    return xo, qo, U
+
+
+def step(x, quat, fnc, pb: Problem, tol=1e-12, max_iter=1_000_000, max_pairs=None):
+    """One full constrained step; returns a dict of every intermediate."""
+    x, quat, fnc = _f64(x, (-1, 3)), _f64(quat, (-1, 4)), _f64(fnc, (-1, 6))
+    pairs = find_pairs(x, quat, pb)
+    asm = assemble(x, quat, fnc, pb, pairs)
+    gamma, res, iters = solve_apgd(quat, pb, pairs, asm["dgeom"], asm["q"], tol=tol, max_iter=max_iter)
+    xo, qo, U = update(x, quat, fnc, pb, pairs, asm["dgeom"], gamma)
+    return {"pairs": pairs, **asm, "gamma": gamma, "residual": res, "iters": iters, "x": xo, "quat": qo, "U": U}
+
+
+def step_native(x, quat, fnc, pb: Problem, tol, max_iter, max_pairs):
+    """The whole step inside one C call (used to time the oracle)."""
+    x, quat, fnc = _f64(x, (-1, 3)), _f64(quat, (-1, 4)), _f64(fnc, (-1, 6))
+    n = x.shape[0]
+    pairs = np.zeros((max_pairs, 3), dtype=np.int32)
+    gamma = np.zeros(max_pairs)
+    xo, qo, U = np.zeros_like(x), np.zeros_like(quat), np.zeros((n, 6))
+    res, it = C.c_double(), C.c_int64()
+    np_ = lib().orc_step(n, _p(x), _p(quat), _p(fnc), C.byref(pb), float(tol), int(max_iter), int(max_pairs),
+                         _p(pairs), _p(gamma), _p(xo), _p(qo), _p(U), C.byref(res), C.byref(it))
+    return {"n_pairs": np_, "pairs": pairs[:max(np_, 0)], "gamma": gamma[:max(np_, 0)], "x": xo, "quat": qo,
+            "U": U, "residual": res.value, "iters": it.value}

@@ -1,0 +1,697 @@
+/*
+ * Plain FP64 CPU oracle for the collision-constraint step of aLENS
+ * (Yan et al., "Towards the cellular-scale simulation of motor-driven
+ * cytoskeletal assemblies", arXiv 2109.08206).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
+ * includes this file; only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark load it.  It shares no code, header, table or helper
+ * with the CUDA path.
+ *
+ * Built with -O2 -ffp-contract=off (no fused multiply-add), so every product
+ * and sum is rounded on its own.  Slow and obvious on purpose:
+ *   - pairs by brute force over all i < j and all 27 periodic image shifts;
+ *   - closest points of two segments by enumerating the interior stationary
+ *     point and the four edges of the parameter square;
+ *   - the complementarity problem by active-set enumeration (tiny systems)
+ *     or by accelerated projected gradient (FISTA with restart), not by the
+ *     Barzilai-Borwein iteration the GPU path uses.
+ *
+ * Readings of passages the paper leaves open (they are parameters or fixed
+ * rules on both sides):
+ *   R1 drag: zeta_perp = 4 pi eta L / ln(2L/D) (the coefficient the paper
+ *      quotes in Section 3 "Filament dynamics"), zeta_par = zeta_perp / 2,
+ *      zeta_rot = zeta_perp L^2 / 12, zeta_spin = pi eta D^2 L.
+ *   R2 L is the cylinder length (caps excluded).
+ *   R3 Phi is the surface gap |r| - D; a pair is kept iff Phi < delta_c.
+ *   R4 parallel segments (det <= 1e-12 a c) whose projections overlap take
+ *      s* at the middle of the overlap and t* as its clamped projection;
+ *      touching centrelines take e = unit(p_i x p_j) turned so e.dx >= 0,
+ *      or, for collinear axes, e = sign(dx.p_i) p_i, or e_x.
+ *   R5 every image shift k in {-1,0,1}^3 with |dx| < L + D + delta_c is its
+ *      own constraint, keyed (i, j, code), code = (kx+1)+3(ky+1)+9(kz+1),
+ *      dx = x_i - x_j - k*box.
+ *   R6 residual r = (h/D) max_c |pi_c|, pi_c = g_c if gamma_c > 0 else
+ *      min(g_c, 0), g = D^T M D gamma + q (projected gradient, in rod
+ *      diameters of linearised gap).
+ *   R7 quaternions (s, v), body axis e_z, lab-frame angular velocity,
+ *      linear update then renormalisation.
+ */
+#define _GNU_SOURCE
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_API __attribute__((visibility("default")))
+
+typedef struct {
+    double box[3];
+    double diameter;
+    double length;
+    double viscosity;
+    double dt;
+    double delta_c;
+} orc_problem;
+
+/* ---------------------------------------------------------------- helpers */
+
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void cross3(const double* a, const double* b, double* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Drag coefficients (reading R1).  Section 3 quotes 4 pi eta L / log(2L/D). */
+ORC_API void orc_drag(double eta, double L, double D, double out[4])
+{
+    double zperp = 4.0 * M_PI * eta * L / log(2.0 * L / D);
+    out[0] = zperp;                 /* perpendicular translation */
+    out[1] = zperp / 2.0;           /* parallel translation */
+    out[2] = zperp * L * L / 12.0;  /* rotation about an axis normal to the rod */
+    out[3] = M_PI * eta * D * D * L;/* spin about the rod axis */
+}
+
+/* Rod axis p = R(theta) e_z for unit quaternion theta = (s, v): third column of
+ * the rotation matrix the quaternion generates (Appendix "Symmetry of the
+ * geometrically constrained optimization problem", y = R Y). */
+ORC_API void orc_axis(int64_t n, const double* quat, double* axis)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const double* q = quat + 4 * i;
+        double s = q[0], a = q[1], b = q[2], c = q[3];
+        axis[3 * i + 0] = 2.0 * (a * c + s * b);
+        axis[3 * i + 1] = 2.0 * (b * c - s * a);
+        axis[3 * i + 2] = s * s - a * a - b * b + c * c;
+    }
+}
+
+/* Wrap a coordinate into [0, box). */
+static double wrap1(double v, double b)
+{
+    double w = v - b * floor(v / b);
+    if (w >= b) w = 0.0;
+    if (w < 0.0) w = 0.0;
+    return w;
+}
+
+ORC_API void orc_wrap(int64_t n, const double* x, const double box[3], double* xw)
+{
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) xw[3 * i + k] = wrap1(x[3 * i + k], box[k]);
+}
+
+/* |dx + s p - t q|^2 */
+static double seg_f(const double* dx, const double* p, const double* q, double s, double t)
+{
+    double r0 = dx[0] + s * p[0] - t * q[0];
+    double r1 = dx[1] + s * p[1] - t * q[1];
+    double r2 = dx[2] + s * p[2] - t * q[2];
+    return r0 * r0 + r1 * r1 + r2 * r2;
+}
+
+/* Closest points of segments P = {s p : |s| <= L/2} and Q = {dx' + t q} where
+ * the offset between centres is dx = x_P - x_Q (Appendix Fig. "pairwise
+ * geometry": r = x_P + y_P - x_Q - y_Q with y_P = s p, y_Q = t q).
+ * Minimises f(s, t) = |dx + s p - t q|^2 over [-L/2, L/2]^2 by checking the
+ * interior stationary point and then the minimum on each of the four edges
+ * (each a clamped one-dimensional projection).  Reading R4 for parallel
+ * segments.  Returns |r| at the minimiser. */
+ORC_API double orc_segment_closest(const double* dx, const double* p, const double* q, double L,
+                                   double* s_out, double* t_out)
+{
+    const double hl = 0.5 * L;
+    double a = dot3(p, p), b = dot3(p, q), c = dot3(q, q);
+    double d = dot3(p, dx), e = dot3(q, dx);
+    double det = a * c - b * b;
+    if (det > 1e-12 * a * c) {
+        double s0 = (b * e - c * d) / det;
+        double t0 = (a * e - b * d) / det;
+        if (fabs(s0) <= hl && fabs(t0) <= hl) {
+            *s_out = s0; *t_out = t0;
+            return sqrt(seg_f(dx, p, q, s0, t0));
+        }
+    } else {
+        /* parallel: points of Q project onto P's axis at s = (b t - d)/a */
+        double e1 = (b * (-hl) - d) / a, e2 = (b * hl - d) / a;
+        double lo = e1 < e2 ? e1 : e2, hi = e1 < e2 ? e2 : e1;
+        if (lo < -hl) lo = -hl;
+        if (hi > hl) hi = hl;
+        if (lo <= hi) {
+            double s0 = 0.5 * (lo + hi);
+            double t0 = clampd((b * s0 + e) / c, -hl, hl);
+            *s_out = s0; *t_out = t0;
+            return sqrt(seg_f(dx, p, q, s0, t0));
+        }
+    }
+    /* the four edges of the parameter square */
+    double best = INFINITY, bs = 0.0, bt = 0.0;
+    for (int edge = 0; edge < 4; ++edge) {
+        double s, t;
+        if (edge < 2) {
+            s = edge == 0 ? -hl : hl;
+            t = clampd((b * s + e) / c, -hl, hl);
+        } else {
+            t = edge == 2 ? -hl : hl;
+            s = clampd((b * t - d) / a, -hl, hl);
+        }
+        double f = seg_f(dx, p, q, s, t);
+        if (f < best) { best = f; bs = s; bt = t; }
+    }
+    *s_out = bs; *t_out = bt;
+    return sqrt(best);
+}
+
+/* Unit normal e for a pair given r (Appendix: e_P = r/|r| = -e_Q), with the
+ * reading R4 when |r| = 0. */
+static void pair_normal(const double* r, double dist, const double* dx, const double* p, const double* q,
+                        double* e)
+{
+    if (dist > 0.0) {
+        e[0] = r[0] / dist; e[1] = r[1] / dist; e[2] = r[2] / dist;
+        return;
+    }
+    double n[3];
+    cross3(p, q, n);
+    double nn = sqrt(dot3(n, n));
+    if (nn > 1e-12) {
+        double sg = dot3(n, dx) < 0.0 ? -1.0 : 1.0;
+        e[0] = sg * n[0] / nn; e[1] = sg * n[1] / nn; e[2] = sg * n[2] / nn;
+        return;
+    }
+    double pd = dot3(p, dx);
+    if (pd != 0.0) {
+        double sg = pd < 0.0 ? -1.0 : 1.0;
+        double pn = sqrt(dot3(p, p));
+        e[0] = sg * p[0] / pn; e[1] = sg * p[1] / pn; e[2] = sg * p[2] / pn;
+        return;
+    }
+    e[0] = 1.0; e[1] = 0.0; e[2] = 0.0;
+}
+
+static void image_shift(int code, int k[3])
+{
+    k[0] = code % 3 - 1;
+    k[1] = (code / 3) % 3 - 1;
+    k[2] = code / 9 - 1;
+}
+
+/* ------------------------------------------------------------------ pairs */
+
+/* Surface gap of pair (i, j) at image code: Phi = |r| - D (reading R3).
+ * Returns 0 and leaves *gap untouched when the centre distance is not below
+ * L + D + delta_c (no segment point can then be within delta_c). */
+static int pair_gap(const double* xw, const double* axis, const orc_problem* pb, int64_t i, int64_t j,
+                    int code, double* gap, double* s, double* t, double* dx)
+{
+    int k[3];
+    image_shift(code, k);
+    for (int c = 0; c < 3; ++c) dx[c] = xw[3 * i + c] - xw[3 * j + c] - (double)k[c] * pb->box[c];
+    double rcut = pb->length + pb->diameter + pb->delta_c;
+    if (dot3(dx, dx) >= rcut * rcut) return 0;
+    double d = orc_segment_closest(dx, axis + 3 * i, axis + 3 * j, pb->length, s, t);
+    *gap = d - pb->diameter;
+    return 1;
+}
+
+/* All pairs (i < j, image) whose surface gap is below delta_c, in (i, j, code)
+ * order (Appendix "Implementation": close pairs whose minimal distance is
+ * below delta_c).  If rows != NULL only pairs with i or j in rows[0..nrows)
+ * are listed (rows must be sorted ascending and unique).  Writes at most cap
+ * pairs (int32 triples) and returns the full count. */
+ORC_API int64_t orc_find_pairs(int64_t n, const double* x, const double* quat, const orc_problem* pb,
+                               const int64_t* rows, int64_t nrows, int32_t* pairs, int64_t cap)
+{
+    double* xw = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double* axis = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    orc_wrap(n, x, pb->box, xw);
+    orc_axis(n, quat, axis);
+    char* mark = NULL;
+    if (rows) {
+        mark = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+        for (int64_t r = 0; r < nrows; ++r) mark[rows[r]] = 1;
+    }
+    int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    /* pass 1: count per i */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c = 0;
+        for (int64_t j = i + 1; j < n; ++j) {
+            if (mark && !mark[i] && !mark[j]) continue;
+            for (int code = 0; code < 27; ++code) {
+                double gap, s, t, dx[3];
+                if (pair_gap(xw, axis, pb, i, j, code, &gap, &s, &t, dx) && gap < pb->delta_c) ++c;
+            }
+        }
+        cnt[i + 1] = c;
+    }
+    for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    int64_t total = cnt[n];
+    if (total <= cap && pairs) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t o = cnt[i];
+            for (int64_t j = i + 1; j < n; ++j) {
+                if (mark && !mark[i] && !mark[j]) continue;
+                for (int code = 0; code < 27; ++code) {
+                    double gap, s, t, dx[3];
+                    if (pair_gap(xw, axis, pb, i, j, code, &gap, &s, &t, dx) && gap < pb->delta_c) {
+                        pairs[3 * o + 0] = (int32_t)i;
+                        pairs[3 * o + 1] = (int32_t)j;
+                        pairs[3 * o + 2] = code;
+                        ++o;
+                    }
+                }
+            }
+        }
+    }
+    free(cnt); free(mark); free(xw); free(axis);
+    return total;
+}
+
+/* Surface gaps of given pairs (for near-threshold accounting in tests). */
+ORC_API void orc_pair_gaps(int64_t n, const double* x, const double* quat, const orc_problem* pb,
+                           int64_t npairs, const int32_t* pairs, double* gap_out)
+{
+    double* xw = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double* axis = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    orc_wrap(n, x, pb->box, xw);
+    orc_axis(n, quat, axis);
+    for (int64_t c = 0; c < npairs; ++c) {
+        int k[3];
+        image_shift(pairs[3 * c + 2], k);
+        int64_t i = pairs[3 * c], j = pairs[3 * c + 1];
+        double dx[3], s, t;
+        for (int m = 0; m < 3; ++m) dx[m] = xw[3 * i + m] - xw[3 * j + m] - (double)k[m] * pb->box[m];
+        gap_out[c] = orc_segment_closest(dx, axis + 3 * i, axis + 3 * j, pb->length, &s, &t) - pb->diameter;
+    }
+    free(xw); free(axis);
+}
+
+/* --------------------------------------------------------------- mobility */
+
+/* U = M F for one rod (Eq. U = M F, Appendix "Constraint quadratic
+ * programming"; M block-diagonal 6x6, reading R1):
+ *   U_t = (p p^T)/zeta_par F + (I - p p^T)/zeta_perp F
+ *   W   = (p p^T)/zeta_spin T + (I - p p^T)/zeta_rot T                    */
+static void mobility_rod(const double* p, const double* zeta, const double* F, double* U)
+{
+    double pf = dot3(p, F), pt = dot3(p, F + 3);
+    for (int k = 0; k < 3; ++k) {
+        double fpar = pf * p[k], tpar = pt * p[k];
+        U[k] = fpar / zeta[1] + (F[k] - fpar) / zeta[0];
+        U[3 + k] = tpar / zeta[3] + (F[3 + k] - tpar) / zeta[2];
+    }
+}
+
+ORC_API void orc_mobility_apply(int64_t n, const double* quat, const orc_problem* pb, const double* F,
+                                double* U)
+{
+    double zeta[4];
+    orc_drag(pb->viscosity, pb->length, pb->diameter, zeta);
+    double* axis = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    orc_axis(n, quat, axis);
+#pragma omp parallel for
+    for (int64_t i = 0; i < n; ++i) mobility_rod(axis + 3 * i, zeta, F + 6 * i, U + 6 * i);
+    free(axis);
+}
+
+/* --------------------------------------------------------------- assembly */
+
+/* Per pair: Phi, the D column and q (Appendix Eq. blockdef A, and the column
+ * D_PQ = [e_P, y_P x e_P, e_Q, y_Q x e_Q] with e_Q = -e_P).
+ * dgeom[c] = (e[3], y_P x e[3], y_Q x e[3]); the column acting on rod Q is
+ * (-e, -(y_Q x e)).  q_c = Phi_c / h + D_c^T M F_nc. */
+ORC_API void orc_assemble(int64_t n, const double* x, const double* quat, const double* fnc,
+                          const orc_problem* pb, int64_t npairs, const int32_t* pairs, double* phi,
+                          double* dgeom, double* q, double* yp_out, double* yq_out)
+{
+    double zeta[4];
+    orc_drag(pb->viscosity, pb->length, pb->diameter, zeta);
+    double* xw = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double* axis = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double* unc = (double*)malloc(sizeof(double) * 6 * (size_t)(n > 0 ? n : 1));
+    orc_wrap(n, x, pb->box, xw);
+    orc_axis(n, quat, axis);
+    for (int64_t i = 0; i < n; ++i) mobility_rod(axis + 3 * i, zeta, fnc + 6 * i, unc + 6 * i);
+#pragma omp parallel for
+    for (int64_t c = 0; c < npairs; ++c) {
+        int64_t i = pairs[3 * c], j = pairs[3 * c + 1];
+        int k[3];
+        image_shift(pairs[3 * c + 2], k);
+        double dx[3], s, t;
+        for (int m = 0; m < 3; ++m) dx[m] = xw[3 * i + m] - xw[3 * j + m] - (double)k[m] * pb->box[m];
+        const double* pi_ = axis + 3 * i;
+        const double* pj_ = axis + 3 * j;
+        double dist = orc_segment_closest(dx, pi_, pj_, pb->length, &s, &t);
+        double yP[3], yQ[3], r[3], e[3];
+        for (int m = 0; m < 3; ++m) {
+            yP[m] = s * pi_[m];
+            yQ[m] = t * pj_[m];
+            r[m] = dx[m] + yP[m] - yQ[m];
+        }
+        pair_normal(r, dist, dx, pi_, pj_, e);
+        double* dg = dgeom + 9 * c;
+        dg[0] = e[0]; dg[1] = e[1]; dg[2] = e[2];
+        cross3(yP, e, dg + 3);
+        cross3(yQ, e, dg + 6);
+        phi[c] = dist - pb->diameter;
+        const double* ui = unc + 6 * i;
+        const double* uj = unc + 6 * j;
+        double dtu = dot3(e, ui) + dot3(dg + 3, ui + 3) - dot3(e, uj) - dot3(dg + 6, uj + 3);
+        q[c] = phi[c] / pb->dt + dtu;
+        if (yp_out) { yp_out[3 * c] = yP[0]; yp_out[3 * c + 1] = yP[1]; yp_out[3 * c + 2] = yP[2]; }
+        if (yq_out) { yq_out[3 * c] = yQ[0]; yq_out[3 * c + 1] = yQ[1]; yq_out[3 * c + 2] = yQ[2]; }
+    }
+    free(xw); free(axis); free(unc);
+}
+
+/* F = D gamma: force and torque on every rod (Eq. dmap F_u = D_u gamma_u). */
+ORC_API void orc_apply_D(int64_t n, int64_t npairs, const int32_t* pairs, const double* dgeom,
+                         const double* gamma, double* F)
+{
+    memset(F, 0, sizeof(double) * 6 * (size_t)n);
+    for (int64_t c = 0; c < npairs; ++c) {
+        int64_t i = pairs[3 * c], j = pairs[3 * c + 1];
+        const double* dg = dgeom + 9 * c;
+        double g = gamma[c];
+        for (int m = 0; m < 3; ++m) {
+            F[6 * i + m] += g * dg[m];
+            F[6 * i + 3 + m] += g * dg[3 + m];
+            F[6 * j + m] -= g * dg[m];
+            F[6 * j + 3 + m] -= g * dg[6 + m];
+        }
+    }
+}
+
+/* out = D^T U */
+ORC_API void orc_apply_Dt(int64_t npairs, const int32_t* pairs, const double* dgeom, const double* U,
+                          double* out)
+{
+#pragma omp parallel for
+    for (int64_t c = 0; c < npairs; ++c) {
+        int64_t i = pairs[3 * c], j = pairs[3 * c + 1];
+        const double* dg = dgeom + 9 * c;
+        out[c] = dot3(dg, U + 6 * i) + dot3(dg + 3, U + 6 * i + 3) - dot3(dg, U + 6 * j) -
+                 dot3(dg + 6, U + 6 * j + 3);
+    }
+}
+
+/* ------------------------------------------------------------------ solve */
+
+typedef struct {
+    int64_t n, npairs;
+    const int32_t* pairs;
+    const double* dgeom;
+    const double* q;
+    double* axis;
+    double zeta[4];
+    double* F;   /* 6n scratch */
+    double* U;   /* 6n scratch */
+} orc_qp;
+
+/* out = (D^T M D) v   (Eq. blockdef B) */
+static void qp_matvec(orc_qp* qp, const double* v, double* out)
+{
+    orc_apply_D(qp->n, qp->npairs, qp->pairs, qp->dgeom, v, qp->F);
+#pragma omp parallel for
+    for (int64_t i = 0; i < qp->n; ++i) mobility_rod(qp->axis + 3 * i, qp->zeta, qp->F + 6 * i, qp->U + 6 * i);
+    orc_apply_Dt(qp->npairs, qp->pairs, qp->dgeom, qp->U, out);
+}
+
+static double qp_residual(const orc_qp* qp, const double* gamma, const double* g, const orc_problem* pb)
+{
+    double m = 0.0;
+    for (int64_t c = 0; c < qp->npairs; ++c) {
+        double pg = gamma[c] > 0.0 ? g[c] : (g[c] < 0.0 ? g[c] : 0.0);
+        double a = fabs(pg);
+        if (a > m) m = a;
+    }
+    return pb->dt / pb->diameter * m;
+}
+
+static int qp_init(orc_qp* qp, int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
+                   const int32_t* pairs, const double* dgeom, const double* q)
+{
+    qp->n = n; qp->npairs = npairs; qp->pairs = pairs; qp->dgeom = dgeom; qp->q = q;
+    orc_drag(pb->viscosity, pb->length, pb->diameter, qp->zeta);
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    qp->axis = (double*)malloc(sizeof(double) * 3 * nn);
+    qp->F = (double*)malloc(sizeof(double) * 6 * nn);
+    qp->U = (double*)malloc(sizeof(double) * 6 * nn);
+    orc_axis(n, quat, qp->axis);
+    return 0;
+}
+
+static void qp_free(orc_qp* qp) { free(qp->axis); free(qp->F); free(qp->U); }
+
+/* g = D^T M D gamma + q and the residual (reading R6). */
+ORC_API double orc_gradient(int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
+                            const int32_t* pairs, const double* dgeom, const double* q, const double* gamma,
+                            double* g)
+{
+    orc_qp qp;
+    qp_init(&qp, n, quat, pb, npairs, pairs, dgeom, q);
+    qp_matvec(&qp, gamma, g);
+    for (int64_t c = 0; c < npairs; ++c) g[c] += q[c];
+    double r = qp_residual(&qp, gamma, g, pb);
+    qp_free(&qp);
+    return r;
+}
+
+/* Dense A = D^T M D for small problems (column c = A e_c). */
+ORC_API void orc_dense_A(int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
+                         const int32_t* pairs, const double* dgeom, double* A)
+{
+    orc_qp qp;
+    qp_init(&qp, n, quat, pb, npairs, pairs, dgeom, NULL);
+    double* ec = (double*)calloc((size_t)npairs, sizeof(double));
+    double* col = (double*)malloc(sizeof(double) * (size_t)npairs);
+    for (int64_t c = 0; c < npairs; ++c) {
+        ec[c] = 1.0;
+        qp_matvec(&qp, ec, col);
+        ec[c] = 0.0;
+        for (int64_t r = 0; r < npairs; ++r) A[r * npairs + c] = col[r];
+    }
+    free(ec); free(col);
+    qp_free(&qp);
+}
+
+/* Solve A_SS x = b by Gaussian elimination with partial pivoting; returns 0
+ * if a pivot falls below tiny (singular), 1 otherwise. */
+static int small_solve(int m, double* A, double* b, double tiny)
+{
+    for (int k = 0; k < m; ++k) {
+        int piv = k;
+        for (int r = k + 1; r < m; ++r)
+            if (fabs(A[r * m + k]) > fabs(A[piv * m + k])) piv = r;
+        if (fabs(A[piv * m + k]) <= tiny) return 0;
+        if (piv != k) {
+            for (int c = 0; c < m; ++c) { double t = A[k * m + c]; A[k * m + c] = A[piv * m + c]; A[piv * m + c] = t; }
+            double t = b[k]; b[k] = b[piv]; b[piv] = t;
+        }
+        for (int r = k + 1; r < m; ++r) {
+            double f = A[r * m + k] / A[k * m + k];
+            for (int c = k; c < m; ++c) A[r * m + c] -= f * A[k * m + c];
+            b[r] -= f * b[k];
+        }
+    }
+    for (int k = m - 1; k >= 0; --k) {
+        double s = b[k];
+        for (int c = k + 1; c < m; ++c) s -= A[k * m + c] * b[c];
+        b[k] = s / A[k * m + k];
+    }
+    return 1;
+}
+
+/* Exact solution of the CQP (Eq. suppcqpdef, unilateral block) for tiny
+ * problems by enumerating active sets: for every subset S, solve
+ * A_SS gamma_S = -q_S and accept the first subset whose KKT conditions hold
+ * (gamma_S >= 0 and g_c >= 0 off S).  A solution with a non-singular A_SS
+ * always exists for an SPSD A.  Returns the accepted subset's bitmask, or -1. */
+ORC_API int64_t orc_solve_enum(int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
+                               const int32_t* pairs, const double* dgeom, const double* q, double* gamma)
+{
+    if (npairs > 20) return -1;
+    int m = (int)npairs;
+    double* A = (double*)malloc(sizeof(double) * (size_t)(m * m + 1));
+    orc_dense_A(n, quat, pb, npairs, pairs, dgeom, A);
+    double amax = 0.0, qmax = 0.0;
+    for (int c = 0; c < m; ++c) {
+        if (A[c * m + c] > amax) amax = A[c * m + c];
+        if (fabs(q[c]) > qmax) qmax = fabs(q[c]);
+    }
+    double* sub = (double*)malloc(sizeof(double) * (size_t)(m * m + 1));
+    double* rhs = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+    int idx[32];
+    int64_t found = -1;
+    for (int64_t mask = 0; mask < ((int64_t)1 << m) && found < 0; ++mask) {
+        int k = 0;
+        for (int c = 0; c < m; ++c) if (mask >> c & 1) idx[k++] = c;
+        for (int r = 0; r < k; ++r) {
+            for (int c = 0; c < k; ++c) sub[r * k + c] = A[idx[r] * m + idx[c]];
+            rhs[r] = -q[idx[r]];
+        }
+        if (k > 0 && !small_solve(k, sub, rhs, 1e-10 * amax)) continue;
+        int ok = 1;
+        for (int r = 0; r < k; ++r) if (rhs[r] < -1e-12 * (1.0 + qmax / (amax > 0 ? amax : 1.0))) { ok = 0; break; }
+        if (!ok) continue;
+        for (int c = 0; c < m; ++c) gamma[c] = 0.0;
+        for (int r = 0; r < k; ++r) gamma[idx[r]] = rhs[r] > 0.0 ? rhs[r] : 0.0;
+        for (int c = 0; c < m && ok; ++c) {
+            if (mask >> c & 1) continue;
+            double g = q[c];
+            for (int r = 0; r < m; ++r) g += A[c * m + r] * gamma[r];
+            if (g < -1e-9 * (1.0 + qmax)) ok = 0;
+        }
+        if (ok) found = mask;
+    }
+    free(A); free(sub); free(rhs);
+    return found;
+}
+
+/* Accelerated projected gradient (FISTA, Beck & Teboulle 2009) with the
+ * gradient restart of O'Donoghue & Candes 2015 on the CQP
+ *   min 1/2 gamma^T A gamma + q^T gamma,  gamma >= 0,  A = D^T M D
+ * (Eq. suppcqpdef; the paper solves it with BBPGD, the GPU path does too;
+ * the oracle uses a different method that converges to the same KKT point).
+ * Step 1/Lip with Lip = 1.1 x the power-iteration estimate of lambda_max(A).
+ * Stops when the residual (reading R6) is <= tol or after max_iter
+ * iterations; the residual is evaluated every 10 iterations.
+ * gamma holds the start on entry (negative entries are projected to 0) and
+ * the result on exit.  Returns the final residual; *iters gets the count. */
+ORC_API double orc_solve_apgd(int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
+                              const int32_t* pairs, const double* dgeom, const double* q, double* gamma,
+                              double tol, int64_t max_iter, int64_t* iters)
+{
+    orc_qp qp;
+    qp_init(&qp, n, quat, pb, npairs, pairs, dgeom, q);
+    size_t m = (size_t)(npairs > 0 ? npairs : 1);
+    double* v = (double*)malloc(sizeof(double) * m);
+    double* w = (double*)malloc(sizeof(double) * m);
+    double* z = (double*)malloc(sizeof(double) * m);
+    double* gz = (double*)malloc(sizeof(double) * m);
+    double* gn = (double*)malloc(sizeof(double) * m);
+    /* power iteration for lambda_max */
+    for (int64_t c = 0; c < npairs; ++c) v[c] = 1.0 + 0.25 * (double)((c * 7919) % 13) / 13.0;
+    double lam = 0.0;
+    for (int it = 0; it < 200 && npairs > 0; ++it) {
+        double nv = 0.0;
+        for (int64_t c = 0; c < npairs; ++c) nv += v[c] * v[c];
+        nv = sqrt(nv);
+        if (nv == 0.0) break;
+        for (int64_t c = 0; c < npairs; ++c) v[c] /= nv;
+        qp_matvec(&qp, v, w);
+        double rq = 0.0;
+        for (int64_t c = 0; c < npairs; ++c) rq += v[c] * w[c];
+        lam = rq;
+        memcpy(v, w, sizeof(double) * (size_t)npairs);
+    }
+    double lip = 1.1 * lam;
+    if (!(lip > 0.0)) lip = 1.0;
+    for (int64_t c = 0; c < npairs; ++c) {
+        if (!(gamma[c] > 0.0)) gamma[c] = 0.0;
+        z[c] = gamma[c];
+    }
+    double t = 1.0, res = INFINITY;
+    int64_t it = 0;
+    for (;;) {
+        if (it % 10 == 0) {
+            qp_matvec(&qp, gamma, gn);
+            for (int64_t c = 0; c < npairs; ++c) gn[c] += q[c];
+            res = qp_residual(&qp, gamma, gn, pb);
+            if (res <= tol || it >= max_iter) break;
+        }
+        qp_matvec(&qp, z, gz);
+        for (int64_t c = 0; c < npairs; ++c) gz[c] += q[c];
+        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        double restart = 0.0;
+        for (int64_t c = 0; c < npairs; ++c) {
+            double gnew = z[c] - gz[c] / lip;
+            if (gnew < 0.0) gnew = 0.0;
+            w[c] = gnew;
+            restart += gz[c] * (gnew - gamma[c]);
+        }
+        double beta = (t - 1.0) / tn;
+        if (restart > 0.0) { tn = 1.0; beta = 0.0; }
+        for (int64_t c = 0; c < npairs; ++c) {
+            z[c] = w[c] + beta * (w[c] - gamma[c]);
+            gamma[c] = w[c];
+        }
+        t = tn;
+        ++it;
+    }
+    if (iters) *iters = it;
+    free(v); free(w); free(z); free(gz); free(gn);
+    qp_free(&qp);
+    return res;
+}
+
+/* ----------------------------------------------------------------- update */
+
+/* C^{k+1} = C^k + h G U (Eq. constrainedeom_euler a), U = M (F_nc + D gamma):
+ *   x' = wrap(x + h U_t),
+ *   theta' = normalise(theta + h Psi(theta) Omega),
+ *   Psi(theta) Omega = 1/2 [ -v.Omega ; s Omega - v x Omega ]
+ * (Appendix, Psi = 1/2 [-p^T; sI - P], P_ij = eps_ikj p_k, so P Omega = v x Omega).
+ * U_out (nullable) receives U = M (F_nc + D gamma). */
+ORC_API void orc_update(int64_t n, const double* x, const double* quat, const double* fnc, const orc_problem* pb,
+                        int64_t npairs, const int32_t* pairs, const double* dgeom, const double* gamma,
+                        double* x_out, double* quat_out, double* U_out)
+{
+    double zeta[4];
+    orc_drag(pb->viscosity, pb->length, pb->diameter, zeta);
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double* F = (double*)malloc(sizeof(double) * 6 * nn);
+    double* axis = (double*)malloc(sizeof(double) * 3 * nn);
+    orc_apply_D(n, npairs, pairs, dgeom, gamma, F);
+    orc_axis(n, quat, axis);
+    for (int64_t i = 0; i < n; ++i) {
+        double Fi[6], Ui[6];
+        for (int k = 0; k < 6; ++k) Fi[k] = fnc[6 * i + k] + F[6 * i + k];
+        mobility_rod(axis + 3 * i, zeta, Fi, Ui);
+        if (U_out) for (int k = 0; k < 6; ++k) U_out[6 * i + k] = Ui[k];
+        for (int k = 0; k < 3; ++k) x_out[3 * i + k] = wrap1(wrap1(x[3 * i + k], pb->box[k]) + pb->dt * Ui[k], pb->box[k]);
+        const double* th = quat + 4 * i;
+        double s = th[0];
+        const double* v = th + 1;
+        const double* om = Ui + 3;
+        double vxo[3];
+        cross3(v, om, vxo);
+        double qn[4];
+        qn[0] = s + pb->dt * 0.5 * (-dot3(v, om));
+        for (int k = 0; k < 3; ++k) qn[1 + k] = v[k] + pb->dt * 0.5 * (s * om[k] - vxo[k]);
+        double nq = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+        for (int k = 0; k < 4; ++k) quat_out[4 * i + k] = qn[k] / nq;
+    }
+    free(F); free(axis);
+}
+
+/* ------------------------------------------------------------- full step */
+
+/* One constrained step: pairs -> assembly -> solve -> update.  Arrays sized
+ * by the caller: pairs cap = max_pairs triples.  Returns the pair count
+ * (or -count-1 if max_pairs was too small; nothing else is then written). */
+ORC_API int64_t orc_step(int64_t n, const double* x, const double* quat, const double* fnc, const orc_problem* pb,
+                         double tol, int64_t max_iter, int64_t max_pairs, int32_t* pairs, double* gamma,
+                         double* x_out, double* quat_out, double* U_out, double* residual, int64_t* iters)
+{
+    int64_t np = orc_find_pairs(n, x, quat, pb, NULL, 0, pairs, max_pairs);
+    if (np > max_pairs) return -np - 1;
+    size_t m = (size_t)(np > 0 ? np : 1);
+    double* phi = (double*)malloc(sizeof(double) * m);
+    double* dg = (double*)malloc(sizeof(double) * 9 * m);
+    double* q = (double*)malloc(sizeof(double) * m);
+    orc_assemble(n, x, quat, fnc, pb, np, pairs, phi, dg, q, NULL, NULL);
+    for (int64_t c = 0; c < np; ++c) gamma[c] = 0.0;
+    double r = orc_solve_apgd(n, quat, pb, np, pairs, dg, q, gamma, tol, max_iter, iters);
+    if (residual) *residual = r;
+    orc_update(n, x, quat, fnc, pb, np, pairs, dg, gamma, x_out, quat_out, U_out);
+    free(phi); free(dg); free(q);
+    return np;
+}
