@@ -1,0 +1,385 @@
+"""Benchmark of the collision-constraint step: rod-steps/s at 1e5 rods.
+
+One step = neighbour search + constraint assembly + BBPGD solve + update
+(the whole hot path) over the 100,000-rod suspension (volume fraction 0.10,
+isotropic, thermal forces plus 50,000 explicit crosslinker springs; seeded,
+synthetic).  Every timed step starts from the same input state, restored
+outside the timed region, and L2 is flushed (256 MB write) between steps.
+
+Reported (one JSON line on rank 0):
+  value        rod-steps/s of the FP32-mixed step at residual <= 1e-5 (device
+               events on the library's stream around aLENS_step, inputs
+               resident in HBM);
+  fp64         the same for the FP64-plain step at the same residual;
+  e2e          the same metric through the C ABI with host buffers: pinned
+               host -> device copy of x, quat, f_nc, the step, and the
+               device -> host copy of x and quat inside the timed region;
+  roofline     the BBPGD kernel (dominant): algorithmic bytes per launch
+               (iterations x per-iteration bytes of the solve) / its event time
+               vs the measured HBM copy bandwidth;
+  cpu_baseline the CPU oracle timed on a bounded spatial sample of the same
+               workload on this host's cores.
+  --impl reference times that oracle alone (the reference arm).
+Multi-GPU (torchrun): independent replicas, one per rank, no collective on
+the data path; value = rods x steps of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "rod-steps/s at 1e5 rods, FP32-mixed vs FP64 plain at residual ≤1e-5"
+UNIT = "rod-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n100k_phi010")
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--sample-rods", type=int, default=10000, help="rods in the oracle's spatial sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            d = json.loads(p.read_text())
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d and isinstance(d[k], (int, float)):
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.idx = device_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            sel = ["-i", str(self.idx)] if self.idx is not None else []
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", *sel], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [v.strip() for v in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def solve_bytes_per_iter(n, m, w):
+    """Algorithmic bytes of one BBPGD iteration: per constraint 24w + 24
+    (D record read by the rod gather and by D^T, gamma x3, g x2, q, two CSR
+    entries), per rod 15w + 4 (axis, U write, U read, row pointer)."""
+    return m * (24 * w + 24) + n * (15 * w + 4)
+
+
+def traffic_from_profile(kernel_src: Path):
+    """DRAM bytes per BBPGD iteration from the committed ncu summary, only if
+    the kernel source is unchanged since the capture (sha256 recorded there)."""
+    prof = ROOT / "profiles" / "k_bbpgd_n100k_mixed.md"
+    if not prof.exists():
+        return None
+    sha = hashlib.sha256(kernel_src.read_bytes()).hexdigest()[:16]
+    txt = prof.read_text()
+    src_line = [l for l in txt.splitlines() if l.startswith("solve_cu_sha256_16:")]
+    val_line = [l for l in txt.splitlines() if l.startswith("dram_bytes_per_iteration:")]
+    if not src_line or not val_line or src_line[0].split(":", 1)[1].strip() != sha:
+        return None
+    return float(val_line[0].split(":", 1)[1].strip())
+
+
+def spatial_sample(s, target):
+    """Rods of the workload whose centres fall in the cube [0, a)^3, with a
+    chosen so that about `target` rods fall inside; the cube is treated as a
+    periodic system of its own (same density, orientations and forces)."""
+    from paper_2109_08206_gb300 import workloads as W
+    box = np.asarray(s.box)
+    frac = (target / s.n) ** (1.0 / 3.0)
+    a = max(float(box.min() * frac), s.length + s.diameter + s.delta_c + 1e-6)
+    sel = np.all(s.x < a, axis=1)
+    sub = W.RodSystem(x=s.x[sel].copy(), quat=s.quat[sel].copy(), f_nc=s.f_nc[sel].copy(), box=(a, a, a),
+                      diameter=s.diameter, length=s.length, viscosity=s.viscosity, dt=s.dt, delta_c=s.delta_c,
+                      tol=s.tol, name=s.name + "_sample")
+    return sub, a
+
+
+def oracle_step_time(s, tol, reps=1):
+    import oracle as O
+    pb = O.problem_of(s)
+    times, out = [], None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        out = O.step_native(s.x, s.quat, s.f_nc, pb, tol, 10_000_000, max(64, 30 * s.n))
+        times.append(time.perf_counter() - t0)
+    return statistics.median(times), out
+
+
+def cpu_cores():
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS") or len(os.sched_getaffinity(0)))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2109_08206_gb300 import workloads as W
+    s = W.workload(args.workload)
+    sub, a = spatial_sample(s, args.sample_rods)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_step_time(sub, args.tol)
+    times = []
+    for _ in range(args.steps):
+        t, out = oracle_step_time(sub, args.tol)
+        times.append(t)
+    t = statistics.mean(times)
+    v = sub.n / t
+    sample = (f"{sub.n} rods of the {s.name} workload with centres in a periodic sub-cube of edge {a:.2f} "
+              f"(same density, orientations, forces); full oracle step (brute-force pairs, FISTA to the same "
+              f"residual {args.tol:g}, update)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload} (oracle on a {sub.n}-rod sample)", "rods": sub.n,
+                       "pairs": int(out["n_pairs"]), "tol": args.tol},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    import paper_2109_08206_gb300 as A
+    from paper_2109_08206_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    A.build()
+    dev = torch.device("cuda", local)
+    s = W.workload(args.workload)
+    n = s.n
+    stream = torch.cuda.Stream(device=dev)
+    x0 = torch.as_tensor(s.x, device=dev)
+    q0 = torch.as_tensor(s.quat, device=dev)
+    f = torch.as_tensor(s.f_nc, device=dev)
+    x, q = x0.clone(), q0.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    max_pairs = 12 * n
+
+    def make_ctx(precision):
+        p = A.params_of(s, precision=precision, tol=args.tol, max_iter=1_000_000)
+        return A.Context(p, n, max_pairs, stream=stream)
+
+    def timed(ctx, K, W_, host=None):
+        """K timed steps after W_ warm-ups; returns per-step ms and infos."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        infos = []
+        with torch.cuda.stream(stream):
+            for k in range(W_ + K):
+                if host is None:
+                    x.copy_(x0); q.copy_(q0)
+                flush.fill_(float(k))
+                if k >= W_:
+                    ev[k - W_][0].record(stream)
+                if host is None:
+                    info = ctx.step(x, q, f)
+                else:
+                    hx, hq, hf, ox, oq = host
+                    x.copy_(hx, non_blocking=True); q.copy_(hq, non_blocking=True); f.copy_(hf, non_blocking=True)
+                    info = ctx.step(x, q, f)
+                    ox.copy_(x, non_blocking=True); oq.copy_(q, non_blocking=True)
+                if k >= W_:
+                    ev[k - W_][1].record(stream)
+                    infos.append(info.as_dict())
+            stream.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], infos
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+
+    def max_over_ranks(v):
+        if pg is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- FP32-mixed: the headline
+    ctx = make_ctx(A.MIXED)
+    barrier()
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    with Clocks(gpu_id) as clk:
+        t0 = time.perf_counter()
+        ms, infos = timed(ctx, args.steps, args.warmup)
+        barrier()
+        wall = time.perf_counter() - t0
+    ms_step = max_over_ranks(statistics.mean(ms))
+    value = ws * n / (ms_step / 1e3)
+    it = [i["iters"] for i in infos]
+    ms_solve = statistics.mean(i["ms_solve"] for i in infos)
+    m = infos[-1]["n_pairs"]
+    res = max(i["residual"] for i in infos)
+    launches = sum(i["launches"] for i in infos)
+    b_iter = solve_bytes_per_iter(n, m, 4)
+    alg_bytes = statistics.mean(it) * b_iter
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (ms_solve / 1e3) / 1e9
+    tr = traffic_from_profile(ROOT / "paper_2109_08206_gb300" / "csrc" / "solve.cu")
+    traffic = None if tr is None else tr * statistics.mean(it)
+
+    # ---- FP64 plain at the same residual
+    fp64 = None
+    if not args.skip_fp64:
+        ctx64 = make_ctx(A.FP64)
+        ms64, inf64 = timed(ctx64, max(2, args.steps // 2), 1)
+        ms64_step = max_over_ranks(statistics.mean(ms64))
+        fp64 = {"value": ws * n / (ms64_step / 1e3), "unit": UNIT, "ms_per_step": ms64_step,
+                "bbpgd_iters": statistics.mean(i["iters"] for i in inf64),
+                "residual": max(i["residual"] for i in inf64),
+                "ms_solve": statistics.mean(i["ms_solve"] for i in inf64),
+                "solve_bytes_per_iter": solve_bytes_per_iter(n, m, 8)}
+        ctx64.close()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.skip_e2e:
+        hx = torch.as_tensor(s.x).pin_memory(); hq = torch.as_tensor(s.quat).pin_memory()
+        hf = torch.as_tensor(s.f_nc).pin_memory()
+        ox = torch.empty_like(hx).pin_memory(); oq = torch.empty_like(hq).pin_memory()
+        mse, _ = timed(ctx, args.steps, 1, host=(hx, hq, hf, ox, oq))
+        mse_step = max_over_ranks(statistics.mean(mse))
+        e2e = {"value": ws * n / (mse_step / 1e3), "unit": UNIT, "ms_per_step": mse_step,
+               "h2d_bytes_per_step": int(hx.numel() * 8 + hq.numel() * 8 + hf.numel() * 8),
+               "d2h_bytes_per_step": int(ox.numel() * 8 + oq.numel() * 8)}
+    ctx.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.skip_cpu and ws == 1:
+        sub, a = spatial_sample(s, args.sample_rods)
+        t_cpu, out = oracle_step_time(sub, args.tol)
+        cpu = {"value": sub.n / t_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{sub.n} rods of {s.name} with centres in a periodic sub-cube of edge {a:.2f}; one full "
+                         f"oracle step (brute-force pairs, FISTA to residual {args.tol:g}, update), {t_cpu:.2f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-mixed (f64 geometry, residual, reductions)", "data": "synthetic",
+        "config": {"workload": s.name, "rods": n, "pairs": m, "box": round(float(s.box[0]), 3),
+                   "volume_fraction": 0.10, "springs": s.meta.get("springs"), "tol": args.tol,
+                   "l2": "flushed (256 MB write) between steps; inputs restored outside the timed region",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "bbpgd_iters": statistics.mean(it), "residual": res,
+        "phase_ms": {k: statistics.mean(i[k] for i in infos) for k in ("ms_build", "ms_assemble", "ms_solve",
+                                                                         "ms_update")},
+        "fp64": fp64, "e2e": e2e,
+        "roofline": {"kernel": "k_bbpgd<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_iter": b_iter},
+        "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary(), "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

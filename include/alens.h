@@ -1,0 +1,181 @@
+/*
+ * alens.h - C ABI of the GB300 library for the hard-body collision-constraint
+ * step of aLENS (Yan et al., arXiv 2109.08206).
+ *
+ * One step takes N rigid spherocylinders (diameter D, cylinder length L) in a
+ * periodic box with given non-constraint forces F_nc and a time step h, and
+ *   1. finds every rod pair (and periodic image) whose surface gap is below
+ *      delta_c                    (Appendix "Implementation", near-neighbour
+ *                                  detection with threshold delta_c),
+ *   2. builds the gap Phi, the sparse constraint matrix D and
+ *      q = Phi/h + D^T M F_nc     (Appendix Eq. blockdef, block A; Eq. dmap),
+ *   3. solves the convex QP  min 1/2 g^T (D^T M D) g + q^T g,  g >= 0
+ *      by Barzilai-Borwein projected gradient descent
+ *                                 (Appendix Eq. suppcqpdef; Section
+ *                                  "Instantiation...": BBPGD),
+ *   4. moves the rods: U = M (F_nc + D gamma), C' = C + h G U
+ *                                 (Appendix Eq. constrainedeom_euler a-c).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Array arguments are DEVICE pointers to caller-owned, contiguous,
+ *   row-major memory on the context's device.  The library never frees a
+ *   caller pointer and keeps none after a call returns.
+ * - x      [n][3] float64  rod centres (any real value; wrapped into [0, box)).
+ * - quat   [n][4] float64  unit quaternions (s, v1, v2, v3); the rod axis is
+ *                          p = R(quat) e_z.  |quat| must be within 1e-6 of 1.
+ * - f_nc   [n][6] float64  non-constraint force (3) then torque (3), lab frame.
+ * - pairs  [m][3] int32    (i, j, image) with i < j, sorted by (i, j, image);
+ *                          image = (kx+1) + 3(ky+1) + 9(kz+1), k in {-1,0,1}^3,
+ *                          and the centre offset of the pair is
+ *                          dx = x_i - x_j - k * box (wrapped centres).
+ * - dgeom  [m][9] float64  per constraint (e, y_P x e, y_Q x e): e = r/|r| is
+ *                          the unit normal from Q to P, y_P / y_Q the contact
+ *                          arms from the rod centres; the column of D acting on
+ *                          rod P is (e, y_P x e), on rod Q (-e, -(y_Q x e)).
+ * - phi    [m] float64     surface gap |r| - D (negative when overlapping).
+ * - gamma  [m] float64     constraint force magnitudes (>= 0, repulsive).
+ * - Mobility per rod (the paper quotes only the slender-body coefficient
+ *   4 pi eta L / ln(2L/D)): zeta_perp = 4 pi eta L / ln(2L/D),
+ *   zeta_par = zeta_perp/2, zeta_rot = zeta_perp L^2/12, zeta_spin =
+ *   pi eta D^2 L; M_t = p p^T/zeta_par + (I - p p^T)/zeta_perp and
+ *   M_r = p p^T/zeta_spin + (I - p p^T)/zeta_rot.
+ * - Residual (the paper does not define one): r = (h/D) max_c |pi_c| with
+ *   pi_c = g_c if gamma_c > 0 else min(g_c, 0), g = D^T M D gamma + q; it is
+ *   the worst linearised post-step gap error in rod diameters.
+ * - All work is ordered on the context's CUDA stream.  Entry points that
+ *   return counts or an aLENS_info synchronise that stream before returning.
+ * - Errors are returned, never raised: ALENS_ERR_INVALID before any output
+ *   is written, ALENS_ERR_CAPACITY with the required size, ALENS_ERR_TIMEOUT
+ *   when a bounded device wait ran out (the context stays usable),
+ *   ALENS_ERR_NOT_CONVERGED with outputs and the residual filled in.
+ * - A context is not thread-safe; use one per host thread.
+ */
+#ifndef ALENS_H
+#define ALENS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ALENS_API __attribute__((visibility("default")))
+#else
+#define ALENS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ALENS_OK = 0,
+    ALENS_ERR_INVALID = 1,        /* bad argument or input (NaN, non-unit quaternion, box too small) */
+    ALENS_ERR_CAPACITY = 2,       /* a buffer is too small; the required count is reported */
+    ALENS_ERR_NOT_CONVERGED = 3,  /* max_iter reached; outputs and residual are valid */
+    ALENS_ERR_TIMEOUT = 4,        /* a bounded grid-wide wait gave up; outputs undefined */
+    ALENS_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    ALENS_ERR_NOMEM = 6,          /* workspace allocation failed */
+    ALENS_ERR_NOT_IMPLEMENTED = 7
+} aLENS_status;
+
+typedef enum {
+    ALENS_FP64 = 0,   /* every stage in float64 */
+    ALENS_MIXED = 1   /* solver iterations (D, M, D^T) in float32; geometry, pair
+                         decisions, the residual and all reductions in float64 */
+} aLENS_precision;
+
+typedef struct {
+    double box[3];      /* periodic edge lengths; each >= length + diameter + delta_c */
+    double diameter;    /* D (the paper's D_fil) */
+    double length;      /* L, cylinder length without the caps */
+    double viscosity;   /* eta; every drag coefficient is proportional to it */
+    double dt;          /* h */
+    double delta_c;     /* pair threshold on the surface gap (paper: delta_c = D) */
+    double tol;         /* residual tolerance, rod diameters */
+    int32_t max_iter;   /* BBPGD iteration cap */
+    int32_t precision;  /* aLENS_precision */
+} aLENS_params;
+
+typedef struct {
+    int64_t n_pairs;    /* constraints in the step */
+    int64_t n_overlap;  /* constraints with phi < 0 */
+    int32_t iters;      /* BBPGD iterations taken */
+    int32_t status;     /* aLENS_status of the call */
+    double residual;    /* final residual (rod diameters) */
+    double min_gap;     /* min phi over the constraints (+inf if none) */
+    float ms_build;     /* device time of the neighbour search */
+    float ms_assemble;  /* device time of the assembly and CSR build */
+    float ms_solve;     /* device time of the BBPGD kernel alone */
+    float ms_update;    /* device time of the update */
+    int32_t launches;   /* kernels the call launched */
+} aLENS_info;
+
+typedef struct aLENS_ctx aLENS_ctx;
+
+/* Create a context on the current CUDA device.  Workspaces for up to
+ * max_rods rods and max_pairs constraints are allocated here and owned by
+ * the context.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  Returns INVALID for bad parameters, NOMEM/CUDA on failure. */
+ALENS_API aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t max_pairs,
+                          void* cuda_stream, aLENS_ctx** out);
+
+/* Release every workspace of the context (synchronises its stream).  NULL is ignored. */
+ALENS_API void aLENS_destroy(aLENS_ctx* ctx);
+
+/* Replace the step parameters.  Returns CAPACITY if the new box needs more
+ * cells than the context allocated at create time, INVALID for bad values. */
+ALENS_API aLENS_status aLENS_set_params(aLENS_ctx* ctx, const aLENS_params* params);
+
+/* Static description of a status code. */
+ALENS_API const char* aLENS_status_string(aLENS_status status);
+
+/* Neighbour search (Appendix "Implementation": close pairs whose minimal
+ * distance is below delta_c).  Writes the sorted pair list into pairs
+ * (capacity pairs_cap triples) and the count into *n_pairs (host pointer).
+ * On CAPACITY *n_pairs is the required count and pairs is unspecified.
+ * The keep/drop decision of every pair is taken in float64. */
+ALENS_API aLENS_status aLENS_build_neighbors(aLENS_ctx* ctx, int64_t n, const double* x, const double* quat,
+                                   int32_t* pairs, int64_t pairs_cap, int64_t* n_pairs);
+
+/* Constraint assembly for a sorted pair list (Appendix Eq. blockdef A and
+ * the column D_PQ = [e_P, y_P x e_P, e_Q, y_Q x e_Q], e_Q = -e_P):
+ * phi[m], dgeom[m][9] and q[m] = phi/h + D^T M f_nc, all float64. */
+ALENS_API aLENS_status aLENS_assemble_constraints(aLENS_ctx* ctx, int64_t n, const double* x, const double* quat,
+                                        const double* f_nc, int64_t n_pairs, const int32_t* pairs,
+                                        double* phi, double* dgeom, double* q);
+
+/* BBPGD solve of the CQP (Appendix Eq. suppcqpdef) for given D (dgeom) and
+ * q.  gamma is read as the start (negative entries projected to 0; pass
+ * zeros for a cold start) and overwritten with the solution.  info (host
+ * pointer, may be NULL) receives iterations and residual. */
+ALENS_API aLENS_status aLENS_solve_lcp(aLENS_ctx* ctx, int64_t n, const double* quat, int64_t n_pairs,
+                             const int32_t* pairs, const double* dgeom, const double* q, double* gamma,
+                             aLENS_info* info);
+
+/* One full constrained step: neighbours -> assembly -> BBPGD -> update.
+ * x and quat are updated in place (x wrapped into [0, box), quat
+ * renormalised).  gamma_out (nullable, capacity max_pairs of the context)
+ * receives gamma in pair order; vel_out (nullable, [n][6]) receives
+ * U = M (f_nc + D gamma).  pairs_out (nullable, capacity max_pairs triples)
+ * receives the pair list.  info (host pointer, may be NULL). */
+ALENS_API aLENS_status aLENS_step(aLENS_ctx* ctx, int64_t n, double* x, double* quat, const double* f_nc,
+                        int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info);
+
+/* Bound on every grid-wide wait inside the solver kernel, in seconds
+ * (default 5).  A wait that runs out makes the call return ALENS_ERR_TIMEOUT. */
+ALENS_API aLENS_status aLENS_set_wait_limit(aLENS_ctx* ctx, double seconds);
+
+/* Test hook: mode 1 makes one thread block of the next solver launch leave
+ * before its first grid-wide arrival, so that the other blocks' bounded
+ * waits run out and the call returns ALENS_ERR_TIMEOUT.  The hook clears
+ * itself after one launch.  mode 0 disables it. */
+ALENS_API aLENS_status aLENS_inject_fault(aLENS_ctx* ctx, int32_t mode);
+
+/* Launch shape of the solver kernel: threads per block (multiple of 32,
+ * <= 1024) and blocks per SM (0 = as many as fit).  For tuning. */
+ALENS_API aLENS_status aLENS_set_launch(aLENS_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALENS_H */

@@ -55,7 +55,8 @@ def lib():
             "orc_axis": (None, [i64, vp, vp]),
             "orc_wrap": (None, [i64, vp, vp, vp]),
             "orc_segment_closest": (d, [vp, vp, vp, d, vp, vp]),
-            "orc_find_pairs": (i64, [i64, vp, vp, P, vp, i64, vp, i64]),
+            "orc_find_pairs": (i64, [i64, vp, vp, P, vp, i64]),
+            "orc_find_pairs_rows": (i64, [i64, vp, vp, P, vp, i64, vp, i64]),
             "orc_pair_gaps": (None, [i64, vp, vp, P, i64, vp, vp]),
             "orc_mobility_apply": (None, [i64, vp, P, vp, vp]),
             "orc_assemble": (None, [i64, vp, vp, vp, P, i64, vp, vp, vp, vp, vp, vp]),
@@ -128,11 +129,15 @@ def segment_closest(dx, p, q, length):
 def find_pairs(x, quat, pb: Problem, rows=None):
     x, quat = _f64(x, (-1, 3)), _f64(quat, (-1, 4))
     n = x.shape[0]
-    r = None if rows is None else np.ascontiguousarray(np.unique(np.asarray(rows, dtype=np.int64)))
-    nr = 0 if r is None else r.shape[0]
-    cnt = lib().orc_find_pairs(n, _p(x), _p(quat), C.byref(pb), _p(r), nr, None, 0)
-    out = np.zeros((max(cnt, 1), 3), dtype=np.int32)
-    cnt2 = lib().orc_find_pairs(n, _p(x), _p(quat), C.byref(pb), _p(r), nr, _p(out), cnt)
+    if rows is None:
+        cnt = lib().orc_find_pairs(n, _p(x), _p(quat), C.byref(pb), None, 0)
+        out = np.zeros((max(cnt, 1), 3), dtype=np.int32)
+        cnt2 = lib().orc_find_pairs(n, _p(x), _p(quat), C.byref(pb), _p(out), cnt)
+    else:
+        r = np.ascontiguousarray(np.unique(np.asarray(rows, dtype=np.int64)))
+        cnt = lib().orc_find_pairs_rows(n, _p(x), _p(quat), C.byref(pb), _p(r), r.shape[0], None, 0)
+        out = np.zeros((max(cnt, 1), 3), dtype=np.int32)
+        cnt2 = lib().orc_find_pairs_rows(n, _p(x), _p(quat), C.byref(pb), _p(r), r.shape[0], _p(out), cnt)
     assert cnt2 == cnt
     return out[:cnt]
 

@@ -221,43 +221,35 @@ static int pair_gap(const double* xw, const double* axis, const orc_problem* pb,
 
 /* All pairs (i < j, image) whose surface gap is below delta_c, in (i, j, code)
  * order (Appendix "Implementation": close pairs whose minimal distance is
- * below delta_c).  If rows != NULL only pairs with i or j in rows[0..nrows)
- * are listed (rows must be sorted ascending and unique).  Writes at most cap
- * pairs (int32 triples) and returns the full count. */
+ * below delta_c).  Writes at most cap pairs (int32 triples) and returns the
+ * full count. */
 ORC_API int64_t orc_find_pairs(int64_t n, const double* x, const double* quat, const orc_problem* pb,
-                               const int64_t* rows, int64_t nrows, int32_t* pairs, int64_t cap)
+                               int32_t* pairs, int64_t cap)
 {
     double* xw = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double* axis = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     orc_wrap(n, x, pb->box, xw);
     orc_axis(n, quat, axis);
-    char* mark = NULL;
-    if (rows) {
-        mark = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
-        for (int64_t r = 0; r < nrows; ++r) mark[rows[r]] = 1;
-    }
     int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
     /* pass 1: count per i */
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n; ++i) {
         int64_t c = 0;
-        for (int64_t j = i + 1; j < n; ++j) {
-            if (mark && !mark[i] && !mark[j]) continue;
+        for (int64_t j = i + 1; j < n; ++j)
             for (int code = 0; code < 27; ++code) {
                 double gap, s, t, dx[3];
                 if (pair_gap(xw, axis, pb, i, j, code, &gap, &s, &t, dx) && gap < pb->delta_c) ++c;
             }
-        }
         cnt[i + 1] = c;
     }
     for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
     int64_t total = cnt[n];
     if (total <= cap && pairs) {
+        /* pass 2: write, each i into its own slot range */
 #pragma omp parallel for schedule(dynamic, 16)
         for (int64_t i = 0; i < n; ++i) {
             int64_t o = cnt[i];
-            for (int64_t j = i + 1; j < n; ++j) {
-                if (mark && !mark[i] && !mark[j]) continue;
+            for (int64_t j = i + 1; j < n; ++j)
                 for (int code = 0; code < 27; ++code) {
                     double gap, s, t, dx[3];
                     if (pair_gap(xw, axis, pb, i, j, code, &gap, &s, &t, dx) && gap < pb->delta_c) {
@@ -267,11 +259,63 @@ ORC_API int64_t orc_find_pairs(int64_t n, const double* x, const double* quat, c
                         ++o;
                     }
                 }
+        }
+    }
+    free(cnt); free(xw); free(axis);
+    return total;
+}
+
+static int cmp_triple(const void* a, const void* b)
+{
+    const int32_t* u = (const int32_t*)a;
+    const int32_t* v = (const int32_t*)b;
+    for (int k = 0; k < 3; ++k)
+        if (u[k] != v[k]) return u[k] < v[k] ? -1 : 1;
+    return 0;
+}
+
+/* The pairs of the full list that involve at least one rod of rows[0..nrows):
+ * for every listed rod r and every other rod j, each image of the pair is
+ * tested in the canonical orientation (min(r,j), max(r,j)); when r > j the
+ * image shift is negated (code -> 26 - code).  Sorted, duplicates removed.
+ * Returns the count; writes at most cap triples. */
+ORC_API int64_t orc_find_pairs_rows(int64_t n, const double* x, const double* quat, const orc_problem* pb,
+                                    const int64_t* rows, int64_t nrows, int32_t* pairs, int64_t cap)
+{
+    double* xw = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double* axis = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    orc_wrap(n, x, pb->box, xw);
+    orc_axis(n, quat, axis);
+    int64_t room = 64, used = 0;
+    int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)room);
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t a = rows[r];
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == a) continue;
+            int64_t i = a < j ? a : j, jj = a < j ? j : a;
+            for (int code = 0; code < 27; ++code) {
+                double gap, s, t, dx[3];
+                if (pair_gap(xw, axis, pb, i, jj, code, &gap, &s, &t, dx) && gap < pb->delta_c) {
+                    if (used == room) {
+                        room *= 2;
+                        buf = (int32_t*)realloc(buf, sizeof(int32_t) * 3 * (size_t)room);
+                    }
+                    buf[3 * used] = (int32_t)i; buf[3 * used + 1] = (int32_t)jj; buf[3 * used + 2] = code;
+                    ++used;
+                }
             }
         }
     }
-    free(cnt); free(mark); free(xw); free(axis);
-    return total;
+    qsort(buf, (size_t)used, 3 * sizeof(int32_t), cmp_triple);
+    int64_t u = 0;
+    for (int64_t k = 0; k < used; ++k) {
+        if (u > 0 && cmp_triple(buf + 3 * k, buf + 3 * (u - 1)) == 0) continue;
+        if (u != k) memcpy(buf + 3 * u, buf + 3 * k, 3 * sizeof(int32_t));
+        ++u;
+    }
+    if (pairs && u <= cap) memcpy(pairs, buf, sizeof(int32_t) * 3 * (size_t)u);
+    free(buf); free(xw); free(axis);
+    return u;
 }
 
 /* Surface gaps of given pairs (for near-threshold accounting in tests). */
@@ -681,7 +725,7 @@ ORC_API int64_t orc_step(int64_t n, const double* x, const double* quat, const d
                          double tol, int64_t max_iter, int64_t max_pairs, int32_t* pairs, double* gamma,
                          double* x_out, double* quat_out, double* U_out, double* residual, int64_t* iters)
 {
-    int64_t np = orc_find_pairs(n, x, quat, pb, NULL, 0, pairs, max_pairs);
+    int64_t np = orc_find_pairs(n, x, quat, pb, pairs, max_pairs);
     if (np > max_pairs) return -np - 1;
     size_t m = (size_t)(np > 0 ? np : 1);
     double* phi = (double*)malloc(sizeof(double) * m);

@@ -1,0 +1,243 @@
+"""GB300 library for the hard-body collision-constraint step of aLENS
+(Yan et al., arXiv 2109.08206): cell-list neighbours, segment-segment
+constraint assembly, BBPGD complementarity solve and the rod update, as
+hand-written CUDA kernels for sm_103a behind the C ABI of ``include/alens.h``.
+
+This module is argument marshalling only: it loads ``_build/libalens.so``
+with ctypes and passes raw device pointers of torch tensors (PyTorch is used
+for device memory and streams).  Every step of the computation runs in the
+library's kernels; there is no CPU fallback, and importing the bindings
+fails loudly when the library has not been built (run ``build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+__all__ = ["build", "lib", "Params", "Info", "Context", "AlensError", "FP64", "MIXED", "STATUS"]
+
+_PKG = Path(__file__).resolve().parent
+_LIB_PATH = _PKG / "_build" / "libalens.so"
+
+FP64, MIXED = 0, 1
+STATUS = {0: "OK", 1: "INVALID", 2: "CAPACITY", 3: "NOT_CONVERGED", 4: "TIMEOUT", 5: "CUDA", 6: "NOMEM",
+          7: "NOT_IMPLEMENTED"}
+
+
+class Params(C.Structure):
+    """aLENS_params (include/alens.h)."""
+    _fields_ = [("box", C.c_double * 3), ("diameter", C.c_double), ("length", C.c_double),
+                ("viscosity", C.c_double), ("dt", C.c_double), ("delta_c", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("precision", C.c_int32)]
+
+
+class Info(C.Structure):
+    """aLENS_info (include/alens.h)."""
+    _fields_ = [("n_pairs", C.c_int64), ("n_overlap", C.c_int64), ("iters", C.c_int32), ("status", C.c_int32),
+                ("residual", C.c_double), ("min_gap", C.c_double), ("ms_build", C.c_float),
+                ("ms_assemble", C.c_float), ("ms_solve", C.c_float), ("ms_update", C.c_float),
+                ("launches", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AlensError(RuntimeError):
+    def __init__(self, status: int, where: str, extra=None):
+        self.status = status
+        self.extra = extra
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_status_string(status)})")
+
+
+def build(force: bool = False, verbose: bool = False) -> Path:
+    """Compile the CUDA library for sm_103a (see nvcc_build.py)."""
+    from . import nvcc_build
+    return nvcc_build.build(force=force, verbose=verbose)
+
+
+_lib = None
+
+
+def lib():
+    """The loaded C library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise RuntimeError(f"CUDA library missing: {_LIB_PATH} (call paper_2109_08206_gb300.build())")
+        L = C.CDLL(str(_LIB_PATH))
+        vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        PP, IP = C.POINTER(Params), C.POINTER(Info)
+        sig = {
+            "aLENS_create": (i32, [PP, i64, i64, vp, C.POINTER(vp)]),
+            "aLENS_destroy": (None, [vp]),
+            "aLENS_set_params": (i32, [vp, PP]),
+            "aLENS_status_string": (C.c_char_p, [i32]),
+            "aLENS_build_neighbors": (i32, [vp, i64, vp, vp, vp, i64, C.POINTER(i64)]),
+            "aLENS_assemble_constraints": (i32, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp]),
+            "aLENS_solve_lcp": (i32, [vp, i64, vp, i64, vp, vp, vp, vp, IP]),
+            "aLENS_step": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, IP]),
+            "aLENS_set_wait_limit": (i32, [vp, d]),
+            "aLENS_inject_fault": (i32, [vp, i32]),
+            "aLENS_set_launch": (i32, [vp, i32, i32]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names declared by include/alens.h (parsed from the header)."""
+    import re
+    text = (_PKG.parent / "include" / "alens.h").read_text()
+    return sorted(set(re.findall(r"\b(aLENS_[a-z_]+)\s*\(", text)))
+
+
+def _status_string(s: int) -> str:
+    try:
+        return lib().aLENS_status_string(int(s)).decode()
+    except Exception:
+        return "?"
+
+
+def make_params(box, diameter=1.0, length=10.0, viscosity=1.0, dt=1e-3, delta_c=None, tol=1e-8,
+                max_iter=100000, precision=FP64) -> Params:
+    b = box if hasattr(box, "__len__") else (box, box, box)
+    return Params((C.c_double * 3)(*[float(v) for v in b]), float(diameter), float(length), float(viscosity),
+                  float(dt), float(diameter if delta_c is None else delta_c), float(tol), int(max_iter),
+                  int(precision))
+
+
+def params_of(sys, precision=FP64, tol=None, max_iter=100000) -> Params:
+    """Params of a ``workloads.RodSystem``."""
+    return make_params(sys.box, sys.diameter, sys.length, sys.viscosity, sys.dt, sys.delta_c,
+                       sys.tol if tol is None else tol, max_iter, precision)
+
+
+def _ptr(t, dtype, shape_tail=None):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor, got {t.dtype}")
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"expected shape [*, {shape_tail}], got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One aLENS_ctx: workspaces for up to max_rods rods and max_pairs constraints,
+    bound to a CUDA stream (default: torch's current stream at creation)."""
+
+    def __init__(self, params: Params, max_rods: int, max_pairs: int, stream=None):
+        import torch
+        self._lib = lib()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.params = params
+        self.max_rods, self.max_pairs = int(max_rods), int(max_pairs)
+        h = C.c_void_p()
+        st = self._lib.aLENS_create(C.byref(params), self.max_rods, self.max_pairs,
+                                    C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise AlensError(st, "aLENS_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.aLENS_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -------------------------------------------------------------- settings
+    def set_params(self, params: Params):
+        st = self._lib.aLENS_set_params(self._h, C.byref(params))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_params")
+        self.params = params
+
+    def set_wait_limit(self, seconds: float):
+        st = self._lib.aLENS_set_wait_limit(self._h, float(seconds))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_wait_limit")
+
+    def inject_fault(self, mode: int):
+        st = self._lib.aLENS_inject_fault(self._h, int(mode))
+        if st != 0:
+            raise AlensError(st, "aLENS_inject_fault")
+
+    def set_launch(self, threads: int, blocks_per_sm: int = 0):
+        st = self._lib.aLENS_set_launch(self._h, int(threads), int(blocks_per_sm))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_launch")
+
+    # ------------------------------------------------------------ entry points
+    def build_neighbors(self, x, quat, pairs=None):
+        """Sorted pair list [m, 3] int32 (i, j, image) on the device."""
+        import torch
+        n = x.shape[0]
+        if pairs is None:
+            pairs = torch.empty((self.max_pairs, 3), dtype=torch.int32, device=x.device)
+        cnt = C.c_int64()
+        st = self._lib.aLENS_build_neighbors(self._h, n, _ptr(x, torch.float64, (3,)), _ptr(quat, torch.float64, (4,)),
+                                             _ptr(pairs, torch.int32, (3,)), pairs.shape[0], C.byref(cnt))
+        if st != 0:
+            raise AlensError(st, "aLENS_build_neighbors", cnt.value)
+        return pairs[:cnt.value]
+
+    def assemble_constraints(self, x, quat, f_nc, pairs):
+        """(phi [m], dgeom [m, 9], q [m]) float64 on the device."""
+        import torch
+        n, m = x.shape[0], pairs.shape[0]
+        dev = x.device
+        phi = torch.empty(m, dtype=torch.float64, device=dev)
+        dgeom = torch.empty((m, 9), dtype=torch.float64, device=dev)
+        q = torch.empty(m, dtype=torch.float64, device=dev)
+        st = self._lib.aLENS_assemble_constraints(
+            self._h, n, _ptr(x, torch.float64, (3,)), _ptr(quat, torch.float64, (4,)),
+            _ptr(f_nc, torch.float64, (6,)), m, _ptr(pairs.contiguous(), torch.int32, (3,)),
+            _ptr(phi, torch.float64), _ptr(dgeom, torch.float64, (9,)), _ptr(q, torch.float64))
+        if st != 0:
+            raise AlensError(st, "aLENS_assemble_constraints")
+        return phi, dgeom, q
+
+    def solve_lcp(self, quat, pairs, dgeom, q, gamma=None, check=True):
+        """BBPGD solve; returns (gamma [m] float64, Info)."""
+        import torch
+        m = pairs.shape[0]
+        if gamma is None:
+            gamma = torch.zeros(m, dtype=torch.float64, device=quat.device)
+        info = Info()
+        st = self._lib.aLENS_solve_lcp(self._h, quat.shape[0], _ptr(quat, torch.float64, (4,)), m,
+                                       _ptr(pairs.contiguous(), torch.int32, (3,)), _ptr(dgeom, torch.float64, (9,)),
+                                       _ptr(q, torch.float64), _ptr(gamma, torch.float64), C.byref(info))
+        if check and st != 0:
+            raise AlensError(st, "aLENS_solve_lcp", info.as_dict())
+        return gamma, info
+
+    def step(self, x, quat, f_nc, pairs_out=None, gamma_out=None, vel_out=None, check=True):
+        """One constrained step in place on x, quat (device float64).  Returns Info."""
+        import torch
+        info = Info()
+        st = self._lib.aLENS_step(self._h, x.shape[0], _ptr(x, torch.float64, (3,)), _ptr(quat, torch.float64, (4,)),
+                                  _ptr(f_nc, torch.float64, (6,)), _ptr(pairs_out, torch.int32, (3,)),
+                                  _ptr(gamma_out, torch.float64), _ptr(vel_out, torch.float64, (6,)), C.byref(info))
+        if check and st != 0:
+            raise AlensError(st, "aLENS_step", info.as_dict())
+        return info

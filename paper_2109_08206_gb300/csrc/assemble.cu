@@ -1,0 +1,268 @@
+// Constraint assembly and the solver's sparse layout.
+//
+// Appendix "Symmetry ...": each collision constraint is one sparse column
+// D_PQ = [e_P, y_P x e_P, e_Q, y_Q x e_Q] with e_P = r/|r| = -e_Q and
+// r = x_P + y_P - x_Q - y_Q between the closest points.  Appendix Eq.
+// blockdef: q = Phi/h + D^T M F_nc.
+//
+// k_assemble: one thread per pair; float64 closest points, Phi, the 9 values
+// (e, y_P x e, y_Q x e) and q.  Overlap count and minimum gap are reduced per
+// warp before one atomic each.
+//
+// Solver layout (k_setup_*): constraint-major records in the solver's
+// working precision, the P-side CSR (pairs sorted by i make each rod's
+// P-constraints one contiguous range), and a Q-side CSR (per rod j, the ids
+// of constraints with Q = j, sorted ascending) with a copy of (e, y_Q x e)
+// laid out in CSR order so that the rod-parallel gather reads it
+// contiguously.
+#include <float.h>
+
+#include "internal.cuh"
+
+namespace alens {
+
+__device__ __forceinline__ long long gap_key(double v)
+{
+    long long b = __double_as_longlong(v);
+    return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+}
+
+__global__ void k_assemble(int m, int n, int np, Geo g, const int32_t* __restrict__ pairs,
+                           const double* __restrict__ xw, const double* __restrict__ axis,
+                           const double* __restrict__ unc, double* __restrict__ phi, double* __restrict__ dgeom,
+                           double* __restrict__ q, unsigned long long* __restrict__ counters, int* __restrict__ flags)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = c < m;
+    bool overlap = false;
+    long long key = LLONG_MAX;
+    if (active) {
+        int i = pairs[3 * (size_t)c], j = pairs[3 * (size_t)c + 1], code = pairs[3 * (size_t)c + 2];
+        if (!(i >= 0 && i < j && j < n && code >= 0 && code < 27)) {
+            if (atomicCAS(&flags[F_ERR], 0, ALENS_ERR_INVALID) == 0) flags[F_ERR_ROD] = c;
+            active = false;
+        } else {
+            int kk[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
+            double dx[3], p[3], qv[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                dx[a] = __dsub_rn(__dsub_rn(xw[a * (size_t)np + i], xw[a * (size_t)np + j]),
+                                  __dmul_rn((double)kk[a], g.box[a]));
+                p[a] = axis[a * (size_t)np + i];
+                qv[a] = axis[a * (size_t)np + j];
+            }
+            double s, t;
+            double dist = segment_closest<double>(dx, p, qv, g.half, kParallelDet64, s, t);
+            double yP[3], yQ[3], r[3], e[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                yP[a] = s * p[a];
+                yQ[a] = t * qv[a];
+                r[a] = dx[a] + yP[a] - yQ[a];
+            }
+            if (dist > 0.0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) e[a] = r[a] / dist;
+            } else {
+                // centrelines touch: normal of the two axes, turned towards P;
+                // collinear axes: along the axis, towards P; coincident: e_x
+                double nx = p[1] * qv[2] - p[2] * qv[1], ny = p[2] * qv[0] - p[0] * qv[2],
+                       nz = p[0] * qv[1] - p[1] * qv[0];
+                double nn = sqrt(nx * nx + ny * ny + nz * nz);
+                if (nn > 1e-12) {
+                    double sg = (nx * dx[0] + ny * dx[1] + nz * dx[2]) < 0.0 ? -1.0 : 1.0;
+                    e[0] = sg * nx / nn; e[1] = sg * ny / nn; e[2] = sg * nz / nn;
+                } else {
+                    double pd = p[0] * dx[0] + p[1] * dx[1] + p[2] * dx[2];
+                    if (pd != 0.0) {
+                        double sg = pd < 0.0 ? -1.0 : 1.0;
+                        double pn = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+                        e[0] = sg * p[0] / pn; e[1] = sg * p[1] / pn; e[2] = sg * p[2] / pn;
+                    } else {
+                        e[0] = 1.0; e[1] = 0.0; e[2] = 0.0;
+                    }
+                }
+            }
+            double ta[3] = {yP[1] * e[2] - yP[2] * e[1], yP[2] * e[0] - yP[0] * e[2], yP[0] * e[1] - yP[1] * e[0]};
+            double tb[3] = {yQ[1] * e[2] - yQ[2] * e[1], yQ[2] * e[0] - yQ[0] * e[2], yQ[0] * e[1] - yQ[1] * e[0]};
+            double* dg = dgeom + 9 * (size_t)c;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                dg[a] = e[a];
+                dg[3 + a] = ta[a];
+                dg[6 + a] = tb[a];
+            }
+            double ph = dist - g.diameter;
+            double dtu = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                dtu += e[a] * (unc[a * (size_t)np + i] - unc[a * (size_t)np + j]);
+                dtu += ta[a] * unc[(3 + a) * (size_t)np + i] - tb[a] * unc[(3 + a) * (size_t)np + j];
+            }
+            phi[c] = ph;
+            q[c] = ph / g.dt + dtu;
+            overlap = ph < 0.0;
+            key = gap_key(ph);
+        }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, overlap);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        long long other = __shfl_down_sync(0xffffffffu, key, o);
+        key = other < key ? other : key;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bal) atomicAdd(&counters[C_OVERLAP], (unsigned long long)__popc(bal));
+        if (key != LLONG_MAX) atomicMin((long long*)&counters[C_MINGAP], key);
+    }
+}
+
+__global__ void k_setup_count(int m, int n, const int32_t* __restrict__ pairs, int* __restrict__ cntP,
+                              int* __restrict__ cntQ, int* __restrict__ flags)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    int i = pairs[3 * (size_t)c], j = pairs[3 * (size_t)c + 1], code = pairs[3 * (size_t)c + 2];
+    bool ok = i >= 0 && i < j && j < n && code >= 0 && code < 27;
+    if (ok && c > 0 && pairs[3 * (size_t)(c - 1)] > i) ok = false;   // must be sorted by i
+    if (!ok) {
+        if (atomicCAS(&flags[F_ERR], 0, ALENS_ERR_INVALID) == 0) flags[F_ERR_ROD] = c;
+        return;
+    }
+    atomicAdd(&cntP[i], 1);
+    atomicAdd(&cntQ[j], 1);
+}
+
+template <typename T>
+__global__ void k_setup_fill(int m, int mp, const int32_t* __restrict__ pairs, const double* __restrict__ dgeom,
+                             const double* __restrict__ q64, const int* __restrict__ rowQ, int* __restrict__ curQ,
+                             int* __restrict__ qlist, int* __restrict__ ci, int* __restrict__ cj, T* __restrict__ rec,
+                             T* __restrict__ qT)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    int i = pairs[3 * (size_t)c], j = pairs[3 * (size_t)c + 1];
+    ci[c] = i;
+    cj[c] = j;
+#pragma unroll
+    for (int u = 0; u < 9; ++u) rec[u * (size_t)mp + c] = (T)dgeom[9 * (size_t)c + u];
+    qT[c] = (T)q64[c];
+    int pos = rowQ[j] + atomicAdd(&curQ[j], 1);
+    qlist[pos] = c;
+}
+
+__global__ void k_sort_qlist(int n, const int* __restrict__ rowQ, int* __restrict__ qlist)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int b = rowQ[j], e = rowQ[j + 1];
+    for (int u = b + 1; u < e; ++u) {
+        int v = qlist[u];
+        int w = u - 1;
+        while (w >= b && qlist[w] > v) {
+            qlist[w + 1] = qlist[w];
+            --w;
+        }
+        qlist[w + 1] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_setup_qe(int m, int mp, const int* __restrict__ qlist, const T* __restrict__ rec,
+                           T* __restrict__ qe)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    int c = qlist[k];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        qe[u * (size_t)mp + k] = rec[u * (size_t)mp + c];
+        qe[(3 + u) * (size_t)mp + k] = rec[(6 + u) * (size_t)mp + c];
+    }
+}
+
+template <typename T>
+__global__ void k_setup_rods(int n, int np, const double* __restrict__ quat, T* __restrict__ ax)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double p0, p1, p2;
+    quat_axis(quat[4 * (size_t)i], quat[4 * (size_t)i + 1], quat[4 * (size_t)i + 2], quat[4 * (size_t)i + 3], p0, p1,
+              p2);
+    ax[i] = (T)p0;
+    ax[np + i] = (T)p1;
+    ax[2 * (size_t)np + i] = (T)p2;
+}
+
+template <typename T>
+__global__ void k_setup_gamma(int m, const double* __restrict__ gin, T* __restrict__ g0)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    double v = gin ? gin[c] : 0.0;
+    g0[c] = v > 0.0 ? (T)v : T(0);
+}
+
+static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
+
+cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, double* phi, double* dgeom, double* q)
+{
+    if (m <= 0) return cudaSuccess;
+    k_assemble<<<nblk(m, 256), 256, 0, ctx->stream>>>(m, n, (int)ctx->max_rods, ctx->geo, pairs, ctx->xw, ctx->axis,
+                                                      ctx->unc, phi, dgeom, q, ctx->dcount, ctx->dflags);
+    ++ctx->launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m, const int32_t* pairs,
+                               const double* dgeom, const double* q, const double* gamma_in, const double* quat)
+{
+    int mp = (int)ctx->max_pairs, np = (int)ctx->max_rods;
+    cudaStream_t st = ctx->stream;
+    if (n > 0) {
+        k_setup_rods<T><<<nblk(n, 256), 256, 0, st>>>(n, np, quat, sb.ax);
+        ++ctx->launches;
+    }
+    if (m <= 0) return cudaGetLastError();
+    k_setup_fill<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, pairs, dgeom, q, ctx->rowQ, ctx->curQ, ctx->qlist, ctx->ci,
+                                                  ctx->cj, sb.rec, sb.q);
+    ++ctx->launches;
+    k_sort_qlist<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
+    ++ctx->launches;
+    k_setup_qe<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->qlist, sb.rec, sb.qe);
+    ++ctx->launches;
+    k_setup_gamma<T><<<nblk(m, 256), 256, 0, st>>>(m, gamma_in, sb.gam[0]);
+    ++ctx->launches;
+    return cudaGetLastError();
+}
+
+// Counts P and Q sides of the pair list (validating i < j, ranges and the
+// sort by i) into rod_count / cntQ.
+cudaError_t launch_solve_setup_check(aLENS_ctx* ctx, int n, int m, const int32_t* pairs)
+{
+    cudaStream_t st = ctx->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ctx->rod_count, 0, sizeof(int) * ((size_t)n + 1), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->cntQ, 0, sizeof(int) * ((size_t)n + 1), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->curQ, 0, sizeof(int) * ((size_t)n + 1), st)) != cudaSuccess) return e;
+    if (m > 0) {
+        k_setup_count<<<nblk(m, 256), 256, 0, st>>>(m, n, pairs, ctx->rod_count, ctx->cntQ, ctx->dflags);
+        ++ctx->launches;
+    }
+    return cudaGetLastError();
+}
+
+// Scans the counts of launch_solve_setup_check into rowP / rowQ, then fills
+// the typed solver buffers.  The pair list must have passed the check.
+cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* dgeom,
+                               const double* q, const double* gamma_in, const double* quat, int precision)
+{
+    cudaError_t e;
+    if ((e = exclusive_scan(ctx, ctx->rod_count, ctx->rowP, n)) != cudaSuccess) return e;
+    if ((e = exclusive_scan(ctx, ctx->cntQ, ctx->rowQ, n)) != cudaSuccess) return e;
+    if (precision == ALENS_MIXED) return setup_typed<float>(ctx, ctx->sb32, n, m, pairs, dgeom, q, gamma_in, quat);
+    return setup_typed<double>(ctx, ctx->sb64, n, m, pairs, dgeom, q, gamma_in, quat);
+}
+
+}  // namespace alens

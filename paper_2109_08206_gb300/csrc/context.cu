@@ -1,0 +1,464 @@
+// Host side of the C ABI (include/alens.h): context and workspaces,
+// argument checks, and the order of launches of each entry point.
+#include <float.h>
+
+#include <algorithm>
+#include <limits.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+using namespace alens;
+
+namespace {
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t err__ = (call);                \
+        if (err__ != cudaSuccess) return ALENS_ERR_CUDA; \
+    } while (0)
+
+bool params_ok(const aLENS_params* p)
+{
+    if (!p) return false;
+    if (!(p->diameter > 0) || !(p->length > 0) || !(p->viscosity > 0) || !(p->dt > 0) || !(p->delta_c >= 0)) return false;
+    if (!(p->tol >= 0) || p->max_iter < 0 || p->max_iter > 10000000) return false;
+    if (p->precision != ALENS_FP64 && p->precision != ALENS_MIXED) return false;
+    if (!(2.0 * p->length / p->diameter > 1.0)) return false;   // ln(2L/D) > 0
+    double rcut = p->length + p->diameter + p->delta_c;
+    for (int k = 0; k < 3; ++k)
+        if (!(p->box[k] >= rcut) || !isfinite(p->box[k])) return false;
+    return true;
+}
+
+// Cell grid and drag coefficients for a parameter set.  Returns the Morton
+// bits needed (or -1 if the grid exceeds 2^kMaxMortonBits cells per edge).
+int make_geo(const aLENS_params* p, Geo* g, Mob* mob)
+{
+    memset(g, 0, sizeof(*g));
+    g->diameter = p->diameter;
+    g->length = p->length;
+    g->half = 0.5 * p->length;
+    g->delta_c = p->delta_c;
+    g->dt = p->dt;
+    g->rcut = p->length + p->diameter + p->delta_c;
+    double maxbox = 0.0;
+    int maxnc = 1;
+    for (int k = 0; k < 3; ++k) {
+        g->box[k] = p->box[k];
+        g->boxf[k] = (float)p->box[k];
+        int nc = (int)floor(p->box[k] / (g->rcut * (1.0 + 1e-9)));
+        if (nc < 1) nc = 1;
+        g->nc[k] = nc;
+        g->cs[k] = p->box[k] / nc;
+        if (p->box[k] > maxbox) maxbox = p->box[k];
+        if (nc > maxnc) maxnc = nc;
+    }
+    int bits = 0;
+    while ((1 << bits) < maxnc) ++bits;
+    g->bits = bits;
+    // float32 screen margin: covers rounding of coordinates of size maxbox
+    // and of the float segment distance (see the search kernel)
+    double margin = 0.02 * p->diameter + 2e-6 * maxbox;
+    g->rcut_screen2 = (float)((g->rcut + margin) * (g->rcut + margin));
+    g->gap_screen = (float)(p->delta_c + margin);
+    double zperp = 4.0 * M_PI * p->viscosity * p->length / log(2.0 * p->length / p->diameter);
+    mob->inv_perp = 1.0 / zperp;
+    mob->inv_par = 2.0 / zperp;
+    mob->inv_rot = 12.0 / (zperp * p->length * p->length);
+    mob->inv_spin = 1.0 / (M_PI * p->viscosity * p->diameter * p->diameter * p->length);
+    return bits <= kMaxMortonBits ? bits : -1;
+}
+
+template <typename P>
+cudaError_t dmalloc(P** ptr, size_t bytes)
+{
+    return cudaMalloc((void**)ptr, bytes > 0 ? bytes : 16);
+}
+
+void free_all(aLENS_ctx* c)
+{
+    void* ptrs[] = {c->xw, c->axis, c->unc, c->pos32, c->ax32, c->cellkey, c->sorted_id, c->spos32, c->sax32,
+                    c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_tmpstart, c->tmp_keys,
+                    c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
+                    c->q64, c->solve_ws, c->partials, c->bar, c->dflags, c->dcount, c->scan_tmp};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->hflags) cudaFreeHost(c->hflags);
+    if (c->hcount) cudaFreeHost(c->hcount);
+    for (int k = 0; k < 8; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+}
+
+__global__ void k_reset_counters(unsigned long long* cnt, int* flags)
+{
+    int t = threadIdx.x;
+    if (t < C_NCOUNT) cnt[t] = t == C_MINGAP ? (unsigned long long)LLONG_MAX : 0ull;
+    if (t < F_NFLAGS) flags[t] = 0;
+}
+
+aLENS_status reset_status(aLENS_ctx* c)
+{
+    k_reset_counters<<<1, 32, 0, c->stream>>>(c->dcount, c->dflags);
+    ++c->launches;
+    return cudaGetLastError() == cudaSuccess ? ALENS_OK : ALENS_ERR_CUDA;
+}
+
+aLENS_status read_status(aLENS_ctx* c)
+{
+    CK(cudaMemcpyAsync(c->hflags, c->dflags, sizeof(int) * F_NFLAGS, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(unsigned long long) * C_NCOUNT, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ALENS_OK;
+}
+
+double decode_gap(unsigned long long k)
+{
+    long long b = (long long)k;
+    if (b == LLONG_MAX) return INFINITY;
+    long long bits = b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+    double v;
+    memcpy(&v, &bits, sizeof(v));
+    return v;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = -1.f;
+    return ms;
+}
+
+bool rods_ok(aLENS_ctx* c, int64_t n) { return c && n >= 0 && n <= c->max_rods; }
+
+// Runs the solver on the layout already set up; fills info.
+aLENS_status run_solver(aLENS_ctx* c, int n, int m, aLENS_info* info, cudaEvent_t e0, cudaEvent_t e1)
+{
+    CK(cudaEventRecord(e0, c->stream));
+    if (m > 0) CK(launch_solve(c, n, m, c->p.precision));
+    CK(cudaEventRecord(e1, c->stream));
+    (void)info;
+    return ALENS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* aLENS_status_string(aLENS_status s)
+{
+    switch (s) {
+        case ALENS_OK: return "ok";
+        case ALENS_ERR_INVALID: return "invalid argument or input";
+        case ALENS_ERR_CAPACITY: return "buffer capacity exceeded";
+        case ALENS_ERR_NOT_CONVERGED: return "solver reached max_iter before the tolerance";
+        case ALENS_ERR_TIMEOUT: return "a bounded grid-wide wait timed out";
+        case ALENS_ERR_CUDA: return "CUDA runtime error";
+        case ALENS_ERR_NOMEM: return "out of device memory";
+        case ALENS_ERR_NOT_IMPLEMENTED: return "not implemented";
+    }
+    return "unknown status";
+}
+
+aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t max_pairs, void* cuda_stream,
+                          aLENS_ctx** out)
+{
+    if (!out) return ALENS_ERR_INVALID;
+    *out = nullptr;
+    if (!params_ok(params) || max_rods < 1 || max_pairs < 1 || max_rods > (1 << 26) || max_pairs > INT_MAX / 9)
+        return ALENS_ERR_INVALID;
+    Geo geo;
+    Mob mob;
+    if (make_geo(params, &geo, &mob) < 0) return ALENS_ERR_INVALID;
+    aLENS_ctx* c = (aLENS_ctx*)calloc(1, sizeof(aLENS_ctx));
+    if (!c) return ALENS_ERR_NOMEM;
+    c->p = *params;
+    c->geo = geo;
+    c->mob = mob;
+    c->max_rods = max_rods;
+    c->max_pairs = max_pairs;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->wait_s = 5.0;
+    c->solve_threads = 256;
+    c->solve_bps = 0;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { free(c); return ALENS_ERR_CUDA; }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) { free(c); return ALENS_ERR_CUDA; }
+    c->num_sms = prop.multiProcessorCount;
+    int clk = 0;
+    cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, c->device);
+    c->clock_khz = clk > 0 ? clk : 2.1e6;
+    c->coop_ok = prop.cooperativeLaunch;
+    c->max_keys = 1 << (3 * geo.bits);
+    c->max_blocks = c->num_sms * 8;
+    size_t np = (size_t)max_rods, mp = (size_t)max_pairs;
+    int scan_tiles = (int)((std::max(np, (size_t)c->max_keys) + 4095) / 4096) + 2;
+    c->scan_tmp_len = scan_tiles;
+    bool ok = true;
+    ok &= dmalloc(&c->xw, 3 * np * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->axis, 3 * np * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->unc, 6 * np * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->pos32, np * sizeof(float4)) == cudaSuccess;
+    ok &= dmalloc(&c->ax32, np * sizeof(float4)) == cudaSuccess;
+    ok &= dmalloc(&c->cellkey, np * sizeof(uint32_t)) == cudaSuccess;
+    ok &= dmalloc(&c->sorted_id, np * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->spos32, np * sizeof(float4)) == cudaSuccess;
+    ok &= dmalloc(&c->sax32, np * sizeof(float4)) == cudaSuccess;
+    ok &= dmalloc(&c->cell_count, ((size_t)c->max_keys + 1) * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->cell_start, ((size_t)c->max_keys + 1) * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->cell_cursor, ((size_t)c->max_keys + 1) * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->rod_count, (np + 1) * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->rod_tmpstart, np * sizeof(long long)) == cudaSuccess;
+    ok &= dmalloc(&c->tmp_keys, mp * sizeof(uint32_t)) == cudaSuccess;
+    ok &= dmalloc(&c->rowP, (np + 1) * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->rowQ, (np + 1) * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->cntQ, (np + 1) * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->curQ, (np + 1) * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->qlist, mp * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->ci, mp * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->cj, mp * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->pairs, 3 * mp * sizeof(int32_t)) == cudaSuccess;
+    ok &= dmalloc(&c->phi, mp * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->dgeom, 9 * mp * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->q64, mp * sizeof(double)) == cudaSuccess;
+    // solver buffers, sized for float64; the float32 views alias the same memory
+    size_t solve_elems = 9 * mp + 6 * mp + mp + 3 * np + 4 * mp + 6 * np;
+    ok &= dmalloc((char**)&c->solve_ws, solve_elems * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->partials, (size_t)c->max_blocks * 4 * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->bar, 4 * sizeof(unsigned)) == cudaSuccess;
+    ok &= dmalloc(&c->dflags, F_NFLAGS * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->dcount, C_NCOUNT * sizeof(unsigned long long)) == cudaSuccess;
+    ok &= dmalloc(&c->scan_tmp, (size_t)scan_tiles * sizeof(int)) == cudaSuccess;
+    ok &= cudaMallocHost((void**)&c->hflags, F_NFLAGS * sizeof(int)) == cudaSuccess;
+    ok &= cudaMallocHost((void**)&c->hcount, C_NCOUNT * sizeof(unsigned long long)) == cudaSuccess;
+    for (int k = 0; k < 8 && ok; ++k) ok &= cudaEventCreate(&c->ev[k]) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(c);
+        free(c);
+        return ALENS_ERR_NOMEM;
+    }
+    {
+        double* base = (double*)c->solve_ws;
+        size_t o = 0;
+        auto carve64 = [&](size_t cnt) { double* r = base + o; o += cnt; return r; };
+        SolveBufs<double>& s = c->sb64;
+        s.rec = carve64(9 * mp); s.qe = carve64(6 * mp); s.q = carve64(mp); s.ax = carve64(3 * np);
+        s.gam[0] = carve64(mp); s.gam[1] = carve64(mp); s.grad[0] = carve64(mp); s.grad[1] = carve64(mp);
+        s.U = carve64(6 * np);
+        float* fb = (float*)c->solve_ws;
+        size_t f = 0;
+        auto carve32 = [&](size_t cnt) { float* r = fb + f; f += cnt; return r; };
+        SolveBufs<float>& t = c->sb32;
+        t.rec = carve32(9 * mp); t.qe = carve32(6 * mp); t.q = carve32(mp); t.ax = carve32(3 * np);
+        t.gam[0] = carve32(mp); t.gam[1] = carve32(mp); t.grad[0] = carve32(mp); t.grad[1] = carve32(mp);
+        t.U = carve32(6 * np);
+    }
+    if (cudaMemsetAsync(c->cell_cursor, 0, ((size_t)c->max_keys + 1) * sizeof(int), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        free_all(c);
+        free(c);
+        return ALENS_ERR_CUDA;
+    }
+    *out = c;
+    return ALENS_OK;
+}
+
+void aLENS_destroy(aLENS_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    free(c);
+}
+
+aLENS_status aLENS_set_params(aLENS_ctx* c, const aLENS_params* params)
+{
+    if (!c || !params_ok(params)) return ALENS_ERR_INVALID;
+    Geo geo;
+    Mob mob;
+    int bits = make_geo(params, &geo, &mob);
+    if (bits < 0) return ALENS_ERR_INVALID;
+    if ((1 << (3 * bits)) > c->max_keys) return ALENS_ERR_CAPACITY;
+    c->p = *params;
+    c->geo = geo;
+    c->mob = mob;
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_set_wait_limit(aLENS_ctx* c, double seconds)
+{
+    if (!c || !(seconds > 0) || seconds > 3600) return ALENS_ERR_INVALID;
+    c->wait_s = seconds;
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_inject_fault(aLENS_ctx* c, int32_t mode)
+{
+    if (!c || mode < 0 || mode > 1) return ALENS_ERR_INVALID;
+    c->fault_mode = mode;
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_set_launch(aLENS_ctx* c, int32_t threads, int32_t blocks_per_sm)
+{
+    if (!c || threads < 32 || threads > 512 || threads % 32 != 0 || blocks_per_sm < 0) return ALENS_ERR_INVALID;
+    c->solve_threads = threads;
+    c->solve_bps = blocks_per_sm;
+    return ALENS_OK;
+}
+
+// Pack + cell list + search; leaves the per-rod counts and keys in the
+// context and the total in hcount[C_PAIRS].  Synchronises once.
+static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const double* quat, const double* fnc,
+                                 long long cap)
+{
+    int nkeys = 1 << (3 * c->geo.bits);
+    aLENS_status st = reset_status(c);
+    if (st != ALENS_OK) return st;
+    CK(cudaMemsetAsync(c->cell_count, 0, ((size_t)nkeys + 1) * sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->cell_cursor, 0, ((size_t)nkeys + 1) * sizeof(int), c->stream));
+    CK(launch_pack(c, n, x, quat, fnc, true));
+    CK(launch_cell_sort(c, n));
+    CK(launch_search(c, n, cap));
+    if ((st = read_status(c)) != ALENS_OK) return st;
+    if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_build_neighbors(aLENS_ctx* c, int64_t n, const double* x, const double* quat, int32_t* pairs,
+                                   int64_t pairs_cap, int64_t* n_pairs)
+{
+    if (c) c->launches = 0;
+    if (!rods_ok(c, n) || !n_pairs || (n > 0 && (!x || !quat)) || pairs_cap < 0 || (pairs_cap > 0 && !pairs))
+        return ALENS_ERR_INVALID;
+    long long cap = std::min<long long>(pairs_cap, c->max_pairs);
+    aLENS_status st = search_phase(c, (int)n, x, quat, nullptr, cap);
+    if (st != ALENS_OK) return st;
+    long long total = (long long)c->hcount[C_PAIRS];
+    *n_pairs = total;
+    if (total > cap) return ALENS_ERR_CAPACITY;
+    CK(launch_emit_pairs(c, (int)n, pairs));
+    CK(cudaStreamSynchronize(c->stream));
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_assemble_constraints(aLENS_ctx* c, int64_t n, const double* x, const double* quat,
+                                        const double* f_nc, int64_t n_pairs, const int32_t* pairs, double* phi,
+                                        double* dgeom, double* q)
+{
+    if (c) c->launches = 0;
+    if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
+    if (n > 0 && (!x || !quat)) return ALENS_ERR_INVALID;
+    if (n_pairs > 0 && (!pairs || !phi || !dgeom || !q)) return ALENS_ERR_INVALID;
+    aLENS_status st = reset_status(c);
+    if (st != ALENS_OK) return st;
+    CK(launch_pack(c, (int)n, x, quat, f_nc, false));
+    CK(launch_assemble(c, (int)n, (int)n_pairs, pairs, phi, dgeom, q));
+    if ((st = read_status(c)) != ALENS_OK) return st;
+    if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
+    return ALENS_OK;
+}
+
+static void fill_info(aLENS_ctx* c, aLENS_info* info, int64_t m, aLENS_status st)
+{
+    if (!info) return;
+    info->n_pairs = m;
+    info->n_overlap = (int64_t)c->hcount[C_OVERLAP];
+    info->min_gap = decode_gap(c->hcount[C_MINGAP]);
+    info->iters = c->hflags[F_ITERS];
+    double res;
+    memcpy(&res, &c->hcount[4], sizeof(res));
+    info->residual = m > 0 ? res : 0.0;
+    info->status = (int32_t)st;
+    info->launches = c->launches;
+}
+
+static aLENS_status solve_status(aLENS_ctx* c, int64_t m)
+{
+    if (c->hflags[F_SOLVE_ERR] != 0) return (aLENS_status)c->hflags[F_SOLVE_ERR];
+    if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
+    if (m > 0) {
+        double res;
+        memcpy(&res, &c->hcount[4], sizeof(res));
+        if (!(res <= c->p.tol)) return ALENS_ERR_NOT_CONVERGED;
+    }
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_solve_lcp(aLENS_ctx* c, int64_t n, const double* quat, int64_t n_pairs, const int32_t* pairs,
+                             const double* dgeom, const double* q, double* gamma, aLENS_info* info)
+{
+    if (c) c->launches = 0;
+    if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
+    if (n > 0 && !quat) return ALENS_ERR_INVALID;
+    if (n_pairs > 0 && (!pairs || !dgeom || !q || !gamma)) return ALENS_ERR_INVALID;
+    if (n_pairs > 0 && !c->coop_ok) return ALENS_ERR_CUDA;
+    aLENS_status st = reset_status(c);
+    if (st != ALENS_OK) return st;
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    CK(launch_solve_setup_check(c, (int)n, (int)n_pairs, pairs));
+    if ((st = read_status(c)) != ALENS_OK) return st;
+    if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
+    CK(launch_solve_setup(c, (int)n, (int)n_pairs, pairs, dgeom, q, gamma, quat, c->p.precision));
+    if ((st = run_solver(c, (int)n, (int)n_pairs, info, c->ev[1], c->ev[2])) != ALENS_OK) return st;
+    if ((st = read_status(c)) != ALENS_OK) return st;
+    if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
+    st = solve_status(c, n_pairs);
+    if (st == ALENS_OK || st == ALENS_ERR_NOT_CONVERGED) {
+        CK(launch_gamma_out(c, (int)n_pairs, c->p.precision, gamma));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    fill_info(c, info, n_pairs, st);
+    if (info) {
+        info->ms_build = 0.f;
+        info->ms_assemble = elapsed(c->ev[0], c->ev[1]);
+        info->ms_solve = elapsed(c->ev[1], c->ev[2]);
+        info->ms_update = 0.f;
+    }
+    return st;
+}
+
+aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc, int32_t* pairs_out,
+                        double* gamma_out, double* vel_out, aLENS_info* info)
+{
+    if (c) c->launches = 0;
+    if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;
+    if (!c->coop_ok) return ALENS_ERR_CUDA;
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    aLENS_status st = search_phase(c, (int)n, x, quat, f_nc, c->max_pairs);
+    if (st != ALENS_OK) {
+        if (info) { memset(info, 0, sizeof(*info)); info->status = st; info->n_pairs = (int64_t)c->hcount[C_PAIRS]; }
+        return st;
+    }
+    long long m = (long long)c->hcount[C_PAIRS];
+    if (m > c->max_pairs) {
+        if (info) { memset(info, 0, sizeof(*info)); info->status = ALENS_ERR_CAPACITY; info->n_pairs = m; }
+        return ALENS_ERR_CAPACITY;
+    }
+    CK(launch_emit_pairs(c, (int)n, c->pairs));
+    CK(cudaEventRecord(c->ev[1], c->stream));
+    CK(launch_assemble(c, (int)n, (int)m, c->pairs, c->phi, c->dgeom, c->q64));
+    CK(launch_solve_setup_check(c, (int)n, (int)m, c->pairs));
+    CK(launch_solve_setup(c, (int)n, (int)m, c->pairs, c->dgeom, c->q64, nullptr, quat, c->p.precision));
+    if ((st = run_solver(c, (int)n, (int)m, info, c->ev[2], c->ev[3])) != ALENS_OK) return st;
+    CK(launch_update(c, (int)n, (int)m, x, quat, c->p.precision, vel_out));
+    CK(cudaEventRecord(c->ev[4], c->stream));
+    if (gamma_out) CK(launch_gamma_out(c, (int)m, c->p.precision, gamma_out));
+    if (pairs_out && m > 0)
+        CK(cudaMemcpyAsync(pairs_out, c->pairs, sizeof(int32_t) * 3 * (size_t)m, cudaMemcpyDeviceToDevice, c->stream));
+    if ((st = read_status(c)) != ALENS_OK) return st;
+    st = solve_status(c, m);
+    fill_info(c, info, m, st);
+    if (info) {
+        info->ms_build = elapsed(c->ev[0], c->ev[1]);
+        info->ms_assemble = elapsed(c->ev[1], c->ev[2]);
+        info->ms_solve = elapsed(c->ev[2], c->ev[3]);
+        info->ms_update = elapsed(c->ev[3], c->ev[4]);
+    }
+    return st;
+}
+
+}  // extern "C"

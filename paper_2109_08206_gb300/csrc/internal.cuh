@@ -1,0 +1,259 @@
+// Internal declarations of the GB300 collision-constraint library.
+// Device helpers shared by the kernels, the context layout, and the host
+// launchers that context.cu strings together.  Nothing here is part of the
+// C ABI (include/alens.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/alens.h"
+
+namespace alens {
+
+// ---------------------------------------------------------------- constants
+
+constexpr int kSearchWarps = 4;          // warps per block of the neighbour search
+constexpr int kPairsPerRodCap = 512;     // per-rod (i < j) list held in shared memory
+constexpr double kParallelDet64 = 1e-12; // a c - b^2 below this (relative) = parallel
+constexpr float kParallelDet32 = 1e-4f;  // float screen: below this go straight to float64
+constexpr int kMaxMortonBits = 7;        // at most 128 cells per edge
+
+// device status words (one int array, see Ctx::dflags)
+enum Flag : int {
+    F_ERR = 0,        // first error code seen by any kernel (aLENS_status)
+    F_ERR_ROD = 1,    // offending rod / pair index for INVALID or per-rod overflow
+    F_SOLVE_ERR = 2,  // solver kernel: ALENS_ERR_TIMEOUT when a grid wait ran out
+    F_FINAL = 3,      // solver kernel: buffer index that holds the final gamma
+    F_ITERS = 4,      // solver kernel: iterations taken
+    F_NFLAGS = 16
+};
+// 64-bit counters (Ctx::dcount)
+enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_NCOUNT = 8 };
+
+// ------------------------------------------------------------ plain structs
+
+struct Geo {                 // everything the geometry kernels need
+    double box[3];
+    double cs[3];            // cell edge per axis (>= L + D + delta_c)
+    int nc[3];               // cells per axis
+    int bits;                // Morton bits per axis
+    double diameter, length, half, delta_c, dt;
+    double rcut;             // L + D + delta_c: centre-distance bound for a close pair
+    float boxf[3];
+    float rcut_screen2;      // (rcut + margin)^2 for the float pre-screen
+    float gap_screen;        // delta_c + margin for the float segment screen
+};
+
+struct Mob {                 // inverse drag coefficients of one rod (all rods alike)
+    double inv_perp, inv_par, inv_rot, inv_spin;
+};
+
+// ------------------------------------------------------------- device helpers
+
+__host__ __device__ inline uint32_t spread_bits3(uint32_t v)
+{
+    // insert two zero bits between each of the low 10 bits
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__host__ __device__ inline uint32_t morton3(int cx, int cy, int cz)
+{
+    return spread_bits3((uint32_t)cx) | (spread_bits3((uint32_t)cy) << 1) | (spread_bits3((uint32_t)cz) << 2);
+}
+
+// Wrap one coordinate into [0, b).
+__device__ __forceinline__ double wrap_coord(double v, double b)
+{
+    double w = __dsub_rn(v, __dmul_rn(b, floor(__ddiv_rn(v, b))));
+    if (!(w < b) || w < 0.0) w = 0.0;
+    return w;
+}
+
+// Rod axis R(theta) e_z of a quaternion (s, a, b, c).
+__device__ __forceinline__ void quat_axis(double s, double a, double b, double c, double& p0, double& p1,
+                                          double& p2)
+{
+    p0 = 2.0 * (a * c + s * b);
+    p1 = 2.0 * (b * c - s * a);
+    p2 = s * s - a * a - b * b + c * c;
+}
+
+template <typename T>
+__device__ __forceinline__ T clampv(T v, T lo, T hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Closest points of two segments {x_P + s p} and {x_Q + t q}, |s|,|t| <= hl,
+// given dx = x_P - x_Q.  Clamped-projection method: take the unconstrained
+// optimum s of the two infinite lines, clamp it, project onto Q for t; if
+// that t leaves Q, clamp t and re-project onto P.  Parallel segments
+// (det <= eps a c) whose projections overlap take s at the middle of the
+// overlap and t as its clamped projection.  Returns |dx + s p - t q|.
+template <typename T>
+__device__ __forceinline__ T segment_closest(const T dx[3], const T p[3], const T q[3], T hl, T det_eps, T& s_out,
+                                             T& t_out)
+{
+    T a = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+    T b = p[0] * q[0] + p[1] * q[1] + p[2] * q[2];
+    T c = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    T d = p[0] * dx[0] + p[1] * dx[1] + p[2] * dx[2];
+    T e = q[0] * dx[0] + q[1] * dx[1] + q[2] * dx[2];
+    T det = a * c - b * b;
+    T s, t;
+    bool done = false;
+    if (det > det_eps * a * c) {
+        s = clampv((b * e - c * d) / det, -hl, hl);
+    } else {
+        // projections of Q's ends onto P's axis
+        T e1 = (-b * hl - d) / a, e2 = (b * hl - d) / a;
+        T lo = e1 < e2 ? e1 : e2, hi = e1 < e2 ? e2 : e1;
+        T olo = lo < -hl ? -hl : lo, ohi = hi > hl ? hl : hi;
+        if (olo <= ohi) {
+            s = T(0.5) * (olo + ohi);
+            t = clampv((b * s + e) / c, -hl, hl);
+            done = true;
+        } else {
+            s = hi < -hl ? -hl : hl;   // P's end nearest to Q's projection
+        }
+    }
+    if (!done) {
+        t = (b * s + e) / c;
+        if (t < -hl) {
+            t = -hl;
+            s = clampv((b * t - d) / a, -hl, hl);
+        } else if (t > hl) {
+            t = hl;
+            s = clampv((b * t - d) / a, -hl, hl);
+        }
+    }
+    T r0 = dx[0] + s * p[0] - t * q[0];
+    T r1 = dx[1] + s * p[1] - t * q[1];
+    T r2 = dx[2] + s * p[2] - t * q[2];
+    s_out = s;
+    t_out = t;
+    return sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+}
+
+// ------------------------------------------------------------ scoped atomics
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p)
+{
+    return *(const volatile int*)p;
+}
+
+// ------------------------------------------------------------- context
+
+template <typename T>
+struct SolveBufs {           // typed views into the solver workspace
+    T* rec;                  // [9][mp]  e, y_P x e, y_Q x e
+    T* qe;                   // [6][mp]  per Q-side entry: e, y_Q x e (CSR order)
+    T* q;                    // [mp]
+    T* ax;                   // [3][np]
+    T* gam[2];               // [mp] x 2
+    T* grad[2];              // [mp] x 2
+    T* U;                    // [6][np]
+};
+
+}  // namespace alens
+
+struct aLENS_ctx {
+    aLENS_params p;
+    int64_t max_rods, max_pairs;
+    cudaStream_t stream;
+    int device, num_sms;
+    double clock_khz;
+    alens::Geo geo;
+    alens::Mob mob;
+    int max_keys;            // histogram size allocated (power of 8)
+
+    // rod workspaces, pitch max_rods
+    double* xw;              // [3][np] wrapped centres
+    double* axis;            // [3][np]
+    double* unc;             // [6][np] M F_nc
+    float4* pos32;           // [np]
+    float4* ax32;            // [np]
+    uint32_t* cellkey;       // [np]
+    int* sorted_id;          // [np]
+    float4* spos32;          // [np] cell-sorted copies
+    float4* sax32;           // [np]
+    int* cell_count;         // [max_keys + 1]
+    int* cell_start;         // [max_keys + 1]
+    int* cell_cursor;        // [max_keys]
+    int* rod_count;          // [np + 1]
+    long long* rod_tmpstart; // [np]
+    uint32_t* tmp_keys;      // [mp]
+    int* rowP;               // [np + 1]
+    int* rowQ;               // [np + 1]
+    int* cntQ;               // [np + 1]
+    int* curQ;               // [np]
+    int* qlist;              // [mp]
+    int* ci;                 // [mp]
+    int* cj;                 // [mp]
+    int32_t* pairs;          // [mp][3] internal pair list of a step
+    double* phi;             // [mp]
+    double* dgeom;           // [mp][9]
+    double* q64;             // [mp]
+    void* solve_ws;          // typed solver buffers (sized for double)
+    alens::SolveBufs<double> sb64;
+    alens::SolveBufs<float> sb32;
+    double* partials;        // [max_blocks][4]
+    int max_blocks;
+    unsigned* bar;           // [4]
+    int* dflags;             // [F_NFLAGS]
+    unsigned long long* dcount;  // [C_NCOUNT]
+    int* scan_tmp;           // block sums for the scans
+    int scan_tmp_len;
+
+    // host side
+    int* hflags;             // pinned mirror of dflags
+    unsigned long long* hcount;
+    cudaEvent_t ev[8];
+    double wait_s;
+    int fault_mode;
+    int solve_threads, solve_bps;
+    int coop_ok;
+    int launches;            // kernels launched since the entry point began
+};
+
+namespace alens {
+
+// scan.cu: exclusive scan of counts[0..n) into out[0..n], out[n] = total.
+cudaError_t exclusive_scan(aLENS_ctx* ctx, const int* counts, int* out, int n);
+
+// neighbors.cu
+cudaError_t launch_pack(aLENS_ctx* ctx, int n, const double* x, const double* quat, const double* fnc, bool cells);
+cudaError_t launch_cell_sort(aLENS_ctx* ctx, int n);
+cudaError_t launch_search(aLENS_ctx* ctx, int n, long long cap);
+cudaError_t launch_emit_pairs(aLENS_ctx* ctx, int n, int32_t* pairs_out);
+
+// assemble.cu
+cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, double* phi, double* dgeom,
+                            double* q);
+// Validates a caller's pair list (ranges, i < j, sorted by i) and counts
+// the P and Q sides; launch_solve_setup must follow only if no error flag was raised.
+cudaError_t launch_solve_setup_check(aLENS_ctx* ctx, int n, int m, const int32_t* pairs);
+cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* dgeom,
+                               const double* q, const double* gamma_in, const double* quat, int precision);
+
+// solve.cu
+cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision);
+cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma_out);
+
+// update.cu
+cudaError_t launch_update(aLENS_ctx* ctx, int n, int m, double* x, double* quat, int precision, double* vel_out);
+
+}  // namespace alens

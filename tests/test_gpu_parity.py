@@ -1,0 +1,357 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Bars:
+- pair lists: bit-exact (i, j, image) triples, sorted.  A pair may differ
+  only if the oracle's float64 surface gap lies within 1e-9 D of delta_c
+  (both sides decide in float64 with different closest-point algorithms;
+  rounding can move such a pair).  The count of such pairs is asserted small.
+- assembly (float64 both sides): Phi and q to 1e-12 relative, D records to
+  1e-9 absolute (closest-point arms are ill-conditioned for near-parallel
+  rods).
+- solve: U = M D gamma (unique even when gamma is not) to 1e-5 relative L2 in
+  float64 mode and 1e-3 in mixed mode; gamma itself to the same bars when the
+  oracle's active-set block is full rank; the oracle's own residual of the
+  GPU gamma must meet the tolerance.
+- step: post-step centres within 1e-6 D (float64) / 1e-5 D (mixed) of the
+  oracle's, quaternions likewise.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2109_08206_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2109_08206_gb300 as A  # noqa: E402
+
+
+def dev(a, dtype=None):
+    dtype = dtype or torch.float64
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    A.build()
+    assert torch.cuda.is_available()
+
+
+def make_ctx(s, precision=A.FP64, tol=None, max_pairs=None, max_iter=200000):
+    p = A.params_of(s, precision=precision, tol=tol, max_iter=max_iter)
+    mp = max_pairs or max(64, 12 * s.n)
+    return A.Context(p, s.n, mp)
+
+
+def compare_pairs(gpu, orc, s, band=1e-9):
+    gpu = np.asarray(gpu).reshape(-1, 3)
+    orc = np.asarray(orc).reshape(-1, 3)
+    keys = [tuple(r) for r in gpu.tolist()]
+    assert keys == sorted(keys), "GPU pair list not sorted by (i, j, image)"
+    if gpu.shape == orc.shape and np.array_equal(gpu, orc):
+        return 0
+    g, o = set(keys), {tuple(r) for r in orc.tolist()}
+    diff = np.array(sorted(g ^ o), dtype=np.int32).reshape(-1, 3)
+    gaps = O.pair_gaps(s.x, s.quat, O.problem_of(s), diff)
+    assert np.all(np.abs(gaps - s.delta_c) <= band * s.diameter), (diff[:5], gaps[:5])
+    assert diff.shape[0] <= max(2, orc.shape[0] // 10000)
+    return diff.shape[0]
+
+
+def periodic_diff(a, b, box):
+    d = a - b
+    bx = np.asarray(box)
+    return d - bx * np.round(d / bx)
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+# --------------------------------------------------------------------- n1000
+
+@pytest.fixture(scope="module")
+def n1000():
+    s = W.workload("n1000_box40")
+    pb = O.problem_of(s)
+    pairs = O.find_pairs(s.x, s.quat, pb)
+    asm = O.assemble(s.x, s.quat, s.f_nc, pb, pairs)
+    gam, res, it = O.solve_apgd(s.quat, pb, pairs, asm["dgeom"], asm["q"], tol=1e-12, max_iter=2_000_000)
+    assert res <= 1e-11
+    xo, qo, Uo = O.update(s.x, s.quat, s.f_nc, pb, pairs, asm["dgeom"], gam)
+    return s, pb, pairs, asm, gam, (xo, qo, Uo)
+
+
+def test_neighbors_n1000_bit_exact(n1000):
+    s, pb, pairs, *_ = n1000
+    with make_ctx(s) as ctx:
+        got = host(ctx.build_neighbors(dev(s.x), dev(s.quat)))
+    assert compare_pairs(got, pairs, s) == 0
+    assert got.shape[0] > 4000
+
+
+def test_assemble_n1000(n1000):
+    s, pb, pairs, asm, *_ = n1000
+    with make_ctx(s) as ctx:
+        phi, dg, q = ctx.assemble_constraints(dev(s.x), dev(s.quat), dev(s.f_nc), dev(pairs, torch.int32))
+        phi, dg, q = host(phi), host(dg), host(q)
+    np.testing.assert_allclose(phi, asm["phi"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(dg, asm["dgeom"], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(q, asm["q"], rtol=1e-12, atol=1e-9)
+
+
+def _active_full_rank(s, pb, pairs, dgeom, gam):
+    act = gam > 0
+    if act.sum() == 0 or act.sum() > 2500:
+        return False
+    sub = pairs[act]
+    A_ = O.dense_A(s.quat, pb, sub, dgeom[act])
+    return np.linalg.matrix_rank(A_, tol=1e-10 * np.abs(A_).max()) == act.sum()
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(A.FP64, 1e-8, 1e-5), (A.MIXED, 1e-6, 1e-3)])
+def test_solve_n1000(n1000, precision, tol, bar):
+    s, pb, pairs, asm, gam_o, (xo, qo, Uo) = n1000
+    with make_ctx(s, precision, tol) as ctx:
+        g, info = ctx.solve_lcp(dev(s.quat), dev(pairs, torch.int32), dev(asm["dgeom"]), dev(asm["q"]))
+        g = host(g)
+    assert info.status == 0 and info.residual <= tol and info.iters > 0
+    assert (g >= 0).all()
+    # the oracle's own residual of the GPU answer
+    _, r = O.gradient(s.quat, pb, pairs, asm["dgeom"], asm["q"], g)
+    assert r <= tol * 1.05 + (1e-9 if precision == A.FP64 else 2e-7)
+    Ug = O.mobility_apply(s.quat, pb, O.apply_D(s.n, pairs, asm["dgeom"], g))
+    Uo_c = O.mobility_apply(s.quat, pb, O.apply_D(s.n, pairs, asm["dgeom"], gam_o))
+    assert rel_l2(Ug, Uo_c) <= bar
+    if _active_full_rank(s, pb, pairs, asm["dgeom"], gam_o):
+        assert rel_l2(g, gam_o) <= bar
+
+
+@pytest.mark.parametrize("precision,tol,xbar", [(A.FP64, 1e-8, 1e-6), (A.MIXED, 1e-6, 1e-5)])
+def test_step_n1000(n1000, precision, tol, xbar):
+    s, pb, pairs, asm, gam_o, (xo, qo, Uo) = n1000
+    x, q = dev(s.x), dev(s.quat)
+    vel = torch.empty((s.n, 6), dtype=torch.float64, device="cuda")
+    with make_ctx(s, precision, tol) as ctx:
+        gam = torch.empty(ctx.max_pairs, dtype=torch.float64, device="cuda")
+        pr = torch.empty((ctx.max_pairs, 3), dtype=torch.int32, device="cuda")
+        info = ctx.step(x, q, dev(s.f_nc), pairs_out=pr, gamma_out=gam, vel_out=vel)
+        m = info.n_pairs
+        got_pairs = host(pr)[:m]
+    assert info.status == 0 and info.residual <= tol
+    assert m == pairs.shape[0] and np.array_equal(got_pairs, pairs)
+    assert info.n_overlap == int((asm["phi"] < 0).sum())
+    assert info.min_gap == pytest.approx(asm["phi"].min(), abs=1e-12)
+    dx = periodic_diff(host(x), xo, s.box)
+    assert np.abs(dx).max() <= xbar * s.diameter
+    np.testing.assert_allclose(host(q), qo, atol=xbar)
+    np.testing.assert_allclose(np.linalg.norm(host(q), axis=1), 1.0, atol=1e-14)
+    assert rel_l2(host(vel), Uo) <= (1e-6 if precision == A.FP64 else 1e-3)
+
+
+def test_step_is_deterministic(n1000):
+    s = n1000[0]
+    outs = []
+    for _ in range(2):
+        x, q = dev(s.x), dev(s.quat)
+        with make_ctx(s, A.MIXED, 1e-6) as ctx:
+            gam = torch.empty(ctx.max_pairs, dtype=torch.float64, device="cuda")
+            info = ctx.step(x, q, dev(s.f_nc), gamma_out=gam)
+            outs.append((host(x), host(q), host(gam)[:info.n_pairs], info.iters))
+    assert outs[0][3] == outs[1][3]
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- tiny systems
+
+TINY = [(seed, n, box, L) for seed, (n, box, L) in enumerate(
+    [(12, 14.0, 3.0), (30, 14.0, 3.0), (40, 11.0, 3.0), (25, 6.0, 3.0), (20, 5.5, 3.0), (60, 16.0, 4.0),
+     (33, 9.0, 2.0), (50, 14.0, 3.0), (8, 7.0, 3.0), (45, 12.0, 5.0)])]
+
+
+@pytest.mark.parametrize("seed,n,box,L", TINY)
+@pytest.mark.parametrize("precision", [A.FP64, A.MIXED])
+def test_step_tiny(seed, n, box, L, precision):
+    s = W.tiny_system(100 + seed, n, box=box, length=L, nematic_spread=0.05 if seed % 3 == 0 else None)
+    s.f_nc *= 30.0
+    pb = O.problem_of(s)
+    ref = O.step(s.x, s.quat, s.f_nc, pb, tol=1e-12)
+    tol = 1e-10 if precision == A.FP64 else 1e-6
+    x, q = dev(s.x), dev(s.quat)
+    with make_ctx(s, precision, tol) as ctx:
+        pr = torch.empty((ctx.max_pairs, 3), dtype=torch.int32, device="cuda")
+        info = ctx.step(x, q, dev(s.f_nc), pairs_out=pr)
+        m = info.n_pairs
+        got = host(pr)[:m]
+    compare_pairs(got, ref["pairs"], s)
+    assert info.status == 0
+    xbar = 1e-6 if precision == A.FP64 else 2e-5
+    assert np.abs(periodic_diff(host(x), ref["x"], s.box)).max() <= xbar
+    assert np.abs(host(q) - ref["quat"]).max() <= xbar
+
+
+def test_adversarial_geometry():
+    # parallel, anti-parallel, crossed, collinear and skew pairs placed at
+    # gaps just inside / outside delta_c and overlapping; small box so that
+    # periodic images matter
+    rng = np.random.default_rng(17)
+    ez = np.array([0, 0, 1.0])
+    xs, axes = [], []
+    def add(c, a):
+        xs.append(c); axes.append(a / np.linalg.norm(a))
+    base = np.array([3.0, 3.0, 3.0])
+    for k, gap in enumerate([0.5, 0.999999, 1.000001, -0.3, 0.0, 1e-9]):
+        o = base + np.array([k * 4.0, 0, 0])
+        add(o, ez); add(o + np.array([1.0 + gap, 0, 0.3]), ez)                    # parallel side by side
+        add(o + np.array([0, 6.0, 0]), ez); add(o + np.array([0, 6.0, 11.0 + gap]), -ez)   # collinear head-on
+        add(o + np.array([0, 12.0, 0]), np.array([1.0, 0, 0]))                    # collinear chain along x
+        add(o + np.array([0.25, 12.0, 1.0 + gap]), np.array([0, 1.0, 0]))          # crossed
+    for _ in range(6):  # near-parallel skew pairs
+        o = rng.uniform(0, 30, 3)
+        a = ez + 1e-7 * rng.standard_normal(3)
+        add(o, ez); add(o + np.array([1.5, 0, 2.0]), a)
+    x = np.array(xs); axis = np.array(axes)
+    box = (30.0, 30.0, 30.0)
+    s = W.RodSystem(x=x - 30.0 * np.floor(x / 30.0), quat=W.quat_from_axis(axis),
+                    f_nc=rng.standard_normal((x.shape[0], 6)) * 10, box=box, tol=1e-10)
+    pb = O.problem_of(s)
+    ref = O.find_pairs(s.x, s.quat, pb)
+    with make_ctx(s) as ctx:
+        got = host(ctx.build_neighbors(dev(s.x), dev(s.quat)))
+        phi, dg, q = ctx.assemble_constraints(dev(s.x), dev(s.quat), dev(s.f_nc), dev(ref, torch.int32))
+    compare_pairs(got, ref, s, band=1e-6)
+    a = O.assemble(s.x, s.quat, s.f_nc, pb, ref)
+    np.testing.assert_allclose(host(phi), a["phi"], atol=1e-12)
+    np.testing.assert_allclose(host(dg), a["dgeom"], atol=1e-6)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_empty_and_isolated_rods():
+    s = W.tiny_system(3, 5, box=200.0, length=3.0)
+    pb = O.problem_of(s)
+    ref = O.step(s.x, s.quat, s.f_nc, pb)
+    assert ref["pairs"].shape[0] == 0
+    x, q = dev(s.x), dev(s.quat)
+    with make_ctx(s) as ctx:
+        info = ctx.step(x, q, dev(s.f_nc))
+        assert info.n_pairs == 0 and info.status == 0 and info.iters == 0
+        assert np.abs(periodic_diff(host(x), ref["x"], s.box)).max() <= 1e-12
+        e = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+        e4 = torch.empty((0, 4), dtype=torch.float64, device="cuda")
+        e6 = torch.empty((0, 6), dtype=torch.float64, device="cuda")
+        info = ctx.step(e, e4, e6)
+        assert info.n_pairs == 0 and info.status == 0
+
+
+def test_capacity_reports_required_count(n1000):
+    s, pb, pairs, *_ = n1000
+    with make_ctx(s, max_pairs=100) as ctx:
+        with pytest.raises(A.AlensError) as ei:
+            ctx.build_neighbors(dev(s.x), dev(s.quat))
+        assert ei.value.status == 2 and ei.value.extra == pairs.shape[0]
+        with pytest.raises(A.AlensError) as ei:
+            ctx.step(dev(s.x), dev(s.quat), dev(s.f_nc))
+        assert ei.value.status == 2 and ei.value.extra["n_pairs"] == pairs.shape[0]
+
+
+def test_invalid_inputs_leave_state_untouched(n1000):
+    s, pb, pairs, asm, *_ = n1000
+    bad = s.quat.copy()
+    bad[7] *= 1.01
+    x, q = dev(s.x), dev(bad)
+    with make_ctx(s) as ctx:
+        with pytest.raises(A.AlensError) as ei:
+            ctx.step(x, q, dev(s.f_nc))
+        assert ei.value.status == 1
+        assert np.array_equal(host(x), s.x) and np.array_equal(host(q), bad)
+        xn = s.x.copy(); xn[3, 1] = np.nan
+        with pytest.raises(A.AlensError):
+            ctx.build_neighbors(dev(xn), dev(s.quat))
+        shuffled = pairs[::-1].copy()
+        with pytest.raises(A.AlensError) as ei:
+            ctx.solve_lcp(dev(s.quat), dev(shuffled, torch.int32), dev(asm["dgeom"][::-1]), dev(asm["q"][::-1]))
+        assert ei.value.status == 1
+        # the context still works afterwards
+        got = host(ctx.build_neighbors(dev(s.x), dev(s.quat)))
+        assert np.array_equal(got, pairs)
+
+
+def test_not_converged_reports_residual(n1000):
+    s, pb, pairs, asm, *_ = n1000
+    with make_ctx(s, A.FP64, 1e-8, max_iter=3) as ctx:
+        g, info = ctx.solve_lcp(dev(s.quat), dev(pairs, torch.int32), dev(asm["dgeom"]), dev(asm["q"]), check=False)
+        assert info.status == 3 and info.iters == 3 and info.residual > 1e-8
+        _, r = O.gradient(s.quat, pb, pairs, asm["dgeom"], asm["q"], host(g))
+        assert r == pytest.approx(info.residual, rel=1e-6)
+
+
+def test_bounded_wait_times_out_and_context_recovers(n1000):
+    # one block of the solver leaves before its first grid-wide arrival; the
+    # others' bounded waits run out, the call returns TIMEOUT, nothing hangs
+    s, pb, pairs, asm, *_ = n1000
+    with make_ctx(s, A.FP64, 1e-8) as ctx:
+        ctx.set_wait_limit(0.2)
+        ctx.inject_fault(1)
+        g, info = ctx.solve_lcp(dev(s.quat), dev(pairs, torch.int32), dev(asm["dgeom"]), dev(asm["q"]), check=False)
+        assert info.status == 4
+        ctx.set_wait_limit(5.0)
+        g, info = ctx.solve_lcp(dev(s.quat), dev(pairs, torch.int32), dev(asm["dgeom"]), dev(asm["q"]))
+        assert info.status == 0 and info.residual <= 1e-8
+
+
+def test_warm_start_converges_immediately(n1000):
+    s, pb, pairs, asm, gam_o, _ = n1000
+    with make_ctx(s, A.FP64, 1e-8) as ctx:
+        g, info = ctx.solve_lcp(dev(s.quat), dev(pairs, torch.int32), dev(asm["dgeom"]), dev(asm["q"]),
+                                gamma=dev(gam_o))
+    assert info.status == 0 and info.iters == 0
+
+
+# ------------------------------------------------------ full-size (1e5 rods)
+
+@pytest.fixture(scope="module")
+def n100k():
+    return W.workload("n100k_phi010")
+
+
+@pytest.mark.parametrize("precision,tol", [(A.FP64, 1e-6), (A.MIXED, 1e-5)])
+def test_n100k_step_properties(n100k, precision, tol):
+    s = n100k
+    pb = O.problem_of(s)
+    x, q = dev(s.x), dev(s.quat)
+    with make_ctx(s, precision, tol, max_pairs=1_000_000) as ctx:
+        gam = torch.empty(ctx.max_pairs, dtype=torch.float64, device="cuda")
+        pr = torch.empty((ctx.max_pairs, 3), dtype=torch.int32, device="cuda")
+        vel = torch.empty((s.n, 6), dtype=torch.float64, device="cuda")
+        info = ctx.step(x, q, dev(s.f_nc), pairs_out=pr, gamma_out=gam, vel_out=vel)
+        m = info.n_pairs
+        pairs, g = host(pr)[:m], host(gam)[:m]
+    assert info.status == 0 and info.residual <= tol and 2e5 < m < 6e5
+    # pair list: every pair touching 150 sampled rods, against the oracle
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(s.n, 150, replace=False))
+    ref = O.find_pairs(s.x, s.quat, pb, rows=rows)
+    sel = pairs[np.isin(pairs[:, 0], rows) | np.isin(pairs[:, 1], rows)]
+    compare_pairs(sel, ref, s)
+    # KKT of the GPU answer, evaluated by the oracle on its own assembly
+    asm = O.assemble(s.x, s.quat, s.f_nc, pb, pairs)
+    assert (g >= 0).all()
+    gr, r = O.gradient(s.quat, pb, pairs, asm["dgeom"], asm["q"], g)
+    assert r <= tol * 1.05 + (1e-9 if precision == A.FP64 else 1e-6)
+    # U = M (F_nc + D gamma) from the oracle's arithmetic on the GPU gamma
+    U = O.mobility_apply(s.quat, pb, s.f_nc + O.apply_D(s.n, pairs, asm["dgeom"], g))
+    assert rel_l2(host(vel), U) <= (1e-9 if precision == A.FP64 else 1e-4)
+    xo = O.wrap(O.wrap(s.x, s.box) + s.dt * U[:, :3], s.box)
+    assert np.abs(periodic_diff(host(x), xo, s.box)).max() <= (1e-9 if precision == A.FP64 else 1e-5)
