@@ -171,7 +171,7 @@ ALENS_API aLENS_status aLENS_set_wait_limit(aLENS_ctx* ctx, double seconds);
 ALENS_API aLENS_status aLENS_inject_fault(aLENS_ctx* ctx, int32_t mode);
 
 /* Launch shape of the solver kernel: threads per block (multiple of 32,
- * <= 1024) and blocks per SM (0 = as many as fit).  For tuning. */
+ * <= 1024; default 1024) and blocks per SM (0 = as many as fit).  For tuning. */
 ALENS_API aLENS_status aLENS_set_launch(aLENS_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 
 #ifdef __cplusplus

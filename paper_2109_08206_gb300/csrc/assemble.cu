@@ -195,12 +195,13 @@ __global__ void k_setup_rods(int n, int np, const double* __restrict__ quat, T* 
 }
 
 template <typename T>
-__global__ void k_setup_gamma(int m, const double* __restrict__ gin, T* __restrict__ g0)
+__global__ void k_setup_gamma(int m, const double* __restrict__ gin, T* __restrict__ gg0)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
     double v = gin ? gin[c] : 0.0;
-    g0[c] = v > 0.0 ? (T)v : T(0);
+    gg0[2 * (size_t)c] = v > 0.0 ? (T)v : T(0);
+    gg0[2 * (size_t)c + 1] = T(0);
 }
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
@@ -232,7 +233,7 @@ static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     ++ctx->launches;
     k_setup_qe<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->qlist, sb.rec, sb.qe);
     ++ctx->launches;
-    k_setup_gamma<T><<<nblk(m, 256), 256, 0, st>>>(m, gamma_in, sb.gam[0]);
+    k_setup_gamma<T><<<nblk(m, 256), 256, 0, st>>>(m, gamma_in, sb.gg[0]);
     ++ctx->launches;
     return cudaGetLastError();
 }

@@ -63,7 +63,9 @@ int make_geo(const aLENS_params* p, Geo* g, Mob* mob)
     // and of the float segment distance (see the search kernel)
     double margin = 0.02 * p->diameter + 2e-6 * maxbox;
     g->rcut_screen2 = (float)((g->rcut + margin) * (g->rcut + margin));
-    g->gap_screen = (float)(p->delta_c + margin);
+    double dmax = p->diameter + p->delta_c + margin;
+    g->screen_d2 = (float)(dmax * dmax);
+    g->half_f = (float)(0.5 * p->length);
     double zperp = 4.0 * M_PI * p->viscosity * p->length / log(2.0 * p->length / p->diameter);
     mob->inv_perp = 1.0 / zperp;
     mob->inv_par = 2.0 / zperp;
@@ -81,7 +83,7 @@ cudaError_t dmalloc(P** ptr, size_t bytes)
 void free_all(aLENS_ctx* c)
 {
     void* ptrs[] = {c->xw, c->axis, c->unc, c->pos32, c->ax32, c->cellkey, c->sorted_id, c->spos32, c->sax32,
-                    c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_tmpstart, c->tmp_keys,
+                    c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand, c->keep,
                     c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
                     c->q64, c->solve_ws, c->partials, c->bar, c->dflags, c->dcount, c->scan_tmp};
     for (void* p : ptrs)
@@ -181,7 +183,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     c->max_pairs = max_pairs;
     c->stream = (cudaStream_t)cuda_stream;
     c->wait_s = 5.0;
-    c->solve_threads = 256;
+    c->solve_threads = 1024;
     c->solve_bps = 0;
     if (cudaGetDevice(&c->device) != cudaSuccess) { free(c); return ALENS_ERR_CUDA; }
     cudaDeviceProp prop;
@@ -210,8 +212,11 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->cell_start, ((size_t)c->max_keys + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->cell_cursor, ((size_t)c->max_keys + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->rod_count, (np + 1) * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->rod_ncand, np * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->rod_tmpstart, np * sizeof(long long)) == cudaSuccess;
-    ok &= dmalloc(&c->tmp_keys, mp * sizeof(uint32_t)) == cudaSuccess;
+    c->cand_cap = 2 * (long long)mp + 4096;
+    ok &= dmalloc(&c->cand, (size_t)c->cand_cap * sizeof(unsigned long long)) == cudaSuccess;
+    ok &= dmalloc(&c->keep, (size_t)c->cand_cap) == cudaSuccess;
     ok &= dmalloc(&c->rowP, (np + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->rowQ, (np + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->cntQ, (np + 1) * sizeof(int)) == cudaSuccess;
@@ -241,20 +246,19 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         return ALENS_ERR_NOMEM;
     }
     {
+        // (gamma, g) pairs first and U next keep their vector loads aligned
         double* base = (double*)c->solve_ws;
         size_t o = 0;
         auto carve64 = [&](size_t cnt) { double* r = base + o; o += cnt; return r; };
         SolveBufs<double>& s = c->sb64;
+        s.gg[0] = carve64(2 * mp); s.gg[1] = carve64(2 * mp); s.U = carve64(6 * np);
         s.rec = carve64(9 * mp); s.qe = carve64(6 * mp); s.q = carve64(mp); s.ax = carve64(3 * np);
-        s.gam[0] = carve64(mp); s.gam[1] = carve64(mp); s.grad[0] = carve64(mp); s.grad[1] = carve64(mp);
-        s.U = carve64(6 * np);
         float* fb = (float*)c->solve_ws;
         size_t f = 0;
         auto carve32 = [&](size_t cnt) { float* r = fb + f; f += cnt; return r; };
         SolveBufs<float>& t = c->sb32;
+        t.gg[0] = carve32(2 * mp); t.gg[1] = carve32(2 * mp); t.U = carve32(6 * np);
         t.rec = carve32(9 * mp); t.qe = carve32(6 * mp); t.q = carve32(mp); t.ax = carve32(3 * np);
-        t.gam[0] = carve32(mp); t.gam[1] = carve32(mp); t.grad[0] = carve32(mp); t.grad[1] = carve32(mp);
-        t.U = carve32(6 * np);
     }
     if (cudaMemsetAsync(c->cell_cursor, 0, ((size_t)c->max_keys + 1) * sizeof(int), c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -304,27 +308,36 @@ aLENS_status aLENS_inject_fault(aLENS_ctx* c, int32_t mode)
 
 aLENS_status aLENS_set_launch(aLENS_ctx* c, int32_t threads, int32_t blocks_per_sm)
 {
-    if (!c || threads < 32 || threads > 512 || threads % 32 != 0 || blocks_per_sm < 0) return ALENS_ERR_INVALID;
+    if (!c || threads < 32 || threads > 1024 || threads % 32 != 0 || blocks_per_sm < 0) return ALENS_ERR_INVALID;
     c->solve_threads = threads;
     c->solve_bps = blocks_per_sm;
     return ALENS_OK;
 }
 
-// Pack + cell list + search; leaves the per-rod counts and keys in the
-// context and the total in hcount[C_PAIRS].  Synchronises once.
-static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const double* quat, const double* fnc,
-                                 long long cap)
+// Pack + cell list + search; leaves the per-rod kept counts and the
+// candidate keys in the context and the pair total in hcount[C_PAIRS].
+// Synchronises once (twice if the candidate buffer overflowed, to count the
+// pairs exactly).
+static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const double* quat, const double* fnc)
 {
     int nkeys = 1 << (3 * c->geo.bits);
     aLENS_status st = reset_status(c);
     if (st != ALENS_OK) return st;
     CK(cudaMemsetAsync(c->cell_count, 0, ((size_t)nkeys + 1) * sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->cell_cursor, 0, ((size_t)nkeys + 1) * sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->rod_count, 0, ((size_t)n + 1) * sizeof(int), c->stream));
     CK(launch_pack(c, n, x, quat, fnc, true));
     CK(launch_cell_sort(c, n));
-    CK(launch_search(c, n, cap));
+    CK(launch_search(c, n));
     if ((st = read_status(c)) != ALENS_OK) return st;
     if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
+    if ((long long)c->hcount[C_CAND] > c->cand_cap) {
+        // candidate buffer too small: count the pairs exactly, report CAPACITY
+        CK(reset_status(c) == ALENS_OK ? cudaSuccess : cudaErrorUnknown);
+        CK(launch_search_count(c, n));
+        if ((st = read_status(c)) != ALENS_OK) return st;
+        return ALENS_ERR_CAPACITY;
+    }
     return ALENS_OK;
 }
 
@@ -335,10 +348,10 @@ aLENS_status aLENS_build_neighbors(aLENS_ctx* c, int64_t n, const double* x, con
     if (!rods_ok(c, n) || !n_pairs || (n > 0 && (!x || !quat)) || pairs_cap < 0 || (pairs_cap > 0 && !pairs))
         return ALENS_ERR_INVALID;
     long long cap = std::min<long long>(pairs_cap, c->max_pairs);
-    aLENS_status st = search_phase(c, (int)n, x, quat, nullptr, cap);
-    if (st != ALENS_OK) return st;
+    aLENS_status st = search_phase(c, (int)n, x, quat, nullptr);
     long long total = (long long)c->hcount[C_PAIRS];
     *n_pairs = total;
+    if (st != ALENS_OK) return st;
     if (total > cap) return ALENS_ERR_CAPACITY;
     CK(launch_emit_pairs(c, (int)n, pairs));
     CK(cudaStreamSynchronize(c->stream));
@@ -370,7 +383,7 @@ static void fill_info(aLENS_ctx* c, aLENS_info* info, int64_t m, aLENS_status st
     info->min_gap = decode_gap(c->hcount[C_MINGAP]);
     info->iters = c->hflags[F_ITERS];
     double res;
-    memcpy(&res, &c->hcount[4], sizeof(res));
+    memcpy(&res, &c->hcount[C_RESID], sizeof(res));
     info->residual = m > 0 ? res : 0.0;
     info->status = (int32_t)st;
     info->launches = c->launches;
@@ -382,7 +395,7 @@ static aLENS_status solve_status(aLENS_ctx* c, int64_t m)
     if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
     if (m > 0) {
         double res;
-        memcpy(&res, &c->hcount[4], sizeof(res));
+        memcpy(&res, &c->hcount[C_RESID], sizeof(res));
         if (!(res <= c->p.tol)) return ALENS_ERR_NOT_CONVERGED;
     }
     return ALENS_OK;
@@ -428,7 +441,7 @@ aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const 
     if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;
     if (!c->coop_ok) return ALENS_ERR_CUDA;
     CK(cudaEventRecord(c->ev[0], c->stream));
-    aLENS_status st = search_phase(c, (int)n, x, quat, f_nc, c->max_pairs);
+    aLENS_status st = search_phase(c, (int)n, x, quat, f_nc);
     if (st != ALENS_OK) {
         if (info) { memset(info, 0, sizeof(*info)); info->status = st; info->n_pairs = (int64_t)c->hcount[C_PAIRS]; }
         return st;

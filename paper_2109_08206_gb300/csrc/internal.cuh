@@ -29,7 +29,7 @@ enum Flag : int {
     F_NFLAGS = 16
 };
 // 64-bit counters (Ctx::dcount)
-enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_NCOUNT = 8 };
+enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_NCOUNT = 8 };
 
 // ------------------------------------------------------------ plain structs
 
@@ -42,7 +42,8 @@ struct Geo {                 // everything the geometry kernels need
     double rcut;             // L + D + delta_c: centre-distance bound for a close pair
     float boxf[3];
     float rcut_screen2;      // (rcut + margin)^2 for the float pre-screen
-    float gap_screen;        // delta_c + margin for the float segment screen
+    float screen_d2;         // (D + delta_c + margin)^2 for the float segment screen
+    float half_f;            // L/2 in float
 };
 
 struct Mob {                 // inverse drag coefficients of one rod (all rods alike)
@@ -163,9 +164,8 @@ struct SolveBufs {           // typed views into the solver workspace
     T* qe;                   // [6][mp]  per Q-side entry: e, y_Q x e (CSR order)
     T* q;                    // [mp]
     T* ax;                   // [3][np]
-    T* gam[2];               // [mp] x 2
-    T* grad[2];              // [mp] x 2
-    T* U;                    // [6][np]
+    T* gg[2];                // [mp][2] x 2: (gamma, g) interleaved, ping-pong
+    T* U;                    // [np][6] constraint velocity M D gamma
 };
 
 }  // namespace alens
@@ -193,9 +193,12 @@ struct aLENS_ctx {
     int* cell_count;         // [max_keys + 1]
     int* cell_start;         // [max_keys + 1]
     int* cell_cursor;        // [max_keys]
-    int* rod_count;          // [np + 1]
-    long long* rod_tmpstart; // [np]
-    uint32_t* tmp_keys;      // [mp]
+    int* rod_count;          // [np + 1] kept pairs per rod (i < j side)
+    int* rod_ncand;          // [np] screened candidates per rod
+    long long* rod_tmpstart; // [np] start of the rod's candidate segment
+    unsigned long long* cand;// [cand_cap] candidate keys (i << 32 | j << 5 | image)
+    unsigned char* keep;     // [cand_cap] float64 decision per candidate
+    long long cand_cap;
     int* rowP;               // [np + 1]
     int* rowQ;               // [np + 1]
     int* cntQ;               // [np + 1]
@@ -237,7 +240,11 @@ cudaError_t exclusive_scan(aLENS_ctx* ctx, const int* counts, int* out, int n);
 // neighbors.cu
 cudaError_t launch_pack(aLENS_ctx* ctx, int n, const double* x, const double* quat, const double* fnc, bool cells);
 cudaError_t launch_cell_sort(aLENS_ctx* ctx, int n);
-cudaError_t launch_search(aLENS_ctx* ctx, int n, long long cap);
+// Screens candidates (float32) into the candidate buffer and decides them
+// (float64); per-rod kept counts in rod_count, totals in dcount.
+cudaError_t launch_search(aLENS_ctx* ctx, int n);
+// Exact pair count only (float64 inline), for a candidate-buffer overflow.
+cudaError_t launch_search_count(aLENS_ctx* ctx, int n);
 cudaError_t launch_emit_pairs(aLENS_ctx* ctx, int n, int32_t* pairs_out);
 
 // assemble.cu

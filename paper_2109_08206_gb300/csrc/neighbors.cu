@@ -87,48 +87,39 @@ __global__ void k_cell_scatter(int n, const uint32_t* __restrict__ cellkey, cons
     sax32[pos] = ax32[i];
 }
 
-// Order rods inside each cell by id, so that the cell-sorted layout (and the
-// order in which the search meets candidates) does not depend on atomics.
-__global__ void k_cell_order(int nkeys, const int* __restrict__ cell_start, int* __restrict__ sorted_id,
-                             float4* __restrict__ spos32, float4* __restrict__ sax32)
-{
-    int key = blockIdx.x * blockDim.x + threadIdx.x;
-    if (key >= nkeys) return;
-    int b = cell_start[key], e = cell_start[key + 1];
-    for (int u = b + 1; u < e; ++u) {
-        int id = sorted_id[u];
-        float4 ps = spos32[u], as = sax32[u];
-        int v = u - 1;
-        while (v >= b && sorted_id[v] > id) {
-            sorted_id[v + 1] = sorted_id[v];
-            spos32[v + 1] = spos32[v];
-            sax32[v + 1] = sax32[v];
-            --v;
-        }
-        sorted_id[v + 1] = id;
-        spos32[v + 1] = ps;
-        sax32[v + 1] = as;
-    }
-}
-
-// Float32 lower-level screen of one candidate: returns false only when the
-// pair is certainly farther than delta_c (with margin); near-parallel pairs
-// always pass to the float64 decision.
+// Float32 screen of one candidate.  Returns false only when the pair is
+// certainly farther apart than delta_c: the clamped closest-point pair below
+// is always a valid point pair of the two (float-rounded) segments, and away
+// from near-parallel axes it is the optimum up to rounding, so its squared
+// distance exceeds (D + delta_c + margin)^2 only if the float64 gap exceeds
+// delta_c.  Unit axes are taken as unit (a = c = 1); near-parallel pairs
+// (1 - (p.q)^2 <= 1e-4) always go on to the float64 decision.
 __device__ __forceinline__ bool screen32(const float4& pi, const float4& ai, const float4& pj, const float4& aj,
                                          float sx, float sy, float sz, const Geo& g)
 {
     float dx[3] = {pi.x - pj.x - sx, pi.y - pj.y - sy, pi.z - pj.z - sz};
     float r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
     if (!(r2 < g.rcut_screen2)) return false;
-    float p[3] = {ai.x, ai.y, ai.z}, q[3] = {aj.x, aj.y, aj.z};
-    float b = p[0] * q[0] + p[1] * q[1] + p[2] * q[2];
+    float b = ai.x * aj.x + ai.y * aj.y + ai.z * aj.z;
     float det = 1.0f - b * b;
-    if (det <= kParallelDet32) return true;   // near-parallel: decide in float64
-    float s, t;
-    float d = segment_closest<float>(dx, p, q, (float)g.half, kParallelDet32, s, t);
-    return d - (float)g.diameter < g.gap_screen;
+    if (det <= kParallelDet32) return true;
+    float d = ai.x * dx[0] + ai.y * dx[1] + ai.z * dx[2];
+    float e = aj.x * dx[0] + aj.y * dx[1] + aj.z * dx[2];
+    const float hl = g.half_f;
+    float s = fminf(fmaxf(__fdividef(b * e - d, det), -hl), hl);
+    float t = b * s + e;
+    if (t < -hl || t > hl) {
+        t = fminf(fmaxf(t, -hl), hl);
+        s = fminf(fmaxf(b * t - d, -hl), hl);
+    }
+    float r0 = dx[0] + s * ai.x - t * aj.x;
+    float r1 = dx[1] + s * ai.y - t * aj.y;
+    float r2b = dx[2] + s * ai.z - t * aj.z;
+    return r0 * r0 + r1 * r1 + r2b * r2b < g.screen_d2;
 }
 
+// Float64 keep/drop decision of pair (i, j) at image shift k: surface gap
+// |r| - D < delta_c at the closest points.
 __device__ __forceinline__ bool decide64(int i, int j, int k0, int k1, int k2, int np, const double* __restrict__ xw,
                                          const double* __restrict__ axis, const Geo& g)
 {
@@ -145,30 +136,41 @@ __device__ __forceinline__ bool decide64(int i, int j, int k0, int k1, int k2, i
     return d - g.diameter < g.delta_c;
 }
 
+__device__ __forceinline__ void decode_cell(uint32_t key, int bits, int cc[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        uint32_t v = 0;
+        for (int bit = 0; bit < bits; ++bit) v |= ((key >> (3 * bit + a)) & 1u) << bit;
+        cc[a] = (int)v;
+    }
+}
+
+// One warp per rod i (rods taken in cell order for locality of the candidate
+// loads).  Lanes stride over the rods of the 27 neighbour cells (each cell
+// visited with the periodic image shift that brings it next to i's cell);
+// candidates j > i that pass the float32 screen are appended to a per-warp
+// list in shared memory with a warp ballot, sorted there by (j, image) with a
+// bitonic network, and written to the candidate buffer as 64-bit keys
+// (i << 32 | j << 5 | image).  COUNT_ONLY: decide in float64 inline and only
+// count the kept pairs (used when the candidate buffer overflows).
+template <bool COUNT_ONLY>
 __global__ void __launch_bounds__(kSearchWarps * 32)
 k_search(int n, int np, Geo g, const int* __restrict__ sorted_id, const float4* __restrict__ spos32,
          const float4* __restrict__ sax32, const uint32_t* __restrict__ cellkey, const double* __restrict__ xw,
-         const double* __restrict__ axis, const int* __restrict__ cell_start, int* __restrict__ rod_count,
-         long long* __restrict__ rod_tmpstart, uint32_t* __restrict__ tmp_keys, long long cap,
+         const double* __restrict__ axis, const int* __restrict__ cell_start, int* __restrict__ rod_ncand,
+         long long* __restrict__ rod_tmpstart, unsigned long long* __restrict__ cand, long long cand_cap,
          unsigned long long* __restrict__ counters, int* __restrict__ flags)
 {
-    __shared__ uint32_t list[kSearchWarps][kPairsPerRodCap];
+    __shared__ uint32_t list[COUNT_ONLY ? 1 : kSearchWarps][COUNT_ONLY ? 1 : kPairsPerRodCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x * kSearchWarps + warp;
     if (k >= n) return;   // uniform per warp
-    uint32_t* L = list[warp];
+    uint32_t* L = list[COUNT_ONLY ? 0 : warp];
     const int i = sorted_id[k];
     const float4 pi = spos32[k], ai = sax32[k];
     int cc[3];
-    {
-        uint32_t key = cellkey[i];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            uint32_t v = 0;
-            for (int bit = 0; bit < g.bits; ++bit) v |= ((key >> (3 * bit + a)) & 1u) << bit;
-            cc[a] = (int)v;
-        }
-    }
+    decode_cell(cellkey[i], g.bits, cc);
     int cnt = 0;
     for (int o = 0; o < 27; ++o) {
         int d[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
@@ -190,16 +192,20 @@ k_search(int n, int np, Geo g, const int* __restrict__ sorted_id, const float4* 
             int j = 0;
             if (m < end) {
                 j = sorted_id[m];
-                if (j > i && screen32(pi, ai, spos32[m], sax32[m], sx, sy, sz, g))
-                    keep = decide64(i, j, sh[0], sh[1], sh[2], np, xw, axis, g);
+                keep = j > i && screen32(pi, ai, spos32[m], sax32[m], sx, sy, sz, g);
+                if (COUNT_ONLY && keep) keep = decide64(i, j, sh[0], sh[1], sh[2], np, xw, axis, g);
             }
             unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
+            if (!COUNT_ONLY && keep) {
                 int pos = cnt + __popc(bal & ((1u << lane) - 1u));
                 if (pos < kPairsPerRodCap) L[pos] = ((uint32_t)j << 5) | code;
             }
             cnt += __popc(bal);
         }
+    }
+    if (COUNT_ONLY) {
+        if (lane == 0) atomicAdd(&counters[C_PAIRS], (unsigned long long)cnt);
+        return;
     }
     __syncwarp();
     if (cnt > kPairsPerRodCap) {
@@ -225,28 +231,61 @@ k_search(int n, int np, Geo g, const int* __restrict__ sorted_id, const float4* 
     }
     long long start = 0;
     if (lane == 0) {
-        start = (long long)atomicAdd(&counters[C_PAIRS], (unsigned long long)cnt);
-        rod_count[i] = cnt;
+        start = (long long)atomicAdd(&counters[C_CAND], (unsigned long long)cnt);
+        rod_ncand[i] = cnt;
         rod_tmpstart[i] = start;
     }
     start = __shfl_sync(0xffffffffu, start, 0);
+    const unsigned long long hi = (unsigned long long)(unsigned)i << 32;
     for (int u = lane; u < cnt; u += 32)
-        if (start + u < cap) tmp_keys[start + u] = L[u];
+        if (start + u < cand_cap) cand[start + u] = hi | L[u];
 }
 
-__global__ void k_emit(int n, const int* __restrict__ rod_count, const long long* __restrict__ rod_tmpstart,
-                       const int* __restrict__ rowP, const uint32_t* __restrict__ tmp_keys, int32_t* __restrict__ out)
+// Float64 decision of every candidate (grid-stride, full warps): keep flag,
+// per-rod kept count and the total.
+__global__ void k_decide(int np, Geo g, const unsigned long long* counters_ro,
+                         const unsigned long long* __restrict__ cand, long long cand_cap,
+                         const double* __restrict__ xw, const double* __restrict__ axis,
+                         unsigned char* __restrict__ keep, int* __restrict__ rod_count,
+                         unsigned long long* counters)
+{
+    long long total = (long long)counters_ro[C_CAND];
+    if (total > cand_cap) total = cand_cap;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k0 = (long long)blockIdx.x * blockDim.x; k0 < total; k0 += stride) {
+        long long k = k0 + threadIdx.x;
+        bool kp = false;
+        if (k < total) {
+            unsigned long long key = cand[k];
+            int i = (int)(key >> 32);
+            int j = (int)((key >> 5) & 0x7ffffffu);
+            int code = (int)(key & 31u);
+            kp = decide64(i, j, code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1, np, xw, axis, g);
+            keep[k] = kp ? 1 : 0;
+            if (kp) atomicAdd(&rod_count[i], 1);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, kp);
+        if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&counters[C_PAIRS], (unsigned long long)__popc(bal));
+    }
+}
+
+// Pairs of rod i in (j, image) order: the kept candidates of its segment.
+__global__ void k_emit(int n, const int* __restrict__ rod_ncand, const long long* __restrict__ rod_tmpstart,
+                       const int* __restrict__ rowP, const unsigned long long* __restrict__ cand,
+                       const unsigned char* __restrict__ keep, int32_t* __restrict__ out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int c = rod_count[i];
+    int c = rod_ncand[i];
     long long s = rod_tmpstart[i];
     long long o = rowP[i];
     for (int u = 0; u < c; ++u) {
-        uint32_t key = tmp_keys[s + u];
-        out[3 * (o + u) + 0] = i;
-        out[3 * (o + u) + 1] = (int32_t)(key >> 5);
-        out[3 * (o + u) + 2] = (int32_t)(key & 31u);
+        if (!keep[s + u]) continue;
+        uint32_t key = (uint32_t)cand[s + u];
+        out[3 * o + 0] = i;
+        out[3 * o + 1] = (int32_t)(key >> 5);
+        out[3 * o + 2] = (int32_t)(key & 31u);
+        ++o;
     }
 }
 
@@ -273,18 +312,29 @@ cudaError_t launch_cell_sort(aLENS_ctx* ctx, int n)
                                                               ctx->sax32);
         ++ctx->launches;
     }
-    k_cell_order<<<nblk(nkeys, 256), 256, 0, ctx->stream>>>(nkeys, ctx->cell_start, ctx->sorted_id, ctx->spos32,
-                                                            ctx->sax32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_search(aLENS_ctx* ctx, int n)
+{
+    if (n <= 0) return cudaSuccess;
+    k_search<false><<<nblk(n, kSearchWarps), kSearchWarps * 32, 0, ctx->stream>>>(
+        n, (int)ctx->max_rods, ctx->geo, ctx->sorted_id, ctx->spos32, ctx->sax32, ctx->cellkey, ctx->xw, ctx->axis,
+        ctx->cell_start, ctx->rod_ncand, ctx->rod_tmpstart, ctx->cand, ctx->cand_cap, ctx->dcount, ctx->dflags);
+    ++ctx->launches;
+    k_decide<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>((int)ctx->max_rods, ctx->geo, ctx->dcount, ctx->cand,
+                                                         ctx->cand_cap, ctx->xw, ctx->axis, ctx->keep,
+                                                         ctx->rod_count, ctx->dcount);
     ++ctx->launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_search(aLENS_ctx* ctx, int n, long long cap)
+cudaError_t launch_search_count(aLENS_ctx* ctx, int n)
 {
     if (n <= 0) return cudaSuccess;
-    k_search<<<nblk(n, kSearchWarps), kSearchWarps * 32, 0, ctx->stream>>>(
+    k_search<true><<<nblk(n, kSearchWarps), kSearchWarps * 32, 0, ctx->stream>>>(
         n, (int)ctx->max_rods, ctx->geo, ctx->sorted_id, ctx->spos32, ctx->sax32, ctx->cellkey, ctx->xw, ctx->axis,
-        ctx->cell_start, ctx->rod_count, ctx->rod_tmpstart, ctx->tmp_keys, cap, ctx->dcount, ctx->dflags);
+        ctx->cell_start, ctx->rod_ncand, ctx->rod_tmpstart, ctx->cand, ctx->cand_cap, ctx->dcount, ctx->dflags);
     ++ctx->launches;
     return cudaGetLastError();
 }
@@ -294,8 +344,8 @@ cudaError_t launch_emit_pairs(aLENS_ctx* ctx, int n, int32_t* pairs_out)
     cudaError_t e = exclusive_scan(ctx, ctx->rod_count, ctx->rowP, n);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        k_emit<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, ctx->rod_count, ctx->rod_tmpstart, ctx->rowP,
-                                                      ctx->tmp_keys, pairs_out);
+        k_emit<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, ctx->rod_ncand, ctx->rod_tmpstart, ctx->rowP, ctx->cand,
+                                                      ctx->keep, pairs_out);
         ++ctx->launches;
     }
     return cudaGetLastError();

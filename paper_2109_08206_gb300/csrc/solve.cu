@@ -15,22 +15,27 @@
 // Stop when (h/D) max |pi_c| <= tol (pi the projected gradient) or after
 // max_iter iterations.
 //
-// One persistent cooperative kernel runs the whole loop.  Per iteration:
+// One persistent cooperative kernel runs the whole loop, one block per SM.
+// Per iteration:
 //   phase A (one thread per rod): gamma_{k+1} of every constraint touching
-//     the rod is formed on the fly from gamma_k, g_k and alpha_k (the P-side
+//     the rod is formed on the fly from (gamma_k, g_k) and alpha_k (the P-side
 //     rod stores it), summed into the rod's force and torque F = D gamma
 //     (P-range contiguous, Q-side list in CSR order), and U = M F is stored;
 //   grid barrier;
-//   phase B (one thread per constraint): g_{k+1} = q + D^T U, plus the four
-//     float64 partial reductions s.s, s.y, y.y and max |pi|, reduced per block
-//     with warp shuffles in a fixed order;
-//   grid barrier; every block then reduces the per-block partials in the
-//     same fixed order, so all blocks take identical step decisions.
+//   phase B (one thread per constraint): g_{k+1} = q + D^T U, and the partial
+//     sums s.s, s.y, y.y and max |pi|: per thread and per warp in the working
+//     precision, across warps and blocks in float64, in a fixed order;
+//   grid barrier; warp 0 of every block then reduces the per-block partials
+//     in the same fixed order, so all blocks take identical step decisions.
 // Two grid barriers per iteration.  Each barrier wait is bounded in time
-// and iterations; a wait that runs out raises ALENS_ERR_TIMEOUT in the
-// device status word and every block leaves.
-// T = double (float64 plain) or float (mixed: the D, M, D^T work in float32,
-// every reduction and the residual in float64).
+// and in polls; a wait that runs out raises ALENS_ERR_TIMEOUT in the device
+// status word and every block leaves.
+//
+// Layout: (gamma, g) interleaved per constraint in two ping-pong buffers,
+// U as [rod][6] (one or two sectors per gather), D records SoA [9][m].
+// T = double (float64 plain) or float (mixed: the D, M, D^T work, per-thread
+// and per-warp sums in float32; the cross-warp and cross-block sums, the
+// residual test and the step sizes in float64; max |pi| is exact in either).
 #include <float.h>
 
 #include "internal.cuh"
@@ -38,6 +43,35 @@
 namespace alens {
 
 enum { A_RAW = 0, A_STEP = 1, A_PG = 2 };
+
+template <typename T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+
+template <typename T>
+__device__ __forceinline__ void ld_pair(const T* p, int c, T& a, T& b)
+{
+    typename V2<T>::t v = reinterpret_cast<const typename V2<T>::t*>(p)[c];
+    a = v.x;
+    b = v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ void ld_u6(const T* U, int i, T u[6])
+{
+    const typename V2<T>::t* p = reinterpret_cast<const typename V2<T>::t*>(U + 6 * (size_t)i);
+    typename V2<T>::t a = p[0], b = p[1], c = p[2];
+    u[0] = a.x; u[1] = a.y; u[2] = b.x; u[3] = b.y; u[4] = c.x; u[5] = c.y;
+}
+
+template <typename T>
+__device__ __forceinline__ void st_u6(T* U, int i, const T u[6])
+{
+    typename V2<T>::t* p = reinterpret_cast<typename V2<T>::t*>(U + 6 * (size_t)i);
+    typename V2<T>::t a, b, c;
+    a.x = u[0]; a.y = u[1]; b.x = u[2]; b.y = u[3]; c.x = u[4]; c.y = u[5];
+    p[0] = a; p[1] = b; p[2] = c;
+}
 
 template <typename T>
 struct SolveArgs {
@@ -51,10 +85,8 @@ struct SolveArgs {
     const T* __restrict__ qe;
     const T* __restrict__ q;
     const T* __restrict__ ax;
-    T* gam0;    // written inside the kernel: no __restrict__/const (no non-coherent loads)
-    T* gam1;
-    T* grad0;
-    T* grad1;
+    T* gg0;     // written inside the kernel: plain (coherent) loads only
+    T* gg1;
     T* U;
     double* partials;
     unsigned* bar;
@@ -78,18 +110,24 @@ __device__ __forceinline__ T a_value(T g, T gr, T alpha)
     return g > T(0) ? gr : (gr < T(0) ? gr : T(0));
 }
 
+// Rod-parallel half of the gradient: F = D gamma' and U = M F for every rod,
+// gamma' per MODE (A_RAW: gamma itself; A_STEP: max(0, gamma - alpha g),
+// stored by the P-side rod; A_PG: the projected gradient, returning the
+// thread's share of pi.A.pi = sum_rods F.M.F instead of storing U).
 template <typename T, int MODE>
-__device__ __forceinline__ double phase_a(const SolveArgs<T>& a, const T* gc, const T* grc, T* gn, T alpha)
+__device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const T* gc, T* gn, T alpha)
 {
-    double fmf = 0.0;
+    T fmf = T(0);
     const int stride = gridDim.x * blockDim.x;
     const size_t mp = a.mp, np = a.np;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         int b = a.rowP[i], e = a.rowP[i + 1];
         for (int c = b; c < e; ++c) {
-            T v = a_value<MODE, T>(gc[c], grc[c], alpha);
-            if (MODE == A_STEP) gn[c] = v;
+            T g, gr;
+            ld_pair(gc, c, g, gr);
+            T v = a_value<MODE, T>(g, gr, alpha);
+            if (MODE == A_STEP) gn[2 * (size_t)c] = v;
 #pragma unroll
             for (int u = 0; u < 6; ++u) F[u] += v * a.rec[u * mp + c];
         }
@@ -97,7 +135,9 @@ __device__ __forceinline__ double phase_a(const SolveArgs<T>& a, const T* gc, co
         e = a.rowQ[i + 1];
         for (int k = b; k < e; ++k) {
             int c = a.qlist[k];
-            T v = a_value<MODE, T>(gc[c], grc[c], alpha);
+            T g, gr;
+            ld_pair(gc, c, g, gr);
+            T v = a_value<MODE, T>(g, gr, alpha);
 #pragma unroll
             for (int u = 0; u < 6; ++u) F[u] -= v * a.qe[u * mp + k];
         }
@@ -109,45 +149,46 @@ __device__ __forceinline__ double phase_a(const SolveArgs<T>& a, const T* gc, co
                    F[3] * a.inv_rot + p0 * ct,  F[4] * a.inv_rot + p1 * ct,  F[5] * a.inv_rot + p2 * ct};
         if (MODE == A_PG) {
 #pragma unroll
-            for (int u = 0; u < 6; ++u) fmf += (double)F[u] * (double)Uv[u];
+            for (int u = 0; u < 6; ++u) fmf += F[u] * Uv[u];
         } else {
-#pragma unroll
-            for (int u = 0; u < 6; ++u) a.U[u * np + i] = Uv[u];
+            st_u6(a.U, i, Uv);
         }
     }
     return fmf;
 }
 
-// g_new = q + D^T U for every constraint, plus the partial reductions:
-// FIRST: acc0 = pi.pi, acc3 = max |pi|; otherwise acc0..2 = s.s, s.y, y.y,
-// acc3 = max |pi|, with s = gnew - gold and y = grnew - grold.
+// Constraint-parallel half: g_new = q + D^T U, written into the y slot of
+// the new (gamma, g) pair, plus the thread's partial sums.
+// FIRST: acc0 = pi.pi; otherwise acc0..2 = s.s, s.y, y.y; acc3 = max |pi|.
 template <typename T, bool FIRST>
-__device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const T* gnew, const T* gold, const T* grold,
-                                        T* grnew, double acc[4])
+__device__ __forceinline__ void phase_b(const SolveArgs<T>& a, T* gnew, const T* gold, T acc[4])
 {
     const int stride = gridDim.x * blockDim.x;
-    const size_t mp = a.mp, np = a.np;
+    const size_t mp = a.mp;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.m; c += stride) {
         int i = a.ci[c], j = a.cj[c];
+        T Ui[6], Uj[6];
+        ld_u6(a.U, i, Ui);
+        ld_u6(a.U, j, Uj);
         T du = T(0);
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
-            T e = a.rec[u * mp + c];
-            du += e * (a.U[u * np + i] - a.U[u * np + j]);
-            du += a.rec[(3 + u) * mp + c] * a.U[(3 + u) * np + i];
-            du -= a.rec[(6 + u) * mp + c] * a.U[(3 + u) * np + j];
+            du += a.rec[u * mp + c] * (Ui[u] - Uj[u]);
+            du += a.rec[(3 + u) * mp + c] * Ui[3 + u];
+            du -= a.rec[(6 + u) * mp + c] * Uj[3 + u];
         }
         T gr = a.q[c] + du;
-        grnew[c] = gr;
-        T gm = gnew[c];
+        T gm = gnew[2 * (size_t)c];
+        gnew[2 * (size_t)c + 1] = gr;
         T pi = gm > T(0) ? gr : (gr < T(0) ? gr : T(0));
-        double api = fabs((double)pi);
+        T api = pi < T(0) ? -pi : pi;
         acc[3] = api > acc[3] ? api : acc[3];
         if (FIRST) {
-            acc[0] += (double)pi * (double)pi;
+            acc[0] += pi * pi;
         } else {
-            double s = (double)gm - (double)gold[c];
-            double y = (double)gr - (double)grold[c];
+            T go, gro;
+            ld_pair(gold, c, go, gro);
+            T s = gm - go, y = gr - gro;
             acc[0] += s * s;
             acc[1] += s * y;
             acc[2] += y * y;
@@ -155,21 +196,22 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const T* gnew, co
     }
 }
 
-// Block reduction of 4 values (sums in 0..2, max in 3); result broadcast to
-// every thread through shared memory.  Fixed order: deterministic.
-__device__ __forceinline__ void block_reduce4(double v[4], double (*red)[4], double* bc)
+// Block partial of (sum, sum, sum, max): warp shuffles in T, then warp 0
+// combines the warp results in float64 and lane 0 stores them.  Fixed order.
+template <typename T>
+__device__ __forceinline__ void block_partial(T v[4], double (*red)[4], double* dst)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
         for (int u = 0; u < 3; ++u) v[u] += __shfl_down_sync(0xffffffffu, v[u], o);
-        double m = __shfl_down_sync(0xffffffffu, v[3], o);
-        v[3] = m > v[3] ? m : v[3];
+        T mx = __shfl_down_sync(0xffffffffu, v[3], o);
+        v[3] = mx > v[3] ? mx : v[3];
     }
     if (lane == 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) red[warp][u] = v[u];
+        for (int u = 0; u < 4; ++u) red[warp][u] = (double)v[u];
     }
     __syncthreads();
     if (warp == 0) {
@@ -182,18 +224,14 @@ __device__ __forceinline__ void block_reduce4(double v[4], double (*red)[4], dou
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
             for (int u = 0; u < 3; ++u) w[u] += __shfl_down_sync(0xffffffffu, w[u], o);
-            double m = __shfl_down_sync(0xffffffffu, w[3], o);
-            w[3] = m > w[3] ? m : w[3];
+            double mx = __shfl_down_sync(0xffffffffu, w[3], o);
+            w[3] = mx > w[3] ? mx : w[3];
         }
         if (lane == 0) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) bc[u] = w[u];
+            for (int u = 0; u < 4; ++u) dst[u] = w[u];
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = bc[u];
-    __syncthreads();
 }
 
 // Bounded grid barrier on a monotone arrival counter: block b's k-th arrival
@@ -223,83 +261,87 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, i
     return ld_volatile_i32(&flags[F_SOLVE_ERR]) == 0;
 }
 
-// Every block reduces the per-block partials in the same fixed order.
-__device__ __forceinline__ void grid_reduce4(const double* partials, int nb, double v[4], double (*red)[4],
-                                             double* bc)
+// After a barrier: warp 0 reduces the per-block partials in float64 in a
+// fixed order and broadcasts the four totals through shared memory.
+__device__ __forceinline__ void grid_total(const double* partials, int nb, double* bc, double out[4])
 {
-    v[0] = v[1] = v[2] = v[3] = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const volatile double* pb = partials + 4 * (size_t)b;
-        v[0] += pb[0];
-        v[1] += pb[1];
-        v[2] += pb[2];
-        double m = pb[3];
-        v[3] = m > v[3] ? m : v[3];
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double w[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = lane; b < nb; b += 32) {
+            const volatile double* pb = partials + 4 * (size_t)b;
+            w[0] += pb[0];
+            w[1] += pb[1];
+            w[2] += pb[2];
+            double mx = pb[3];
+            w[3] = mx > w[3] ? mx : w[3];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int u = 0; u < 3; ++u) w[u] += __shfl_down_sync(0xffffffffu, w[u], o);
+            double mx = __shfl_down_sync(0xffffffffu, w[3], o);
+            w[3] = mx > w[3] ? mx : w[3];
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) bc[u] = w[u];
+        }
     }
-    block_reduce4(v, red, bc);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) out[u] = bc[u];
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_bbpgd(SolveArgs<T> a)
+__global__ void __launch_bounds__(1024, 1) k_bbpgd(SolveArgs<T> a)
 {
     __shared__ double red[32][4];
     __shared__ double bc[4];
     if (a.fault == 1 && blockIdx.x == 0) return;   // test hook: this block never arrives
     const unsigned nb = gridDim.x;
+    double* mine = a.partials + 4 * (size_t)blockIdx.x;
     unsigned epoch = 0;
-    T* gam[2] = {a.gam0, a.gam1};
-    T* grad[2] = {a.grad0, a.grad1};
-    double v[4];
+    T* gg[2] = {a.gg0, a.gg1};
+    double tot[4];
+    T v[4];
 
     // U = M D gamma_0
-    phase_a<T, A_RAW>(a, gam[0], grad[0], nullptr, T(0));
+    phase_a<T, A_RAW>(a, gg[0], nullptr, T(0));
     if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
     // g_0 and the projected gradient at gamma_0
-    v[0] = v[1] = v[2] = v[3] = 0.0;
-    phase_b<T, true>(a, gam[0], nullptr, nullptr, grad[0], v);
-    block_reduce4(v, red, bc);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a.partials[4 * (size_t)blockIdx.x + u] = v[u];
-    }
+    v[0] = v[1] = v[2] = v[3] = T(0);
+    phase_b<T, true>(a, gg[0], nullptr, v);
+    block_partial(v, red, mine);
     if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
-    grid_reduce4(a.partials, nb, v, red, bc);
-    const double pp = v[0];
-    double res = a.hD * v[3];
+    grid_total(a.partials, nb, bc, tot);
+    const double pp = tot[0];
+    double res = a.hD * tot[3];
     int cur = 0, iters = 0;
     if (res > a.tol && a.max_iter > 0) {
         // alpha_0 = pi.pi / pi.A.pi (exact line step along the projected gradient)
-        double fmf = phase_a<T, A_PG>(a, gam[0], grad[0], nullptr, T(0));
-        v[0] = fmf; v[1] = v[2] = v[3] = 0.0;
-        block_reduce4(v, red, bc);
-        if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;   // all reads of partials done
-        if (threadIdx.x == 0) a.partials[4 * (size_t)blockIdx.x] = v[0];
-        if (threadIdx.x == 0) {
-            a.partials[4 * (size_t)blockIdx.x + 1] = 0.0;
-            a.partials[4 * (size_t)blockIdx.x + 2] = 0.0;
-            a.partials[4 * (size_t)blockIdx.x + 3] = 0.0;
-        }
+        v[0] = phase_a<T, A_PG>(a, gg[0], nullptr, T(0));
+        v[1] = v[2] = v[3] = T(0);
+        // every block has read the partials (grid_total) before any rewrites them
         if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
-        grid_reduce4(a.partials, nb, v, red, bc);
-        const double pap = v[0];
+        block_partial(v, red, mine);
+        if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
+        grid_total(a.partials, nb, bc, tot);
+        const double pap = tot[0];
         double alpha0 = pp / pap;
         if (!(pap > 0.0) || !isfinite(alpha0) || !(alpha0 > 0.0)) alpha0 = 1.0;
         double alpha = alpha0;
         for (int k = 0; k < a.max_iter; ++k) {
             const int nx = cur ^ 1;
-            phase_a<T, A_STEP>(a, gam[cur], grad[cur], gam[nx], (T)alpha);
+            phase_a<T, A_STEP>(a, gg[cur], gg[nx], (T)alpha);
             if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
-            v[0] = v[1] = v[2] = v[3] = 0.0;
-            phase_b<T, false>(a, gam[nx], gam[cur], grad[cur], grad[nx], v);
-            block_reduce4(v, red, bc);
-            if (threadIdx.x == 0) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) a.partials[4 * (size_t)blockIdx.x + u] = v[u];
-            }
+            v[0] = v[1] = v[2] = v[3] = T(0);
+            phase_b<T, false>(a, gg[nx], gg[cur], v);
+            block_partial(v, red, mine);
             if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
-            grid_reduce4(a.partials, nb, v, red, bc);
-            const double ss = v[0], sy = v[1], yy = v[2];
-            res = a.hD * v[3];
+            grid_total(a.partials, nb, bc, tot);
+            const double ss = tot[0], sy = tot[1], yy = tot[2];
+            res = a.hD * tot[3];
             cur = nx;
             iters = k + 1;
             if (!(res > a.tol)) break;
@@ -317,13 +359,13 @@ __global__ void __launch_bounds__(512) k_bbpgd(SolveArgs<T> a)
 }
 
 template <typename T>
-__global__ void k_gamma_out(int m, const int* __restrict__ flags, const T* g0, const T* g1, double* __restrict__ out)
+__global__ void k_gamma_out(int m, const int* __restrict__ flags, const T* gg0, const T* gg1, double* __restrict__ out)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
     if (flags[F_SOLVE_ERR] != 0) return;
-    const T* g = flags[F_FINAL] == 0 ? g0 : g1;
-    out[c] = (double)g[c];
+    const T* g = flags[F_FINAL] == 0 ? gg0 : gg1;
+    out[c] = (double)g[2 * (size_t)c];
 }
 
 template <typename T>
@@ -333,9 +375,9 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     a.n = n; a.m = m; a.np = (int)ctx->max_rods; a.mp = (int)ctx->max_pairs;
     a.rowP = ctx->rowP; a.rowQ = ctx->rowQ; a.qlist = ctx->qlist; a.ci = ctx->ci; a.cj = ctx->cj;
     a.rec = sb.rec; a.qe = sb.qe; a.q = sb.q; a.ax = sb.ax;
-    a.gam0 = sb.gam[0]; a.gam1 = sb.gam[1]; a.grad0 = sb.grad[0]; a.grad1 = sb.grad[1]; a.U = sb.U;
+    a.gg0 = sb.gg[0]; a.gg1 = sb.gg[1]; a.U = sb.U;
     a.partials = ctx->partials; a.bar = ctx->bar; a.flags = ctx->dflags;
-    a.out = reinterpret_cast<double*>(ctx->dcount + 4);
+    a.out = reinterpret_cast<double*>(ctx->dcount + C_RESID);
     a.inv_perp = (T)ctx->mob.inv_perp; a.inv_par = (T)ctx->mob.inv_par;
     a.inv_rot = (T)ctx->mob.inv_rot; a.inv_spin = (T)ctx->mob.inv_spin;
     a.hD = ctx->p.dt / ctx->p.diameter; a.tol = ctx->p.tol; a.max_iter = ctx->p.max_iter;
@@ -371,12 +413,11 @@ cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma
     if (m <= 0 || !gamma_out) return cudaSuccess;
     int b = (m + 255) / 256;
     if (precision == ALENS_MIXED) {
-        k_gamma_out<float><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->sb32.gam[0], ctx->sb32.gam[1], gamma_out);
-        ++ctx->launches;
+        k_gamma_out<float><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->sb32.gg[0], ctx->sb32.gg[1], gamma_out);
     } else {
-        k_gamma_out<double><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->sb64.gam[0], ctx->sb64.gam[1], gamma_out);
-        ++ctx->launches;
+        k_gamma_out<double><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->sb64.gg[0], ctx->sb64.gg[1], gamma_out);
     }
+    ++ctx->launches;
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ __global__ void k_update(int n, int np, bool have_uc, Geo g, const int* __restri
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
         U[u] = unc[u * (size_t)np + i];
-        if (have_uc) U[u] += (double)Uc[u * (size_t)np + i];
+        if (have_uc) U[u] += (double)Uc[6 * (size_t)i + u];
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) x[3 * (size_t)i + k] = wrap_coord(xw[k * (size_t)np + i] + g.dt * U[k], g.box[k]);
