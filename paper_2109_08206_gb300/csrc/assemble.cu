@@ -117,54 +117,106 @@ __global__ void k_assemble(int m, int n, int np, Geo g, const int32_t* __restric
     }
 }
 
-__global__ void k_setup_count(int m, int n, const int32_t* __restrict__ pairs, int* __restrict__ cntP,
-                              int* __restrict__ cntQ, int* __restrict__ flags)
+// Validation of a caller's pair list: ranges, i < j, sorted by i.
+__global__ void k_check_pairs(int m, int n, const int32_t* __restrict__ pairs, int* __restrict__ flags)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
     int i = pairs[3 * (size_t)c], j = pairs[3 * (size_t)c + 1], code = pairs[3 * (size_t)c + 2];
     bool ok = i >= 0 && i < j && j < n && code >= 0 && code < 27;
-    if (ok && c > 0 && pairs[3 * (size_t)(c - 1)] > i) ok = false;   // must be sorted by i
-    if (!ok) {
-        if (atomicCAS(&flags[F_ERR], 0, ALENS_ERR_INVALID) == 0) flags[F_ERR_ROD] = c;
-        return;
-    }
-    atomicAdd(&cntP[i], 1);
-    atomicAdd(&cntQ[j], 1);
+    if (ok && c > 0 && pairs[3 * (size_t)(c - 1)] > i) ok = false;
+    if (!ok && atomicCAS(&flags[F_ERR], 0, ALENS_ERR_INVALID) == 0) flags[F_ERR_ROD] = c;
 }
 
-template <typename T>
-__global__ void k_setup_fill(int m, int mp, const int32_t* __restrict__ pairs, const double* __restrict__ dgeom,
-                             const double* __restrict__ q64, const int* __restrict__ rowQ, int* __restrict__ curQ,
-                             int* __restrict__ qlist, int* __restrict__ ci, int* __restrict__ cj, T* __restrict__ rec,
-                             T* __restrict__ qT)
+// The solver numbers rods by rank (their position in the cell-sorted order
+// when one is given, else their id) and gives each constraint to the
+// endpoint of lower rank (the "owner"; the other endpoint is its Q side).
+__device__ __forceinline__ void owner_other(const int32_t* pairs, const int* rank, int c, int& ro, int& rq, bool& flip)
+{
+    int i = pairs[3 * (size_t)c], j = pairs[3 * (size_t)c + 1];
+    int ri = rank ? rank[i] : i, rj = rank ? rank[j] : j;
+    flip = ri > rj;
+    ro = flip ? rj : ri;
+    rq = flip ? ri : rj;
+}
+
+__global__ void k_count_sides(int m, const int32_t* __restrict__ pairs, const int* __restrict__ rank,
+                              int* __restrict__ cntP, int* __restrict__ cntQ)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
-    int i = pairs[3 * (size_t)c], j = pairs[3 * (size_t)c + 1];
-    ci[c] = i;
-    cj[c] = j;
-#pragma unroll
-    for (int u = 0; u < 9; ++u) rec[u * (size_t)mp + c] = (T)dgeom[9 * (size_t)c + u];
-    qT[c] = (T)q64[c];
-    int pos = rowQ[j] + atomicAdd(&curQ[j], 1);
-    qlist[pos] = c;
+    int ro, rq;
+    bool flip;
+    owner_other(pairs, rank, c, ro, rq, flip);
+    atomicAdd(&cntP[ro], 1);
+    atomicAdd(&cntQ[rq], 1);
 }
 
-__global__ void k_sort_qlist(int n, const int* __restrict__ rowQ, int* __restrict__ qlist)
+__global__ void k_scatter_owner(int m, const int32_t* __restrict__ pairs, const int* __restrict__ rank,
+                                const int* __restrict__ rowP, int* __restrict__ curP, int* __restrict__ perm)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    int b = rowQ[j], e = rowQ[j + 1];
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    int ro, rq;
+    bool flip;
+    owner_other(pairs, rank, c, ro, rq, flip);
+    perm[rowP[ro] + atomicAdd(&curP[ro], 1)] = c;
+}
+
+// Ascending order inside every CSR segment (segments are short), so that
+// the layout does not depend on the order of the atomics above.
+__global__ void k_sort_segments(int n, const int* __restrict__ row, int* __restrict__ list)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int b = row[r], e = row[r + 1];
     for (int u = b + 1; u < e; ++u) {
-        int v = qlist[u];
+        int v = list[u];
         int w = u - 1;
-        while (w >= b && qlist[w] > v) {
-            qlist[w + 1] = qlist[w];
+        while (w >= b && list[w] > v) {
+            list[w + 1] = list[w];
             --w;
         }
-        qlist[w + 1] = v;
+        list[w + 1] = v;
     }
+}
+
+// Internal constraint cc (owner-major) <- caller constraint perm[cc].  When
+// the owner is the caller's Q rod the column is written from its side:
+// e' = -e, (owner arm x e') = -(y_Q x e), (other arm x e') = -(y_P x e).
+template <typename T>
+__global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const int32_t* __restrict__ pairs,
+                             const int* __restrict__ rank, const double* __restrict__ dgeom,
+                             const double* __restrict__ q64, const double* __restrict__ gin,
+                             const int* __restrict__ rowQ, int* __restrict__ curQ, int* __restrict__ qlist,
+                             int* __restrict__ ci, int* __restrict__ cj, T* __restrict__ rec, T* __restrict__ qT,
+                             T* __restrict__ gg0)
+{
+    int cc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cc >= m) return;
+    int c = perm[cc];
+    int ro, rq;
+    bool flip;
+    owner_other(pairs, rank, c, ro, rq, flip);
+    ci[cc] = ro;
+    cj[cc] = rq;
+    const double* dg = dgeom + 9 * (size_t)c;
+    if (!flip) {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) rec[u * (size_t)mp + cc] = (T)dg[u];
+    } else {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            rec[u * (size_t)mp + cc] = (T)(-dg[u]);
+            rec[(3 + u) * (size_t)mp + cc] = (T)(-dg[6 + u]);
+            rec[(6 + u) * (size_t)mp + cc] = (T)(-dg[3 + u]);
+        }
+    }
+    qT[cc] = (T)q64[c];
+    double v = gin ? gin[c] : 0.0;
+    gg0[2 * (size_t)cc] = v > 0.0 ? (T)v : T(0);
+    gg0[2 * (size_t)cc + 1] = T(0);
+    qlist[rowQ[rq] + atomicAdd(&curQ[rq], 1)] = cc;
 }
 
 template <typename T>
@@ -182,26 +234,18 @@ __global__ void k_setup_qe(int m, int mp, const int* __restrict__ qlist, const T
 }
 
 template <typename T>
-__global__ void k_setup_rods(int n, int np, const double* __restrict__ quat, T* __restrict__ ax)
+__global__ void k_setup_rods(int n, int np, const double* __restrict__ quat, const int* __restrict__ rank,
+                             T* __restrict__ ax)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double p0, p1, p2;
     quat_axis(quat[4 * (size_t)i], quat[4 * (size_t)i + 1], quat[4 * (size_t)i + 2], quat[4 * (size_t)i + 3], p0, p1,
               p2);
-    ax[i] = (T)p0;
-    ax[np + i] = (T)p1;
-    ax[2 * (size_t)np + i] = (T)p2;
-}
-
-template <typename T>
-__global__ void k_setup_gamma(int m, const double* __restrict__ gin, T* __restrict__ gg0)
-{
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m) return;
-    double v = gin ? gin[c] : 0.0;
-    gg0[2 * (size_t)c] = v > 0.0 ? (T)v : T(0);
-    gg0[2 * (size_t)c + 1] = T(0);
+    int r = rank ? rank[i] : i;
+    ax[r] = (T)p0;
+    ax[np + r] = (T)p1;
+    ax[2 * (size_t)np + r] = (T)p2;
 }
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
@@ -217,53 +261,64 @@ cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, 
 
 template <typename T>
 static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m, const int32_t* pairs,
-                               const double* dgeom, const double* q, const double* gamma_in, const double* quat)
+                               const double* dgeom, const double* q, const double* gamma_in, const double* quat,
+                               const int* rank)
 {
     int mp = (int)ctx->max_pairs, np = (int)ctx->max_rods;
     cudaStream_t st = ctx->stream;
     if (n > 0) {
-        k_setup_rods<T><<<nblk(n, 256), 256, 0, st>>>(n, np, quat, sb.ax);
+        k_setup_rods<T><<<nblk(n, 256), 256, 0, st>>>(n, np, quat, rank, sb.ax);
         ++ctx->launches;
     }
     if (m <= 0) return cudaGetLastError();
-    k_setup_fill<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, pairs, dgeom, q, ctx->rowQ, ctx->curQ, ctx->qlist, ctx->ci,
-                                                  ctx->cj, sb.rec, sb.q);
+    k_setup_fill<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->perm, pairs, rank, dgeom, q, gamma_in, ctx->rowQ,
+                                                  ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0]);
     ++ctx->launches;
-    k_sort_qlist<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
+    k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
     ++ctx->launches;
     k_setup_qe<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->qlist, sb.rec, sb.qe);
-    ++ctx->launches;
-    k_setup_gamma<T><<<nblk(m, 256), 256, 0, st>>>(m, gamma_in, sb.gg[0]);
     ++ctx->launches;
     return cudaGetLastError();
 }
 
-// Counts P and Q sides of the pair list (validating i < j, ranges and the
-// sort by i) into rod_count / cntQ.
+// Validates a caller's pair list (ranges, i < j, sorted by i).
 cudaError_t launch_solve_setup_check(aLENS_ctx* ctx, int n, int m, const int32_t* pairs)
 {
-    cudaStream_t st = ctx->stream;
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(ctx->rod_count, 0, sizeof(int) * ((size_t)n + 1), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ctx->cntQ, 0, sizeof(int) * ((size_t)n + 1), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ctx->curQ, 0, sizeof(int) * ((size_t)n + 1), st)) != cudaSuccess) return e;
     if (m > 0) {
-        k_setup_count<<<nblk(m, 256), 256, 0, st>>>(m, n, pairs, ctx->rod_count, ctx->cntQ, ctx->dflags);
+        k_check_pairs<<<nblk(m, 256), 256, 0, ctx->stream>>>(m, n, pairs, ctx->dflags);
         ++ctx->launches;
     }
     return cudaGetLastError();
 }
 
-// Scans the counts of launch_solve_setup_check into rowP / rowQ, then fills
-// the typed solver buffers.  The pair list must have passed the check.
+// Owner-major constraint layout over rod ranks, the Q-side CSR, and the
+// typed solver buffers.  The pair list must have passed the check.
 cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* dgeom,
-                               const double* q, const double* gamma_in, const double* quat, int precision)
+                               const double* q, const double* gamma_in, const double* quat, int precision,
+                               const int* rank)
 {
+    cudaStream_t st = ctx->stream;
     cudaError_t e;
+    size_t bytes = sizeof(int) * ((size_t)n + 1);
+    if ((e = cudaMemsetAsync(ctx->rod_count, 0, bytes, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->cntQ, 0, bytes, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->curQ, 0, bytes, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->curP, 0, bytes, st)) != cudaSuccess) return e;
+    if (m > 0) {
+        k_count_sides<<<nblk(m, 256), 256, 0, st>>>(m, pairs, rank, ctx->rod_count, ctx->cntQ);
+        ++ctx->launches;
+    }
     if ((e = exclusive_scan(ctx, ctx->rod_count, ctx->rowP, n)) != cudaSuccess) return e;
     if ((e = exclusive_scan(ctx, ctx->cntQ, ctx->rowQ, n)) != cudaSuccess) return e;
-    if (precision == ALENS_MIXED) return setup_typed<float>(ctx, ctx->sb32, n, m, pairs, dgeom, q, gamma_in, quat);
-    return setup_typed<double>(ctx, ctx->sb64, n, m, pairs, dgeom, q, gamma_in, quat);
+    if (m > 0) {
+        k_scatter_owner<<<nblk(m, 256), 256, 0, st>>>(m, pairs, rank, ctx->rowP, ctx->curP, ctx->perm);
+        ++ctx->launches;
+        k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowP, ctx->perm);
+        ++ctx->launches;
+    }
+    if (precision == ALENS_MIXED)
+        return setup_typed<float>(ctx, ctx->sb32, n, m, pairs, dgeom, q, gamma_in, quat, rank);
+    return setup_typed<double>(ctx, ctx->sb64, n, m, pairs, dgeom, q, gamma_in, quat, rank);
 }
 
 }  // namespace alens

@@ -84,7 +84,7 @@ void free_all(aLENS_ctx* c)
 {
     void* ptrs[] = {c->xw, c->axis, c->unc, c->pos32, c->ax32, c->cellkey, c->sorted_id, c->spos32, c->sax32,
                     c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand, c->keep,
-                    c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
+                    c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->perm, c->rank, c->curP, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
                     c->q64, c->solve_ws, c->partials, c->bar, c->dflags, c->dcount, c->scan_tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -222,6 +222,9 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->cntQ, (np + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->curQ, (np + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->qlist, mp * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->perm, mp * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->rank, np * sizeof(int)) == cudaSuccess;
+    ok &= dmalloc(&c->curP, (np + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->ci, mp * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->cj, mp * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->pairs, 3 * mp * sizeof(int32_t)) == cudaSuccess;
@@ -415,7 +418,7 @@ aLENS_status aLENS_solve_lcp(aLENS_ctx* c, int64_t n, const double* quat, int64_
     CK(launch_solve_setup_check(c, (int)n, (int)n_pairs, pairs));
     if ((st = read_status(c)) != ALENS_OK) return st;
     if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
-    CK(launch_solve_setup(c, (int)n, (int)n_pairs, pairs, dgeom, q, gamma, quat, c->p.precision));
+    CK(launch_solve_setup(c, (int)n, (int)n_pairs, pairs, dgeom, q, gamma, quat, c->p.precision, nullptr));
     if ((st = run_solver(c, (int)n, (int)n_pairs, info, c->ev[1], c->ev[2])) != ALENS_OK) return st;
     if ((st = read_status(c)) != ALENS_OK) return st;
     if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
@@ -454,10 +457,10 @@ aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const 
     CK(launch_emit_pairs(c, (int)n, c->pairs));
     CK(cudaEventRecord(c->ev[1], c->stream));
     CK(launch_assemble(c, (int)n, (int)m, c->pairs, c->phi, c->dgeom, c->q64));
-    CK(launch_solve_setup_check(c, (int)n, (int)m, c->pairs));
-    CK(launch_solve_setup(c, (int)n, (int)m, c->pairs, c->dgeom, c->q64, nullptr, quat, c->p.precision));
+    CK(launch_rank(c, (int)n));
+    CK(launch_solve_setup(c, (int)n, (int)m, c->pairs, c->dgeom, c->q64, nullptr, quat, c->p.precision, c->rank));
     if ((st = run_solver(c, (int)n, (int)m, info, c->ev[2], c->ev[3])) != ALENS_OK) return st;
-    CK(launch_update(c, (int)n, (int)m, x, quat, c->p.precision, vel_out));
+    CK(launch_update(c, (int)n, (int)m, x, quat, c->p.precision, vel_out, c->rank));
     CK(cudaEventRecord(c->ev[4], c->stream));
     if (gamma_out) CK(launch_gamma_out(c, (int)m, c->p.precision, gamma_out));
     if (pairs_out && m > 0)

@@ -203,7 +203,10 @@ struct aLENS_ctx {
     int* rowQ;               // [np + 1]
     int* cntQ;               // [np + 1]
     int* curQ;               // [np]
-    int* qlist;              // [mp]
+    int* qlist;              // [mp] Q-side CSR: internal constraint ids per rod rank
+    int* perm;               // [mp] internal (owner-major) constraint -> caller constraint
+    int* rank;               // [np] solver position of each rod (cell-sorted order)
+    int* curP;               // [np + 1]
     int* ci;                 // [mp]
     int* cj;                 // [mp]
     int32_t* pairs;          // [mp][3] internal pair list of a step
@@ -253,14 +256,19 @@ cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, 
 // Validates a caller's pair list (ranges, i < j, sorted by i) and counts
 // the P and Q sides; launch_solve_setup must follow only if no error flag was raised.
 cudaError_t launch_solve_setup_check(aLENS_ctx* ctx, int n, int m, const int32_t* pairs);
+// rank (nullable): solver position of each rod (identity when NULL).
 cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* dgeom,
-                               const double* q, const double* gamma_in, const double* quat, int precision);
+                               const double* q, const double* gamma_in, const double* quat, int precision,
+                               const int* rank);
+// rank[sorted_id[k]] = k: the cell-sorted position of every rod.
+cudaError_t launch_rank(aLENS_ctx* ctx, int n);
 
 // solve.cu
 cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision);
 cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma_out);
 
 // update.cu
-cudaError_t launch_update(aLENS_ctx* ctx, int n, int m, double* x, double* quat, int precision, double* vel_out);
+cudaError_t launch_update(aLENS_ctx* ctx, int n, int m, double* x, double* quat, int precision, double* vel_out,
+                          const int* rank);
 
 }  // namespace alens

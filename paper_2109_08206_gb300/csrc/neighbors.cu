@@ -74,17 +74,49 @@ __global__ void k_pack(int n, int np, const double* __restrict__ x, const double
 }
 
 __global__ void k_cell_scatter(int n, const uint32_t* __restrict__ cellkey, const int* __restrict__ cell_start,
-                               int* __restrict__ cell_cursor, const float4* __restrict__ pos32,
-                               const float4* __restrict__ ax32, int* __restrict__ sorted_id,
-                               float4* __restrict__ spos32, float4* __restrict__ sax32)
+                               int* __restrict__ cell_cursor, int* __restrict__ sorted_id)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t key = cellkey[i];
-    int pos = cell_start[key] + atomicAdd(&cell_cursor[key], 1);
-    sorted_id[pos] = i;
-    spos32[pos] = pos32[i];
-    sax32[pos] = ax32[i];
+    sorted_id[cell_start[key] + atomicAdd(&cell_cursor[key], 1)] = i;
+}
+
+// Rods of each cell in ascending id, so that the cell-sorted order (which the
+// solver also uses to number rods) does not depend on the atomics above.
+__global__ void k_cell_sort_ids(int nkeys, const int* __restrict__ cell_start, int* __restrict__ sorted_id)
+{
+    constexpr int kLocal = 64;
+    int key = blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= nkeys) return;
+    const int b = cell_start[key], e = cell_start[key + 1];
+    if (e - b <= kLocal) {
+        int v[kLocal];
+        const int len = e - b;
+        for (int u = 0; u < len; ++u) v[u] = sorted_id[b + u];
+        for (int u = 1; u < len; ++u) {
+            int x = v[u], w = u - 1;
+            while (w >= 0 && v[w] > x) { v[w + 1] = v[w]; --w; }
+            v[w + 1] = x;
+        }
+        for (int u = 0; u < len; ++u) sorted_id[b + u] = v[u];
+    } else {
+        for (int u = b + 1; u < e; ++u) {
+            int x = sorted_id[u], w = u - 1;
+            while (w >= b && sorted_id[w] > x) { sorted_id[w + 1] = sorted_id[w]; --w; }
+            sorted_id[w + 1] = x;
+        }
+    }
+}
+
+__global__ void k_cell_gather(int n, const int* __restrict__ sorted_id, const float4* __restrict__ pos32,
+                              const float4* __restrict__ ax32, float4* __restrict__ spos32, float4* __restrict__ sax32)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int i = sorted_id[k];
+    spos32[k] = pos32[i];
+    sax32[k] = ax32[i];
 }
 
 // Float32 screen of one candidate.  Returns false only when the pair is
@@ -308,8 +340,12 @@ cudaError_t launch_cell_sort(aLENS_ctx* ctx, int n)
     if (e != cudaSuccess) return e;
     if (n > 0) {
         k_cell_scatter<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, ctx->cellkey, ctx->cell_start, ctx->cell_cursor,
-                                                              ctx->pos32, ctx->ax32, ctx->sorted_id, ctx->spos32,
-                                                              ctx->sax32);
+                                                              ctx->sorted_id);
+        ++ctx->launches;
+        k_cell_sort_ids<<<nblk(nkeys, 128), 128, 0, ctx->stream>>>(nkeys, ctx->cell_start, ctx->sorted_id);
+        ++ctx->launches;
+        k_cell_gather<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, ctx->sorted_id, ctx->pos32, ctx->ax32, ctx->spos32,
+                                                             ctx->sax32);
         ++ctx->launches;
     }
     return cudaGetLastError();

@@ -43,6 +43,10 @@
 namespace alens {
 
 enum { A_RAW = 0, A_STEP = 1, A_PG = 2 };
+constexpr int kRoundB = 1;  // constraints per thread and round in phase B
+// CSR entries whose loads a thread issues together (float64 values need the
+// registers twice over)
+template <typename T> struct Batch { static constexpr int v = sizeof(T) == 4 ? 2 : 1; };
 
 template <typename T> struct V2;
 template <> struct V2<float> { using t = float2; };
@@ -110,48 +114,84 @@ __device__ __forceinline__ T a_value(T g, T gr, T alpha)
     return g > T(0) ? gr : (gr < T(0) ? gr : T(0));
 }
 
-// Rod-parallel half of the gradient: F = D gamma' and U = M F for every rod,
-// gamma' per MODE (A_RAW: gamma itself; A_STEP: max(0, gamma - alpha g),
-// stored by the P-side rod; A_PG: the projected gradient, returning the
-// thread's share of pi.A.pi = sum_rods F.M.F instead of storing U).
+// Rod-parallel half of the gradient: F = D gamma' and U = M F for the
+// block's rods [r0, r1), gamma' per MODE (A_RAW: gamma itself; A_STEP:
+// max(0, gamma - alpha g), stored by the P-side rod; A_PG: the projected
+// gradient, returning the thread's share of pi.A.pi = sum_rods F.M.F
+// instead of storing U).  Two threads per rod: the even lane sums the rod's
+// P-range (contiguous), the odd lane its Q-side list; one shuffle combines them.
 template <typename T, int MODE>
-__device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const T* gc, T* gn, T alpha)
+__device__ __forceinline__ T phase_a(const SolveArgs<T>& a, int r0, int r1, const T* gc, T* gn, T alpha)
 {
     T fmf = T(0);
-    const int stride = gridDim.x * blockDim.x;
     const size_t mp = a.mp, np = a.np;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    constexpr int kBatch = Batch<T>::v;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const bool act = true;
         T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-        int b = a.rowP[i], e = a.rowP[i + 1];
-        for (int c = b; c < e; ++c) {
-            T g, gr;
-            ld_pair(gc, c, g, gr);
-            T v = a_value<MODE, T>(g, gr, alpha);
-            if (MODE == A_STEP) gn[2 * (size_t)c] = v;
+        {
+            // the rod's own constraints: loads of up to kBatch entries issued together
+            const int b = a.rowP[i], e = a.rowP[i + 1];
+            for (int c = b; c < e; c += kBatch) {
+                T gv[kBatch], grv[kBatch], rv[kBatch][6];
 #pragma unroll
-            for (int u = 0; u < 6; ++u) F[u] += v * a.rec[u * mp + c];
+                for (int u = 0; u < kBatch; ++u) {
+                    if (c + u < e) {
+                        ld_pair(gc, c + u, gv[u], grv[u]);
+#pragma unroll
+                        for (int w = 0; w < 6; ++w) rv[u][w] = a.rec[w * mp + c + u];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    if (c + u < e) {
+                        T v = a_value<MODE, T>(gv[u], grv[u], alpha);
+                        if (MODE == A_STEP) gn[2 * (size_t)(c + u)] = v;
+#pragma unroll
+                        for (int w = 0; w < 6; ++w) F[w] += v * rv[u][w];
+                    }
+                }
+            }
         }
-        b = a.rowQ[i];
-        e = a.rowQ[i + 1];
-        for (int k = b; k < e; ++k) {
-            int c = a.qlist[k];
-            T g, gr;
-            ld_pair(gc, c, g, gr);
-            T v = a_value<MODE, T>(g, gr, alpha);
+        {
+            // constraints owned by other rods: ids first, then their (gamma, g) and arms
+            const int b = a.rowQ[i], e = a.rowQ[i + 1];
+            for (int k = b; k < e; k += kBatch) {
+                int cid[kBatch];
 #pragma unroll
-            for (int u = 0; u < 6; ++u) F[u] -= v * a.qe[u * mp + k];
+                for (int u = 0; u < kBatch; ++u) cid[u] = k + u < e ? a.qlist[k + u] : -1;
+                T gv[kBatch], grv[kBatch], qv[kBatch][6];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    if (cid[u] >= 0) {
+                        ld_pair(gc, cid[u], gv[u], grv[u]);
+#pragma unroll
+                        for (int w = 0; w < 6; ++w) qv[u][w] = a.qe[w * mp + k + u];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    if (cid[u] >= 0) {
+                        T v = a_value<MODE, T>(gv[u], grv[u], alpha);
+#pragma unroll
+                        for (int w = 0; w < 6; ++w) F[w] -= v * qv[u][w];
+                    }
+                }
+            }
         }
-        T p0 = a.ax[i], p1 = a.ax[np + i], p2 = a.ax[2 * np + i];
-        T pf = p0 * F[0] + p1 * F[1] + p2 * F[2];
-        T pt = p0 * F[3] + p1 * F[4] + p2 * F[5];
-        T cf = pf * (a.inv_par - a.inv_perp), ct = pt * (a.inv_spin - a.inv_rot);
-        T Uv[6] = {F[0] * a.inv_perp + p0 * cf, F[1] * a.inv_perp + p1 * cf, F[2] * a.inv_perp + p2 * cf,
-                   F[3] * a.inv_rot + p0 * ct,  F[4] * a.inv_rot + p1 * ct,  F[5] * a.inv_rot + p2 * ct};
-        if (MODE == A_PG) {
+        {
+            T p0 = a.ax[i], p1 = a.ax[np + i], p2 = a.ax[2 * np + i];
+            T pf = p0 * F[0] + p1 * F[1] + p2 * F[2];
+            T pt = p0 * F[3] + p1 * F[4] + p2 * F[5];
+            T cf = pf * (a.inv_par - a.inv_perp), ct = pt * (a.inv_spin - a.inv_rot);
+            T Uv[6] = {F[0] * a.inv_perp + p0 * cf, F[1] * a.inv_perp + p1 * cf, F[2] * a.inv_perp + p2 * cf,
+                       F[3] * a.inv_rot + p0 * ct,  F[4] * a.inv_rot + p1 * ct,  F[5] * a.inv_rot + p2 * ct};
+            if (MODE == A_PG) {
 #pragma unroll
-            for (int u = 0; u < 6; ++u) fmf += F[u] * Uv[u];
-        } else {
-            st_u6(a.U, i, Uv);
+                for (int u = 0; u < 6; ++u) fmf += F[u] * Uv[u];
+            } else {
+                st_u6(a.U, i, Uv);
+            }
         }
     }
     return fmf;
@@ -161,37 +201,53 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const T* gc, T* gn, 
 // the new (gamma, g) pair, plus the thread's partial sums.
 // FIRST: acc0 = pi.pi; otherwise acc0..2 = s.s, s.y, y.y; acc3 = max |pi|.
 template <typename T, bool FIRST>
-__device__ __forceinline__ void phase_b(const SolveArgs<T>& a, T* gnew, const T* gold, T acc[4])
+__device__ __forceinline__ void phase_b(const SolveArgs<T>& a, int c0, int c1, T* gnew, const T* gold, T acc[4])
 {
-    const int stride = gridDim.x * blockDim.x;
     const size_t mp = a.mp;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.m; c += stride) {
-        int i = a.ci[c], j = a.cj[c];
-        T Ui[6], Uj[6];
-        ld_u6(a.U, i, Ui);
-        ld_u6(a.U, j, Uj);
-        T du = T(0);
+    const int nt = blockDim.x;
+    // two constraints per thread and round; every load of both is issued
+    // before the first store
+    for (int cA = c0 + threadIdx.x; cA < c1; cA += kRoundB * nt) {
+        const int cB = cA + nt;
+        const bool hasB = kRoundB > 1 && cB < c1;
+        int idx[2] = {cA, hasB ? cB : cA};
+        T Ui[2][6], Uj[2][6], r[2][9], qq[2], gm[2], go[2], gro[2];
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            du += a.rec[u * mp + c] * (Ui[u] - Uj[u]);
-            du += a.rec[(3 + u) * mp + c] * Ui[3 + u];
-            du -= a.rec[(6 + u) * mp + c] * Uj[3 + u];
+        for (int h = 0; h < 2; ++h) {
+            const int c = idx[h];
+            ld_u6(a.U, a.ci[c], Ui[h]);
+            ld_u6(a.U, a.cj[c], Uj[h]);
+#pragma unroll
+            for (int w = 0; w < 9; ++w) r[h][w] = a.rec[w * mp + c];
+            qq[h] = a.q[c];
+            gm[h] = gnew[2 * (size_t)c];
+            if (!FIRST) ld_pair(gold, c, go[h], gro[h]);
         }
-        T gr = a.q[c] + du;
-        T gm = gnew[2 * (size_t)c];
-        gnew[2 * (size_t)c + 1] = gr;
-        T pi = gm > T(0) ? gr : (gr < T(0) ? gr : T(0));
-        T api = pi < T(0) ? -pi : pi;
-        acc[3] = api > acc[3] ? api : acc[3];
-        if (FIRST) {
-            acc[0] += pi * pi;
-        } else {
-            T go, gro;
-            ld_pair(gold, c, go, gro);
-            T s = gm - go, y = gr - gro;
-            acc[0] += s * s;
-            acc[1] += s * y;
-            acc[2] += y * y;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !hasB) break;
+            const int c = idx[h];
+            T du = T(0);
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                du += r[h][u] * (Ui[h][u] - Uj[h][u]);
+                du += r[h][3 + u] * Ui[h][3 + u];
+                du -= r[h][6 + u] * Uj[h][3 + u];
+            }
+            const T gr = qq[h] + du;
+            gnew[2 * (size_t)c + 1] = gr;
+            const T g1 = gm[h];
+            T pi = g1 > T(0) ? gr : (gr < T(0) ? gr : T(0));
+            T api = pi < T(0) ? -pi : pi;
+            acc[3] = api > acc[3] ? api : acc[3];
+            if (FIRST) {
+                acc[0] += pi * pi;
+            } else {
+                T sv = g1 - go[h], yv = gr - gro[h];
+                acc[0] += sv * sv;
+                acc[1] += sv * yv;
+                acc[2] += yv * yv;
+            }
         }
     }
 }
@@ -293,79 +349,130 @@ __device__ __forceinline__ void grid_total(const double* partials, int nb, doubl
     for (int u = 0; u < 4; ++u) out[u] = bc[u];
 }
 
+// Step-size bookkeeping, done by thread 0 alone (float64 division is slow
+// on this part; every other thread only reads the broadcast).
+struct StepState {
+    double alpha0, alpha, res;
+    int iters, cur, done;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) k_bbpgd(SolveArgs<T> a)
 {
     __shared__ double red[32][4];
     __shared__ double bc[4];
+    __shared__ T s_alpha;
+    __shared__ int s_done;
     if (a.fault == 1 && blockIdx.x == 0) return;   // test hook: this block never arrives
     const unsigned nb = gridDim.x;
     double* mine = a.partials + 4 * (size_t)blockIdx.x;
     unsigned epoch = 0;
-    T* gg[2] = {a.gg0, a.gg1};
+    // this block's rods (an even split) and the P-side constraints they own
+    const int per = (a.n + (int)nb - 1) / (int)nb;
+    const int r0 = min(a.n, (int)blockIdx.x * per), r1 = min(a.n, r0 + per);
+    const int c0 = a.rowP[r0], c1 = a.rowP[r1];
     double tot[4];
     T v[4];
+    StepState st;   // meaningful in thread 0 only
 
     // U = M D gamma_0
-    phase_a<T, A_RAW>(a, gg[0], nullptr, T(0));
+    phase_a<T, A_RAW>(a, r0, r1, a.gg0, nullptr, T(0));
     if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
     // g_0 and the projected gradient at gamma_0
     v[0] = v[1] = v[2] = v[3] = T(0);
-    phase_b<T, true>(a, gg[0], nullptr, v);
+    phase_b<T, true>(a, c0, c1, a.gg0, nullptr, v);
     block_partial(v, red, mine);
     if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
     grid_total(a.partials, nb, bc, tot);
-    const double pp = tot[0];
-    double res = a.hD * tot[3];
-    int cur = 0, iters = 0;
-    if (res > a.tol && a.max_iter > 0) {
+    if (threadIdx.x == 0) {
+        st.res = a.hD * tot[3];
+        st.iters = 0;
+        st.cur = 0;
+        st.done = !(st.res > a.tol && a.max_iter > 0);
+        s_done = st.done;
+    }
+    __syncthreads();
+    if (!s_done) {
+        const double pp = tot[0];
         // alpha_0 = pi.pi / pi.A.pi (exact line step along the projected gradient)
-        v[0] = phase_a<T, A_PG>(a, gg[0], nullptr, T(0));
+        v[0] = phase_a<T, A_PG>(a, r0, r1, a.gg0, nullptr, T(0));
         v[1] = v[2] = v[3] = T(0);
         // every block has read the partials (grid_total) before any rewrites them
         if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
         block_partial(v, red, mine);
         if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
         grid_total(a.partials, nb, bc, tot);
-        const double pap = tot[0];
-        double alpha0 = pp / pap;
-        if (!(pap > 0.0) || !isfinite(alpha0) || !(alpha0 > 0.0)) alpha0 = 1.0;
-        double alpha = alpha0;
+        if (threadIdx.x == 0) {
+            const double pap = tot[0];
+            double alpha0 = pp / pap;
+            if (!(pap > 0.0) || !isfinite(alpha0) || !(alpha0 > 0.0)) alpha0 = 1.0;
+            st.alpha0 = st.alpha = alpha0;
+            s_alpha = (T)alpha0;
+        }
+        __syncthreads();
+        int cur = 0;
         for (int k = 0; k < a.max_iter; ++k) {
             const int nx = cur ^ 1;
-            phase_a<T, A_STEP>(a, gg[cur], gg[nx], (T)alpha);
+            T* gc = cur ? a.gg1 : a.gg0;
+            T* gn = cur ? a.gg0 : a.gg1;
+            phase_a<T, A_STEP>(a, r0, r1, gc, gn, s_alpha);
             if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
             v[0] = v[1] = v[2] = v[3] = T(0);
-            phase_b<T, false>(a, gg[nx], gg[cur], v);
+            phase_b<T, false>(a, c0, c1, gn, gc, v);
             block_partial(v, red, mine);
             if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
             grid_total(a.partials, nb, bc, tot);
-            const double ss = tot[0], sy = tot[1], yy = tot[2];
-            res = a.hD * tot[3];
             cur = nx;
-            iters = k + 1;
-            if (!(res > a.tol)) break;
-            double an = (k & 1) == 0 ? ss / sy : sy / yy;
-            if (!(sy > 0.0) || !isfinite(an) || !(an > 0.0)) an = alpha0;
-            alpha = an;
+            if (threadIdx.x == 0) {
+                const double ss = tot[0], sy = tot[1], yy = tot[2];
+                st.res = a.hD * tot[3];
+                st.cur = cur;
+                st.iters = k + 1;
+                st.done = !(st.res > a.tol);
+                if (!st.done) {
+                    double an = (k & 1) == 0 ? ss / sy : sy / yy;
+                    if (!(sy > 0.0) || !isfinite(an) || !(an > 0.0)) an = st.alpha0;
+                    st.alpha = an;
+                    s_alpha = (T)an;
+                }
+                s_done = st.done;
+            }
+            __syncthreads();
+            if (s_done) break;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.out[1] = alpha0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.out[1] = st.alpha0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.flags[F_FINAL] = cur;
-        a.flags[F_ITERS] = iters;
-        a.out[0] = res;
+        a.flags[F_FINAL] = st.cur;
+        a.flags[F_ITERS] = st.iters;
+        a.out[0] = st.res;
     }
 }
 
+// gamma back in the caller's pair order.
 template <typename T>
-__global__ void k_gamma_out(int m, const int* __restrict__ flags, const T* gg0, const T* gg1, double* __restrict__ out)
+__global__ void k_gamma_out(int m, const int* __restrict__ flags, const int* __restrict__ perm, const T* gg0,
+                            const T* gg1, double* __restrict__ out)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
     if (flags[F_SOLVE_ERR] != 0) return;
     const T* g = flags[F_FINAL] == 0 ? gg0 : gg1;
-    out[c] = (double)g[2 * (size_t)c];
+    out[perm[c]] = (double)g[2 * (size_t)c];
+}
+
+__global__ void k_rank(int n, const int* __restrict__ sorted_id, int* __restrict__ rank)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) rank[sorted_id[k]] = k;
+}
+
+cudaError_t launch_rank(aLENS_ctx* ctx, int n)
+{
+    if (n <= 0) return cudaSuccess;
+    k_rank<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->sorted_id, ctx->rank);
+    ++ctx->launches;
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -391,7 +498,8 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (ctx->solve_bps > 0 && ctx->solve_bps < per_sm) per_sm = ctx->solve_bps;
-    long long want = ((long long)(n > m ? n : m) + threads - 1) / threads;
+    // enough blocks that each has at least a warp of rods
+    long long want = ((long long)n + 31) / 32;
     long long blocks = (long long)per_sm * ctx->num_sms;
     if (want < blocks) blocks = want < 1 ? 1 : want;
     if (blocks > ctx->max_blocks) blocks = ctx->max_blocks;
@@ -413,9 +521,9 @@ cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma
     if (m <= 0 || !gamma_out) return cudaSuccess;
     int b = (m + 255) / 256;
     if (precision == ALENS_MIXED) {
-        k_gamma_out<float><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->sb32.gg[0], ctx->sb32.gg[1], gamma_out);
+        k_gamma_out<float><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->perm, ctx->sb32.gg[0], ctx->sb32.gg[1], gamma_out);
     } else {
-        k_gamma_out<double><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->sb64.gg[0], ctx->sb64.gg[1], gamma_out);
+        k_gamma_out<double><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->perm, ctx->sb64.gg[0], ctx->sb64.gg[1], gamma_out);
     }
     ++ctx->launches;
     return cudaGetLastError();
