@@ -174,6 +174,34 @@ ALENS_API aLENS_status aLENS_inject_fault(aLENS_ctx* ctx, int32_t mode);
  * <= 1024; default 1024) and blocks per SM (0 = as many as fit).  For tuning. */
 ALENS_API aLENS_status aLENS_set_launch(aLENS_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free solve.  The paper has no counterpart: this entry point
+ * exists for callers that may not allocate device memory - a host
+ * application or plugin whose memory manager owns the whole device budget,
+ * or a latency-critical loop where cudaMalloc / cudaFree would take the
+ * allocator lock or synchronise the device.  Such callers cannot create an
+ * aLENS_ctx, because aLENS_create allocates its workspaces.
+ *
+ * It runs the same BBPGD solve as aLENS_solve_lcp (same arguments and
+ * outputs, params->box and delta_c unused) with its workspace in one static
+ * device array of the library (about 3.3 MB, held on every GPU that loads
+ * the library until the process exits), and calls no allocating routine.
+ * Limits: n <= ALENS_NOALLOC_MAX_RODS and n_pairs <= ALENS_NOALLOC_MAX_PAIRS;
+ * larger problems return ALENS_ERR_CAPACITY before any work is queued.
+ * The first call on a device (with that device current) looks up the
+ * array's device address; make it before any stream capture.  Every call
+ * reuses the same array (the counters that must start at zero are cleared
+ * on each call), so calls whose GPU work overlaps - on different streams or
+ * from different host threads - race; serialise them.  The call
+ * synchronises cuda_stream.  info (may be NULL) gets iterations and
+ * residual; its timing fields are 0. */
+#define ALENS_NOALLOC_MAX_RODS 4096
+#define ALENS_NOALLOC_MAX_PAIRS 16384
+ALENS_API aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int64_t n, const double* quat,
+                                               int64_t n_pairs, const int32_t* pairs, const double* dgeom,
+                                               const double* q, double* gamma, void* cuda_stream,
+                                               aLENS_info* info);
+
 #ifdef __cplusplus
 }
 #endif
