@@ -17,12 +17,14 @@
 //
 // One persistent cooperative kernel runs the whole loop, one block per SM.
 // Per iteration:
-//   phase A (one thread per rod): gamma_{k+1} of every constraint touching
-//     the rod is formed on the fly from (gamma_k, g_k) and alpha_k (the P-side
-//     rod stores it), summed into the rod's force and torque F = D gamma
-//     (P-range contiguous, Q-side list in CSR order), and U = M F is stored;
+//   phase A (one thread per rod, the block's rods an even share in cell
+//     order): gamma_{k+1} of every constraint touching the rod is formed on
+//     the fly from (gamma_k, g_k) and alpha_k (the owning rod stores it),
+//     summed into the rod's force and torque F = D gamma (owned range
+//     contiguous, other-side list in CSR order), and U = M F is stored;
 //   grid barrier;
-//   phase B (one thread per constraint): g_{k+1} = q + D^T U, and the partial
+//   phase B (one thread per constraint, the block's owned range): g_{k+1} =
+//     q + D^T U, and the partial
 //     sums s.s, s.y, y.y and max |pi|: per thread and per warp in the working
 //     precision, across warps and blocks in float64, in a fixed order;
 //   grid barrier; warp 0 of every block then reduces the per-block partials
@@ -127,7 +129,6 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, int r0, int r1, cons
     const size_t mp = a.mp, np = a.np;
     constexpr int kBatch = Batch<T>::v;
     for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        const bool act = true;
         T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         {
             // the rod's own constraints: loads of up to kBatch entries issued together
