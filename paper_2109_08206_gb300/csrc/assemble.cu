@@ -219,6 +219,8 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
     qlist[rowQ[rq] + atomicAdd(&curQ[rq], 1)] = cc;
 }
 
+// Other-side arms in CSR order, one 8-value record per entry (e, arm x e,
+// two pad values) so that the solver's gather is one or two vector loads.
 template <typename T>
 __global__ void k_setup_qe(int m, int mp, const int* __restrict__ qlist, const T* __restrict__ rec,
                            T* __restrict__ qe)
@@ -226,11 +228,14 @@ __global__ void k_setup_qe(int m, int mp, const int* __restrict__ qlist, const T
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m) return;
     int c = qlist[k];
+    T* o = qe + 8 * (size_t)k;
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
-        qe[u * (size_t)mp + k] = rec[u * (size_t)mp + c];
-        qe[(3 + u) * (size_t)mp + k] = rec[(6 + u) * (size_t)mp + c];
+        o[u] = rec[u * (size_t)mp + c];
+        o[3 + u] = rec[(6 + u) * (size_t)mp + c];
     }
+    o[6] = T(0);
+    o[7] = T(0);
 }
 
 template <typename T>

@@ -85,7 +85,7 @@ void free_all(aLENS_ctx* c)
     void* ptrs[] = {c->xw, c->axis, c->unc, c->pos32, c->ax32, c->cellkey, c->sorted_id, c->spos32, c->sax32,
                     c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand, c->keep,
                     c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->perm, c->rank, c->curP, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
-                    c->q64, c->solve_ws, c->partials, c->bar, c->dflags, c->dcount, c->scan_tmp};
+                    c->q64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->hflags) cudaFreeHost(c->hflags);
@@ -232,9 +232,11 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->dgeom, 9 * mp * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->q64, mp * sizeof(double)) == cudaSuccess;
     // solver buffers, sized for float64; the float32 views alias the same memory
-    size_t solve_elems = 9 * mp + 6 * mp + mp + 3 * np + 4 * mp + 6 * np;
+    // every slice starts on a 64-byte boundary (vector loads): 8 elements of slack each
+    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 4 * mp + 6 * np + 8 * 8;
     ok &= dmalloc((char**)&c->solve_ws, solve_elems * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->partials, (size_t)c->max_blocks * 4 * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->bstart, ((size_t)c->max_blocks + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->bar, 4 * sizeof(unsigned)) == cudaSuccess;
     ok &= dmalloc(&c->dflags, F_NFLAGS * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->dcount, C_NCOUNT * sizeof(unsigned long long)) == cudaSuccess;
@@ -252,16 +254,16 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         // (gamma, g) pairs first and U next keep their vector loads aligned
         double* base = (double*)c->solve_ws;
         size_t o = 0;
-        auto carve64 = [&](size_t cnt) { double* r = base + o; o += cnt; return r; };
+        auto carve64 = [&](size_t cnt) { double* r = base + o; o = (o + cnt + 7) & ~(size_t)7; return r; };
         SolveBufs<double>& s = c->sb64;
         s.gg[0] = carve64(2 * mp); s.gg[1] = carve64(2 * mp); s.U = carve64(6 * np);
-        s.rec = carve64(9 * mp); s.qe = carve64(6 * mp); s.q = carve64(mp); s.ax = carve64(3 * np);
+        s.rec = carve64(9 * mp); s.qe = carve64(8 * mp); s.q = carve64(mp); s.ax = carve64(3 * np);
         float* fb = (float*)c->solve_ws;
         size_t f = 0;
-        auto carve32 = [&](size_t cnt) { float* r = fb + f; f += cnt; return r; };
+        auto carve32 = [&](size_t cnt) { float* r = fb + f; f = (f + cnt + 7) & ~(size_t)7; return r; };
         SolveBufs<float>& t = c->sb32;
         t.gg[0] = carve32(2 * mp); t.gg[1] = carve32(2 * mp); t.U = carve32(6 * np);
-        t.rec = carve32(9 * mp); t.qe = carve32(6 * mp); t.q = carve32(mp); t.ax = carve32(3 * np);
+        t.rec = carve32(9 * mp); t.qe = carve32(8 * mp); t.q = carve32(mp); t.ax = carve32(3 * np);
     }
     if (cudaMemsetAsync(c->cell_cursor, 0, ((size_t)c->max_keys + 1) * sizeof(int), c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {

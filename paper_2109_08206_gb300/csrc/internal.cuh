@@ -29,7 +29,7 @@ enum Flag : int {
     F_NFLAGS = 16
 };
 // 64-bit counters (Ctx::dcount)
-enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_NCOUNT = 8 };
+enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_SMEM = 6, C_NCOUNT = 8 };
 
 // ------------------------------------------------------------ plain structs
 
@@ -218,6 +218,7 @@ struct aLENS_ctx {
     alens::SolveBufs<float> sb32;
     double* partials;        // [max_blocks][4]
     int max_blocks;
+    int* bstart;             // [max_blocks + 1] solver block boundaries (rod ranks)
     unsigned* bar;           // [4]
     int* dflags;             // [F_NFLAGS]
     unsigned long long* dcount;  // [C_NCOUNT]

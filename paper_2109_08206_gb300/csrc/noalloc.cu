@@ -38,12 +38,13 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kRodInts = align256(sizeof(int) * (kNoallocMaxRods + 1));
 constexpr size_t kPairInts = align256(sizeof(int) * kNoallocMaxPairs);
 constexpr size_t kSolveWs =
-    align256(sizeof(double) * (20 * (size_t)kNoallocMaxPairs + 9 * (size_t)kNoallocMaxRods));
+    align256(sizeof(double) * (22 * (size_t)kNoallocMaxPairs + 9 * (size_t)kNoallocMaxRods + 64));
 constexpr size_t kPartials = align256(sizeof(double) * 4 * kNoallocMaxBlocks);
+constexpr size_t kBstart = align256(sizeof(int) * (kNoallocMaxBlocks + 1));
 constexpr int kScanTmpLen = (kNoallocMaxRods + 4095) / 4096 + 2;
 constexpr size_t kSmall = align256(16 * sizeof(unsigned)) + align256(F_NFLAGS * sizeof(int)) +
                           align256(C_NCOUNT * sizeof(unsigned long long)) + align256(kScanTmpLen * sizeof(int));
-constexpr size_t kNoallocScratchBytes = 6 * kRodInts + 4 * kPairInts + kSolveWs + kPartials + kSmall;
+constexpr size_t kNoallocScratchBytes = 6 * kRodInts + 4 * kPairInts + kSolveWs + kPartials + kBstart + kSmall;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
@@ -125,6 +126,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
     c.cj = (int*)take(kPairInts);
     c.solve_ws = take(kSolveWs);
     c.partials = (double*)take(kPartials);
+    c.bstart = (int*)take(kBstart);
     c.bar = (unsigned*)take(16 * sizeof(unsigned));
     c.dflags = (int*)take(F_NFLAGS * sizeof(int));
     c.dcount = (unsigned long long*)take(C_NCOUNT * sizeof(unsigned long long));
@@ -134,14 +136,14 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
         const size_t mp = kNoallocMaxPairs, np = kNoallocMaxRods;
         double* b64 = (double*)c.solve_ws;
         size_t u = 0;
-        auto c64 = [&](size_t cnt) { double* r = b64 + u; u += cnt; return r; };
+        auto c64 = [&](size_t cnt) { double* r = b64 + u; u = (u + cnt + 7) & ~(size_t)7; return r; };
         c.sb64.gg[0] = c64(2 * mp); c.sb64.gg[1] = c64(2 * mp); c.sb64.U = c64(6 * np);
-        c.sb64.rec = c64(9 * mp); c.sb64.qe = c64(6 * mp); c.sb64.q = c64(mp); c.sb64.ax = c64(3 * np);
+        c.sb64.rec = c64(9 * mp); c.sb64.qe = c64(8 * mp); c.sb64.q = c64(mp); c.sb64.ax = c64(3 * np);
         float* b32 = (float*)c.solve_ws;
         size_t v = 0;
-        auto c32 = [&](size_t cnt) { float* r = b32 + v; v += cnt; return r; };
+        auto c32 = [&](size_t cnt) { float* r = b32 + v; v = (v + cnt + 7) & ~(size_t)7; return r; };
         c.sb32.gg[0] = c32(2 * mp); c.sb32.gg[1] = c32(2 * mp); c.sb32.U = c32(6 * np);
-        c.sb32.rec = c32(9 * mp); c.sb32.qe = c32(6 * mp); c.sb32.q = c32(mp); c.sb32.ax = c32(3 * np);
+        c.sb32.rec = c32(9 * mp); c.sb32.qe = c32(8 * mp); c.sb32.q = c32(mp); c.sb32.ax = c32(3 * np);
     }
 
     int hflags[F_NFLAGS];

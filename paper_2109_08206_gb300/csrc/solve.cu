@@ -16,25 +16,30 @@
 // max_iter iterations.
 //
 // One persistent cooperative kernel runs the whole loop, one block per SM.
-// Per iteration:
-//   phase A (one thread per rod, the block's rods an even share in cell
-//     order): gamma_{k+1} of every constraint touching the rod is formed on
-//     the fly from (gamma_k, g_k) and alpha_k (the owning rod stores it),
-//     summed into the rod's force and torque F = D gamma (owned range
-//     contiguous, other-side list in CSR order), and U = M F is stored;
+// Rods are numbered in cell order; block b owns an even share of rods
+// [r0, r1) and the constraints they own [c0, c1) (owner = lower-ranked end).
+// When they fit, the block keeps its own constraints' records, q, gamma and
+// g, and its rods' axes and velocities in shared memory for the whole solve
+// (at 1e5 rods the mixed working set, about 30 MB, spreads over the SMs'
+// shared memory); global memory then carries only what other blocks read:
+// gamma, g and U mirrors.  Blocks whose share does not fit work from the
+// global arrays.  Per iteration:
+//   phase A (one thread per rod): gamma_{k+1} of every constraint touching
+//     the rod is formed on the fly from (gamma_k, g_k) and alpha_k (the owner
+//     stores it), summed into the rod's force and torque F = D gamma (owned
+//     range contiguous, other-side list in CSR order), and U = M F is stored;
 //   grid barrier;
-//   phase B (one thread per constraint, the block's owned range): g_{k+1} =
-//     q + D^T U, and the partial
-//     sums s.s, s.y, y.y and max |pi|: per thread and per warp in the working
-//     precision, across warps and blocks in float64, in a fixed order;
+//   phase B (one thread per owned constraint): g_{k+1} = q + D^T U, and the
+//     partial sums s.s, s.y, y.y and max |pi|: per thread and per warp in the
+//     working precision, across warps and blocks in float64, in a fixed order;
 //   grid barrier; warp 0 of every block then reduces the per-block partials
 //     in the same fixed order, so all blocks take identical step decisions.
 // Two grid barriers per iteration.  Each barrier wait is bounded in time
 // and in polls; a wait that runs out raises ALENS_ERR_TIMEOUT in the device
 // status word and every block leaves.
 //
-// Layout: (gamma, g) interleaved per constraint in two ping-pong buffers,
-// U as [rod][6] (one or two sectors per gather), D records SoA [9][m].
+// Global layout: (gamma, g) interleaved per constraint in two ping-pong
+// buffers, U as [rod][6], D records SoA [9][m] in owner-major order.
 // T = double (float64 plain) or float (mixed: the D, M, D^T work, per-thread
 // and per-warp sums in float32; the cross-warp and cross-block sums, the
 // residual test and the step sizes in float64; max |pi| is exact in either).
@@ -45,7 +50,6 @@
 namespace alens {
 
 enum { A_RAW = 0, A_STEP = 1, A_PG = 2 };
-constexpr int kRoundB = 1;  // constraints per thread and round in phase B
 // CSR entries whose loads a thread issues together (float64 values need the
 // registers twice over)
 template <typename T> struct Batch { static constexpr int v = sizeof(T) == 4 ? 2 : 1; };
@@ -70,6 +74,20 @@ __device__ __forceinline__ void ld_u6(const T* U, int i, T u[6])
     u[0] = a.x; u[1] = a.y; u[2] = b.x; u[3] = b.y; u[4] = c.x; u[5] = c.y;
 }
 
+// Other-side arms of CSR entry k, packed as [m][8] (e, arm x e, 2 pad).
+__device__ __forceinline__ void ld_arm(const float* qe, int k, float v[6])
+{
+    const float4 a = __ldg(reinterpret_cast<const float4*>(qe) + 2 * (size_t)k);
+    const float2 b = __ldg(reinterpret_cast<const float2*>(qe) + 4 * (size_t)k + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+}
+__device__ __forceinline__ void ld_arm(const double* qe, int k, double v[6])
+{
+    const double2* p = reinterpret_cast<const double2*>(qe) + 4 * (size_t)k;
+    const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+
 template <typename T>
 __device__ __forceinline__ void st_u6(T* U, int i, const T u[6])
 {
@@ -77,6 +95,11 @@ __device__ __forceinline__ void st_u6(T* U, int i, const T u[6])
     typename V2<T>::t a, b, c;
     a.x = u[0]; a.y = u[1]; b.x = u[2]; b.y = u[3]; c.x = u[4]; c.y = u[5];
     p[0] = a; p[1] = b; p[2] = c;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 template <typename T>
@@ -103,7 +126,78 @@ struct SolveArgs {
     int max_iter;
     long long wait_cycles;
     int fault;
+    const int* __restrict__ bstart;   // [gridDim.x + 1] rod-rank boundaries of the blocks
 };
+
+// A block's own rods [r0, r1) and constraints [c0, c1), with their
+// shared-memory copies (valid when the block is staged).
+template <typename T>
+struct Own {
+    int r0, r1, c0, c1, q0, q1, cap_c, cap_r, cap_q;
+    T* rec;      // [9][cap_c]
+    T* q;        // [cap_c]
+    T* gs[2];    // [cap_c] gamma, ping-pong
+    T* grs;      // [cap_c] g (phase B updates it in place, one thread per entry)
+    T* ax;       // [3][cap_r]
+    T* U;        // [6][cap_r]
+    int* cj;     // [cap_c] other end (rank)
+    int* ci;     // [cap_c] owner, local index
+    int* rowP;   // [cap_r + 1] owned ranges (global constraint ids)
+    int* rowQ;   // [cap_r + 1] other-side ranges (global CSR positions)
+    int* qlist;  // [cap_q] other-side constraint ids of the block's rods
+};
+
+template <typename T>
+__host__ __device__ inline size_t staged_bytes(int cap_c, int cap_r, int cap_q)
+{
+    return (13 * (size_t)cap_c + 9 * (size_t)cap_r) * sizeof(T) +
+           (2 * (size_t)cap_c + 2 * (size_t)cap_r + 2 + (size_t)cap_q) * sizeof(int);
+}
+
+template <typename T>
+__device__ void carve(Own<T>& o, unsigned char* base)
+{
+    T* t = reinterpret_cast<T*>(base);
+    const size_t C = o.cap_c, R = o.cap_r;
+    o.rec = t; t += 9 * C;
+    o.q = t; t += C;
+    o.gs[0] = t; t += C;
+    o.gs[1] = t; t += C;
+    o.grs = t; t += C;
+    o.ax = t; t += 3 * R;
+    o.U = t; t += 6 * R;
+    int* ip = reinterpret_cast<int*>(t);
+    o.cj = ip; ip += C;
+    o.ci = ip; ip += C;
+    o.rowP = ip; ip += R + 1;
+    o.rowQ = ip; ip += R + 1;
+    o.qlist = ip;
+}
+
+template <typename T>
+__device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
+{
+    const int nr = o.r1 - o.r0, nc = o.c1 - o.c0;
+    const size_t mp = a.mp, np = a.np;
+    for (int li = threadIdx.x; li <= nr; li += blockDim.x) {
+        o.rowP[li] = a.rowP[o.r0 + li];
+        o.rowQ[li] = a.rowQ[o.r0 + li];
+    }
+    for (int li = threadIdx.x; li < nr; li += blockDim.x)
+        for (int w = 0; w < 3; ++w) o.ax[w * o.cap_r + li] = a.ax[w * np + o.r0 + li];
+    for (int lc = threadIdx.x; lc < nc; lc += blockDim.x) {
+        const int c = o.c0 + lc;
+#pragma unroll
+        for (int w = 0; w < 9; ++w) o.rec[w * o.cap_c + lc] = a.rec[w * mp + c];
+        o.q[lc] = a.q[c];
+        o.cj[lc] = a.cj[c];
+        o.ci[lc] = a.ci[c] - o.r0;
+        o.gs[0][lc] = a.gg0[2 * (size_t)c];
+        o.grs[lc] = T(0);
+    }
+    for (int k = threadIdx.x; k < o.q1 - o.q0; k += blockDim.x) o.qlist[k] = a.qlist[o.q0 + k];
+    __syncthreads();
+}
 
 template <int MODE, typename T>
 __device__ __forceinline__ T a_value(T g, T gr, T alpha)
@@ -116,62 +210,90 @@ __device__ __forceinline__ T a_value(T g, T gr, T alpha)
     return g > T(0) ? gr : (gr < T(0) ? gr : T(0));
 }
 
-// Rod-parallel half of the gradient: F = D gamma' and U = M F for the
-// block's rods [r0, r1), gamma' per MODE (A_RAW: gamma itself; A_STEP:
-// max(0, gamma - alpha g), stored by the P-side rod; A_PG: the projected
+// Rod-parallel half of the gradient for the block's rods: F = D gamma' and
+// U = M F, gamma' per MODE (A_RAW: gamma itself; A_STEP: max(0, gamma -
+// alpha g), stored by the owner into buffer cur^1; A_PG: the projected
 // gradient, returning the thread's share of pi.A.pi = sum_rods F.M.F
-// instead of storing U).  Two threads per rod: the even lane sums the rod's
-// P-range (contiguous), the odd lane its Q-side list; one shuffle combines them.
-template <typename T, int MODE>
-__device__ __forceinline__ T phase_a(const SolveArgs<T>& a, int r0, int r1, const T* gc, T* gn, T alpha)
+// instead of storing U).  (gamma_k, g_k) are in buffer cur.
+template <typename T, int MODE, bool ST>
+__device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int cur, T alpha)
 {
     T fmf = T(0);
     const size_t mp = a.mp, np = a.np;
-    constexpr int kBatch = Batch<T>::v;
-    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    constexpr int B = Batch<T>::v;
+    constexpr int BO = ST ? 1 : B;   // owned entries come from shared memory when staged
+    const T* gc = cur ? a.gg1 : a.gg0;
+    T* gn = cur ? a.gg0 : a.gg1;
+    const T* sgc = cur ? o.gs[1] : o.gs[0];      // shared copies (staged blocks)
+    const T* sgrc = o.grs;
+    T* sgn = cur ? o.gs[0] : o.gs[1];
+    for (int i = o.r0 + threadIdx.x; i < o.r1; i += blockDim.x) {
+        const int li = i - o.r0;
         T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-        {
-            // the rod's own constraints: loads of up to kBatch entries issued together
-            const int b = a.rowP[i], e = a.rowP[i + 1];
-            for (int c = b; c < e; c += kBatch) {
-                T gv[kBatch], grv[kBatch], rv[kBatch][6];
+        {   // owned constraints: loads of up to BO entries issued together
+            const int b = ST ? o.rowP[li] : a.rowP[i], e = ST ? o.rowP[li + 1] : a.rowP[i + 1];
+            for (int c = b; c < e; c += BO) {
+                T gv[BO], grv[BO], rv[BO][6];
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
+                for (int u = 0; u < BO; ++u) {
                     if (c + u < e) {
-                        ld_pair(gc, c + u, gv[u], grv[u]);
+                        if (ST) {
+                            const int lc = c + u - o.c0;
+                            gv[u] = sgc[lc];
+                            grv[u] = sgrc[lc];
 #pragma unroll
-                        for (int w = 0; w < 6; ++w) rv[u][w] = a.rec[w * mp + c + u];
+                            for (int w = 0; w < 6; ++w) rv[u][w] = o.rec[w * o.cap_c + lc];
+                        } else {
+                            ld_pair(gc, c + u, gv[u], grv[u]);
+#pragma unroll
+                            for (int w = 0; w < 6; ++w) rv[u][w] = a.rec[w * mp + c + u];
+                        }
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
+                for (int u = 0; u < BO; ++u) {
                     if (c + u < e) {
                         T v = a_value<MODE, T>(gv[u], grv[u], alpha);
-                        if (MODE == A_STEP) gn[2 * (size_t)(c + u)] = v;
+                        if (MODE == A_STEP) {
+                            if (ST) sgn[c + u - o.c0] = v;       // global copy written in phase B
+                            else gn[2 * (size_t)(c + u)] = v;
+                        }
 #pragma unroll
                         for (int w = 0; w < 6; ++w) F[w] += v * rv[u][w];
                     }
                 }
             }
         }
-        {
-            // constraints owned by other rods: ids first, then their (gamma, g) and arms
-            const int b = a.rowQ[i], e = a.rowQ[i + 1];
-            for (int k = b; k < e; k += kBatch) {
-                int cid[kBatch];
+        {   // constraints owned by other rods: ids first, then (gamma, g) and arms
+            // (from shared memory when the owner is one of the block's rods)
+            constexpr int BQ = B;
+            const int b = ST ? o.rowQ[li] : a.rowQ[i], e = ST ? o.rowQ[li + 1] : a.rowQ[i + 1];
+            for (int k = b; k < e; k += BQ) {
+                int cid[BQ];
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) cid[u] = k + u < e ? a.qlist[k + u] : -1;
-                T gv[kBatch], grv[kBatch], qv[kBatch][6];
+                for (int u = 0; u < BQ; ++u)
+                    cid[u] = k + u < e ? (ST ? o.qlist[k + u - o.q0] : __ldg(&a.qlist[k + u])) : -1;
+                T gv[BQ], grv[BQ], qv[BQ][6];
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
+                for (int u = 0; u < BQ; ++u) {
                     if (cid[u] >= 0) {
-                        ld_pair(gc, cid[u], gv[u], grv[u]);
+                        if (ST && cid[u] >= o.c0 && cid[u] < o.c1) {
+                            const int lc = cid[u] - o.c0;
+                            gv[u] = sgc[lc];
+                            grv[u] = sgrc[lc];
 #pragma unroll
-                        for (int w = 0; w < 6; ++w) qv[u][w] = a.qe[w * mp + k + u];
+                            for (int w = 0; w < 3; ++w) {
+                                qv[u][w] = o.rec[w * o.cap_c + lc];
+                                qv[u][3 + w] = o.rec[(6 + w) * o.cap_c + lc];
+                            }
+                        } else {
+                            ld_pair(gc, cid[u], gv[u], grv[u]);
+                            ld_arm(a.qe, k + u, qv[u]);
+                        }
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
+                for (int u = 0; u < BQ; ++u) {
                     if (cid[u] >= 0) {
                         T v = a_value<MODE, T>(gv[u], grv[u], alpha);
 #pragma unroll
@@ -180,83 +302,112 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, int r0, int r1, cons
                 }
             }
         }
-        {
-            T p0 = a.ax[i], p1 = a.ax[np + i], p2 = a.ax[2 * np + i];
-            T pf = p0 * F[0] + p1 * F[1] + p2 * F[2];
-            T pt = p0 * F[3] + p1 * F[4] + p2 * F[5];
-            T cf = pf * (a.inv_par - a.inv_perp), ct = pt * (a.inv_spin - a.inv_rot);
-            T Uv[6] = {F[0] * a.inv_perp + p0 * cf, F[1] * a.inv_perp + p1 * cf, F[2] * a.inv_perp + p2 * cf,
-                       F[3] * a.inv_rot + p0 * ct,  F[4] * a.inv_rot + p1 * ct,  F[5] * a.inv_rot + p2 * ct};
-            if (MODE == A_PG) {
+        T p0, p1, p2;
+        if (ST) {
+            p0 = o.ax[li]; p1 = o.ax[o.cap_r + li]; p2 = o.ax[2 * o.cap_r + li];
+        } else {
+            p0 = a.ax[i]; p1 = a.ax[np + i]; p2 = a.ax[2 * np + i];
+        }
+        const T pf = p0 * F[0] + p1 * F[1] + p2 * F[2];
+        const T pt = p0 * F[3] + p1 * F[4] + p2 * F[5];
+        const T cf = pf * (a.inv_par - a.inv_perp), ct = pt * (a.inv_spin - a.inv_rot);
+        T Uv[6] = {F[0] * a.inv_perp + p0 * cf, F[1] * a.inv_perp + p1 * cf, F[2] * a.inv_perp + p2 * cf,
+                   F[3] * a.inv_rot + p0 * ct,  F[4] * a.inv_rot + p1 * ct,  F[5] * a.inv_rot + p2 * ct};
+        if (MODE == A_PG) {
 #pragma unroll
-                for (int u = 0; u < 6; ++u) fmf += F[u] * Uv[u];
-            } else {
-                st_u6(a.U, i, Uv);
+            for (int w = 0; w < 6; ++w) fmf += F[w] * Uv[w];
+        } else {
+            st_u6(a.U, i, Uv);
+            if (ST) {
+#pragma unroll
+                for (int w = 0; w < 6; ++w) o.U[w * o.cap_r + li] = Uv[w];
             }
         }
     }
     return fmf;
 }
 
-// Constraint-parallel half: g_new = q + D^T U, written into the y slot of
-// the new (gamma, g) pair, plus the thread's partial sums.
-// FIRST: acc0 = pi.pi; otherwise acc0..2 = s.s, s.y, y.y; acc3 = max |pi|.
-template <typename T, bool FIRST>
-__device__ __forceinline__ void phase_b(const SolveArgs<T>& a, int c0, int c1, T* gnew, const T* gold, T acc[4])
+// Constraint-parallel half for the block's owned constraints: g_new = q +
+// D^T U into buffer nx (its y slot; gamma_new is its x slot), plus the
+// thread's partial sums.  FIRST: nx = cur = 0 and acc0 = pi.pi; otherwise
+// acc0..2 = s.s, s.y, y.y against buffer cur; acc3 = max |pi|.
+template <typename T, bool FIRST, bool ST>
+__device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, int cur, int nx, T acc[4])
 {
     const size_t mp = a.mp;
-    const int nt = blockDim.x;
-    // two constraints per thread and round; every load of both is issued
-    // before the first store
-    for (int cA = c0 + threadIdx.x; cA < c1; cA += kRoundB * nt) {
-        const int cB = cA + nt;
-        const bool hasB = kRoundB > 1 && cB < c1;
-        int idx[2] = {cA, hasB ? cB : cA};
-        T Ui[2][6], Uj[2][6], r[2][9], qq[2], gm[2], go[2], gro[2];
+    T* gnew = nx ? a.gg1 : a.gg0;
+    const T* gold = cur ? a.gg1 : a.gg0;
+    const T* sgnew = nx ? o.gs[1] : o.gs[0];     // shared copies (staged blocks)
+    T* sgr = o.grs;                              // g_k in, g_{k+1} out (same thread)
+    const T* sgold = cur ? o.gs[1] : o.gs[0];
+    const int nc = o.c1 - o.c0;
+    for (int lc = threadIdx.x; lc < nc; lc += blockDim.x) {
+        const int c = o.c0 + lc;
+        T Ui[6], Uj[6], r[9], qq, gm, go = T(0), gro = T(0);
+        if (ST) {
+            const int il = o.ci[lc], j = o.cj[lc];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = idx[h];
-            ld_u6(a.U, a.ci[c], Ui[h]);
-            ld_u6(a.U, a.cj[c], Uj[h]);
+            for (int w = 0; w < 6; ++w) Ui[w] = o.U[w * o.cap_r + il];
+            if (j >= o.r0 && j < o.r1) {
 #pragma unroll
-            for (int w = 0; w < 9; ++w) r[h][w] = a.rec[w * mp + c];
-            qq[h] = a.q[c];
-            gm[h] = gnew[2 * (size_t)c];
-            if (!FIRST) ld_pair(gold, c, go[h], gro[h]);
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (h == 1 && !hasB) break;
-            const int c = idx[h];
-            T du = T(0);
-#pragma unroll
-            for (int u = 0; u < 3; ++u) {
-                du += r[h][u] * (Ui[h][u] - Uj[h][u]);
-                du += r[h][3 + u] * Ui[h][3 + u];
-                du -= r[h][6 + u] * Uj[h][3 + u];
-            }
-            const T gr = qq[h] + du;
-            gnew[2 * (size_t)c + 1] = gr;
-            const T g1 = gm[h];
-            T pi = g1 > T(0) ? gr : (gr < T(0) ? gr : T(0));
-            T api = pi < T(0) ? -pi : pi;
-            acc[3] = api > acc[3] ? api : acc[3];
-            if (FIRST) {
-                acc[0] += pi * pi;
+                for (int w = 0; w < 6; ++w) Uj[w] = o.U[w * o.cap_r + (j - o.r0)];
             } else {
-                T sv = g1 - go[h], yv = gr - gro[h];
-                acc[0] += sv * sv;
-                acc[1] += sv * yv;
-                acc[2] += yv * yv;
+                ld_u6(a.U, j, Uj);
             }
+#pragma unroll
+            for (int w = 0; w < 9; ++w) r[w] = o.rec[w * o.cap_c + lc];
+            qq = o.q[lc];
+            gm = sgnew[lc];
+            if (!FIRST) {
+                go = sgold[lc];
+                gro = sgr[lc];
+            }
+        } else {
+            ld_u6(a.U, a.ci[c], Ui);
+            ld_u6(a.U, a.cj[c], Uj);
+#pragma unroll
+            for (int w = 0; w < 9; ++w) r[w] = a.rec[w * mp + c];
+            qq = a.q[c];
+            gm = gnew[2 * (size_t)c];
+            if (!FIRST) ld_pair(gold, c, go, gro);
+        }
+        T du = T(0);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            du += r[u] * (Ui[u] - Uj[u]);
+            du += r[3 + u] * Ui[3 + u];
+            du -= r[6 + u] * Uj[3 + u];
+        }
+        const T gr = qq + du;
+        if (ST) {
+            sgr[lc] = gr;
+            // the pair other blocks read in the next phase A
+            typename V2<T>::t pr;
+            pr.x = gm;
+            pr.y = gr;
+            reinterpret_cast<typename V2<T>::t*>(gnew)[c] = pr;
+        } else {
+            gnew[2 * (size_t)c + 1] = gr;
+        }
+        T pi = gm > T(0) ? gr : (gr < T(0) ? gr : T(0));
+        T api = pi < T(0) ? -pi : pi;
+        acc[3] = api > acc[3] ? api : acc[3];
+        if (FIRST) {
+            acc[0] += pi * pi;
+        } else {
+            const T sv = gm - go, yv = gr - gro;
+            acc[0] += sv * sv;
+            acc[1] += sv * yv;
+            acc[2] += yv * yv;
         }
     }
 }
 
-// Block partial of (sum, sum, sum, max): warp shuffles in T, then warp 0
-// combines the warp results in float64 and lane 0 stores them.  Fixed order.
+// Block partial of (sum, sum, sum, max) in the working precision (warp
+// shuffles, then warp 0 over the warp results, fixed order); lane 0 stores
+// it as float64 for the cross-block sum.
 template <typename T>
-__device__ __forceinline__ void block_partial(T v[4], double (*red)[4], double* dst)
+__device__ __forceinline__ void block_partial(T v[4], T (*red)[4], double* dst)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -268,11 +419,11 @@ __device__ __forceinline__ void block_partial(T v[4], double (*red)[4], double* 
     }
     if (lane == 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) red[warp][u] = (double)v[u];
+        for (int u = 0; u < 4; ++u) red[warp][u] = v[u];
     }
     __syncthreads();
     if (warp == 0) {
-        double w[4] = {0.0, 0.0, 0.0, 0.0};
+        T w[4] = {T(0), T(0), T(0), T(0)};
         if (lane < nw) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) w[u] = red[lane][u];
@@ -281,69 +432,68 @@ __device__ __forceinline__ void block_partial(T v[4], double (*red)[4], double* 
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
             for (int u = 0; u < 3; ++u) w[u] += __shfl_down_sync(0xffffffffu, w[u], o);
-            double mx = __shfl_down_sync(0xffffffffu, w[3], o);
+            T mx = __shfl_down_sync(0xffffffffu, w[3], o);
             w[3] = mx > w[3] ? mx : w[3];
         }
         if (lane == 0) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) dst[u] = w[u];
+            for (int u = 0; u < 4; ++u) dst[u] = (double)w[u];
         }
     }
 }
 
 // Bounded grid barrier on a monotone arrival counter: block b's k-th arrival
-// waits until the counter reaches k * gridDim.x.  The wait gives up after
-// wait_cycles clock cycles or 2^28 polls, records ALENS_ERR_TIMEOUT and
-// returns false; it also returns false as soon as any block has recorded an
-// error, so every block leaves.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* flags, long long wait_cycles)
+// waits until the counter reaches k * gridDim.x.  Arrival is a release
+// reduction and the wait an acquire poll by thread 0, whose verdict the
+// block reads from shared memory.  The wait gives up after wait_cycles clock
+// cycles or 2^28 polls, records ALENS_ERR_TIMEOUT and returns false; it also
+// returns false as soon as any block has recorded an error, so every block
+// leaves.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* flags, long long wait_cycles,
+                                             int* s_ok)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(count, 1u);
+        red_release_add(count, 1u);
         long long t0 = clock64();
+        int ok = 1;
         for (unsigned polls = 0;; ++polls) {
             unsigned v = ld_acquire_u32(count);
             if ((int)(v - target) >= 0) break;
-            if (ld_volatile_i32(&flags[F_SOLVE_ERR]) != 0) break;
+            if (ld_volatile_i32(&flags[F_SOLVE_ERR]) != 0) { ok = 0; break; }
             if (clock64() - t0 > wait_cycles || polls > (1u << 28)) {
                 atomicCAS(&flags[F_SOLVE_ERR], 0, ALENS_ERR_TIMEOUT);
+                ok = 0;
                 break;
             }
         }
-        __threadfence();
+        if (ok && ld_volatile_i32(&flags[F_SOLVE_ERR]) != 0) ok = 0;
+        *s_ok = ok;
     }
     __syncthreads();
-    return ld_volatile_i32(&flags[F_SOLVE_ERR]) == 0;
+    return *s_ok != 0;
 }
 
-// After a barrier: warp 0 reduces the per-block partials in float64 in a
-// fixed order and broadcasts the four totals through shared memory.
+// After a barrier: warps 0-3 each reduce one component of the per-block
+// partials in float64 in a fixed order (L2 loads, several blocks per lane in
+// flight) and the four totals are broadcast through shared memory.
 __device__ __forceinline__ void grid_total(const double* partials, int nb, double* bc, double out[4])
 {
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        double w[4] = {0.0, 0.0, 0.0, 0.0};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {
+        const bool is_max = warp == 3;
+        double w = 0.0;
+#pragma unroll 4
         for (int b = lane; b < nb; b += 32) {
-            const volatile double* pb = partials + 4 * (size_t)b;
-            w[0] += pb[0];
-            w[1] += pb[1];
-            w[2] += pb[2];
-            double mx = pb[3];
-            w[3] = mx > w[3] ? mx : w[3];
+            const double x = __ldcg(partials + 4 * (size_t)b + warp);
+            w = is_max ? (x > w ? x : w) : w + x;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int u = 0; u < 3; ++u) w[u] += __shfl_down_sync(0xffffffffu, w[u], o);
-            double mx = __shfl_down_sync(0xffffffffu, w[3], o);
-            w[3] = mx > w[3] ? mx : w[3];
+            const double y = __shfl_down_sync(0xffffffffu, w, o);
+            w = is_max ? (y > w ? y : w) : w + y;
         }
-        if (lane == 0) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) bc[u] = w[u];
-        }
+        if (lane == 0) bc[warp] = w;
     }
     __syncthreads();
 #pragma unroll
@@ -358,71 +508,102 @@ struct StepState {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(1024, 1) k_bbpgd(SolveArgs<T> a)
+struct Shared {
+    T red[32][4];
+    double bc[4];
+    T alpha;
+    int done, ok;
+};
+
+// Smallest rank r in [0, n] whose cumulative work W(r) = rowP[r] +
+// kOtherWork * rowQ[r] + kRodWork * r reaches target (an other-side entry,
+// gathered from another block, costs about twice an owned one); W is
+// strictly increasing and W(n) >= target.  One warp: 32 probes per round,
+// then a final scan of at most 32 ranks.
+constexpr int kRodWork = 2;
+constexpr int kOtherWork = 2;
+__device__ __forceinline__ int find_rank(const int* rowP, const int* rowQ, int n, long long target)
 {
-    __shared__ double red[32][4];
-    __shared__ double bc[4];
-    __shared__ T s_alpha;
-    __shared__ int s_done;
-    if (a.fault == 1 && blockIdx.x == 0) return;   // test hook: this block never arrives
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n;
+    while (hi - lo >= 32) {
+        const long long span = hi - lo;
+        const int p = lo + (int)(span * (lane + 1) / 33);
+        const long long w = (long long)rowP[p] + (long long)kOtherWork * rowQ[p] + (long long)kRodWork * p;
+        const unsigned ge = __ballot_sync(0xffffffffu, w >= target);
+        if (ge == 0) {
+            lo = __shfl_sync(0xffffffffu, p, 31) + 1;
+        } else {
+            const int f = __ffs(ge) - 1;
+            const int pf = __shfl_sync(0xffffffffu, p, f);
+            const int pb = __shfl_sync(0xffffffffu, p, f > 0 ? f - 1 : 0);
+            if (f > 0) lo = pb + 1;
+            hi = pf;
+        }
+    }
+    const int p = lo + lane;
+    bool ge = false;
+    if (p <= hi) ge = (long long)rowP[p] + (long long)kOtherWork * rowQ[p] + (long long)kRodWork * p >= target;
+    const unsigned m = __ballot_sync(0xffffffffu, ge);
+    return m ? lo + __ffs(m) - 1 : hi;
+}
+
+template <typename T, bool ST>
+__device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& o, Shared<T>& sh)
+{
     const unsigned nb = gridDim.x;
     double* mine = a.partials + 4 * (size_t)blockIdx.x;
     unsigned epoch = 0;
-    // this block's rods (an even split) and the P-side constraints they own
-    const int per = (a.n + (int)nb - 1) / (int)nb;
-    const int r0 = min(a.n, (int)blockIdx.x * per), r1 = min(a.n, r0 + per);
-    const int c0 = a.rowP[r0], c1 = a.rowP[r1];
     double tot[4];
     T v[4];
     StepState st;   // meaningful in thread 0 only
+    st.alpha0 = 1.0;
 
     // U = M D gamma_0
-    phase_a<T, A_RAW>(a, r0, r1, a.gg0, nullptr, T(0));
-    if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
+    phase_a<T, A_RAW, ST>(a, o, 0, T(0));
+    if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
     // g_0 and the projected gradient at gamma_0
     v[0] = v[1] = v[2] = v[3] = T(0);
-    phase_b<T, true>(a, c0, c1, a.gg0, nullptr, v);
-    block_partial(v, red, mine);
-    if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
-    grid_total(a.partials, nb, bc, tot);
+    phase_b<T, true, ST>(a, o, 0, 0, v);
+    block_partial(v, sh.red, mine);
+    if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+    grid_total(a.partials, nb, sh.bc, tot);
     if (threadIdx.x == 0) {
         st.res = a.hD * tot[3];
         st.iters = 0;
         st.cur = 0;
         st.done = !(st.res > a.tol && a.max_iter > 0);
-        s_done = st.done;
+        sh.done = st.done;
     }
     __syncthreads();
-    if (!s_done) {
+    if (!sh.done) {
         const double pp = tot[0];
         // alpha_0 = pi.pi / pi.A.pi (exact line step along the projected gradient)
-        v[0] = phase_a<T, A_PG>(a, r0, r1, a.gg0, nullptr, T(0));
+        v[0] = phase_a<T, A_PG, ST>(a, o, 0, T(0));
         v[1] = v[2] = v[3] = T(0);
         // every block has read the partials (grid_total) before any rewrites them
-        if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
-        block_partial(v, red, mine);
-        if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
-        grid_total(a.partials, nb, bc, tot);
+        if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+        block_partial(v, sh.red, mine);
+        if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+        grid_total(a.partials, nb, sh.bc, tot);
         if (threadIdx.x == 0) {
             const double pap = tot[0];
             double alpha0 = pp / pap;
             if (!(pap > 0.0) || !isfinite(alpha0) || !(alpha0 > 0.0)) alpha0 = 1.0;
             st.alpha0 = st.alpha = alpha0;
-            s_alpha = (T)alpha0;
+            sh.alpha = (T)alpha0;
         }
         __syncthreads();
         int cur = 0;
         for (int k = 0; k < a.max_iter; ++k) {
             const int nx = cur ^ 1;
-            T* gc = cur ? a.gg1 : a.gg0;
-            T* gn = cur ? a.gg0 : a.gg1;
-            phase_a<T, A_STEP>(a, r0, r1, gc, gn, s_alpha);
-            if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
+            phase_a<T, A_STEP, ST>(a, o, cur, sh.alpha);
+            if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
             v[0] = v[1] = v[2] = v[3] = T(0);
-            phase_b<T, false>(a, c0, c1, gn, gc, v);
-            block_partial(v, red, mine);
-            if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles)) return;
-            grid_total(a.partials, nb, bc, tot);
+            phase_b<T, false, ST>(a, o, cur, nx, v);
+            block_partial(v, sh.red, mine);
+            if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+            grid_total(a.partials, nb, sh.bc, tot);
             cur = nx;
             if (threadIdx.x == 0) {
                 const double ss = tot[0], sy = tot[1], yy = tot[2];
@@ -434,20 +615,67 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd(SolveArgs<T> a)
                     double an = (k & 1) == 0 ? ss / sy : sy / yy;
                     if (!(sy > 0.0) || !isfinite(an) || !(an > 0.0)) an = st.alpha0;
                     st.alpha = an;
-                    s_alpha = (T)an;
+                    sh.alpha = (T)an;
                 }
-                s_done = st.done;
+                sh.done = st.done;
             }
             __syncthreads();
-            if (s_done) break;
+            if (sh.done) break;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.out[1] = st.alpha0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.out[1] = st.alpha0;
         a.flags[F_FINAL] = st.cur;
         a.flags[F_ITERS] = st.iters;
         a.out[0] = st.res;
     }
+}
+
+// One warp per block boundary b in [0, nb]: the work-balanced split.
+__global__ void k_partition(int n, int m, int nb, const int* __restrict__ rowP, const int* __restrict__ rowQ,
+                            int* __restrict__ bstart)
+{
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b > nb) return;   // uniform per warp
+    const long long total = (1LL + kOtherWork) * m + (long long)kRodWork * n;
+    const int r = b == nb ? n : find_rank(rowP, rowQ, n, total * b / nb);
+    if ((threadIdx.x & 31) == 0) bstart[b] = r;
+}
+
+// Largest shared-memory share over the blocks (bytes, for element size esize).
+__global__ void k_stage_need(int nb, int esize, const int* __restrict__ bstart, const int* __restrict__ rowP,
+                             const int* __restrict__ rowQ, unsigned long long* __restrict__ need)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int r0 = bstart[b], r1 = bstart[b + 1];
+    const size_t nc = rowP[r1] - rowP[r0], nq = rowQ[r1] - rowQ[r0], nr = r1 - r0;
+    const size_t bytes = (13 * nc + 9 * nr) * (size_t)esize + (2 * nc + 2 * nr + 2 + nq) * sizeof(int);
+    atomicMax(need, (unsigned long long)bytes);
+}
+
+template <typename T, bool ST>
+__global__ void __launch_bounds__(1024, 1) k_bbpgd(SolveArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ Shared<T> sh;
+    if (a.fault == 1 && blockIdx.x == 0) return;   // test hook: this block never arrives
+    Own<T> o;
+    o.r0 = a.bstart[blockIdx.x];
+    o.r1 = a.bstart[blockIdx.x + 1];
+    o.c0 = a.rowP[o.r0];
+    o.c1 = a.rowP[o.r1];
+    o.q0 = a.rowQ[o.r0];
+    o.q1 = a.rowQ[o.r1];
+    // the carve uses the block's own counts (all of them fit: checked on launch)
+    o.cap_c = o.c1 - o.c0;
+    o.cap_r = o.r1 - o.r0;
+    o.cap_q = o.q1 - o.q0;
+    if (ST) {
+        carve(o, dyn);
+        stage_in(a, o);
+    }
+    solve_loop<T, ST>(a, o, sh);
 }
 
 // gamma back in the caller's pair order.
@@ -493,22 +721,45 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     a.fault = ctx->fault_mode;
     ctx->fault_mode = 0;
 
-    int threads = ctx->solve_threads;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bbpgd<T>, threads, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (ctx->solve_bps > 0 && ctx->solve_bps < per_sm) per_sm = ctx->solve_bps;
+    const int threads = ctx->solve_threads;
+    const int bps = ctx->solve_bps > 0 ? ctx->solve_bps : 1;
     // enough blocks that each has at least a warp of rods
     long long want = ((long long)n + 31) / 32;
-    long long blocks = (long long)per_sm * ctx->num_sms;
+    long long blocks = (long long)bps * ctx->num_sms;
     if (want < blocks) blocks = want < 1 ? 1 : want;
     if (blocks > ctx->max_blocks) blocks = ctx->max_blocks;
+    // work-balanced split, then the largest shared-memory share: stage every
+    // block's data when all shares fit the opt-in budget (one readback)
+    cudaError_t e;
+    a.bstart = ctx->bstart;
+    const int nbw = (int)blocks + 1;
+    k_partition<<<(nbw * 32 + 255) / 256, 256, 0, ctx->stream>>>(n, m, (int)blocks, ctx->rowP, ctx->rowQ, ctx->bstart);
+    ++ctx->launches;
+    if ((e = cudaMemsetAsync(ctx->dcount + C_SMEM, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess) return e;
+    k_stage_need<<<((int)blocks + 127) / 128, 128, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart, ctx->rowP,
+                                                                  ctx->rowQ, ctx->dcount + C_SMEM);
+    ++ctx->launches;
+    unsigned long long need = 0;
+    if ((e = cudaMemcpyAsync(&need, ctx->dcount + C_SMEM, sizeof(need), cudaMemcpyDeviceToHost, ctx->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+        return e;
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device)) != cudaSuccess)
+        return e;
+    const long long budget = (long long)optin / bps - (long long)sizeof(Shared<T>) - 1024;
+    const bool staged = (long long)need <= budget;
+    const size_t smem = staged ? (size_t)need : 0;
+    const void* fn = staged ? (const void*)k_bbpgd<T, true> : (const void*)k_bbpgd<T, false>;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem)) != cudaSuccess) return e;
+    if ((long long)per_sm * ctx->num_sms < blocks) return cudaErrorCooperativeLaunchTooLarge;
     if ((e = cudaMemsetAsync(ctx->bar, 0, 4 * sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
     void* args[] = {&a};
     ++ctx->launches;
-    return cudaLaunchCooperativeKernel((const void*)k_bbpgd<T>, dim3((unsigned)blocks), dim3(threads), args, 0,
-                                       ctx->stream);
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, ctx->stream);
 }
 
 cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision)
