@@ -193,6 +193,22 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def replica_time(ms_local, pg=None, device=None):
+    """Step time of a replicas run: the slowest rank's (MAX all-reduce; the
+    ranks run independent systems, so this is the only collective)."""
+    if pg is None:
+        return ms_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ms_step, rods_per_rank, world_size):
+    """Whole-job rod-steps/s: rods of all ranks over the slowest rank's step time."""
+    return world_size * rods_per_rank / (ms_step / 1e3)
+
+
 # ------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -283,11 +299,7 @@ def run_ours(args):
             pg.barrier()
 
     def max_over_ranks(v):
-        if pg is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return replica_time(v, pg, dev)
 
     # ---- FP32-mixed: the headline
     ctx = make_ctx(A.MIXED)
@@ -303,7 +315,7 @@ def run_ours(args):
         barrier()
         wall = time.perf_counter() - t0
     ms_step = max_over_ranks(statistics.mean(ms))
-    value = ws * n / (ms_step / 1e3)
+    value = replica_value(ms_step, n, ws)
     it = [i["iters"] for i in infos]
     ms_solve = statistics.mean(i["ms_solve"] for i in infos)
     m = infos[-1]["n_pairs"]
@@ -322,7 +334,7 @@ def run_ours(args):
         ctx64 = make_ctx(A.FP64)
         ms64, inf64 = timed(ctx64, max(2, args.steps // 2), 1)
         ms64_step = max_over_ranks(statistics.mean(ms64))
-        fp64 = {"value": ws * n / (ms64_step / 1e3), "unit": UNIT, "ms_per_step": ms64_step,
+        fp64 = {"value": replica_value(ms64_step, n, ws), "unit": UNIT, "ms_per_step": ms64_step,
                 "bbpgd_iters": statistics.mean(i["iters"] for i in inf64),
                 "residual": max(i["residual"] for i in inf64),
                 "ms_solve": statistics.mean(i["ms_solve"] for i in inf64),
@@ -337,7 +349,7 @@ def run_ours(args):
         ox = torch.empty_like(hx).pin_memory(); oq = torch.empty_like(hq).pin_memory()
         mse, _ = timed(ctx, args.steps, 1, host=(hx, hq, hf, ox, oq))
         mse_step = max_over_ranks(statistics.mean(mse))
-        e2e = {"value": ws * n / (mse_step / 1e3), "unit": UNIT, "ms_per_step": mse_step,
+        e2e = {"value": replica_value(mse_step, n, ws), "unit": UNIT, "ms_per_step": mse_step,
                "h2d_bytes_per_step": int(hx.numel() * 8 + hq.numel() * 8 + hf.numel() * 8),
                "d2h_bytes_per_step": int(ox.numel() * 8 + oq.numel() * 8)}
     ctx.close()
