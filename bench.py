@@ -98,7 +98,7 @@ class Clocks:
         try:
             sel = ["-i", str(self.idx)] if self.idx is not None else []
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", *sel], stdout=subprocess.PIPE,
+                                          "-lms", "50", *sel], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -309,11 +309,11 @@ def run_ours(args):
         gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
     except Exception:
         gpu_id = None
-    with Clocks(gpu_id) as clk:
-        t0 = time.perf_counter()
-        ms, infos = timed(ctx, args.steps, args.warmup)
-        barrier()
-        wall = time.perf_counter() - t0
+    clk = Clocks(gpu_id).__enter__()   # sampled across every timed region below
+    t0 = time.perf_counter()
+    ms, infos = timed(ctx, args.steps, args.warmup)
+    barrier()
+    wall = time.perf_counter() - t0
     ms_step = max_over_ranks(statistics.mean(ms))
     value = replica_value(ms_step, n, ws)
     it = [i["iters"] for i in infos]
@@ -352,6 +352,26 @@ def run_ours(args):
         e2e = {"value": replica_value(mse_step, n, ws), "unit": UNIT, "ms_per_step": mse_step,
                "h2d_bytes_per_step": int(hx.numel() * 8 + hq.numel() * 8 + hf.numel() * 8),
                "d2h_bytes_per_step": int(ox.numel() * 8 + oq.numel() * 8)}
+    clk.__exit__(None, None, None)
+
+    # ---- the mixed step's deviation from the float64 step (outside the timed regions)
+    mixed_vs_fp64 = None
+    if not args.skip_fp64:
+        outs = {}
+        for prec in (A.MIXED, A.FP64):
+            c2 = make_ctx(prec)
+            xx, qq = x0.clone(), q0.clone()
+            gam = torch.empty(max_pairs, dtype=torch.float64, device=dev)
+            inf = c2.step(xx, qq, f, gamma_out=gam)
+            outs[prec] = (xx, qq, gam[: inf.n_pairs].clone())
+            c2.close()
+        dx = outs[A.MIXED][0] - outs[A.FP64][0]
+        boxt = torch.tensor(s.box, dtype=torch.float64, device=dev)
+        dx = dx - boxt * torch.round(dx / boxt)
+        g32, g64 = outs[A.MIXED][2], outs[A.FP64][2]
+        mixed_vs_fp64 = {"max_dx_over_D": float(dx.abs().max()) / s.diameter,
+                         "gamma_rel_l2": float(torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64)),
+                         "max_dquat": float((outs[A.MIXED][1] - outs[A.FP64][1]).abs().max())}
     ctx.close()
 
     if rank != 0:
@@ -374,7 +394,7 @@ def run_ours(args):
         "bbpgd_iters": statistics.mean(it), "residual": res,
         "phase_ms": {k: statistics.mean(i[k] for i in infos) for k in ("ms_build", "ms_assemble", "ms_solve",
                                                                          "ms_update")},
-        "fp64": fp64, "e2e": e2e,
+        "fp64": fp64, "e2e": e2e, "mixed_vs_fp64": mixed_vs_fp64,
         "roofline": {"kernel": "k_bbpgd<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_iter": b_iter},
