@@ -286,35 +286,49 @@ ORC_API int64_t orc_find_pairs_rows(int64_t n, const double* x, const double* qu
     double* axis = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     orc_wrap(n, x, pb->box, xw);
     orc_axis(n, quat, axis);
-    int64_t room = 64, used = 0;
-    int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)room);
+    /* one growable buffer per listed rod, filled in parallel, then joined */
+    int32_t** bufs = (int32_t**)calloc((size_t)(nrows > 0 ? nrows : 1), sizeof(int32_t*));
+    int64_t* used = (int64_t*)calloc((size_t)(nrows > 0 ? nrows : 1), sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic, 1)
     for (int64_t r = 0; r < nrows; ++r) {
-        int64_t a = rows[r];
+        int64_t a = rows[r], room = 64, u = 0;
+        int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)room);
         for (int64_t j = 0; j < n; ++j) {
             if (j == a) continue;
             int64_t i = a < j ? a : j, jj = a < j ? j : a;
             for (int code = 0; code < 27; ++code) {
                 double gap, s, t, dx[3];
                 if (pair_gap(xw, axis, pb, i, jj, code, &gap, &s, &t, dx) && gap < pb->delta_c) {
-                    if (used == room) {
+                    if (u == room) {
                         room *= 2;
                         buf = (int32_t*)realloc(buf, sizeof(int32_t) * 3 * (size_t)room);
                     }
-                    buf[3 * used] = (int32_t)i; buf[3 * used + 1] = (int32_t)jj; buf[3 * used + 2] = code;
-                    ++used;
+                    buf[3 * u] = (int32_t)i; buf[3 * u + 1] = (int32_t)jj; buf[3 * u + 2] = code;
+                    ++u;
                 }
             }
         }
+        bufs[r] = buf;
+        used[r] = u;
     }
-    qsort(buf, (size_t)used, 3 * sizeof(int32_t), cmp_triple);
+    int64_t total = 0;
+    for (int64_t r = 0; r < nrows; ++r) total += used[r];
+    int32_t* all = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)(total > 0 ? total : 1));
+    int64_t o = 0;
+    for (int64_t r = 0; r < nrows; ++r) {
+        memcpy(all + 3 * o, bufs[r], sizeof(int32_t) * 3 * (size_t)used[r]);
+        o += used[r];
+        free(bufs[r]);
+    }
+    qsort(all, (size_t)total, 3 * sizeof(int32_t), cmp_triple);
     int64_t u = 0;
-    for (int64_t k = 0; k < used; ++k) {
-        if (u > 0 && cmp_triple(buf + 3 * k, buf + 3 * (u - 1)) == 0) continue;
-        if (u != k) memcpy(buf + 3 * u, buf + 3 * k, 3 * sizeof(int32_t));
+    for (int64_t k = 0; k < total; ++k) {
+        if (u > 0 && cmp_triple(all + 3 * k, all + 3 * (u - 1)) == 0) continue;
+        if (u != k) memcpy(all + 3 * u, all + 3 * k, 3 * sizeof(int32_t));
         ++u;
     }
-    if (pairs && u <= cap) memcpy(pairs, buf, sizeof(int32_t) * 3 * (size_t)u);
-    free(buf); free(xw); free(axis);
+    if (pairs && u <= cap) memcpy(pairs, all, sizeof(int32_t) * 3 * (size_t)u);
+    free(all); free(bufs); free(used); free(xw); free(axis);
     return u;
 }
 

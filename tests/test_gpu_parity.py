@@ -355,3 +355,42 @@ def test_n100k_step_properties(n100k, precision, tol):
     assert rel_l2(host(vel), U) <= (1e-9 if precision == A.FP64 else 1e-4)
     xo = O.wrap(O.wrap(s.x, s.box) + s.dt * U[:, :3], s.box)
     assert np.abs(periodic_diff(host(x), xo, s.box)).max() <= (1e-9 if precision == A.FP64 else 1e-5)
+
+
+# -------------------------------------------- 4e5 rods, nematic, mixed precision
+
+@pytest.fixture(scope="module")
+def n400k():
+    return W.workload("n400k_nematic")
+
+
+def test_n400k_nematic_mixed_against_oracle_and_fp64(n400k):
+    # the dense nematic pack: FP32-mixed iterations at tol 1e-5; errors
+    # reported against the float64 oracle (KKT of the GPU answer) and the
+    # float64 GPU step
+    s = n400k
+    pb = O.problem_of(s)
+    mp = 12 * s.n
+    res = {}
+    for prec in (A.MIXED, A.FP64):
+        x, q = dev(s.x), dev(s.quat)
+        with make_ctx(s, prec, 1e-5, max_pairs=mp) as ctx:
+            gam = torch.empty(mp, dtype=torch.float64, device="cuda")
+            pr = torch.empty((mp, 3), dtype=torch.int32, device="cuda")
+            info = ctx.step(x, q, dev(s.f_nc), pairs_out=pr, gamma_out=gam)
+            m = info.n_pairs
+            res[prec] = (info, host(x), host(q), host(pr)[:m], host(gam)[:m])
+    info, x32, q32, pairs, g32 = res[A.MIXED]
+    assert info.status == 0 and info.residual <= 1e-5 and 1e6 < info.n_pairs < 4e6
+    assert np.array_equal(pairs, res[A.FP64][3])
+    rng = np.random.default_rng(1)
+    rows = np.sort(rng.choice(s.n, 40, replace=False))
+    ref = O.find_pairs(s.x, s.quat, pb, rows=rows)
+    compare_pairs(pairs[np.isin(pairs[:, 0], rows) | np.isin(pairs[:, 1], rows)], ref, s)
+    asm = O.assemble(s.x, s.quat, s.f_nc, pb, pairs)
+    _, r = O.gradient(s.quat, pb, pairs, asm["dgeom"], asm["q"], g32)
+    print(f"\nn400k mixed: {info.iters} iterations, GPU residual {info.residual:.3e}, "
+          f"oracle residual of the mixed gamma {r:.3e}, "
+          f"max |x_mixed - x_fp64| = {np.abs(periodic_diff(x32, res[A.FP64][1], s.box)).max():.3e} D")
+    assert r <= 1.05e-5 + 1e-6
+    assert np.abs(periodic_diff(x32, res[A.FP64][1], s.box)).max() <= 1e-4 * s.diameter
