@@ -190,7 +190,7 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
                              const double* __restrict__ q64, const double* __restrict__ gin,
                              const int* __restrict__ rowQ, int* __restrict__ curQ, int* __restrict__ qlist,
                              int* __restrict__ ci, int* __restrict__ cj, T* __restrict__ rec, T* __restrict__ qT,
-                             T* __restrict__ gg0)
+                             T* __restrict__ gg0, T* __restrict__ gg1)
 {
     int cc = blockIdx.x * blockDim.x + threadIdx.x;
     if (cc >= m) return;
@@ -214,8 +214,15 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
     }
     qT[cc] = (T)q64[c];
     double v = gin ? gin[c] : 0.0;
-    gg0[2 * (size_t)cc] = v > 0.0 ? (T)v : T(0);
-    gg0[2 * (size_t)cc + 1] = T(0);
+    // solver state (delta, g, gamma_ref, 0) in both buffers: gamma_0 is the
+    // first reference
+    for (int b = 0; b < 2; ++b) {
+        T* st = (b ? gg1 : gg0) + 4 * (size_t)cc;
+        st[0] = T(0);
+        st[1] = T(0);
+        st[2] = v > 0.0 ? (T)v : T(0);
+        st[3] = T(0);
+    }
     qlist[rowQ[rq] + atomicAdd(&curQ[rq], 1)] = cc;
 }
 
@@ -277,7 +284,7 @@ static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     }
     if (m <= 0) return cudaGetLastError();
     k_setup_fill<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->perm, pairs, rank, dgeom, q, gamma_in, ctx->rowQ,
-                                                  ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0]);
+                                                  ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0], sb.gg[1]);
     ++ctx->launches;
     k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
     ++ctx->launches;

@@ -233,7 +233,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->q64, mp * sizeof(double)) == cudaSuccess;
     // solver buffers, sized for float64; the float32 views alias the same memory
     // every slice starts on a 64-byte boundary (vector loads): 8 elements of slack each
-    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 4 * mp + 6 * np + 8 * 8;
+    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 12 * np + mp + 8 * 10;
     ok &= dmalloc((char**)&c->solve_ws, solve_elems * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->partials, (size_t)c->max_blocks * 4 * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->bstart, ((size_t)c->max_blocks + 1) * sizeof(int)) == cudaSuccess;
@@ -256,13 +256,15 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         size_t o = 0;
         auto carve64 = [&](size_t cnt) { double* r = base + o; o = (o + cnt + 7) & ~(size_t)7; return r; };
         SolveBufs<double>& s = c->sb64;
-        s.gg[0] = carve64(2 * mp); s.gg[1] = carve64(2 * mp); s.U = carve64(6 * np);
+        s.gg[0] = carve64(4 * mp); s.gg[1] = carve64(4 * mp); s.U = carve64(6 * np); s.Uref = carve64(6 * np);
+        s.gref = carve64(mp);
         s.rec = carve64(9 * mp); s.qe = carve64(8 * mp); s.q = carve64(mp); s.ax = carve64(3 * np);
         float* fb = (float*)c->solve_ws;
         size_t f = 0;
         auto carve32 = [&](size_t cnt) { float* r = fb + f; f = (f + cnt + 7) & ~(size_t)7; return r; };
         SolveBufs<float>& t = c->sb32;
-        t.gg[0] = carve32(2 * mp); t.gg[1] = carve32(2 * mp); t.U = carve32(6 * np);
+        t.gg[0] = carve32(4 * mp); t.gg[1] = carve32(4 * mp); t.U = carve32(6 * np); t.Uref = carve32(6 * np);
+        t.gref = carve32(mp);
         t.rec = carve32(9 * mp); t.qe = carve32(8 * mp); t.q = carve32(mp); t.ax = carve32(3 * np);
     }
     if (cudaMemsetAsync(c->cell_cursor, 0, ((size_t)c->max_keys + 1) * sizeof(int), c->stream) != cudaSuccess ||

@@ -164,8 +164,10 @@ struct SolveBufs {           // typed views into the solver workspace
     T* qe;                   // [6][mp]  per Q-side entry: e, y_Q x e (CSR order)
     T* q;                    // [mp]
     T* ax;                   // [3][np]
-    T* gg[2];                // [mp][2] x 2: (gamma, g) interleaved, ping-pong
-    T* U;                    // [np][6] constraint velocity M D gamma
+    T* gg[2];                // [mp][4] x 2: (delta, g, gamma_ref, 0), ping-pong
+    T* U;                    // [np][6] velocity increment M D delta
+    T* Uref;                 // [np][6] reference velocity M D gamma_ref
+    T* gref;                 // [mp] reference gradient q + D^T Uref
 };
 
 }  // namespace alens

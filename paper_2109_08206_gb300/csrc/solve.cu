@@ -49,10 +49,10 @@
 
 namespace alens {
 
-enum { A_RAW = 0, A_STEP = 1, A_PG = 2 };
 // CSR entries whose loads a thread issues together (float64 values need the
 // registers twice over)
-template <typename T> struct Batch { static constexpr int v = sizeof(T) == 4 ? 2 : 1; };
+template <typename T> struct Batch { static constexpr int v = 1; };
+constexpr int kRefresh = 32;   // float32 iterations between reference refreshes
 
 template <typename T> struct V2;
 template <> struct V2<float> { using t = float2; };
@@ -102,6 +102,64 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Constraint state (delta, g, gamma_ref, 0) of constraint c in a [m][4]
+// buffer: one vector load (float32) or two (float64).
+__device__ __forceinline__ void ld_state(const float* p, int c, float& d, float& g, float& gr)
+{
+    const float4 v = reinterpret_cast<const float4*>(p)[c];
+    d = v.x; g = v.y; gr = v.z;
+}
+__device__ __forceinline__ void ld_state(const double* p, int c, double& d, double& g, double& gr)
+{
+    const double2* q = reinterpret_cast<const double2*>(p) + 2 * (size_t)c;
+    const double2 a = q[0], b = q[1];
+    d = a.x; g = a.y; gr = b.x;
+}
+__device__ __forceinline__ void st_state(float* p, int c, float d, float g, float gr)
+{
+    reinterpret_cast<float4*>(p)[c] = make_float4(d, g, gr, 0.f);
+}
+__device__ __forceinline__ void st_state(double* p, int c, double d, double g, double gr)
+{
+    double2* q = reinterpret_cast<double2*>(p) + 2 * (size_t)c;
+    q[0] = make_double2(d, g);
+    q[1] = make_double2(gr, 0.0);
+}
+
+// Exact sum: a + b = s + e.
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e)
+{
+    s = a + b;
+    const T bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Sum-of-products accumulator.  COMP (float32 reference passes): an
+// unevaluated (hi, lo) pair fed by error-free transformations - the product
+// split through one FMA, the sum through TwoSum - so large contact forces
+// that cancel on a rod, or q and D^T U that cancel in a gradient entry, lose
+// no digits.  Otherwise a plain sum.
+template <typename T, bool COMP>
+struct Acc {
+    T hi, lo;
+    __device__ __forceinline__ void init(T v) { hi = v; lo = T(0); }
+    __device__ __forceinline__ void add_prod(T a, T b)
+    {
+        if (!COMP) {
+            hi += a * b;
+        } else {
+            const T p = a * b;
+            const T ep = fma(a, b, -p);
+            T sum, es;
+            two_sum(hi, p, sum, es);
+            hi = sum;
+            lo += es + ep;
+        }
+    }
+    __device__ __forceinline__ T value() const { return COMP ? hi + lo : hi; }
+};
+
 template <typename T>
 struct SolveArgs {
     int n, m, np, mp;
@@ -114,9 +172,11 @@ struct SolveArgs {
     const T* __restrict__ qe;
     const T* __restrict__ q;
     const T* __restrict__ ax;
-    T* gg0;     // written inside the kernel: plain (coherent) loads only
+    T* gg0;     // [m][4] (delta, g, gamma_ref, 0): written inside the kernel, plain (coherent) loads only
     T* gg1;
-    T* U;
+    T* U;       // [n][6] velocity increment M D delta
+    T* Uref;    // [n][6] reference velocity M D gamma_ref
+    T* gref;    // [m] reference gradient q + D^T Uref (blocks working from global memory)
     double* partials;
     unsigned* bar;
     int* flags;
@@ -124,6 +184,7 @@ struct SolveArgs {
     T inv_perp, inv_par, inv_rot, inv_spin;
     double hD, tol;
     int max_iter;
+    int refresh;   // fold delta into gamma_ref every this many iterations (0: never)
     long long wait_cycles;
     int fault;
     const int* __restrict__ bstart;   // [gridDim.x + 1] rod-rank boundaries of the blocks
@@ -135,23 +196,26 @@ template <typename T>
 struct Own {
     int r0, r1, c0, c1, q0, q1, cap_c, cap_r, cap_q;
     T* rec;      // [9][cap_c]
-    T* q;        // [cap_c]
-    T* gs[2];    // [cap_c] gamma, ping-pong
+    T* gref;     // [cap_c] q + D^T Uref
+    T* ds[2];    // [cap_c] delta, ping-pong
     T* grs;      // [cap_c] g (phase B updates it in place, one thread per entry)
+    T* gam;      // [cap_c] gamma_ref
     T* ax;       // [3][cap_r]
-    T* U;        // [6][cap_r]
+    T* U;        // [6][cap_r] delta velocity (the reference velocity during a refresh)
     int* cj;     // [cap_c] other end (rank)
-    int* ci;     // [cap_c] owner, local index
+    unsigned short* ci;   // [cap_c] owner, local index
     int* rowP;   // [cap_r + 1] owned ranges (global constraint ids)
     int* rowQ;   // [cap_r + 1] other-side ranges (global CSR positions)
     int* qlist;  // [cap_q] other-side constraint ids of the block's rods
 };
 
-template <typename T>
-__host__ __device__ inline size_t staged_bytes(int cap_c, int cap_r, int cap_q)
+// Shared-memory bytes of a block's share: per owned constraint 14 values
+// and 6 bytes of indices, per rod 9 values and two row pointers, per
+// other-side entry one id (owner indices are 16-bit: at most 65535 rods).
+__host__ __device__ inline size_t staged_bytes(int esize, size_t cap_c, size_t cap_r, size_t cap_q)
 {
-    return (13 * (size_t)cap_c + 9 * (size_t)cap_r) * sizeof(T) +
-           (2 * (size_t)cap_c + 2 * (size_t)cap_r + 2 + (size_t)cap_q) * sizeof(int);
+    return (14 * cap_c + 9 * cap_r) * (size_t)esize + (cap_c + 2 * cap_r + 2 + cap_q) * sizeof(int) +
+           ((cap_c * sizeof(unsigned short) + 3) & ~(size_t)3);
 }
 
 template <typename T>
@@ -160,18 +224,19 @@ __device__ void carve(Own<T>& o, unsigned char* base)
     T* t = reinterpret_cast<T*>(base);
     const size_t C = o.cap_c, R = o.cap_r;
     o.rec = t; t += 9 * C;
-    o.q = t; t += C;
-    o.gs[0] = t; t += C;
-    o.gs[1] = t; t += C;
+    o.gref = t; t += C;
+    o.ds[0] = t; t += C;
+    o.ds[1] = t; t += C;
     o.grs = t; t += C;
+    o.gam = t; t += C;
     o.ax = t; t += 3 * R;
     o.U = t; t += 6 * R;
     int* ip = reinterpret_cast<int*>(t);
     o.cj = ip; ip += C;
-    o.ci = ip; ip += C;
     o.rowP = ip; ip += R + 1;
     o.rowQ = ip; ip += R + 1;
-    o.qlist = ip;
+    o.qlist = ip; ip += o.cap_q;
+    o.ci = reinterpret_cast<unsigned short*>(ip);
 }
 
 template <typename T>
@@ -189,62 +254,72 @@ __device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
         const int c = o.c0 + lc;
 #pragma unroll
         for (int w = 0; w < 9; ++w) o.rec[w * o.cap_c + lc] = a.rec[w * mp + c];
-        o.q[lc] = a.q[c];
         o.cj[lc] = a.cj[c];
-        o.ci[lc] = a.ci[c] - o.r0;
-        o.gs[0][lc] = a.gg0[2 * (size_t)c];
+        o.ci[lc] = (unsigned short)(a.ci[c] - o.r0);
+        T d, g, gr;
+        ld_state(a.gg0, c, d, g, gr);
+        o.ds[0][lc] = d;
+        o.gam[lc] = gr;
         o.grs[lc] = T(0);
     }
     for (int k = threadIdx.x; k < o.q1 - o.q0; k += blockDim.x) o.qlist[k] = a.qlist[o.q0 + k];
     __syncthreads();
 }
 
+// Rod phase modes: A_STEP forms delta_{k+1} = max(-gamma_ref, delta - alpha g)
+// (the owner stores it) and stores dU = M D delta_{k+1}; A_PG sums pi.A.pi
+// for the projected gradient pi (returned, nothing stored); A_REF stores the
+// reference velocity Uref = M D gamma_ref with compensated sums.
+enum { A_STEP = 0, A_PG = 1, A_REF = 2 };
+// Constraint phase modes: B_STEP g_{k+1} = gref + D^T dU and the BB sums;
+// B_REF gref = q + D^T Uref (compensated); B_FIRST = B_REF, then g_0 = gref
+// and pi.pi, max |pi| at gamma_0.
+enum { B_STEP = 0, B_REF = 1, B_FIRST = 2 };
+
 template <int MODE, typename T>
-__device__ __forceinline__ T a_value(T g, T gr, T alpha)
+__device__ __forceinline__ T a_value(T d, T g, T gr, T alpha)
 {
-    if (MODE == A_RAW) return g;
+    if (MODE == A_REF) return gr;
     if (MODE == A_STEP) {
-        T v = g - alpha * gr;
-        return v > T(0) ? v : T(0);
+        const T v = d - alpha * g;
+        return v > -gr ? v : -gr;
     }
-    return g > T(0) ? gr : (gr < T(0) ? gr : T(0));
+    return d > -gr ? g : (g < T(0) ? g : T(0));   // projected gradient at gamma = gr + d
 }
 
-// Rod-parallel half of the gradient for the block's rods: F = D gamma' and
-// U = M F, gamma' per MODE (A_RAW: gamma itself; A_STEP: max(0, gamma -
-// alpha g), stored by the owner into buffer cur^1; A_PG: the projected
-// gradient, returning the thread's share of pi.A.pi = sum_rods F.M.F
-// instead of storing U).  (gamma_k, g_k) are in buffer cur.
 template <typename T, int MODE, bool ST>
 __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int cur, T alpha)
 {
+    constexpr bool COMP = MODE == A_REF && sizeof(T) == 4;
     T fmf = T(0);
     const size_t mp = a.mp, np = a.np;
     constexpr int B = Batch<T>::v;
     constexpr int BO = ST ? 1 : B;   // owned entries come from shared memory when staged
     const T* gc = cur ? a.gg1 : a.gg0;
     T* gn = cur ? a.gg0 : a.gg1;
-    const T* sgc = cur ? o.gs[1] : o.gs[0];      // shared copies (staged blocks)
-    const T* sgrc = o.grs;
-    T* sgn = cur ? o.gs[0] : o.gs[1];
+    const T* sdc = cur ? o.ds[1] : o.ds[0];      // shared copies (staged blocks)
+    T* sdn = cur ? o.ds[0] : o.ds[1];
     for (int i = o.r0 + threadIdx.x; i < o.r1; i += blockDim.x) {
         const int li = i - o.r0;
-        T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        Acc<T, COMP> Fa[6];
+#pragma unroll
+        for (int w = 0; w < 6; ++w) Fa[w].init(T(0));
         {   // owned constraints: loads of up to BO entries issued together
             const int b = ST ? o.rowP[li] : a.rowP[i], e = ST ? o.rowP[li + 1] : a.rowP[i + 1];
             for (int c = b; c < e; c += BO) {
-                T gv[BO], grv[BO], rv[BO][6];
+                T dv[BO], gv[BO], rv_[BO], rv[BO][6];
 #pragma unroll
                 for (int u = 0; u < BO; ++u) {
                     if (c + u < e) {
                         if (ST) {
                             const int lc = c + u - o.c0;
-                            gv[u] = sgc[lc];
-                            grv[u] = sgrc[lc];
+                            dv[u] = sdc[lc];
+                            gv[u] = o.grs[lc];
+                            rv_[u] = o.gam[lc];
 #pragma unroll
                             for (int w = 0; w < 6; ++w) rv[u][w] = o.rec[w * o.cap_c + lc];
                         } else {
-                            ld_pair(gc, c + u, gv[u], grv[u]);
+                            ld_state(gc, c + u, dv[u], gv[u], rv_[u]);
 #pragma unroll
                             for (int w = 0; w < 6; ++w) rv[u][w] = a.rec[w * mp + c + u];
                         }
@@ -253,55 +328,58 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
 #pragma unroll
                 for (int u = 0; u < BO; ++u) {
                     if (c + u < e) {
-                        T v = a_value<MODE, T>(gv[u], grv[u], alpha);
+                        const T v = a_value<MODE, T>(dv[u], gv[u], rv_[u], alpha);
                         if (MODE == A_STEP) {
-                            if (ST) sgn[c + u - o.c0] = v;       // global copy written in phase B
-                            else gn[2 * (size_t)(c + u)] = v;
+                            if (ST) sdn[c + u - o.c0] = v;       // global copy written in phase B
+                            else gn[4 * (size_t)(c + u)] = v;
                         }
 #pragma unroll
-                        for (int w = 0; w < 6; ++w) F[w] += v * rv[u][w];
+                        for (int w = 0; w < 6; ++w) Fa[w].add_prod(v, rv[u][w]);
                     }
                 }
             }
         }
-        {   // constraints owned by other rods: ids first, then (gamma, g) and arms
+        {   // constraints owned by other rods: ids first, then their state and arms
             // (from shared memory when the owner is one of the block's rods)
-            constexpr int BQ = B;
             const int b = ST ? o.rowQ[li] : a.rowQ[i], e = ST ? o.rowQ[li + 1] : a.rowQ[i + 1];
-            for (int k = b; k < e; k += BQ) {
-                int cid[BQ];
+            for (int k = b; k < e; k += B) {
+                int cid[B];
 #pragma unroll
-                for (int u = 0; u < BQ; ++u)
+                for (int u = 0; u < B; ++u)
                     cid[u] = k + u < e ? (ST ? o.qlist[k + u - o.q0] : __ldg(&a.qlist[k + u])) : -1;
-                T gv[BQ], grv[BQ], qv[BQ][6];
+                T dv[B], gv[B], rv_[B], qv[B][6];
 #pragma unroll
-                for (int u = 0; u < BQ; ++u) {
+                for (int u = 0; u < B; ++u) {
                     if (cid[u] >= 0) {
                         if (ST && cid[u] >= o.c0 && cid[u] < o.c1) {
                             const int lc = cid[u] - o.c0;
-                            gv[u] = sgc[lc];
-                            grv[u] = sgrc[lc];
+                            dv[u] = sdc[lc];
+                            gv[u] = o.grs[lc];
+                            rv_[u] = o.gam[lc];
 #pragma unroll
                             for (int w = 0; w < 3; ++w) {
                                 qv[u][w] = o.rec[w * o.cap_c + lc];
                                 qv[u][3 + w] = o.rec[(6 + w) * o.cap_c + lc];
                             }
                         } else {
-                            ld_pair(gc, cid[u], gv[u], grv[u]);
+                            ld_state(gc, cid[u], dv[u], gv[u], rv_[u]);
                             ld_arm(a.qe, k + u, qv[u]);
                         }
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < BQ; ++u) {
+                for (int u = 0; u < B; ++u) {
                     if (cid[u] >= 0) {
-                        T v = a_value<MODE, T>(gv[u], grv[u], alpha);
+                        const T v = a_value<MODE, T>(dv[u], gv[u], rv_[u], alpha);
 #pragma unroll
-                        for (int w = 0; w < 6; ++w) F[w] -= v * qv[u][w];
+                        for (int w = 0; w < 6; ++w) Fa[w].add_prod(-v, qv[u][w]);
                     }
                 }
             }
         }
+        T F[6];
+#pragma unroll
+        for (int w = 0; w < 6; ++w) F[w] = Fa[w].value();
         T p0, p1, p2;
         if (ST) {
             p0 = o.ax[li]; p1 = o.ax[o.cap_r + li]; p2 = o.ax[2 * o.cap_r + li];
@@ -317,7 +395,7 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
 #pragma unroll
             for (int w = 0; w < 6; ++w) fmf += F[w] * Uv[w];
         } else {
-            st_u6(a.U, i, Uv);
+            st_u6(MODE == A_REF ? a.Uref : a.U, i, Uv);
             if (ST) {
 #pragma unroll
                 for (int w = 0; w < 6; ++w) o.U[w * o.cap_r + li] = Uv[w];
@@ -327,23 +405,23 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
     return fmf;
 }
 
-// Constraint-parallel half for the block's owned constraints: g_new = q +
-// D^T U into buffer nx (its y slot; gamma_new is its x slot), plus the
-// thread's partial sums.  FIRST: nx = cur = 0 and acc0 = pi.pi; otherwise
-// acc0..2 = s.s, s.y, y.y against buffer cur; acc3 = max |pi|.
-template <typename T, bool FIRST, bool ST>
+// Constraint phase for the block's owned constraints (modes above).  In
+// B_STEP the new state (delta_{k+1}, g_{k+1}, gamma_ref) goes to buffer nx,
+// and acc0..2 = s.s, s.y, y.y against buffer cur; acc3 = max |pi|.
+template <typename T, int MODE, bool ST>
 __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, int cur, int nx, T acc[4])
 {
+    constexpr bool COMP = MODE != B_STEP && sizeof(T) == 4;
     const size_t mp = a.mp;
     T* gnew = nx ? a.gg1 : a.gg0;
     const T* gold = cur ? a.gg1 : a.gg0;
-    const T* sgnew = nx ? o.gs[1] : o.gs[0];     // shared copies (staged blocks)
-    T* sgr = o.grs;                              // g_k in, g_{k+1} out (same thread)
-    const T* sgold = cur ? o.gs[1] : o.gs[0];
+    const T* sdnew = nx ? o.ds[1] : o.ds[0];     // shared copies (staged blocks)
+    const T* sdold = cur ? o.ds[1] : o.ds[0];
+    const T* Uu = MODE == B_STEP ? a.U : a.Uref;
     const int nc = o.c1 - o.c0;
     for (int lc = threadIdx.x; lc < nc; lc += blockDim.x) {
         const int c = o.c0 + lc;
-        T Ui[6], Uj[6], r[9], qq, gm, go = T(0), gro = T(0);
+        T Ui[6], Uj[6], r[9], base, dm, gam, dold = T(0), gro = T(0);
         if (ST) {
             const int il = o.ci[lc], j = o.cj[lc];
 #pragma unroll
@@ -352,54 +430,95 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
 #pragma unroll
                 for (int w = 0; w < 6; ++w) Uj[w] = o.U[w * o.cap_r + (j - o.r0)];
             } else {
-                ld_u6(a.U, j, Uj);
+                ld_u6(Uu, j, Uj);
             }
 #pragma unroll
             for (int w = 0; w < 9; ++w) r[w] = o.rec[w * o.cap_c + lc];
-            qq = o.q[lc];
-            gm = sgnew[lc];
-            if (!FIRST) {
-                go = sgold[lc];
-                gro = sgr[lc];
+            base = MODE == B_STEP ? o.gref[lc] : a.q[c];
+            dm = sdnew[lc];
+            gam = o.gam[lc];
+            if (MODE == B_STEP) {
+                dold = sdold[lc];
+                gro = o.grs[lc];
             }
         } else {
-            ld_u6(a.U, a.ci[c], Ui);
-            ld_u6(a.U, a.cj[c], Uj);
+            ld_u6(Uu, a.ci[c], Ui);
+            ld_u6(Uu, a.cj[c], Uj);
 #pragma unroll
             for (int w = 0; w < 9; ++w) r[w] = a.rec[w * mp + c];
-            qq = a.q[c];
-            gm = gnew[2 * (size_t)c];
-            if (!FIRST) ld_pair(gold, c, go, gro);
+            base = MODE == B_STEP ? a.gref[c] : a.q[c];
+            T gdummy;
+            ld_state(gnew, c, dm, gdummy, gam);
+            if (MODE == B_STEP) {
+                T g2;
+                ld_state(gold, c, dold, gro, g2);
+            }
         }
-        T du = T(0);
+        Acc<T, COMP> du;
+        du.init(base);
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
-            du += r[u] * (Ui[u] - Uj[u]);
-            du += r[3 + u] * Ui[3 + u];
-            du -= r[6 + u] * Uj[3 + u];
+            du.add_prod(r[u], Ui[u]);
+            du.add_prod(-r[u], Uj[u]);
+            du.add_prod(r[3 + u], Ui[3 + u]);
+            du.add_prod(-r[6 + u], Uj[3 + u]);
         }
-        const T gr = qq + du;
+        const T gr = du.value();
+        if (MODE == B_REF) {
+            if (ST) o.gref[lc] = gr;
+            else a.gref[c] = gr;
+            continue;
+        }
+        if (MODE == B_FIRST) {
+            if (ST) o.gref[lc] = gr;
+            else a.gref[c] = gr;
+        }
+        // g of the new iterate (for B_FIRST: gamma_0 with g_0 = gref)
         if (ST) {
-            sgr[lc] = gr;
-            // the pair other blocks read in the next phase A
-            typename V2<T>::t pr;
-            pr.x = gm;
-            pr.y = gr;
-            reinterpret_cast<typename V2<T>::t*>(gnew)[c] = pr;
+            o.grs[lc] = gr;
+            st_state(gnew, c, dm, gr, gam);    // the state other blocks read in the next phase A
         } else {
-            gnew[2 * (size_t)c + 1] = gr;
+            gnew[4 * (size_t)c + 1] = gr;
         }
-        T pi = gm > T(0) ? gr : (gr < T(0) ? gr : T(0));
-        T api = pi < T(0) ? -pi : pi;
+        const T pi = dm > -gam ? gr : (gr < T(0) ? gr : T(0));
+        const T api = pi < T(0) ? -pi : pi;
         acc[3] = api > acc[3] ? api : acc[3];
-        if (FIRST) {
+        if (MODE == B_FIRST) {
             acc[0] += pi * pi;
         } else {
-            const T sv = gm - go, yv = gr - gro;
+            const T sv = dm - dold, yv = gr - gro;
             acc[0] += sv * sv;
             acc[1] += sv * yv;
             acc[2] += yv * yv;
         }
+    }
+}
+
+// Refresh: gamma_ref absorbs delta (TwoSum: the new delta is the exact
+// remainder), in shared memory and in both global state buffers.
+template <typename T, bool ST>
+__device__ __forceinline__ void fold_delta(const SolveArgs<T>& a, const Own<T>& o, int cur)
+{
+    T* gc = cur ? a.gg1 : a.gg0;
+    T* go = cur ? a.gg0 : a.gg1;
+    T* sdc = cur ? o.ds[1] : o.ds[0];
+    const int nc = o.c1 - o.c0;
+    for (int lc = threadIdx.x; lc < nc; lc += blockDim.x) {
+        const int c = o.c0 + lc;
+        T d, g, gr;
+        if (ST) {
+            d = sdc[lc]; g = o.grs[lc]; gr = o.gam[lc];
+        } else {
+            ld_state(gc, c, d, g, gr);
+        }
+        T ns, rem;
+        two_sum(gr, d, ns, rem);
+        if (ST) {
+            sdc[lc] = rem;
+            o.gam[lc] = ns;
+        }
+        st_state(gc, c, rem, g, ns);
+        go[4 * (size_t)c + 2] = ns;
     }
 }
 
@@ -559,12 +678,12 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
     StepState st;   // meaningful in thread 0 only
     st.alpha0 = 1.0;
 
-    // U = M D gamma_0
-    phase_a<T, A_RAW, ST>(a, o, 0, T(0));
+    // gamma_0 is the reference (delta = 0): Uref = M D gamma_0, then
+    // gref = q + D^T Uref = g_0 and the projected gradient at gamma_0
+    phase_a<T, A_REF, ST>(a, o, 0, T(0));
     if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
-    // g_0 and the projected gradient at gamma_0
     v[0] = v[1] = v[2] = v[3] = T(0);
-    phase_b<T, true, ST>(a, o, 0, 0, v);
+    phase_b<T, B_FIRST, ST>(a, o, 0, 0, v);
     block_partial(v, sh.red, mine);
     if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
     grid_total(a.partials, nb, sh.bc, tot);
@@ -600,7 +719,7 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
             phase_a<T, A_STEP, ST>(a, o, cur, sh.alpha);
             if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
             v[0] = v[1] = v[2] = v[3] = T(0);
-            phase_b<T, false, ST>(a, o, cur, nx, v);
+            phase_b<T, B_STEP, ST>(a, o, cur, nx, v);
             block_partial(v, sh.red, mine);
             if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
             grid_total(a.partials, nb, sh.bc, tot);
@@ -621,6 +740,16 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
             }
             __syncthreads();
             if (sh.done) break;
+            if (a.refresh > 0 && (k + 1) % a.refresh == 0) {
+                // gamma_ref absorbs delta; Uref and gref are recomputed with
+                // compensated sums (g itself is unchanged: same gamma)
+                fold_delta<T, ST>(a, o, cur);
+                if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+                phase_a<T, A_REF, ST>(a, o, cur, T(0));
+                if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+                phase_b<T, B_REF, ST>(a, o, cur, cur, v);
+                __syncthreads();
+            }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -650,7 +779,7 @@ __global__ void k_stage_need(int nb, int esize, const int* __restrict__ bstart, 
     if (b >= nb) return;
     const int r0 = bstart[b], r1 = bstart[b + 1];
     const size_t nc = rowP[r1] - rowP[r0], nq = rowQ[r1] - rowQ[r0], nr = r1 - r0;
-    const size_t bytes = (13 * nc + 9 * nr) * (size_t)esize + (2 * nc + 2 * nr + 2 + nq) * sizeof(int);
+    const size_t bytes = staged_bytes(esize, nc, nr, nq);
     atomicMax(need, (unsigned long long)bytes);
 }
 
@@ -687,7 +816,7 @@ __global__ void k_gamma_out(int m, const int* __restrict__ flags, const int* __r
     if (c >= m) return;
     if (flags[F_SOLVE_ERR] != 0) return;
     const T* g = flags[F_FINAL] == 0 ? gg0 : gg1;
-    out[perm[c]] = (double)g[2 * (size_t)c];
+    out[perm[c]] = (double)g[4 * (size_t)c + 2] + (double)g[4 * (size_t)c];   // gamma_ref + delta
 }
 
 __global__ void k_rank(int n, const int* __restrict__ sorted_id, int* __restrict__ rank)
@@ -711,7 +840,10 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     a.n = n; a.m = m; a.np = (int)ctx->max_rods; a.mp = (int)ctx->max_pairs;
     a.rowP = ctx->rowP; a.rowQ = ctx->rowQ; a.qlist = ctx->qlist; a.ci = ctx->ci; a.cj = ctx->cj;
     a.rec = sb.rec; a.qe = sb.qe; a.q = sb.q; a.ax = sb.ax;
-    a.gg0 = sb.gg[0]; a.gg1 = sb.gg[1]; a.U = sb.U;
+    a.gg0 = sb.gg[0]; a.gg1 = sb.gg[1]; a.U = sb.U; a.Uref = sb.Uref; a.gref = sb.gref;
+    // float32 iterations work on increments over a reference that absorbs
+    // them every kRefresh iterations; float64 needs no refresh
+    a.refresh = sizeof(T) == 4 ? kRefresh : 0;
     a.partials = ctx->partials; a.bar = ctx->bar; a.flags = ctx->dflags;
     a.out = reinterpret_cast<double*>(ctx->dcount + C_RESID);
     a.inv_perp = (T)ctx->mob.inv_perp; a.inv_par = (T)ctx->mob.inv_par;
@@ -748,7 +880,7 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device)) != cudaSuccess)
         return e;
     const long long budget = (long long)optin / bps - (long long)sizeof(Shared<T>) - 1024;
-    const bool staged = (long long)need <= budget;
+    const bool staged = (long long)need <= budget && (long long)n / blocks < 60000;
     const size_t smem = staged ? (size_t)need : 0;
     const void* fn = staged ? (const void*)k_bbpgd<T, true> : (const void*)k_bbpgd<T, false>;
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
