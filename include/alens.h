@@ -160,6 +160,44 @@ ALENS_API aLENS_status aLENS_solve_lcp(aLENS_ctx* ctx, int64_t n, const double* 
 ALENS_API aLENS_status aLENS_step(aLENS_ctx* ctx, int64_t n, double* x, double* quat, const double* f_nc,
                         int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info);
 
+/* ------------------------------------------------------------------------
+ * Batched step of independent periodic systems.  The paper steps one system
+ * (distributed over many processes); an ensemble of many small, uneven
+ * systems is stepped here in one call, each system with the step of
+ * aLENS_step (Appendix Eq. blockdef A, Eq. suppcqpdef, Eq.
+ * constrainedeom_euler a-c).
+ *
+ * systems    [n_systems] HOST array: periodic box and cylinder length of each
+ *            system; each box edge >= length + diameter + delta_c.  Diameter,
+ *            viscosity, dt, delta_c, tol, max_iter and precision are the
+ *            context's parameters, shared by every system.
+ * rod_offset [n_systems + 1] HOST array: system s owns rods
+ *            [rod_offset[s], rod_offset[s+1]) of x, quat, f_nc and vel_out;
+ *            rod_offset[0] = 0, non-decreasing, last entry = the rod count
+ *            (<= max_rods of the context).  Empty systems are allowed.
+ * x, quat, f_nc, pairs_out, gamma_out, vel_out, info: as for aLENS_step,
+ *            over all rods of the batch with global rod indices.  No pair
+ *            joins two systems, so each system's pairs form one contiguous
+ *            run of pairs_out (they are sorted by i).
+ *
+ * The systems' constraint problems are solved together by one BBPGD run on
+ * their block-diagonal union: its residual is the largest of the systems'
+ * residuals, so the tolerance holds for every system.  info aggregates the
+ * batch (pair, overlap and launch counts summed; iterations, residual and
+ * minimum gap over the union).  The first call with more systems or cell
+ * keys than any call before grows the context's tables (this allocates and
+ * synchronises); later calls with the same systems reuse the uploaded tables.
+ * Errors as for aLENS_step; INVALID also for a bad table or a system whose
+ * cell grid would exceed 2^7 cells along an edge. */
+typedef struct {
+    double box[3];    /* periodic edge lengths of the system */
+    double length;    /* cylinder length L of its rods */
+} aLENS_system;
+
+ALENS_API aLENS_status aLENS_step_batch(aLENS_ctx* ctx, int32_t n_systems, const aLENS_system* systems,
+                                        const int64_t* rod_offset, double* x, double* quat, const double* f_nc,
+                                        int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info);
+
 /* Bound on every grid-wide wait inside the solver kernel, in seconds
  * (default 5).  A wait that runs out makes the call return ALENS_ERR_TIMEOUT. */
 ALENS_API aLENS_status aLENS_set_wait_limit(aLENS_ctx* ctx, double seconds);

@@ -14,7 +14,7 @@ from __future__ import annotations
 import ctypes as C
 from pathlib import Path
 
-__all__ = ["build", "lib", "Params", "Info", "Context", "AlensError", "FP64", "MIXED", "STATUS"]
+__all__ = ["build", "lib", "Params", "Info", "System", "Context", "AlensError", "FP64", "MIXED", "STATUS"]
 
 _PKG = Path(__file__).resolve().parent
 _LIB_PATH = _PKG / "_build" / "libalens.so"
@@ -42,11 +42,19 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class System(C.Structure):
+    """aLENS_system (include/alens.h): one system of a batch."""
+    _fields_ = [("box", C.c_double * 3), ("length", C.c_double)]
+
+
 class AlensError(RuntimeError):
     def __init__(self, status: int, where: str, extra=None):
         self.status = status
         self.extra = extra
-        super().__init__(f"{where}: {STATUS.get(status, status)} ({_status_string(status)})")
+        msg = f"{where}: {STATUS.get(status, status)} ({_status_string(status)})"
+        if isinstance(extra, dict) and "iters" in extra:
+            msg += f" iters={extra['iters']} residual={extra['residual']:.3e} n_pairs={extra['n_pairs']}"
+        super().__init__(msg)
 
 
 def build(force: bool = False, verbose: bool = False) -> Path:
@@ -76,6 +84,7 @@ def lib():
             "aLENS_assemble_constraints": (i32, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp]),
             "aLENS_solve_lcp": (i32, [vp, i64, vp, i64, vp, vp, vp, vp, IP]),
             "aLENS_step": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, IP]),
+            "aLENS_step_batch": (i32, [vp, i32, C.POINTER(System), C.POINTER(i64), vp, vp, vp, vp, vp, vp, IP]),
             "aLENS_set_wait_limit": (i32, [vp, d]),
             "aLENS_inject_fault": (i32, [vp, i32]),
             "aLENS_set_launch": (i32, [vp, i32, i32]),
@@ -240,4 +249,28 @@ class Context:
                                   _ptr(gamma_out, torch.float64), _ptr(vel_out, torch.float64, (6,)), C.byref(info))
         if check and st != 0:
             raise AlensError(st, "aLENS_step", info.as_dict())
+        return info
+
+    def step_batch(self, systems, rod_offset, x, quat, f_nc, pairs_out=None, gamma_out=None, vel_out=None,
+                   check=True):
+        """One constrained step of a batch of independent systems, in place on x, quat.
+
+        ``systems``: sequence of (box, length) with box a 3-sequence or a scalar;
+        ``rod_offset``: n_systems + 1 integers, system s owning rods
+        [rod_offset[s], rod_offset[s+1]).  Returns Info (aggregated over the batch).
+        """
+        import torch
+        ns = len(systems)
+        tab = (System * ns)()
+        for s, (box, length) in enumerate(systems):
+            b = box if hasattr(box, "__len__") else (box, box, box)
+            tab[s] = System((C.c_double * 3)(*[float(v) for v in b]), float(length))
+        off = (C.c_int64 * (ns + 1))(*[int(v) for v in rod_offset])
+        info = Info()
+        st = self._lib.aLENS_step_batch(self._h, ns, tab, off, _ptr(x, torch.float64, (3,)),
+                                        _ptr(quat, torch.float64, (4,)), _ptr(f_nc, torch.float64, (6,)),
+                                        _ptr(pairs_out, torch.int32, (3,)), _ptr(gamma_out, torch.float64),
+                                        _ptr(vel_out, torch.float64, (6,)), C.byref(info))
+        if check and st != 0:
+            raise AlensError(st, "aLENS_step_batch", info.as_dict())
         return info

@@ -27,7 +27,8 @@ __device__ __forceinline__ long long gap_key(double v)
     return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
 }
 
-__global__ void k_assemble(int m, int n, int np, Geo g, const int32_t* __restrict__ pairs,
+__global__ void k_assemble(int m, int n, int np, Geo g0, const SysGeo* __restrict__ systab,
+                           const int* __restrict__ sysid, const int32_t* __restrict__ pairs,
                            const double* __restrict__ xw, const double* __restrict__ axis,
                            const double* __restrict__ unc, double* __restrict__ phi, double* __restrict__ dgeom,
                            double* __restrict__ q, unsigned long long* __restrict__ counters, int* __restrict__ flags)
@@ -41,7 +42,11 @@ __global__ void k_assemble(int m, int n, int np, Geo g, const int32_t* __restric
         if (!(i >= 0 && i < j && j < n && code >= 0 && code < 27)) {
             if (atomicCAS(&flags[F_ERR], 0, ALENS_ERR_INVALID) == 0) flags[F_ERR_ROD] = c;
             active = false;
+        } else if (systab && sysid[i] != sysid[j]) {   // a batch pair must stay inside one system
+            if (atomicCAS(&flags[F_ERR], 0, ALENS_ERR_INVALID) == 0) flags[F_ERR_ROD] = c;
+            active = false;
         } else {
+            const Geo& g = geo_of(g0, systab, sysid, i);
             int kk[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
             double dx[3], p[3], qv[3];
 #pragma unroll
@@ -190,7 +195,7 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
                              const double* __restrict__ q64, const double* __restrict__ gin,
                              const int* __restrict__ rowQ, int* __restrict__ curQ, int* __restrict__ qlist,
                              int* __restrict__ ci, int* __restrict__ cj, T* __restrict__ rec, T* __restrict__ qT,
-                             T* __restrict__ gg0, T* __restrict__ gg1)
+                             T* __restrict__ gg0, T* __restrict__ gg1, T* __restrict__ rec_lo, T* __restrict__ q_lo)
 {
     int cc = blockIdx.x * blockDim.x + threadIdx.x;
     if (cc >= m) return;
@@ -201,27 +206,39 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
     ci[cc] = ro;
     cj[cc] = rq;
     const double* dg = dgeom + 9 * (size_t)c;
+    double r[9];
     if (!flip) {
 #pragma unroll
-        for (int u = 0; u < 9; ++u) rec[u * (size_t)mp + cc] = (T)dg[u];
+        for (int u = 0; u < 9; ++u) r[u] = dg[u];
     } else {
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
-            rec[u * (size_t)mp + cc] = (T)(-dg[u]);
-            rec[(3 + u) * (size_t)mp + cc] = (T)(-dg[6 + u]);
-            rec[(6 + u) * (size_t)mp + cc] = (T)(-dg[3 + u]);
+            r[u] = -dg[u];
+            r[3 + u] = -dg[6 + u];
+            r[6 + u] = -dg[3 + u];
         }
     }
-    qT[cc] = (T)q64[c];
+#pragma unroll
+    for (int u = 0; u < 9; ++u) {
+        const T hi = (T)r[u];
+        rec[u * (size_t)mp + cc] = hi;
+        if (rec_lo) rec_lo[u * (size_t)mp + cc] = (T)(r[u] - (double)hi);   // float32: the rounding error
+    }
+    const T qh = (T)q64[c];
+    qT[cc] = qh;
+    if (q_lo) q_lo[cc] = (T)(q64[c] - (double)qh);
     double v = gin ? gin[c] : 0.0;
-    // solver state (delta, g, gamma_ref, 0) in both buffers: gamma_0 is the
+    if (!(v > 0.0)) v = 0.0;
+    // solver state (delta, g, gamma_ref, gamma_lo) in both buffers: gamma_0
+    // (split into a working-precision value and its rounding error) is the
     // first reference
+    const T vh = (T)v;
     for (int b = 0; b < 2; ++b) {
         T* st = (b ? gg1 : gg0) + 4 * (size_t)cc;
         st[0] = T(0);
         st[1] = T(0);
-        st[2] = v > 0.0 ? (T)v : T(0);
-        st[3] = T(0);
+        st[2] = vh;
+        st[3] = (T)(v - (double)vh);
     }
     qlist[rowQ[rq] + atomicAdd(&curQ[rq], 1)] = cc;
 }
@@ -230,7 +247,7 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
 // two pad values) so that the solver's gather is one or two vector loads.
 template <typename T>
 __global__ void k_setup_qe(int m, int mp, const int* __restrict__ qlist, const T* __restrict__ rec,
-                           T* __restrict__ qe)
+                           T* __restrict__ qe, const T* __restrict__ rec_lo, T* __restrict__ qe_lo)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m) return;
@@ -243,11 +260,22 @@ __global__ void k_setup_qe(int m, int mp, const int* __restrict__ qlist, const T
     }
     o[6] = T(0);
     o[7] = T(0);
+    if (rec_lo) {
+        T* l = qe_lo + 8 * (size_t)k;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            l[u] = rec_lo[u * (size_t)mp + c];
+            l[3 + u] = rec_lo[(6 + u) * (size_t)mp + c];
+        }
+        l[6] = T(0);
+        l[7] = T(0);
+    }
 }
 
 template <typename T>
 __global__ void k_setup_rods(int n, int np, const double* __restrict__ quat, const int* __restrict__ rank,
-                             T* __restrict__ ax)
+                             const SysGeo* __restrict__ systab, const int* __restrict__ sysid, T* __restrict__ ax,
+                             T* __restrict__ mobr)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -258,6 +286,13 @@ __global__ void k_setup_rods(int n, int np, const double* __restrict__ quat, con
     ax[r] = (T)p0;
     ax[np + r] = (T)p1;
     ax[2 * (size_t)np + r] = (T)p2;
+    if (systab) {   // batches: the drags of the rod's system
+        const Mob& mb = systab[sysid[i]].mob;
+        mobr[r] = (T)mb.inv_perp;
+        mobr[np + r] = (T)mb.inv_par;
+        mobr[2 * (size_t)np + r] = (T)mb.inv_rot;
+        mobr[3 * (size_t)np + r] = (T)mb.inv_spin;
+    }
 }
 
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
@@ -265,8 +300,9 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t > 0 ? 
 cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, double* phi, double* dgeom, double* q)
 {
     if (m <= 0) return cudaSuccess;
-    k_assemble<<<nblk(m, 256), 256, 0, ctx->stream>>>(m, n, (int)ctx->max_rods, ctx->geo, pairs, ctx->xw, ctx->axis,
-                                                      ctx->unc, phi, dgeom, q, ctx->dcount, ctx->dflags);
+    k_assemble<<<nblk(m, 256), 256, 0, ctx->stream>>>(m, n, (int)ctx->max_rods, ctx->geo, ctx->cur_systab,
+                                                      ctx->cur_sysid, pairs, ctx->xw, ctx->axis, ctx->unc, phi, dgeom, q,
+                                                      ctx->dcount, ctx->dflags);
     ++ctx->launches;
     return cudaGetLastError();
 }
@@ -279,16 +315,18 @@ static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     int mp = (int)ctx->max_pairs, np = (int)ctx->max_rods;
     cudaStream_t st = ctx->stream;
     if (n > 0) {
-        k_setup_rods<T><<<nblk(n, 256), 256, 0, st>>>(n, np, quat, rank, sb.ax);
+        k_setup_rods<T><<<nblk(n, 256), 256, 0, st>>>(n, np, quat, rank, ctx->cur_systab, ctx->cur_sysid, sb.ax,
+                                                       sb.mobr);
         ++ctx->launches;
     }
     if (m <= 0) return cudaGetLastError();
     k_setup_fill<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->perm, pairs, rank, dgeom, q, gamma_in, ctx->rowQ,
-                                                  ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0], sb.gg[1]);
+                                                  ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0], sb.gg[1],
+                                                  sb.rec_lo, sb.q_lo);
     ++ctx->launches;
     k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
     ++ctx->launches;
-    k_setup_qe<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->qlist, sb.rec, sb.qe);
+    k_setup_qe<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->qlist, sb.rec, sb.qe, sb.rec_lo, sb.qe_lo);
     ++ctx->launches;
     return cudaGetLastError();
 }

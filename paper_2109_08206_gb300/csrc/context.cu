@@ -85,9 +85,12 @@ void free_all(aLENS_ctx* c)
     void* ptrs[] = {c->xw, c->axis, c->unc, c->pos32, c->ax32, c->cellkey, c->sorted_id, c->spos32, c->sax32,
                     c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand, c->keep,
                     c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->perm, c->rank, c->curP, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
-                    c->q64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp};
+                    c->q64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp,
+                    c->systab, c->sysid, c->sysoff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    free(c->batch_host);
+    free(c->batch_off_host);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->hcount) cudaFreeHost(c->hcount);
     for (int k = 0; k < 8; ++k)
@@ -134,6 +137,139 @@ float elapsed(cudaEvent_t a, cudaEvent_t b)
 }
 
 bool rods_ok(aLENS_ctx* c, int64_t n) { return c && n >= 0 && n <= c->max_rods; }
+
+// Every entry point but aLENS_step_batch works on the one system of the
+// context's parameters.
+void single_mode(aLENS_ctx* c)
+{
+    c->cur_systab = nullptr;
+    c->cur_sysid = nullptr;
+    c->cur_nkeys = 1 << (3 * c->geo.bits);
+}
+
+// sysid[i] = the system whose rod range [off[s], off[s+1]) holds rod i.
+__global__ void k_fill_sysid(int n, int ns, const long long* __restrict__ off, int* __restrict__ sysid)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = ns - 1;   // last s with off[s] <= i
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    sysid[i] = lo;
+}
+
+// Grows the cell arrays to hold nkeys cell keys (contents are reset by every search).
+aLENS_status grow_keys(aLENS_ctx* c, long long nkeys)
+{
+    if (nkeys <= c->max_keys) return ALENS_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    int* na[3] = {nullptr, nullptr, nullptr};
+    int* nscan = nullptr;
+    int tiles = (int)((std::max((long long)c->max_rods, nkeys) + 4095) / 4096) + 2;
+    bool ok = true;
+    for (int k = 0; k < 3; ++k) ok &= dmalloc(&na[k], ((size_t)nkeys + 1) * sizeof(int)) == cudaSuccess;
+    if (tiles > c->scan_tmp_len) ok &= dmalloc(&nscan, (size_t)tiles * sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        for (int k = 0; k < 3; ++k) if (na[k]) cudaFree(na[k]);
+        if (nscan) cudaFree(nscan);
+        return ALENS_ERR_NOMEM;
+    }
+    cudaFree(c->cell_count); cudaFree(c->cell_start); cudaFree(c->cell_cursor);
+    c->cell_count = na[0]; c->cell_start = na[1]; c->cell_cursor = na[2];
+    if (nscan) { cudaFree(c->scan_tmp); c->scan_tmp = nscan; c->scan_tmp_len = tiles; }
+    c->max_keys = (int)nkeys;
+    return ALENS_OK;
+}
+
+// Validates the batch description and puts its tables on the device:
+// per-system geometry (cell keys offset so that the systems' key ranges are
+// disjoint and in system order) and the system id of every rod.
+aLENS_status batch_tables(aLENS_ctx* c, int ns, const aLENS_system* sys, const int64_t* off)
+{
+    if (ns < 1 || ns > (1 << 20) || !sys || !off || off[0] != 0) return ALENS_ERR_INVALID;
+    for (int s = 0; s < ns; ++s)
+        if (off[s + 1] < off[s]) return ALENS_ERR_INVALID;
+    if (off[ns] > c->max_rods) return ALENS_ERR_INVALID;
+    const bool same = c->batch_n == ns && c->batch_host && c->batch_off_host &&
+                      memcmp(c->batch_host, sys, sizeof(aLENS_system) * ns) == 0 &&
+                      memcmp(c->batch_off_host, off, sizeof(int64_t) * (ns + 1)) == 0;
+    if (same) {
+        c->cur_nkeys = c->batch_keys;
+        return ALENS_OK;
+    }
+    SysGeo* tab = (SysGeo*)calloc((size_t)ns, sizeof(SysGeo));
+    long long* loff = (long long*)malloc(sizeof(long long) * (ns + 1));
+    if (!tab || !loff) { free(tab); free(loff); return ALENS_ERR_NOMEM; }
+    long long keys = 0;
+    aLENS_status st = ALENS_OK;
+    for (int s = 0; s < ns && st == ALENS_OK; ++s) {
+        aLENS_params p = c->p;
+        for (int k = 0; k < 3; ++k) p.box[k] = sys[s].box[k];
+        p.length = sys[s].length;
+        int bits;
+        if (!params_ok(&p) || (bits = make_geo(&p, &tab[s].g, &tab[s].mob)) < 0) { st = ALENS_ERR_INVALID; break; }
+        tab[s].key_base = (int)keys;
+        keys += 1ll << (3 * bits);
+        if (keys > (1ll << 30)) st = ALENS_ERR_INVALID;
+    }
+    for (int s = 0; s <= ns; ++s) loff[s] = (long long)off[s];
+    if (st == ALENS_OK) st = grow_keys(c, keys);
+    if (st == ALENS_OK && ns > c->max_systems) {
+        cudaStreamSynchronize(c->stream);
+        if (c->systab) cudaFree(c->systab);
+        if (c->sysoff) cudaFree(c->sysoff);
+        c->systab = nullptr; c->sysoff = nullptr; c->max_systems = 0;
+        if (dmalloc(&c->systab, sizeof(SysGeo) * ns) != cudaSuccess ||
+            dmalloc(&c->sysoff, sizeof(long long) * (ns + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            st = ALENS_ERR_NOMEM;
+        } else {
+            c->max_systems = ns;
+        }
+    }
+    if (st == ALENS_OK && !c->sysid && dmalloc(&c->sysid, sizeof(int) * (size_t)c->max_rods) != cudaSuccess) {
+        cudaGetLastError();
+        st = ALENS_ERR_NOMEM;
+    }
+    void* hs = nullptr;
+    int64_t* ho = nullptr;
+    if (st == ALENS_OK) {
+        hs = malloc(sizeof(aLENS_system) * ns);
+        ho = (int64_t*)malloc(sizeof(int64_t) * (ns + 1));
+        if (!hs || !ho) st = ALENS_ERR_NOMEM;
+    }
+    if (st == ALENS_OK) {
+        // pageable sources: the calls return once the data is staged
+        if (cudaMemcpyAsync(c->systab, tab, sizeof(SysGeo) * ns, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(c->sysoff, loff, sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess)
+            st = ALENS_ERR_CUDA;
+    }
+    if (st == ALENS_OK && off[ns] > 0) {
+        int n = (int)off[ns];
+        k_fill_sysid<<<(n + 255) / 256, 256, 0, c->stream>>>(n, ns, c->sysoff, c->sysid);
+        ++c->launches;
+        if (cudaGetLastError() != cudaSuccess) st = ALENS_ERR_CUDA;
+    }
+    free(tab);
+    free(loff);
+    if (st != ALENS_OK) {
+        free(hs); free(ho);
+        c->batch_n = 0;   // the device tables may be stale
+        return st;
+    }
+    memcpy(hs, sys, sizeof(aLENS_system) * ns);
+    memcpy(ho, off, sizeof(int64_t) * (ns + 1));
+    free(c->batch_host); free(c->batch_off_host);
+    c->batch_host = hs; c->batch_off_host = ho;
+    c->batch_n = ns;
+    c->batch_keys = (int)keys;
+    c->cur_nkeys = (int)keys;
+    return ALENS_OK;
+}
 
 // Runs the solver on the layout already set up; fills info.
 aLENS_status run_solver(aLENS_ctx* c, int n, int m, aLENS_info* info, cudaEvent_t e0, cudaEvent_t e1)
@@ -233,7 +369,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->q64, mp * sizeof(double)) == cudaSuccess;
     // solver buffers, sized for float64; the float32 views alias the same memory
     // every slice starts on a 64-byte boundary (vector loads): 8 elements of slack each
-    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 12 * np + mp + 8 * 10;
+    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 12 * np + mp + 4 * np + 8 * 11;
     ok &= dmalloc((char**)&c->solve_ws, solve_elems * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->partials, (size_t)c->max_blocks * 4 * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->bstart, ((size_t)c->max_blocks + 1) * sizeof(int)) == cudaSuccess;
@@ -259,6 +395,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         s.gg[0] = carve64(4 * mp); s.gg[1] = carve64(4 * mp); s.U = carve64(6 * np); s.Uref = carve64(6 * np);
         s.gref = carve64(mp);
         s.rec = carve64(9 * mp); s.qe = carve64(8 * mp); s.q = carve64(mp); s.ax = carve64(3 * np);
+        s.mobr = carve64(4 * np);
         float* fb = (float*)c->solve_ws;
         size_t f = 0;
         auto carve32 = [&](size_t cnt) { float* r = fb + f; f = (f + cnt + 7) & ~(size_t)7; return r; };
@@ -266,6 +403,9 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         t.gg[0] = carve32(4 * mp); t.gg[1] = carve32(4 * mp); t.U = carve32(6 * np); t.Uref = carve32(6 * np);
         t.gref = carve32(mp);
         t.rec = carve32(9 * mp); t.qe = carve32(8 * mp); t.q = carve32(mp); t.ax = carve32(3 * np);
+        t.mobr = carve32(4 * np);
+        // the float32 views use at most half of the workspace: room for the low parts
+        t.rec_lo = carve32(9 * mp); t.qe_lo = carve32(8 * mp); t.q_lo = carve32(mp);
     }
     if (cudaMemsetAsync(c->cell_cursor, 0, ((size_t)c->max_keys + 1) * sizeof(int), c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -296,6 +436,7 @@ aLENS_status aLENS_set_params(aLENS_ctx* c, const aLENS_params* params)
     c->p = *params;
     c->geo = geo;
     c->mob = mob;
+    c->batch_n = 0;   // batch tables derive from the parameters: rebuild on the next batch
     return ALENS_OK;
 }
 
@@ -327,7 +468,7 @@ aLENS_status aLENS_set_launch(aLENS_ctx* c, int32_t threads, int32_t blocks_per_
 // pairs exactly).
 static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const double* quat, const double* fnc)
 {
-    int nkeys = 1 << (3 * c->geo.bits);
+    int nkeys = c->cur_nkeys;
     aLENS_status st = reset_status(c);
     if (st != ALENS_OK) return st;
     CK(cudaMemsetAsync(c->cell_count, 0, ((size_t)nkeys + 1) * sizeof(int), c->stream));
@@ -351,7 +492,7 @@ static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const dou
 aLENS_status aLENS_build_neighbors(aLENS_ctx* c, int64_t n, const double* x, const double* quat, int32_t* pairs,
                                    int64_t pairs_cap, int64_t* n_pairs)
 {
-    if (c) c->launches = 0;
+    if (c) { c->launches = 0; single_mode(c); }
     if (!rods_ok(c, n) || !n_pairs || (n > 0 && (!x || !quat)) || pairs_cap < 0 || (pairs_cap > 0 && !pairs))
         return ALENS_ERR_INVALID;
     long long cap = std::min<long long>(pairs_cap, c->max_pairs);
@@ -369,7 +510,7 @@ aLENS_status aLENS_assemble_constraints(aLENS_ctx* c, int64_t n, const double* x
                                         const double* f_nc, int64_t n_pairs, const int32_t* pairs, double* phi,
                                         double* dgeom, double* q)
 {
-    if (c) c->launches = 0;
+    if (c) { c->launches = 0; single_mode(c); }
     if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
     if (n > 0 && (!x || !quat)) return ALENS_ERR_INVALID;
     if (n_pairs > 0 && (!pairs || !phi || !dgeom || !q)) return ALENS_ERR_INVALID;
@@ -411,7 +552,7 @@ static aLENS_status solve_status(aLENS_ctx* c, int64_t m)
 aLENS_status aLENS_solve_lcp(aLENS_ctx* c, int64_t n, const double* quat, int64_t n_pairs, const int32_t* pairs,
                              const double* dgeom, const double* q, double* gamma, aLENS_info* info)
 {
-    if (c) c->launches = 0;
+    if (c) { c->launches = 0; single_mode(c); }
     if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
     if (n > 0 && !quat) return ALENS_ERR_INVALID;
     if (n_pairs > 0 && (!pairs || !dgeom || !q || !gamma)) return ALENS_ERR_INVALID;
@@ -441,12 +582,12 @@ aLENS_status aLENS_solve_lcp(aLENS_ctx* c, int64_t n, const double* quat, int64_
     return st;
 }
 
-aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc, int32_t* pairs_out,
-                        double* gamma_out, double* vel_out, aLENS_info* info)
+}  // extern "C"
+
+// The step on the system(s) selected by cur_systab / cur_sysid / cur_nkeys.
+static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
+                              int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info)
 {
-    if (c) c->launches = 0;
-    if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;
-    if (!c->coop_ok) return ALENS_ERR_CUDA;
     CK(cudaEventRecord(c->ev[0], c->stream));
     aLENS_status st = search_phase(c, (int)n, x, quat, f_nc);
     if (st != ALENS_OK) {
@@ -478,6 +619,35 @@ aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const 
         info->ms_solve = elapsed(c->ev[2], c->ev[3]);
         info->ms_update = elapsed(c->ev[3], c->ev[4]);
     }
+    return st;
+}
+
+extern "C" {
+
+aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc, int32_t* pairs_out,
+                        double* gamma_out, double* vel_out, aLENS_info* info)
+{
+    if (c) { c->launches = 0; single_mode(c); }
+    if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;
+    if (!c->coop_ok) return ALENS_ERR_CUDA;
+    return step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
+}
+
+aLENS_status aLENS_step_batch(aLENS_ctx* c, int32_t n_systems, const aLENS_system* systems, const int64_t* rod_offset,
+                              double* x, double* quat, const double* f_nc, int32_t* pairs_out, double* gamma_out,
+                              double* vel_out, aLENS_info* info)
+{
+    if (c) { c->launches = 0; single_mode(c); }
+    if (!c || n_systems < 1 || !systems || !rod_offset) return ALENS_ERR_INVALID;
+    const int64_t n = rod_offset[n_systems];
+    if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;
+    if (!c->coop_ok) return ALENS_ERR_CUDA;
+    aLENS_status st = batch_tables(c, n_systems, systems, rod_offset);
+    if (st != ALENS_OK) { single_mode(c); return st; }
+    c->cur_systab = c->systab;
+    c->cur_sysid = c->sysid;
+    st = step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
+    single_mode(c);
     return st;
 }
 

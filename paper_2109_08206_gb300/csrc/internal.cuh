@@ -50,6 +50,19 @@ struct Mob {                 // inverse drag coefficients of one rod (all rods a
     double inv_perp, inv_par, inv_rot, inv_spin;
 };
 
+struct SysGeo {              // one system of a batch: its geometry, drags and cell keys
+    Geo g;
+    Mob mob;
+    int key_base;            // first cell key of the system in the batch's key space
+    int pad;
+};
+
+// Geometry of rod i: its system's entry when a batch table is given.
+__device__ __forceinline__ const Geo& geo_of(const Geo& g, const SysGeo* systab, const int* sys, int i)
+{
+    return systab ? systab[sys[i]].g : g;
+}
+
 // ------------------------------------------------------------- device helpers
 
 __host__ __device__ inline uint32_t spread_bits3(uint32_t v)
@@ -161,13 +174,19 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p)
 template <typename T>
 struct SolveBufs {           // typed views into the solver workspace
     T* rec;                  // [9][mp]  e, y_P x e, y_Q x e
-    T* qe;                   // [6][mp]  per Q-side entry: e, y_Q x e (CSR order)
+    T* qe;                   // [mp][8]  per Q-side entry: e, y_Q x e, 2 pad (CSR order)
     T* q;                    // [mp]
     T* ax;                   // [3][np]
     T* gg[2];                // [mp][4] x 2: (delta, g, gamma_ref, 0), ping-pong
     T* U;                    // [np][6] velocity increment M D delta
     T* Uref;                 // [np][6] reference velocity M D gamma_ref
     T* gref;                 // [mp] reference gradient q + D^T Uref
+    T* mobr;                 // [4][np] per-rod inverse drags (batches)
+    // float32 only: low parts of the float64 inputs (x = hi + lo to about
+    // 48 bits), read by the reference passes
+    T* rec_lo;               // [9][mp]
+    T* qe_lo;                // [mp][8]
+    T* q_lo;                 // [mp]
 };
 
 }  // namespace alens
@@ -236,6 +255,19 @@ struct aLENS_ctx {
     int solve_threads, solve_bps;
     int coop_ok;
     int launches;            // kernels launched since the entry point began
+    // batches (aLENS_step_batch): per-system table and per-rod system id;
+    // NULL outside a batched step
+    alens::SysGeo* systab;   // [max_systems] device
+    int* sysid;              // [np] device
+    long long* sysoff;       // [max_systems + 1] device rod offsets
+    int max_systems;
+    const alens::SysGeo* cur_systab;   // set for the duration of a batched step
+    const int* cur_sysid;
+    int cur_nkeys;           // cell keys of the step (batch: all systems)
+    int batch_n;             // systems described by the tables now on the device
+    int batch_keys;          // their cell keys
+    void* batch_host;        // host copy of the last aLENS_system array (to skip re-uploads)
+    int64_t* batch_off_host; // host copy of the last rod offsets
 };
 
 namespace alens {

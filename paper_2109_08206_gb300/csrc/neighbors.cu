@@ -18,13 +18,17 @@
 namespace alens {
 
 __global__ void k_pack(int n, int np, const double* __restrict__ x, const double* __restrict__ quat,
-                       const double* __restrict__ fnc, Geo g, Mob mob, bool cells, double* __restrict__ xw,
+                       const double* __restrict__ fnc, Geo g0, Mob mob0, const SysGeo* __restrict__ systab,
+                       const int* __restrict__ sysid, bool cells, double* __restrict__ xw,
                        double* __restrict__ axis, double* __restrict__ unc, float4* __restrict__ pos32,
                        float4* __restrict__ ax32, uint32_t* __restrict__ cellkey, int* __restrict__ cell_count,
                        int* __restrict__ flags)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const Geo& g = geo_of(g0, systab, sysid, i);
+    const Mob& mob = systab ? systab[sysid[i]].mob : mob0;
+    const uint32_t key_base = systab ? (uint32_t)systab[sysid[i]].key_base : 0u;
     double s = quat[4 * (size_t)i], a = quat[4 * (size_t)i + 1], b = quat[4 * (size_t)i + 2],
            c = quat[4 * (size_t)i + 3];
     double nq = s * s + a * a + b * b + c * c;
@@ -49,7 +53,7 @@ __global__ void k_pack(int n, int np, const double* __restrict__ x, const double
     pos32[i] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.f);
     ax32[i] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.f);
     if (cells) {
-        uint32_t key = morton3(cc[0], cc[1], cc[2]);
+        uint32_t key = key_base + morton3(cc[0], cc[1], cc[2]);
         cellkey[i] = key;
         atomicAdd(&cell_count[key], 1);
     }
@@ -188,7 +192,8 @@ __device__ __forceinline__ void decode_cell(uint32_t key, int bits, int cc[3])
 // count the kept pairs (used when the candidate buffer overflows).
 template <bool COUNT_ONLY>
 __global__ void __launch_bounds__(kSearchWarps * 32)
-k_search(int n, int np, Geo g, const int* __restrict__ sorted_id, const float4* __restrict__ spos32,
+k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __restrict__ sysid,
+         const int* __restrict__ sorted_id, const float4* __restrict__ spos32,
          const float4* __restrict__ sax32, const uint32_t* __restrict__ cellkey, const double* __restrict__ xw,
          const double* __restrict__ axis, const int* __restrict__ cell_start, int* __restrict__ rod_ncand,
          long long* __restrict__ rod_tmpstart, unsigned long long* __restrict__ cand, long long cand_cap,
@@ -201,8 +206,10 @@ k_search(int n, int np, Geo g, const int* __restrict__ sorted_id, const float4* 
     uint32_t* L = list[COUNT_ONLY ? 0 : warp];
     const int i = sorted_id[k];
     const float4 pi = spos32[k], ai = sax32[k];
+    const Geo& g = geo_of(g0, systab, sysid, i);
+    const uint32_t key_base = systab ? (uint32_t)systab[sysid[i]].key_base : 0u;
     int cc[3];
-    decode_cell(cellkey[i], g.bits, cc);
+    decode_cell(cellkey[i] - key_base, g.bits, cc);
     int cnt = 0;
     for (int o = 0; o < 27; ++o) {
         int d[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
@@ -215,7 +222,7 @@ k_search(int n, int np, Geo g, const int* __restrict__ sorted_id, const float4* 
             else if (c[a] >= g.nc[a]) { c[a] -= g.nc[a]; sh[a] = 1; }
         }
         const uint32_t code = (uint32_t)((sh[0] + 1) + 3 * (sh[1] + 1) + 9 * (sh[2] + 1));
-        const uint32_t key = morton3(c[0], c[1], c[2]);
+        const uint32_t key = key_base + morton3(c[0], c[1], c[2]);
         const int beg = cell_start[key], end = cell_start[key + 1];
         const float sx = (float)sh[0] * g.boxf[0], sy = (float)sh[1] * g.boxf[1], sz = (float)sh[2] * g.boxf[2];
         for (int base = beg; base < end; base += 32) {
@@ -275,7 +282,8 @@ k_search(int n, int np, Geo g, const int* __restrict__ sorted_id, const float4* 
 
 // Float64 decision of every candidate (grid-stride, full warps): keep flag,
 // per-rod kept count and the total.
-__global__ void k_decide(int np, Geo g, const unsigned long long* counters_ro,
+__global__ void k_decide(int np, Geo g0, const SysGeo* __restrict__ systab, const int* __restrict__ sysid,
+                         const unsigned long long* counters_ro,
                          const unsigned long long* __restrict__ cand, long long cand_cap,
                          const double* __restrict__ xw, const double* __restrict__ axis,
                          unsigned char* __restrict__ keep, int* __restrict__ rod_count,
@@ -292,7 +300,8 @@ __global__ void k_decide(int np, Geo g, const unsigned long long* counters_ro,
             int i = (int)(key >> 32);
             int j = (int)((key >> 5) & 0x7ffffffu);
             int code = (int)(key & 31u);
-            kp = decide64(i, j, code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1, np, xw, axis, g);
+            kp = decide64(i, j, code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1, np, xw, axis,
+                          geo_of(g0, systab, sysid, i));
             keep[k] = kp ? 1 : 0;
             if (kp) atomicAdd(&rod_count[i], 1);
         }
@@ -326,7 +335,8 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t > 0 ? 
 cudaError_t launch_pack(aLENS_ctx* ctx, int n, const double* x, const double* quat, const double* fnc, bool cells)
 {
     if (n <= 0) return cudaSuccess;
-    k_pack<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, (int)ctx->max_rods, x, quat, fnc, ctx->geo, ctx->mob, cells,
+    k_pack<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, (int)ctx->max_rods, x, quat, fnc, ctx->geo, ctx->mob,
+                                                   ctx->cur_systab, ctx->cur_sysid, cells,
                                                    ctx->xw, ctx->axis, ctx->unc, ctx->pos32, ctx->ax32,
                                                    ctx->cellkey, ctx->cell_count, ctx->dflags);
     ++ctx->launches;
@@ -335,7 +345,7 @@ cudaError_t launch_pack(aLENS_ctx* ctx, int n, const double* x, const double* qu
 
 cudaError_t launch_cell_sort(aLENS_ctx* ctx, int n)
 {
-    int nkeys = 1 << (3 * ctx->geo.bits);
+    int nkeys = ctx->cur_nkeys;
     cudaError_t e = exclusive_scan(ctx, ctx->cell_count, ctx->cell_start, nkeys);
     if (e != cudaSuccess) return e;
     if (n > 0) {
@@ -355,10 +365,12 @@ cudaError_t launch_search(aLENS_ctx* ctx, int n)
 {
     if (n <= 0) return cudaSuccess;
     k_search<false><<<nblk(n, kSearchWarps), kSearchWarps * 32, 0, ctx->stream>>>(
-        n, (int)ctx->max_rods, ctx->geo, ctx->sorted_id, ctx->spos32, ctx->sax32, ctx->cellkey, ctx->xw, ctx->axis,
-        ctx->cell_start, ctx->rod_ncand, ctx->rod_tmpstart, ctx->cand, ctx->cand_cap, ctx->dcount, ctx->dflags);
+        n, (int)ctx->max_rods, ctx->geo, ctx->cur_systab, ctx->cur_sysid, ctx->sorted_id, ctx->spos32, ctx->sax32,
+        ctx->cellkey, ctx->xw, ctx->axis, ctx->cell_start, ctx->rod_ncand, ctx->rod_tmpstart, ctx->cand, ctx->cand_cap,
+        ctx->dcount, ctx->dflags);
     ++ctx->launches;
-    k_decide<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>((int)ctx->max_rods, ctx->geo, ctx->dcount, ctx->cand,
+    k_decide<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>((int)ctx->max_rods, ctx->geo, ctx->cur_systab, ctx->cur_sysid,
+                                                         ctx->dcount, ctx->cand,
                                                          ctx->cand_cap, ctx->xw, ctx->axis, ctx->keep,
                                                          ctx->rod_count, ctx->dcount);
     ++ctx->launches;
@@ -369,8 +381,9 @@ cudaError_t launch_search_count(aLENS_ctx* ctx, int n)
 {
     if (n <= 0) return cudaSuccess;
     k_search<true><<<nblk(n, kSearchWarps), kSearchWarps * 32, 0, ctx->stream>>>(
-        n, (int)ctx->max_rods, ctx->geo, ctx->sorted_id, ctx->spos32, ctx->sax32, ctx->cellkey, ctx->xw, ctx->axis,
-        ctx->cell_start, ctx->rod_ncand, ctx->rod_tmpstart, ctx->cand, ctx->cand_cap, ctx->dcount, ctx->dflags);
+        n, (int)ctx->max_rods, ctx->geo, ctx->cur_systab, ctx->cur_sysid, ctx->sorted_id, ctx->spos32, ctx->sax32,
+        ctx->cellkey, ctx->xw, ctx->axis, ctx->cell_start, ctx->rod_ncand, ctx->rod_tmpstart, ctx->cand, ctx->cand_cap,
+        ctx->dcount, ctx->dflags);
     ++ctx->launches;
     return cudaGetLastError();
 }

@@ -102,28 +102,35 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Constraint state (delta, g, gamma_ref, 0) of constraint c in a [m][4]
-// buffer: one vector load (float32) or two (float64).
-__device__ __forceinline__ void ld_state(const float* p, int c, float& d, float& g, float& gr)
+// Constraint state (delta, g, gamma_ref, gamma_lo) of constraint c in a
+// [m][4] buffer: one vector load (float32) or two (float64).  The iterate
+// is gamma = gamma_ref + gamma_lo + delta: in float32 (gamma_ref, gamma_lo)
+// is an unevaluated sum carrying about 48 bits (gamma_lo is 0 in float64).
+__device__ __forceinline__ void ld_state(const float* p, int c, float& d, float& g, float& gr, float& gl)
 {
     const float4 v = reinterpret_cast<const float4*>(p)[c];
-    d = v.x; g = v.y; gr = v.z;
+    d = v.x; g = v.y; gr = v.z; gl = v.w;
 }
-__device__ __forceinline__ void ld_state(const double* p, int c, double& d, double& g, double& gr)
+__device__ __forceinline__ void ld_state(const double* p, int c, double& d, double& g, double& gr, double& gl)
 {
     const double2* q = reinterpret_cast<const double2*>(p) + 2 * (size_t)c;
     const double2 a = q[0], b = q[1];
-    d = a.x; g = a.y; gr = b.x;
+    d = a.x; g = a.y; gr = b.x; gl = b.y;
 }
-__device__ __forceinline__ void st_state(float* p, int c, float d, float g, float gr)
+// (delta, g) and (gamma_ref, gamma_lo) halves of a state
+template <typename T>
+__device__ __forceinline__ void st_dg(T* p, int c, T d, T g)
 {
-    reinterpret_cast<float4*>(p)[c] = make_float4(d, g, gr, 0.f);
+    typename V2<T>::t v;
+    v.x = d; v.y = g;
+    reinterpret_cast<typename V2<T>::t*>(p)[2 * (size_t)c] = v;
 }
-__device__ __forceinline__ void st_state(double* p, int c, double d, double g, double gr)
+template <typename T>
+__device__ __forceinline__ void st_ref(T* p, int c, T gr, T gl)
 {
-    double2* q = reinterpret_cast<double2*>(p) + 2 * (size_t)c;
-    q[0] = make_double2(d, g);
-    q[1] = make_double2(gr, 0.0);
+    typename V2<T>::t v;
+    v.x = gr; v.y = gl;
+    reinterpret_cast<typename V2<T>::t*>(p)[2 * (size_t)c + 1] = v;
 }
 
 // Exact sum: a + b = s + e.
@@ -157,6 +164,8 @@ struct Acc {
             lo += es + ep;
         }
     }
+    // a term far below hi (a product with a low part): into lo directly
+    __device__ __forceinline__ void add_lo(T x) { lo += x; }
     __device__ __forceinline__ T value() const { return COMP ? hi + lo : hi; }
 };
 
@@ -182,9 +191,13 @@ struct SolveArgs {
     int* flags;
     double* out;   // [0] residual, [1] alpha0
     T inv_perp, inv_par, inv_rot, inv_spin;
+    const T* __restrict__ mobr;   // [4][np] per-rod inverse drags (batches), or NULL for the uniform ones
+    const T* __restrict__ rec_lo; // float32: low parts of rec, qe and q for the reference passes (else NULL)
+    const T* __restrict__ qe_lo;
+    const T* __restrict__ q_lo;
     double hD, tol;
     int max_iter;
-    int refresh;   // fold delta into gamma_ref every this many iterations (0: never)
+    int refresh;   // refresh the reference every this many iterations (0: never)
     long long wait_cycles;
     int fault;
     const int* __restrict__ bstart;   // [gridDim.x + 1] rod-rank boundaries of the blocks
@@ -256,8 +269,8 @@ __device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
         for (int w = 0; w < 9; ++w) o.rec[w * o.cap_c + lc] = a.rec[w * mp + c];
         o.cj[lc] = a.cj[c];
         o.ci[lc] = (unsigned short)(a.ci[c] - o.r0);
-        T d, g, gr;
-        ld_state(a.gg0, c, d, g, gr);
+        T d, g, gr, gl;
+        ld_state(a.gg0, c, d, g, gr, gl);
         o.ds[0][lc] = d;
         o.gam[lc] = gr;
         o.grs[lc] = T(0);
@@ -269,12 +282,13 @@ __device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
 // Rod phase modes: A_STEP forms delta_{k+1} = max(-gamma_ref, delta - alpha g)
 // (the owner stores it) and stores dU = M D delta_{k+1}; A_PG sums pi.A.pi
 // for the projected gradient pi (returned, nothing stored); A_REF stores the
-// reference velocity Uref = M D gamma_ref with compensated sums.
+// reference velocity Uref = M D gamma_ref with compensated sums over the
+// split (hi + lo) records, and clears dU.
 enum { A_STEP = 0, A_PG = 1, A_REF = 2 };
 // Constraint phase modes: B_STEP g_{k+1} = gref + D^T dU and the BB sums;
-// B_REF gref = q + D^T Uref (compensated); B_FIRST = B_REF, then g_0 = gref
-// and pi.pi, max |pi| at gamma_0.
-enum { B_STEP = 0, B_REF = 1, B_FIRST = 2 };
+// B_REF gref = q + D^T Uref (compensated, split records and q), then
+// g = gref (delta is 0 there) and pi.pi, max |pi| at gamma_ref.
+enum { B_STEP = 0, B_REF = 2 };
 
 template <int MODE, typename T>
 __device__ __forceinline__ T a_value(T d, T g, T gr, T alpha)
@@ -307,7 +321,7 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
         {   // owned constraints: loads of up to BO entries issued together
             const int b = ST ? o.rowP[li] : a.rowP[i], e = ST ? o.rowP[li + 1] : a.rowP[i + 1];
             for (int c = b; c < e; c += BO) {
-                T dv[BO], gv[BO], rv_[BO], rv[BO][6];
+                T dv[BO], gv[BO], rv_[BO], gl[BO], rv[BO][6];
 #pragma unroll
                 for (int u = 0; u < BO; ++u) {
                     if (c + u < e) {
@@ -316,10 +330,11 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
                             dv[u] = sdc[lc];
                             gv[u] = o.grs[lc];
                             rv_[u] = o.gam[lc];
+                            if (MODE == A_REF && COMP) gl[u] = gc[4 * (size_t)(c + u) + 3];
 #pragma unroll
                             for (int w = 0; w < 6; ++w) rv[u][w] = o.rec[w * o.cap_c + lc];
                         } else {
-                            ld_state(gc, c + u, dv[u], gv[u], rv_[u]);
+                            ld_state(gc, c + u, dv[u], gv[u], rv_[u], gl[u]);
 #pragma unroll
                             for (int w = 0; w < 6; ++w) rv[u][w] = a.rec[w * mp + c + u];
                         }
@@ -335,6 +350,11 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
                         }
 #pragma unroll
                         for (int w = 0; w < 6; ++w) Fa[w].add_prod(v, rv[u][w]);
+                        if (MODE == A_REF && COMP) {   // gamma_lo and the records' low parts
+#pragma unroll
+                            for (int w = 0; w < 6; ++w)
+                                Fa[w].add_lo(v * __ldg(&a.rec_lo[w * mp + c + u]) + gl[u] * rv[u][w]);
+                        }
                     }
                 }
             }
@@ -347,7 +367,7 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
 #pragma unroll
                 for (int u = 0; u < B; ++u)
                     cid[u] = k + u < e ? (ST ? o.qlist[k + u - o.q0] : __ldg(&a.qlist[k + u])) : -1;
-                T dv[B], gv[B], rv_[B], qv[B][6];
+                T dv[B], gv[B], rv_[B], gl[B], qv[B][6];
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
                     if (cid[u] >= 0) {
@@ -356,13 +376,14 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
                             dv[u] = sdc[lc];
                             gv[u] = o.grs[lc];
                             rv_[u] = o.gam[lc];
+                            if (MODE == A_REF && COMP) gl[u] = gc[4 * (size_t)cid[u] + 3];
 #pragma unroll
                             for (int w = 0; w < 3; ++w) {
                                 qv[u][w] = o.rec[w * o.cap_c + lc];
                                 qv[u][3 + w] = o.rec[(6 + w) * o.cap_c + lc];
                             }
                         } else {
-                            ld_state(gc, cid[u], dv[u], gv[u], rv_[u]);
+                            ld_state(gc, cid[u], dv[u], gv[u], rv_[u], gl[u]);
                             ld_arm(a.qe, k + u, qv[u]);
                         }
                     }
@@ -373,6 +394,12 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
                         const T v = a_value<MODE, T>(dv[u], gv[u], rv_[u], alpha);
 #pragma unroll
                         for (int w = 0; w < 6; ++w) Fa[w].add_prod(-v, qv[u][w]);
+                        if (MODE == A_REF && COMP) {
+                            T ql[6];
+                            ld_arm(a.qe_lo, k + u, ql);
+#pragma unroll
+                            for (int w = 0; w < 6; ++w) Fa[w].add_lo(-(v * ql[w] + gl[u] * qv[u][w]));
+                        }
                     }
                 }
             }
@@ -386,16 +413,25 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
         } else {
             p0 = a.ax[i]; p1 = a.ax[np + i]; p2 = a.ax[2 * np + i];
         }
+        T ip = a.inv_perp, ipa = a.inv_par, ir = a.inv_rot, is = a.inv_spin;
+        if (a.mobr) {
+            ip = __ldg(&a.mobr[i]); ipa = __ldg(&a.mobr[np + i]);
+            ir = __ldg(&a.mobr[2 * np + i]); is = __ldg(&a.mobr[3 * np + i]);
+        }
         const T pf = p0 * F[0] + p1 * F[1] + p2 * F[2];
         const T pt = p0 * F[3] + p1 * F[4] + p2 * F[5];
-        const T cf = pf * (a.inv_par - a.inv_perp), ct = pt * (a.inv_spin - a.inv_rot);
-        T Uv[6] = {F[0] * a.inv_perp + p0 * cf, F[1] * a.inv_perp + p1 * cf, F[2] * a.inv_perp + p2 * cf,
-                   F[3] * a.inv_rot + p0 * ct,  F[4] * a.inv_rot + p1 * ct,  F[5] * a.inv_rot + p2 * ct};
+        const T cf = pf * (ipa - ip), ct = pt * (is - ir);
+        T Uv[6] = {F[0] * ip + p0 * cf, F[1] * ip + p1 * cf, F[2] * ip + p2 * cf,
+                   F[3] * ir + p0 * ct, F[4] * ir + p1 * ct, F[5] * ir + p2 * ct};
         if (MODE == A_PG) {
 #pragma unroll
             for (int w = 0; w < 6; ++w) fmf += F[w] * Uv[w];
         } else {
             st_u6(MODE == A_REF ? a.Uref : a.U, i, Uv);
+            if (MODE == A_REF) {
+                const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                st_u6(a.U, i, z);   // dU = 0: delta is 0 after a reference pass
+            }
             if (ST) {
 #pragma unroll
                 for (int w = 0; w < 6; ++w) o.U[w * o.cap_r + li] = Uv[w];
@@ -447,11 +483,11 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
 #pragma unroll
             for (int w = 0; w < 9; ++w) r[w] = a.rec[w * mp + c];
             base = MODE == B_STEP ? a.gref[c] : a.q[c];
-            T gdummy;
-            ld_state(gnew, c, dm, gdummy, gam);
+            T gdummy, gl;
+            ld_state(gnew, c, dm, gdummy, gam, gl);
             if (MODE == B_STEP) {
-                T g2;
-                ld_state(gold, c, dold, gro, g2);
+                T g2, gl2;
+                ld_state(gold, c, dold, gro, g2, gl2);
             }
         }
         Acc<T, COMP> du;
@@ -463,27 +499,33 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
             du.add_prod(r[3 + u], Ui[3 + u]);
             du.add_prod(-r[6 + u], Uj[3 + u]);
         }
+        if (MODE == B_REF && COMP) {
+            // low parts of q and of the record
+            T rl[9];
+#pragma unroll
+            for (int w = 0; w < 9; ++w) rl[w] = __ldg(&a.rec_lo[w * mp + c]);
+            T t = __ldg(&a.q_lo[c]);
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+                t += rl[u] * (Ui[u] - Uj[u]) + rl[3 + u] * Ui[3 + u] - rl[6 + u] * Uj[3 + u];
+            du.add_lo(t);
+        }
         const T gr = du.value();
         if (MODE == B_REF) {
             if (ST) o.gref[lc] = gr;
             else a.gref[c] = gr;
-            continue;
         }
-        if (MODE == B_FIRST) {
-            if (ST) o.gref[lc] = gr;
-            else a.gref[c] = gr;
-        }
-        // g of the new iterate (for B_FIRST: gamma_0 with g_0 = gref)
+        // g of the new iterate (for B_REF: gamma_ref itself, delta = 0)
         if (ST) {
             o.grs[lc] = gr;
-            st_state(gnew, c, dm, gr, gam);    // the state other blocks read in the next phase A
+            st_dg(gnew, c, dm, gr);    // the state other blocks read in the next phase A
         } else {
             gnew[4 * (size_t)c + 1] = gr;
         }
         const T pi = dm > -gam ? gr : (gr < T(0) ? gr : T(0));
         const T api = pi < T(0) ? -pi : pi;
         acc[3] = api > acc[3] ? api : acc[3];
-        if (MODE == B_FIRST) {
+        if (MODE == B_REF) {
             acc[0] += pi * pi;
         } else {
             const T sv = dm - dold, yv = gr - gro;
@@ -494,8 +536,11 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
     }
 }
 
-// Refresh: gamma_ref absorbs delta (TwoSum: the new delta is the exact
-// remainder), in shared memory and in both global state buffers.
+// Refresh, first half: (gamma_ref, gamma_lo) absorbs delta as a
+// double-float sum (TwoSum, then renormalised so that |gamma_lo| is at most
+// half an ulp of gamma_ref) and delta becomes 0, in shared memory and in
+// both global state buffers.  A constraint held at the bound (delta =
+// -gamma_ref) gets gamma = 0 exactly.
 template <typename T, bool ST>
 __device__ __forceinline__ void fold_delta(const SolveArgs<T>& a, const Own<T>& o, int cur)
 {
@@ -505,20 +550,27 @@ __device__ __forceinline__ void fold_delta(const SolveArgs<T>& a, const Own<T>& 
     const int nc = o.c1 - o.c0;
     for (int lc = threadIdx.x; lc < nc; lc += blockDim.x) {
         const int c = o.c0 + lc;
-        T d, g, gr;
+        T d, g, gr, gl;
+        ld_state(gc, c, d, g, gr, gl);
         if (ST) {
             d = sdc[lc]; g = o.grs[lc]; gr = o.gam[lc];
-        } else {
-            ld_state(gc, c, d, g, gr);
         }
-        T ns, rem;
-        two_sum(gr, d, ns, rem);
+        T hi = T(0), lo = T(0);
+        if (d > -gr) {
+            T s, e;
+            two_sum(gr, d, s, e);
+            const T l = gl + e;
+            hi = s + l;
+            lo = l - (hi - s);
+            if (hi < T(0) || (hi == T(0) && lo < T(0))) { hi = T(0); lo = T(0); }
+        }
         if (ST) {
-            sdc[lc] = rem;
-            o.gam[lc] = ns;
+            sdc[lc] = T(0);
+            o.gam[lc] = hi;
         }
-        st_state(gc, c, rem, g, ns);
-        go[4 * (size_t)c + 2] = ns;
+        st_dg(gc, c, T(0), g);
+        st_ref(gc, c, hi, lo);
+        st_ref(go, c, hi, lo);
     }
 }
 
@@ -631,7 +683,7 @@ struct Shared {
     T red[32][4];
     double bc[4];
     T alpha;
-    int done, ok;
+    int done, ok, refresh;
 };
 
 // Smallest rank r in [0, n] whose cumulative work W(r) = rowP[r] +
@@ -683,7 +735,7 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
     phase_a<T, A_REF, ST>(a, o, 0, T(0));
     if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
     v[0] = v[1] = v[2] = v[3] = T(0);
-    phase_b<T, B_FIRST, ST>(a, o, 0, 0, v);
+    phase_b<T, B_REF, ST>(a, o, 0, 0, v);
     block_partial(v, sh.red, mine);
     if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
     grid_total(a.partials, nb, sh.bc, tot);
@@ -729,26 +781,40 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
                 st.res = a.hD * tot[3];
                 st.cur = cur;
                 st.iters = k + 1;
-                st.done = !(st.res > a.tol);
-                if (!st.done) {
-                    double an = (k & 1) == 0 ? ss / sy : sy / yy;
-                    if (!(sy > 0.0) || !isfinite(an) || !(an > 0.0)) an = st.alpha0;
-                    st.alpha = an;
-                    sh.alpha = (T)an;
-                }
+                const bool below = !(st.res > a.tol);
+                double an = (k & 1) == 0 ? ss / sy : sy / yy;
+                if (!(sy > 0.0) || !isfinite(an) || !(an > 0.0)) an = st.alpha0;
+                st.alpha = an;
+                sh.alpha = (T)an;
+                // float32: a residual below tol is confirmed on a fresh
+                // reference before the loop stops (the increments since the
+                // last refresh carry float32 rounding)
+                st.done = below && a.refresh == 0;
+                sh.refresh = a.refresh > 0 && (below || (k + 1) % a.refresh == 0);
                 sh.done = st.done;
             }
             __syncthreads();
             if (sh.done) break;
-            if (a.refresh > 0 && (k + 1) % a.refresh == 0) {
-                // gamma_ref absorbs delta; Uref and gref are recomputed with
-                // compensated sums (g itself is unchanged: same gamma)
+            if (sh.refresh) {
+                // the reference takes the iterate; Uref, gref and g are
+                // recomputed from the split records with compensated sums, and
+                // max |pi| with them
                 fold_delta<T, ST>(a, o, cur);
                 if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
                 phase_a<T, A_REF, ST>(a, o, cur, T(0));
                 if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+                v[0] = v[1] = v[2] = v[3] = T(0);
                 phase_b<T, B_REF, ST>(a, o, cur, cur, v);
+                block_partial(v, sh.red, mine);
+                if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+                grid_total(a.partials, nb, sh.bc, tot);
+                if (threadIdx.x == 0) {
+                    st.res = a.hD * tot[3];
+                    st.done = !(st.res > a.tol);
+                    sh.done = st.done;
+                }
                 __syncthreads();
+                if (sh.done) break;
             }
         }
     }
@@ -816,7 +882,8 @@ __global__ void k_gamma_out(int m, const int* __restrict__ flags, const int* __r
     if (c >= m) return;
     if (flags[F_SOLVE_ERR] != 0) return;
     const T* g = flags[F_FINAL] == 0 ? gg0 : gg1;
-    out[perm[c]] = (double)g[4 * (size_t)c + 2] + (double)g[4 * (size_t)c];   // gamma_ref + delta
+    // gamma_ref + gamma_lo + delta
+    out[perm[c]] = ((double)g[4 * (size_t)c + 2] + (double)g[4 * (size_t)c + 3]) + (double)g[4 * (size_t)c];
 }
 
 __global__ void k_rank(int n, const int* __restrict__ sorted_id, int* __restrict__ rank)
@@ -841,13 +908,16 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     a.rowP = ctx->rowP; a.rowQ = ctx->rowQ; a.qlist = ctx->qlist; a.ci = ctx->ci; a.cj = ctx->cj;
     a.rec = sb.rec; a.qe = sb.qe; a.q = sb.q; a.ax = sb.ax;
     a.gg0 = sb.gg[0]; a.gg1 = sb.gg[1]; a.U = sb.U; a.Uref = sb.Uref; a.gref = sb.gref;
-    // float32 iterations work on increments over a reference that absorbs
-    // them every kRefresh iterations; float64 needs no refresh
+    // float32 iterations work on increments over a reference that takes
+    // the iterate every kRefresh iterations (and to confirm convergence);
+    // float64 needs no refresh
     a.refresh = sizeof(T) == 4 ? kRefresh : 0;
     a.partials = ctx->partials; a.bar = ctx->bar; a.flags = ctx->dflags;
     a.out = reinterpret_cast<double*>(ctx->dcount + C_RESID);
     a.inv_perp = (T)ctx->mob.inv_perp; a.inv_par = (T)ctx->mob.inv_par;
     a.inv_rot = (T)ctx->mob.inv_rot; a.inv_spin = (T)ctx->mob.inv_spin;
+    a.mobr = ctx->cur_systab ? sb.mobr : nullptr;
+    a.rec_lo = sb.rec_lo; a.qe_lo = sb.qe_lo; a.q_lo = sb.q_lo;
     a.hD = ctx->p.dt / ctx->p.diameter; a.tol = ctx->p.tol; a.max_iter = ctx->p.max_iter;
     a.wait_cycles = (long long)(ctx->wait_s * ctx->clock_khz * 1e3);
     a.fault = ctx->fault_mode;

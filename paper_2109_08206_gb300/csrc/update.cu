@@ -9,7 +9,8 @@
 namespace alens {
 
 template <typename T>
-__global__ void k_update(int n, int np, bool have_uc, Geo g, const int* __restrict__ flags,
+__global__ void k_update(int n, int np, bool have_uc, Geo g0, const SysGeo* __restrict__ systab,
+                         const int* __restrict__ sysid, const int* __restrict__ flags,
                          const double* __restrict__ xw, const double* __restrict__ unc, const T* __restrict__ Uref,
                          const T* __restrict__ dU, const int* __restrict__ rank, double* __restrict__ x,
                          double* __restrict__ quat, double* __restrict__ vel_out)
@@ -17,15 +18,15 @@ __global__ void k_update(int n, int np, bool have_uc, Geo g, const int* __restri
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (flags[F_ERR] != 0 || flags[F_SOLVE_ERR] != 0) return;   // leave the state untouched after a failure
+    const Geo& g = geo_of(g0, systab, sysid, i);
     double U[6];
     const int r = rank ? rank[i] : i;   // the solver's position of rod i
-    const bool stepped = flags[F_ITERS] > 0;   // the increment exists once an iteration ran
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
         U[u] = unc[u * (size_t)np + i];
         if (have_uc) {
-            U[u] += (double)Uref[6 * (size_t)r + u];      // M D gamma = Uref + M D delta
-            if (stepped) U[u] += (double)dU[6 * (size_t)r + u];
+            // M D gamma = Uref + M D delta (every reference pass clears the increment)
+            U[u] += (double)Uref[6 * (size_t)r + u] + (double)dU[6 * (size_t)r + u];
         }
     }
 #pragma unroll
@@ -57,11 +58,11 @@ cudaError_t launch_update(aLENS_ctx* ctx, int n, int m, double* x, double* quat,
     int b = (n + 255) / 256;
     int np = (int)ctx->max_rods;
     if (precision == ALENS_MIXED) {
-        k_update<float><<<b, 256, 0, ctx->stream>>>(n, np, m > 0, ctx->geo, ctx->dflags, ctx->xw, ctx->unc, ctx->sb32.Uref, ctx->sb32.U, rank, x, quat,
+        k_update<float><<<b, 256, 0, ctx->stream>>>(n, np, m > 0, ctx->geo, ctx->cur_systab, ctx->cur_sysid, ctx->dflags, ctx->xw, ctx->unc, ctx->sb32.Uref, ctx->sb32.U, rank, x, quat,
                                                     vel_out);
         ++ctx->launches;
     } else {
-        k_update<double><<<b, 256, 0, ctx->stream>>>(n, np, m > 0, ctx->geo, ctx->dflags, ctx->xw, ctx->unc, ctx->sb64.Uref, ctx->sb64.U, rank, x, quat,
+        k_update<double><<<b, 256, 0, ctx->stream>>>(n, np, m > 0, ctx->geo, ctx->cur_systab, ctx->cur_sysid, ctx->dflags, ctx->xw, ctx->unc, ctx->sb64.Uref, ctx->sb64.U, rank, x, quat,
                                                      vel_out);
         ++ctx->launches;
     }

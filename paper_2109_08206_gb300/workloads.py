@@ -268,6 +268,16 @@ def ensemble(seed: int = 1000, count: int = 256, scale: float = 1.0) -> list[Rod
     return out
 
 
+def batch_arrays(systems: list[RodSystem]):
+    """Concatenated inputs of a batch: (rod_offset [S+1], x, quat, f_nc, [(box, length)] * S)."""
+    off = np.zeros(len(systems) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([s.n for s in systems])
+    cat = lambda name, w: (np.concatenate([getattr(s, name) for s in systems]) if off[-1] > 0
+                           else np.zeros((0, w)))
+    return (off, np.ascontiguousarray(cat("x", 3)), np.ascontiguousarray(cat("quat", 4)),
+            np.ascontiguousarray(cat("f_nc", 6)), [(s.box, s.length) for s in systems])
+
+
 def tiny_system(seed: int, n: int, box: float = 14.0, length: float = 3.0, forces: str = "unit",
                 dt: float = 1e-3, nematic_spread: float | None = None) -> RodSystem:
     """A small random system for brute-force and active-set checks."""

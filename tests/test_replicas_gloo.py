@@ -31,7 +31,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_replicas_take_the_slowest_rank():
     world = 2
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     for r in range(world):
         ms, value = out[r]
