@@ -180,11 +180,14 @@ ALENS_API aLENS_status aLENS_step(aLENS_ctx* ctx, int64_t n, double* x, double* 
  *            joins two systems, so each system's pairs form one contiguous
  *            run of pairs_out (they are sorted by i).
  *
- * The systems' constraint problems are solved together by one BBPGD run on
- * their block-diagonal union: its residual is the largest of the systems'
- * residuals, so the tolerance holds for every system.  info aggregates the
- * batch (pair, overlap and launch counts summed; iterations, residual and
- * minimum gap over the union).  The first call with more systems or cell
+ * Every system's constraint problem is solved by its own BBPGD run (its own
+ * step sizes, residual and stopping test), all of them in one launch of the
+ * per-system solver (thread-block clusters taking systems from a queue,
+ * largest first); a batch of one system uses the solver of aLENS_step.
+ * info aggregates the batch: pair, overlap and launch counts summed,
+ * iterations and residual the largest over the systems (so the call
+ * returns OK only when every system met the tolerance), minimum gap over
+ * all constraints.  aLENS_batch_results gives the per-system figures.  The first call with more systems or cell
  * keys than any call before grows the context's tables (this allocates and
  * synchronises); later calls with the same systems reuse the uploaded tables.
  * Errors as for aLENS_step; INVALID also for a bad table or a system whose
@@ -197,6 +200,17 @@ typedef struct {
 ALENS_API aLENS_status aLENS_step_batch(aLENS_ctx* ctx, int32_t n_systems, const aLENS_system* systems,
                                         const int64_t* rod_offset, double* x, double* quat, const double* f_nc,
                                         int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info);
+
+/* Per-system results of the last aLENS_step_batch on this context: iters
+ * and residual are HOST arrays of n_systems entries (either may be NULL);
+ * n_systems must equal that call's.  For a batch of one system the values
+ * are those of its info.  Synchronises the context's stream. */
+ALENS_API aLENS_status aLENS_batch_results(aLENS_ctx* ctx, int32_t n_systems, int32_t* iters, double* residual);
+
+/* Launch shape of the per-system solver of aLENS_step_batch: threads per
+ * block (multiple of 32, <= 1024; default 1024) and blocks per cluster
+ * (1, 2, 4 or 8; default 8).  For tuning. */
+ALENS_API aLENS_status aLENS_set_batch_launch(aLENS_ctx* ctx, int32_t threads, int32_t cluster_blocks);
 
 /* Bound on every grid-wide wait inside the solver kernel, in seconds
  * (default 5).  A wait that runs out makes the call return ALENS_ERR_TIMEOUT. */

@@ -85,6 +85,8 @@ def lib():
             "aLENS_solve_lcp": (i32, [vp, i64, vp, i64, vp, vp, vp, vp, IP]),
             "aLENS_step": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, IP]),
             "aLENS_step_batch": (i32, [vp, i32, C.POINTER(System), C.POINTER(i64), vp, vp, vp, vp, vp, vp, IP]),
+            "aLENS_batch_results": (i32, [vp, i32, vp, vp]),
+            "aLENS_set_batch_launch": (i32, [vp, i32, i32]),
             "aLENS_set_wait_limit": (i32, [vp, d]),
             "aLENS_inject_fault": (i32, [vp, i32]),
             "aLENS_set_launch": (i32, [vp, i32, i32]),
@@ -274,3 +276,19 @@ class Context:
         if check and st != 0:
             raise AlensError(st, "aLENS_step_batch", info.as_dict())
         return info
+
+    def batch_results(self, n_systems: int):
+        """(iters [S] int32, residual [S] float64) numpy arrays of the last step_batch."""
+        import numpy as np
+        it = np.zeros(n_systems, dtype=np.int32)
+        res = np.zeros(n_systems, dtype=np.float64)
+        st = self._lib.aLENS_batch_results(self._h, int(n_systems), it.ctypes.data_as(C.c_void_p),
+                                           res.ctypes.data_as(C.c_void_p))
+        if st != 0:
+            raise AlensError(st, "aLENS_batch_results")
+        return it, res
+
+    def set_batch_launch(self, threads: int, cluster_blocks: int):
+        st = self._lib.aLENS_set_batch_launch(self._h, int(threads), int(cluster_blocks))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_batch_launch")

@@ -86,7 +86,7 @@ void free_all(aLENS_ctx* c)
                     c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand, c->keep,
                     c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->perm, c->rank, c->curP, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
                     c->q64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp,
-                    c->systab, c->sysid, c->sysoff};
+                    c->systab, c->sysid, c->sysoff, c->sys_order, c->sys_iters, c->sys_res};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free(c->batch_host);
@@ -219,11 +219,16 @@ aLENS_status batch_tables(aLENS_ctx* c, int ns, const aLENS_system* sys, const i
     if (st == ALENS_OK) st = grow_keys(c, keys);
     if (st == ALENS_OK && ns > c->max_systems) {
         cudaStreamSynchronize(c->stream);
-        if (c->systab) cudaFree(c->systab);
-        if (c->sysoff) cudaFree(c->sysoff);
-        c->systab = nullptr; c->sysoff = nullptr; c->max_systems = 0;
+        void* old[] = {c->systab, c->sysoff, c->sys_order, c->sys_iters, c->sys_res};
+        for (void* q : old)
+            if (q) cudaFree(q);
+        c->systab = nullptr; c->sysoff = nullptr; c->sys_order = nullptr; c->sys_iters = nullptr;
+        c->sys_res = nullptr; c->max_systems = 0;
         if (dmalloc(&c->systab, sizeof(SysGeo) * ns) != cudaSuccess ||
-            dmalloc(&c->sysoff, sizeof(long long) * (ns + 1)) != cudaSuccess) {
+            dmalloc(&c->sysoff, sizeof(long long) * (ns + 1)) != cudaSuccess ||
+            dmalloc(&c->sys_order, sizeof(int) * ns) != cudaSuccess ||
+            dmalloc(&c->sys_iters, sizeof(int) * ns) != cudaSuccess ||
+            dmalloc(&c->sys_res, sizeof(double) * ns) != cudaSuccess) {
             cudaGetLastError();
             st = ALENS_ERR_NOMEM;
         } else {
@@ -321,6 +326,8 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     c->wait_s = 5.0;
     c->solve_threads = 1024;
     c->solve_bps = 0;
+    c->batch_threads = 1024;
+    c->batch_cluster = 8;
     if (cudaGetDevice(&c->device) != cudaSuccess) { free(c); return ALENS_ERR_CUDA; }
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) { free(c); return ALENS_ERR_CUDA; }
@@ -633,6 +640,31 @@ aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const 
     return step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
 }
 
+aLENS_status aLENS_set_batch_launch(aLENS_ctx* c, int32_t threads, int32_t cluster_blocks)
+{
+    if (!c || threads < 32 || threads > 1024 || threads % 32 != 0) return ALENS_ERR_INVALID;
+    if (cluster_blocks != 1 && cluster_blocks != 2 && cluster_blocks != 4 && cluster_blocks != 8)
+        return ALENS_ERR_INVALID;
+    c->batch_threads = threads;
+    c->batch_cluster = cluster_blocks;
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_batch_results(aLENS_ctx* c, int32_t n_systems, int32_t* iters, double* residual)
+{
+    if (!c || n_systems < 1 || n_systems != c->last_batch_n) return ALENS_ERR_INVALID;
+    if (n_systems == 1) {
+        if (iters) iters[0] = c->hflags[F_ITERS];
+        if (residual) memcpy(residual, &c->hcount[C_RESID], sizeof(double));
+        return ALENS_OK;
+    }
+    if (iters) CK(cudaMemcpyAsync(iters, c->sys_iters, sizeof(int32_t) * n_systems, cudaMemcpyDeviceToHost, c->stream));
+    if (residual)
+        CK(cudaMemcpyAsync(residual, c->sys_res, sizeof(double) * n_systems, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ALENS_OK;
+}
+
 aLENS_status aLENS_step_batch(aLENS_ctx* c, int32_t n_systems, const aLENS_system* systems, const int64_t* rod_offset,
                               double* x, double* quat, const double* f_nc, int32_t* pairs_out, double* gamma_out,
                               double* vel_out, aLENS_info* info)
@@ -646,7 +678,9 @@ aLENS_status aLENS_step_batch(aLENS_ctx* c, int32_t n_systems, const aLENS_syste
     if (st != ALENS_OK) { single_mode(c); return st; }
     c->cur_systab = c->systab;
     c->cur_sysid = c->sysid;
+    c->last_batch_n = 0;
     st = step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
+    if (st == ALENS_OK || st == ALENS_ERR_NOT_CONVERGED) c->last_batch_n = n_systems;
     single_mode(c);
     return st;
 }

@@ -29,7 +29,8 @@ enum Flag : int {
     F_NFLAGS = 16
 };
 // 64-bit counters (Ctx::dcount)
-enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_SMEM = 6, C_NCOUNT = 8 };
+enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_SMEM = 6,
+                   C_QUEUE = 7, C_NCOUNT = 8 };
 
 // ------------------------------------------------------------ plain structs
 
@@ -268,6 +269,12 @@ struct aLENS_ctx {
     int batch_keys;          // their cell keys
     void* batch_host;        // host copy of the last aLENS_system array (to skip re-uploads)
     int64_t* batch_off_host; // host copy of the last rod offsets
+    int* sys_order;          // [max_systems] queue order of the per-system solver
+    int* sys_iters;          // [max_systems] iterations of each system's solve
+    double* sys_res;         // [max_systems] final residual of each system
+    int last_batch_n;        // systems of the last completed aLENS_step_batch (0: none)
+    int batch_threads;       // per-system solver: threads per block
+    int batch_cluster;       // per-system solver: blocks per cluster
 };
 
 namespace alens {

@@ -43,9 +43,12 @@
 // T = double (float64 plain) or float (mixed: the D, M, D^T work, per-thread
 // and per-warp sums in float32; the cross-warp and cross-block sums, the
 // residual test and the step sizes in float64; max |pi| is exact in either).
+#include <cooperative_groups.h>
 #include <float.h>
 
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace alens {
 
@@ -682,21 +685,77 @@ template <typename T>
 struct Shared {
     T red[32][4];
     double bc[4];
+    double part[4];   // this block's partial (cluster solver: read by the cluster's blocks)
     T alpha;
-    int done, ok, refresh;
+    int done, ok, refresh, cur, sys;
 };
 
-// Smallest rank r in [0, n] whose cumulative work W(r) = rowP[r] +
+// Synchronisation of the blocks that share one problem.
+// Grid: all blocks of a cooperative launch, bounded barrier on a global
+// counter, partials in global memory.
+struct GridSync {
+    unsigned* bar;
+    int* flags;
+    long long wait_cycles;
+    double* partials;
+    unsigned nb, epoch;
+    template <typename SH>
+    __device__ __forceinline__ bool barrier(SH& sh)
+    {
+        return grid_barrier(bar, nb * ++epoch, flags, wait_cycles, &sh.ok);
+    }
+    template <typename SH>
+    __device__ __forceinline__ double* slot(SH&) { return partials + 4 * (size_t)blockIdx.x; }
+    template <typename SH>
+    __device__ __forceinline__ void total(SH& sh, double tot[4]) { grid_total(partials, nb, sh.bc, tot); }
+};
+
+// Cluster: the blocks of one thread-block cluster, hardware cluster barrier,
+// partials in each block's shared memory read through distributed shared
+// memory (every block sums them in the same order: identical decisions).
+struct ClusterSync {
+    template <typename SH>
+    __device__ __forceinline__ bool barrier(SH&)
+    {
+        cg::this_cluster().sync();
+        return true;
+    }
+    template <typename SH>
+    __device__ __forceinline__ double* slot(SH& sh) { return sh.part; }
+    template <typename SH>
+    __device__ __forceinline__ void total(SH& sh, double tot[4])
+    {
+        cg::cluster_group cl = cg::this_cluster();
+        if (threadIdx.x < 4) {
+            const int u = threadIdx.x;
+            const unsigned cs = cl.num_blocks();
+            double w = 0.0;
+            for (unsigned r = 0; r < cs; ++r) {
+                const double x = cl.map_shared_rank(sh.part, r)[u];
+                w = u == 3 ? (x > w ? x : w) : w + x;
+            }
+            sh.bc[u] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tot[u] = sh.bc[u];
+    }
+};
+
+// Smallest rank r in [lo, hi] whose cumulative work W(r) = rowP[r] +
 // kOtherWork * rowQ[r] + kRodWork * r reaches target (an other-side entry,
 // gathered from another block, costs about twice an owned one); W is
-// strictly increasing and W(n) >= target.  One warp: 32 probes per round,
+// strictly increasing and W(hi) >= target.  One warp: 32 probes per round,
 // then a final scan of at most 32 ranks.
 constexpr int kRodWork = 2;
 constexpr int kOtherWork = 2;
-__device__ __forceinline__ int find_rank(const int* rowP, const int* rowQ, int n, long long target)
+__device__ __forceinline__ long long rank_work(const int* rowP, const int* rowQ, int r)
+{
+    return (long long)rowP[r] + (long long)kOtherWork * rowQ[r] + (long long)kRodWork * r;
+}
+__device__ __forceinline__ int find_rank(const int* rowP, const int* rowQ, int lo, int hi, long long target)
 {
     const int lane = threadIdx.x & 31;
-    int lo = 0, hi = n;
     while (hi - lo >= 32) {
         const long long span = hi - lo;
         const int p = lo + (int)(span * (lane + 1) / 33);
@@ -719,26 +778,28 @@ __device__ __forceinline__ int find_rank(const int* rowP, const int* rowQ, int n
     return m ? lo + __ffs(m) - 1 : hi;
 }
 
-template <typename T, bool ST>
-__device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& o, Shared<T>& sh)
+// The BBPGD loop over the problem shared by the blocks that SY synchronises.
+// On return thread 0 holds the step state; sh.cur is the final buffer.
+template <typename T, bool ST, typename SY>
+__device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& o, Shared<T>& sh, SY& sy,
+                                           StepState& st)
 {
-    const unsigned nb = gridDim.x;
-    double* mine = a.partials + 4 * (size_t)blockIdx.x;
-    unsigned epoch = 0;
+    double* mine = sy.slot(sh);
     double tot[4];
     T v[4];
-    StepState st;   // meaningful in thread 0 only
     st.alpha0 = 1.0;
+    st.cur = 0;
+    if (threadIdx.x == 0) sh.cur = 0;
 
     // gamma_0 is the reference (delta = 0): Uref = M D gamma_0, then
     // gref = q + D^T Uref = g_0 and the projected gradient at gamma_0
     phase_a<T, A_REF, ST>(a, o, 0, T(0));
-    if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+    if (!sy.barrier(sh)) return;
     v[0] = v[1] = v[2] = v[3] = T(0);
     phase_b<T, B_REF, ST>(a, o, 0, 0, v);
     block_partial(v, sh.red, mine);
-    if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
-    grid_total(a.partials, nb, sh.bc, tot);
+    if (!sy.barrier(sh)) return;
+    sy.total(sh, tot);
     if (threadIdx.x == 0) {
         st.res = a.hD * tot[3];
         st.iters = 0;
@@ -753,10 +814,10 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
         v[0] = phase_a<T, A_PG, ST>(a, o, 0, T(0));
         v[1] = v[2] = v[3] = T(0);
         // every block has read the partials (grid_total) before any rewrites them
-        if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+        if (!sy.barrier(sh)) return;
         block_partial(v, sh.red, mine);
-        if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
-        grid_total(a.partials, nb, sh.bc, tot);
+        if (!sy.barrier(sh)) return;
+        sy.total(sh, tot);
         if (threadIdx.x == 0) {
             const double pap = tot[0];
             double alpha0 = pp / pap;
@@ -769,12 +830,12 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
         for (int k = 0; k < a.max_iter; ++k) {
             const int nx = cur ^ 1;
             phase_a<T, A_STEP, ST>(a, o, cur, sh.alpha);
-            if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+            if (!sy.barrier(sh)) return;
             v[0] = v[1] = v[2] = v[3] = T(0);
             phase_b<T, B_STEP, ST>(a, o, cur, nx, v);
             block_partial(v, sh.red, mine);
-            if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
-            grid_total(a.partials, nb, sh.bc, tot);
+            if (!sy.barrier(sh)) return;
+            sy.total(sh, tot);
             cur = nx;
             if (threadIdx.x == 0) {
                 const double ss = tot[0], sy = tot[1], yy = tot[2];
@@ -800,14 +861,14 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
                 // recomputed from the split records with compensated sums, and
                 // max |pi| with them
                 fold_delta<T, ST>(a, o, cur);
-                if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+                if (!sy.barrier(sh)) return;
                 phase_a<T, A_REF, ST>(a, o, cur, T(0));
-                if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
+                if (!sy.barrier(sh)) return;
                 v[0] = v[1] = v[2] = v[3] = T(0);
                 phase_b<T, B_REF, ST>(a, o, cur, cur, v);
                 block_partial(v, sh.red, mine);
-                if (!grid_barrier(a.bar, nb * ++epoch, a.flags, a.wait_cycles, &sh.ok)) return;
-                grid_total(a.partials, nb, sh.bc, tot);
+                if (!sy.barrier(sh)) return;
+                sy.total(sh, tot);
                 if (threadIdx.x == 0) {
                     st.res = a.hD * tot[3];
                     st.done = !(st.res > a.tol);
@@ -818,12 +879,8 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
             }
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.out[1] = st.alpha0;
-        a.flags[F_FINAL] = st.cur;
-        a.flags[F_ITERS] = st.iters;
-        a.out[0] = st.res;
-    }
+    if (threadIdx.x == 0) sh.cur = st.cur;
+    __syncthreads();
 }
 
 // One warp per block boundary b in [0, nb]: the work-balanced split.
@@ -833,7 +890,7 @@ __global__ void k_partition(int n, int m, int nb, const int* __restrict__ rowP, 
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b > nb) return;   // uniform per warp
     const long long total = (1LL + kOtherWork) * m + (long long)kRodWork * n;
-    const int r = b == nb ? n : find_rank(rowP, rowQ, n, total * b / nb);
+    const int r = b == nb ? n : find_rank(rowP, rowQ, 0, n, total * b / nb);
     if ((threadIdx.x & 31) == 0) bstart[b] = r;
 }
 
@@ -870,7 +927,98 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd(SolveArgs<T> a)
         carve(o, dyn);
         stage_in(a, o);
     }
-    solve_loop<T, ST>(a, o, sh);
+    GridSync sy;
+    sy.bar = a.bar; sy.flags = a.flags; sy.wait_cycles = a.wait_cycles; sy.partials = a.partials;
+    sy.nb = gridDim.x; sy.epoch = 0;
+    StepState st;   // meaningful in thread 0 only
+    solve_loop<T, ST>(a, o, sh, sy, st);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.out[1] = st.alpha0;
+        a.flags[F_FINAL] = st.cur;
+        a.flags[F_ITERS] = st.iters;
+        a.out[0] = st.res;
+    }
+}
+
+// Batches: every cluster takes whole systems from a queue (largest first)
+// and runs the BBPGD of each on its own, with the system's own step sizes,
+// residual and stopping test.  A system's rods are the contiguous ranks
+// [sysoff[s], sysoff[s+1]) and its constraints the contiguous owner-major
+// range they own, so each block of the cluster takes a work-balanced share
+// of them exactly as the grid solver does.  The final state is left in
+// buffer 0; per-system iterations and residuals are written out, and the
+// largest of each into the step's counters.
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+k_bbpgd_sys(SolveArgs<T> a, int ns, const long long* __restrict__ sysoff, const int* __restrict__ order,
+            unsigned long long* __restrict__ queue, int* __restrict__ sys_iters, double* __restrict__ sys_res)
+{
+    __shared__ Shared<T> sh;
+    __shared__ int bounds[2];
+    cg::cluster_group cl = cg::this_cluster();
+    const int crank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
+    for (;;) {
+        if (crank == 0 && threadIdx.x == 0) {
+            const unsigned long long k = atomicAdd(queue, 1ull);
+            sh.sys = k < (unsigned long long)ns ? order[k] : -1;
+        }
+        cl.sync();
+        const int s = *cl.map_shared_rank(&sh.sys, 0);
+        cl.sync();   // every block has the id before block 0 takes the next one
+        if (s < 0) break;
+        const int R0 = (int)sysoff[s], R1 = (int)sysoff[s + 1];
+        if (threadIdx.x < 64) {   // warp w finds end w of this block's share
+            const int w = threadIdx.x >> 5, k = crank + w;
+            const long long W0 = rank_work(a.rowP, a.rowQ, R0), W1 = rank_work(a.rowP, a.rowQ, R1);
+            const int r = k == 0 ? R0 : (k == cs ? R1 : find_rank(a.rowP, a.rowQ, R0, R1, W0 + (W1 - W0) * k / cs));
+            if ((threadIdx.x & 31) == 0) bounds[w] = r;
+        }
+        __syncthreads();
+        Own<T> o;
+        o.r0 = bounds[0];
+        o.r1 = bounds[1];
+        o.c0 = a.rowP[o.r0];
+        o.c1 = a.rowP[o.r1];
+        o.q0 = a.rowQ[o.r0];
+        o.q1 = a.rowQ[o.r1];
+        o.cap_c = o.c1 - o.c0;
+        o.cap_r = o.r1 - o.r0;
+        o.cap_q = o.q1 - o.q0;
+        ClusterSync sy;
+        StepState st;
+        solve_loop<T, false>(a, o, sh, sy, st);
+        if (sh.cur == 1) {
+            for (int c = o.c0 + threadIdx.x; c < o.c1; c += blockDim.x) {
+                T d, g, gr, gl;
+                ld_state(a.gg1, c, d, g, gr, gl);
+                st_dg(a.gg0, c, d, g);
+                st_ref(a.gg0, c, gr, gl);
+            }
+        }
+        if (crank == 0 && threadIdx.x == 0) {
+            sys_iters[s] = st.iters;
+            sys_res[s] = st.res;
+            atomicMax(&a.flags[F_ITERS], st.iters);
+            const double r = st.res < 0.0 ? 0.0 : st.res;   // a NaN stays NaN (its bits order above every number)
+            atomicMax(reinterpret_cast<unsigned long long*>(a.out), (unsigned long long)__double_as_longlong(r));
+        }
+        __syncthreads();   // bounds and sh are rewritten for the next system
+    }
+}
+
+// Queue order of the systems: descending constraint count (ties by index).
+__global__ void k_sys_order(int ns, const long long* __restrict__ sysoff, const int* __restrict__ rowP,
+                            int* __restrict__ order)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    const int ms = rowP[sysoff[s + 1]] - rowP[sysoff[s]];
+    int pos = 0;
+    for (int t = 0; t < ns; ++t) {
+        const int mt = rowP[sysoff[t + 1]] - rowP[sysoff[t]];
+        pos += mt > ms || (mt == ms && t < s);
+    }
+    order[pos] = s;
 }
 
 // gamma back in the caller's pair order.
@@ -901,7 +1049,7 @@ cudaError_t launch_rank(aLENS_ctx* ctx, int n)
 }
 
 template <typename T>
-static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m)
+static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m)
 {
     SolveArgs<T> a;
     a.n = n; a.m = m; a.np = (int)ctx->max_rods; a.mp = (int)ctx->max_pairs;
@@ -920,6 +1068,15 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     a.rec_lo = sb.rec_lo; a.qe_lo = sb.qe_lo; a.q_lo = sb.q_lo;
     a.hD = ctx->p.dt / ctx->p.diameter; a.tol = ctx->p.tol; a.max_iter = ctx->p.max_iter;
     a.wait_cycles = (long long)(ctx->wait_s * ctx->clock_khz * 1e3);
+    a.fault = 0;
+    a.bstart = ctx->bstart;
+    return a;
+}
+
+template <typename T>
+static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m)
+{
+    SolveArgs<T> a = make_args(ctx, sb, n, m);
     a.fault = ctx->fault_mode;
     ctx->fault_mode = 0;
 
@@ -933,7 +1090,6 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     // work-balanced split, then the largest shared-memory share: stage every
     // block's data when all shares fit the opt-in budget (one readback)
     cudaError_t e;
-    a.bstart = ctx->bstart;
     const int nbw = (int)blocks + 1;
     k_partition<<<(nbw * 32 + 255) / 256, 256, 0, ctx->stream>>>(n, m, (int)blocks, ctx->rowP, ctx->rowQ, ctx->bstart);
     ++ctx->launches;
@@ -964,10 +1120,46 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, ctx->stream);
 }
 
+// Batches: the per-system solver on thread-block clusters (one launch).
+template <typename T>
+static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m)
+{
+    SolveArgs<T> a = make_args(ctx, sb, n, m);
+    ctx->fault_mode = 0;
+    const int ns = ctx->batch_n;
+    cudaError_t e;
+    k_sys_order<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(ns, ctx->sysoff, ctx->rowP, ctx->sys_order);
+    ++ctx->launches;
+    if ((e = cudaMemsetAsync(ctx->dcount + C_QUEUE, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ctx->batch_cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3((unsigned)ctx->batch_threads);
+    cfg.gridDim = dim3((unsigned)ctx->batch_cluster);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(&nclusters, k_bbpgd_sys<T>, &cfg)) != cudaSuccess) return e;
+    if (nclusters < 1) return cudaErrorInvalidConfiguration;
+    if (nclusters > ns) nclusters = ns;   // a cluster per system at most
+    cfg.gridDim = dim3((unsigned)(nclusters * ctx->batch_cluster));
+    ++ctx->launches;
+    return cudaLaunchKernelEx(&cfg, k_bbpgd_sys<T>, a, ns, (const long long*)ctx->sysoff, (const int*)ctx->sys_order,
+                              ctx->dcount + C_QUEUE, ctx->sys_iters, ctx->sys_res);
+}
+
 cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision)
 {
-    if (precision == ALENS_MIXED) return solve_typed<float>(ctx, ctx->sb32, n, m);
-    return solve_typed<double>(ctx, ctx->sb64, n, m);
+    const bool per_system = ctx->cur_systab != nullptr && ctx->batch_n > 1;
+    if (precision == ALENS_MIXED)
+        return per_system ? solve_batch_typed<float>(ctx, ctx->sb32, n, m) : solve_typed<float>(ctx, ctx->sb32, n, m);
+    return per_system ? solve_batch_typed<double>(ctx, ctx->sb64, n, m) : solve_typed<double>(ctx, ctx->sb64, n, m);
 }
 
 cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma_out)

@@ -29,7 +29,9 @@ of thousands of filaments in periodic boxes, isotropic or nematic):
                      isotropic, thermal forces.
   ``ensemble256``    256 independent systems, rod counts log-uniform in
                      [500, 20000], lengths log-uniform in [5, 20], volume
-                     fraction uniform in [0.05, 0.20], thermal forces.
+                     fraction uniform in [0.05, 0.20], axes nematic about
+                     a random director per system (spread 0.1 rad),
+                     thermal forces.
 """
 from __future__ import annotations
 
@@ -82,12 +84,27 @@ def unit_axes_isotropic(rng: np.random.Generator, n: int) -> np.ndarray:
     return v / np.linalg.norm(v, axis=1, keepdims=True)
 
 
-def unit_axes_nematic(rng: np.random.Generator, n: int, spread: float = 0.1) -> np.ndarray:
-    """Axes about +z with a Gaussian angular spread: (spread*xi1, spread*xi2, 1) normalised."""
+def unit_axes_nematic(rng: np.random.Generator, n: int, spread: float = 0.1, director=None) -> np.ndarray:
+    """Axes about +z with a Gaussian angular spread: (spread*xi1, spread*xi2, 1)
+    normalised; then, if a unit ``director`` is given, turned by the rotation
+    taking e_z onto it (Rodrigues' formula about e_z x director)."""
     v = np.empty((n, 3))
     v[:, 0:2] = spread * rng.standard_normal((n, 2))
     v[:, 2] = 1.0
-    return v / np.linalg.norm(v, axis=1, keepdims=True)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    if director is not None:
+        d = np.asarray(director, dtype=np.float64)
+        d = d / np.linalg.norm(d)
+        k = np.array([-d[1], d[0], 0.0])      # e_z x d
+        sn, cs = np.linalg.norm(k), d[2]
+        if sn > 1e-12:
+            k /= sn
+            kv = np.cross(k, v)
+            v = v * cs + kv * sn + np.outer(v @ k, k) * (1.0 - cs)
+        elif cs < 0:
+            v = -v
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v
 
 
 def quat_from_axis(axis: np.ndarray) -> np.ndarray:
@@ -176,7 +193,7 @@ def spring_forces(rng: np.random.Generator, x: np.ndarray, axis: np.ndarray, box
 
 
 def random_system(seed: int, n: int, box, *, length: float = 10.0, diameter: float = 1.0,
-                  nematic_spread: float | None = None, forces: str = "unit",
+                  nematic_spread: float | None = None, director=None, forces: str = "unit",
                   n_springs: int = 0, viscosity: float = 1.0, dt: float = 1e-3,
                   delta_c: float | None = None, tol: float = 1e-8, name: str = "") -> RodSystem:
     """Uniform centres in [0, box)^3 and isotropic (or nematic) axes.
@@ -189,7 +206,8 @@ def random_system(seed: int, n: int, box, *, length: float = 10.0, diameter: flo
     boxt = tuple(float(b) for b in (box if np.ndim(box) else (box, box, box)))
     x = rng.uniform(0.0, 1.0, size=(n, 3)) * np.asarray(boxt)
     x = np.where(x >= np.asarray(boxt), 0.0, x)
-    axis = unit_axes_isotropic(rng, n) if nematic_spread is None else unit_axes_nematic(rng, n, nematic_spread)
+    axis = (unit_axes_isotropic(rng, n) if nematic_spread is None
+            else unit_axes_nematic(rng, n, nematic_spread, director))
     quat = quat_from_axis(axis)
     if forces == "unit":
         f = rng.standard_normal((n, 6))
@@ -243,28 +261,34 @@ def workload(name: str, **kw) -> RodSystem:
     return WORKLOADS[name](**kw)
 
 
+ENSEMBLE_SPREAD = 0.1   # angular spread (rad) of every ensemble system about its director
+
+
 def ensemble_specs(seed: int = 1000, count: int = 256):
-    """Per-system (n, length, phi, seed) of the batched ensemble."""
+    """Per-system (n, length, phi, seed, director) of the batched ensemble."""
     rng = np.random.default_rng(seed)
     n = np.exp(rng.uniform(math.log(500), math.log(20000), size=count)).astype(np.int64)
     length = np.exp(rng.uniform(math.log(5.0), math.log(20.0), size=count))
     phi = rng.uniform(0.05, 0.20, size=count)
-    return [(int(n[s]), float(length[s]), float(phi[s]), seed + s) for s in range(count)]
+    director = unit_axes_isotropic(rng, count)
+    return [(int(n[s]), float(length[s]), float(phi[s]), seed + s, director[s]) for s in range(count)]
 
 
 def ensemble(seed: int = 1000, count: int = 256, scale: float = 1.0) -> list[RodSystem]:
-    """The batched ensemble: independent periodic systems of uneven size.
+    """The batched ensemble: independent periodic systems of uneven size,
+    each a nematic domain about its own random director (spread
+    ENSEMBLE_SPREAD), uniform centres and thermal forces.
 
     ``scale`` < 1 shrinks every rod count (for quick tests); lengths and
-    volume fractions are kept.
+    volume fractions are kept (boxes never below L + 2 D).
     """
     out = []
-    for n, length, phi, s in ensemble_specs(seed, count):
+    for n, length, phi, s, director in ensemble_specs(seed, count):
         n_s = max(2, int(round(n * scale)))
         box = box_for_fraction(n_s, 1.0, length, phi)
         box = max(box, length + 2.0 + 1e-6)
-        out.append(random_system(s, n_s, box, length=length, forces="thermal", tol=1e-5,
-                                 name=f"ensemble_{s}"))
+        out.append(random_system(s, n_s, box, length=length, nematic_spread=ENSEMBLE_SPREAD, director=director,
+                                 forces="thermal", tol=1e-5, name=f"ensemble_{s}"))
     return out
 
 

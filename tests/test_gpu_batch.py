@@ -62,6 +62,10 @@ def run_batch(systems, precision, tol):
         gam = torch.empty(ctx.max_pairs, dtype=torch.float64, device="cuda")
         info = ctx.step_batch(spec, off, xd, qd, dev(fnc), pairs_out=pr, gamma_out=gam, vel_out=vel[:n])
         m = info.n_pairs
+        its, res = ctx.batch_results(len(systems))
+        # the aggregate is the worst system
+        assert info.iters == its.max() and info.residual == res.max()
+        assert np.all(res <= tol)
         return off, host(xd), host(qd), host(pr)[:m], host(gam)[:m], host(vel)[:n], info
 
 
@@ -110,8 +114,9 @@ def test_batch_matches_oracle_per_system(precision, tol, xbar, ubar):
 
 @pytest.mark.parametrize("precision", [A.FP64, A.MIXED])
 def test_batch_of_one_equals_single_step(precision):
-    # one system through the batch tables (per-system geometry, per-rod drags)
-    # must reproduce the single-system step bit for bit
+    # one system through the batch tables (per-system geometry, per-rod drags;
+    # a batch of one uses the single-system solver) must reproduce the
+    # single-system step bit for bit
     s = W.tiny_system(5, 60, box=11.0, length=3.0)
     s.f_nc *= 30.0
     tol = 1e-10 if precision == A.FP64 else 1e-6
@@ -182,8 +187,9 @@ def test_batch_rejects_bad_tables():
 
 
 def test_full_ensemble_sampled_systems():
-    # the 256-system ensemble (about 1.3 million rods, float32 iterations):
-    # the smallest, a middle and the largest system against the oracle
+    # the 256-system ensemble (about 1.3 million rods, float32 iterations,
+    # every system solved to the tolerance on its own): the smallest, a
+    # middle and the largest system against the oracle
     systems = W.ensemble(seed=1000, count=256)
     tol = 1e-5
     off, x, q, pairs, gam, vel, info = run_batch(systems, A.MIXED, tol)
