@@ -5,6 +5,8 @@ One step = neighbour search + constraint assembly + BBPGD solve + update
 isotropic, thermal forces plus 50,000 explicit crosslinker springs; seeded,
 synthetic).  Every timed step starts from the same input state, restored
 outside the timed region, and L2 is flushed (256 MB write) between steps.
+``--workload ensemble256`` times the batched step (aLENS_step_batch) of the
+256-system ensemble instead (about 1.28 million rods in one call).
 
 Reported (one JSON line on rank 0):
   value        rod-steps/s of the FP32-mixed step at residual <= 1e-5 (device
@@ -42,6 +44,11 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "rod-steps/s at 1e5 rods, FP32-mixed vs FP64 plain at residual ≤1e-5"
+METRIC_ENSEMBLE = "rod-steps/s of the 256-system batched ensemble (one call), FP32-mixed vs FP64 plain at residual ≤1e-5"
+
+
+def metric_of(workload):
+    return METRIC_ENSEMBLE if workload == "ensemble256" else METRIC
 UNIT = "rod-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -58,6 +65,7 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--sample-rods", type=int, default=10000, help="rods in the oracle's spatial sample")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default solver launch shape")
     return ap.parse_args()
 
 
@@ -175,6 +183,122 @@ def spatial_sample(s, target):
     return sub, a
 
 
+def ensemble_sample(systems, target, seed=7):
+    """Systems of the ensemble in a seeded random order until about `target`
+    rods are taken (the oracle's CPU sample of the batched workload)."""
+    rng = np.random.default_rng(seed)
+    take, rods = [], 0
+    for k in rng.permutation(len(systems)):
+        if rods >= target:
+            break
+        take.append(int(k))
+        rods += systems[k].n
+    return take, rods
+
+
+class SingleJob:
+    """One system stepped by aLENS_step."""
+
+    def __init__(self, s):
+        self.s = s
+        self.n = s.n
+        self.name = s.name
+
+    def context(self, A, precision, tol, stream):
+        p = A.params_of(self.s, precision=precision, tol=tol, max_iter=1_000_000)
+        return A.Context(p, self.n, 12 * self.n, stream=stream)
+
+    def step(self, ctx, x, q, f, **kw):
+        return ctx.step(x, q, f, **kw)
+
+    def tune(self, T, ctx, x, q, f, precision):
+        return T.tune_single(ctx, x, q, f, precision)
+
+    def solve_bytes(self, ctx, info, w):
+        """Algorithmic bytes of the BBPGD launch of the last step."""
+        return info["iters"] * solve_bytes_per_iter(self.n, info["n_pairs"], w)
+
+    def arrays(self):
+        return self.s.x, self.s.quat, self.s.f_nc
+
+    def periodic_box(self):
+        return np.broadcast_to(np.asarray(self.s.box, dtype=np.float64), (self.n, 3))
+
+    def config(self, W, m):
+        s = self.s
+        return {"workload": s.name, "rods": self.n, "pairs": m, "box": round(float(s.box[0]), 3),
+                "volume_fraction": round(self.n * W.rod_volume(s.diameter, s.length) / float(np.prod(s.box)), 4),
+                "springs": s.meta.get("springs")}
+
+    def cpu(self, args):
+        sub, a = spatial_sample(self.s, args.sample_rods)
+        t_cpu, out = oracle_step_time(sub, args.tol)
+        return sub.n, t_cpu, (f"{sub.n} rods of {self.s.name} with centres in a periodic sub-cube of edge {a:.2f}; "
+                              f"one full oracle step (brute-force pairs, FISTA to residual {args.tol:g}, update), "
+                              f"{t_cpu:.2f} s")
+
+
+class BatchJob:
+    """The ensemble stepped by one aLENS_step_batch call."""
+
+    def __init__(self, systems):
+        from paper_2109_08206_gb300 import workloads as W
+        self.systems = systems
+        self.off, self.x, self.quat, self.f_nc, self.spec = W.batch_arrays(systems)
+        self.n = int(self.off[-1])
+        self.name = f"ensemble{len(systems)}"
+        self.ms = None   # per-system constraint counts (set by the first step with pairs_out)
+
+    def context(self, A, precision, tol, stream):
+        s0 = self.systems[0]
+        p = A.make_params(s0.box, s0.diameter, s0.length, s0.viscosity, s0.dt, s0.delta_c, tol, 1_000_000,
+                          precision)
+        return A.Context(p, self.n, 12 * self.n, stream=stream)
+
+    def step(self, ctx, x, q, f, **kw):
+        return ctx.step_batch(self.spec, self.off, x, q, f, **kw)
+
+    def tune(self, T, ctx, x, q, f, precision):
+        return T.tune_batch(ctx, self.spec, self.off, x, q, f, precision)
+
+    def count_pairs(self, pairs):
+        sys_i = np.searchsorted(self.off, pairs[:, 0], side="right") - 1
+        self.ms = np.bincount(sys_i, minlength=len(self.systems))
+
+    def solve_bytes(self, ctx, info, w):
+        its, _ = ctx.batch_results(len(self.systems))
+        ns = np.diff(self.off)
+        return float(np.sum(its * (self.ms * (24 * w + 24) + ns * (15 * w + 4))))
+
+    def arrays(self):
+        return self.x, self.quat, self.f_nc
+
+    def periodic_box(self):
+        return np.repeat(np.asarray([s.box for s in self.systems], dtype=np.float64), np.diff(self.off), axis=0)
+
+    def config(self, W, m):
+        return {"workload": self.name, "systems": len(self.systems), "rods": self.n, "pairs": m,
+                "rods_per_system": [int(np.diff(self.off).min()), int(np.diff(self.off).max())],
+                "orientation": f"nematic domains, spread {W.ENSEMBLE_SPREAD} rad about a random director each"}
+
+    def cpu(self, args):
+        take, rods = ensemble_sample(self.systems, args.sample_rods)
+        t_cpu = 0.0
+        for k in take:
+            t, _ = oracle_step_time(self.systems[k], args.tol)
+            t_cpu += t
+        return rods, t_cpu, (f"{len(take)} whole systems of the ensemble ({rods} rods, seeded random pick), "
+                             f"each one full oracle step (brute-force pairs, FISTA to residual {args.tol:g}, "
+                             f"update), {t_cpu:.2f} s in total")
+
+
+def make_job(name):
+    from paper_2109_08206_gb300 import workloads as W
+    if name == "ensemble256":
+        return BatchJob(W.ensemble(seed=1000, count=256))
+    return SingleJob(W.workload(name))
+
+
 def oracle_step_time(s, tol, reps=1):
     import oracle as O
     pb = O.problem_of(s)
@@ -215,25 +339,20 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from paper_2109_08206_gb300 import workloads as W
-    s = W.workload(args.workload)
-    sub, a = spatial_sample(s, args.sample_rods)
+    job = make_job(args.workload)
     for _ in range(max(0, min(args.warmup, 1))):
-        oracle_step_time(sub, args.tol)
+        job.cpu(args)
     times = []
     for _ in range(args.steps):
-        t, out = oracle_step_time(sub, args.tol)
+        rods, t, sample = job.cpu(args)
         times.append(t)
     t = statistics.mean(times)
-    v = sub.n / t
-    sample = (f"{sub.n} rods of the {s.name} workload with centres in a periodic sub-cube of edge {a:.2f} "
-              f"(same density, orientations, forces); full oracle step (brute-force pairs, FISTA to the same "
-              f"residual {args.tol:g}, update)")
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+    v = rods / t
+    line = {"impl": "reference", "metric": metric_of(args.workload), "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload} (oracle on a {sub.n}-rod sample)", "rods": sub.n,
-                       "pairs": int(out["n_pairs"]), "tol": args.tol},
+            "config": {"workload": f"{args.workload} (oracle on a {rods}-rod sample)", "rods": rods,
+                       "tol": args.tol},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -255,24 +374,25 @@ def run_ours(args):
         pg = dist
     A.build()
     dev = torch.device("cuda", local)
-    s = W.workload(args.workload)
-    n = s.n
+    job = make_job(args.workload)
+    n = job.n
+    hx0, hq0, hf0 = job.arrays()
     stream = torch.cuda.Stream(device=dev)
-    x0 = torch.as_tensor(s.x, device=dev)
-    q0 = torch.as_tensor(s.quat, device=dev)
-    f = torch.as_tensor(s.f_nc, device=dev)
+    x0 = torch.as_tensor(hx0, device=dev)
+    q0 = torch.as_tensor(hq0, device=dev)
+    f = torch.as_tensor(hf0, device=dev)
     x, q = x0.clone(), q0.clone()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     max_pairs = 12 * n
 
     def make_ctx(precision):
-        p = A.params_of(s, precision=precision, tol=args.tol, max_iter=1_000_000)
-        return A.Context(p, n, max_pairs, stream=stream)
+        return job.context(A, precision, args.tol, stream)
 
-    def timed(ctx, K, W_, host=None):
-        """K timed steps after W_ warm-ups; returns per-step ms and infos."""
+    def timed(ctx, K, W_, host=None, w=4):
+        """K timed steps after W_ warm-ups; returns per-step ms, infos and the
+        algorithmic bytes of each step's BBPGD launch."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        infos = []
+        infos, sbytes = [], []
         with torch.cuda.stream(stream):
             for k in range(W_ + K):
                 if host is None:
@@ -281,17 +401,18 @@ def run_ours(args):
                 if k >= W_:
                     ev[k - W_][0].record(stream)
                 if host is None:
-                    info = ctx.step(x, q, f)
+                    info = job.step(ctx, x, q, f)
                 else:
                     hx, hq, hf, ox, oq = host
                     x.copy_(hx, non_blocking=True); q.copy_(hq, non_blocking=True); f.copy_(hf, non_blocking=True)
-                    info = ctx.step(x, q, f)
+                    info = job.step(ctx, x, q, f)
                     ox.copy_(x, non_blocking=True); oq.copy_(q, non_blocking=True)
                 if k >= W_:
                     ev[k - W_][1].record(stream)
                     infos.append(info.as_dict())
+                    sbytes.append(job.solve_bytes(ctx, infos[-1], w))
             stream.synchronize()
-        return [a.elapsed_time(b) for a, b in ev], infos
+        return [a.elapsed_time(b) for a, b in ev], infos, sbytes
 
     def barrier():
         torch.cuda.synchronize()
@@ -301,8 +422,24 @@ def run_ours(args):
     def max_over_ranks(v):
         return replica_time(v, pg, dev)
 
-    # ---- FP32-mixed: the headline
+    # ---- untimed: the solver's launch shape (autotuned) and, for a batch,
+    # the per-system constraint counts
+    import paper_2109_08206_gb300.autotune as T
     ctx = make_ctx(A.MIXED)
+    tuned = None
+    if not args.no_tune:
+        xx, qq = x0.clone(), q0.clone()
+        shape, times = job.tune(T, ctx, xx, qq, f, A.MIXED)
+        tuned = {"shape": list(shape), "ms_solve": times}
+        del xx, qq
+    if isinstance(job, BatchJob):
+        pr = torch.empty((max_pairs, 3), dtype=torch.int32, device=dev)
+        xx, qq = x0.clone(), q0.clone()
+        inf = job.step(ctx, xx, qq, f, pairs_out=pr)
+        job.count_pairs(pr[: inf.n_pairs].cpu().numpy())
+        del pr, xx, qq
+
+    # ---- FP32-mixed: the headline
     barrier()
     try:
         gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
@@ -311,7 +448,7 @@ def run_ours(args):
         gpu_id = None
     clk = Clocks(gpu_id).__enter__()   # sampled across every timed region below
     t0 = time.perf_counter()
-    ms, infos = timed(ctx, args.steps, args.warmup)
+    ms, infos, sbytes = timed(ctx, args.steps, args.warmup)
     barrier()
     wall = time.perf_counter() - t0
     ms_step = max_over_ranks(statistics.mean(ms))
@@ -322,7 +459,7 @@ def run_ours(args):
     res = max(i["residual"] for i in infos)
     launches = sum(i["launches"] for i in infos)
     b_iter = solve_bytes_per_iter(n, m, 4)
-    alg_bytes = statistics.mean(it) * b_iter
+    alg_bytes = statistics.mean(sbytes)
     peak, peak_kind = peaks()
     achieved = alg_bytes / (ms_solve / 1e3) / 1e9
     tr = traffic_from_profile(ROOT / "paper_2109_08206_gb300" / "csrc" / "solve.cu") \
@@ -333,22 +470,26 @@ def run_ours(args):
     fp64 = None
     if not args.skip_fp64:
         ctx64 = make_ctx(A.FP64)
-        ms64, inf64 = timed(ctx64, max(2, args.steps // 2), 1)
+        if not args.no_tune:
+            xx, qq = x0.clone(), q0.clone()
+            job.tune(T, ctx64, xx, qq, f, A.FP64)
+            del xx, qq
+        ms64, inf64, sb64 = timed(ctx64, max(2, args.steps // 2), 1, w=8)
         ms64_step = max_over_ranks(statistics.mean(ms64))
         fp64 = {"value": replica_value(ms64_step, n, ws), "unit": UNIT, "ms_per_step": ms64_step,
                 "bbpgd_iters": statistics.mean(i["iters"] for i in inf64),
                 "residual": max(i["residual"] for i in inf64),
                 "ms_solve": statistics.mean(i["ms_solve"] for i in inf64),
-                "solve_bytes_per_iter": solve_bytes_per_iter(n, m, 8)}
+                "solve_bytes_per_launch": statistics.mean(sb64)}
         ctx64.close()
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.skip_e2e:
-        hx = torch.as_tensor(s.x).pin_memory(); hq = torch.as_tensor(s.quat).pin_memory()
-        hf = torch.as_tensor(s.f_nc).pin_memory()
+        hx = torch.as_tensor(hx0).pin_memory(); hq = torch.as_tensor(hq0).pin_memory()
+        hf = torch.as_tensor(hf0).pin_memory()
         ox = torch.empty_like(hx).pin_memory(); oq = torch.empty_like(hq).pin_memory()
-        mse, _ = timed(ctx, args.steps, 1, host=(hx, hq, hf, ox, oq))
+        mse, _, _ = timed(ctx, args.steps, 1, host=(hx, hq, hf, ox, oq))
         mse_step = max_over_ranks(statistics.mean(mse))
         e2e = {"value": replica_value(mse_step, n, ws), "unit": UNIT, "ms_per_step": mse_step,
                "h2d_bytes_per_step": int(hx.numel() * 8 + hq.numel() * 8 + hf.numel() * 8),
@@ -363,14 +504,14 @@ def run_ours(args):
             c2 = make_ctx(prec)
             xx, qq = x0.clone(), q0.clone()
             gam = torch.empty(max_pairs, dtype=torch.float64, device=dev)
-            inf = c2.step(xx, qq, f, gamma_out=gam)
+            inf = job.step(c2, xx, qq, f, gamma_out=gam)
             outs[prec] = (xx, qq, gam[: inf.n_pairs].clone())
             c2.close()
         dx = outs[A.MIXED][0] - outs[A.FP64][0]
-        boxt = torch.tensor(s.box, dtype=torch.float64, device=dev)
+        boxt = torch.as_tensor(job.periodic_box(), device=dev)
         dx = dx - boxt * torch.round(dx / boxt)
         g32, g64 = outs[A.MIXED][2], outs[A.FP64][2]
-        mixed_vs_fp64 = {"max_dx_over_D": float(dx.abs().max()) / s.diameter,
+        mixed_vs_fp64 = {"max_dx_over_D": float(dx.abs().max()),
                          "gamma_rel_l2": float(torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64)),
                          "max_dquat": float((outs[A.MIXED][1] - outs[A.FP64][1]).abs().max())}
     ctx.close()
@@ -379,24 +520,23 @@ def run_ours(args):
         return
     cpu = None
     if not args.skip_cpu and ws == 1:
-        sub, a = spatial_sample(s, args.sample_rods)
-        t_cpu, out = oracle_step_time(sub, args.tol)
-        cpu = {"value": sub.n / t_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"{sub.n} rods of {s.name} with centres in a periodic sub-cube of edge {a:.2f}; one full "
-                         f"oracle step (brute-force pairs, FISTA to residual {args.tol:g}, update), {t_cpu:.2f} s"}
+        rods, t_cpu, sample = job.cpu(args)
+        cpu = {"value": rods / t_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample}
+    kernel = "k_bbpgd_sys<float>" if isinstance(job, BatchJob) else "k_bbpgd<float>"
+    config = job.config(W, m)
+    config.update({"tol": args.tol,
+                   "l2": "flushed (256 MB write) between steps; inputs restored outside the timed region",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"})
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "metric": metric_of(args.workload), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32-mixed (f64 geometry, residual, reductions)", "data": "synthetic",
-        "config": {"workload": s.name, "rods": n, "pairs": m, "box": round(float(s.box[0]), 3),
-                   "volume_fraction": round(n * W.rod_volume(s.diameter, s.length) / float(np.prod(s.box)), 4), "springs": s.meta.get("springs"), "tol": args.tol,
-                   "l2": "flushed (256 MB write) between steps; inputs restored outside the timed region",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "bbpgd_iters": statistics.mean(it), "residual": res,
+        "config": config,
+        "bbpgd_iters": statistics.mean(it), "residual": res, "launch_shape": tuned,
         "phase_ms": {k: statistics.mean(i[k] for i in infos) for k in ("ms_build", "ms_assemble", "ms_solve",
                                                                          "ms_update")},
         "fp64": fp64, "e2e": e2e, "mixed_vs_fp64": mixed_vs_fp64,
-        "roofline": {"kernel": "k_bbpgd<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_iter": b_iter},
         "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary(), "wall_s": wall,

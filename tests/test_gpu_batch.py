@@ -207,3 +207,18 @@ def test_full_ensemble_sampled_systems():
         U = vel[lo:hi]
         assert np.linalg.norm(U - ref["U"]) <= 1e-3 * np.linalg.norm(ref["U"]), s.name
         assert np.abs(periodic_diff(x[lo:hi], ref["x"], s.box)).max() <= 1e-4 * s.diameter, s.name
+
+
+def test_autotune_batch_picks_and_caches():
+    import paper_2109_08206_gb300.autotune as T
+    systems = small_batch()
+    off, x, quat, fnc, spec = W.batch_arrays(systems)
+    xd, qd, fd = dev(x), dev(quat), dev(fnc)
+    with batch_ctx(systems, A.MIXED, 1e-6) as ctx:
+        shape, times = T.tune_batch(ctx, spec, off, xd, qd, fd, A.MIXED)
+        assert shape in T.BATCH_CANDIDATES and len(times) == len(T.BATCH_CANDIDATES)
+        assert np.array_equal(host(xd), x)   # inputs restored
+        info = ctx.step_batch(spec, off, xd, qd, fd)
+        assert info.status == 0
+        assert T.apply_cached(ctx, "batch", A.MIXED, int(off[-1]), info.n_pairs, len(systems))
+
