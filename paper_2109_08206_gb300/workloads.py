@@ -26,7 +26,8 @@ of thousands of filaments in periodic boxes, isotropic or nematic):
   ``n400k_nematic``  400,000 rods, volume fraction 0.25 (box 237.5),
                      axes ~ (0.1 xi1, 0.1 xi2, 1) normalised, thermal forces.
   ``n20k_phi015``    20,000 rods, volume fraction 0.15 (box 103.8),
-                     isotropic, thermal forces.
+                     isotropic, thermal forces (the differentiation
+                     workload; ``loss_targets`` draws its loss targets).
   ``ensemble256``    256 independent systems, rod counts log-uniform in
                      [500, 20000], lengths log-uniform in [5, 20], volume
                      fraction uniform in [0.05, 0.20], axes nematic about
@@ -290,6 +291,13 @@ def ensemble(seed: int = 1000, count: int = 256, scale: float = 1.0) -> list[Rod
         out.append(random_system(s, n_s, box, length=length, nematic_spread=ENSEMBLE_SPREAD, director=director,
                                  forces="thermal", tol=1e-5, name=f"ensemble_{s}"))
     return out
+
+
+def loss_targets(s: RodSystem, seed: int = 11, sigma: float = 0.01) -> np.ndarray:
+    """Seeded targets of the differentiation workload's loss: the initial
+    centres displaced by N(0, sigma^2) per component."""
+    rng = np.random.default_rng(seed)
+    return s.x + sigma * rng.standard_normal(s.x.shape)
 
 
 def batch_arrays(systems: list[RodSystem]):
