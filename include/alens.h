@@ -201,6 +201,41 @@ ALENS_API aLENS_status aLENS_step_batch(aLENS_ctx* ctx, int32_t n_systems, const
                                         const int64_t* rod_offset, double* x, double* quat, const double* f_nc,
                                         int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info);
 
+/* ------------------------------------------------------------------------
+ * Adjoint of aLENS_step (reverse-mode gradient of a scalar loss L(x', quat')
+ * of the post-step state).  The paper does not differentiate its step; this
+ * differentiates the same step (Appendix Eq. constrainedeom_euler a-c with
+ * the constraint problem of Eq. suppcqpdef) on the forward step's pair list
+ * and active set {c : gamma_c > 0}, where the KKT conditions read
+ * (D^T M D gamma + q)_c = 0:
+ *   u = dL/dU through the update; b = D^T M u; lambda solves
+ *   (D^T M D)_AA lambda_A = b_A by conjugate gradients (from 0: the
+ *   minimum-norm multiplier when the block is singular); then the
+ *   derivatives of q, D (closest points on their branch: both parameters
+ *   free, one clamped, both clamped; parallel segments with s*, t* held)
+ *   and of M (axes, viscosity).
+ * x, quat, f_nc: the state the forward aLENS_step started from (device,
+ *   as for aLENS_step; the caller keeps a copy, aLENS_step overwrote them).
+ * pairs [n_pairs][3], gamma [n_pairs]: that step's pairs_out and gamma_out.
+ * dL_dx_new [n][3], dL_dquat_new [n][4]: dL/dx' and dL/dquat' (either may
+ *   be NULL = zero).  x' is the unwrapped x + h U_t.
+ * Outputs (device): dL_dx [n][3]; dL_dquat [n][4], the gradient projected
+ *   onto the unit quaternion's tangent space; dL_dfnc [n][6] (nullable);
+ *   dL_deta (HOST pointer, nullable): derivative with respect to the
+ *   viscosity, to which every drag coefficient is proportional.
+ * The CG operator runs in the context's precision (float32 records in mixed
+ * mode), everything else in float64.  info: iters = CG iterations,
+ * residual = final relative CG residual |r|/|b_A| (tolerance 1e-13 in
+ * FP64, 1e-7 mixed; NOT_CONVERGED with the outputs filled if max_iter CG
+ * iterations did not reach it).  The first call allocates the adjoint's
+ * workspace (46 doubles per rod and 13 per constraint of the context's capacity).
+ * Single systems only (batches: call it per system). */
+ALENS_API aLENS_status aLENS_step_adjoint(aLENS_ctx* ctx, int64_t n, const double* x, const double* quat,
+                                          const double* f_nc, int64_t n_pairs, const int32_t* pairs,
+                                          const double* gamma, const double* dL_dx_new, const double* dL_dquat_new,
+                                          double* dL_dx, double* dL_dquat, double* dL_dfnc, double* dL_deta,
+                                          aLENS_info* info);
+
 /* Per-system results of the last aLENS_step_batch on this context: iters
  * and residual are HOST arrays of n_systems entries (either may be NULL);
  * n_systems must equal that call's.  For a batch of one system the values

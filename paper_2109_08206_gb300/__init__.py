@@ -86,6 +86,8 @@ def lib():
             "aLENS_step": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, IP]),
             "aLENS_step_batch": (i32, [vp, i32, C.POINTER(System), C.POINTER(i64), vp, vp, vp, vp, vp, vp, IP]),
             "aLENS_batch_results": (i32, [vp, i32, vp, vp]),
+            "aLENS_step_adjoint": (i32, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp,
+                                         C.POINTER(d), IP]),
             "aLENS_set_batch_launch": (i32, [vp, i32, i32]),
             "aLENS_set_wait_limit": (i32, [vp, d]),
             "aLENS_inject_fault": (i32, [vp, i32]),
@@ -292,3 +294,27 @@ class Context:
         st = self._lib.aLENS_set_batch_launch(self._h, int(threads), int(cluster_blocks))
         if st != 0:
             raise AlensError(st, "aLENS_set_batch_launch")
+
+    def step_adjoint(self, x, quat, f_nc, pairs, gamma, dL_dx_new=None, dL_dquat_new=None, check=True):
+        """Gradient of a loss of the post-step state through one aLENS_step.
+
+        x, quat, f_nc: the state the forward step started from; pairs, gamma:
+        its pairs_out and gamma_out (device, first n_pairs rows).  Returns
+        (dL/dx [n,3], dL/dquat [n,4] (tangent), dL/dF_nc [n,6], dL/deta, Info).
+        """
+        import torch
+        n, m = x.shape[0], pairs.shape[0]
+        gx = torch.empty((n, 3), dtype=torch.float64, device=x.device)
+        gq = torch.empty((n, 4), dtype=torch.float64, device=x.device)
+        gf = torch.empty((n, 6), dtype=torch.float64, device=x.device)
+        geta = C.c_double()
+        info = Info()
+        st = self._lib.aLENS_step_adjoint(
+            self._h, n, _ptr(x, torch.float64, (3,)), _ptr(quat, torch.float64, (4,)),
+            _ptr(f_nc, torch.float64, (6,)), m, _ptr(pairs.contiguous(), torch.int32, (3,)),
+            _ptr(gamma.contiguous(), torch.float64), _ptr(dL_dx_new, torch.float64, (3,)),
+            _ptr(dL_dquat_new, torch.float64, (4,)), _ptr(gx, torch.float64, (3,)), _ptr(gq, torch.float64, (4,)),
+            _ptr(gf, torch.float64, (6,)), C.byref(geta), C.byref(info))
+        if check and st != 0:
+            raise AlensError(st, "aLENS_step_adjoint", info.as_dict())
+        return gx, gq, gf, geta.value, info

@@ -86,7 +86,7 @@ void free_all(aLENS_ctx* c)
                     c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand, c->keep,
                     c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->perm, c->rank, c->curP, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
                     c->q64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp,
-                    c->systab, c->sysid, c->sysoff, c->sys_order, c->sys_iters, c->sys_res};
+                    c->systab, c->sysid, c->sysoff, c->sys_order, c->sys_iters, c->sys_res, c->adj_ws};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free(c->batch_host);
@@ -638,6 +638,46 @@ aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const 
     if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;
     if (!c->coop_ok) return ALENS_ERR_CUDA;
     return step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
+}
+
+aLENS_status aLENS_step_adjoint(aLENS_ctx* c, int64_t n, const double* x, const double* quat, const double* f_nc,
+                                int64_t n_pairs, const int32_t* pairs, const double* gamma, const double* dL_dx_new,
+                                const double* dL_dquat_new, double* dL_dx, double* dL_dquat, double* dL_dfnc,
+                                double* dL_deta, aLENS_info* info)
+{
+    if (c) { c->launches = 0; single_mode(c); }
+    if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
+    if (n > 0 && (!x || !quat || !dL_dx || !dL_dquat)) return ALENS_ERR_INVALID;
+    if (n_pairs > 0 && (!pairs || !gamma)) return ALENS_ERR_INVALID;
+    if (cudaGetLastError() != cudaSuccess) return ALENS_ERR_CUDA;
+    if (adjoint_reserve(c) != cudaSuccess) { cudaGetLastError(); return ALENS_ERR_NOMEM; }
+    aLENS_status st = reset_status(c);
+    if (st != ALENS_OK) return st;
+    const int m = (int)n_pairs;
+    CK(launch_pack(c, (int)n, x, quat, f_nc, false));
+    CK(launch_solve_setup_check(c, (int)n, m, pairs));
+    if ((st = read_status(c)) != ALENS_OK) return st;
+    if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
+    CK(launch_assemble(c, (int)n, m, pairs, c->phi, c->dgeom, c->q64));
+    CK(launch_solve_setup(c, (int)n, m, pairs, c->dgeom, c->q64, gamma, quat, c->p.precision, nullptr));
+    int iters = 0;
+    double rel = 0.0;
+    CK(launch_adjoint(c, (int)n, m, quat, f_nc, pairs, gamma, dL_dx_new, dL_dquat_new, dL_dx, dL_dquat, dL_dfnc,
+                      &iters, &rel, dL_deta));
+    if ((st = read_status(c)) != ALENS_OK) return st;
+    if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
+    const double tol = c->p.precision == ALENS_MIXED ? 1e-7 : 1e-13;
+    st = (m > 0 && !(rel <= tol)) ? ALENS_ERR_NOT_CONVERGED : ALENS_OK;
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->n_pairs = n_pairs;
+        info->iters = iters;
+        info->residual = rel;
+        info->status = (int32_t)st;
+        info->min_gap = INFINITY;
+        info->launches = c->launches;
+    }
+    return st;
 }
 
 aLENS_status aLENS_set_batch_launch(aLENS_ctx* c, int32_t threads, int32_t cluster_blocks)

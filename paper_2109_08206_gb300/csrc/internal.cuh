@@ -273,6 +273,7 @@ struct aLENS_ctx {
     int* sys_iters;          // [max_systems] iterations of each system's solve
     double* sys_res;         // [max_systems] final residual of each system
     int last_batch_n;        // systems of the last completed aLENS_step_batch (0: none)
+    void* adj_ws;            // adjoint workspace (allocated by the first aLENS_step_adjoint)
     int batch_threads;       // per-system solver: threads per block
     int batch_cluster;       // per-system solver: blocks per cluster
 };
@@ -308,6 +309,14 @@ cudaError_t launch_rank(aLENS_ctx* ctx, int n);
 // solve.cu
 cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision);
 cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma_out);
+
+// adjoint.cu: workspace (once) and the adjoint pipeline after pack, assembly
+// and the solver setup of the forward step's pair list (identity ranks).
+cudaError_t adjoint_reserve(aLENS_ctx* ctx);
+cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, const double* fnc,
+                           const int32_t* pairs, const double* gamma, const double* gxn, const double* gqn,
+                           double* out_x, double* out_q, double* out_f, int* cg_iters, double* cg_rel,
+                           double* deta);
 
 // update.cu
 cudaError_t launch_update(aLENS_ctx* ctx, int n, int m, double* x, double* quat, int precision, double* vel_out,
