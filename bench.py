@@ -45,10 +45,12 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "rod-steps/s at 1e5 rods, FP32-mixed vs FP64 plain at residual ≤1e-5"
 METRIC_ENSEMBLE = "rod-steps/s of the 256-system batched ensemble (one call), FP32-mixed vs FP64 plain at residual ≤1e-5"
+METRIC_GRAD = ("rod-steps/s of one step plus its adjoint (gradient of the post-step centre loss) at 2e4 rods, "
+               "FP32-mixed vs FP64 plain at residual ≤1e-5")
 
 
 def metric_of(workload):
-    return METRIC_ENSEMBLE if workload == "ensemble256" else METRIC
+    return {"ensemble256": METRIC_ENSEMBLE, "n20k_grad": METRIC_GRAD}.get(workload, METRIC)
 UNIT = "rod-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -292,10 +294,86 @@ class BatchJob:
                              f"update), {t_cpu:.2f} s in total")
 
 
+def cg_bytes_per_iter(n, m, w):
+    """Algorithmic bytes of one CG iteration of the adjoint: per constraint
+    12w + 48 (its record and (gamma, r, p) gathered from both ends), 21w + 40
+    (apply: record, both ends' velocities, gamma, r, p, Ap) and 64 (update of
+    lambda, r, p); per rod 9w + 8 (row pointers, axis, velocity write)."""
+    return m * (33 * w + 152) + n * (9 * w + 8)
+
+
+class GradJob(SingleJob):
+    """One step and its adjoint (aLENS_step + aLENS_step_adjoint) for the loss
+    sum |x' - target|^2 of the differentiation workload."""
+
+    class Out:
+        def __init__(self, d):
+            self.d = d
+
+        def as_dict(self):
+            return self.d
+
+    def __init__(self, s):
+        super().__init__(s)
+        from paper_2109_08206_gb300 import workloads as W
+        self.name = s.name + "_grad"
+        self.T = W.loss_targets(s)
+        self._bufs = None
+
+    def step(self, ctx, x, q, f, **kw):
+        import torch
+        if self._bufs is None or self._bufs[0].shape[0] < ctx.max_pairs:
+            dev = x.device
+            self._bufs = (torch.empty((ctx.max_pairs, 3), dtype=torch.int32, device=dev),
+                          torch.empty(ctx.max_pairs, dtype=torch.float64, device=dev),
+                          torch.empty((self.n, 6), dtype=torch.float64, device=dev),
+                          torch.as_tensor(self.T, device=dev),
+                          torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        pr, gm, vel, T, e0, e1 = self._bufs
+        x0, q0 = x.clone(), q.clone()
+        info = ctx.step(x, q, f, pairs_out=pr, gamma_out=gm, vel_out=vel)
+        m = info.n_pairs
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        xn = x0 + ctx.params.dt * vel[:, :3]
+        gx, gq, gf, geta, ainfo = ctx.step_adjoint(x0, q0, f, pr[:m], gm[:m], 2.0 * (xn - T))
+        e1.record(stream)
+        e1.synchronize()
+        d = info.as_dict()
+        d.update({"cg_iters": ainfo.iters, "cg_residual": ainfo.residual, "ms_adjoint": e0.elapsed_time(e1),
+                  "launches": d["launches"] + ainfo.launches})
+        return GradJob.Out(d)
+
+    def tune(self, T, ctx, x, q, f, precision):
+        return T.tune_single(ctx, x, q, f, precision)
+
+    def cpu(self, args):
+        """The oracle's step and dense adjoint on a spatial sample (about 500
+        rods: the dense adjoint holds (6n)^2 mobility entries)."""
+        import oracle as O
+        from oracle import adjoint as ADJ
+        sub, a = spatial_sample(self.s, min(args.sample_rods, 500))
+        from paper_2109_08206_gb300 import workloads as W
+        T = W.loss_targets(sub)
+        t0 = time.perf_counter()
+        ADJ.loss_and_grad(sub.x, sub.quat, sub.f_nc, O.problem_of(sub), T)
+        t = time.perf_counter() - t0
+        return sub.n, t, (f"{sub.n} rods of {self.s.name} with centres in a periodic sub-cube of edge {a:.2f}; "
+                          f"oracle step (exact or FISTA solve) and its dense adjoint, {t:.2f} s")
+
+    def config(self, W, m):
+        c = super().config(W, m)
+        c["workload"] = self.name
+        c["loss"] = "sum of squared post-step centre displacements from seeded targets (sigma 0.01)"
+        return c
+
+
 def make_job(name):
     from paper_2109_08206_gb300 import workloads as W
     if name == "ensemble256":
         return BatchJob(W.ensemble(seed=1000, count=256))
+    if name == "n20k_grad":
+        return GradJob(W.workload("n20k_phi015"))
     return SingleJob(W.workload(name))
 
 
@@ -478,6 +556,8 @@ def run_ours(args):
         ms64_step = max_over_ranks(statistics.mean(ms64))
         fp64 = {"value": replica_value(ms64_step, n, ws), "unit": UNIT, "ms_per_step": ms64_step,
                 "bbpgd_iters": statistics.mean(i["iters"] for i in inf64),
+                **({"cg_iters": statistics.mean(i["cg_iters"] for i in inf64),
+                    "ms_adjoint": statistics.mean(i["ms_adjoint"] for i in inf64)} if "cg_iters" in inf64[0] else {}),
                 "residual": max(i["residual"] for i in inf64),
                 "ms_solve": statistics.mean(i["ms_solve"] for i in inf64),
                 "solve_bytes_per_launch": statistics.mean(sb64)}
@@ -504,7 +584,8 @@ def run_ours(args):
             c2 = make_ctx(prec)
             xx, qq = x0.clone(), q0.clone()
             gam = torch.empty(max_pairs, dtype=torch.float64, device=dev)
-            inf = job.step(c2, xx, qq, f, gamma_out=gam)
+            inf = SingleJob.step(job, c2, xx, qq, f, gamma_out=gam) if isinstance(job, GradJob) \
+                else job.step(c2, xx, qq, f, gamma_out=gam)
             outs[prec] = (xx, qq, gam[: inf.n_pairs].clone())
             c2.close()
         dx = outs[A.MIXED][0] - outs[A.FP64][0]
@@ -534,7 +615,14 @@ def run_ours(args):
         "config": config,
         "bbpgd_iters": statistics.mean(it), "residual": res, "launch_shape": tuned,
         "phase_ms": {k: statistics.mean(i[k] for i in infos) for k in ("ms_build", "ms_assemble", "ms_solve",
-                                                                         "ms_update")},
+                                                                         "ms_update", "ms_adjoint") if k in infos[0]},
+        "adjoint": None if "cg_iters" not in infos[0] else {
+            "cg_iters": statistics.mean(i["cg_iters"] for i in infos),
+            "cg_residual": max(i["cg_residual"] for i in infos),
+            "ms": statistics.mean(i["ms_adjoint"] for i in infos),
+            "cg_bytes_per_iter": cg_bytes_per_iter(n, m, 4),
+            "cg_GBps_algorithmic": statistics.mean(i["cg_iters"] for i in infos) * cg_bytes_per_iter(n, m, 4)
+                                   / (statistics.mean(i["ms_adjoint"] for i in infos) / 1e3) / 1e9},
         "fp64": fp64, "e2e": e2e, "mixed_vs_fp64": mixed_vs_fp64,
         "roofline": {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

@@ -94,12 +94,18 @@ __device__ __forceinline__ bool last_block_total(double part, double* partials, 
     }
     __syncthreads();
     if (!last) return false;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // warp 0: lane l sums partials l, l + 32, ... (loads in flight
+        // together), then a fixed shuffle tree
         __threadfence();
         double acc = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) acc += __ldcg(&partials[b]);
-        *tot = acc;
-        *counter = 0u;   // ready for the next reduction
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) acc += __ldcg(&partials[b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) {
+            *tot = acc;
+            *counter = 0u;   // ready for the next reduction
+        }
     }
     return true;
 }
@@ -581,7 +587,7 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
     cudaStream_t st = ctx->stream;
     const int mixed = ctx->p.precision == ALENS_MIXED;
     const double h = ctx->p.dt;
-    const int G = ctx->num_sms * 2 < ctx->max_blocks ? ctx->num_sms * 2 : ctx->max_blocks;
+    const int G = ctx->num_sms < ctx->max_blocks ? ctx->num_sms : ctx->max_blocks;
     unsigned* counter = ctx->bar;   // the solver's barrier words are free here
     cudaError_t e;
     if ((e = cudaMemsetAsync(ctx->bar, 0, 4 * sizeof(unsigned), st)) != cudaSuccess) return e;
