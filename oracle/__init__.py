@@ -62,10 +62,11 @@ def lib():
             "orc_assemble": (None, [i64, vp, vp, vp, P, i64, vp, vp, vp, vp, vp, vp]),
             "orc_apply_D": (None, [i64, i64, vp, vp, vp, vp]),
             "orc_apply_Dt": (None, [i64, vp, vp, vp, vp]),
-            "orc_gradient": (d, [i64, vp, P, i64, vp, vp, vp, vp, vp]),
-            "orc_dense_A": (None, [i64, vp, P, i64, vp, vp, vp]),
-            "orc_solve_enum": (i64, [i64, vp, P, i64, vp, vp, vp, vp]),
-            "orc_solve_apgd": (d, [i64, vp, P, i64, vp, vp, vp, vp, d, i64, vp]),
+            "orc_gradient": (d, [i64, vp, P, i64, vp, vp, vp, vp, vp, vp]),
+            "orc_dense_A": (None, [i64, vp, P, i64, vp, vp, vp, vp]),
+            "orc_solve_enum": (i64, [i64, vp, P, i64, vp, vp, vp, vp, vp]),
+            "orc_solve_apgd": (d, [i64, vp, P, i64, vp, vp, vp, vp, vp, d, i64, vp]),
+            "orc_assemble_springs": (None, [i64, vp, vp, vp, P, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "orc_update": (None, [i64, vp, vp, vp, P, i64, vp, vp, vp, vp, vp, vp]),
             "orc_step": (i64, [i64, vp, vp, vp, P, d, i64, i64, vp, vp, vp, vp, vp, vp, vp]),
         }
@@ -184,43 +185,65 @@ def apply_Dt(pairs, dgeom, U):
     return out
 
 
-def gradient(quat, pb: Problem, pairs, dgeom, q, gamma):
+def _comp(comp):
+    return None if comp is None else _f64(comp)
+
+
+def gradient(quat, pb: Problem, pairs, dgeom, q, gamma, comp=None):
+    """g = (D^T M D + diag(comp+)) gamma + q and the residual; comp (nullable)
+    marks bilateral constraints (>= 0: compliance 1/(h kappa)) among unilateral ones (< 0)."""
     quat = _f64(quat, (-1, 4))
     pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
-    dg, q, gm = _f64(dgeom, (-1, 9)), _f64(q), _f64(gamma)
+    dg, q, gm, cp = _f64(dgeom, (-1, 9)), _f64(q), _f64(gamma), _comp(comp)
     g = np.zeros(pr.shape[0])
-    r = lib().orc_gradient(quat.shape[0], _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(q), _p(gm), _p(g))
+    r = lib().orc_gradient(quat.shape[0], _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(q), _p(cp),
+                           _p(gm), _p(g))
     return g, r
 
 
-def dense_A(quat, pb: Problem, pairs, dgeom):
+def dense_A(quat, pb: Problem, pairs, dgeom, comp=None):
     quat = _f64(quat, (-1, 4))
     pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
-    dg = _f64(dgeom, (-1, 9))
+    dg, cp = _f64(dgeom, (-1, 9)), _comp(comp)
     m = pr.shape[0]
     A = np.zeros((m, m))
-    lib().orc_dense_A(quat.shape[0], _p(quat), C.byref(pb), m, _p(pr), _p(dg), _p(A))
+    lib().orc_dense_A(quat.shape[0], _p(quat), C.byref(pb), m, _p(pr), _p(dg), _p(cp), _p(A))
     return A
 
 
-def solve_enum(quat, pb: Problem, pairs, dgeom, q):
+def solve_enum(quat, pb: Problem, pairs, dgeom, q, comp=None):
     quat = _f64(quat, (-1, 4))
     pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
-    dg, q = _f64(dgeom, (-1, 9)), _f64(q)
+    dg, q, cp = _f64(dgeom, (-1, 9)), _f64(q), _comp(comp)
     gm = np.zeros(pr.shape[0])
-    mask = lib().orc_solve_enum(quat.shape[0], _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(q), _p(gm))
+    mask = lib().orc_solve_enum(quat.shape[0], _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(q), _p(cp),
+                                _p(gm))
     return gm, mask
 
 
-def solve_apgd(quat, pb: Problem, pairs, dgeom, q, tol=1e-12, max_iter=1_000_000, gamma0=None):
+def solve_apgd(quat, pb: Problem, pairs, dgeom, q, tol=1e-12, max_iter=1_000_000, gamma0=None, comp=None):
     quat = _f64(quat, (-1, 4))
     pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 3)
-    dg, q = _f64(dgeom, (-1, 9)), _f64(q)
+    dg, q, cp = _f64(dgeom, (-1, 9)), _f64(q), _comp(comp)
     gm = np.zeros(pr.shape[0]) if gamma0 is None else _f64(gamma0).copy()
     it = C.c_int64()
-    r = lib().orc_solve_apgd(quat.shape[0], _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(q), _p(gm),
-                             float(tol), int(max_iter), C.byref(it))
+    r = lib().orc_solve_apgd(quat.shape[0], _p(quat), C.byref(pb), pr.shape[0], _p(pr), _p(dg), _p(q), _p(cp),
+                             _p(gm), float(tol), int(max_iter), C.byref(it))
     return gm, r, it.value
+
+
+def assemble_springs(x, quat, fnc, pb: Problem, ends, arms, kappa, rest):
+    """Bilateral constraints of the springs: dict with pairs (P, Q, image),
+    dgeom, q, length (Phi_b) and comp = 1/(h kappa)."""
+    x, quat, fnc = _f64(x, (-1, 3)), _f64(quat, (-1, 4)), _f64(fnc, (-1, 6))
+    en = np.ascontiguousarray(ends, dtype=np.int32).reshape(-1, 2)
+    ar, kp, rs = _f64(arms, (-1, 2)), _f64(kappa), _f64(rest)
+    nb = en.shape[0]
+    pr = np.zeros((nb, 3), dtype=np.int32)
+    dg, q, ln, cp = np.zeros((nb, 9)), np.zeros(nb), np.zeros(nb), np.zeros(nb)
+    lib().orc_assemble_springs(x.shape[0], _p(x), _p(quat), _p(fnc), C.byref(pb), nb, _p(en), _p(ar), _p(kp),
+                               _p(rs), _p(pr), _p(dg), _p(q), _p(ln), _p(cp))
+    return {"pairs": pr, "dgeom": dg, "q": q, "length": ln, "comp": cp}
 
 
 def update(x, quat, fnc, pb: Problem, pairs, dgeom, gamma):
@@ -233,14 +256,34 @@ def update(x, quat, fnc, pb: Problem, pairs, dgeom, gamma):
     return xo, qo, U
 
 
-def step(x, quat, fnc, pb: Problem, tol=1e-12, max_iter=1_000_000, max_pairs=None):
-    """One full constrained step; returns a dict of every intermediate."""
+def step(x, quat, fnc, pb: Problem, tol=1e-12, max_iter=1_000_000, max_pairs=None, springs=None):
+    """One full constrained step; returns a dict of every intermediate.
+
+    ``springs`` (nullable): dict of ends [nb, 2], arms [nb, 2], kappa [nb],
+    rest [nb]: bilateral constraints solved together with the collisions
+    (Eq. linearconstraints b); ``gamma`` then holds the collision forces
+    followed by the spring forces."""
     x, quat, fnc = _f64(x, (-1, 3)), _f64(quat, (-1, 4)), _f64(fnc, (-1, 6))
     pairs = find_pairs(x, quat, pb)
     asm = assemble(x, quat, fnc, pb, pairs)
-    gamma, res, iters = solve_apgd(quat, pb, pairs, asm["dgeom"], asm["q"], tol=tol, max_iter=max_iter)
-    xo, qo, U = update(x, quat, fnc, pb, pairs, asm["dgeom"], gamma)
-    return {"pairs": pairs, **asm, "gamma": gamma, "residual": res, "iters": iters, "x": xo, "quat": qo, "U": U}
+    if springs is None:
+        gamma, res, iters = solve_apgd(quat, pb, pairs, asm["dgeom"], asm["q"], tol=tol, max_iter=max_iter)
+        xo, qo, U = update(x, quat, fnc, pb, pairs, asm["dgeom"], gamma)
+        return {"pairs": pairs, **asm, "gamma": gamma, "residual": res, "iters": iters, "x": xo, "quat": qo, "U": U}
+    sb = assemble_springs(x, quat, fnc, pb, springs["ends"], springs["arms"], springs["kappa"], springs["rest"])
+    allp = np.concatenate([pairs.reshape(-1, 3), sb["pairs"]]).astype(np.int32)
+    dg = np.concatenate([asm["dgeom"].reshape(-1, 9), sb["dgeom"]])
+    q = np.concatenate([asm["q"], sb["q"]])
+    comp = np.concatenate([-np.ones(pairs.shape[0]), sb["comp"]])
+    if allp.shape[0] <= 20:
+        gamma, _ = solve_enum(quat, pb, allp, dg, q, comp=comp)
+        res = gradient(quat, pb, allp, dg, q, gamma, comp=comp)[1]
+        iters = 0
+    else:
+        gamma, res, iters = solve_apgd(quat, pb, allp, dg, q, tol=tol, max_iter=max_iter, comp=comp)
+    xo, qo, U = update(x, quat, fnc, pb, allp, dg, gamma)
+    return {"pairs": pairs, **asm, "springs": sb, "all_pairs": allp, "all_dgeom": dg, "all_q": q, "comp": comp,
+            "gamma": gamma, "residual": res, "iters": iters, "x": xo, "quat": qo, "U": U}
 
 
 def step_native(x, quat, fnc, pb: Problem, tol, max_iter, max_pairs):

@@ -429,6 +429,61 @@ ORC_API void orc_assemble(int64_t n, const double* x, const double* quat, const 
     free(xw); free(axis); free(unc);
 }
 
+/* Bilateral (spring) constraints (Appendix: Phi_b is the distance between
+ * two fixed points of particles P and Q, K [Phi_b - Phi_b^0] = -gamma_b;
+ * Eqs. linearconstraints b and blockdef D, F).  Spring b joins the point at
+ * arclength arms[b][0] on rod ends[b][0] (P) to arclength arms[b][1] on rod
+ * ends[b][1] (Q): r = x_P + s_P p_P - x_Q - s_Q p_Q over the minimum periodic
+ * image of the two points, Phi_b = |r|, e = r / |r|, and the D column is
+ * (e, y_P x e | -e, -(y_Q x e)) with y = s p, exactly as for a collision.
+ * Outputs per spring: pairs (P, Q, image code), dgeom, q = (Phi_b -
+ * rest)/h + D^T M F_nc, the length Phi_b and comp = 1/(h kappa). */
+ORC_API void orc_assemble_springs(int64_t n, const double* x, const double* quat, const double* fnc,
+                                  const orc_problem* pb, int64_t nb, const int32_t* ends, const double* arms,
+                                  const double* kappa, const double* rest, int32_t* pairs, double* dgeom,
+                                  double* q, double* length, double* comp)
+{
+    double zeta[4];
+    orc_drag(pb->viscosity, pb->length, pb->diameter, zeta);
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double* xw = (double*)malloc(sizeof(double) * 3 * nn);
+    double* axis = (double*)malloc(sizeof(double) * 3 * nn);
+    orc_wrap(n, x, pb->box, xw);
+    orc_axis(n, quat, axis);
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t i = ends[2 * b], j = ends[2 * b + 1];
+        const double *pi_ = axis + 3 * i, *pj_ = axis + 3 * j;
+        double yP[3], yQ[3], r[3], e[3];
+        int k[3];
+        for (int m = 0; m < 3; ++m) {
+            yP[m] = arms[2 * b] * pi_[m];
+            yQ[m] = arms[2 * b + 1] * pj_[m];
+            double d = xw[3 * i + m] + yP[m] - xw[3 * j + m] - yQ[m];
+            k[m] = (int)nearbyint(d / pb->box[m]);
+            if (k[m] > 1) k[m] = 1;
+            if (k[m] < -1) k[m] = -1;
+            r[m] = d - (double)k[m] * pb->box[m];
+        }
+        double len = sqrt(dot3(r, r));
+        for (int m = 0; m < 3; ++m) e[m] = len > 0.0 ? r[m] / len : (m == 0 ? 1.0 : 0.0);
+        pairs[3 * b] = (int32_t)i;
+        pairs[3 * b + 1] = (int32_t)j;
+        pairs[3 * b + 2] = (int32_t)((k[0] + 1) + 3 * (k[1] + 1) + 9 * (k[2] + 1));
+        double* dg = dgeom + 9 * b;
+        dg[0] = e[0]; dg[1] = e[1]; dg[2] = e[2];
+        cross3(yP, e, dg + 3);
+        cross3(yQ, e, dg + 6);
+        double ui[6], uj[6];
+        mobility_rod(pi_, zeta, fnc + 6 * i, ui);
+        mobility_rod(pj_, zeta, fnc + 6 * j, uj);
+        double dtu = dot3(e, ui) + dot3(dg + 3, ui + 3) - dot3(e, uj) - dot3(dg + 6, uj + 3);
+        length[b] = len;
+        q[b] = (len - rest[b]) / pb->dt + dtu;
+        comp[b] = 1.0 / (pb->dt * kappa[b]);
+    }
+    free(xw); free(axis);
+}
+
 /* F = D gamma: force and torque on every rod (Eq. dmap F_u = D_u gamma_u). */
 ORC_API void orc_apply_D(int64_t n, int64_t npairs, const int32_t* pairs, const double* dgeom,
                          const double* gamma, double* F)
@@ -467,26 +522,33 @@ typedef struct {
     const int32_t* pairs;
     const double* dgeom;
     const double* q;
+    const double* comp;   /* NULL, or per constraint: < 0 unilateral, >= 0 bilateral compliance 1/(h kappa) */
     double* axis;
     double zeta[4];
     double* F;   /* 6n scratch */
     double* U;   /* 6n scratch */
 } orc_qp;
 
-/* out = (D^T M D) v   (Eq. blockdef B) */
+static int is_bilateral(const orc_qp* qp, int64_t c) { return qp->comp && qp->comp[c] >= 0.0; }
+
+/* out = (D^T M D + diag(0, K^{-1}/h)) v   (Eq. blockdef B, C, E, F) */
 static void qp_matvec(orc_qp* qp, const double* v, double* out)
 {
     orc_apply_D(qp->n, qp->npairs, qp->pairs, qp->dgeom, v, qp->F);
 #pragma omp parallel for
     for (int64_t i = 0; i < qp->n; ++i) mobility_rod(qp->axis + 3 * i, qp->zeta, qp->F + 6 * i, qp->U + 6 * i);
     orc_apply_Dt(qp->npairs, qp->pairs, qp->dgeom, qp->U, out);
+    if (qp->comp)
+        for (int64_t c = 0; c < qp->npairs; ++c)
+            if (qp->comp[c] >= 0.0) out[c] += qp->comp[c] * v[c];
 }
 
 static double qp_residual(const orc_qp* qp, const double* gamma, const double* g, const orc_problem* pb)
 {
     double m = 0.0;
     for (int64_t c = 0; c < qp->npairs; ++c) {
-        double pg = gamma[c] > 0.0 ? g[c] : (g[c] < 0.0 ? g[c] : 0.0);
+        /* bilateral entries are free: their projected gradient is g */
+        double pg = (gamma[c] > 0.0 || is_bilateral(qp, c)) ? g[c] : (g[c] < 0.0 ? g[c] : 0.0);
         double a = fabs(pg);
         if (a > m) m = a;
     }
@@ -494,9 +556,9 @@ static double qp_residual(const orc_qp* qp, const double* gamma, const double* g
 }
 
 static int qp_init(orc_qp* qp, int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
-                   const int32_t* pairs, const double* dgeom, const double* q)
+                   const int32_t* pairs, const double* dgeom, const double* q, const double* comp)
 {
-    qp->n = n; qp->npairs = npairs; qp->pairs = pairs; qp->dgeom = dgeom; qp->q = q;
+    qp->n = n; qp->npairs = npairs; qp->pairs = pairs; qp->dgeom = dgeom; qp->q = q; qp->comp = comp;
     orc_drag(pb->viscosity, pb->length, pb->diameter, qp->zeta);
     size_t nn = (size_t)(n > 0 ? n : 1);
     qp->axis = (double*)malloc(sizeof(double) * 3 * nn);
@@ -510,11 +572,11 @@ static void qp_free(orc_qp* qp) { free(qp->axis); free(qp->F); free(qp->U); }
 
 /* g = D^T M D gamma + q and the residual (reading R6). */
 ORC_API double orc_gradient(int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
-                            const int32_t* pairs, const double* dgeom, const double* q, const double* gamma,
-                            double* g)
+                            const int32_t* pairs, const double* dgeom, const double* q, const double* comp,
+                            const double* gamma, double* g)
 {
     orc_qp qp;
-    qp_init(&qp, n, quat, pb, npairs, pairs, dgeom, q);
+    qp_init(&qp, n, quat, pb, npairs, pairs, dgeom, q, comp);
     qp_matvec(&qp, gamma, g);
     for (int64_t c = 0; c < npairs; ++c) g[c] += q[c];
     double r = qp_residual(&qp, gamma, g, pb);
@@ -524,10 +586,10 @@ ORC_API double orc_gradient(int64_t n, const double* quat, const orc_problem* pb
 
 /* Dense A = D^T M D for small problems (column c = A e_c). */
 ORC_API void orc_dense_A(int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
-                         const int32_t* pairs, const double* dgeom, double* A)
+                         const int32_t* pairs, const double* dgeom, const double* comp, double* A)
 {
     orc_qp qp;
-    qp_init(&qp, n, quat, pb, npairs, pairs, dgeom, NULL);
+    qp_init(&qp, n, quat, pb, npairs, pairs, dgeom, NULL, comp);
     double* ec = (double*)calloc((size_t)npairs, sizeof(double));
     double* col = (double*)malloc(sizeof(double) * (size_t)npairs);
     for (int64_t c = 0; c < npairs; ++c) {
@@ -567,18 +629,23 @@ static int small_solve(int m, double* A, double* b, double tiny)
     return 1;
 }
 
-/* Exact solution of the CQP (Eq. suppcqpdef, unilateral block) for tiny
- * problems by enumerating active sets: for every subset S, solve
- * A_SS gamma_S = -q_S and accept the first subset whose KKT conditions hold
- * (gamma_S >= 0 and g_c >= 0 off S).  A solution with a non-singular A_SS
- * always exists for an SPSD A.  Returns the accepted subset's bitmask, or -1. */
+/* Exact solution of the CQP (Eq. suppcqpdef) for tiny problems by
+ * enumerating active sets: for every subset S that contains every bilateral
+ * constraint, solve A_SS gamma_S = -q_S and accept the first subset whose
+ * KKT conditions hold (gamma_S >= 0 on its unilateral entries, g_c >= 0 off
+ * S).  A solution with a non-singular A_SS always exists for an SPSD A.
+ * Returns the accepted subset's bitmask, or -1. */
 ORC_API int64_t orc_solve_enum(int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
-                               const int32_t* pairs, const double* dgeom, const double* q, double* gamma)
+                               const int32_t* pairs, const double* dgeom, const double* q, const double* comp,
+                               double* gamma)
 {
     if (npairs > 20) return -1;
     int m = (int)npairs;
+    int64_t must = 0;
+    for (int c = 0; c < m; ++c)
+        if (comp && comp[c] >= 0.0) must |= (int64_t)1 << c;
     double* A = (double*)malloc(sizeof(double) * (size_t)(m * m + 1));
-    orc_dense_A(n, quat, pb, npairs, pairs, dgeom, A);
+    orc_dense_A(n, quat, pb, npairs, pairs, dgeom, comp, A);
     double amax = 0.0, qmax = 0.0;
     for (int c = 0; c < m; ++c) {
         if (A[c * m + c] > amax) amax = A[c * m + c];
@@ -589,6 +656,7 @@ ORC_API int64_t orc_solve_enum(int64_t n, const double* quat, const orc_problem*
     int idx[32];
     int64_t found = -1;
     for (int64_t mask = 0; mask < ((int64_t)1 << m) && found < 0; ++mask) {
+        if ((mask & must) != must) continue;
         int k = 0;
         for (int c = 0; c < m; ++c) if (mask >> c & 1) idx[k++] = c;
         for (int r = 0; r < k; ++r) {
@@ -597,10 +665,11 @@ ORC_API int64_t orc_solve_enum(int64_t n, const double* quat, const orc_problem*
         }
         if (k > 0 && !small_solve(k, sub, rhs, 1e-10 * amax)) continue;
         int ok = 1;
-        for (int r = 0; r < k; ++r) if (rhs[r] < -1e-12 * (1.0 + qmax / (amax > 0 ? amax : 1.0))) { ok = 0; break; }
+        for (int r = 0; r < k; ++r)
+            if (!(must >> idx[r] & 1) && rhs[r] < -1e-12 * (1.0 + qmax / (amax > 0 ? amax : 1.0))) { ok = 0; break; }
         if (!ok) continue;
         for (int c = 0; c < m; ++c) gamma[c] = 0.0;
-        for (int r = 0; r < k; ++r) gamma[idx[r]] = rhs[r] > 0.0 ? rhs[r] : 0.0;
+        for (int r = 0; r < k; ++r) gamma[idx[r]] = (must >> idx[r] & 1) ? rhs[r] : (rhs[r] > 0.0 ? rhs[r] : 0.0);
         for (int c = 0; c < m && ok; ++c) {
             if (mask >> c & 1) continue;
             double g = q[c];
@@ -624,11 +693,11 @@ ORC_API int64_t orc_solve_enum(int64_t n, const double* quat, const orc_problem*
  * gamma holds the start on entry (negative entries are projected to 0) and
  * the result on exit.  Returns the final residual; *iters gets the count. */
 ORC_API double orc_solve_apgd(int64_t n, const double* quat, const orc_problem* pb, int64_t npairs,
-                              const int32_t* pairs, const double* dgeom, const double* q, double* gamma,
-                              double tol, int64_t max_iter, int64_t* iters)
+                              const int32_t* pairs, const double* dgeom, const double* q, const double* comp,
+                              double* gamma, double tol, int64_t max_iter, int64_t* iters)
 {
     orc_qp qp;
-    qp_init(&qp, n, quat, pb, npairs, pairs, dgeom, q);
+    qp_init(&qp, n, quat, pb, npairs, pairs, dgeom, q, comp);
     size_t m = (size_t)(npairs > 0 ? npairs : 1);
     double* v = (double*)malloc(sizeof(double) * m);
     double* w = (double*)malloc(sizeof(double) * m);
@@ -653,7 +722,7 @@ ORC_API double orc_solve_apgd(int64_t n, const double* quat, const orc_problem* 
     double lip = 1.1 * lam;
     if (!(lip > 0.0)) lip = 1.0;
     for (int64_t c = 0; c < npairs; ++c) {
-        if (!(gamma[c] > 0.0)) gamma[c] = 0.0;
+        if (!(gamma[c] > 0.0) && !is_bilateral(&qp, c)) gamma[c] = 0.0;
         z[c] = gamma[c];
     }
     double t = 1.0, res = INFINITY;
@@ -671,7 +740,7 @@ ORC_API double orc_solve_apgd(int64_t n, const double* quat, const orc_problem* 
         double restart = 0.0;
         for (int64_t c = 0; c < npairs; ++c) {
             double gnew = z[c] - gz[c] / lip;
-            if (gnew < 0.0) gnew = 0.0;
+            if (gnew < 0.0 && !is_bilateral(&qp, c)) gnew = 0.0;   /* projection on the unilateral block only */
             w[c] = gnew;
             restart += gz[c] * (gnew - gamma[c]);
         }
@@ -747,7 +816,7 @@ ORC_API int64_t orc_step(int64_t n, const double* x, const double* quat, const d
     double* q = (double*)malloc(sizeof(double) * m);
     orc_assemble(n, x, quat, fnc, pb, np, pairs, phi, dg, q, NULL, NULL);
     for (int64_t c = 0; c < np; ++c) gamma[c] = 0.0;
-    double r = orc_solve_apgd(n, quat, pb, np, pairs, dg, q, gamma, tol, max_iter, iters);
+    double r = orc_solve_apgd(n, quat, pb, np, pairs, dg, q, NULL, gamma, tol, max_iter, iters);
     if (residual) *residual = r;
     orc_update(n, x, quat, fnc, pb, np, pairs, dg, gamma, x_out, quat_out, U_out);
     free(phi); free(dg); free(q);

@@ -293,6 +293,25 @@ def ensemble(seed: int = 1000, count: int = 256, scale: float = 1.0) -> list[Rod
     return out
 
 
+def spring_set(s: RodSystem, count: int, seed: int = 21, kappa: float = 10.0, rest: float = 1.5) -> dict:
+    """Bilateral crosslinker springs for a system: ``count`` rod pairs drawn
+    uniformly among the pairs whose centres (minimum image) lie closer than
+    L, attachment arclengths uniform in [-L/2, L/2], stiffness ``kappa`` and
+    rest length ``rest``.  Returns ends [nb, 2] int32 (i < j), arms [nb, 2],
+    kappa [nb], rest [nb]."""
+    from scipy.spatial import cKDTree  # input preparation only
+
+    rng = np.random.default_rng(seed)
+    boxa = np.asarray(s.box, dtype=np.float64)
+    cand = cKDTree(s.x, boxsize=boxa).query_pairs(r=s.length, output_type="ndarray")
+    cand = cand[np.lexsort((cand[:, 1], cand[:, 0]))]
+    pick = np.sort(rng.choice(cand.shape[0], size=min(count, cand.shape[0]), replace=False))
+    ends = np.ascontiguousarray(cand[pick], dtype=np.int32)
+    arms = rng.uniform(-s.length / 2, s.length / 2, size=(ends.shape[0], 2))
+    nb = ends.shape[0]
+    return {"ends": ends, "arms": arms, "kappa": np.full(nb, float(kappa)), "rest": np.full(nb, float(rest))}
+
+
 def loss_targets(s: RodSystem, seed: int = 11, sigma: float = 0.01) -> np.ndarray:
     """Seeded targets of the differentiation workload's loss: the initial
     centres displaced by N(0, sigma^2) per component."""
