@@ -45,12 +45,15 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "rod-steps/s at 1e5 rods, FP32-mixed vs FP64 plain at residual ≤1e-5"
 METRIC_ENSEMBLE = "rod-steps/s of the 256-system batched ensemble (one call), FP32-mixed vs FP64 plain at residual ≤1e-5"
+METRIC_SPRINGS = ("rod-steps/s at 1e5 rods with 5e4 bilateral spring constraints, FP32-mixed vs FP64 plain at "
+                  "residual ≤1e-5")
 METRIC_GRAD = ("rod-steps/s of one step plus its adjoint (gradient of the post-step centre loss) at 2e4 rods, "
                "FP32-mixed vs FP64 plain at residual ≤1e-5")
 
 
 def metric_of(workload):
-    return {"ensemble256": METRIC_ENSEMBLE, "n20k_grad": METRIC_GRAD}.get(workload, METRIC)
+    return {"ensemble256": METRIC_ENSEMBLE, "n20k_grad": METRIC_GRAD,
+            "n100k_springs": METRIC_SPRINGS}.get(workload, METRIC)
 UNIT = "rod-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -368,8 +371,56 @@ class GradJob(SingleJob):
         return c
 
 
+class SpringJob(SingleJob):
+    """The 1e5-rod suspension with its 50,000 crosslinkers as bilateral
+    spring constraints (aLENS_set_springs) instead of explicit forces."""
+
+    def __init__(self, s, springs):
+        super().__init__(s)
+        self.sp = springs
+        self.name = s.name + "_bilateral"
+        self.nb = len(springs["kappa"])
+
+    def context(self, A, precision, tol, stream):
+        import torch
+        ctx = super().context(A, precision, tol, stream)
+        p = A.params_of(self.s, precision=precision, tol=tol, max_iter=1_000_000)
+        ctx.close()
+        ctx = A.Context(p, self.n, 12 * self.n + self.nb, stream=stream)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        sp = self.sp
+        ctx.set_springs(torch.as_tensor(sp["ends"], dtype=torch.int32, device=dev),
+                        torch.as_tensor(sp["arms"], device=dev), torch.as_tensor(sp["kappa"], device=dev),
+                        torch.as_tensor(sp["rest"], device=dev))
+        return ctx
+
+    def solve_bytes(self, ctx, info, w):
+        return info["iters"] * solve_bytes_per_iter(self.n, info["n_pairs"] + self.nb, w)
+
+    def config(self, W, m):
+        c = super().config(W, m)
+        c.update({"workload": self.name, "springs": None, "bilateral_springs": self.nb,
+                  "spring_model": "kappa 10, rest 1.5, attachment arclengths uniform"})
+        return c
+
+    def cpu(self, args):
+        import oracle as O
+        sub, a = spatial_sample(self.s, args.sample_rods)
+        from paper_2109_08206_gb300 import workloads as W
+        nb = max(1, int(round(self.nb * sub.n / self.n)))
+        sp = W.spring_set(sub, nb, seed=21)
+        t0 = time.perf_counter()
+        O.step(sub.x, sub.quat, sub.f_nc, O.problem_of(sub), tol=args.tol, springs=sp)
+        t = time.perf_counter() - t0
+        return sub.n, t, (f"{sub.n} rods of {self.s.name} with centres in a periodic sub-cube of edge {a:.2f} and "
+                          f"{nb} springs; one oracle step with the bilateral constraints, {t:.2f} s")
+
+
 def make_job(name):
     from paper_2109_08206_gb300 import workloads as W
+    if name == "n100k_springs":
+        s = W.workload("n100k_phi010", n_springs=0)
+        return SpringJob(s, W.spring_set(s, 50_000, seed=21))
     if name == "ensemble256":
         return BatchJob(W.ensemble(seed=1000, count=256))
     if name == "n20k_grad":

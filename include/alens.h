@@ -161,6 +161,31 @@ ALENS_API aLENS_status aLENS_step(aLENS_ctx* ctx, int64_t n, double* x, double* 
                         int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info);
 
 /* ------------------------------------------------------------------------
+ * Bilateral (spring) constraints: doubly bound crosslinkers (Appendix: Phi_b
+ * is the distance between two fixed points of particles P and Q, and
+ * K [Phi_b - Phi_b^0] = -gamma_b; linearised as Eq. linearconstraints b and
+ * solved with the collisions as one CQP, Eq. suppcqpdef, whose matrix gains
+ * the diagonal compliance K^{-1}/h on the spring block (Eq. blockdef F) and
+ * whose spring forces are not projected).
+ * ends  [n_springs][2] int32: rods P and Q of each spring (P != Q, any order).
+ * arms  [n_springs][2] float64: arclengths s_P, s_Q of the attachment points
+ *       along the rods' axes from their centres (y = s p).
+ * kappa [n_springs] float64 > 0: stiffness; rest [n_springs]: rest length.
+ * All DEVICE pointers; the context copies them (stream-ordered) and every
+ * later aLENS_step / aLENS_step_batch solves them with that step's
+ * collisions: the point pair is taken over its minimum periodic image, the
+ * column is (e, y_P x e | -e, -(y_Q x e)) as for a collision, and
+ * gamma_out holds the collision forces followed by the spring forces
+ * (gamma_b > 0 pushes the points apart, gamma_b = -kappa (Phi_b' - rest)
+ * at the linearised new length).  Capacity: collisions + springs <=
+ * max_pairs.  n_springs = 0 removes the springs.  A spring whose rods are
+ * out of range, equal, in different systems of a batch, or whose kappa is
+ * not positive makes the step return INVALID with nothing moved.  Not
+ * covered by aLENS_step_adjoint (NOT_IMPLEMENTED while springs are set). */
+ALENS_API aLENS_status aLENS_set_springs(aLENS_ctx* ctx, int64_t n_springs, const int32_t* ends, const double* arms,
+                                         const double* kappa, const double* rest);
+
+/* ------------------------------------------------------------------------
  * Batched step of independent periodic systems.  The paper steps one system
  * (distributed over many processes); an ensemble of many small, uneven
  * systems is stepped here in one call, each system with the step of

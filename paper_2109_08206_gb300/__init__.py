@@ -89,6 +89,7 @@ def lib():
             "aLENS_step_adjoint": (i32, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp,
                                          C.POINTER(d), IP]),
             "aLENS_set_batch_launch": (i32, [vp, i32, i32]),
+            "aLENS_set_springs": (i32, [vp, i64, vp, vp, vp, vp]),
             "aLENS_set_wait_limit": (i32, [vp, d]),
             "aLENS_inject_fault": (i32, [vp, i32]),
             "aLENS_set_launch": (i32, [vp, i32, i32]),
@@ -318,3 +319,18 @@ class Context:
         if check and st != 0:
             raise AlensError(st, "aLENS_step_adjoint", info.as_dict())
         return gx, gq, gf, geta.value, info
+
+    def set_springs(self, ends=None, arms=None, kappa=None, rest=None):
+        """Bilateral springs solved with every later step (device tensors:
+        ends [nb, 2] int32, arms [nb, 2], kappa [nb], rest [nb] float64);
+        no arguments removes them."""
+        import torch
+        nb = 0 if ends is None else int(ends.shape[0])
+        st = self._lib.aLENS_set_springs(
+            self._h, nb, _ptr(None if nb == 0 else ends.contiguous(), torch.int32, (2,)),
+            _ptr(None if nb == 0 else arms.contiguous(), torch.float64, (2,)),
+            _ptr(None if nb == 0 else kappa.contiguous(), torch.float64),
+            _ptr(None if nb == 0 else rest.contiguous(), torch.float64))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_springs")
+        self._springs = (ends, arms, kappa, rest) if nb > 0 else None   # keep the caller's tensors alive

@@ -195,7 +195,8 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
                              const double* __restrict__ q64, const double* __restrict__ gin,
                              const int* __restrict__ rowQ, int* __restrict__ curQ, int* __restrict__ qlist,
                              int* __restrict__ ci, int* __restrict__ cj, T* __restrict__ rec, T* __restrict__ qT,
-                             T* __restrict__ gg0, T* __restrict__ gg1, T* __restrict__ rec_lo, T* __restrict__ q_lo)
+                             T* __restrict__ gg0, T* __restrict__ gg1, T* __restrict__ rec_lo, T* __restrict__ q_lo,
+                             const double* __restrict__ comp64, T* __restrict__ compT)
 {
     int cc = blockIdx.x * blockDim.x + threadIdx.x;
     if (cc >= m) return;
@@ -227,8 +228,10 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
     const T qh = (T)q64[c];
     qT[cc] = qh;
     if (q_lo) q_lo[cc] = (T)(q64[c] - (double)qh);
+    const double cmp = comp64 ? comp64[c] : -1.0;
+    if (comp64) compT[cc] = (T)cmp;
     double v = gin ? gin[c] : 0.0;
-    if (!(v > 0.0)) v = 0.0;
+    if (!(v > 0.0) && !(cmp >= 0.0)) v = 0.0;   // collisions start at gamma >= 0, springs anywhere
     // solver state (delta, g, gamma_ref, gamma_lo) in both buffers: gamma_0
     // (split into a working-precision value and its rounding error) is the
     // first reference
@@ -295,7 +298,85 @@ __global__ void k_setup_rods(int n, int np, const double* __restrict__ quat, con
     }
 }
 
+// Spring b (bilateral constraint; Appendix: Phi_b is the distance between
+// two fixed points of particles P and Q, K [Phi_b - Phi_b^0] = -gamma_b;
+// Eqs. linearconstraints b, blockdef D and F): the point at arclength s_P on
+// rod P and the point at s_Q on rod Q, taken over their minimum periodic
+// image; Phi_b = |r|, e = r / |r| and the D column (e, y_P x e | -e,
+// -(y_Q x e)) exactly as for a collision.  Row mu + b of the constraint list:
+// pairs (P, Q, image), phi = Phi_b, dgeom, q = (Phi_b - rest)/h + D^T M F_nc,
+// comp64 = 1/(h kappa).  Rows below mu (collisions) get comp64 = -1.
+__global__ void k_assemble_springs(int nb, int n, int np, int mu, Geo g0, const SysGeo* __restrict__ systab,
+                                   const int* __restrict__ sysid, const int32_t* __restrict__ ends,
+                                   const double* __restrict__ arms, const double* __restrict__ kappa,
+                                   const double* __restrict__ rest, const double* __restrict__ xw,
+                                   const double* __restrict__ axis, const double* __restrict__ unc,
+                                   int32_t* __restrict__ pairs, double* __restrict__ phi, double* __restrict__ dgeom,
+                                   double* __restrict__ q, double* __restrict__ comp64, int* __restrict__ flags)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < mu) comp64[t] = -1.0;
+    if (t >= nb) return;
+    const int b = t, i = ends[2 * (size_t)b], j = ends[2 * (size_t)b + 1];
+    const double sP = arms[2 * (size_t)b], sQ = arms[2 * (size_t)b + 1], kp = kappa[b], r0 = rest[b];
+    bool ok = i >= 0 && i < n && j >= 0 && j < n && i != j && kp > 0.0 && isfinite(kp) && isfinite(sP) &&
+              isfinite(sQ) && isfinite(r0);
+    if (ok && systab && sysid[i] != sysid[j]) ok = false;   // a batch spring stays inside one system
+    if (!ok) {
+        if (atomicCAS(&flags[F_ERR], 0, ALENS_ERR_INVALID) == 0) flags[F_ERR_ROD] = mu + b;
+        return;
+    }
+    const Geo& g = geo_of(g0, systab, sysid, i);
+    double yP[3], yQ[3], r[3], e[3];
+    int k[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        yP[a] = sP * axis[a * (size_t)np + i];
+        yQ[a] = sQ * axis[a * (size_t)np + j];
+        const double d = xw[a * (size_t)np + i] + yP[a] - xw[a * (size_t)np + j] - yQ[a];
+        int kk = (int)nearbyint(d / g.box[a]);
+        kk = kk > 1 ? 1 : (kk < -1 ? -1 : kk);
+        k[a] = kk;
+        r[a] = d - (double)kk * g.box[a];
+    }
+    const double len = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) e[a] = len > 0.0 ? r[a] / len : (a == 0 ? 1.0 : 0.0);
+    const double ta[3] = {yP[1] * e[2] - yP[2] * e[1], yP[2] * e[0] - yP[0] * e[2], yP[0] * e[1] - yP[1] * e[0]};
+    const double tb[3] = {yQ[1] * e[2] - yQ[2] * e[1], yQ[2] * e[0] - yQ[0] * e[2], yQ[0] * e[1] - yQ[1] * e[0]};
+    const size_t row = (size_t)mu + b;
+    double* dg = dgeom + 9 * row;
+    double dtu = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        dg[a] = e[a];
+        dg[3 + a] = ta[a];
+        dg[6 + a] = tb[a];
+        dtu += e[a] * (unc[a * (size_t)np + i] - unc[a * (size_t)np + j]);
+        dtu += ta[a] * unc[(3 + a) * (size_t)np + i] - tb[a] * unc[(3 + a) * (size_t)np + j];
+    }
+    pairs[3 * row] = i;
+    pairs[3 * row + 1] = j;
+    pairs[3 * row + 2] = (k[0] + 1) + 3 * (k[1] + 1) + 9 * (k[2] + 1);
+    phi[row] = len;
+    q[row] = (len - r0) / g.dt + dtu;
+    comp64[row] = 1.0 / (g.dt * kp);
+}
+
 static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
+
+cudaError_t launch_assemble_springs(aLENS_ctx* ctx, int n, int mu)
+{
+    const int nb = (int)ctx->sp_n;
+    const int work = nb > mu ? nb : mu;
+    if (work <= 0) return cudaSuccess;
+    k_assemble_springs<<<nblk(work, 256), 256, 0, ctx->stream>>>(
+        nb, n, (int)ctx->max_rods, mu, ctx->geo, ctx->cur_systab, ctx->cur_sysid, ctx->sp_ends, ctx->sp_arms,
+        ctx->sp_kappa, ctx->sp_rest, ctx->xw, ctx->axis, ctx->unc, ctx->pairs, ctx->phi, ctx->dgeom, ctx->q64,
+        ctx->comp64, ctx->dflags);
+    ++ctx->launches;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, double* phi, double* dgeom, double* q)
 {
@@ -322,7 +403,7 @@ static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     if (m <= 0) return cudaGetLastError();
     k_setup_fill<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->perm, pairs, rank, dgeom, q, gamma_in, ctx->rowQ,
                                                   ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0], sb.gg[1],
-                                                  sb.rec_lo, sb.q_lo);
+                                                  sb.rec_lo, sb.q_lo, ctx->cur_comp, sb.comp);
     ++ctx->launches;
     k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
     ++ctx->launches;

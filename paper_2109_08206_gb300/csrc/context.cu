@@ -86,7 +86,8 @@ void free_all(aLENS_ctx* c)
                     c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand, c->keep,
                     c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->perm, c->rank, c->curP, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
                     c->q64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp,
-                    c->systab, c->sysid, c->sysoff, c->sys_order, c->sys_iters, c->sys_res, c->adj_ws};
+                    c->systab, c->sysid, c->sysoff, c->sys_order, c->sys_iters, c->sys_res, c->adj_ws,
+                    c->sp_ends, c->sp_arms, c->sp_kappa, c->sp_rest, c->comp64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free(c->batch_host);
@@ -144,6 +145,7 @@ void single_mode(aLENS_ctx* c)
 {
     c->cur_systab = nullptr;
     c->cur_sysid = nullptr;
+    c->cur_comp = nullptr;
     c->cur_nkeys = 1 << (3 * c->geo.bits);
 }
 
@@ -376,7 +378,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->q64, mp * sizeof(double)) == cudaSuccess;
     // solver buffers, sized for float64; the float32 views alias the same memory
     // every slice starts on a 64-byte boundary (vector loads): 8 elements of slack each
-    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 12 * np + mp + 4 * np + 8 * 11;
+    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 12 * np + mp + 4 * np + mp + 8 * 12;
     ok &= dmalloc((char**)&c->solve_ws, solve_elems * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->partials, (size_t)c->max_blocks * 4 * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->bstart, ((size_t)c->max_blocks + 1) * sizeof(int)) == cudaSuccess;
@@ -403,6 +405,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         s.gref = carve64(mp);
         s.rec = carve64(9 * mp); s.qe = carve64(8 * mp); s.q = carve64(mp); s.ax = carve64(3 * np);
         s.mobr = carve64(4 * np);
+        s.comp = carve64(mp);
         float* fb = (float*)c->solve_ws;
         size_t f = 0;
         auto carve32 = [&](size_t cnt) { float* r = fb + f; f = (f + cnt + 7) & ~(size_t)7; return r; };
@@ -411,6 +414,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         t.gref = carve32(mp);
         t.rec = carve32(9 * mp); t.qe = carve32(8 * mp); t.q = carve32(mp); t.ax = carve32(3 * np);
         t.mobr = carve32(4 * np);
+        t.comp = carve32(mp);
         // the float32 views use at most half of the workspace: room for the low parts
         t.rec_lo = carve32(9 * mp); t.qe_lo = carve32(8 * mp); t.q_lo = carve32(mp);
     }
@@ -601,26 +605,38 @@ static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, 
         if (info) { memset(info, 0, sizeof(*info)); info->status = st; info->n_pairs = (int64_t)c->hcount[C_PAIRS]; }
         return st;
     }
-    long long m = (long long)c->hcount[C_PAIRS];
+    const long long mu = (long long)c->hcount[C_PAIRS];   // collisions
+    const long long m = mu + c->sp_n;                      // collisions, then springs
     if (m > c->max_pairs) {
-        if (info) { memset(info, 0, sizeof(*info)); info->status = ALENS_ERR_CAPACITY; info->n_pairs = m; }
+        if (info) { memset(info, 0, sizeof(*info)); info->status = ALENS_ERR_CAPACITY; info->n_pairs = mu; }
         return ALENS_ERR_CAPACITY;
     }
     CK(launch_emit_pairs(c, (int)n, c->pairs));
     CK(cudaEventRecord(c->ev[1], c->stream));
-    CK(launch_assemble(c, (int)n, (int)m, c->pairs, c->phi, c->dgeom, c->q64));
+    CK(launch_assemble(c, (int)n, (int)mu, c->pairs, c->phi, c->dgeom, c->q64));
+    if (c->sp_n > 0) {
+        CK(launch_assemble_springs(c, (int)n, (int)mu));
+        if ((st = read_status(c)) != ALENS_OK) return st;
+        if (c->hflags[F_ERR] != 0) {   // a bad spring: nothing moved
+            if (info) { memset(info, 0, sizeof(*info)); info->status = c->hflags[F_ERR]; info->n_pairs = mu; }
+            return (aLENS_status)c->hflags[F_ERR];
+        }
+        c->cur_comp = c->comp64;
+    }
     CK(launch_rank(c, (int)n));
     CK(launch_solve_setup(c, (int)n, (int)m, c->pairs, c->dgeom, c->q64, nullptr, quat, c->p.precision, c->rank));
     if ((st = run_solver(c, (int)n, (int)m, info, c->ev[2], c->ev[3])) != ALENS_OK) return st;
+    c->cur_comp = nullptr;
     CK(launch_update(c, (int)n, (int)m, x, quat, c->p.precision, vel_out, c->rank));
     CK(cudaEventRecord(c->ev[4], c->stream));
     if (gamma_out) CK(launch_gamma_out(c, (int)m, c->p.precision, gamma_out));
-    if (pairs_out && m > 0)
-        CK(cudaMemcpyAsync(pairs_out, c->pairs, sizeof(int32_t) * 3 * (size_t)m, cudaMemcpyDeviceToDevice, c->stream));
+    if (pairs_out && mu > 0)
+        CK(cudaMemcpyAsync(pairs_out, c->pairs, sizeof(int32_t) * 3 * (size_t)mu, cudaMemcpyDeviceToDevice, c->stream));
     if ((st = read_status(c)) != ALENS_OK) return st;
     st = solve_status(c, m);
     fill_info(c, info, m, st);
     if (info) {
+        info->n_pairs = mu;
         info->ms_build = elapsed(c->ev[0], c->ev[1]);
         info->ms_assemble = elapsed(c->ev[1], c->ev[2]);
         info->ms_solve = elapsed(c->ev[2], c->ev[3]);
@@ -640,6 +656,46 @@ aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const 
     return step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
 }
 
+aLENS_status aLENS_set_springs(aLENS_ctx* c, int64_t n_springs, const int32_t* ends, const double* arms,
+                               const double* kappa, const double* rest)
+{
+    if (!c || n_springs < 0 || n_springs > c->max_pairs) return ALENS_ERR_INVALID;
+    if (n_springs > 0 && (!ends || !arms || !kappa || !rest)) return ALENS_ERR_INVALID;
+    if (n_springs > c->sp_cap) {
+        CK(cudaStreamSynchronize(c->stream));
+        void* old[] = {c->sp_ends, c->sp_arms, c->sp_kappa, c->sp_rest};
+        for (void* q : old)
+            if (q) cudaFree(q);
+        c->sp_ends = nullptr; c->sp_arms = nullptr; c->sp_kappa = nullptr; c->sp_rest = nullptr;
+        c->sp_cap = 0;
+        c->sp_n = 0;
+        const size_t nb = (size_t)n_springs;
+        if (dmalloc(&c->sp_ends, 2 * nb * sizeof(int32_t)) != cudaSuccess ||
+            dmalloc(&c->sp_arms, 2 * nb * sizeof(double)) != cudaSuccess ||
+            dmalloc(&c->sp_kappa, nb * sizeof(double)) != cudaSuccess ||
+            dmalloc(&c->sp_rest, nb * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return ALENS_ERR_NOMEM;
+        }
+        c->sp_cap = n_springs;
+    }
+    if (n_springs > 0 && !c->comp64) {
+        if (dmalloc(&c->comp64, (size_t)c->max_pairs * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return ALENS_ERR_NOMEM;
+        }
+    }
+    const size_t nb = (size_t)n_springs;
+    if (nb > 0) {
+        CK(cudaMemcpyAsync(c->sp_ends, ends, 2 * nb * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->sp_arms, arms, 2 * nb * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->sp_kappa, kappa, nb * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->sp_rest, rest, nb * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    c->sp_n = n_springs;
+    return ALENS_OK;
+}
+
 aLENS_status aLENS_step_adjoint(aLENS_ctx* c, int64_t n, const double* x, const double* quat, const double* f_nc,
                                 int64_t n_pairs, const int32_t* pairs, const double* gamma, const double* dL_dx_new,
                                 const double* dL_dquat_new, double* dL_dx, double* dL_dquat, double* dL_dfnc,
@@ -649,6 +705,7 @@ aLENS_status aLENS_step_adjoint(aLENS_ctx* c, int64_t n, const double* x, const 
     if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
     if (n > 0 && (!x || !quat || !dL_dx || !dL_dquat)) return ALENS_ERR_INVALID;
     if (n_pairs > 0 && (!pairs || !gamma)) return ALENS_ERR_INVALID;
+    if (c->sp_n > 0) return ALENS_ERR_NOT_IMPLEMENTED;   // the adjoint covers collision constraints only
     if (cudaGetLastError() != cudaSuccess) return ALENS_ERR_CUDA;
     if (adjoint_reserve(c) != cudaSuccess) { cudaGetLastError(); return ALENS_ERR_NOMEM; }
     aLENS_status st = reset_status(c);

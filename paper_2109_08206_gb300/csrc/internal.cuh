@@ -188,6 +188,7 @@ struct SolveBufs {           // typed views into the solver workspace
     T* rec_lo;               // [9][mp]
     T* qe_lo;                // [mp][8]
     T* q_lo;                 // [mp]
+    T* comp;                 // [mp] < 0 collision, >= 0 spring compliance 1/(h kappa) (solver order)
 };
 
 }  // namespace alens
@@ -274,6 +275,14 @@ struct aLENS_ctx {
     double* sys_res;         // [max_systems] final residual of each system
     int last_batch_n;        // systems of the last completed aLENS_step_batch (0: none)
     void* adj_ws;            // adjoint workspace (allocated by the first aLENS_step_adjoint)
+    // springs (aLENS_set_springs): bilateral constraints appended to every step's collisions
+    int32_t* sp_ends;        // [sp_cap][2] rods P, Q
+    double* sp_arms;         // [sp_cap][2] attachment arclengths on P and Q
+    double* sp_kappa;        // [sp_cap]
+    double* sp_rest;         // [sp_cap]
+    int64_t sp_n, sp_cap;
+    double* comp64;          // [mp] pair order: -1 collisions, 1/(h kappa) springs (allocated with the springs)
+    const double* cur_comp;  // comp64 while a step with springs is set up and solved, else NULL
     int batch_threads;       // per-system solver: threads per block
     int batch_cluster;       // per-system solver: blocks per cluster
 };
@@ -309,6 +318,10 @@ cudaError_t launch_rank(aLENS_ctx* ctx, int n);
 // solve.cu
 cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision);
 cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma_out);
+
+// Springs: rows mu .. mu + nb of the internal constraint list (pairs, phi,
+// dgeom, q) and comp64 for every row (collisions -1).
+cudaError_t launch_assemble_springs(aLENS_ctx* ctx, int n, int mu);
 
 // adjoint.cu: workspace (once) and the adjoint pipeline after pack, assembly
 // and the solver setup of the forward step's pair list (identity ranks).

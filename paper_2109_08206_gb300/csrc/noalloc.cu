@@ -38,7 +38,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kRodInts = align256(sizeof(int) * (kNoallocMaxRods + 1));
 constexpr size_t kPairInts = align256(sizeof(int) * kNoallocMaxPairs);
 constexpr size_t kSolveWs =
-    align256(sizeof(double) * (27 * (size_t)kNoallocMaxPairs + 19 * (size_t)kNoallocMaxRods + 88));
+    align256(sizeof(double) * (28 * (size_t)kNoallocMaxPairs + 19 * (size_t)kNoallocMaxRods + 96));
 constexpr size_t kPartials = align256(sizeof(double) * 4 * kNoallocMaxBlocks);
 constexpr size_t kBstart = align256(sizeof(int) * (kNoallocMaxBlocks + 1));
 constexpr int kScanTmpLen = (kNoallocMaxRods + 4095) / 4096 + 2;
@@ -141,6 +141,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
         c.sb64.gref = c64(mp);
         c.sb64.rec = c64(9 * mp); c.sb64.qe = c64(8 * mp); c.sb64.q = c64(mp); c.sb64.ax = c64(3 * np);
         c.sb64.mobr = c64(4 * np);
+        c.sb64.comp = c64(mp);
         float* b32 = (float*)c.solve_ws;
         size_t v = 0;
         auto c32 = [&](size_t cnt) { float* r = b32 + v; v = (v + cnt + 7) & ~(size_t)7; return r; };
@@ -148,6 +149,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
         c.sb32.gref = c32(mp);
         c.sb32.rec = c32(9 * mp); c.sb32.qe = c32(8 * mp); c.sb32.q = c32(mp); c.sb32.ax = c32(3 * np);
         c.sb32.mobr = c32(4 * np);
+        c.sb32.comp = c32(mp);
         // the float32 views use at most half of the workspace: room for the low parts
         c.sb32.rec_lo = c32(9 * mp); c.sb32.qe_lo = c32(8 * mp); c.sb32.q_lo = c32(mp);
     }

@@ -120,6 +120,9 @@ __device__ __forceinline__ void ld_state(const double* p, int c, double& d, doub
     const double2 a = q[0], b = q[1];
     d = a.x; g = a.y; gr = b.x; gl = b.y;
 }
+__device__ __forceinline__ float gl_of_state(const float* p, int c) { return p[4 * (size_t)c + 3]; }
+__device__ __forceinline__ double gl_of_state(const double* p, int c) { return p[4 * (size_t)c + 3]; }
+
 // (delta, g) and (gamma_ref, gamma_lo) halves of a state
 template <typename T>
 __device__ __forceinline__ void st_dg(T* p, int c, T d, T g)
@@ -195,6 +198,7 @@ struct SolveArgs {
     double* out;   // [0] residual, [1] alpha0
     T inv_perp, inv_par, inv_rot, inv_spin;
     const T* __restrict__ mobr;   // [4][np] per-rod inverse drags (batches), or NULL for the uniform ones
+    const T* __restrict__ comp;   // [mp] per constraint: < 0 collision, >= 0 spring compliance 1/(h kappa); NULL: all collisions
     const T* __restrict__ rec_lo; // float32: low parts of rec, qe and q for the reference passes (else NULL)
     const T* __restrict__ qe_lo;
     const T* __restrict__ q_lo;
@@ -293,15 +297,23 @@ enum { A_STEP = 0, A_PG = 1, A_REF = 2 };
 // g = gref (delta is 0 there) and pi.pi, max |pi| at gamma_ref.
 enum { B_STEP = 0, B_REF = 2 };
 
+// bil: a spring (bilateral) constraint, whose force has no sign constraint
+// (Eq. linearconstraints b): no projection.
 template <int MODE, typename T>
-__device__ __forceinline__ T a_value(T d, T g, T gr, T alpha)
+__device__ __forceinline__ T a_value(T d, T g, T gr, T alpha, bool bil)
 {
     if (MODE == A_REF) return gr;
     if (MODE == A_STEP) {
         const T v = d - alpha * g;
-        return v > -gr ? v : -gr;
+        return (bil || v > -gr) ? v : -gr;
     }
-    return d > -gr ? g : (g < T(0) ? g : T(0));   // projected gradient at gamma = gr + d
+    return (bil || d > -gr) ? g : (g < T(0) ? g : T(0));   // projected gradient at gamma = gr + d
+}
+
+template <typename T>
+__device__ __forceinline__ T comp_of(const SolveArgs<T>& a, int c)
+{
+    return a.comp ? __ldg(&a.comp[c]) : T(-1);
 }
 
 template <typename T, int MODE, bool ST>
@@ -346,7 +358,9 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
 #pragma unroll
                 for (int u = 0; u < BO; ++u) {
                     if (c + u < e) {
-                        const T v = a_value<MODE, T>(dv[u], gv[u], rv_[u], alpha);
+                        const T cmp = comp_of(a, c + u);
+                        const T v = a_value<MODE, T>(dv[u], gv[u], rv_[u], alpha, cmp >= T(0));
+                        if (MODE == A_PG && cmp >= T(0)) fmf += cmp * v * v;   // the spring's compliance term
                         if (MODE == A_STEP) {
                             if (ST) sdn[c + u - o.c0] = v;       // global copy written in phase B
                             else gn[4 * (size_t)(c + u)] = v;
@@ -394,7 +408,7 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
                     if (cid[u] >= 0) {
-                        const T v = a_value<MODE, T>(dv[u], gv[u], rv_[u], alpha);
+                        const T v = a_value<MODE, T>(dv[u], gv[u], rv_[u], alpha, comp_of(a, cid[u]) >= T(0));
 #pragma unroll
                         for (int w = 0; w < 6; ++w) Fa[w].add_prod(-v, qv[u][w]);
                         if (MODE == A_REF && COMP) {
@@ -502,6 +516,19 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
             du.add_prod(r[3 + u], Ui[3 + u]);
             du.add_prod(-r[6 + u], Uj[3 + u]);
         }
+        // springs: + (1/(h kappa)) gamma (Eq. blockdef F); the increment's
+        // part in a step, the whole force in a reference pass
+        const T cmp = comp_of(a, c);
+        const bool bil = cmp >= T(0);
+        if (bil) {
+            if (MODE == B_STEP) {
+                du.add_prod(cmp, dm);
+            } else {
+                const T glo = gl_of_state(gnew, c);
+                du.add_prod(cmp, gam);
+                du.add_lo(cmp * glo);
+            }
+        }
         if (MODE == B_REF && COMP) {
             // low parts of q and of the record
             T rl[9];
@@ -525,7 +552,7 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
         } else {
             gnew[4 * (size_t)c + 1] = gr;
         }
-        const T pi = dm > -gam ? gr : (gr < T(0) ? gr : T(0));
+        const T pi = (bil || dm > -gam) ? gr : (gr < T(0) ? gr : T(0));
         const T api = pi < T(0) ? -pi : pi;
         acc[3] = api > acc[3] ? api : acc[3];
         if (MODE == B_REF) {
@@ -558,14 +585,15 @@ __device__ __forceinline__ void fold_delta(const SolveArgs<T>& a, const Own<T>& 
         if (ST) {
             d = sdc[lc]; g = o.grs[lc]; gr = o.gam[lc];
         }
+        const bool bil = comp_of(a, c) >= T(0);   // springs: no bound
         T hi = T(0), lo = T(0);
-        if (d > -gr) {
+        if (bil || d > -gr) {
             T s, e;
             two_sum(gr, d, s, e);
             const T l = gl + e;
             hi = s + l;
             lo = l - (hi - s);
-            if (hi < T(0) || (hi == T(0) && lo < T(0))) { hi = T(0); lo = T(0); }
+            if (!bil && (hi < T(0) || (hi == T(0) && lo < T(0)))) { hi = T(0); lo = T(0); }
         }
         if (ST) {
             sdc[lc] = T(0);
@@ -1066,6 +1094,7 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.inv_rot = (T)ctx->mob.inv_rot; a.inv_spin = (T)ctx->mob.inv_spin;
     a.mobr = ctx->cur_systab ? sb.mobr : nullptr;
     a.rec_lo = sb.rec_lo; a.qe_lo = sb.qe_lo; a.q_lo = sb.q_lo;
+    a.comp = ctx->cur_comp ? sb.comp : nullptr;
     a.hD = ctx->p.dt / ctx->p.diameter; a.tol = ctx->p.tol; a.max_iter = ctx->p.max_iter;
     a.wait_cycles = (long long)(ctx->wait_s * ctx->clock_khz * 1e3);
     a.fault = 0;
