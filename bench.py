@@ -383,9 +383,7 @@ class SpringJob(SingleJob):
 
     def context(self, A, precision, tol, stream):
         import torch
-        ctx = super().context(A, precision, tol, stream)
         p = A.params_of(self.s, precision=precision, tol=tol, max_iter=1_000_000)
-        ctx.close()
         ctx = A.Context(p, self.n, 12 * self.n + self.nb, stream=stream)
         dev = torch.device("cuda", torch.cuda.current_device())
         sp = self.sp
