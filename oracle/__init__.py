@@ -67,6 +67,10 @@ def lib():
             "orc_solve_enum": (i64, [i64, vp, P, i64, vp, vp, vp, vp, vp]),
             "orc_solve_apgd": (d, [i64, vp, P, i64, vp, vp, vp, vp, vp, d, i64, vp]),
             "orc_assemble_springs": (None, [i64, vp, vp, vp, P, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "orc_philox4x32": (None, [vp, vp, vp]),
+            "orc_normals6": (None, [C.c_uint64, C.c_uint64, i64, vp]),
+            "orc_brownian": (None, [i64, vp, P, d, C.c_uint64, C.c_uint64, vp, vp]),
+            "orc_assemble_walls": (i64, [i64, vp, vp, vp, P, C.c_int, d, d, i64, vp, vp, vp, vp]),
             "orc_update": (None, [i64, vp, vp, vp, P, i64, vp, vp, vp, vp, vp, vp]),
             "orc_step": (i64, [i64, vp, vp, vp, P, d, i64, i64, vp, vp, vp, vp, vp, vp, vp]),
         }
@@ -256,25 +260,72 @@ def update(x, quat, fnc, pb: Problem, pairs, dgeom, gamma):
     return xo, qo, U
 
 
-def step(x, quat, fnc, pb: Problem, tol=1e-12, max_iter=1_000_000, max_pairs=None, springs=None):
+def philox4x32(ctr, key):
+    """Philox4x32-10 of four 32-bit counter words and a two-word key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32(_p(c), _p(k), _p(out))
+    return out
+
+
+def normals6(seed, step, i):
+    z = np.zeros(6)
+    lib().orc_normals6(int(seed), int(step), int(i), _p(z))
+    return z
+
+
+def brownian(quat, pb: Problem, kT, seed, step, f_ext=None):
+    """F_nc of one trajectory step: f_ext plus the Brownian force and torque."""
+    quat = _f64(quat, (-1, 4))
+    out = np.zeros((quat.shape[0], 6))
+    fe = None if f_ext is None else _f64(f_ext, (-1, 6))
+    lib().orc_brownian(quat.shape[0], _p(quat), C.byref(pb), float(kT), int(seed), int(step), _p(fe), _p(out))
+    return out
+
+
+def assemble_walls(x, quat, fnc, pb: Problem, axis_w, lo, hi):
+    """One-sided wall constraints: dict pairs (i, -1, 2 side + end), dgeom, q, phi."""
+    x, quat, fnc = _f64(x, (-1, 3)), _f64(quat, (-1, 4)), _f64(fnc, (-1, 6))
+    n = x.shape[0]
+    cnt = lib().orc_assemble_walls(n, _p(x), _p(quat), _p(fnc), C.byref(pb), int(axis_w), float(lo), float(hi), 0,
+                                   None, None, None, None)
+    pr = np.zeros((max(cnt, 1), 3), dtype=np.int32)
+    dg, q, ph = np.zeros((max(cnt, 1), 9)), np.zeros(max(cnt, 1)), np.zeros(max(cnt, 1))
+    lib().orc_assemble_walls(n, _p(x), _p(quat), _p(fnc), C.byref(pb), int(axis_w), float(lo), float(hi), cnt,
+                             _p(pr), _p(dg), _p(q), _p(ph))
+    return {"pairs": pr[:cnt], "dgeom": dg[:cnt], "q": q[:cnt], "phi": ph[:cnt]}
+
+
+def step(x, quat, fnc, pb: Problem, tol=1e-12, max_iter=1_000_000, max_pairs=None, springs=None, walls=None):
     """One full constrained step; returns a dict of every intermediate.
 
     ``springs`` (nullable): dict of ends [nb, 2], arms [nb, 2], kappa [nb],
     rest [nb]: bilateral constraints solved together with the collisions
-    (Eq. linearconstraints b); ``gamma`` then holds the collision forces
-    followed by the spring forces."""
+    (Eq. linearconstraints b).  ``walls`` (nullable): (axis, lo, hi), two
+    flat confining walls (one-sided constraints).  ``gamma`` holds the
+    collision forces, then the wall forces, then the spring forces."""
     x, quat, fnc = _f64(x, (-1, 3)), _f64(quat, (-1, 4)), _f64(fnc, (-1, 6))
     pairs = find_pairs(x, quat, pb)
     asm = assemble(x, quat, fnc, pb, pairs)
-    if springs is None:
+    if springs is None and walls is None:
         gamma, res, iters = solve_apgd(quat, pb, pairs, asm["dgeom"], asm["q"], tol=tol, max_iter=max_iter)
         xo, qo, U = update(x, quat, fnc, pb, pairs, asm["dgeom"], gamma)
         return {"pairs": pairs, **asm, "gamma": gamma, "residual": res, "iters": iters, "x": xo, "quat": qo, "U": U}
-    sb = assemble_springs(x, quat, fnc, pb, springs["ends"], springs["arms"], springs["kappa"], springs["rest"])
-    allp = np.concatenate([pairs.reshape(-1, 3), sb["pairs"]]).astype(np.int32)
-    dg = np.concatenate([asm["dgeom"].reshape(-1, 9), sb["dgeom"]])
-    q = np.concatenate([asm["q"], sb["q"]])
-    comp = np.concatenate([-np.ones(pairs.shape[0]), sb["comp"]])
+    rows_p, rows_d, rows_q = [pairs.reshape(-1, 3)], [asm["dgeom"].reshape(-1, 9)], [asm["q"]]
+    comps = [-np.ones(pairs.shape[0])]
+    wb = sb = None
+    if walls is not None:
+        wb = assemble_walls(x, quat, fnc, pb, *walls)
+        rows_p.append(wb["pairs"]); rows_d.append(wb["dgeom"]); rows_q.append(wb["q"])
+        comps.append(-np.ones(wb["pairs"].shape[0]))
+    if springs is not None:
+        sb = assemble_springs(x, quat, fnc, pb, springs["ends"], springs["arms"], springs["kappa"], springs["rest"])
+        rows_p.append(sb["pairs"]); rows_d.append(sb["dgeom"]); rows_q.append(sb["q"]); comps.append(sb["comp"])
+    allp = np.concatenate(rows_p).astype(np.int32)
+    dg = np.concatenate(rows_d)
+    q = np.concatenate(rows_q)
+    comp = np.concatenate(comps)
     if allp.shape[0] <= 20:
         gamma, _ = solve_enum(quat, pb, allp, dg, q, comp=comp)
         res = gradient(quat, pb, allp, dg, q, gamma, comp=comp)[1]
@@ -282,8 +333,27 @@ def step(x, quat, fnc, pb: Problem, tol=1e-12, max_iter=1_000_000, max_pairs=Non
     else:
         gamma, res, iters = solve_apgd(quat, pb, allp, dg, q, tol=tol, max_iter=max_iter, comp=comp)
     xo, qo, U = update(x, quat, fnc, pb, allp, dg, gamma)
-    return {"pairs": pairs, **asm, "springs": sb, "all_pairs": allp, "all_dgeom": dg, "all_q": q, "comp": comp,
-            "gamma": gamma, "residual": res, "iters": iters, "x": xo, "quat": qo, "U": U}
+    return {"pairs": pairs, **asm, "springs": sb, "walls": wb, "all_pairs": allp, "all_dgeom": dg, "all_q": q,
+            "comp": comp, "gamma": gamma, "residual": res, "iters": iters, "x": xo, "quat": qo, "U": U}
+
+
+def trajectory(x, quat, pb: Problem, n_steps, kT, seed, first_step=0, f_ext=None, springs=None, walls=None,
+               tol=1e-12):
+    """n_steps constrained Brownian steps (F_nc = f_ext + the Brownian force
+    of step first_step + k); returns (x, quat, per-step list of dicts with
+    the pair count, residual and minimum gap)."""
+    x, quat = _f64(x, (-1, 3)).copy(), _f64(quat, (-1, 4)).copy()
+    stats = []
+    for k in range(n_steps):
+        fnc = brownian(quat, pb, kT, seed, first_step + k, f_ext)
+        out = step(x, quat, fnc, pb, tol=tol, springs=springs, walls=walls)
+        gaps = [out["phi"]] if out["pairs"].shape[0] else []
+        if out.get("walls") is not None and out["walls"]["pairs"].shape[0]:
+            gaps.append(out["walls"]["phi"])
+        stats.append({"n_pairs": int(out["pairs"].shape[0]), "residual": out["residual"],
+                      "min_gap": float(np.min(np.concatenate(gaps))) if gaps else float("inf")})
+        x, quat = out["x"], out["quat"]
+    return x, quat, stats
 
 
 def step_native(x, quat, fnc, pb: Problem, tol, max_iter, max_pairs):

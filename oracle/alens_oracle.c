@@ -496,6 +496,7 @@ ORC_API void orc_apply_D(int64_t n, int64_t npairs, const int32_t* pairs, const 
         for (int m = 0; m < 3; ++m) {
             F[6 * i + m] += g * dg[m];
             F[6 * i + 3 + m] += g * dg[3 + m];
+            if (j < 0) continue;   /* a wall: one-sided column */
             F[6 * j + m] -= g * dg[m];
             F[6 * j + 3 + m] -= g * dg[6 + m];
         }
@@ -510,8 +511,8 @@ ORC_API void orc_apply_Dt(int64_t npairs, const int32_t* pairs, const double* dg
     for (int64_t c = 0; c < npairs; ++c) {
         int64_t i = pairs[3 * c], j = pairs[3 * c + 1];
         const double* dg = dgeom + 9 * c;
-        out[c] = dot3(dg, U + 6 * i) + dot3(dg + 3, U + 6 * i + 3) - dot3(dg, U + 6 * j) -
-                 dot3(dg + 6, U + 6 * j + 3);
+        out[c] = dot3(dg, U + 6 * i) + dot3(dg + 3, U + 6 * i + 3);
+        if (j >= 0) out[c] -= dot3(dg, U + 6 * j) + dot3(dg + 6, U + 6 * j + 3);
     }
 }
 
@@ -757,6 +758,133 @@ ORC_API double orc_solve_apgd(int64_t n, const double* quat, const orc_problem* 
     free(v); free(w); free(z); free(gz); free(gn);
     qp_free(&qp);
     return res;
+}
+
+/* -------------------------------------------------------- Brownian forces */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11, "Parallel random
+ * numbers: as easy as 1, 2, 3"): ten rounds of two 32x32->64 multiplications
+ * (multipliers 0xD2511F53 and 0xCD9E8D57) whose high halves are mixed with
+ * the other counter words and the key; the key is bumped by the Weyl
+ * constants 0x9E3779B9 and 0xBB67AE85 between rounds. */
+ORC_API void orc_philox4x32(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Six standard normals for rod i at step k from seed: Philox with key =
+ * (seed low, seed high) and counters (i, k low, k high, w) for w = 0, 1;
+ * each word gives u = (x + 0.5) 2^-32 in (0, 1) and each pair (u1, u2) two
+ * normals by Box-Muller: sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2). */
+ORC_API void orc_normals6(uint64_t seed, uint64_t step, int64_t i, double z[6])
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double u[8];
+    for (int w = 0; w < 2; ++w) {
+        const uint32_t ctr[4] = {(uint32_t)i, (uint32_t)step, (uint32_t)(step >> 32), (uint32_t)w};
+        uint32_t o[4];
+        orc_philox4x32(ctr, key, o);
+        for (int k = 0; k < 4; ++k) u[4 * w + k] = ((double)o[k] + 0.5) * (1.0 / 4294967296.0);
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double r = sqrt(-2.0 * log(u[2 * k]));
+        z[2 * k] = r * cos(2.0 * M_PI * u[2 * k + 1]);
+        z[2 * k + 1] = r * sin(2.0 * M_PI * u[2 * k + 1]);
+    }
+}
+
+/* Brownian force and torque of every rod at step k, consistent with the
+ * mobility (fluctuation-dissipation: covariance 2 kT M^-1 / h per rod):
+ *   F = sqrt(2 kT / h) [sqrt(zeta_par) (p.xi) p + sqrt(zeta_perp) (xi - (p.xi) p)],
+ *   T = sqrt(2 kT / h) [sqrt(zeta_spin) (p.chi) p + sqrt(zeta_rot) (chi - (p.chi) p)],
+ * xi, chi = the six normals of (seed, k, i); added to f_ext (nullable) into out. */
+ORC_API void orc_brownian(int64_t n, const double* quat, const orc_problem* pb, double kT, uint64_t seed,
+                          uint64_t step, const double* f_ext, double* out)
+{
+    double zeta[4];
+    orc_drag(pb->viscosity, pb->length, pb->diameter, zeta);
+    double* axis = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    orc_axis(n, quat, axis);
+    const double a = sqrt(2.0 * kT / pb->dt);
+    for (int64_t i = 0; i < n; ++i) {
+        double z[6];
+        orc_normals6(seed, step, i, z);
+        const double* p = axis + 3 * i;
+        const double pt = dot3(p, z), pr = dot3(p, z + 3);
+        for (int m = 0; m < 3; ++m) {
+            double ft = a * (sqrt(zeta[1]) * pt * p[m] + sqrt(zeta[0]) * (z[m] - pt * p[m]));
+            double fr = a * (sqrt(zeta[3]) * pr * p[m] + sqrt(zeta[2]) * (z[3 + m] - pr * p[m]));
+            out[6 * i + m] = (f_ext ? f_ext[6 * i + m] : 0.0) + ft;
+            out[6 * i + 3 + m] = (f_ext ? f_ext[6 * i + 3 + m] : 0.0) + fr;
+        }
+    }
+    free(axis);
+}
+
+/* ------------------------------------------------------------------ walls */
+
+/* Confinement by two flat walls normal to axis w at coordinates lo < hi
+ * (Appendix: a collision with an external boundary keeps only the
+ * particle's side of the column).  The lowest point of a segment over a
+ * plane is one of its ends (both, when it lies flat), so each end of a rod,
+ * y = s p with s = -L/2 and s = +L/2, is a contact candidate with each wall:
+ * gap Phi = x_w + s p_w - lo - D/2 and normal e = +e_w for the lower wall,
+ * Phi = hi - x_w - s p_w - D/2 and e = -e_w for the upper one.  A row is
+ * made when Phi < delta_c: pairs (i, -1, 2 side + end), dgeom (e, y x e, 0),
+ * q = Phi/h + (e, y x e).U_nc, phi.  Rows are in (rod, side, end) order.
+ * Returns the row count (rows written only if cap allows). */
+ORC_API int64_t orc_assemble_walls(int64_t n, const double* x, const double* quat, const double* fnc,
+                                   const orc_problem* pb, int axis_w, double lo, double hi, int64_t cap,
+                                   int32_t* pairs, double* dgeom, double* q, double* phi)
+{
+    double zeta[4];
+    orc_drag(pb->viscosity, pb->length, pb->diameter, zeta);
+    const double hl = 0.5 * pb->length;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double th[4] = {quat[4 * i], quat[4 * i + 1], quat[4 * i + 2], quat[4 * i + 3]};
+        double p[3];
+        orc_axis(1, th, p);
+        const double xw = wrap1(x[3 * i + axis_w], pb->box[axis_w]);
+        for (int side = 0; side < 2; ++side)
+        for (int end = 0; end < 2; ++end) {
+            const double sg = side == 0 ? 1.0 : -1.0;   /* normal into the domain */
+            const double pw = p[axis_w];
+            const double s = end == 0 ? -hl : hl;
+            const double tip = xw + s * pw;
+            const double ph = side == 0 ? tip - lo - 0.5 * pb->diameter : hi - tip - 0.5 * pb->diameter;
+            if (!(ph < pb->delta_c)) continue;
+            if (cnt < cap) {
+                double e[3] = {0.0, 0.0, 0.0}, y[3], ye[3];
+                e[axis_w] = sg;
+                for (int m = 0; m < 3; ++m) y[m] = s * p[m];
+                cross3(y, e, ye);
+                pairs[3 * cnt] = (int32_t)i;
+                pairs[3 * cnt + 1] = -1;
+                pairs[3 * cnt + 2] = 2 * side + end;
+                double* dg = dgeom + 9 * cnt;
+                for (int m = 0; m < 3; ++m) { dg[m] = e[m]; dg[3 + m] = ye[m]; dg[6 + m] = 0.0; }
+                double U[6];
+                mobility_rod(p, zeta, fnc + 6 * i, U);
+                q[cnt] = ph / pb->dt + dot3(e, U) + dot3(ye, U + 3);
+                phi[cnt] = ph;
+            }
+            ++cnt;
+        }
+    }
+    return cnt;
 }
 
 /* ----------------------------------------------------------------- update */
