@@ -186,6 +186,70 @@ ALENS_API aLENS_status aLENS_set_springs(aLENS_ctx* ctx, int64_t n_springs, cons
                                          const double* kappa, const double* rest);
 
 /* ------------------------------------------------------------------------
+ * Multi-step trajectories (Appendix Eq. constrainedeom_euler repeated in
+ * time, with the Brownian force F_B among the non-constraint forces).
+ *
+ * aLENS_set_walls: two flat confining walls normal to axis (0, 1, 2; -1
+ * removes them) at coordinates lo < hi (Appendix: a collision with an
+ * external boundary keeps only the particle's side of the D column).  The
+ * lowest point of a rod over a plane is one of its ends (both when it lies
+ * flat), so each end y = s p (s = -L/2, +L/2) is a contact candidate with
+ * each wall: gap Phi = x_axis + s p_axis - lo - D/2 and normal +e_axis for
+ * the lower wall (the upper wall alike, normal -e_axis); every candidate
+ * with Phi < delta_c is a unilateral constraint solved with the collisions,
+ * its force listed after the collisions (and before the springs) in
+ * gamma_out, in (rod, wall, end) order.  Requires 0 <= lo < hi <= box[axis]
+ * and box[axis] - (hi - lo) >= L + D + delta_c, so that no pair interacts
+ * through the periodic boundary across the walls.  Single systems only
+ * (aLENS_step_batch returns NOT_IMPLEMENTED while walls are set); not
+ * covered by aLENS_step_adjoint. */
+ALENS_API aLENS_status aLENS_set_walls(aLENS_ctx* ctx, int32_t axis, double lo, double hi);
+
+/* The non-constraint force of trajectory step `step`: out [n][6] = f_ext
+ * (nullable) + the Brownian force and torque of every rod, with covariance
+ * 2 kT M^-1 / h per rod (fluctuation-dissipation: the step's displacement
+ * then has covariance 2 kT h M):
+ *   F = sqrt(2 kT / h) [sqrt(zeta_par) (p.xi) p + sqrt(zeta_perp) (xi - (p.xi) p)]
+ *   T = sqrt(2 kT / h) [sqrt(zeta_spin) (p.chi) p + sqrt(zeta_rot) (chi - (p.chi) p)]
+ * where (xi, chi) are six standard normals of (seed, step, rod): the
+ * counter-based generator Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11)
+ * with key (seed low, seed high) and counters (rod, step low, step high, w),
+ * w = 0, 1, each 32-bit word x giving u = (x + 0.5) 2^-32, each pair of
+ * words two normals by Box-Muller.  quat, f_ext, out: device. */
+ALENS_API aLENS_status aLENS_brownian(aLENS_ctx* ctx, int64_t n, const double* quat, double kT, uint64_t seed,
+                                      int64_t step, const double* f_ext, double* out);
+
+/* The eight raw generator words of every rod for (seed, step) (device
+ * out [n][8]): the counters w = 0 then w = 1 of aLENS_brownian. */
+ALENS_API aLENS_status aLENS_random_words(aLENS_ctx* ctx, int64_t n, uint64_t seed, int64_t step, uint32_t* out);
+
+typedef struct {
+    int64_t n_pairs;    /* collisions of the step */
+    int64_t n_walls;    /* wall contacts of the step */
+    int32_t iters;      /* BBPGD iterations */
+    int32_t status;     /* aLENS_status of the step */
+    double residual;
+    double min_gap;     /* min Phi over collisions and wall contacts */
+    float ms_step;      /* device time of the step (search to update) */
+} aLENS_step_stats;
+
+/* n_steps constrained steps of x, quat in place; step k (k = 0 ..
+ * n_steps-1) uses the forces of aLENS_brownian(first_step + k), so that a
+ * long run split into calls reproduces the run done in one call.  Walls and
+ * springs set on the context take part.  warm_start != 0 starts every
+ * solve from the previous step's forces, matched per constraint (a
+ * collision by (i, j, image), a wall contact by (rod, wall, end), a spring
+ * by its index while the spring list is unchanged), instead of from 0.
+ * stats (HOST array [n_steps], nullable) receives per-step figures; info
+ * aggregates (iterations summed, residual max, min_gap min, phase times
+ * summed).  The first call allocates the trajectory buffers (6 doubles per
+ * rod and 4 words per constraint of the context's capacity).  Stops at the
+ * first step whose status is neither OK nor NOT_CONVERGED. */
+ALENS_API aLENS_status aLENS_run(aLENS_ctx* ctx, int64_t n, double* x, double* quat, const double* f_ext,
+                                 int64_t n_steps, double kT, uint64_t seed, int64_t first_step, int32_t warm_start,
+                                 aLENS_step_stats* stats, aLENS_info* info);
+
+/* ------------------------------------------------------------------------
  * Batched step of independent periodic systems.  The paper steps one system
  * (distributed over many processes); an ensemble of many small, uneven
  * systems is stepped here in one call, each system with the step of

@@ -42,6 +42,15 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class StepStats(C.Structure):
+    """aLENS_step_stats (include/alens.h): one step of a trajectory."""
+    _fields_ = [("n_pairs", C.c_int64), ("n_walls", C.c_int64), ("iters", C.c_int32), ("status", C.c_int32),
+                ("residual", C.c_double), ("min_gap", C.c_double), ("ms_step", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class System(C.Structure):
     """aLENS_system (include/alens.h): one system of a batch."""
     _fields_ = [("box", C.c_double * 3), ("length", C.c_double)]
@@ -90,6 +99,10 @@ def lib():
                                          C.POINTER(d), IP]),
             "aLENS_set_batch_launch": (i32, [vp, i32, i32]),
             "aLENS_set_springs": (i32, [vp, i64, vp, vp, vp, vp]),
+            "aLENS_set_walls": (i32, [vp, i32, d, d]),
+            "aLENS_brownian": (i32, [vp, i64, vp, d, C.c_uint64, i64, vp, vp]),
+            "aLENS_random_words": (i32, [vp, i64, C.c_uint64, i64, vp]),
+            "aLENS_run": (i32, [vp, i64, vp, vp, vp, i64, d, C.c_uint64, i64, i32, C.POINTER(StepStats), IP]),
             "aLENS_set_wait_limit": (i32, [vp, d]),
             "aLENS_inject_fault": (i32, [vp, i32]),
             "aLENS_set_launch": (i32, [vp, i32, i32]),
@@ -334,3 +347,41 @@ class Context:
         if st != 0:
             raise AlensError(st, "aLENS_set_springs")
         self._springs = (ends, arms, kappa, rest) if nb > 0 else None   # keep the caller's tensors alive
+
+    def set_walls(self, axis: int = -1, lo: float = 0.0, hi: float = 0.0):
+        """Two flat confining walls normal to `axis` at lo < hi (axis -1 removes them)."""
+        st = self._lib.aLENS_set_walls(self._h, int(axis), float(lo), float(hi))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_walls")
+
+    def brownian(self, quat, kT: float, seed: int, step: int, f_ext=None):
+        """[n, 6] non-constraint force of trajectory step `step` (f_ext + Brownian)."""
+        import torch
+        out = torch.empty((quat.shape[0], 6), dtype=torch.float64, device=quat.device)
+        st = self._lib.aLENS_brownian(self._h, quat.shape[0], _ptr(quat, torch.float64, (4,)), float(kT), int(seed),
+                                      int(step), _ptr(f_ext, torch.float64, (6,)), _ptr(out, torch.float64, (6,)))
+        if st != 0:
+            raise AlensError(st, "aLENS_brownian")
+        return out
+
+    def random_words(self, n: int, seed: int, step: int):
+        """[n, 8] int32 view of the generator's raw 32-bit words (device)."""
+        import torch
+        out = torch.empty((n, 8), dtype=torch.int32, device="cuda")
+        st = self._lib.aLENS_random_words(self._h, int(n), int(seed), int(step), C.c_void_p(out.data_ptr()))
+        if st != 0:
+            raise AlensError(st, "aLENS_random_words")
+        return out
+
+    def run(self, x, quat, n_steps: int, kT: float, seed: int, first_step: int = 0, f_ext=None,
+            warm_start: bool = True, check=True):
+        """n_steps Brownian constrained steps in place; returns (Info, [StepStats dicts])."""
+        import torch
+        stats = (StepStats * max(int(n_steps), 1))()
+        info = Info()
+        st = self._lib.aLENS_run(self._h, x.shape[0], _ptr(x, torch.float64, (3,)), _ptr(quat, torch.float64, (4,)),
+                                 _ptr(f_ext, torch.float64, (6,)), int(n_steps), float(kT), int(seed),
+                                 int(first_step), int(bool(warm_start)), stats, C.byref(info))
+        if check and st != 0:
+            raise AlensError(st, "aLENS_run", info.as_dict())
+        return info, [stats[k].as_dict() for k in range(int(n_steps))]

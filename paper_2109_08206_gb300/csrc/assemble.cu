@@ -136,9 +136,16 @@ __global__ void k_check_pairs(int m, int n, const int32_t* __restrict__ pairs, i
 // The solver numbers rods by rank (their position in the cell-sorted order
 // when one is given, else their id) and gives each constraint to the
 // endpoint of lower rank (the "owner"; the other endpoint is its Q side).
+// A wall row (j = -1) has no other side: rq = -1, owner i.
 __device__ __forceinline__ void owner_other(const int32_t* pairs, const int* rank, int c, int& ro, int& rq, bool& flip)
 {
     int i = pairs[3 * (size_t)c], j = pairs[3 * (size_t)c + 1];
+    if (j < 0) {
+        ro = rank ? rank[i] : i;
+        rq = -1;
+        flip = false;
+        return;
+    }
     int ri = rank ? rank[i] : i, rj = rank ? rank[j] : j;
     flip = ri > rj;
     ro = flip ? rj : ri;
@@ -154,7 +161,7 @@ __global__ void k_count_sides(int m, const int32_t* __restrict__ pairs, const in
     bool flip;
     owner_other(pairs, rank, c, ro, rq, flip);
     atomicAdd(&cntP[ro], 1);
-    atomicAdd(&cntQ[rq], 1);
+    if (rq >= 0) atomicAdd(&cntQ[rq], 1);
 }
 
 __global__ void k_scatter_owner(int m, const int32_t* __restrict__ pairs, const int* __restrict__ rank,
@@ -243,7 +250,7 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
         st[2] = vh;
         st[3] = (T)(v - (double)vh);
     }
-    qlist[rowQ[rq] + atomicAdd(&curQ[rq], 1)] = cc;
+    if (rq >= 0) qlist[rowQ[rq] + atomicAdd(&curQ[rq], 1)] = cc;
 }
 
 // Other-side arms in CSR order, one 8-value record per entry (e, arm x e,

@@ -87,7 +87,8 @@ void free_all(aLENS_ctx* c)
                     c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->perm, c->rank, c->curP, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
                     c->q64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp,
                     c->systab, c->sysid, c->sysoff, c->sys_order, c->sys_iters, c->sys_res, c->adj_ws,
-                    c->sp_ends, c->sp_arms, c->sp_kappa, c->sp_rest, c->comp64};
+                    c->sp_ends, c->sp_arms, c->sp_kappa, c->sp_rest, c->comp64, c->fnc_buf, c->gin_buf,
+                    c->row_keys, c->prev_keys, c->prev_gam};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free(c->batch_host);
@@ -330,6 +331,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     c->solve_bps = 0;
     c->batch_threads = 1024;
     c->batch_cluster = 8;
+    c->wall_axis = -1;
     if (cudaGetDevice(&c->device) != cudaSuccess) { free(c); return ALENS_ERR_CUDA; }
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) { free(c); return ALENS_ERR_CUDA; }
@@ -448,6 +450,7 @@ aLENS_status aLENS_set_params(aLENS_ctx* c, const aLENS_params* params)
     c->geo = geo;
     c->mob = mob;
     c->batch_n = 0;   // batch tables derive from the parameters: rebuild on the next batch
+    c->prev_valid = 0;
     return ALENS_OK;
 }
 
@@ -486,6 +489,10 @@ static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const dou
     CK(cudaMemsetAsync(c->cell_cursor, 0, ((size_t)nkeys + 1) * sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->rod_count, 0, ((size_t)n + 1) * sizeof(int), c->stream));
     CK(launch_pack(c, n, x, quat, fnc, true));
+    if (c->wall_axis >= 0 && c->cur_systab == nullptr) {
+        CK(cudaMemsetAsync(c->cntQ, 0, ((size_t)n + 1) * sizeof(int), c->stream));
+        CK(launch_count_walls(c, n));
+    }
     CK(launch_cell_sort(c, n));
     CK(launch_search(c, n));
     if ((st = read_status(c)) != ALENS_OK) return st;
@@ -596,8 +603,16 @@ aLENS_status aLENS_solve_lcp(aLENS_ctx* c, int64_t n, const double* quat, int64_
 }  // extern "C"
 
 // The step on the system(s) selected by cur_systab / cur_sysid / cur_nkeys.
+// Trajectories: warm = start from the previous step's forces (matched row by
+// row), keep = record this step's rows and forces for the next step.
+struct StepOpts {
+    bool warm = false;
+    bool keep = false;
+};
+
 static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
-                              int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info)
+                              int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info,
+                              StepOpts opt = StepOpts(), int64_t* walls_out = nullptr)
 {
     CK(cudaEventRecord(c->ev[0], c->stream));
     aLENS_status st = search_phase(c, (int)n, x, quat, f_nc);
@@ -605,8 +620,11 @@ static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, 
         if (info) { memset(info, 0, sizeof(*info)); info->status = st; info->n_pairs = (int64_t)c->hcount[C_PAIRS]; }
         return st;
     }
-    const long long mu = (long long)c->hcount[C_PAIRS];   // collisions
-    const long long m = mu + c->sp_n;                      // collisions, then springs
+    const bool walls = c->wall_axis >= 0 && c->cur_systab == nullptr;
+    const long long mu = (long long)c->hcount[C_PAIRS];                  // collisions
+    const long long mw = walls ? (long long)c->hcount[C_WALLS] : 0;     // wall contacts
+    const long long m = mu + mw + c->sp_n;                               // then springs
+    if (walls_out) *walls_out = mw;
     if (m > c->max_pairs) {
         if (info) { memset(info, 0, sizeof(*info)); info->status = ALENS_ERR_CAPACITY; info->n_pairs = mu; }
         return ALENS_ERR_CAPACITY;
@@ -614,8 +632,9 @@ static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, 
     CK(launch_emit_pairs(c, (int)n, c->pairs));
     CK(cudaEventRecord(c->ev[1], c->stream));
     CK(launch_assemble(c, (int)n, (int)mu, c->pairs, c->phi, c->dgeom, c->q64));
+    if (walls) CK(launch_emit_walls(c, (int)n, (int)mu));
     if (c->sp_n > 0) {
-        CK(launch_assemble_springs(c, (int)n, (int)mu));
+        CK(launch_assemble_springs(c, (int)n, (int)(mu + mw)));
         if ((st = read_status(c)) != ALENS_OK) return st;
         if (c->hflags[F_ERR] != 0) {   // a bad spring: nothing moved
             if (info) { memset(info, 0, sizeof(*info)); info->status = c->hflags[F_ERR]; info->n_pairs = mu; }
@@ -623,17 +642,27 @@ static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, 
         }
         c->cur_comp = c->comp64;
     }
+    const double* gin = nullptr;
+    if (opt.warm && c->prev_valid) {
+        CK(launch_warm(c, (int)m, (int)mu, (int)mw, c->gin_buf));
+        gin = c->gin_buf;
+    }
     CK(launch_rank(c, (int)n));
-    CK(launch_solve_setup(c, (int)n, (int)m, c->pairs, c->dgeom, c->q64, nullptr, quat, c->p.precision, c->rank));
+    CK(launch_solve_setup(c, (int)n, (int)m, c->pairs, c->dgeom, c->q64, gin, quat, c->p.precision, c->rank));
     if ((st = run_solver(c, (int)n, (int)m, info, c->ev[2], c->ev[3])) != ALENS_OK) return st;
     c->cur_comp = nullptr;
     CK(launch_update(c, (int)n, (int)m, x, quat, c->p.precision, vel_out, c->rank));
     CK(cudaEventRecord(c->ev[4], c->stream));
     if (gamma_out) CK(launch_gamma_out(c, (int)m, c->p.precision, gamma_out));
+    if (opt.keep) {
+        CK(launch_gamma_out(c, (int)m, c->p.precision, c->prev_gam));
+        CK(launch_keep_keys(c, (int)m, (int)mu, (int)mw));
+    }
     if (pairs_out && mu > 0)
         CK(cudaMemcpyAsync(pairs_out, c->pairs, sizeof(int32_t) * 3 * (size_t)mu, cudaMemcpyDeviceToDevice, c->stream));
     if ((st = read_status(c)) != ALENS_OK) return st;
     st = solve_status(c, m);
+    if (opt.keep) c->prev_valid = st == ALENS_OK || st == ALENS_ERR_NOT_CONVERGED;
     fill_info(c, info, m, st);
     if (info) {
         info->n_pairs = mu;
@@ -693,7 +722,111 @@ aLENS_status aLENS_set_springs(aLENS_ctx* c, int64_t n_springs, const int32_t* e
         CK(cudaMemcpyAsync(c->sp_rest, rest, nb * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
     c->sp_n = n_springs;
+    ++c->sp_version;
     return ALENS_OK;
+}
+
+aLENS_status aLENS_set_walls(aLENS_ctx* c, int32_t axis, double lo, double hi)
+{
+    if (!c || axis < -1 || axis > 2) return ALENS_ERR_INVALID;
+    if (axis >= 0) {
+        const double box = c->p.box[axis];
+        const double rcut = c->p.length + c->p.diameter + c->p.delta_c;
+        if (!(lo >= 0.0) || !(hi > lo) || !(hi <= box) || !(box - (hi - lo) >= rcut)) return ALENS_ERR_INVALID;
+    }
+    c->wall_axis = axis;
+    c->wall_lo = lo;
+    c->wall_hi = hi;
+    c->prev_valid = 0;
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_brownian(aLENS_ctx* c, int64_t n, const double* quat, double kT, uint64_t seed, int64_t step,
+                            const double* f_ext, double* out)
+{
+    if (!rods_ok(c, n) || (n > 0 && (!quat || !out)) || !(kT >= 0.0) || step < 0) return ALENS_ERR_INVALID;
+    c->launches = 0;
+    CK(launch_brownian(c, (int)n, quat, kT, seed, (unsigned long long)step, f_ext, out));
+    CK(cudaStreamSynchronize(c->stream));
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_random_words(aLENS_ctx* c, int64_t n, uint64_t seed, int64_t step, uint32_t* out)
+{
+    if (!rods_ok(c, n) || (n > 0 && !out) || step < 0) return ALENS_ERR_INVALID;
+    c->launches = 0;
+    CK(launch_random_words(c, (int)n, seed, (unsigned long long)step, out));
+    CK(cudaStreamSynchronize(c->stream));
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_run(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_ext, int64_t n_steps,
+                       double kT, uint64_t seed, int64_t first_step, int32_t warm_start, aLENS_step_stats* stats,
+                       aLENS_info* info)
+{
+    if (c) { c->launches = 0; single_mode(c); }
+    if (!rods_ok(c, n) || (n > 0 && (!x || !quat)) || n_steps < 0 || !(kT >= 0.0) || first_step < 0)
+        return ALENS_ERR_INVALID;
+    if (!c->coop_ok) return ALENS_ERR_CUDA;
+    const size_t np = (size_t)c->max_rods, mp = (size_t)c->max_pairs;
+    if (!c->fnc_buf) {
+        bool ok = dmalloc(&c->fnc_buf, 6 * np * sizeof(double)) == cudaSuccess &&
+                  dmalloc(&c->gin_buf, mp * sizeof(double)) == cudaSuccess &&
+                  dmalloc(&c->row_keys, mp * sizeof(unsigned long long)) == cudaSuccess &&
+                  dmalloc(&c->prev_keys, mp * sizeof(unsigned long long)) == cudaSuccess &&
+                  dmalloc(&c->prev_gam, mp * sizeof(double)) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            void* bufs[] = {c->fnc_buf, c->gin_buf, c->row_keys, c->prev_keys, c->prev_gam};
+            for (void* q : bufs)
+                if (q) cudaFree(q);
+            c->fnc_buf = nullptr; c->gin_buf = nullptr; c->row_keys = nullptr; c->prev_keys = nullptr;
+            c->prev_gam = nullptr;
+            return ALENS_ERR_NOMEM;
+        }
+        c->prev_valid = 0;
+    }
+    StepOpts opt;
+    opt.warm = warm_start != 0;
+    opt.keep = true;
+    aLENS_info agg;
+    memset(&agg, 0, sizeof(agg));
+    agg.min_gap = INFINITY;
+    int launches = 0;
+    aLENS_status st = ALENS_OK;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        c->launches = 0;
+        CK(launch_brownian(c, (int)n, quat, kT, seed, (unsigned long long)(first_step + k), f_ext, c->fnc_buf));
+        aLENS_info si;
+        memset(&si, 0, sizeof(si));
+        int64_t mw = 0;
+        st = step_impl(c, n, x, quat, c->fnc_buf, nullptr, nullptr, nullptr, &si, opt, &mw);
+        launches += c->launches;
+        if (stats) {
+            aLENS_step_stats& o = stats[k];
+            o.n_pairs = si.n_pairs;
+            o.n_walls = mw;
+            o.iters = si.iters;
+            o.status = (int32_t)st;
+            o.residual = si.residual;
+            o.min_gap = si.min_gap;
+            o.ms_step = si.ms_build + si.ms_assemble + si.ms_solve + si.ms_update;
+        }
+        agg.n_pairs = si.n_pairs;
+        agg.n_overlap = si.n_overlap;
+        agg.iters += si.iters;
+        if (si.residual > agg.residual) agg.residual = si.residual;
+        if (si.min_gap < agg.min_gap) agg.min_gap = si.min_gap;
+        agg.ms_build += si.ms_build;
+        agg.ms_assemble += si.ms_assemble;
+        agg.ms_solve += si.ms_solve;
+        agg.ms_update += si.ms_update;
+        if (st != ALENS_OK && st != ALENS_ERR_NOT_CONVERGED) break;
+    }
+    agg.status = (int32_t)st;
+    agg.launches = launches;
+    if (info) *info = agg;
+    return st;
 }
 
 aLENS_status aLENS_step_adjoint(aLENS_ctx* c, int64_t n, const double* x, const double* quat, const double* f_nc,
@@ -705,7 +838,7 @@ aLENS_status aLENS_step_adjoint(aLENS_ctx* c, int64_t n, const double* x, const 
     if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
     if (n > 0 && (!x || !quat || !dL_dx || !dL_dquat)) return ALENS_ERR_INVALID;
     if (n_pairs > 0 && (!pairs || !gamma)) return ALENS_ERR_INVALID;
-    if (c->sp_n > 0) return ALENS_ERR_NOT_IMPLEMENTED;   // the adjoint covers collision constraints only
+    if (c->sp_n > 0 || c->wall_axis >= 0) return ALENS_ERR_NOT_IMPLEMENTED;   // collisions only
     if (cudaGetLastError() != cudaSuccess) return ALENS_ERR_CUDA;
     if (adjoint_reserve(c) != cudaSuccess) { cudaGetLastError(); return ALENS_ERR_NOMEM; }
     aLENS_status st = reset_status(c);
@@ -771,6 +904,7 @@ aLENS_status aLENS_step_batch(aLENS_ctx* c, int32_t n_systems, const aLENS_syste
     const int64_t n = rod_offset[n_systems];
     if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;
     if (!c->coop_ok) return ALENS_ERR_CUDA;
+    if (c->wall_axis >= 0) return ALENS_ERR_NOT_IMPLEMENTED;   // walls belong to single systems
     aLENS_status st = batch_tables(c, n_systems, systems, rod_offset);
     if (st != ALENS_OK) { single_mode(c); return st; }
     c->cur_systab = c->systab;

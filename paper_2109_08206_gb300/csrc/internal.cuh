@@ -30,7 +30,7 @@ enum Flag : int {
 };
 // 64-bit counters (Ctx::dcount)
 enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_SMEM = 6,
-                   C_QUEUE = 7, C_NCOUNT = 8 };
+                   C_QUEUE = 7, C_WALLS = 8, C_NCOUNT = 9 };
 
 // ------------------------------------------------------------ plain structs
 
@@ -283,6 +283,18 @@ struct aLENS_ctx {
     int64_t sp_n, sp_cap;
     double* comp64;          // [mp] pair order: -1 collisions, 1/(h kappa) springs (allocated with the springs)
     const double* cur_comp;  // comp64 while a step with springs is set up and solved, else NULL
+    int64_t sp_version;      // bumped by every aLENS_set_springs (warm start matches springs by index)
+    // walls (aLENS_set_walls): axis (-1: none) and the two wall coordinates
+    int wall_axis;
+    double wall_lo, wall_hi;
+    // trajectories (aLENS_run): forces of a step, warm start from the previous step
+    double* fnc_buf;         // [np][6]
+    double* gin_buf;         // [mp]
+    unsigned long long* row_keys;   // [mp] keys of this step's rows
+    unsigned long long* prev_keys;  // [mp] keys of the previous step's rows
+    double* prev_gam;        // [mp] the previous step's forces
+    int64_t prev_mu, prev_mw, prev_ms, prev_sp_version;
+    int prev_valid;
     int batch_threads;       // per-system solver: threads per block
     int batch_cluster;       // per-system solver: blocks per cluster
 };
@@ -322,6 +334,17 @@ cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma
 // Springs: rows mu .. mu + nb of the internal constraint list (pairs, phi,
 // dgeom, q) and comp64 for every row (collisions -1).
 cudaError_t launch_assemble_springs(aLENS_ctx* ctx, int n, int mu);
+
+// trajectory.cu: walls (count during the search, rows after the
+// collisions), Brownian forces, raw generator words, warm start.
+cudaError_t launch_count_walls(aLENS_ctx* ctx, int n);
+cudaError_t launch_emit_walls(aLENS_ctx* ctx, int n, int row0);
+cudaError_t launch_brownian(aLENS_ctx* ctx, int n, const double* quat, double kT, unsigned long long seed,
+                            unsigned long long step, const double* fext, double* out);
+cudaError_t launch_random_words(aLENS_ctx* ctx, int n, unsigned long long seed, unsigned long long step,
+                                uint32_t* out);
+cudaError_t launch_warm(aLENS_ctx* ctx, int m, int mu, int mw, double* gin);
+cudaError_t launch_keep_keys(aLENS_ctx* ctx, int m, int mu, int mw);
 
 // adjoint.cu: workspace (once) and the adjoint pipeline after pack, assembly
 // and the solver setup of the forward step's pair list (identity ranks).

@@ -106,6 +106,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
     c.max_blocks = c.num_sms * 8 < kNoallocMaxBlocks ? c.num_sms * 8 : kNoallocMaxBlocks;
     c.wait_s = 5.0;
     c.solve_threads = 1024;
+    c.wall_axis = -1;
     double zperp = 4.0 * M_PI * params->viscosity * params->length / log(2.0 * params->length / params->diameter);
     c.mob.inv_perp = 1.0 / zperp;
     c.mob.inv_par = 2.0 / zperp;

@@ -479,7 +479,10 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
             const int il = o.ci[lc], j = o.cj[lc];
 #pragma unroll
             for (int w = 0; w < 6; ++w) Ui[w] = o.U[w * o.cap_r + il];
-            if (j >= o.r0 && j < o.r1) {
+            if (j < 0) {   // a wall: no other side
+#pragma unroll
+                for (int w = 0; w < 6; ++w) Uj[w] = T(0);
+            } else if (j >= o.r0 && j < o.r1) {
 #pragma unroll
                 for (int w = 0; w < 6; ++w) Uj[w] = o.U[w * o.cap_r + (j - o.r0)];
             } else {
@@ -496,7 +499,13 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
             }
         } else {
             ld_u6(Uu, a.ci[c], Ui);
-            ld_u6(Uu, a.cj[c], Uj);
+            const int j = a.cj[c];
+            if (j < 0) {   // a wall: no other side
+#pragma unroll
+                for (int w = 0; w < 6; ++w) Uj[w] = T(0);
+            } else {
+                ld_u6(Uu, j, Uj);
+            }
 #pragma unroll
             for (int w = 0; w < 9; ++w) r[w] = a.rec[w * mp + c];
             base = MODE == B_STEP ? a.gref[c] : a.q[c];

@@ -23,7 +23,7 @@ LIB = BUILD / "libalens.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "--expt-relaxed-constexpr",
           f"-I{ROOT / 'include'}"]
-NO_FMA = {"neighbors.cu", "assemble.cu", "update.cu", "adjoint.cu"}
+NO_FMA = {"neighbors.cu", "assemble.cu", "update.cu", "adjoint.cu", "trajectory.cu"}
 
 
 def _nvcc() -> str:
