@@ -47,13 +47,15 @@ METRIC = "rod-steps/s at 1e5 rods, FP32-mixed vs FP64 plain at residual ≤1e-5"
 METRIC_ENSEMBLE = "rod-steps/s of the 256-system batched ensemble (one call), FP32-mixed vs FP64 plain at residual ≤1e-5"
 METRIC_SPRINGS = ("rod-steps/s at 1e5 rods with 5e4 bilateral spring constraints, FP32-mixed vs FP64 plain at "
                   "residual ≤1e-5")
+METRIC_TRAJ = ("rod-steps/s of a 1e5-rod Brownian trajectory (10 steps per call, warm start), FP32-mixed vs FP64 "
+               "plain at residual ≤1e-5")
 METRIC_GRAD = ("rod-steps/s of one step plus its adjoint (gradient of the post-step centre loss) at 2e4 rods, "
                "FP32-mixed vs FP64 plain at residual ≤1e-5")
 
 
 def metric_of(workload):
     return {"ensemble256": METRIC_ENSEMBLE, "n20k_grad": METRIC_GRAD,
-            "n100k_springs": METRIC_SPRINGS}.get(workload, METRIC)
+            "n100k_springs": METRIC_SPRINGS, "n100k_traj": METRIC_TRAJ}.get(workload, METRIC)
 UNIT = "rod-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -414,8 +416,56 @@ class SpringJob(SingleJob):
                           f"{nb} springs; one oracle step with the bilateral constraints, {t:.2f} s")
 
 
+class TrajJob(SingleJob):
+    """A Brownian trajectory of the 1e5-rod suspension: every timed call is
+    aLENS_run over `steps_per_call` steps (kT = 1, Brownian forces drawn on
+    the device, the workload's own forces held as f_ext, warm start)."""
+
+    steps_per_call = 10
+
+    class Out:
+        def __init__(self, d):
+            self.d = d
+
+        def as_dict(self):
+            return self.d
+
+    def __init__(self, s):
+        super().__init__(s)
+        self.name = s.name + "_trajectory"
+
+    def step(self, ctx, x, q, f, **kw):
+        info, stats = ctx.run(x, q, self.steps_per_call, kT=1.0, seed=77, first_step=0, f_ext=f, warm_start=True,
+                              check=False)
+        d = info.as_dict()
+        d["iters"] = info.iters / self.steps_per_call   # per constrained step
+        d["stats"] = stats
+        return TrajJob.Out(d)
+
+    def solve_bytes(self, ctx, info, w):
+        return sum(st["iters"] * solve_bytes_per_iter(self.n, st["n_pairs"], w) for st in info["stats"])
+
+    def config(self, W, m):
+        c = super().config(W, m)
+        c.update({"workload": self.name, "steps_per_call": self.steps_per_call, "kT": 1.0,
+                  "brownian": "Philox4x32-10 on the device, covariance 2 kT M^-1 / h", "warm_start": True})
+        return c
+
+    def cpu(self, args):
+        import oracle as O
+        sub, a = spatial_sample(self.s, min(args.sample_rods, 4000))
+        K = 3
+        t0 = time.perf_counter()
+        O.trajectory(sub.x, sub.quat, O.problem_of(sub), K, 1.0, 77, f_ext=sub.f_nc, tol=args.tol)
+        t = time.perf_counter() - t0
+        return sub.n * K, t, (f"{sub.n} rods of {self.s.name} with centres in a periodic sub-cube of edge {a:.2f}; "
+                              f"{K} oracle trajectory steps (Brownian forces, FISTA to {args.tol:g}), {t:.2f} s")
+
+
 def make_job(name):
     from paper_2109_08206_gb300 import workloads as W
+    if name == "n100k_traj":
+        return TrajJob(W.workload("n100k_phi010"))
     if name == "n100k_springs":
         s = W.workload("n100k_phi010", n_springs=0)
         return SpringJob(s, W.spring_set(s, 50_000, seed=21))
@@ -579,7 +629,8 @@ def run_ours(args):
     barrier()
     wall = time.perf_counter() - t0
     ms_step = max_over_ranks(statistics.mean(ms))
-    value = replica_value(ms_step, n, ws)
+    spc = getattr(job, "steps_per_call", 1)   # constrained steps in one timed call
+    value = replica_value(ms_step, n * spc, ws)
     it = [i["iters"] for i in infos]
     ms_solve = statistics.mean(i["ms_solve"] for i in infos)
     m = infos[-1]["n_pairs"]
@@ -603,7 +654,7 @@ def run_ours(args):
             del xx, qq
         ms64, inf64, sb64 = timed(ctx64, max(2, args.steps // 2), 1, w=8)
         ms64_step = max_over_ranks(statistics.mean(ms64))
-        fp64 = {"value": replica_value(ms64_step, n, ws), "unit": UNIT, "ms_per_step": ms64_step,
+        fp64 = {"value": replica_value(ms64_step, n * spc, ws), "unit": UNIT, "ms_per_step": ms64_step,
                 "bbpgd_iters": statistics.mean(i["iters"] for i in inf64),
                 **({"cg_iters": statistics.mean(i["cg_iters"] for i in inf64),
                     "ms_adjoint": statistics.mean(i["ms_adjoint"] for i in inf64)} if "cg_iters" in inf64[0] else {}),
@@ -620,7 +671,7 @@ def run_ours(args):
         ox = torch.empty_like(hx).pin_memory(); oq = torch.empty_like(hq).pin_memory()
         mse, _, _ = timed(ctx, args.steps, 1, host=(hx, hq, hf, ox, oq))
         mse_step = max_over_ranks(statistics.mean(mse))
-        e2e = {"value": replica_value(mse_step, n, ws), "unit": UNIT, "ms_per_step": mse_step,
+        e2e = {"value": replica_value(mse_step, n * spc, ws), "unit": UNIT, "ms_per_step": mse_step,
                "h2d_bytes_per_step": int(hx.numel() * 8 + hq.numel() * 8 + hf.numel() * 8),
                "d2h_bytes_per_step": int(ox.numel() * 8 + oq.numel() * 8)}
     clk.__exit__(None, None, None)
@@ -633,7 +684,7 @@ def run_ours(args):
             c2 = make_ctx(prec)
             xx, qq = x0.clone(), q0.clone()
             gam = torch.empty(max_pairs, dtype=torch.float64, device=dev)
-            inf = SingleJob.step(job, c2, xx, qq, f, gamma_out=gam) if isinstance(job, GradJob) \
+            inf = SingleJob.step(job, c2, xx, qq, f, gamma_out=gam) if isinstance(job, (GradJob, TrajJob)) \
                 else job.step(c2, xx, qq, f, gamma_out=gam)
             outs[prec] = (xx, qq, gam[: inf.n_pairs].clone())
             c2.close()
