@@ -55,7 +55,7 @@ namespace alens {
 // CSR entries whose loads a thread issues together (float64 values need the
 // registers twice over)
 template <typename T> struct Batch { static constexpr int v = 1; };
-constexpr int kRefresh = 32;   // float32 iterations between reference refreshes
+constexpr int kRefresh = 64;   // float32 iterations between reference refreshes
 
 template <typename T> struct V2;
 template <> struct V2<float> { using t = float2; };
@@ -618,7 +618,7 @@ __device__ __forceinline__ void fold_delta(const SolveArgs<T>& a, const Own<T>& 
 // shuffles, then warp 0 over the warp results, fixed order); lane 0 stores
 // it as float64 for the cross-block sum.
 template <typename T>
-__device__ __forceinline__ void block_partial(T v[4], T (*red)[4], double* dst)
+__device__ __forceinline__ void block_partial(T v[4], T (*red)[4], double* dst, int stride)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -648,7 +648,7 @@ __device__ __forceinline__ void block_partial(T v[4], T (*red)[4], double* dst)
         }
         if (lane == 0) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) dst[u] = (double)w[u];
+            for (int u = 0; u < 4; ++u) dst[u * stride] = (double)w[u];
         }
     }
 }
@@ -686,17 +686,26 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, i
 }
 
 // After a barrier: warps 0-3 each reduce one component of the per-block
-// partials in float64 in a fixed order (L2 loads, several blocks per lane in
-// flight) and the four totals are broadcast through shared memory.
+// partials ([4][nb]: a warp reads one contiguous row) in float64 in a fixed
+// order, the first 8 loads of every lane in flight together, and the four
+// totals are broadcast through shared memory.
 __device__ __forceinline__ void grid_total(const double* partials, int nb, double* bc, double out[4])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 4) {
         const bool is_max = warp == 3;
+        const double* row = partials + (size_t)warp * nb;
+        double xs[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int b = lane + 32 * k;
+            xs[k] = b < nb ? __ldcg(row + b) : 0.0;
+        }
         double w = 0.0;
-#pragma unroll 4
-        for (int b = lane; b < nb; b += 32) {
-            const double x = __ldcg(partials + 4 * (size_t)b + warp);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w = is_max ? (xs[k] > w ? xs[k] : w) : w + xs[k];
+        for (int b = lane + 256; b < nb; b += 32) {
+            const double x = __ldcg(row + b);
             w = is_max ? (x > w ? x : w) : w + x;
         }
 #pragma unroll
@@ -716,6 +725,7 @@ __device__ __forceinline__ void grid_total(const double* partials, int nb, doubl
 struct StepState {
     double alpha0, alpha, res;
     int iters, cur, done;
+    int since;   // iterations since the last reference refresh
 };
 
 template <typename T>
@@ -742,7 +752,8 @@ struct GridSync {
         return grid_barrier(bar, nb * ++epoch, flags, wait_cycles, &sh.ok);
     }
     template <typename SH>
-    __device__ __forceinline__ double* slot(SH&) { return partials + 4 * (size_t)blockIdx.x; }
+    __device__ __forceinline__ double* slot(SH&) { return partials + blockIdx.x; }
+    __device__ __forceinline__ int stride() const { return (int)nb; }   // partials are [4][nb]
     template <typename SH>
     __device__ __forceinline__ void total(SH& sh, double tot[4]) { grid_total(partials, nb, sh.bc, tot); }
 };
@@ -759,6 +770,7 @@ struct ClusterSync {
     }
     template <typename SH>
     __device__ __forceinline__ double* slot(SH& sh) { return sh.part; }
+    __device__ __forceinline__ int stride() const { return 1; }
     template <typename SH>
     __device__ __forceinline__ void total(SH& sh, double tot[4])
     {
@@ -826,6 +838,7 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
     T v[4];
     st.alpha0 = 1.0;
     st.cur = 0;
+    st.since = 0;
     if (threadIdx.x == 0) sh.cur = 0;
 
     // gamma_0 is the reference (delta = 0): Uref = M D gamma_0, then
@@ -834,7 +847,7 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
     if (!sy.barrier(sh)) return;
     v[0] = v[1] = v[2] = v[3] = T(0);
     phase_b<T, B_REF, ST>(a, o, 0, 0, v);
-    block_partial(v, sh.red, mine);
+    block_partial(v, sh.red, mine, sy.stride());
     if (!sy.barrier(sh)) return;
     sy.total(sh, tot);
     if (threadIdx.x == 0) {
@@ -852,7 +865,7 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
         v[1] = v[2] = v[3] = T(0);
         // every block has read the partials (grid_total) before any rewrites them
         if (!sy.barrier(sh)) return;
-        block_partial(v, sh.red, mine);
+        block_partial(v, sh.red, mine, sy.stride());
         if (!sy.barrier(sh)) return;
         sy.total(sh, tot);
         if (threadIdx.x == 0) {
@@ -870,7 +883,7 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
             if (!sy.barrier(sh)) return;
             v[0] = v[1] = v[2] = v[3] = T(0);
             phase_b<T, B_STEP, ST>(a, o, cur, nx, v);
-            block_partial(v, sh.red, mine);
+            block_partial(v, sh.red, mine, sy.stride());
             if (!sy.barrier(sh)) return;
             sy.total(sh, tot);
             cur = nx;
@@ -886,9 +899,12 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
                 sh.alpha = (T)an;
                 // float32: a residual below tol is confirmed on a fresh
                 // reference before the loop stops (the increments since the
-                // last refresh carry float32 rounding)
+                // last refresh carry float32 rounding); after a refresh that
+                // did not confirm it, the next try waits two iterations
                 st.done = below && a.refresh == 0;
-                sh.refresh = a.refresh > 0 && (below || (k + 1) % a.refresh == 0);
+                ++st.since;
+                sh.refresh = a.refresh > 0 && ((below && st.since >= 3) || st.since >= a.refresh);
+                if (sh.refresh) st.since = 0;
                 sh.done = st.done;
             }
             __syncthreads();
@@ -903,7 +919,7 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
                 if (!sy.barrier(sh)) return;
                 v[0] = v[1] = v[2] = v[3] = T(0);
                 phase_b<T, B_REF, ST>(a, o, cur, cur, v);
-                block_partial(v, sh.red, mine);
+                block_partial(v, sh.red, mine, sy.stride());
                 if (!sy.barrier(sh)) return;
                 sy.total(sh, tot);
                 if (threadIdx.x == 0) {
