@@ -711,7 +711,7 @@ def run_ours(args):
     line = {
         "metric": metric_of(args.workload), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32-mixed (f64 geometry, residual, reductions)", "data": "synthetic",
+        "dtype": "f32-mixed (f64 geometry, reference passes and residual test)", "data": "synthetic",
         "config": config,
         "bbpgd_iters": statistics.mean(it), "residual": res, "launch_shape": tuned,
         "phase_ms": {k: statistics.mean(i[k] for i in infos) for k in ("ms_build", "ms_assemble", "ms_solve",

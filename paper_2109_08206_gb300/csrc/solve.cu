@@ -22,29 +22,43 @@
 // g, and its rods' axes and velocities in shared memory for the whole solve
 // (at 1e5 rods the mixed working set, about 30 MB, spreads over the SMs'
 // shared memory); global memory then carries only what other blocks read:
-// gamma, g and U mirrors.  Blocks whose share does not fit work from the
-// global arrays.  Per iteration:
-//   phase A (one thread per rod): gamma_{k+1} of every constraint touching
-//     the rod is formed on the fly from (gamma_k, g_k) and alpha_k (the owner
-//     stores it), summed into the rod's force and torque F = D gamma (owned
-//     range contiguous, other-side list in CSR order), and U = M F is stored;
+// the state of constraints whose other rod is another block's, and the
+// velocities of rods that another block's constraints touch (the rest is
+// written once when the solve ends).  Without that fit every block works
+// from the global arrays.  Per iteration:
+//   phase A (one thread per rod, rods taken in ascending order of their
+//     entry counts so that a warp's loops have similar lengths):
+//     delta_{k+1} of every constraint touching the rod is formed on the fly
+//     from (delta_k, g_k, gamma_ref) and alpha_k, summed into the rod's
+//     force and torque F = D delta (owned range contiguous, other-side list
+//     in CSR order), and dU = M F is stored;
 //   grid barrier;
-//   phase B (one thread per owned constraint): g_{k+1} = q + D^T U, and the
-//     partial sums s.s, s.y, y.y and max |pi|: per thread and per warp in the
-//     working precision, across warps and blocks in float64, in a fixed order;
-//   grid barrier; warp 0 of every block then reduces the per-block partials
-//     in the same fixed order, so all blocks take identical step decisions.
+//   phase B (one thread per owned constraint): delta_{k+1} again (same
+//     inputs and rounding), g_{k+1} = gref + D^T dU, and the partial sums
+//     s.s, s.y, y.y and max |pi| (per thread, per warp and per block in a
+//     fixed order);
+//   grid barrier; warps 0-3 of every block then reduce the per-block
+//     partials in the same fixed order, so all blocks take identical step
+//     decisions.
 // Two grid barriers per iteration.  Each barrier wait is bounded in time
 // and in polls; a wait that runs out raises ALENS_ERR_TIMEOUT in the device
 // status word and every block leaves.
 //
-// Global layout: (gamma, g) interleaved per constraint in two ping-pong
-// buffers, U as [rod][6], D records SoA [9][m] in owner-major order.
-// T = double (float64 plain) or float (mixed: the D, M, D^T work, per-thread
-// and per-warp sums in float32; the cross-warp and cross-block sums, the
-// residual test and the step sizes in float64; max |pi| is exact in either).
+// Global layout: the state (delta, g, gamma_ref, gamma_lo) of each
+// constraint in two ping-pong [m][4] buffers, U as [rod][6], D records SoA
+// [9][m] in owner-major order.
+// T = double (float64 plain) or float (mixed: the D, M, D^T work, the sums
+// and the step sizes in float32).  max |pi| is exact in either, and the
+// stopping test takes the float64 decision (h/D) max |pi| <= tol in both:
+// in float32 as max |pi| <= pi_tol, the largest float for which the float64
+// product stays within tol.  The per-iteration reductions and decisions stay
+// off float64 in the mixed solver because this part's float64 latency is
+// about ten times float32's (an add 62 cycles, a divide 561).
 #include <cooperative_groups.h>
 #include <float.h>
+
+#include <cmath>
+#include <limits>
 
 #include "internal.cuh"
 
@@ -203,6 +217,7 @@ struct SolveArgs {
     const T* __restrict__ qe_lo;
     const T* __restrict__ q_lo;
     double hD, tol;
+    T pi_tol;      // stopping threshold on max |pi| (float32: see above)
     int max_iter;
     int refresh;   // refresh the reference every this many iterations (0: never)
     long long wait_cycles;
@@ -217,7 +232,7 @@ struct Own {
     int r0, r1, c0, c1, q0, q1, cap_c, cap_r, cap_q;
     T* rec;      // [9][cap_c]
     T* gref;     // [cap_c] q + D^T Uref
-    T* ds[2];    // [cap_c] delta, ping-pong
+    T* ds;       // [cap_c] delta (phase B updates it in place, one thread per entry)
     T* grs;      // [cap_c] g (phase B updates it in place, one thread per entry)
     T* gam;      // [cap_c] gamma_ref
     T* ax;       // [3][cap_r]
@@ -227,15 +242,19 @@ struct Own {
     int* rowP;   // [cap_r + 1] owned ranges (global constraint ids)
     int* rowQ;   // [cap_r + 1] other-side ranges (global CSR positions)
     int* qlist;  // [cap_q] other-side constraint ids of the block's rods
+    unsigned short* perm;   // [cap_r] the order in which the rod phase's threads take the rods
+    unsigned* xrod;         // [(cap_r + 31) / 32] bit li: another block reads rod li's velocity
 };
 
-// Shared-memory bytes of a block's share: per owned constraint 14 values
-// and 6 bytes of indices, per rod 9 values and two row pointers, per
-// other-side entry one id (owner indices are 16-bit: at most 65535 rods).
+// Shared-memory bytes of a block's share: per owned constraint 13 values
+// and 6 bytes of indices, per rod 9 values, two row pointers, a 16-bit slot
+// of the rod order and an export bit, per other-side entry one id (owner
+// indices are 16-bit: at most 65535 rods).
 __host__ __device__ inline size_t staged_bytes(int esize, size_t cap_c, size_t cap_r, size_t cap_q)
 {
-    return (14 * cap_c + 9 * cap_r) * (size_t)esize + (cap_c + 2 * cap_r + 2 + cap_q) * sizeof(int) +
-           ((cap_c * sizeof(unsigned short) + 3) & ~(size_t)3);
+    return (13 * cap_c + 9 * cap_r) * (size_t)esize +
+           (cap_c + 2 * cap_r + 2 + cap_q + (cap_r + 31) / 32) * sizeof(int) +
+           (((cap_c + cap_r) * sizeof(unsigned short) + 3) & ~(size_t)3);
 }
 
 template <typename T>
@@ -245,8 +264,7 @@ __device__ void carve(Own<T>& o, unsigned char* base)
     const size_t C = o.cap_c, R = o.cap_r;
     o.rec = t; t += 9 * C;
     o.gref = t; t += C;
-    o.ds[0] = t; t += C;
-    o.ds[1] = t; t += C;
+    o.ds = t; t += C;
     o.grs = t; t += C;
     o.gam = t; t += C;
     o.ax = t; t += 3 * R;
@@ -256,7 +274,9 @@ __device__ void carve(Own<T>& o, unsigned char* base)
     o.rowP = ip; ip += R + 1;
     o.rowQ = ip; ip += R + 1;
     o.qlist = ip; ip += o.cap_q;
+    o.xrod = reinterpret_cast<unsigned*>(ip); ip += (R + 31) / 32;
     o.ci = reinterpret_cast<unsigned short*>(ip);
+    o.perm = o.ci + C;
 }
 
 template <typename T>
@@ -270,6 +290,7 @@ __device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
     }
     for (int li = threadIdx.x; li < nr; li += blockDim.x)
         for (int w = 0; w < 3; ++w) o.ax[w * o.cap_r + li] = a.ax[w * np + o.r0 + li];
+#pragma unroll 1
     for (int lc = threadIdx.x; lc < nc; lc += blockDim.x) {
         const int c = o.c0 + lc;
 #pragma unroll
@@ -278,11 +299,42 @@ __device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
         o.ci[lc] = (unsigned short)(a.ci[c] - o.r0);
         T d, g, gr, gl;
         ld_state(a.gg0, c, d, g, gr, gl);
-        o.ds[0][lc] = d;
+        o.ds[lc] = d;
         o.gam[lc] = gr;
         o.grs[lc] = T(0);
     }
     for (int k = threadIdx.x; k < o.q1 - o.q0; k += blockDim.x) o.qlist[k] = a.qlist[o.q0 + k];
+    for (int w = threadIdx.x; w < (nr + 31) / 32; w += blockDim.x) o.xrod[w] = 0u;
+    // rod order of the rod phase: ascending (owned, other-side) entry
+    // counts, so that the 32 rods of a warp run loops of about the same
+    // lengths (a warp runs each loop as long as its longest rod's).  Rank
+    // sort on unique keys (count pair, then index), the keys and ranks held
+    // in the velocity array, which the first rod phase writes before anyone
+    // reads it.
+    unsigned* key = reinterpret_cast<unsigned*>(o.U);
+    int* rk = reinterpret_cast<int*>(o.U) + nr;   // 6 cap_r values hold 2 nr words
+    __syncthreads();
+    for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+        const int no = min(o.rowP[li + 1] - o.rowP[li], 255), nq = min(o.rowQ[li + 1] - o.rowQ[li], 255);
+        key[li] = ((unsigned)(no << 8 | nq) << 16) | (unsigned)li;
+        // exported: a constraint on the rod is owned by another block, whose
+        // constraint phase reads the rod's velocity
+        bool ex = false;
+        for (int k = o.rowQ[li] - o.q0; k < o.rowQ[li + 1] - o.q0; ++k) {
+            const int cid = o.qlist[k];
+            ex |= cid < o.c0 || cid >= o.c1;
+        }
+        if (ex) atomicOr(&o.xrod[li >> 5], 1u << (li & 31));
+    }
+    __syncthreads();
+    for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+        const unsigned kk = key[li];
+        int r = 0;
+        for (int lj = 0; lj < nr; ++lj) r += key[lj] < kk;
+        rk[li] = r;
+    }
+    __syncthreads();
+    for (int li = threadIdx.x; li < nr; li += blockDim.x) o.perm[rk[li]] = (unsigned short)li;
     __syncthreads();
 }
 
@@ -304,7 +356,7 @@ __device__ __forceinline__ T a_value(T d, T g, T gr, T alpha, bool bil)
 {
     if (MODE == A_REF) return gr;
     if (MODE == A_STEP) {
-        const T v = d - alpha * g;
+        const T v = fma(-alpha, g, d);   // one rounding, the same in both phases that form it
         return (bil || v > -gr) ? v : -gr;
     }
     return (bil || d > -gr) ? g : (g < T(0) ? g : T(0));   // projected gradient at gamma = gr + d
@@ -326,15 +378,16 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
     constexpr int BO = ST ? 1 : B;   // owned entries come from shared memory when staged
     const T* gc = cur ? a.gg1 : a.gg0;
     T* gn = cur ? a.gg0 : a.gg1;
-    const T* sdc = cur ? o.ds[1] : o.ds[0];      // shared copies (staged blocks)
-    T* sdn = cur ? o.ds[0] : o.ds[1];
-    for (int i = o.r0 + threadIdx.x; i < o.r1; i += blockDim.x) {
-        const int li = i - o.r0;
+    const T* sdc = o.ds;   // shared copy (staged blocks)
+#pragma unroll 1
+    for (int t = threadIdx.x; t < o.r1 - o.r0; t += blockDim.x) {
+        const int li = ST ? (int)o.perm[t] : t, i = o.r0 + li;
         Acc<T, COMP> Fa[6];
 #pragma unroll
         for (int w = 0; w < 6; ++w) Fa[w].init(T(0));
         {   // owned constraints: loads of up to BO entries issued together
             const int b = ST ? o.rowP[li] : a.rowP[i], e = ST ? o.rowP[li + 1] : a.rowP[i + 1];
+#pragma unroll 1
             for (int c = b; c < e; c += BO) {
                 T dv[BO], gv[BO], rv_[BO], gl[BO], rv[BO][6];
 #pragma unroll
@@ -361,10 +414,8 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
                         const T cmp = comp_of(a, c + u);
                         const T v = a_value<MODE, T>(dv[u], gv[u], rv_[u], alpha, cmp >= T(0));
                         if (MODE == A_PG && cmp >= T(0)) fmf += cmp * v * v;   // the spring's compliance term
-                        if (MODE == A_STEP) {
-                            if (ST) sdn[c + u - o.c0] = v;       // global copy written in phase B
-                            else gn[4 * (size_t)(c + u)] = v;
-                        }
+                        // staged: phase B forms delta_{k+1} again from the same values
+                        if (MODE == A_STEP && !ST) gn[4 * (size_t)(c + u)] = v;
 #pragma unroll
                         for (int w = 0; w < 6; ++w) Fa[w].add_prod(v, rv[u][w]);
                         if (MODE == A_REF && COMP) {   // gamma_lo and the records' low parts
@@ -379,6 +430,7 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
         {   // constraints owned by other rods: ids first, then their state and arms
             // (from shared memory when the owner is one of the block's rods)
             const int b = ST ? o.rowQ[li] : a.rowQ[i], e = ST ? o.rowQ[li + 1] : a.rowQ[i + 1];
+#pragma unroll 1
             for (int k = b; k < e; k += B) {
                 int cid[B];
 #pragma unroll
@@ -444,7 +496,8 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
 #pragma unroll
             for (int w = 0; w < 6; ++w) fmf += F[w] * Uv[w];
         } else {
-            st_u6(MODE == A_REF ? a.Uref : a.U, i, Uv);
+            // staged steps: the global copy is written in rank order below
+            if (!(ST && MODE == A_STEP)) st_u6(MODE == A_REF ? a.Uref : a.U, i, Uv);
             if (MODE == A_REF) {
                 const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
                 st_u6(a.U, i, z);   // dU = 0: delta is 0 after a reference pass
@@ -458,25 +511,43 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
     return fmf;
 }
 
+// Staged steps: dU of the block's rods to global memory in rank order
+// (the rod phase takes its rods in count order), only the rods whose
+// velocity another block reads (EXPORTED) or all of them.  Stores before a
+// grid barrier are paid for in its release fence: a step writes only what
+// other blocks read, and the rest once when the solve ends.
+template <typename T, bool EXPORTED>
+__device__ __forceinline__ void store_du(const SolveArgs<T>& a, const Own<T>& o)
+{
+    __syncthreads();
+    const int nv = 6 * (o.r1 - o.r0);
+    T* dst = a.U + 6 * (size_t)o.r0;
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int li = k / 6, w = k - 6 * li;
+        if (!EXPORTED || ((o.xrod[li >> 5] >> (li & 31)) & 1u)) dst[k] = o.U[w * o.cap_r + li];
+    }
+}
+
 // Constraint phase for the block's owned constraints (modes above).  In
 // B_STEP the new state (delta_{k+1}, g_{k+1}, gamma_ref) goes to buffer nx,
 // and acc0..2 = s.s, s.y, y.y against buffer cur; acc3 = max |pi|.
 template <typename T, int MODE, bool ST>
-__device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, int cur, int nx, T acc[4])
+__device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, int cur, int nx, T alpha, T acc[4])
 {
     constexpr bool COMP = MODE != B_STEP && sizeof(T) == 4;
     const size_t mp = a.mp;
     T* gnew = nx ? a.gg1 : a.gg0;
     const T* gold = cur ? a.gg1 : a.gg0;
-    const T* sdnew = nx ? o.ds[1] : o.ds[0];     // shared copies (staged blocks)
-    const T* sdold = cur ? o.ds[1] : o.ds[0];
     const T* Uu = MODE == B_STEP ? a.U : a.Uref;
     const int nc = o.c1 - o.c0;
+#pragma unroll 1
     for (int lc = threadIdx.x; lc < nc; lc += blockDim.x) {
         const int c = o.c0 + lc;
         T Ui[6], Uj[6], r[9], base, dm, gam, dold = T(0), gro = T(0);
+        bool xstate = false;
         if (ST) {
             const int il = o.ci[lc], j = o.cj[lc];
+            xstate = j >= 0 && (j < o.r0 || j >= o.r1);
 #pragma unroll
             for (int w = 0; w < 6; ++w) Ui[w] = o.U[w * o.cap_r + il];
             if (j < 0) {   // a wall: no other side
@@ -491,11 +562,15 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
 #pragma unroll
             for (int w = 0; w < 9; ++w) r[w] = o.rec[w * o.cap_c + lc];
             base = MODE == B_STEP ? o.gref[lc] : a.q[c];
-            dm = sdnew[lc];
             gam = o.gam[lc];
             if (MODE == B_STEP) {
-                dold = sdold[lc];
+                // delta_{k+1} as the rod phase formed it (same inputs, same rounding)
+                dold = o.ds[lc];
                 gro = o.grs[lc];
+                dm = a_value<A_STEP, T>(dold, gro, gam, alpha, comp_of(a, c) >= T(0));
+                o.ds[lc] = dm;
+            } else {
+                dm = o.ds[lc];
             }
         } else {
             ld_u6(Uu, a.ci[c], Ui);
@@ -557,7 +632,9 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
         // g of the new iterate (for B_REF: gamma_ref itself, delta = 0)
         if (ST) {
             o.grs[lc] = gr;
-            st_dg(gnew, c, dm, gr);    // the state other blocks read in the next phase A
+            // the state other blocks read in the next rod phase: in a step,
+            // only that of constraints whose other rod is another block's
+            if (MODE != B_STEP || xstate) st_dg(gnew, c, dm, gr);
         } else {
             gnew[4 * (size_t)c + 1] = gr;
         }
@@ -585,8 +662,9 @@ __device__ __forceinline__ void fold_delta(const SolveArgs<T>& a, const Own<T>& 
 {
     T* gc = cur ? a.gg1 : a.gg0;
     T* go = cur ? a.gg0 : a.gg1;
-    T* sdc = cur ? o.ds[1] : o.ds[0];
+    T* sdc = o.ds;
     const int nc = o.c1 - o.c0;
+#pragma unroll 1
     for (int lc = threadIdx.x; lc < nc; lc += blockDim.x) {
         const int c = o.c0 + lc;
         T d, g, gr, gl;
@@ -616,9 +694,9 @@ __device__ __forceinline__ void fold_delta(const SolveArgs<T>& a, const Own<T>& 
 
 // Block partial of (sum, sum, sum, max) in the working precision (warp
 // shuffles, then warp 0 over the warp results, fixed order); lane 0 stores
-// it as float64 for the cross-block sum.
+// it for the cross-block sum.
 template <typename T>
-__device__ __forceinline__ void block_partial(T v[4], T (*red)[4], double* dst, int stride)
+__device__ __forceinline__ void block_partial(T v[4], T (*red)[4], T* dst, int stride)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -648,7 +726,7 @@ __device__ __forceinline__ void block_partial(T v[4], T (*red)[4], double* dst, 
         }
         if (lane == 0) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) dst[u * stride] = (double)w[u];
+            for (int u = 0; u < 4; ++u) dst[u * stride] = w[u];
         }
     }
 }
@@ -686,32 +764,40 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, i
 }
 
 // After a barrier: warps 0-3 each reduce one component of the per-block
-// partials ([4][nb]: a warp reads one contiguous row) in float64 in a fixed
-// order, the first 8 loads of every lane in flight together, and the four
-// totals are broadcast through shared memory.
-__device__ __forceinline__ void grid_total(const double* partials, int nb, double* bc, double out[4])
+// partials ([4][nb]: a warp reads one contiguous row) in the working
+// precision in a fixed order, the first 8 loads of every lane in flight
+// together, and the four totals are broadcast through shared memory.
+template <typename T>
+__device__ __forceinline__ void grid_total(const T* partials, int nb, T* bc, T out[4])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 4) {
-        const bool is_max = warp == 3;
-        const double* row = partials + (size_t)warp * nb;
-        double xs[8];
+        const T* row = partials + (size_t)warp * nb;
+        T xs[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int b = lane + 32 * k;
-            xs[k] = b < nb ? __ldcg(row + b) : 0.0;
+            xs[k] = b < nb ? __ldcg(row + b) : T(0);
         }
-        double w = 0.0;
+        T w = T(0);
+        if (warp == 3) {   // max |pi| (every entry >= 0)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) w = is_max ? (xs[k] > w ? xs[k] : w) : w + xs[k];
-        for (int b = lane + 256; b < nb; b += 32) {
-            const double x = __ldcg(row + b);
-            w = is_max ? (x > w ? x : w) : w + x;
-        }
+            for (int k = 0; k < 8; ++k) w = xs[k] > w ? xs[k] : w;
+            for (int b = lane + 256; b < nb; b += 32) {
+                const T x = __ldcg(row + b);
+                w = x > w ? x : w;
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double y = __shfl_down_sync(0xffffffffu, w, o);
-            w = is_max ? (y > w ? y : w) : w + y;
+            for (int o = 16; o > 0; o >>= 1) {
+                const T y = __shfl_down_sync(0xffffffffu, w, o);
+                w = y > w ? y : w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) w += xs[k];
+            for (int b = lane + 256; b < nb; b += 32) w += __ldcg(row + b);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
         }
         if (lane == 0) bc[warp] = w;
     }
@@ -720,31 +806,43 @@ __device__ __forceinline__ void grid_total(const double* partials, int nb, doubl
     for (int u = 0; u < 4; ++u) out[u] = bc[u];
 }
 
-// Step-size bookkeeping, done by thread 0 alone (float64 division is slow
-// on this part; every other thread only reads the broadcast).
+// The stopping test's complement: (h/D) max |pi| > tol, decided in float64
+// (float64 iterations) or by the equivalent float32 threshold.
+__device__ __forceinline__ bool above_tol(const SolveArgs<double>& a, double pimax) { return a.hD * pimax > a.tol; }
+__device__ __forceinline__ bool above_tol(const SolveArgs<float>& a, float pimax) { return pimax > a.pi_tol; }
+
+// Step-size bookkeeping, done by thread 0 alone (every other thread only
+// reads the broadcast).
+// Pass kinds of the loop: a step, a reference pass, the line step of alpha_0.
+enum { P_STEP = 0, P_REF = 1, P_PG = 2 };
+
+template <typename T>
 struct StepState {
-    double alpha0, alpha, res;
+    T alpha0, pimax;   // max |pi| of the last test: the residual is (h/D) pimax
+    double pp;         // pi.pi at gamma_0 (for alpha_0)
     int iters, cur, done;
     int since;   // iterations since the last reference refresh
+    __device__ __forceinline__ double residual(double hD) const { return hD * (double)pimax; }
 };
 
 template <typename T>
 struct Shared {
     T red[32][4];
-    double bc[4];
-    double part[4];   // this block's partial (cluster solver: read by the cluster's blocks)
+    T bc[4];
+    T part[4];   // this block's partial (cluster solver: read by the cluster's blocks)
     T alpha;
-    int done, ok, refresh, cur, sys;
+    int done, ok, kind, cur, sys;
 };
 
 // Synchronisation of the blocks that share one problem.
 // Grid: all blocks of a cooperative launch, bounded barrier on a global
 // counter, partials in global memory.
+template <typename T>
 struct GridSync {
     unsigned* bar;
     int* flags;
     long long wait_cycles;
-    double* partials;
+    T* partials;   // [4][nb]
     unsigned nb, epoch;
     template <typename SH>
     __device__ __forceinline__ bool barrier(SH& sh)
@@ -752,10 +850,10 @@ struct GridSync {
         return grid_barrier(bar, nb * ++epoch, flags, wait_cycles, &sh.ok);
     }
     template <typename SH>
-    __device__ __forceinline__ double* slot(SH&) { return partials + blockIdx.x; }
-    __device__ __forceinline__ int stride() const { return (int)nb; }   // partials are [4][nb]
+    __device__ __forceinline__ T* slot(SH&) { return partials + blockIdx.x; }
+    __device__ __forceinline__ int stride() const { return (int)nb; }
     template <typename SH>
-    __device__ __forceinline__ void total(SH& sh, double tot[4]) { grid_total(partials, nb, sh.bc, tot); }
+    __device__ __forceinline__ void total(SH& sh, T tot[4]) { grid_total(partials, nb, sh.bc, tot); }
 };
 
 // Cluster: the blocks of one thread-block cluster, hardware cluster barrier,
@@ -769,18 +867,18 @@ struct ClusterSync {
         return true;
     }
     template <typename SH>
-    __device__ __forceinline__ double* slot(SH& sh) { return sh.part; }
+    __device__ __forceinline__ auto slot(SH& sh) { return sh.part; }
     __device__ __forceinline__ int stride() const { return 1; }
-    template <typename SH>
-    __device__ __forceinline__ void total(SH& sh, double tot[4])
+    template <typename SH, typename T>
+    __device__ __forceinline__ void total(SH& sh, T tot[4])
     {
         cg::cluster_group cl = cg::this_cluster();
         if (threadIdx.x < 4) {
             const int u = threadIdx.x;
             const unsigned cs = cl.num_blocks();
-            double w = 0.0;
+            T w = T(0);
             for (unsigned r = 0; r < cs; ++r) {
-                const double x = cl.map_shared_rank(sh.part, r)[u];
+                const T x = cl.map_shared_rank(sh.part, r)[u];
                 w = u == 3 ? (x > w ? x : w) : w + x;
             }
             sh.bc[u] = w;
@@ -831,106 +929,116 @@ __device__ __forceinline__ int find_rank(const int* rowP, const int* rowQ, int l
 // On return thread 0 holds the step state; sh.cur is the final buffer.
 template <typename T, bool ST, typename SY>
 __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& o, Shared<T>& sh, SY& sy,
-                                           StepState& st)
+                                           StepState<T>& st)
 {
-    double* mine = sy.slot(sh);
-    double tot[4];
+    T* mine = sy.slot(sh);
+    T tot[4];
     T v[4];
-    st.alpha0 = 1.0;
+    st.alpha0 = T(1);
+    st.pimax = T(0);
+    st.pp = 0.0;
     st.cur = 0;
     st.since = 0;
-    if (threadIdx.x == 0) sh.cur = 0;
-
-    // gamma_0 is the reference (delta = 0): Uref = M D gamma_0, then
-    // gref = q + D^T Uref = g_0 and the projected gradient at gamma_0
-    phase_a<T, A_REF, ST>(a, o, 0, T(0));
-    if (!sy.barrier(sh)) return;
-    v[0] = v[1] = v[2] = v[3] = T(0);
-    phase_b<T, B_REF, ST>(a, o, 0, 0, v);
-    block_partial(v, sh.red, mine, sy.stride());
-    if (!sy.barrier(sh)) return;
-    sy.total(sh, tot);
+    st.iters = 0;
     if (threadIdx.x == 0) {
-        st.res = a.hD * tot[3];
-        st.iters = 0;
-        st.cur = 0;
-        st.done = !(st.res > a.tol && a.max_iter > 0);
-        sh.done = st.done;
+        sh.cur = 0;
+        sh.kind = P_REF;
     }
     __syncthreads();
-    if (!sh.done) {
-        const double pp = tot[0];
-        // alpha_0 = pi.pi / pi.A.pi (exact line step along the projected gradient)
-        v[0] = phase_a<T, A_PG, ST>(a, o, 0, T(0));
-        v[1] = v[2] = v[3] = T(0);
-        // every block has read the partials (grid_total) before any rewrites them
-        if (!sy.barrier(sh)) return;
+    int cur = 0, k = 0;           // k: steps taken
+    bool first = true;            // the first pass: the reference is gamma_0 (delta = 0)
+    bool du_pending = false;      // staged: the last step's dU is in shared memory only
+    // Every pass ends in the same reduction and decision code, and each
+    // pass's code appears once: the persistent kernel's code must stay
+    // within the instruction cache (inlined copies made every warp stall on
+    // instruction fetch after each barrier).
+    for (;;) {
+        const int kind = sh.kind;
+        const bool initial = first;   // this pass is the reference pass at gamma_0
+        const int nx = cur ^ 1;
+        v[0] = v[1] = v[2] = v[3] = T(0);
+        if (kind == P_STEP) {
+            phase_a<T, A_STEP, ST>(a, o, cur, sh.alpha);
+            du_pending = ST;
+            if (ST) store_du<T, true>(a, o);
+            if (!sy.barrier(sh)) return;
+            phase_b<T, B_STEP, ST>(a, o, cur, nx, sh.alpha, v);
+        } else if (kind == P_REF) {
+            // the reference takes the iterate; Uref = M D gamma_ref, gref =
+            // q + D^T Uref and g are recomputed from the split records with
+            // compensated sums, and pi.pi and max |pi| with them
+            if (!first) {
+                fold_delta<T, ST>(a, o, cur);
+                if (!sy.barrier(sh)) return;
+            }
+            first = false;
+            phase_a<T, A_REF, ST>(a, o, cur, T(0));
+            du_pending = false;
+            if (!sy.barrier(sh)) return;
+            phase_b<T, B_REF, ST>(a, o, cur, cur, T(0), v);
+        } else {
+            // pi.A.pi for alpha_0 = pi.pi / pi.A.pi (exact line step along
+            // the projected gradient at gamma_0)
+            v[0] = phase_a<T, A_PG, ST>(a, o, cur, T(0));
+            // every block has read the partials (grid_total) before any rewrites them
+            if (!sy.barrier(sh)) return;
+        }
         block_partial(v, sh.red, mine, sy.stride());
         if (!sy.barrier(sh)) return;
         sy.total(sh, tot);
+        if (kind == P_STEP) cur = nx;
         if (threadIdx.x == 0) {
-            const double pap = tot[0];
-            double alpha0 = pp / pap;
-            if (!(pap > 0.0) || !isfinite(alpha0) || !(alpha0 > 0.0)) alpha0 = 1.0;
-            st.alpha0 = st.alpha = alpha0;
-            sh.alpha = (T)alpha0;
-        }
-        __syncthreads();
-        int cur = 0;
-        for (int k = 0; k < a.max_iter; ++k) {
-            const int nx = cur ^ 1;
-            phase_a<T, A_STEP, ST>(a, o, cur, sh.alpha);
-            if (!sy.barrier(sh)) return;
-            v[0] = v[1] = v[2] = v[3] = T(0);
-            phase_b<T, B_STEP, ST>(a, o, cur, nx, v);
-            block_partial(v, sh.red, mine, sy.stride());
-            if (!sy.barrier(sh)) return;
-            sy.total(sh, tot);
-            cur = nx;
-            if (threadIdx.x == 0) {
-                const double ss = tot[0], sy = tot[1], yy = tot[2];
-                st.res = a.hD * tot[3];
+            int next = P_STEP;
+            if (kind == P_STEP) {
+                const T ss = tot[0], sy = tot[1], yy = tot[2];
+                st.pimax = tot[3];
                 st.cur = cur;
                 st.iters = k + 1;
-                const bool below = !(st.res > a.tol);
-                double an = (k & 1) == 0 ? ss / sy : sy / yy;
-                if (!(sy > 0.0) || !isfinite(an) || !(an > 0.0)) an = st.alpha0;
-                st.alpha = an;
-                sh.alpha = (T)an;
+                const bool below = !above_tol(a, tot[3]);
+                T an = (k & 1) == 0 ? ss / sy : sy / yy;
+                if (!(sy > T(0)) || !isfinite(an) || !(an > T(0))) an = st.alpha0;
+                sh.alpha = an;
                 // float32: a residual below tol is confirmed on a fresh
                 // reference before the loop stops (the increments since the
                 // last refresh carry float32 rounding); after a refresh that
                 // did not confirm it, the next try waits two iterations
                 st.done = below && a.refresh == 0;
                 ++st.since;
-                sh.refresh = a.refresh > 0 && ((below && st.since >= 3) || st.since >= a.refresh);
-                if (sh.refresh) st.since = 0;
-                sh.done = st.done;
-            }
-            __syncthreads();
-            if (sh.done) break;
-            if (sh.refresh) {
-                // the reference takes the iterate; Uref, gref and g are
-                // recomputed from the split records with compensated sums, and
-                // max |pi| with them
-                fold_delta<T, ST>(a, o, cur);
-                if (!sy.barrier(sh)) return;
-                phase_a<T, A_REF, ST>(a, o, cur, T(0));
-                if (!sy.barrier(sh)) return;
-                v[0] = v[1] = v[2] = v[3] = T(0);
-                phase_b<T, B_REF, ST>(a, o, cur, cur, v);
-                block_partial(v, sh.red, mine, sy.stride());
-                if (!sy.barrier(sh)) return;
-                sy.total(sh, tot);
-                if (threadIdx.x == 0) {
-                    st.res = a.hD * tot[3];
-                    st.done = !(st.res > a.tol);
-                    sh.done = st.done;
+                const bool refresh = a.refresh > 0 && ((below && st.since >= 3) || st.since >= a.refresh);
+                if (refresh) {
+                    st.since = 0;
+                    next = P_REF;
+                } else if (k + 1 >= a.max_iter) {
+                    st.done = 1;
                 }
-                __syncthreads();
-                if (sh.done) break;
+            } else if (kind == P_REF) {
+                st.pimax = tot[3];
+                st.done = !above_tol(a, tot[3]) || k >= a.max_iter;
+                if (initial) {   // gamma_0: the line step comes next
+                    st.pp = (double)tot[0];
+                    next = P_PG;
+                }
+            } else {
+                const double pap = (double)tot[0];
+                double alpha0 = st.pp / pap;
+                if (!(pap > 0.0) || !isfinite(alpha0) || !(alpha0 > 0.0) || !isfinite((T)alpha0)) alpha0 = 1.0;
+                st.alpha0 = (T)alpha0;
+                sh.alpha = (T)alpha0;
+                st.done = 0;
             }
+            sh.kind = next;
+            sh.done = st.done;
         }
+        __syncthreads();
+        if (kind == P_STEP) ++k;
+        if (sh.done) break;
+    }
+    if (ST) {
+        // the final state of every owned constraint, and dU of every rod
+        // when the last rod phase was a step
+        T* gf = cur ? a.gg1 : a.gg0;
+        for (int lc = threadIdx.x; lc < o.c1 - o.c0; lc += blockDim.x) st_dg(gf, o.c0 + lc, o.ds[lc], o.grs[lc]);
+        if (du_pending) store_du<T, false>(a, o);
     }
     if (threadIdx.x == 0) sh.cur = st.cur;
     __syncthreads();
@@ -980,16 +1088,17 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd(SolveArgs<T> a)
         carve(o, dyn);
         stage_in(a, o);
     }
-    GridSync sy;
-    sy.bar = a.bar; sy.flags = a.flags; sy.wait_cycles = a.wait_cycles; sy.partials = a.partials;
+    GridSync<T> sy;
+    sy.bar = a.bar; sy.flags = a.flags; sy.wait_cycles = a.wait_cycles;
+    sy.partials = reinterpret_cast<T*>(a.partials);
     sy.nb = gridDim.x; sy.epoch = 0;
-    StepState st;   // meaningful in thread 0 only
+    StepState<T> st;   // meaningful in thread 0 only
     solve_loop<T, ST>(a, o, sh, sy, st);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.out[1] = st.alpha0;
+        a.out[1] = (double)st.alpha0;
         a.flags[F_FINAL] = st.cur;
         a.flags[F_ITERS] = st.iters;
-        a.out[0] = st.res;
+        a.out[0] = st.residual(a.hD);
     }
 }
 
@@ -1038,7 +1147,7 @@ k_bbpgd_sys(SolveArgs<T> a, int ns, const long long* __restrict__ sysoff, const 
         o.cap_r = o.r1 - o.r0;
         o.cap_q = o.q1 - o.q0;
         ClusterSync sy;
-        StepState st;
+        StepState<T> st;
         solve_loop<T, false>(a, o, sh, sy, st);
         if (sh.cur == 1) {
             for (int c = o.c0 + threadIdx.x; c < o.c1; c += blockDim.x) {
@@ -1050,9 +1159,10 @@ k_bbpgd_sys(SolveArgs<T> a, int ns, const long long* __restrict__ sysoff, const 
         }
         if (crank == 0 && threadIdx.x == 0) {
             sys_iters[s] = st.iters;
-            sys_res[s] = st.res;
+            const double res = st.residual(a.hD);
+            sys_res[s] = res;
             atomicMax(&a.flags[F_ITERS], st.iters);
-            const double r = st.res < 0.0 ? 0.0 : st.res;   // a NaN stays NaN (its bits order above every number)
+            const double r = res < 0.0 ? 0.0 : res;   // a NaN stays NaN (its bits order above every number)
             atomicMax(reinterpret_cast<unsigned long long*>(a.out), (unsigned long long)__double_as_longlong(r));
         }
         __syncthreads();   // bounds and sh are rewritten for the next system
@@ -1101,6 +1211,24 @@ cudaError_t launch_rank(aLENS_ctx* ctx, int n)
     return cudaGetLastError();
 }
 
+// Largest value f of type T with hD * (double)f <= tol in float64 (the
+// float64 product is monotone in f, so max |pi| <= f exactly when the float64
+// residual test passes); -1 when no f >= 0 passes.
+template <typename T>
+static T pi_threshold(double hD, double tol)
+{
+    if (!(hD * 0.0 <= tol)) return T(-1);
+    T f = (T)(tol / hD);
+    if (!(f >= T(0))) f = T(0);
+    while (f > T(0) && !(hD * (double)f <= tol)) f = std::nextafter(f, T(0));
+    for (;;) {
+        const T g = std::nextafter(f, std::numeric_limits<T>::infinity());
+        if (!(g < std::numeric_limits<T>::infinity()) || !(hD * (double)g <= tol)) break;
+        f = g;
+    }
+    return f;
+}
+
 template <typename T>
 static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m)
 {
@@ -1121,6 +1249,7 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.rec_lo = sb.rec_lo; a.qe_lo = sb.qe_lo; a.q_lo = sb.q_lo;
     a.comp = ctx->cur_comp ? sb.comp : nullptr;
     a.hD = ctx->p.dt / ctx->p.diameter; a.tol = ctx->p.tol; a.max_iter = ctx->p.max_iter;
+    a.pi_tol = pi_threshold<T>(a.hD, a.tol);
     a.wait_cycles = (long long)(ctx->wait_s * ctx->clock_khz * 1e3);
     a.fault = 0;
     a.bstart = ctx->bstart;
