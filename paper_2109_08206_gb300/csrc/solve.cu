@@ -21,11 +21,11 @@
 // When they fit, the block keeps its own constraints' records, q, gamma and
 // g, and its rods' axes and velocities in shared memory for the whole solve
 // (at 1e5 rods the mixed working set, about 30 MB, spreads over the SMs'
-// shared memory); global memory then carries only what other blocks read:
-// the state of constraints whose other rod is another block's, and the
-// velocities of rods that another block's constraints touch (the rest is
-// written once when the solve ends).  Without that fit every block works
-// from the global arrays.  Per iteration:
+// shared memory); global memory then carries what other blocks read: the
+// velocities, and the state of constraints whose other rod is another
+// block's (the rest of the state is written once when the solve ends).
+// Without that fit every block works from the global arrays.  Per
+// iteration:
 //   phase A (one thread per rod, rods taken in ascending order of their
 //     entry counts so that a warp's loops have similar lengths):
 //     delta_{k+1} of every constraint touching the rod is formed on the fly
@@ -243,17 +243,15 @@ struct Own {
     int* rowQ;   // [cap_r + 1] other-side ranges (global CSR positions)
     int* qlist;  // [cap_q] other-side constraint ids of the block's rods
     unsigned short* perm;   // [cap_r] the order in which the rod phase's threads take the rods
-    unsigned* xrod;         // [(cap_r + 31) / 32] bit li: another block reads rod li's velocity
 };
 
 // Shared-memory bytes of a block's share: per owned constraint 13 values
-// and 6 bytes of indices, per rod 9 values, two row pointers, a 16-bit slot
-// of the rod order and an export bit, per other-side entry one id (owner
-// indices are 16-bit: at most 65535 rods).
+// and 6 bytes of indices, per rod 9 values, two row pointers and a 16-bit
+// slot of the rod order, per other-side entry one id (owner indices are
+// 16-bit: at most 65535 rods).
 __host__ __device__ inline size_t staged_bytes(int esize, size_t cap_c, size_t cap_r, size_t cap_q)
 {
-    return (13 * cap_c + 9 * cap_r) * (size_t)esize +
-           (cap_c + 2 * cap_r + 2 + cap_q + (cap_r + 31) / 32) * sizeof(int) +
+    return (13 * cap_c + 9 * cap_r) * (size_t)esize + (cap_c + 2 * cap_r + 2 + cap_q) * sizeof(int) +
            (((cap_c + cap_r) * sizeof(unsigned short) + 3) & ~(size_t)3);
 }
 
@@ -274,7 +272,6 @@ __device__ void carve(Own<T>& o, unsigned char* base)
     o.rowP = ip; ip += R + 1;
     o.rowQ = ip; ip += R + 1;
     o.qlist = ip; ip += o.cap_q;
-    o.xrod = reinterpret_cast<unsigned*>(ip); ip += (R + 31) / 32;
     o.ci = reinterpret_cast<unsigned short*>(ip);
     o.perm = o.ci + C;
 }
@@ -304,7 +301,6 @@ __device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
         o.grs[lc] = T(0);
     }
     for (int k = threadIdx.x; k < o.q1 - o.q0; k += blockDim.x) o.qlist[k] = a.qlist[o.q0 + k];
-    for (int w = threadIdx.x; w < (nr + 31) / 32; w += blockDim.x) o.xrod[w] = 0u;
     // rod order of the rod phase: ascending (owned, other-side) entry
     // counts, so that the 32 rods of a warp run loops of about the same
     // lengths (a warp runs each loop as long as its longest rod's).  Rank
@@ -317,14 +313,6 @@ __device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
     for (int li = threadIdx.x; li < nr; li += blockDim.x) {
         const int no = min(o.rowP[li + 1] - o.rowP[li], 255), nq = min(o.rowQ[li + 1] - o.rowQ[li], 255);
         key[li] = ((unsigned)(no << 8 | nq) << 16) | (unsigned)li;
-        // exported: a constraint on the rod is owned by another block, whose
-        // constraint phase reads the rod's velocity
-        bool ex = false;
-        for (int k = o.rowQ[li] - o.q0; k < o.rowQ[li + 1] - o.q0; ++k) {
-            const int cid = o.qlist[k];
-            ex |= cid < o.c0 || cid >= o.c1;
-        }
-        if (ex) atomicOr(&o.xrod[li >> 5], 1u << (li & 31));
     }
     __syncthreads();
     for (int li = threadIdx.x; li < nr; li += blockDim.x) {
@@ -496,8 +484,7 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
 #pragma unroll
             for (int w = 0; w < 6; ++w) fmf += F[w] * Uv[w];
         } else {
-            // staged steps: the global copy is written in rank order below
-            if (!(ST && MODE == A_STEP)) st_u6(MODE == A_REF ? a.Uref : a.U, i, Uv);
+            st_u6(MODE == A_REF ? a.Uref : a.U, i, Uv);
             if (MODE == A_REF) {
                 const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
                 st_u6(a.U, i, z);   // dU = 0: delta is 0 after a reference pass
@@ -509,23 +496,6 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
         }
     }
     return fmf;
-}
-
-// Staged steps: dU of the block's rods to global memory in rank order
-// (the rod phase takes its rods in count order), only the rods whose
-// velocity another block reads (EXPORTED) or all of them.  Stores before a
-// grid barrier are paid for in its release fence: a step writes only what
-// other blocks read, and the rest once when the solve ends.
-template <typename T, bool EXPORTED>
-__device__ __forceinline__ void store_du(const SolveArgs<T>& a, const Own<T>& o)
-{
-    __syncthreads();
-    const int nv = 6 * (o.r1 - o.r0);
-    T* dst = a.U + 6 * (size_t)o.r0;
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-        const int li = k / 6, w = k - 6 * li;
-        if (!EXPORTED || ((o.xrod[li >> 5] >> (li & 31)) & 1u)) dst[k] = o.U[w * o.cap_r + li];
-    }
 }
 
 // Constraint phase for the block's owned constraints (modes above).  In
@@ -947,7 +917,6 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
     __syncthreads();
     int cur = 0, k = 0;           // k: steps taken
     bool first = true;            // the first pass: the reference is gamma_0 (delta = 0)
-    bool du_pending = false;      // staged: the last step's dU is in shared memory only
     // Every pass ends in the same reduction and decision code, and each
     // pass's code appears once: the persistent kernel's code must stay
     // within the instruction cache (inlined copies made every warp stall on
@@ -959,8 +928,6 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
         v[0] = v[1] = v[2] = v[3] = T(0);
         if (kind == P_STEP) {
             phase_a<T, A_STEP, ST>(a, o, cur, sh.alpha);
-            du_pending = ST;
-            if (ST) store_du<T, true>(a, o);
             if (!sy.barrier(sh)) return;
             phase_b<T, B_STEP, ST>(a, o, cur, nx, sh.alpha, v);
         } else if (kind == P_REF) {
@@ -973,7 +940,6 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
             }
             first = false;
             phase_a<T, A_REF, ST>(a, o, cur, T(0));
-            du_pending = false;
             if (!sy.barrier(sh)) return;
             phase_b<T, B_REF, ST>(a, o, cur, cur, T(0), v);
         } else {
@@ -1034,11 +1000,10 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
         if (sh.done) break;
     }
     if (ST) {
-        // the final state of every owned constraint, and dU of every rod
-        // when the last rod phase was a step
+        // the final state of every owned constraint (a step stores only the
+        // state that other blocks read)
         T* gf = cur ? a.gg1 : a.gg0;
         for (int lc = threadIdx.x; lc < o.c1 - o.c0; lc += blockDim.x) st_dg(gf, o.c0 + lc, o.ds[lc], o.grs[lc]);
-        if (du_pending) store_du<T, false>(a, o);
     }
     if (threadIdx.x == 0) sh.cur = st.cur;
     __syncthreads();
