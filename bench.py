@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--sample-rods", type=int, default=10000, help="rods in the oracle's spatial sample")
     ap.add_argument("--no-tune", action="store_true", help="keep the default solver launch shape")
+    ap.add_argument("--scaling", type=float, default=None,
+                    help="diagonal scaling exponent of the BBPGD iteration (default: the library's, 0.5)")
     return ap.parse_args()
 
 
@@ -563,7 +565,10 @@ def run_ours(args):
     max_pairs = 12 * n
 
     def make_ctx(precision):
-        return job.context(A, precision, args.tol, stream)
+        ctx = job.context(A, precision, args.tol, stream)
+        if args.scaling is not None:
+            ctx.set_scaling(args.scaling)
+        return ctx
 
     def timed(ctx, K, W_, host=None, w=4):
         """K timed steps after W_ warm-ups; returns per-step ms, infos and the
@@ -705,7 +710,7 @@ def run_ours(args):
         cpu = {"value": rods / t_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample}
     kernel = "k_bbpgd_sys<float>" if isinstance(job, BatchJob) else "k_bbpgd<float>"
     config = job.config(W, m)
-    config.update({"tol": args.tol,
+    config.update({"tol": args.tol, "scaling_beta": 0.5 if args.scaling is None else args.scaling,
                    "l2": "flushed (256 MB write) between steps; inputs restored outside the timed region",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"})
     line = {

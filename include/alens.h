@@ -79,8 +79,10 @@ typedef enum {
 
 typedef enum {
     ALENS_FP64 = 0,   /* every stage in float64 */
-    ALENS_MIXED = 1   /* solver iterations (D, M, D^T) in float32; geometry, pair
-                         decisions, the residual and all reductions in float64 */
+    ALENS_MIXED = 1   /* solver iterations (D, M, D^T, their sums and step sizes)
+                         in float32 on a float64-accurate reference refreshed
+                         every 64 iterations; geometry, pair decisions, the
+                         reference passes and the stopping decision in float64 */
 } aLENS_precision;
 
 typedef struct {
@@ -339,6 +341,16 @@ ALENS_API aLENS_status aLENS_set_batch_launch(aLENS_ctx* ctx, int32_t threads, i
 /* Bound on every grid-wide wait inside the solver kernel, in seconds
  * (default 5).  A wait that runs out makes the call return ALENS_ERR_TIMEOUT. */
 ALENS_API aLENS_status aLENS_set_wait_limit(aLENS_ctx* ctx, double seconds);
+
+/* Diagonal scaling of the BBPGD iteration (Appendix Eq. suppcqpdef is
+ * solved for gamma = S gamma~ with S = diag(sigma_c)): the iteration runs on
+ * the records sigma_c D_c, q~_c = sigma_c q_c and the compliance sigma_c^2
+ * C_c, with sigma_c = (D_c^T M D_c + C_c)^(-beta/2) computed in float64 when
+ * the solve is set up.  The minimiser, the residual (taken on the unscaled
+ * projected gradient) and every output are those of the unscaled problem;
+ * only the path and the iteration count change.  beta in [0, 1]: 0 is the
+ * unscaled iteration, 1 Jacobi scaling; default 0.5.  INVALID otherwise. */
+ALENS_API aLENS_status aLENS_set_scaling(aLENS_ctx* ctx, double beta);
 
 /* Test hook: mode 1 makes one thread block of the next solver launch leave
  * before its first grid-wide arrival, so that the other blocks' bounded

@@ -104,6 +104,7 @@ def lib():
             "aLENS_random_words": (i32, [vp, i64, C.c_uint64, i64, vp]),
             "aLENS_run": (i32, [vp, i64, vp, vp, vp, i64, d, C.c_uint64, i64, i32, C.POINTER(StepStats), IP]),
             "aLENS_set_wait_limit": (i32, [vp, d]),
+            "aLENS_set_scaling": (i32, [vp, d]),
             "aLENS_inject_fault": (i32, [vp, i32]),
             "aLENS_set_launch": (i32, [vp, i32, i32]),
         }
@@ -203,6 +204,12 @@ class Context:
         st = self._lib.aLENS_set_wait_limit(self._h, float(seconds))
         if st != 0:
             raise AlensError(st, "aLENS_set_wait_limit")
+
+    def set_scaling(self, beta: float):
+        """Diagonal scaling exponent of the BBPGD iteration (0 = unscaled)."""
+        st = self._lib.aLENS_set_scaling(self._h, float(beta))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_scaling")
 
     def inject_fault(self, mode: int):
         st = self._lib.aLENS_inject_fault(self._h, int(mode))

@@ -85,7 +85,7 @@ void free_all(aLENS_ctx* c)
     void* ptrs[] = {c->xw, c->axis, c->unc, c->pos32, c->ax32, c->cellkey, c->sorted_id, c->spos32, c->sax32,
                     c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand, c->keep,
                     c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->perm, c->rank, c->curP, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
-                    c->q64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp,
+                    c->q64, c->scale64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp,
                     c->systab, c->sysid, c->sysoff, c->sys_order, c->sys_iters, c->sys_res, c->adj_ws,
                     c->sp_ends, c->sp_arms, c->sp_kappa, c->sp_rest, c->comp64, c->fnc_buf, c->gin_buf,
                     c->row_keys, c->prev_keys, c->prev_gam};
@@ -327,6 +327,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     c->max_pairs = max_pairs;
     c->stream = (cudaStream_t)cuda_stream;
     c->wait_s = 5.0;
+    c->scale_beta = kDefaultScaleBeta;
     c->solve_threads = 1024;
     c->solve_bps = 0;
     c->batch_threads = 1024;
@@ -378,9 +379,10 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->phi, mp * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->dgeom, 9 * mp * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->q64, mp * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->scale64, mp * sizeof(double)) == cudaSuccess;
     // solver buffers, sized for float64; the float32 views alias the same memory
     // every slice starts on a 64-byte boundary (vector loads): 8 elements of slack each
-    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 12 * np + mp + 4 * np + mp + 8 * 12;
+    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 12 * np + mp + 4 * np + mp + mp + 8 * 13;
     ok &= dmalloc((char**)&c->solve_ws, solve_elems * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->partials, (size_t)c->max_blocks * 4 * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->bstart, ((size_t)c->max_blocks + 1) * sizeof(int)) == cudaSuccess;
@@ -408,6 +410,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         s.rec = carve64(9 * mp); s.qe = carve64(8 * mp); s.q = carve64(mp); s.ax = carve64(3 * np);
         s.mobr = carve64(4 * np);
         s.comp = carve64(mp);
+        s.isc = carve64(mp);
         float* fb = (float*)c->solve_ws;
         size_t f = 0;
         auto carve32 = [&](size_t cnt) { float* r = fb + f; f = (f + cnt + 7) & ~(size_t)7; return r; };
@@ -417,6 +420,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         t.rec = carve32(9 * mp); t.qe = carve32(8 * mp); t.q = carve32(mp); t.ax = carve32(3 * np);
         t.mobr = carve32(4 * np);
         t.comp = carve32(mp);
+        t.isc = carve32(mp);
         // the float32 views use at most half of the workspace: room for the low parts
         t.rec_lo = carve32(9 * mp); t.qe_lo = carve32(8 * mp); t.q_lo = carve32(mp);
     }
@@ -458,6 +462,13 @@ aLENS_status aLENS_set_wait_limit(aLENS_ctx* c, double seconds)
 {
     if (!c || !(seconds > 0) || seconds > 3600) return ALENS_ERR_INVALID;
     c->wait_s = seconds;
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_set_scaling(aLENS_ctx* c, double beta)
+{
+    if (!c || !(beta >= 0.0 && beta <= 1.0)) return ALENS_ERR_INVALID;
+    c->scale_beta = beta;
     return ALENS_OK;
 }
 

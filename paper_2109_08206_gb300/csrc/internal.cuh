@@ -47,6 +47,9 @@ struct Geo {                 // everything the geometry kernels need
     float half_f;            // L/2 in float
 };
 
+// Default exponent of the solver's diagonal scaling sigma_c = A_cc^(-beta/2).
+constexpr double kDefaultScaleBeta = 0.5;
+
 struct Mob {                 // inverse drag coefficients of one rod (all rods alike)
     double inv_perp, inv_par, inv_rot, inv_spin;
 };
@@ -189,6 +192,7 @@ struct SolveBufs {           // typed views into the solver workspace
     T* qe_lo;                // [mp][8]
     T* q_lo;                 // [mp]
     T* comp;                 // [mp] < 0 collision, >= 0 spring compliance 1/(h kappa) (solver order)
+    T* isc;                  // [mp] 1 / sigma_c: the constraint's scaling undone (solver order)
 };
 
 }  // namespace alens
@@ -236,6 +240,8 @@ struct aLENS_ctx {
     double* phi;             // [mp]
     double* dgeom;           // [mp][9]
     double* q64;             // [mp]
+    double* scale64;         // [mp] sigma_c of the solver's diagonal scaling (solver order)
+    double scale_beta;       // sigma_c = A_cc^(-beta/2); 0: the unscaled iteration
     void* solve_ws;          // typed solver buffers (sized for double)
     alens::SolveBufs<double> sb64;
     alens::SolveBufs<float> sb32;

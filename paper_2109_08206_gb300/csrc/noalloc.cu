@@ -38,13 +38,15 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kRodInts = align256(sizeof(int) * (kNoallocMaxRods + 1));
 constexpr size_t kPairInts = align256(sizeof(int) * kNoallocMaxPairs);
 constexpr size_t kSolveWs =
-    align256(sizeof(double) * (28 * (size_t)kNoallocMaxPairs + 19 * (size_t)kNoallocMaxRods + 96));
+    align256(sizeof(double) * (29 * (size_t)kNoallocMaxPairs + 19 * (size_t)kNoallocMaxRods + 104));
+constexpr size_t kPairDoubles = align256(sizeof(double) * kNoallocMaxPairs);
 constexpr size_t kPartials = align256(sizeof(double) * 4 * kNoallocMaxBlocks);
 constexpr size_t kBstart = align256(sizeof(int) * (kNoallocMaxBlocks + 1));
 constexpr int kScanTmpLen = (kNoallocMaxRods + 4095) / 4096 + 2;
 constexpr size_t kSmall = align256(16 * sizeof(unsigned)) + align256(F_NFLAGS * sizeof(int)) +
                           align256(C_NCOUNT * sizeof(unsigned long long)) + align256(kScanTmpLen * sizeof(int));
-constexpr size_t kNoallocScratchBytes = 6 * kRodInts + 4 * kPairInts + kSolveWs + kPartials + kBstart + kSmall;
+constexpr size_t kNoallocScratchBytes =
+    6 * kRodInts + 4 * kPairInts + kPairDoubles + kSolveWs + kPartials + kBstart + kSmall;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
@@ -105,6 +107,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
     c.clock_khz = clk > 0 ? clk : 2.1e6;
     c.max_blocks = c.num_sms * 8 < kNoallocMaxBlocks ? c.num_sms * 8 : kNoallocMaxBlocks;
     c.wait_s = 5.0;
+    c.scale_beta = kDefaultScaleBeta;
     c.solve_threads = 1024;
     c.wall_axis = -1;
     double zperp = 4.0 * M_PI * params->viscosity * params->length / log(2.0 * params->length / params->diameter);
@@ -125,6 +128,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
     c.qlist = (int*)take(kPairInts);
     c.ci = (int*)take(kPairInts);
     c.cj = (int*)take(kPairInts);
+    c.scale64 = (double*)take(kPairDoubles);
     c.solve_ws = take(kSolveWs);
     c.partials = (double*)take(kPartials);
     c.bstart = (int*)take(kBstart);
@@ -143,6 +147,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
         c.sb64.rec = c64(9 * mp); c.sb64.qe = c64(8 * mp); c.sb64.q = c64(mp); c.sb64.ax = c64(3 * np);
         c.sb64.mobr = c64(4 * np);
         c.sb64.comp = c64(mp);
+        c.sb64.isc = c64(mp);
         float* b32 = (float*)c.solve_ws;
         size_t v = 0;
         auto c32 = [&](size_t cnt) { float* r = b32 + v; v = (v + cnt + 7) & ~(size_t)7; return r; };
@@ -151,6 +156,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
         c.sb32.rec = c32(9 * mp); c.sb32.qe = c32(8 * mp); c.sb32.q = c32(mp); c.sb32.ax = c32(3 * np);
         c.sb32.mobr = c32(4 * np);
         c.sb32.comp = c32(mp);
+        c.sb32.isc = c32(mp);
         // the float32 views use at most half of the workspace: room for the low parts
         c.sb32.rec_lo = c32(9 * mp); c.sb32.qe_lo = c32(8 * mp); c.sb32.q_lo = c32(mp);
     }

@@ -216,6 +216,7 @@ struct SolveArgs {
     const T* __restrict__ rec_lo; // float32: low parts of rec, qe and q for the reference passes (else NULL)
     const T* __restrict__ qe_lo;
     const T* __restrict__ q_lo;
+    const T* __restrict__ isc;    // [mp] 1/sigma_c of the diagonal scaling (1 when unscaled)
     double hD, tol;
     T pi_tol;      // stopping threshold on max |pi| (float32: see above)
     int max_iter;
@@ -609,7 +610,8 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
             gnew[4 * (size_t)c + 1] = gr;
         }
         const T pi = (bil || dm > -gam) ? gr : (gr < T(0) ? gr : T(0));
-        const T api = pi < T(0) ? -pi : pi;
+        // the residual is taken on the unscaled projected gradient pi / sigma_c
+        const T api = (pi < T(0) ? -pi : pi) * __ldg(&a.isc[c]);
         acc[3] = api > acc[3] ? api : acc[3];
         if (MODE == B_REF) {
             acc[0] += pi * pi;
@@ -1152,14 +1154,14 @@ __global__ void k_sys_order(int ns, const long long* __restrict__ sysoff, const 
 // gamma back in the caller's pair order.
 template <typename T>
 __global__ void k_gamma_out(int m, const int* __restrict__ flags, const int* __restrict__ perm, const T* gg0,
-                            const T* gg1, double* __restrict__ out)
+                            const T* gg1, const double* __restrict__ scale64, double* __restrict__ out)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
     if (flags[F_SOLVE_ERR] != 0) return;
     const T* g = flags[F_FINAL] == 0 ? gg0 : gg1;
-    // gamma_ref + gamma_lo + delta
-    out[perm[c]] = ((double)g[4 * (size_t)c + 2] + (double)g[4 * (size_t)c + 3]) + (double)g[4 * (size_t)c];
+    // sigma_c (gamma_ref + gamma_lo + delta): the scaled iterate mapped back
+    out[perm[c]] = scale64[c] * (((double)g[4 * (size_t)c + 2] + (double)g[4 * (size_t)c + 3]) + (double)g[4 * (size_t)c]);
 }
 
 __global__ void k_rank(int n, const int* __restrict__ sorted_id, int* __restrict__ rank)
@@ -1212,6 +1214,7 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.inv_rot = (T)ctx->mob.inv_rot; a.inv_spin = (T)ctx->mob.inv_spin;
     a.mobr = ctx->cur_systab ? sb.mobr : nullptr;
     a.rec_lo = sb.rec_lo; a.qe_lo = sb.qe_lo; a.q_lo = sb.q_lo;
+    a.isc = sb.isc;
     a.comp = ctx->cur_comp ? sb.comp : nullptr;
     a.hD = ctx->p.dt / ctx->p.diameter; a.tol = ctx->p.tol; a.max_iter = ctx->p.max_iter;
     a.pi_tol = pi_threshold<T>(a.hD, a.tol);
@@ -1315,9 +1318,11 @@ cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma
     if (m <= 0 || !gamma_out) return cudaSuccess;
     int b = (m + 255) / 256;
     if (precision == ALENS_MIXED) {
-        k_gamma_out<float><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->perm, ctx->sb32.gg[0], ctx->sb32.gg[1], gamma_out);
+        k_gamma_out<float><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->perm, ctx->sb32.gg[0], ctx->sb32.gg[1],
+                                                       ctx->scale64, gamma_out);
     } else {
-        k_gamma_out<double><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->perm, ctx->sb64.gg[0], ctx->sb64.gg[1], gamma_out);
+        k_gamma_out<double><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->perm, ctx->sb64.gg[0], ctx->sb64.gg[1],
+                                                        ctx->scale64, gamma_out);
     }
     ++ctx->launches;
     return cudaGetLastError();
