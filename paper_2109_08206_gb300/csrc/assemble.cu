@@ -195,15 +195,19 @@ __global__ void k_sort_segments(int n, const int* __restrict__ row, int* __restr
 
 // One rod's part of a constraint's diagonal entry D_c^T M D_c: e.M_t.e +
 // a.M_r.a for the normal e and the rod's arm cross normal a (Eq. blockdef
-// M with the rod's drag tensors; the signs of e and a do not matter).
-__device__ __forceinline__ double rod_quad(const double* e, const double* a, const double* quat, const Mob& mb)
+// M with the rod's drag tensors; the signs of e and a do not matter).  In
+// float32: the entry only sets the scaling, which needs to be positive and
+// consistent, not exact.
+template <typename T>
+__device__ __forceinline__ float rod_quad(const double* e, const double* a, const T* ax, int np, int r, float ip,
+                                          float ipa, float ir, float is)
 {
-    double p0, p1, p2;
-    quat_axis(quat[0], quat[1], quat[2], quat[3], p0, p1, p2);
-    const double pe = p0 * e[0] + p1 * e[1] + p2 * e[2], pa = p0 * a[0] + p1 * a[1] + p2 * a[2];
-    const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2], aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
-    return mb.inv_perp * ee + (mb.inv_par - mb.inv_perp) * (pe * pe) + mb.inv_rot * aa +
-           (mb.inv_spin - mb.inv_rot) * (pa * pa);
+    const float p0 = (float)ax[r], p1 = (float)ax[np + r], p2 = (float)ax[2 * (size_t)np + r];
+    const float e0 = (float)e[0], e1 = (float)e[1], e2 = (float)e[2];
+    const float a0 = (float)a[0], a1 = (float)a[1], a2 = (float)a[2];
+    const float pe = p0 * e0 + p1 * e1 + p2 * e2, pa = p0 * a0 + p1 * a1 + p2 * a2;
+    const float ee = e0 * e0 + e1 * e1 + e2 * e2, aa = a0 * a0 + a1 * a1 + a2 * a2;
+    return ip * ee + (ipa - ip) * (pe * pe) + ir * aa + (is - ir) * (pa * pa);
 }
 
 // Internal constraint cc (owner-major) <- caller constraint perm[cc].  When
@@ -211,9 +215,10 @@ __device__ __forceinline__ double rod_quad(const double* e, const double* a, con
 // e' = -e, (owner arm x e') = -(y_Q x e), (other arm x e') = -(y_P x e).
 // With beta > 0 the solver works on the diagonally scaled problem gamma =
 // sigma gamma~ (aLENS_set_scaling): the record and q are multiplied by
-// sigma_c = (D_c^T M D_c + C_c)^(-beta/2), the compliance by sigma_c^2 and
-// the starting gamma divided by sigma_c; sigma_c itself (float64) and
-// 1/sigma_c (working precision) are kept for the output and the residual.
+// sigma_c = (D_c^T M D_c + C_c)^(-beta/2) (evaluated in float32, so a
+// float value held exactly in float64), the compliance by sigma_c^2 and the
+// starting gamma divided by sigma_c; sigma_c and 1/sigma_c (working
+// precision) are kept for the output and the residual.
 template <typename T>
 __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const int32_t* __restrict__ pairs,
                              const int* __restrict__ rank, const double* __restrict__ dgeom,
@@ -221,9 +226,9 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
                              const int* __restrict__ rowQ, int* __restrict__ curQ, int* __restrict__ qlist,
                              int* __restrict__ ci, int* __restrict__ cj, T* __restrict__ rec, T* __restrict__ qT,
                              T* __restrict__ gg0, T* __restrict__ gg1, T* __restrict__ rec_lo, T* __restrict__ q_lo,
-                             const double* __restrict__ comp64, T* __restrict__ compT, const double* __restrict__ quat,
-                             Mob mob0, const SysGeo* __restrict__ systab, const int* __restrict__ sysid, double beta,
-                             double* __restrict__ scale64, T* __restrict__ isc)
+                             const double* __restrict__ comp64, T* __restrict__ compT, int np, const T* __restrict__ ax,
+                             const T* __restrict__ mobr, Mob mob0, double beta, double* __restrict__ scale64,
+                             T* __restrict__ isc)
 {
     int cc = blockIdx.x * blockDim.x + threadIdx.x;
     if (cc >= m) return;
@@ -248,15 +253,21 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
     }
     double cmp = comp64 ? comp64[c] : -1.0;
     double sig = 1.0;
-    if (beta > 0.0 && quat) {
-        const int i = pairs[3 * (size_t)c], j = pairs[3 * (size_t)c + 1];
-        const int io = flip ? j : i, iq = flip ? i : j;   // caller indices (iq < 0: a wall)
-        double a = rod_quad(r, r + 3, quat + 4 * (size_t)io, systab ? systab[sysid[io]].mob : mob0);
-        if (iq >= 0) a += rod_quad(r, r + 6, quat + 4 * (size_t)iq, systab ? systab[sysid[iq]].mob : mob0);
-        if (cmp >= 0.0) a += cmp;
-        if (a > 0.0 && isfinite(a)) {
-            const double s2 = pow(a, -beta);
-            if (s2 > 0.0 && isfinite(s2)) sig = sqrt(s2);
+    if (beta > 0.0) {
+        // the rods' axes and drags in rank order (written just before)
+        auto part = [&](const double* arm, int rr) {
+            if (mobr)
+                return rod_quad(r, arm, ax, np, rr, (float)mobr[rr], (float)mobr[np + rr], (float)mobr[2 * (size_t)np + rr],
+                                (float)mobr[3 * (size_t)np + rr]);
+            return rod_quad(r, arm, ax, np, rr, (float)mob0.inv_perp, (float)mob0.inv_par, (float)mob0.inv_rot,
+                            (float)mob0.inv_spin);
+        };
+        float a = part(r + 3, ro);
+        if (rq >= 0) a += part(r + 6, rq);   // rq < 0: a wall
+        if (cmp >= 0.0) a += (float)cmp;
+        if (a > 0.0f && isfinite(a)) {
+            const float sf = exp2f(-0.5f * (float)beta * log2f(a));
+            if (sf > 0.0f && isfinite(sf)) sig = (double)sf;
         }
     }
     scale64[cc] = sig;
@@ -446,8 +457,9 @@ static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     if (m <= 0) return cudaGetLastError();
     k_setup_fill<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->perm, pairs, rank, dgeom, q, gamma_in, ctx->rowQ,
                                                   ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0], sb.gg[1],
-                                                  sb.rec_lo, sb.q_lo, ctx->cur_comp, sb.comp, quat, ctx->mob,
-                                                  ctx->cur_systab, ctx->cur_sysid, ctx->scale_beta, ctx->scale64, sb.isc);
+                                                  sb.rec_lo, sb.q_lo, ctx->cur_comp, sb.comp, np, sb.ax,
+                                                  ctx->cur_systab ? sb.mobr : (const T*)nullptr, ctx->mob, ctx->scale_beta,
+                                                  ctx->scale64, sb.isc);
     ++ctx->launches;
     k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
     ++ctx->launches;

@@ -860,7 +860,13 @@ aLENS_status aLENS_step_adjoint(aLENS_ctx* c, int64_t n, const double* x, const 
     if ((st = read_status(c)) != ALENS_OK) return st;
     if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
     CK(launch_assemble(c, (int)n, m, pairs, c->phi, c->dgeom, c->q64));
-    CK(launch_solve_setup(c, (int)n, m, pairs, c->dgeom, c->q64, gamma, quat, c->p.precision, nullptr));
+    // the adjoint's operator reads the solver's records as D itself: set
+    // them up unscaled
+    const double beta = c->scale_beta;
+    c->scale_beta = 0.0;
+    const cudaError_t se = launch_solve_setup(c, (int)n, m, pairs, c->dgeom, c->q64, gamma, quat, c->p.precision, nullptr);
+    c->scale_beta = beta;
+    CK(se);
     int iters = 0;
     double rel = 0.0;
     CK(launch_adjoint(c, (int)n, m, quat, f_nc, pairs, gamma, dL_dx_new, dL_dquat_new, dL_dx, dL_dquat, dL_dfnc,

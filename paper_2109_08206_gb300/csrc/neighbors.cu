@@ -183,8 +183,10 @@ __device__ __forceinline__ void decode_cell(uint32_t key, int bits, int cc[3])
 }
 
 // One warp per rod i (rods taken in cell order for locality of the candidate
-// loads).  Lanes stride over the rods of the 27 neighbour cells (each cell
-// visited with the periodic image shift that brings it next to i's cell);
+// loads).  Lanes 0-26 fetch the rod ranges of the 27 neighbour cells at once
+// (each cell with the periodic image shift that brings it next to i's cell);
+// the warp then walks the concatenated candidates in full chunks of 32, each
+// lane finding its cell by a binary search over the prefix of the counts;
 // candidates j > i that pass the float32 screen are appended to a per-warp
 // list in shared memory with a warp ballot, sorted there by (j, image) with a
 // bitonic network, and written to the candidate buffer as 64-bit keys
@@ -210,9 +212,12 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
     const uint32_t key_base = systab ? (uint32_t)systab[sysid[i]].key_base : 0u;
     int cc[3];
     decode_cell(cellkey[i] - key_base, g.bits, cc);
-    int cnt = 0;
-    for (int o = 0; o < 27; ++o) {
-        int d[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+    // the 27 neighbour cells, one per lane: each with the periodic image
+    // shift that brings it next to i's cell, its rod range and its image code
+    int cbeg = 0, ccnt = 0;
+    uint32_t ccode = 0;
+    if (lane < 27) {
+        const int d[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
         int c[3], sh[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -221,26 +226,53 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
             if (c[a] < 0) { c[a] += g.nc[a]; sh[a] = -1; }
             else if (c[a] >= g.nc[a]) { c[a] -= g.nc[a]; sh[a] = 1; }
         }
-        const uint32_t code = (uint32_t)((sh[0] + 1) + 3 * (sh[1] + 1) + 9 * (sh[2] + 1));
+        ccode = (uint32_t)((sh[0] + 1) + 3 * (sh[1] + 1) + 9 * (sh[2] + 1));
         const uint32_t key = key_base + morton3(c[0], c[1], c[2]);
-        const int beg = cell_start[key], end = cell_start[key + 1];
-        const float sx = (float)sh[0] * g.boxf[0], sy = (float)sh[1] * g.boxf[1], sz = (float)sh[2] * g.boxf[2];
-        for (int base = beg; base < end; base += 32) {
-            int m = base + lane;
-            bool keep = false;
-            int j = 0;
-            if (m < end) {
-                j = sorted_id[m];
-                keep = j > i && screen32(pi, ai, spos32[m], sax32[m], sx, sy, sz, g);
-                if (COUNT_ONLY && keep) keep = decide64(i, j, sh[0], sh[1], sh[2], np, xw, axis, g);
-            }
-            unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (!COUNT_ONLY && keep) {
-                int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-                if (pos < kPairsPerRodCap) L[pos] = ((uint32_t)j << 5) | code;
-            }
-            cnt += __popc(bal);
+        cbeg = cell_start[key];
+        ccnt = cell_start[key + 1] - cbeg;
+    }
+    // inclusive prefix of the cells' counts: candidate t lies in the cell o
+    // with incl[o - 1] <= t < incl[o]
+    int incl = ccnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int cnt = 0;
+    // the candidates of all 27 cells in full chunks of 32 lanes
+    for (int base = 0; base < total; base += 32) {
+        const int t = base + lane;
+        int lo = 0, hi = 26;   // smallest o with incl[o] > t
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+            const int mid = (lo + hi) >> 1;
+            const int im = __shfl_sync(0xffffffffu, incl, mid);
+            if (im > t) hi = mid;
+            else lo = mid + 1;
         }
+        const int o = lo < 26 ? lo : 26;
+        const int ob = __shfl_sync(0xffffffffu, cbeg, o);
+        const int oc = __shfl_sync(0xffffffffu, ccnt, o);
+        const int oi = __shfl_sync(0xffffffffu, incl, o);
+        const uint32_t code = __shfl_sync(0xffffffffu, ccode, o);
+        bool keep = false;
+        int j = 0;
+        if (t < total) {
+            const int m = ob + (t - (oi - oc));
+            const int s0 = (int)(code % 3u) - 1, s1 = (int)((code / 3u) % 3u) - 1, s2 = (int)(code / 9u) - 1;
+            j = sorted_id[m];
+            keep = j > i && screen32(pi, ai, spos32[m], sax32[m], (float)s0 * g.boxf[0], (float)s1 * g.boxf[1],
+                                     (float)s2 * g.boxf[2], g);
+            if (COUNT_ONLY && keep) keep = decide64(i, j, s0, s1, s2, np, xw, axis, g);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (!COUNT_ONLY && keep) {
+            const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+            if (pos < kPairsPerRodCap) L[pos] = ((uint32_t)j << 5) | code;
+        }
+        cnt += __popc(bal);
     }
     if (COUNT_ONLY) {
         if (lane == 0) atomicAdd(&counters[C_PAIRS], (unsigned long long)cnt);
