@@ -318,7 +318,9 @@ ALENS_API aLENS_status aLENS_step_batch(aLENS_ctx* ctx, int32_t n_systems, const
  * mode), everything else in float64.  info: iters = CG iterations,
  * residual = final relative CG residual |r|/|b_A| (tolerance 1e-13 in
  * FP64, 1e-7 mixed; NOT_CONVERGED with the outputs filled if max_iter CG
- * iterations did not reach it).  The first call allocates the adjoint's
+ * iterations did not reach it).  The CG loop is one persistent cooperative
+ * kernel with bounded grid-wide waits: TIMEOUT when one runs out (see
+ * aLENS_set_wait_limit).  The first call allocates the adjoint's
  * workspace (46 doubles per rod and 13 per constraint of the context's capacity).
  * Single systems only (batches: call it per system). */
 ALENS_API aLENS_status aLENS_step_adjoint(aLENS_ctx* ctx, int64_t n, const double* x, const double* quat,

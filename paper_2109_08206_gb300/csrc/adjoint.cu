@@ -25,11 +25,13 @@
 //
 // Everything runs in float64 except the CG operator, which uses the
 // solver's records in its working precision (float32 in mixed mode).  The
-// CG loop is a fixed sequence of three kernels per iteration (rod gather,
-// constraint apply + step length, update + direction coefficient); the
-// scalar reductions finish in the last block to arrive (fixed order, so
-// the result is deterministic), and every kernel is a no-op once the
-// converged flag is set.
+// CG loop is one persistent cooperative kernel, one block per SM: per
+// iteration a rod pass (F = D_A p, Up = M F), a grid barrier, a constraint
+// pass (Ap and p.Ap), a grid-wide sum, the update, and a second grid-wide
+// sum; every block sums the per-block partials in block order, so all take
+// the same step lengths and the result is deterministic.  The setup and
+// the passes before and after the loop are ordinary kernels whose scalar
+// reductions finish in the last block to arrive.
 #include <float.h>
 
 #include "internal.cuh"
@@ -237,98 +239,177 @@ __global__ void k_adj_b(int m, const int32_t* __restrict__ pairs, const double* 
     }
 }
 
-// CG rod pass: the direction p_new = r + beta p (formed where it is read),
-// F = D_A p_new, Up = M F, in the working precision.
+// Arguments of the persistent CG.
 template <typename T>
-__global__ void k_cg_rod(int n, int np, int mp, const int* __restrict__ rowP, const int* __restrict__ rowQ,
-                         const int* __restrict__ qlist, const T* __restrict__ rec, const T* __restrict__ qe,
-                         const T* __restrict__ ax, T inv_perp, T inv_par, T inv_rot, T inv_spin,
-                         const double* __restrict__ gamma, const double* __restrict__ r,
-                         const double* __restrict__ pv, const double* scal, const int* iflag, T* __restrict__ Up)
+struct CgArgs {
+    int n, m, np, mp;
+    const int* __restrict__ rowP;
+    const int* __restrict__ rowQ;
+    const int* __restrict__ qlist;
+    const int* __restrict__ ci;
+    const int* __restrict__ cj;
+    const T* __restrict__ rec;
+    const T* __restrict__ qe;
+    const T* __restrict__ ax;
+    T inv_perp, inv_par, inv_rot, inv_spin;
+    const double* __restrict__ gamma;   // the active set: gamma_c > 0
+    double* lam;
+    double* r;
+    double* pv;
+    double* Ap;
+    T* Up;               // [n][6] rod velocities of the direction
+    double* partials;    // [2][gridDim.x]: the two sums of an iteration
+    unsigned* bar;       // monotone grid-barrier counter
+    int* flags;          // device status: ALENS_ERR_TIMEOUT when a wait runs out
+    double* scal;
+    int* iflag;
+    long long wait_cycles;
+};
+
+// Sum of v over the grid, the same value in every block: block sums into
+// part[blockIdx.x], a grid barrier, then warp 0 of every block adds the
+// partials in block order (lanes strided, then a fixed shuffle tree).
+__device__ __forceinline__ bool grid_sum(double v, double* part, unsigned* bar, unsigned& epoch, int* flags,
+                                         long long wait_cycles, double* red, int* s_ok, double* bc, double& out)
 {
-    if (iflag[I_DONE]) return;
-    const double beta = scal[S_BETA];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    for (int c = rowP[i]; c < rowP[i + 1]; ++c) {
-        if (!(gamma[c] > 0.0)) continue;
-        const T v = (T)(r[c] + beta * pv[c]);
+    const double s = block_sum(v, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (!grid_barrier(bar, ++epoch * gridDim.x, flags, wait_cycles, s_ok)) return false;
+    if (threadIdx.x < 32) {
+        double acc = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) acc += __ldcg(&part[b]);
 #pragma unroll
-        for (int w = 0; w < 6; ++w) F[w] += v * rec[w * (size_t)mp + c];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) *bc = acc;
     }
-    for (int k = rowQ[i]; k < rowQ[i + 1]; ++k) {
-        const int c = qlist[k];
-        if (!(gamma[c] > 0.0)) continue;
-        const T v = (T)(r[c] + beta * pv[c]);
-        const T* q8 = qe + 8 * (size_t)k;
-#pragma unroll
-        for (int w = 0; w < 6; ++w) F[w] -= v * q8[w];
-    }
-    const T p0 = ax[i], p1 = ax[np + i], p2 = ax[2 * (size_t)np + i];
-    const T pf = p0 * F[0] + p1 * F[1] + p2 * F[2], pt = p0 * F[3] + p1 * F[4] + p2 * F[5];
-    const T cf = pf * (inv_par - inv_perp), ct = pt * (inv_spin - inv_rot);
-    T* o = Up + 6 * (size_t)i;
-    o[0] = F[0] * inv_perp + p0 * cf; o[1] = F[1] * inv_perp + p1 * cf; o[2] = F[2] * inv_perp + p2 * cf;
-    o[3] = F[3] * inv_rot + p0 * ct; o[4] = F[4] * inv_rot + p1 * ct; o[5] = F[5] * inv_rot + p2 * ct;
+    __syncthreads();
+    out = *bc;
+    return true;
 }
 
-// CG constraint pass: Ap = (D^T Up)_A, p.Ap; the last block sets alpha.
+// CG on A_AA lambda_A = b_A from the state k_adj_b left (lambda = 0, r =
+// b_A, p = 0, r.r and the stopping bound in scal).  Block b takes a
+// contiguous share of the rods (kCgLanes lanes per rod, each over every
+// kCgLanes-th entry of the rod's lists, the force summed over the lanes by
+// shuffles) and of the constraints (a thread each).  An iteration:
+//   rod pass:   p_new = r + beta p (formed where it is read), F = D_A p_new,
+//               Up = M F (working precision);
+//   constraint: Ap = (D^T Up)_A and p_new.Ap -> alpha = r.r / p.Ap;
+//   update:     p = p_new, lambda += alpha p, r -= alpha Ap, and r.r ->
+//               beta = r.r / previous r.r.
+// Stops when r.r <= tol^2 r0.r0, alpha <= 0 or after max_iter iterations.
+// The two sums alternate between two partials buffers: a grid barrier
+// separates every rewrite of a buffer from the reads of its last use.
+constexpr int kCgLanes = 8;
+
 template <typename T>
-__global__ void k_cg_con(int m, int mp, const int* __restrict__ ci, const int* __restrict__ cj,
-                         const T* __restrict__ rec, const double* __restrict__ gamma, const double* __restrict__ r,
-                         const double* __restrict__ pv, const T* __restrict__ Up, double* __restrict__ Ap,
-                         double* __restrict__ partials, unsigned* counter, double* scal, const int* iflag)
+__global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
 {
-    if (iflag[I_DONE]) return;
-    const double beta = scal[S_BETA];
-    double acc = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
-        double a = 0.0;
-        if (gamma[c] > 0.0) {
-            const T* ui = Up + 6 * (size_t)ci[c];
-            const T* uj = Up + 6 * (size_t)cj[c];
-            T s = T(0);
+    __shared__ double red[32];
+    __shared__ double bc;
+    __shared__ int s_ok;
+    if (a.iflag[I_DONE]) return;   // written by k_adj_b before the launch: uniform
+    const size_t mp = a.mp, np = a.np;
+    const int r0 = (int)((long long)a.n * blockIdx.x / gridDim.x);
+    const int r1 = (int)((long long)a.n * (blockIdx.x + 1) / gridDim.x);
+    const int c0 = (int)((long long)a.m * blockIdx.x / gridDim.x);
+    const int c1 = (int)((long long)a.m * (blockIdx.x + 1) / gridDim.x);
+    const int sub = threadIdx.x & (kCgLanes - 1);
+    constexpr int kRodsPerWarp = 32 / kCgLanes;
+    double rr = a.scal[S_RR];
+    const double tol2 = a.scal[S_TOL2];
+    const int maxit = a.iflag[I_MAXIT];
+    double beta = 0.0, alpha = 0.0;
+    unsigned epoch = 0;
+    int it = 0;
+    while (it < maxit) {
+        // the loop runs while the warp's first rod is in range (uniform per warp:
+        // every lane takes part in the shuffles)
+        for (int base = r0 + (int)(threadIdx.x >> 5) * kRodsPerWarp; base < r1;
+             base += (int)(blockDim.x >> 5) * kRodsPerWarp) {
+            const int i = base + (int)((threadIdx.x & 31) / kCgLanes);
+            T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+            if (i < r1) {
+                // every load of an entry is issued before the active-set test
+                // (an inactive entry contributes 0)
+                for (int c = a.rowP[i] + sub; c < a.rowP[i + 1]; c += kCgLanes) {
+                    const double g = a.gamma[c], rc = a.r[c], pc = a.pv[c];
+                    T rv[6];
 #pragma unroll
-            for (int w = 0; w < 3; ++w)
-                s += rec[w * (size_t)mp + c] * (ui[w] - uj[w]) + rec[(3 + w) * (size_t)mp + c] * ui[3 + w] -
-                     rec[(6 + w) * (size_t)mp + c] * uj[3 + w];
-            a = (double)s;
-            acc += (r[c] + beta * pv[c]) * a;
+                    for (int w = 0; w < 6; ++w) rv[w] = a.rec[w * mp + c];
+                    const T v = g > 0.0 ? (T)(rc + beta * pc) : T(0);
+#pragma unroll
+                    for (int w = 0; w < 6; ++w) F[w] += v * rv[w];
+                }
+                for (int k = a.rowQ[i] + sub; k < a.rowQ[i + 1]; k += kCgLanes) {
+                    const int c = a.qlist[k];
+                    const T* q8 = a.qe + 8 * (size_t)k;
+                    T qv[6];
+#pragma unroll
+                    for (int w = 0; w < 6; ++w) qv[w] = q8[w];
+                    const double g = a.gamma[c], rc = a.r[c], pc = a.pv[c];
+                    const T v = g > 0.0 ? (T)(rc + beta * pc) : T(0);
+#pragma unroll
+                    for (int w = 0; w < 6; ++w) F[w] -= v * qv[w];
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < kCgLanes; o <<= 1) {
+#pragma unroll
+                for (int w = 0; w < 6; ++w) F[w] += __shfl_xor_sync(0xffffffffu, F[w], o);
+            }
+            if (sub != 0 || i >= r1) continue;
+            const T p0 = a.ax[i], p1 = a.ax[np + i], p2 = a.ax[2 * np + i];
+            const T pf = p0 * F[0] + p1 * F[1] + p2 * F[2], pt = p0 * F[3] + p1 * F[4] + p2 * F[5];
+            const T cf = pf * (a.inv_par - a.inv_perp), ct = pt * (a.inv_spin - a.inv_rot);
+            T* o = a.Up + 6 * (size_t)i;
+            o[0] = F[0] * a.inv_perp + p0 * cf; o[1] = F[1] * a.inv_perp + p1 * cf; o[2] = F[2] * a.inv_perp + p2 * cf;
+            o[3] = F[3] * a.inv_rot + p0 * ct; o[4] = F[4] * a.inv_rot + p1 * ct; o[5] = F[5] * a.inv_rot + p2 * ct;
         }
-        Ap[c] = a;
+        if (!grid_barrier(a.bar, ++epoch * gridDim.x, a.flags, a.wait_cycles, &s_ok)) return;
+        double acc = 0.0;
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            double ap = 0.0;
+            if (a.gamma[c] > 0.0) {
+                const T* ui = a.Up + 6 * (size_t)a.ci[c];
+                const T* uj = a.Up + 6 * (size_t)a.cj[c];
+                T s = T(0);
+#pragma unroll
+                for (int w = 0; w < 3; ++w)
+                    s += a.rec[w * mp + c] * (ui[w] - uj[w]) + a.rec[(3 + w) * mp + c] * ui[3 + w] -
+                         a.rec[(6 + w) * mp + c] * uj[3 + w];
+                ap = (double)s;
+                acc += (a.r[c] + beta * a.pv[c]) * ap;
+            }
+            a.Ap[c] = ap;
+        }
+        double pap;
+        if (!grid_sum(acc, a.partials, a.bar, epoch, a.flags, a.wait_cycles, red, &s_ok, &bc, pap)) return;
+        alpha = pap > 0.0 ? rr / pap : 0.0;
+        double acc2 = 0.0;
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            if (!(a.gamma[c] > 0.0)) continue;
+            const double pn = a.r[c] + beta * a.pv[c];
+            const double rn = a.r[c] - alpha * a.Ap[c];
+            a.lam[c] += alpha * pn;
+            a.pv[c] = pn;
+            a.r[c] = rn;
+            acc2 += rn * rn;
+        }
+        double rrn;
+        if (!grid_sum(acc2, a.partials + gridDim.x, a.bar, epoch, a.flags, a.wait_cycles, red, &s_ok, &bc, rrn))
+            return;
+        beta = rr > 0.0 ? rrn / rr : 0.0;
+        rr = rrn;
+        ++it;
+        if (!(rr > tol2) || !(alpha > 0.0)) break;
     }
-    double tot;
-    if (last_block_total(acc, partials, counter, &tot) && threadIdx.x == 0)
-        scal[S_ALPHA] = tot > 0.0 ? scal[S_RR] / tot : 0.0;
-}
-
-// CG update: p = r + beta p, lambda += alpha p, r -= alpha Ap; the last block
-// sets beta = r.r / previous r.r, counts the iteration and tests convergence.
-__global__ void k_cg_upd(int m, const double* __restrict__ gamma, double* __restrict__ lam, double* __restrict__ r,
-                         double* __restrict__ pv, const double* __restrict__ Ap, double* __restrict__ partials,
-                         unsigned* counter, double* scal, int* iflag)
-{
-    if (iflag[I_DONE]) return;
-    const double beta = scal[S_BETA], alpha = scal[S_ALPHA];
-    double acc = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
-        if (!(gamma[c] > 0.0)) continue;
-        const double pn = r[c] + beta * pv[c];
-        const double rn = r[c] - alpha * Ap[c];
-        lam[c] += alpha * pn;
-        pv[c] = pn;
-        r[c] = rn;
-        acc += rn * rn;
-    }
-    double tot;
-    if (last_block_total(acc, partials, counter, &tot) && threadIdx.x == 0) {
-        const double rr = scal[S_RR];
-        scal[S_BETA] = rr > 0.0 ? tot / rr : 0.0;
-        scal[S_RR] = tot;
-        const int it = iflag[I_ITERS] + 1;
-        iflag[I_ITERS] = it;
-        if (!(tot > scal[S_TOL2]) || it >= iflag[I_MAXIT] || !(scal[S_ALPHA] > 0.0)) iflag[I_DONE] = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.scal[S_RR] = rr;
+        a.scal[S_ALPHA] = alpha;
+        a.scal[S_BETA] = beta;
+        a.iflag[I_ITERS] = it;
+        a.iflag[I_DONE] = 1;
     }
 }
 
@@ -607,35 +688,35 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
         k_adj_b<<<G, 256, 0, st>>>(m, pairs, ctx->dgeom, gamma, Mu, lam, r, pv, ctx->partials, counter, scal, iflag,
                                    tol);
         ++ctx->launches;
-        int hflag[I_NI];
-        for (int done = 0; !done;) {
-            for (int k = 0; k < 32; ++k) {
-                if (mixed) {
-                    const SolveBufs<float>& sb = ctx->sb32;
-                    k_cg_rod<float><<<nblk(n, 128), 128, 0, st>>>(
-                        n, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, sb.rec, sb.qe, sb.ax,
-                        (float)ctx->mob.inv_perp, (float)ctx->mob.inv_par, (float)ctx->mob.inv_rot,
-                        (float)ctx->mob.inv_spin, gamma, r, pv, scal, iflag, (float*)Upd);
-                    k_cg_con<float><<<G, 256, 0, st>>>(m, (int)mp, ctx->ci, ctx->cj, sb.rec, gamma, r, pv,
-                                                       (const float*)Upd, Ap, ctx->partials, counter, scal, iflag);
-                } else {
-                    const SolveBufs<double>& sb = ctx->sb64;
-                    k_cg_rod<double><<<nblk(n, 128), 128, 0, st>>>(
-                        n, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, sb.rec, sb.qe, sb.ax,
-                        ctx->mob.inv_perp, ctx->mob.inv_par, ctx->mob.inv_rot, ctx->mob.inv_spin, gamma, r, pv, scal,
-                        iflag, Upd);
-                    k_cg_con<double><<<G, 256, 0, st>>>(m, (int)mp, ctx->ci, ctx->cj, sb.rec, gamma, r, pv, Upd, Ap,
-                                                        ctx->partials, counter, scal, iflag);
-                }
-                k_cg_upd<<<G, 256, 0, st>>>(m, gamma, lam, r, pv, Ap, ctx->partials, counter, scal, iflag);
-                ctx->launches += 3;
-            }
-            if ((e = cudaMemcpyAsync(hflag, iflag, sizeof(hflag), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        // the persistent CG: one block per SM (cooperative launch)
+        const void* fn = mixed ? (const void*)k_cg<float> : (const void*)k_cg<double>;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 1024, 0)) != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+        const long long wait = (long long)(ctx->wait_s * ctx->clock_khz * 1e3);
+        if (mixed) {
+            const SolveBufs<float>& sb = ctx->sb32;
+            CgArgs<float> ca{n, m, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.qe,
+                             sb.ax, (float)ctx->mob.inv_perp, (float)ctx->mob.inv_par, (float)ctx->mob.inv_rot,
+                             (float)ctx->mob.inv_spin, gamma, lam, r, pv, Ap, (float*)Upd, ctx->partials,
+                             ctx->bar + 2, ctx->dflags, scal, iflag, wait};
+            void* args[] = {&ca};
+            if ((e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(1024), args, 0, st)) != cudaSuccess)
                 return e;
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            done = hflag[I_DONE];
+        } else {
+            const SolveBufs<double>& sb = ctx->sb64;
+            CgArgs<double> ca{n, m, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec,
+                              sb.qe, sb.ax, ctx->mob.inv_perp, ctx->mob.inv_par, ctx->mob.inv_rot, ctx->mob.inv_spin,
+                              gamma, lam, r, pv, Ap, Upd, ctx->partials, ctx->bar + 2, ctx->dflags, scal, iflag, wait};
+            void* args[] = {&ca};
+            if ((e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(1024), args, 0, st)) != cudaSuccess)
+                return e;
         }
+        ++ctx->launches;
+        int hflag[I_NI];
+        if ((e = cudaMemcpyAsync(hflag, iflag, sizeof(hflag), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return e;
         iters = hflag[I_ITERS];
         double hs[S_NSCAL];
         if ((e = cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

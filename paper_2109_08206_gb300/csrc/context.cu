@@ -872,6 +872,7 @@ aLENS_status aLENS_step_adjoint(aLENS_ctx* c, int64_t n, const double* x, const 
     CK(launch_adjoint(c, (int)n, m, quat, f_nc, pairs, gamma, dL_dx_new, dL_dquat_new, dL_dx, dL_dquat, dL_dfnc,
                       &iters, &rel, dL_deta));
     if ((st = read_status(c)) != ALENS_OK) return st;
+    if (c->hflags[F_SOLVE_ERR] != 0) return (aLENS_status)c->hflags[F_SOLVE_ERR];   // a CG grid wait ran out
     if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
     const double tol = c->p.precision == ALENS_MIXED ? 1e-7 : 1e-13;
     st = (m > 0 && !(rel <= tol)) ? ALENS_ERR_NOT_CONVERGED : ALENS_OK;

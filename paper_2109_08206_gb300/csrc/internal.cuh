@@ -173,6 +173,43 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p)
     return *(const volatile int*)p;
 }
 
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded grid barrier on a monotone arrival counter: block b's k-th arrival
+// waits until the counter reaches k * gridDim.x.  Arrival is a release
+// reduction and the wait an acquire poll by thread 0, whose verdict the
+// block reads from shared memory.  The wait gives up after wait_cycles clock
+// cycles or 2^28 polls, records ALENS_ERR_TIMEOUT and returns false; it also
+// returns false as soon as any block has recorded an error, so every block
+// leaves.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* flags, long long wait_cycles,
+                                             int* s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        red_release_add(count, 1u);
+        long long t0 = clock64();
+        int ok = 1;
+        for (unsigned polls = 0;; ++polls) {
+            unsigned v = ld_acquire_u32(count);
+            if ((int)(v - target) >= 0) break;
+            if (ld_volatile_i32(&flags[F_SOLVE_ERR]) != 0) { ok = 0; break; }
+            if (clock64() - t0 > wait_cycles || polls > (1u << 28)) {
+                atomicCAS(&flags[F_SOLVE_ERR], 0, ALENS_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        if (ok && ld_volatile_i32(&flags[F_SOLVE_ERR]) != 0) ok = 0;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
 // ------------------------------------------------------------- context
 
 template <typename T>

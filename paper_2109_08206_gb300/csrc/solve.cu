@@ -114,11 +114,6 @@ __device__ __forceinline__ void st_u6(T* U, int i, const T u[6])
     p[0] = a; p[1] = b; p[2] = c;
 }
 
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
-{
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Constraint state (delta, g, gamma_ref, gamma_lo) of constraint c in a
 // [m][4] buffer: one vector load (float32) or two (float64).  The iterate
 // is gamma = gamma_ref + gamma_lo + delta: in float32 (gamma_ref, gamma_lo)
@@ -701,38 +696,6 @@ __device__ __forceinline__ void block_partial(T v[4], T (*red)[4], T* dst, int s
             for (int u = 0; u < 4; ++u) dst[u * stride] = w[u];
         }
     }
-}
-
-// Bounded grid barrier on a monotone arrival counter: block b's k-th arrival
-// waits until the counter reaches k * gridDim.x.  Arrival is a release
-// reduction and the wait an acquire poll by thread 0, whose verdict the
-// block reads from shared memory.  The wait gives up after wait_cycles clock
-// cycles or 2^28 polls, records ALENS_ERR_TIMEOUT and returns false; it also
-// returns false as soon as any block has recorded an error, so every block
-// leaves.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* flags, long long wait_cycles,
-                                             int* s_ok)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        red_release_add(count, 1u);
-        long long t0 = clock64();
-        int ok = 1;
-        for (unsigned polls = 0;; ++polls) {
-            unsigned v = ld_acquire_u32(count);
-            if ((int)(v - target) >= 0) break;
-            if (ld_volatile_i32(&flags[F_SOLVE_ERR]) != 0) { ok = 0; break; }
-            if (clock64() - t0 > wait_cycles || polls > (1u << 28)) {
-                atomicCAS(&flags[F_SOLVE_ERR], 0, ALENS_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-        }
-        if (ok && ld_volatile_i32(&flags[F_SOLVE_ERR]) != 0) ok = 0;
-        *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
 }
 
 // After a barrier: warps 0-3 each reduce one component of the per-block
