@@ -88,29 +88,50 @@ __global__ void k_cell_scatter(int n, const uint32_t* __restrict__ cellkey, cons
 
 // Rods of each cell in ascending id, so that the cell-sorted order (which the
 // solver also uses to number rods) does not depend on the atomics above.
-__global__ void k_cell_sort_ids(int nkeys, const int* __restrict__ cell_start, int* __restrict__ sorted_id)
+// One warp per cell: the cell's ids (distinct) are staged in shared memory
+// and each goes to its rank, the count of smaller ids in the cell.  A cell
+// longer than kSortCap (none in the benchmark workloads) is sorted in place
+// by lane 0.
+constexpr int kSortCap = 256;
+constexpr int kSortWarps = 4;
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_cell_sort_ids(int nkeys, const int* __restrict__ cell_start, int* __restrict__ sorted_id)
 {
-    constexpr int kLocal = 64;
-    int key = blockIdx.x * blockDim.x + threadIdx.x;
-    if (key >= nkeys) return;
-    const int b = cell_start[key], e = cell_start[key + 1];
-    if (e - b <= kLocal) {
-        int v[kLocal];
-        const int len = e - b;
-        for (int u = 0; u < len; ++u) v[u] = sorted_id[b + u];
-        for (int u = 1; u < len; ++u) {
-            int x = v[u], w = u - 1;
-            while (w >= 0 && v[w] > x) { v[w + 1] = v[w]; --w; }
-            v[w + 1] = x;
+    __shared__ int buf[kSortWarps][kSortCap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int key = blockIdx.x * kSortWarps + warp;
+    if (key >= nkeys) return;   // uniform per warp
+    const int b = cell_start[key], e = cell_start[key + 1], len = e - b;
+    if (len <= 1) return;
+    if (len > kSortCap) {
+        if (lane == 0) {
+            for (int u = b + 1; u < e; ++u) {
+                int x = sorted_id[u], w = u - 1;
+                while (w >= b && sorted_id[w] > x) { sorted_id[w + 1] = sorted_id[w]; --w; }
+                sorted_id[w + 1] = x;
+            }
         }
-        for (int u = 0; u < len; ++u) sorted_id[b + u] = v[u];
-    } else {
-        for (int u = b + 1; u < e; ++u) {
-            int x = sorted_id[u], w = u - 1;
-            while (w >= b && sorted_id[w] > x) { sorted_id[w + 1] = sorted_id[w]; --w; }
-            sorted_id[w + 1] = x;
+        return;
+    }
+    int* sv = buf[warp];
+    for (int u = lane; u < len; u += 32) sv[u] = sorted_id[b + u];
+    __syncwarp();
+    int rk[kSortCap / 32], xv[kSortCap / 32];
+#pragma unroll
+    for (int q = 0; q < kSortCap / 32; ++q) {
+        const int u = lane + 32 * q;
+        rk[q] = -1;
+        if (u < len) {
+            const int x = sv[u];
+            int r = 0;
+            for (int t = 0; t < len; ++t) r += sv[t] < x;
+            rk[q] = r;
+            xv[q] = x;
         }
     }
+#pragma unroll
+    for (int q = 0; q < kSortCap / 32; ++q)
+        if (rk[q] >= 0) sorted_id[b + rk[q]] = xv[q];
 }
 
 __global__ void k_cell_gather(int n, const int* __restrict__ sorted_id, const float4* __restrict__ pos32,
@@ -384,7 +405,8 @@ cudaError_t launch_cell_sort(aLENS_ctx* ctx, int n)
         k_cell_scatter<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, ctx->cellkey, ctx->cell_start, ctx->cell_cursor,
                                                               ctx->sorted_id);
         ++ctx->launches;
-        k_cell_sort_ids<<<nblk(nkeys, 128), 128, 0, ctx->stream>>>(nkeys, ctx->cell_start, ctx->sorted_id);
+        k_cell_sort_ids<<<nblk(nkeys, kSortWarps), kSortWarps * 32, 0, ctx->stream>>>(nkeys, ctx->cell_start,
+                                                                                       ctx->sorted_id);
         ++ctx->launches;
         k_cell_gather<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, ctx->sorted_id, ctx->pos32, ctx->ax32, ctx->spos32,
                                                              ctx->sax32);
