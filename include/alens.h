@@ -354,10 +354,11 @@ ALENS_API aLENS_status aLENS_set_wait_limit(aLENS_ctx* ctx, double seconds);
  * unscaled iteration, 1 Jacobi scaling; default 0.5.  INVALID otherwise. */
 ALENS_API aLENS_status aLENS_set_scaling(aLENS_ctx* ctx, double beta);
 
-/* Test hook: mode 1 makes one thread block of the next solver launch leave
- * before its first grid-wide arrival, so that the other blocks' bounded
- * waits run out and the call returns ALENS_ERR_TIMEOUT.  The hook clears
- * itself after one launch.  mode 0 disables it. */
+/* Test hook: mode 1 makes one thread block of the next solver launch (the
+ * BBPGD of a step or solve, or the CG of aLENS_step_adjoint) leave before
+ * its first grid-wide arrival, so that the other blocks' bounded waits run
+ * out and the call returns ALENS_ERR_TIMEOUT.  The hook clears itself after
+ * one launch.  mode 0 disables it. */
 ALENS_API aLENS_status aLENS_inject_fault(aLENS_ctx* ctx, int32_t mode);
 
 /* Launch shape of the solver kernel: threads per block (multiple of 32,

@@ -264,6 +264,7 @@ struct CgArgs {
     double* scal;
     int* iflag;
     long long wait_cycles;
+    int fault;           // test hook (aLENS_inject_fault): 1 = block 0 leaves before its first arrival
 };
 
 // Sum of v over the grid, the same value in every block: block sums into
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
     __shared__ double bc;
     __shared__ int s_ok;
     if (a.iflag[I_DONE]) return;   // written by k_adj_b before the launch: uniform
+    if (a.fault == 1 && blockIdx.x == 0) return;   // test hook: the others' bounded waits run out
     const size_t mp = a.mp, np = a.np;
     const int r0 = (int)((long long)a.n * blockIdx.x / gridDim.x);
     const int r1 = (int)((long long)a.n * (blockIdx.x + 1) / gridDim.x);
@@ -694,12 +696,14 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 1024, 0)) != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
         const long long wait = (long long)(ctx->wait_s * ctx->clock_khz * 1e3);
+        const int fault = ctx->fault_mode;   // a pending hook is taken by this launch
+        ctx->fault_mode = 0;
         if (mixed) {
             const SolveBufs<float>& sb = ctx->sb32;
             CgArgs<float> ca{n, m, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.qe,
                              sb.ax, (float)ctx->mob.inv_perp, (float)ctx->mob.inv_par, (float)ctx->mob.inv_rot,
                              (float)ctx->mob.inv_spin, gamma, lam, r, pv, Ap, (float*)Upd, ctx->partials,
-                             ctx->bar + 2, ctx->dflags, scal, iflag, wait};
+                             ctx->bar + 2, ctx->dflags, scal, iflag, wait, fault};
             void* args[] = {&ca};
             if ((e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(1024), args, 0, st)) != cudaSuccess)
                 return e;
@@ -707,7 +711,8 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
             const SolveBufs<double>& sb = ctx->sb64;
             CgArgs<double> ca{n, m, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec,
                               sb.qe, sb.ax, ctx->mob.inv_perp, ctx->mob.inv_par, ctx->mob.inv_rot, ctx->mob.inv_spin,
-                              gamma, lam, r, pv, Ap, Upd, ctx->partials, ctx->bar + 2, ctx->dflags, scal, iflag, wait};
+                              gamma, lam, r, pv, Ap, Upd, ctx->partials, ctx->bar + 2, ctx->dflags, scal, iflag, wait,
+                              fault};
             void* args[] = {&ca};
             if ((e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(1024), args, 0, st)) != cudaSuccess)
                 return e;

@@ -214,3 +214,21 @@ def test_n20k_mixed_gradient_close_to_fp64(n20k):
     assert rel(g32[0], g64[0]) < 1e-3
     assert rel(g32[1], g64[1]) < 1e-3
     assert g32[3] == pytest.approx(g64[3], rel=1e-3)
+
+
+def test_adjoint_bounded_wait_times_out_and_context_recovers():
+    # one block of the CG leaves before its first grid-wide arrival; the
+    # others' bounded waits run out, the call returns TIMEOUT, nothing hangs,
+    # and the next call on the same context is exact again
+    s, T = small(2, 30, 10.0, 3.0)
+    with ctx_for(s, A.FP64) as ctx:
+        xn, qn, pr, gam, x0, q0 = gpu_forward(ctx, s)
+        ctx.set_wait_limit(0.2)
+        ctx.inject_fault(1)
+        with pytest.raises(A.AlensError) as e:
+            ctx.step_adjoint(x0, q0, dev(s.f_nc), pr, gam, 2.0 * (xn - dev(T)))
+        assert e.value.status == 4
+        ctx.set_wait_limit(5.0)
+        gx, gq, gf, geta, info = ctx.step_adjoint(x0, q0, dev(s.f_nc), pr, gam, 2.0 * (xn - dev(T)))
+    ref_L, ref, fw = ADJ.loss_and_grad(s.x, s.quat, s.f_nc, O.problem_of(s), T)
+    assert rel(host(gx), ref["x"]) < 1e-7
