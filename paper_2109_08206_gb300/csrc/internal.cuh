@@ -30,7 +30,7 @@ enum Flag : int {
 };
 // 64-bit counters (Ctx::dcount)
 enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_SMEM = 6,
-                   C_QUEUE = 7, C_WALLS = 8, C_NCOUNT = 9 };
+                   C_QUEUE = 7, C_WALLS = 8, C_MAXRODS = 9, C_NCOUNT = 10 };
 
 // ------------------------------------------------------------ plain structs
 

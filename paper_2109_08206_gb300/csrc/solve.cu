@@ -216,6 +216,7 @@ struct SolveArgs {
     T pi_tol;      // stopping threshold on max |pi| (float32: see above)
     int max_iter;
     int refresh;   // refresh the reference every this many iterations (0: never)
+    int sort_ns;   // global-memory blocks sort their rods (shared memory for the order was given)
     long long wait_cycles;
     int fault;
     const int* __restrict__ bstart;   // [gridDim.x + 1] rod-rank boundaries of the blocks
@@ -272,6 +273,30 @@ __device__ void carve(Own<T>& o, unsigned char* base)
     o.perm = o.ci + C;
 }
 
+// Rod order of the rod phase: ascending (owned, other-side) entry counts,
+// so that the 32 rods of a warp run loops of about the same lengths (a warp
+// runs each loop as long as its longest rod's).  Rank sort on unique keys
+// (count pair, then the block-local index, < 65536) in the scratch key and
+// rk ([nr] each); rowP and rowQ point at the block's first rod's row
+// pointers.
+__device__ void sort_rods(const int* rowP, const int* rowQ, int nr, unsigned* key, int* rk, unsigned short* perm)
+{
+    for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+        const int no = min(rowP[li + 1] - rowP[li], 255), nq = min(rowQ[li + 1] - rowQ[li], 255);
+        key[li] = ((unsigned)(no << 8 | nq) << 16) | (unsigned)li;
+    }
+    __syncthreads();
+    for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+        const unsigned kk = key[li];
+        int r = 0;
+        for (int lj = 0; lj < nr; ++lj) r += key[lj] < kk;
+        rk[li] = r;
+    }
+    __syncthreads();
+    for (int li = threadIdx.x; li < nr; li += blockDim.x) perm[rk[li]] = (unsigned short)li;
+    __syncthreads();
+}
+
 template <typename T>
 __device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
 {
@@ -297,29 +322,11 @@ __device__ void stage_in(const SolveArgs<T>& a, Own<T>& o)
         o.grs[lc] = T(0);
     }
     for (int k = threadIdx.x; k < o.q1 - o.q0; k += blockDim.x) o.qlist[k] = a.qlist[o.q0 + k];
-    // rod order of the rod phase: ascending (owned, other-side) entry
-    // counts, so that the 32 rods of a warp run loops of about the same
-    // lengths (a warp runs each loop as long as its longest rod's).  Rank
-    // sort on unique keys (count pair, then index), the keys and ranks held
-    // in the velocity array, which the first rod phase writes before anyone
-    // reads it.
-    unsigned* key = reinterpret_cast<unsigned*>(o.U);
-    int* rk = reinterpret_cast<int*>(o.U) + nr;   // 6 cap_r values hold 2 nr words
+    // the keys and ranks of the rod order live in the velocity array, which
+    // the first rod phase writes before anyone reads it (6 cap_r values hold
+    // 2 nr words)
     __syncthreads();
-    for (int li = threadIdx.x; li < nr; li += blockDim.x) {
-        const int no = min(o.rowP[li + 1] - o.rowP[li], 255), nq = min(o.rowQ[li + 1] - o.rowQ[li], 255);
-        key[li] = ((unsigned)(no << 8 | nq) << 16) | (unsigned)li;
-    }
-    __syncthreads();
-    for (int li = threadIdx.x; li < nr; li += blockDim.x) {
-        const unsigned kk = key[li];
-        int r = 0;
-        for (int lj = 0; lj < nr; ++lj) r += key[lj] < kk;
-        rk[li] = r;
-    }
-    __syncthreads();
-    for (int li = threadIdx.x; li < nr; li += blockDim.x) o.perm[rk[li]] = (unsigned short)li;
-    __syncthreads();
+    sort_rods(o.rowP, o.rowQ, nr, reinterpret_cast<unsigned*>(o.U), reinterpret_cast<int*>(o.U) + nr, o.perm);
 }
 
 // Rod phase modes: A_STEP forms delta_{k+1} = max(-gamma_ref, delta - alpha g)
@@ -365,7 +372,7 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
     const T* sdc = o.ds;   // shared copy (staged blocks)
 #pragma unroll 1
     for (int t = threadIdx.x; t < o.r1 - o.r0; t += blockDim.x) {
-        const int li = ST ? (int)o.perm[t] : t, i = o.r0 + li;
+        const int li = o.perm ? (int)o.perm[t] : t, i = o.r0 + li;
         Acc<T, COMP> Fa[6];
 #pragma unroll
         for (int w = 0; w < 6; ++w) Fa[w].init(T(0));
@@ -985,9 +992,11 @@ __global__ void k_partition(int n, int m, int nb, const int* __restrict__ rowP, 
     if ((threadIdx.x & 31) == 0) bstart[b] = r;
 }
 
-// Largest shared-memory share over the blocks (bytes, for element size esize).
+// Largest shared-memory share over the blocks (bytes, for element size esize)
+// and the largest rod count of a block.
 __global__ void k_stage_need(int nb, int esize, const int* __restrict__ bstart, const int* __restrict__ rowP,
-                             const int* __restrict__ rowQ, unsigned long long* __restrict__ need)
+                             const int* __restrict__ rowQ, unsigned long long* __restrict__ need,
+                             unsigned long long* __restrict__ maxrods)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -995,6 +1004,7 @@ __global__ void k_stage_need(int nb, int esize, const int* __restrict__ bstart, 
     const size_t nc = rowP[r1] - rowP[r0], nq = rowQ[r1] - rowQ[r0], nr = r1 - r0;
     const size_t bytes = staged_bytes(esize, nc, nr, nq);
     atomicMax(need, (unsigned long long)bytes);
+    atomicMax(maxrods, (unsigned long long)nr);
 }
 
 template <typename T, bool ST>
@@ -1014,9 +1024,17 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd(SolveArgs<T> a)
     o.cap_c = o.c1 - o.c0;
     o.cap_r = o.r1 - o.r0;
     o.cap_q = o.q1 - o.q0;
+    o.perm = nullptr;
     if (ST) {
         carve(o, dyn);
         stage_in(a, o);
+    } else if (a.sort_ns) {
+        // global-memory blocks: the rod order alone in shared memory
+        const int nr = o.r1 - o.r0;
+        unsigned* key = reinterpret_cast<unsigned*>(dyn);
+        int* rk = reinterpret_cast<int*>(key + nr);
+        o.perm = reinterpret_cast<unsigned short*>(rk + nr);
+        sort_rods(a.rowP + o.r0, a.rowQ + o.r0, nr, key, rk, o.perm);
     }
     GridSync<T> sy;
     sy.bar = a.bar; sy.flags = a.flags; sy.wait_cycles = a.wait_cycles;
@@ -1067,6 +1085,7 @@ k_bbpgd_sys(SolveArgs<T> a, int ns, const long long* __restrict__ sysoff, const 
         }
         __syncthreads();
         Own<T> o;
+        o.perm = nullptr;
         o.r0 = bounds[0];
         o.r1 = bounds[1];
         o.c0 = a.rowP[o.r0];
@@ -1183,6 +1202,7 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.pi_tol = pi_threshold<T>(a.hD, a.tol);
     a.wait_cycles = (long long)(ctx->wait_s * ctx->clock_khz * 1e3);
     a.fault = 0;
+    a.sort_ns = 0;
     a.bstart = ctx->bstart;
     return a;
 }
@@ -1207,13 +1227,18 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     const int nbw = (int)blocks + 1;
     k_partition<<<(nbw * 32 + 255) / 256, 256, 0, ctx->stream>>>(n, m, (int)blocks, ctx->rowP, ctx->rowQ, ctx->bstart);
     ++ctx->launches;
-    if ((e = cudaMemsetAsync(ctx->dcount + C_SMEM, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->dcount + C_SMEM, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ctx->dcount + C_MAXRODS, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
+        return e;
     k_stage_need<<<((int)blocks + 127) / 128, 128, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart, ctx->rowP,
-                                                                  ctx->rowQ, ctx->dcount + C_SMEM);
+                                                                  ctx->rowQ, ctx->dcount + C_SMEM,
+                                                                  ctx->dcount + C_MAXRODS);
     ++ctx->launches;
-    unsigned long long need = 0;
+    unsigned long long need = 0, maxrods = 0;
     if ((e = cudaMemcpyAsync(&need, ctx->dcount + C_SMEM, sizeof(need), cudaMemcpyDeviceToHost, ctx->stream)) !=
             cudaSuccess ||
+        (e = cudaMemcpyAsync(&maxrods, ctx->dcount + C_MAXRODS, sizeof(maxrods), cudaMemcpyDeviceToHost,
+                             ctx->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
         return e;
     int optin = 0;
@@ -1221,7 +1246,11 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
         return e;
     const long long budget = (long long)optin / bps - (long long)sizeof(Shared<T>) - 1024;
     const bool staged = (long long)need <= budget && (long long)n / blocks < 60000;
-    const size_t smem = staged ? (size_t)need : 0;
+    // global-memory blocks still take their rods in count order when the
+    // order (10 bytes of scratch per rod) fits
+    const long long sort_bytes = 10 * (long long)maxrods;
+    a.sort_ns = !staged && maxrods > 0 && maxrods < 65536 && sort_bytes <= budget;
+    const size_t smem = staged ? (size_t)need : (a.sort_ns ? (size_t)sort_bytes : 0);
     const void* fn = staged ? (const void*)k_bbpgd<T, true> : (const void*)k_bbpgd<T, false>;
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
