@@ -217,6 +217,7 @@ struct SolveArgs {
     int max_iter;
     int refresh;   // refresh the reference every this many iterations (0: never)
     int sort_ns;   // global-memory blocks sort their rods (shared memory for the order was given)
+    int sort_cap;  // rods the order's scratch holds (a larger share keeps the rank order)
     long long wait_cycles;
     int fault;
     const int* __restrict__ bstart;   // [gridDim.x + 1] rod-rank boundaries of the blocks
@@ -1063,6 +1064,7 @@ __global__ void __launch_bounds__(1024, 1)
 k_bbpgd_sys(SolveArgs<T> a, int ns, const long long* __restrict__ sysoff, const int* __restrict__ order,
             unsigned long long* __restrict__ queue, int* __restrict__ sys_iters, double* __restrict__ sys_res)
 {
+    extern __shared__ __align__(16) unsigned char dyn[];   // rod order scratch (when a.sort_ns)
     __shared__ Shared<T> sh;
     __shared__ int bounds[2];
     cg::cluster_group cl = cg::this_cluster();
@@ -1088,6 +1090,13 @@ k_bbpgd_sys(SolveArgs<T> a, int ns, const long long* __restrict__ sysoff, const 
         o.perm = nullptr;
         o.r0 = bounds[0];
         o.r1 = bounds[1];
+        if (a.sort_ns && o.r1 - o.r0 <= a.sort_cap) {   // the block's share in entry-count order
+            const int nr = o.r1 - o.r0;
+            unsigned* key = reinterpret_cast<unsigned*>(dyn);
+            int* rk = reinterpret_cast<int*>(key + nr);
+            o.perm = reinterpret_cast<unsigned short*>(rk + nr);
+            sort_rods(a.rowP + o.r0, a.rowQ + o.r0, nr, key, rk, o.perm);
+        }
         o.c0 = a.rowP[o.r0];
         o.c1 = a.rowP[o.r1];
         o.q0 = a.rowQ[o.r0];
@@ -1203,6 +1212,7 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.wait_cycles = (long long)(ctx->wait_s * ctx->clock_khz * 1e3);
     a.fault = 0;
     a.sort_ns = 0;
+    a.sort_cap = 0;
     a.bstart = ctx->bstart;
     return a;
 }
@@ -1250,6 +1260,7 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     // order (10 bytes of scratch per rod) fits
     const long long sort_bytes = 10 * (long long)maxrods;
     a.sort_ns = !staged && maxrods > 0 && maxrods < 65536 && sort_bytes <= budget;
+    a.sort_cap = (int)maxrods;
     const size_t smem = staged ? (size_t)need : (a.sort_ns ? (size_t)sort_bytes : 0);
     const void* fn = staged ? (const void*)k_bbpgd<T, true> : (const void*)k_bbpgd<T, false>;
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -1281,9 +1292,24 @@ static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int
     attr[0].val.clusterDim.x = (unsigned)ctx->batch_cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    // rod order scratch: 10 bytes per rod for twice a cluster block's even
+    // share of the largest system (a block with a larger share keeps the
+    // rank order); kept small, since this solver reads its data through L1
+    long long max_sys = 0;
+    for (int s = 0; s < ns; ++s) {
+        const long long r = ctx->batch_off_host[s + 1] - ctx->batch_off_host[s];
+        if (r > max_sys) max_sys = r;
+    }
+    const long long cap = 2 * ((max_sys + ctx->batch_cluster - 1) / ctx->batch_cluster);
+    a.sort_cap = (int)(cap < 65535 ? cap : 65535);
+    const long long sort_bytes = 10 * (long long)a.sort_cap;
+    a.sort_ns = cap > 0 && sort_bytes <= 64 * 1024;
+    const size_t smem = a.sort_ns ? (size_t)sort_bytes : 0;
+    if ((e = cudaFuncSetAttribute(k_bbpgd_sys<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
     cfg.blockDim = dim3((unsigned)ctx->batch_threads);
     cfg.gridDim = dim3((unsigned)ctx->batch_cluster);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = ctx->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
