@@ -321,7 +321,8 @@ ALENS_API aLENS_status aLENS_step_batch(aLENS_ctx* ctx, int32_t n_systems, const
  * iterations did not reach it).  The CG loop is one persistent cooperative
  * kernel with bounded grid-wide waits: TIMEOUT when one runs out (see
  * aLENS_set_wait_limit).  The first call allocates the adjoint's
- * workspace (46 doubles per rod and 13 per constraint of the context's capacity).
+ * workspace (46 doubles and 4 ints per rod, 13 doubles and 3 ints per
+ * constraint of the context's capacity).
  * Single systems only (batches: call it per system). */
 ALENS_API aLENS_status aLENS_step_adjoint(aLENS_ctx* ctx, int64_t n, const double* x, const double* quat,
                                           const double* f_nc, int64_t n_pairs, const int32_t* pairs,

@@ -239,6 +239,43 @@ __global__ void k_adj_b(int m, const int32_t* __restrict__ pairs, const double* 
     }
 }
 
+// Active-set lists of the CG: per rod, the counts of its active owned
+// constraints and active other-side entries, then (after the scans) the
+// lists themselves in CSR order.
+__global__ void k_act_count(int n, const int* __restrict__ rowP, const int* __restrict__ rowQ,
+                            const int* __restrict__ qlist, const double* __restrict__ gamma, int* __restrict__ cA,
+                            int* __restrict__ cB)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int na = 0, nb = 0;
+    for (int c = rowP[i]; c < rowP[i + 1]; ++c) na += gamma[c] > 0.0;
+    for (int k = rowQ[i]; k < rowQ[i + 1]; ++k) nb += gamma[qlist[k]] > 0.0;
+    cA[i] = na;
+    cB[i] = nb;
+}
+
+__global__ void k_act_fill(int n, const int* __restrict__ rowP, const int* __restrict__ rowQ,
+                           const int* __restrict__ qlist, const double* __restrict__ gamma,
+                           const int* __restrict__ aP, const int* __restrict__ aQ, int* __restrict__ alist,
+                           int* __restrict__ bk, int* __restrict__ bc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int t = aP[i];
+    for (int c = rowP[i]; c < rowP[i + 1]; ++c)
+        if (gamma[c] > 0.0) alist[t++] = c;
+    t = aQ[i];
+    for (int k = rowQ[i]; k < rowQ[i + 1]; ++k) {
+        const int c = qlist[k];
+        if (gamma[c] > 0.0) {
+            bk[t] = k;
+            bc[t] = c;
+            ++t;
+        }
+    }
+}
+
 // Arguments of the persistent CG.
 template <typename T>
 struct CgArgs {
@@ -252,7 +289,15 @@ struct CgArgs {
     const T* __restrict__ qe;
     const T* __restrict__ ax;
     T inv_perp, inv_par, inv_rot, inv_spin;
-    const double* __restrict__ gamma;   // the active set: gamma_c > 0
+    // the active set {c : gamma_c > 0}: per rod, its active owned constraints
+    // alist[aP[i] .. aP[i+1]) and active other-side entries (arm record bk,
+    // constraint bc) [aQ[i] .. aQ[i+1]); alist[0 .. aP[n]) lists every active
+    // constraint
+    const int* __restrict__ aP;
+    const int* __restrict__ aQ;
+    const int* __restrict__ alist;
+    const int* __restrict__ bk;
+    const int* __restrict__ bc;
     double* lam;
     double* r;
     double* pv;
@@ -314,8 +359,9 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
     const size_t mp = a.mp, np = a.np;
     const int r0 = (int)((long long)a.n * blockIdx.x / gridDim.x);
     const int r1 = (int)((long long)a.n * (blockIdx.x + 1) / gridDim.x);
-    const int c0 = (int)((long long)a.m * blockIdx.x / gridDim.x);
-    const int c1 = (int)((long long)a.m * (blockIdx.x + 1) / gridDim.x);
+    const int na = a.aP[a.n];   // active constraints
+    const int c0 = (int)((long long)na * blockIdx.x / gridDim.x);
+    const int c1 = (int)((long long)na * (blockIdx.x + 1) / gridDim.x);
     const int sub = threadIdx.x & (kCgLanes - 1);
     constexpr int kRodsPerWarp = 32 / kCgLanes;
     double rr = a.scal[S_RR];
@@ -332,25 +378,19 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
             const int i = base + (int)((threadIdx.x & 31) / kCgLanes);
             T F[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
             if (i < r1) {
-                // every load of an entry is issued before the active-set test
-                // (an inactive entry contributes 0)
-                for (int c = a.rowP[i] + sub; c < a.rowP[i + 1]; c += kCgLanes) {
-                    const double g = a.gamma[c], rc = a.r[c], pc = a.pv[c];
-                    T rv[6];
+                for (int t = a.aP[i] + sub; t < a.aP[i + 1]; t += kCgLanes) {
+                    const int c = a.alist[t];
+                    const T v = (T)(a.r[c] + beta * a.pv[c]);
 #pragma unroll
-                    for (int w = 0; w < 6; ++w) rv[w] = a.rec[w * mp + c];
-                    const T v = g > 0.0 ? (T)(rc + beta * pc) : T(0);
-#pragma unroll
-                    for (int w = 0; w < 6; ++w) F[w] += v * rv[w];
+                    for (int w = 0; w < 6; ++w) F[w] += v * a.rec[w * mp + c];
                 }
-                for (int k = a.rowQ[i] + sub; k < a.rowQ[i + 1]; k += kCgLanes) {
-                    const int c = a.qlist[k];
-                    const T* q8 = a.qe + 8 * (size_t)k;
+                for (int t = a.aQ[i] + sub; t < a.aQ[i + 1]; t += kCgLanes) {
+                    const int c = a.bc[t];
+                    const T* q8 = a.qe + 8 * (size_t)a.bk[t];
                     T qv[6];
 #pragma unroll
                     for (int w = 0; w < 6; ++w) qv[w] = q8[w];
-                    const double g = a.gamma[c], rc = a.r[c], pc = a.pv[c];
-                    const T v = g > 0.0 ? (T)(rc + beta * pc) : T(0);
+                    const T v = (T)(a.r[c] + beta * a.pv[c]);
 #pragma unroll
                     for (int w = 0; w < 6; ++w) F[w] -= v * qv[w];
                 }
@@ -370,27 +410,25 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
         }
         if (!grid_barrier(a.bar, ++epoch * gridDim.x, a.flags, a.wait_cycles, &s_ok)) return;
         double acc = 0.0;
-        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            double ap = 0.0;
-            if (a.gamma[c] > 0.0) {
-                const T* ui = a.Up + 6 * (size_t)a.ci[c];
-                const T* uj = a.Up + 6 * (size_t)a.cj[c];
-                T s = T(0);
+        for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
+            const int c = a.alist[t];
+            const T* ui = a.Up + 6 * (size_t)a.ci[c];
+            const T* uj = a.Up + 6 * (size_t)a.cj[c];
+            T s = T(0);
 #pragma unroll
-                for (int w = 0; w < 3; ++w)
-                    s += a.rec[w * mp + c] * (ui[w] - uj[w]) + a.rec[(3 + w) * mp + c] * ui[3 + w] -
-                         a.rec[(6 + w) * mp + c] * uj[3 + w];
-                ap = (double)s;
-                acc += (a.r[c] + beta * a.pv[c]) * ap;
-            }
+            for (int w = 0; w < 3; ++w)
+                s += a.rec[w * mp + c] * (ui[w] - uj[w]) + a.rec[(3 + w) * mp + c] * ui[3 + w] -
+                     a.rec[(6 + w) * mp + c] * uj[3 + w];
+            const double ap = (double)s;
+            acc += (a.r[c] + beta * a.pv[c]) * ap;
             a.Ap[c] = ap;
         }
         double pap;
         if (!grid_sum(acc, a.partials, a.bar, epoch, a.flags, a.wait_cycles, red, &s_ok, &bc, pap)) return;
         alpha = pap > 0.0 ? rr / pap : 0.0;
         double acc2 = 0.0;
-        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            if (!(a.gamma[c] > 0.0)) continue;
+        for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
+            const int c = a.alist[t];
             const double pn = a.r[c] + beta * a.pv[c];
             const double rn = a.r[c] - alpha * a.Ap[c];
             a.lam[c] += alpha * pn;
@@ -634,7 +672,10 @@ cudaError_t adjoint_reserve(aLENS_ctx* ctx)
     // per rod: Ftot, U, u, Mu, nu, Up (6 each), gx, gp (3), gq (4); per constraint: lam, r, p, Ap, geo (9)
     // (each slice is rounded up to 8 doubles: 15 slices, at most 105 doubles of padding)
     const size_t doubles = np * (6 * 6 + 3 + 3 + 4) + mp * (4 + 9) + S_NSCAL + 128;
-    cudaError_t e = cudaMalloc(&ctx->adj_ws, doubles * sizeof(double) + I_NI * sizeof(int));
+    // then the flags and the CG's active-set lists (ints): counts and row
+    // pointers of the owned and other-side lists, the lists (3 mp)
+    const size_t ints = I_NI + 4 * (np + 1) + 3 * mp + 64;
+    cudaError_t e = cudaMalloc(&ctx->adj_ws, doubles * sizeof(double) + ints * sizeof(int));
     if (e != cudaSuccess) {
         ctx->adj_ws = nullptr;
         return e;
@@ -667,6 +708,13 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
     double* geo = take(9 * mp);
     double* scal = take(S_NSCAL);
     int* iflag = (int*)(base + o);
+    int* cA = iflag + 16;       // [np] active owned constraints per rod
+    int* cB = cA + np;          // [np] active other-side entries per rod
+    int* aP = cB + np;          // [np + 1]
+    int* aQ = aP + np + 1;      // [np + 1]
+    int* alist = aQ + np + 1;   // [mp]
+    int* bk = alist + mp;       // [mp]
+    int* bc = bk + mp;          // [mp]
     cudaStream_t st = ctx->stream;
     const int mixed = ctx->p.precision == ALENS_MIXED;
     const double h = ctx->p.dt;
@@ -690,6 +738,13 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
         k_adj_b<<<G, 256, 0, st>>>(m, pairs, ctx->dgeom, gamma, Mu, lam, r, pv, ctx->partials, counter, scal, iflag,
                                    tol);
         ++ctx->launches;
+        // the active set as lists (the CG touches active constraints only)
+        k_act_count<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowP, ctx->rowQ, ctx->qlist, gamma, cA, cB);
+        ++ctx->launches;
+        if ((e = exclusive_scan(ctx, cA, aP, n)) != cudaSuccess || (e = exclusive_scan(ctx, cB, aQ, n)) != cudaSuccess)
+            return e;
+        k_act_fill<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowP, ctx->rowQ, ctx->qlist, gamma, aP, aQ, alist, bk, bc);
+        ++ctx->launches;
         // the persistent CG: one block per SM (cooperative launch)
         const void* fn = mixed ? (const void*)k_cg<float> : (const void*)k_cg<double>;
         int per_sm = 0;
@@ -702,7 +757,7 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
             const SolveBufs<float>& sb = ctx->sb32;
             CgArgs<float> ca{n, m, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.qe,
                              sb.ax, (float)ctx->mob.inv_perp, (float)ctx->mob.inv_par, (float)ctx->mob.inv_rot,
-                             (float)ctx->mob.inv_spin, gamma, lam, r, pv, Ap, (float*)Upd, ctx->partials,
+                             (float)ctx->mob.inv_spin, aP, aQ, alist, bk, bc, lam, r, pv, Ap, (float*)Upd, ctx->partials,
                              ctx->bar + 2, ctx->dflags, scal, iflag, wait, fault};
             void* args[] = {&ca};
             if ((e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(1024), args, 0, st)) != cudaSuccess)
@@ -711,7 +766,8 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
             const SolveBufs<double>& sb = ctx->sb64;
             CgArgs<double> ca{n, m, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec,
                               sb.qe, sb.ax, ctx->mob.inv_perp, ctx->mob.inv_par, ctx->mob.inv_rot, ctx->mob.inv_spin,
-                              gamma, lam, r, pv, Ap, Upd, ctx->partials, ctx->bar + 2, ctx->dflags, scal, iflag, wait,
+                              aP, aQ, alist, bk, bc, lam, r, pv, Ap, Upd, ctx->partials, ctx->bar + 2, ctx->dflags, scal,
+                              iflag, wait,
                               fault};
             void* args[] = {&ca};
             if ((e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(1024), args, 0, st)) != cudaSuccess)
