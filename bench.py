@@ -302,7 +302,8 @@ class BatchJob:
 
 
 def cg_bytes_per_iter(n, m, w):
-    """Algorithmic bytes of one CG iteration of the adjoint: per constraint
+    """Algorithmic bytes of one CG iteration of the adjoint, m the ACTIVE
+    constraints (the CG works on the active set only): per constraint
     12w + 48 (its record and (gamma, r, p) gathered from both ends), 21w + 40
     (apply: record, both ends' velocities, gamma, r, p, Ap) and 64 (update of
     lambda, r, p); per rod 9w + 8 (row pointers, axis, velocity write)."""
@@ -326,6 +327,7 @@ class GradJob(SingleJob):
         self.name = s.name + "_grad"
         self.T = W.loss_targets(s)
         self._bufs = None
+        self._active = None   # active constraints of the workload's step (counted once)
 
     def step(self, ctx, x, q, f, **kw):
         import torch
@@ -347,8 +349,10 @@ class GradJob(SingleJob):
         e1.record(stream)
         e1.synchronize()
         d = info.as_dict()
+        if self._active is None:   # the first (untimed) step: the same input every step
+            self._active = int((gm[:m] > 0).sum().item())
         d.update({"cg_iters": ainfo.iters, "cg_residual": ainfo.residual, "ms_adjoint": e0.elapsed_time(e1),
-                  "launches": d["launches"] + ainfo.launches})
+                  "launches": d["launches"] + ainfo.launches, "active": self._active})
         return GradJob.Out(d)
 
     def tune(self, T, ctx, x, q, f, precision):
@@ -725,8 +729,10 @@ def run_ours(args):
             "cg_iters": statistics.mean(i["cg_iters"] for i in infos),
             "cg_residual": max(i["cg_residual"] for i in infos),
             "ms": statistics.mean(i["ms_adjoint"] for i in infos),
-            "cg_bytes_per_iter": cg_bytes_per_iter(n, m, 4),
-            "cg_GBps_algorithmic": statistics.mean(i["cg_iters"] for i in infos) * cg_bytes_per_iter(n, m, 4)
+            "active_constraints": infos[0].get("active", m),
+            "cg_bytes_per_iter": cg_bytes_per_iter(n, infos[0].get("active", m), 4),
+            "cg_GBps_algorithmic": statistics.mean(i["cg_iters"] for i in infos)
+                                   * cg_bytes_per_iter(n, infos[0].get("active", m), 4)
                                    / (statistics.mean(i["ms_adjoint"] for i in infos) / 1e3) / 1e9},
         "fp64": fp64, "e2e": e2e, "mixed_vs_fp64": mixed_vs_fp64,
         "roofline": {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
