@@ -205,7 +205,8 @@ __device__ __forceinline__ void decode_cell(uint32_t key, int bits, int cc[3])
 
 // One warp per rod i (rods taken in cell order for locality of the candidate
 // loads).  Lanes 0-26 fetch the rod ranges of the 27 neighbour cells at once
-// (each cell with the periodic image shift that brings it next to i's cell);
+// (each cell with the periodic image shift that brings it next to i's cell),
+// cut to the suffix of ids above i;
 // the warp then walks the concatenated candidates in full chunks of 32, each
 // lane finding its cell by a binary search over the prefix of the counts;
 // candidates j > i that pass the float32 screen are appended to a per-warp
@@ -249,8 +250,16 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
         }
         ccode = (uint32_t)((sh[0] + 1) + 3 * (sh[1] + 1) + 9 * (sh[2] + 1));
         const uint32_t key = key_base + morton3(c[0], c[1], c[2]);
-        cbeg = cell_start[key];
-        ccnt = cell_start[key + 1] - cbeg;
+        int b = cell_start[key], e = cell_start[key + 1];
+        // a cell's ids ascend (k_cell_sort_ids): the candidates j > i are a
+        // suffix of its range, found by a binary search
+        while (b < e) {
+            const int mid = (b + e) >> 1;
+            if (sorted_id[mid] > i) e = mid;
+            else b = mid + 1;
+        }
+        cbeg = b;
+        ccnt = cell_start[key + 1] - b;
     }
     // inclusive prefix of the cells' counts: candidate t lies in the cell o
     // with incl[o - 1] <= t < incl[o]
