@@ -162,19 +162,24 @@ def solve_bytes_per_iter(n, m, w):
     return m * (24 * w + 24) + n * (15 * w + 4)
 
 
-def traffic_from_profile(kernel_src: Path):
-    """DRAM bytes per BBPGD iteration from the committed ncu summary, only if
-    the kernel source is unchanged since the capture (sha256 recorded there)."""
+def traffic_from_profile(kernel_src: Path, shape):
+    """DRAM bytes of one BBPGD launch from the committed ncu summary, only if
+    the kernel source is unchanged since the capture (sha256 recorded there)
+    and the capture ran in the same launch shape (threads x blocks per SM)."""
     prof = ROOT / "profiles" / "k_bbpgd_n100k_mixed.md"
     if not prof.exists():
         return None
     sha = hashlib.sha256(kernel_src.read_bytes()).hexdigest()[:16]
-    txt = prof.read_text()
-    src_line = [l for l in txt.splitlines() if l.startswith("solve_cu_sha256_16:")]
-    val_line = [l for l in txt.splitlines() if l.startswith("dram_bytes_per_iteration:")]
-    if not src_line or not val_line or src_line[0].split(":", 1)[1].strip() != sha:
+    fields = {}
+    for l in prof.read_text().splitlines():
+        k, sep, v = l.partition(":")
+        if sep and k in ("solve_cu_sha256_16", "launch_shape", "dram_bytes_per_launch"):
+            fields[k] = v.strip()
+    if len(fields) != 3 or fields["solve_cu_sha256_16"] != sha:
         return None
-    return float(val_line[0].split(":", 1)[1].strip())
+    if shape is None or fields["launch_shape"] != f"{shape[0]}x{shape[1]}":
+        return None
+    return float(fields["dram_bytes_per_launch"])
 
 
 def spatial_sample(s, target):
@@ -618,6 +623,8 @@ def run_ours(args):
         shape, times = job.tune(T, ctx, xx, qq, f, A.MIXED)
         tuned = {"shape": list(shape), "ms_solve": times}
         del xx, qq
+    # the library's default shape: 1024 threads, as many blocks per SM as fit (one, at 64 registers)
+    shape_now = tuple(tuned["shape"]) if tuned else (1024, 1)
     if isinstance(job, BatchJob):
         pr = torch.empty((max_pairs, 3), dtype=torch.int32, device=dev)
         xx, qq = x0.clone(), q0.clone()
@@ -649,9 +656,8 @@ def run_ours(args):
     alg_bytes = statistics.mean(sbytes)
     peak, peak_kind = peaks()
     achieved = alg_bytes / (ms_solve / 1e3) / 1e9
-    tr = traffic_from_profile(ROOT / "paper_2109_08206_gb300" / "csrc" / "solve.cu") \
+    traffic = traffic_from_profile(ROOT / "paper_2109_08206_gb300" / "csrc" / "solve.cu", shape_now) \
         if args.workload == "n100k_phi010" else None   # the committed capture is of this workload
-    traffic = None if tr is None else tr * statistics.mean(it)
 
     # ---- FP64 plain at the same residual
     fp64 = None
