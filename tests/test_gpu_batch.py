@@ -52,12 +52,14 @@ def batch_ctx(systems, precision, tol, max_iter=400000):
     return A.Context(p, max(n, 1), max(64, 12 * n))
 
 
-def run_batch(systems, precision, tol):
+def run_batch(systems, precision, tol, shape=None):
     off, x, quat, fnc, spec = W.batch_arrays(systems)
     xd, qd = dev(x), dev(quat)
     n = int(off[-1])
     vel = torch.empty((max(n, 1), 6), dtype=torch.float64, device="cuda")
     with batch_ctx(systems, precision, tol) as ctx:
+        if shape is not None:
+            ctx.set_batch_launch(*shape)
         pr = torch.empty((ctx.max_pairs, 3), dtype=torch.int32, device="cuda")
         gam = torch.empty(ctx.max_pairs, dtype=torch.float64, device="cuda")
         info = ctx.step_batch(spec, off, xd, qd, dev(fnc), pairs_out=pr, gamma_out=gam, vel_out=vel[:n])
@@ -188,25 +190,29 @@ def test_batch_rejects_bad_tables():
 
 def test_full_ensemble_sampled_systems():
     # the 256-system ensemble (about 1.3 million rods, float32 iterations,
-    # every system solved to the tolerance on its own): the smallest, a
-    # middle and the largest system against the oracle
+    # every system solved to the tolerance on its own), in every launch shape
+    # the autotuner may pick for the timed steps (the default 1024 x 8 among
+    # them): the smallest, a middle and the largest system against the oracle
+    import paper_2109_08206_gb300.autotune as T
     systems = W.ensemble(seed=1000, count=256)
     tol = 1e-5
-    off, x, q, pairs, gam, vel, info = run_batch(systems, A.MIXED, tol)
-    assert info.status == 0 and info.residual <= tol
     order = np.argsort([s.n for s in systems])
-    for k in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
-        s = systems[k]
-        lo, hi = off[k], off[k + 1]
-        pb = O.problem_of(s)
-        ref = O.step(s.x, s.quat, s.f_nc, pb, tol=1e-10)
-        sel = (pairs[:, 0] >= lo) & (pairs[:, 0] < hi)
-        mine = pairs[sel].copy()
-        mine[:, :2] -= lo
-        compare_pairs(mine, ref["pairs"], s)
-        U = vel[lo:hi]
-        assert np.linalg.norm(U - ref["U"]) <= 1e-3 * np.linalg.norm(ref["U"]), s.name
-        assert np.abs(periodic_diff(x[lo:hi], ref["x"], s.box)).max() <= 1e-4 * s.diameter, s.name
+    picks = (int(order[0]), int(order[len(order) // 2]), int(order[-1]))
+    refs = {k: O.step(systems[k].x, systems[k].quat, systems[k].f_nc, O.problem_of(systems[k]), tol=1e-10)
+            for k in picks}
+    for shape in T.BATCH_CANDIDATES:
+        off, x, q, pairs, gam, vel, info = run_batch(systems, A.MIXED, tol, shape)
+        assert info.status == 0 and info.residual <= tol, shape
+        for k in picks:
+            s, ref = systems[k], refs[k]
+            lo, hi = off[k], off[k + 1]
+            sel = (pairs[:, 0] >= lo) & (pairs[:, 0] < hi)
+            mine = pairs[sel].copy()
+            mine[:, :2] -= lo
+            compare_pairs(mine, ref["pairs"], s)
+            U = vel[lo:hi]
+            assert np.linalg.norm(U - ref["U"]) <= 1e-3 * np.linalg.norm(ref["U"]), (s.name, shape)
+            assert np.abs(periodic_diff(x[lo:hi], ref["x"], s.box)).max() <= 1e-4 * s.diameter, (s.name, shape)
 
 
 def test_autotune_batch_picks_and_caches():

@@ -357,6 +357,39 @@ def test_n100k_step_properties(n100k, precision, tol):
     assert np.abs(periodic_diff(host(x), xo, s.box)).max() <= (1e-9 if precision == A.FP64 else 1e-5)
 
 
+def test_n100k_mixed_in_every_launch_shape(n100k):
+    # the autotuner picks the solver's launch shape among these for the timed
+    # steps; each must give a gamma that the oracle finds optimal, the same
+    # pair list and a post-step state within the mixed-precision bars
+    import paper_2109_08206_gb300.autotune as T
+    s = n100k
+    pb = O.problem_of(s)
+    tol = 1e-5
+    out = {}
+    for shape in T.SINGLE_CANDIDATES:
+        x, q = dev(s.x), dev(s.quat)
+        with make_ctx(s, A.MIXED, tol, max_pairs=1_000_000) as ctx:
+            ctx.set_launch(*shape)
+            gam = torch.empty(ctx.max_pairs, dtype=torch.float64, device="cuda")
+            pr = torch.empty((ctx.max_pairs, 3), dtype=torch.int32, device="cuda")
+            vel = torch.empty((s.n, 6), dtype=torch.float64, device="cuda")
+            info = ctx.step(x, q, dev(s.f_nc), pairs_out=pr, gamma_out=gam, vel_out=vel)
+            m = info.n_pairs
+            assert info.status == 0 and info.residual <= tol, shape
+            out[shape] = (host(pr)[:m], host(gam)[:m], host(vel), host(x), info.iters)
+    pairs = out[T.SINGLE_CANDIDATES[0]][0]
+    asm = O.assemble(s.x, s.quat, s.f_nc, pb, pairs)
+    for shape, (pr, g, vel, xg, iters) in out.items():
+        assert np.array_equal(pr, pairs), shape
+        assert (g >= 0).all()
+        _, r = O.gradient(s.quat, pb, pairs, asm["dgeom"], asm["q"], g)
+        assert r <= tol * 1.05 + 1e-6, (shape, r)
+        U = O.mobility_apply(s.quat, pb, s.f_nc + O.apply_D(s.n, pairs, asm["dgeom"], g))
+        assert rel_l2(vel, U) <= 1e-4, shape
+        xo = O.wrap(O.wrap(s.x, s.box) + s.dt * U[:, :3], s.box)
+        assert np.abs(periodic_diff(xg, xo, s.box)).max() <= 1e-5, shape
+
+
 # -------------------------------------------- 4e5 rods, nematic, mixed precision
 
 @pytest.fixture(scope="module")
