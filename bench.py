@@ -309,10 +309,11 @@ class BatchJob:
 def cg_bytes_per_iter(n, m, w):
     """Algorithmic bytes of one CG iteration of the adjoint, m the ACTIVE
     constraints (the CG works on the active set only): per constraint
-    12w + 48 (its record and (gamma, r, p) gathered from both ends), 21w + 40
-    (apply: record, both ends' velocities, gamma, r, p, Ap) and 64 (update of
-    lambda, r, p); per rod 9w + 8 (row pointers, axis, velocity write)."""
-    return m * (33 * w + 152) + n * (9 * w + 8)
+    12w + 60 (rod pass: its record arms and (r, p, Ap) gathered from both
+    ends, with the list entries) and 21w + 76 (constraint pass: record, both
+    ends' velocities, list entry and end indices, (r, p, Ap, lambda) read and
+    written); per rod 9w + 8 (row pointers, axis, velocity write)."""
+    return m * (33 * w + 136) + n * (9 * w + 8)
 
 
 class GradJob(SingleJob):

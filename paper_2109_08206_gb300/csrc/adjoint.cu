@@ -207,11 +207,12 @@ __global__ void k_adj_rods1(int n, int np, Mob mob, double h, const double* __re
     for (int a = 0; a < 4; ++a) gq[4 * (size_t)i + a] = gqi[a];
 }
 
-// b = D^T M u on the active set; CG start lambda = 0, r = b_A, p = 0, beta = 0.
+// b = D^T M u on the active set; CG start lambda = 0, r = b_A, p = 0, Ap = 0,
+// alpha = beta = 0.
 __global__ void k_adj_b(int m, const int32_t* __restrict__ pairs, const double* __restrict__ dgeom,
                         const double* __restrict__ gamma, const double* __restrict__ Mu, double* __restrict__ lam,
-                        double* __restrict__ r, double* __restrict__ pv, double* __restrict__ partials,
-                        unsigned* counter, double* scal, int* iflag, double tol)
+                        double* __restrict__ r, double* __restrict__ pv, double* __restrict__ Ap,
+                        double* __restrict__ partials, unsigned* counter, double* scal, int* iflag, double tol)
 {
     double acc = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
@@ -226,6 +227,7 @@ __global__ void k_adj_b(int m, const int32_t* __restrict__ pairs, const double* 
         r[c] = rc;
         lam[c] = 0.0;
         pv[c] = 0.0;
+        Ap[c] = 0.0;
         acc += rc * rc;
     }
     double tot;
@@ -312,47 +314,87 @@ struct CgArgs {
     int fault;           // test hook (aLENS_inject_fault): 1 = block 0 leaves before its first arrival
 };
 
-// Sum of v over the grid, the same value in every block: block sums into
-// part[blockIdx.x], a grid barrier, then warp 0 of every block adds the
-// partials in block order (lanes strided, then a fixed shuffle tree).
-__device__ __forceinline__ bool grid_sum(double v, double* part, unsigned* bar, unsigned& epoch, int* flags,
-                                         long long wait_cycles, double* red, int* s_ok, double* bc, double& out)
+// Float64 arithmetic is scarce on this part (a warp-wide add occupies the
+// SM's float64 pipe for many cycles), so the CG's sums avoid shuffle trees
+// over every warp.  Block sums of v[0..3]: every thread puts its values in
+// vals[u][thread]; warp w adds, for value u = w % 4, the rows (32 threads
+// each) w / 4, w / 4 + G, ... (G = warps / 4 groups) of the first `rows`
+// rows lane by lane into its own row; warp u < 4 then adds the G group rows
+// lane by lane and finishes with a shuffle tree.  Only the first `rows` rows
+// can hold non-zero values (threads that had no constraint add nothing).
+// Lane 0 of warp u stores the block sum of value u in part[u * gridDim.x +
+// blockIdx.x].  Needs blockDim.x a multiple of 128.
+__device__ __forceinline__ void block_sums4(const double v[4], double (*vals)[1024], int rows, double* part)
 {
-    const double s = block_sum(v, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-    if (!grid_barrier(bar, ++epoch * gridDim.x, flags, wait_cycles, s_ok)) return false;
-    if (threadIdx.x < 32) {
-        double acc = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) acc += __ldcg(&part[b]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, groups = (int)(blockDim.x >> 7);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (threadIdx.x == 0) *bc = acc;
+    for (int u = 0; u < 4; ++u) vals[u][threadIdx.x] = v[u];
+    __syncthreads();
+    {
+        const int u = warp & 3, g = warp >> 2;
+        if (g < rows) {
+            double s = vals[u][g * 32 + lane];
+            for (int k = g + groups; k < rows; k += groups) s += vals[u][k * 32 + lane];
+            vals[u][g * 32 + lane] = s;   // row g is read by this warp alone
+        }
     }
     __syncthreads();
-    out = *bc;
+    if (warp < 4) {
+        const int gmax = rows < groups ? rows : groups;
+        double s = vals[warp][lane];
+        for (int g = 1; g < gmax; ++g) s += vals[warp][g * 32 + lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) part[warp * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// Grid totals of the four block sums, the same values in every block: a grid
+// barrier, then warp u < 4 of every block adds the partials of value u in
+// block order (lanes strided, then a fixed shuffle tree) into tot[u].
+__device__ __forceinline__ bool grid_totals4(const double* part, unsigned* bar, unsigned& epoch, int* flags,
+                                             long long wait_cycles, int* s_ok, double* tot)
+{
+    if (!grid_barrier(bar, ++epoch * gridDim.x, flags, wait_cycles, s_ok)) return false;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < 4) {
+        double acc = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) acc += __ldcg(&part[warp * gridDim.x + b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) tot[warp] = acc;
+    }
+    __syncthreads();
     return true;
 }
 
 // CG on A_AA lambda_A = b_A from the state k_adj_b left (lambda = 0, r =
-// b_A, p = 0, r.r and the stopping bound in scal).  Block b takes a
+// b_A, p = 0, Ap = 0, r.r and the stopping bound in scal).  Block b takes a
 // contiguous share of the rods (kCgLanes lanes per rod, each over every
 // kCgLanes-th entry of the rod's lists, the force summed over the lanes by
-// shuffles) and of the constraints (a thread each).  An iteration:
-//   rod pass:   p_new = r + beta p (formed where it is read), F = D_A p_new,
-//               Up = M F (working precision);
-//   constraint: Ap = (D^T Up)_A and p_new.Ap -> alpha = r.r / p.Ap;
-//   update:     p = p_new, lambda += alpha p, r -= alpha Ap, and r.r ->
-//               beta = r.r / previous r.r.
-// Stops when r.r <= tol^2 r0.r0, alpha <= 0 or after max_iter iterations.
-// The two sums alternate between two partials buffers: a grid barrier
-// separates every rewrite of a buffer from the reads of its last use.
+// shuffles) and of the constraints (a thread each).  Iteration k finds in
+// memory r_{k-1}, p_{k-1}, Ap_{k-1} and lambda_{k-1}, and holds alpha_{k-1},
+// beta_{k-1} (all zero for k = 0, when r holds r_0):
+//   rod pass:   r_k = r_{k-1} - alpha Ap_{k-1}, p_k = r_k + beta p_{k-1}
+//               (formed where they are read), F = D_A p_k, Up = M F
+//               (working precision);
+//   constraint: the same r_k and p_k, lambda_k = lambda_{k-1} + alpha p_{k-1},
+//               stored with Ap_k = (D^T Up)_A;
+//   one grid sum of p_k.Ap_k, r_k.Ap_k, Ap_k.Ap_k and r_k.r_k.
+// Then alpha_k = r_k.r_k / p_k.Ap_k and beta_k = r_{k+1}.r_{k+1} / r_k.r_k,
+// with r_{k+1}.r_{k+1} = r_k.r_k - 2 alpha_k r_k.Ap_k + alpha_k^2 Ap_k.Ap_k
+// expanded from r_{k+1} = r_k - alpha_k Ap_k; the same iterates as the
+// textbook loop, with two grid-wide synchronisations an iteration instead
+// of three.  Stops with lambda_k when r_k.r_k <= tol^2 r_0.r_0, when k
+// reaches max_iter, or when alpha_k <= 0; k is the iteration count.
 constexpr int kCgLanes = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
 {
-    __shared__ double red[32];
-    __shared__ double bc;
+    __shared__ double vals[4][1024];
+    __shared__ double tot[4];
+    __shared__ double sc[4];   // alpha, beta, r.r, stop flag (thread 0 writes them)
     __shared__ int s_ok;
     if (a.iflag[I_DONE]) return;   // written by k_adj_b before the launch: uniform
     if (a.fault == 1 && blockIdx.x == 0) return;   // test hook: the others' bounded waits run out
@@ -364,13 +406,12 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
     const int c1 = (int)((long long)na * (blockIdx.x + 1) / gridDim.x);
     const int sub = threadIdx.x & (kCgLanes - 1);
     constexpr int kRodsPerWarp = 32 / kCgLanes;
-    double rr = a.scal[S_RR];
     const double tol2 = a.scal[S_TOL2];
     const int maxit = a.iflag[I_MAXIT];
-    double beta = 0.0, alpha = 0.0;
+    double rr = a.scal[S_RR], beta = 0.0, alpha = 0.0;
     unsigned epoch = 0;
     int it = 0;
-    while (it < maxit) {
+    for (;; ++it) {
         // the loop runs while the warp's first rod is in range (uniform per warp:
         // every lane takes part in the shuffles)
         for (int base = r0 + (int)(threadIdx.x >> 5) * kRodsPerWarp; base < r1;
@@ -380,7 +421,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
             if (i < r1) {
                 for (int t = a.aP[i] + sub; t < a.aP[i + 1]; t += kCgLanes) {
                     const int c = a.alist[t];
-                    const T v = (T)(a.r[c] + beta * a.pv[c]);
+                    const T v = (T)(fma(-alpha, a.Ap[c], a.r[c]) + beta * a.pv[c]);
 #pragma unroll
                     for (int w = 0; w < 6; ++w) F[w] += v * a.rec[w * mp + c];
                 }
@@ -390,7 +431,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
                     T qv[6];
 #pragma unroll
                     for (int w = 0; w < 6; ++w) qv[w] = q8[w];
-                    const T v = (T)(a.r[c] + beta * a.pv[c]);
+                    const T v = (T)(fma(-alpha, a.Ap[c], a.r[c]) + beta * a.pv[c]);
 #pragma unroll
                     for (int w = 0; w < 6; ++w) F[w] -= v * qv[w];
                 }
@@ -409,7 +450,7 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
             o[3] = F[3] * a.inv_rot + p0 * ct; o[4] = F[4] * a.inv_rot + p1 * ct; o[5] = F[5] * a.inv_rot + p2 * ct;
         }
         if (!grid_barrier(a.bar, ++epoch * gridDim.x, a.flags, a.wait_cycles, &s_ok)) return;
-        double acc = 0.0;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};   // p.Ap, r.Ap, Ap.Ap, r.r
         for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
             const int c = a.alist[t];
             const T* ui = a.Up + 6 * (size_t)a.ci[c];
@@ -420,29 +461,43 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
                 s += a.rec[w * mp + c] * (ui[w] - uj[w]) + a.rec[(3 + w) * mp + c] * ui[3 + w] -
                      a.rec[(6 + w) * mp + c] * uj[3 + w];
             const double ap = (double)s;
-            acc += (a.r[c] + beta * a.pv[c]) * ap;
-            a.Ap[c] = ap;
-        }
-        double pap;
-        if (!grid_sum(acc, a.partials, a.bar, epoch, a.flags, a.wait_cycles, red, &s_ok, &bc, pap)) return;
-        alpha = pap > 0.0 ? rr / pap : 0.0;
-        double acc2 = 0.0;
-        for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
-            const int c = a.alist[t];
-            const double pn = a.r[c] + beta * a.pv[c];
-            const double rn = a.r[c] - alpha * a.Ap[c];
-            a.lam[c] += alpha * pn;
-            a.pv[c] = pn;
+            const double pold = a.pv[c];
+            const double rn = fma(-alpha, a.Ap[c], a.r[c]);
+            const double pn = rn + beta * pold;
+            a.lam[c] += alpha * pold;
             a.r[c] = rn;
-            acc2 += rn * rn;
+            a.pv[c] = pn;
+            a.Ap[c] = ap;
+            acc[0] += pn * ap;
+            acc[1] += rn * ap;
+            acc[2] += ap * ap;
+            acc[3] += rn * rn;
         }
-        double rrn;
-        if (!grid_sum(acc2, a.partials + gridDim.x, a.bar, epoch, a.flags, a.wait_cycles, red, &s_ok, &bc, rrn))
-            return;
-        beta = rr > 0.0 ? rrn / rr : 0.0;
-        rr = rrn;
-        ++it;
-        if (!(rr > tol2) || !(alpha > 0.0)) break;
+        const int busy = c1 - c0 < (int)blockDim.x ? c1 - c0 : (int)blockDim.x;   // threads that held a constraint
+        block_sums4(acc, vals, (busy + 31) >> 5, a.partials);
+        if (!grid_totals4(a.partials, a.bar, epoch, a.flags, a.wait_cycles, &s_ok, tot)) return;
+        // the step scalars in one thread (every block finds the same totals)
+        if (threadIdx.x == 0) {
+            const double rk = tot[3], pap = tot[0];
+            double al = alpha, be = beta, stop = 0.0;
+            if (!(rk > tol2) || it >= maxit) {
+                stop = 1.0;
+            } else {
+                al = pap > 0.0 ? rk / pap : 0.0;
+                if (!(al > 0.0)) {
+                    stop = 1.0;
+                } else {
+                    const double rrn = rk - 2.0 * al * tot[1] + al * al * tot[2];
+                    be = rrn > 0.0 ? rrn / rk : 0.0;
+                }
+            }
+            sc[0] = al; sc[1] = be; sc[2] = rk; sc[3] = stop;
+        }
+        __syncthreads();
+        alpha = sc[0];
+        beta = sc[1];
+        rr = sc[2];
+        if (sc[3] != 0.0) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.scal[S_RR] = rr;
@@ -735,7 +790,7 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
     int iters = 0;
     double rel = 0.0;
     if (m > 0) {
-        k_adj_b<<<G, 256, 0, st>>>(m, pairs, ctx->dgeom, gamma, Mu, lam, r, pv, ctx->partials, counter, scal, iflag,
+        k_adj_b<<<G, 256, 0, st>>>(m, pairs, ctx->dgeom, gamma, Mu, lam, r, pv, Ap, ctx->partials, counter, scal, iflag,
                                    tol);
         ++ctx->launches;
         // the active set as lists (the CG touches active constraints only)
