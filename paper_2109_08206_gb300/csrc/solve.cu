@@ -488,7 +488,8 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
 #pragma unroll
             for (int w = 0; w < 6; ++w) fmf += F[w] * Uv[w];
         } else {
-            st_u6(MODE == A_REF ? a.Uref : a.U, i, Uv);
+            // staged steps publish dU after the rod loop, coalesced (copy_out_du)
+            if (!(ST && MODE == A_STEP)) st_u6(MODE == A_REF ? a.Uref : a.U, i, Uv);
             if (MODE == A_REF) {
                 const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
                 st_u6(a.U, i, z);   // dU = 0: delta is 0 after a reference pass
@@ -500,6 +501,27 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
         }
     }
     return fmf;
+}
+
+// A staged step's dU for the other blocks: the block's rods [r0, r1) are
+// contiguous in the [n][6] global array, so after the rod loop the block
+// copies its shared [6][cap_r] values out with consecutive threads writing
+// consecutive pairs.  The rod loop's own stores would be three scattered
+// 8-byte stores per rod (its threads take the rods in count order), which
+// the grid barrier's release then waits for.
+template <typename T>
+__device__ __forceinline__ void copy_out_du(const SolveArgs<T>& a, const Own<T>& o)
+{
+    __syncthreads();
+    const int nr = o.r1 - o.r0;
+    typename V2<T>::t* g = reinterpret_cast<typename V2<T>::t*>(a.U + 6 * (size_t)o.r0);
+    for (int k = threadIdx.x; k < 3 * nr; k += blockDim.x) {
+        const int r = k / 3, w = 2 * (k - 3 * r);
+        typename V2<T>::t v;
+        v.x = o.U[w * o.cap_r + r];
+        v.y = o.U[(w + 1) * o.cap_r + r];
+        g[k] = v;
+    }
 }
 
 // Constraint phase for the block's owned constraints (modes above).  In
@@ -901,6 +923,7 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
         v[0] = v[1] = v[2] = v[3] = T(0);
         if (kind == P_STEP) {
             phase_a<T, A_STEP, ST>(a, o, cur, sh.alpha);
+            if (ST) copy_out_du(a, o);
             if (!sy.barrier(sh)) return;
             phase_b<T, B_STEP, ST>(a, o, cur, nx, sh.alpha, v);
         } else if (kind == P_REF) {
