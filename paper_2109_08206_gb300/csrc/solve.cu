@@ -730,25 +730,26 @@ __device__ __forceinline__ void block_partial(T v[4], T (*red)[4], T* dst, int s
 
 // After a barrier: warps 0-3 each reduce one component of the per-block
 // partials ([4][nb]: a warp reads one contiguous row) in the working
-// precision in a fixed order, the first 8 loads of every lane in flight
-// together, and the four totals are broadcast through shared memory.
+// precision in a fixed order, the first 12 loads of every lane in flight
+// together (one L2 round trip for up to 384 blocks: 304 at 512 threads x 2
+// blocks per SM), and the four totals are broadcast through shared memory.
 template <typename T>
 __device__ __forceinline__ void grid_total(const T* partials, int nb, T* bc, T out[4])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 4) {
         const T* row = partials + (size_t)warp * nb;
-        T xs[8];
+        T xs[12];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 12; ++k) {
             const int b = lane + 32 * k;
             xs[k] = b < nb ? __ldcg(row + b) : T(0);
         }
         T w = T(0);
         if (warp == 3) {   // max |pi| (every entry >= 0)
 #pragma unroll
-            for (int k = 0; k < 8; ++k) w = xs[k] > w ? xs[k] : w;
-            for (int b = lane + 256; b < nb; b += 32) {
+            for (int k = 0; k < 12; ++k) w = xs[k] > w ? xs[k] : w;
+            for (int b = lane + 384; b < nb; b += 32) {
                 const T x = __ldcg(row + b);
                 w = x > w ? x : w;
             }
@@ -759,8 +760,8 @@ __device__ __forceinline__ void grid_total(const T* partials, int nb, T* bc, T o
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) w += xs[k];
-            for (int b = lane + 256; b < nb; b += 32) w += __ldcg(row + b);
+            for (int k = 0; k < 12; ++k) w += xs[k];
+            for (int b = lane + 384; b < nb; b += 32) w += __ldcg(row + b);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
         }
