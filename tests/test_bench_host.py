@@ -1,5 +1,7 @@
 """Host-side pieces of bench.py (no GPU): the oracle's sample of the batched
-ensemble and the algorithmic-bytes count of a batch's BBPGD launch."""
+ensemble, the algorithmic-bytes count of a batch's BBPGD launch, and the
+roofline's DRAM traffic taken from the committed ncu summary only for the
+source and launch shape it was captured on."""
 import numpy as np
 
 import bench
@@ -42,3 +44,24 @@ def test_batch_solve_bytes_sum_over_systems():
     box = job.periodic_box()
     assert box.shape == (job.n, 3)
     assert np.array_equal(box[job.off[2]], np.asarray(systems[2].box))
+
+
+def test_roofline_traffic_only_for_the_captured_source_and_shape(tmp_path, monkeypatch):
+    # the committed ncu summary carries the kernel source's hash and the launch
+    # shape; its per-launch DRAM bytes are reported only while both match
+    import hashlib
+    src = tmp_path / "solve.cu"
+    src.write_text("// kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k_bbpgd_n100k_mixed.md").write_text(
+        f"# summary\n\nsolve_cu_sha256_16: {sha}\nlaunch_shape: 512x2\niterations: 182\n"
+        "dram_bytes_per_launch: 66724864\n")
+    monkeypatch.setattr(bench, "ROOT", tmp_path)
+    assert bench.traffic_from_profile(src, (512, 2)) == 66724864.0
+    assert bench.traffic_from_profile(src, (1024, 1)) is None
+    assert bench.traffic_from_profile(src, None) is None
+    src.write_text("// kernel source, changed\n")
+    assert bench.traffic_from_profile(src, (512, 2)) is None
+
