@@ -81,8 +81,10 @@ typedef enum {
     ALENS_FP64 = 0,   /* every stage in float64 */
     ALENS_MIXED = 1   /* solver iterations (D, M, D^T, their sums and step sizes)
                          in float32 on a float64-accurate reference refreshed
-                         every 64 iterations; geometry, pair decisions, the
-                         reference passes and the stopping decision in float64 */
+                         every 64 iterations (the reference passes use
+                         compensated float32 sums over the float64 records
+                         split into float32 pairs); geometry, pair decisions
+                         and the stopping decision in float64 */
 } aLENS_precision;
 
 typedef struct {
