@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the default solver launch shape")
     ap.add_argument("--scaling", type=float, default=None,
                     help="diagonal scaling exponent of the BBPGD iteration (default: the library's, 0.5)")
+    ap.add_argument("--barriers", type=int, default=None, choices=[1, 2],
+                    help="grid barriers per BBPGD iteration (default: the library's, one where it fits)")
     return ap.parse_args()
 
 
@@ -578,6 +580,8 @@ def run_ours(args):
         ctx = job.context(A, precision, args.tol, stream)
         if args.scaling is not None:
             ctx.set_scaling(args.scaling)
+        if args.barriers is not None:
+            ctx.set_solver_schedule(args.barriers)
         return ctx
 
     def timed(ctx, K, W_, host=None, w=4):
@@ -730,6 +734,8 @@ def run_ours(args):
         "dtype": "f32-mixed (f64 geometry, reference passes and residual test)", "data": "synthetic",
         "config": config,
         "bbpgd_iters": statistics.mean(it), "residual": res, "launch_shape": tuned,
+        "solver_kernel": {0: None, 1: "one grid barrier per iteration", 2: "two barriers, shared-memory shares",
+                          3: "two barriers, global memory", 4: "per-system clusters"}.get(infos[-1].get("solver")),
         "phase_ms": {k: statistics.mean(i[k] for i in infos) for k in ("ms_build", "ms_assemble", "ms_solve",
                                                                          "ms_update", "ms_adjoint") if k in infos[0]},
         "adjoint": None if "cg_iters" not in infos[0] else {

@@ -111,6 +111,9 @@ typedef struct {
     float ms_solve;     /* device time of the BBPGD kernel alone */
     float ms_update;    /* device time of the update */
     int32_t launches;   /* kernels the call launched */
+    int32_t solver;     /* solver kernel of the call: 0 none, 1 one grid barrier per
+                           iteration, 2 two barriers with shared-memory shares,
+                           3 two barriers from global memory, 4 per-system clusters */
 } aLENS_info;
 
 typedef struct aLENS_ctx aLENS_ctx;
@@ -368,6 +371,18 @@ ALENS_API aLENS_status aLENS_inject_fault(aLENS_ctx* ctx, int32_t mode);
  * <= 1024; default 1024) and blocks per SM (0 = as many as fit).  For tuning. */
 ALENS_API aLENS_status aLENS_set_launch(aLENS_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 
+/* Grid-wide synchronisations per BBPGD iteration (Appendix "Implementation":
+ * the BBPGD iterations are the step's dominant cost).  barriers = 1
+ * (default): where every block's share of the constraints, plus a copy of
+ * each constraint another block owns that touches one of its rods, fits in
+ * shared memory, the solver synchronises the grid once per iteration and
+ * takes the Barzilai-Borwein step length one iteration late; elsewhere it
+ * falls back to barriers = 2, the two-barrier iteration with the current
+ * step length.  Both stop on the residual of the returned gamma and reach
+ * the same minimiser; iteration counts differ.  For tuning and tests;
+ * ALENS_ERR_INVALID for any other value. */
+ALENS_API aLENS_status aLENS_set_solver_schedule(aLENS_ctx* ctx, int32_t barriers);
+
 /* ------------------------------------------------------------------------
  * Allocation-free solve.  The paper has no counterpart: this entry point
  * exists for callers that may not allocate device memory - a host
@@ -378,12 +393,16 @@ ALENS_API aLENS_status aLENS_set_launch(aLENS_ctx* ctx, int32_t threads, int32_t
  *
  * It runs the same BBPGD solve as aLENS_solve_lcp (same arguments and
  * outputs, params->box and delta_c unused) with its workspace in one static
- * device array of the library (about 3.3 MB, held on every GPU that loads
- * the library until the process exits), and calls no allocating routine.
+ * device array of the library (5.19 MB, held on every GPU that loads the
+ * library until the process exits), and calls no allocating routine.
  * Limits: n <= ALENS_NOALLOC_MAX_RODS and n_pairs <= ALENS_NOALLOC_MAX_PAIRS;
  * larger problems return ALENS_ERR_CAPACITY before any work is queued.
  * The first call on a device (with that device current) looks up the
- * array's device address; make it before any stream capture.  Every call
+ * array's device address and keeps it for the life of the process; make it
+ * before any stream capture.  cudaDeviceReset (or anything else that
+ * destroys the device's primary context) unloads the library's device code
+ * and leaves that address stale: do not call this entry point on a device
+ * after resetting it.  Every call
  * reuses the same array (the counters that must start at zero are cleared
  * on each call), so calls whose GPU work overlaps - on different streams or
  * from different host threads - race; serialise them.  The call

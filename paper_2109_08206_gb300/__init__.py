@@ -36,7 +36,7 @@ class Info(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("n_overlap", C.c_int64), ("iters", C.c_int32), ("status", C.c_int32),
                 ("residual", C.c_double), ("min_gap", C.c_double), ("ms_build", C.c_float),
                 ("ms_assemble", C.c_float), ("ms_solve", C.c_float), ("ms_update", C.c_float),
-                ("launches", C.c_int32)]
+                ("launches", C.c_int32), ("solver", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,6 +107,7 @@ def lib():
             "aLENS_set_scaling": (i32, [vp, d]),
             "aLENS_inject_fault": (i32, [vp, i32]),
             "aLENS_set_launch": (i32, [vp, i32, i32]),
+            "aLENS_set_solver_schedule": (i32, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -220,6 +221,12 @@ class Context:
         st = self._lib.aLENS_set_launch(self._h, int(threads), int(blocks_per_sm))
         if st != 0:
             raise AlensError(st, "aLENS_set_launch")
+
+    def set_solver_schedule(self, barriers: int):
+        """1: one grid barrier per BBPGD iteration where it fits (default); 2: two."""
+        st = self._lib.aLENS_set_solver_schedule(self._h, int(barriers))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_solver_schedule")
 
     # ------------------------------------------------------------ entry points
     def build_neighbors(self, x, quat, pairs=None):

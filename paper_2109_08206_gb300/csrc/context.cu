@@ -330,6 +330,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     c->scale_beta = kDefaultScaleBeta;
     c->solve_threads = 1024;
     c->solve_bps = 0;
+    c->solve_barriers = 1;
     c->batch_threads = 1024;
     c->batch_cluster = 8;
     c->wall_axis = -1;
@@ -382,9 +383,9 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->scale64, mp * sizeof(double)) == cudaSuccess;
     // solver buffers, sized for float64; the float32 views alias the same memory
     // every slice starts on a 64-byte boundary (vector loads): 8 elements of slack each
-    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 12 * np + mp + 4 * np + mp + mp + 8 * 13;
+    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 18 * np + mp + 4 * np + mp + mp + 8 * 14;
     ok &= dmalloc((char**)&c->solve_ws, solve_elems * sizeof(double)) == cudaSuccess;
-    ok &= dmalloc(&c->partials, (size_t)c->max_blocks * 4 * sizeof(double)) == cudaSuccess;
+    ok &= dmalloc(&c->partials, ((size_t)c->max_blocks + 4) * 8 * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->bstart, ((size_t)c->max_blocks + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->bar, 4 * sizeof(unsigned)) == cudaSuccess;
     ok &= dmalloc(&c->dflags, F_NFLAGS * sizeof(int)) == cudaSuccess;
@@ -405,7 +406,8 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         size_t o = 0;
         auto carve64 = [&](size_t cnt) { double* r = base + o; o = (o + cnt + 7) & ~(size_t)7; return r; };
         SolveBufs<double>& s = c->sb64;
-        s.gg[0] = carve64(4 * mp); s.gg[1] = carve64(4 * mp); s.U = carve64(6 * np); s.Uref = carve64(6 * np);
+        s.gg[0] = carve64(4 * mp); s.gg[1] = carve64(4 * mp); s.U = carve64(6 * np); s.U2 = carve64(6 * np);
+        s.Uref = carve64(6 * np);
         s.gref = carve64(mp);
         s.rec = carve64(9 * mp); s.qe = carve64(8 * mp); s.q = carve64(mp); s.ax = carve64(3 * np);
         s.mobr = carve64(4 * np);
@@ -415,7 +417,8 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         size_t f = 0;
         auto carve32 = [&](size_t cnt) { float* r = fb + f; f = (f + cnt + 7) & ~(size_t)7; return r; };
         SolveBufs<float>& t = c->sb32;
-        t.gg[0] = carve32(4 * mp); t.gg[1] = carve32(4 * mp); t.U = carve32(6 * np); t.Uref = carve32(6 * np);
+        t.gg[0] = carve32(4 * mp); t.gg[1] = carve32(4 * mp); t.U = carve32(6 * np); t.U2 = carve32(6 * np);
+        t.Uref = carve32(6 * np);
         t.gref = carve32(mp);
         t.rec = carve32(9 * mp); t.qe = carve32(8 * mp); t.q = carve32(mp); t.ax = carve32(3 * np);
         t.mobr = carve32(4 * np);
@@ -487,6 +490,13 @@ aLENS_status aLENS_set_launch(aLENS_ctx* c, int32_t threads, int32_t blocks_per_
     return ALENS_OK;
 }
 
+aLENS_status aLENS_set_solver_schedule(aLENS_ctx* c, int32_t barriers)
+{
+    if (!c || (barriers != 1 && barriers != 2)) return ALENS_ERR_INVALID;
+    c->solve_barriers = barriers;
+    return ALENS_OK;
+}
+
 // Pack + cell list + search; leaves the per-rod kept counts and the
 // candidate keys in the context and the pair total in hcount[C_PAIRS].
 // Synchronises once (twice if the candidate buffer overflowed, to count the
@@ -521,7 +531,7 @@ static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const dou
 aLENS_status aLENS_build_neighbors(aLENS_ctx* c, int64_t n, const double* x, const double* quat, int32_t* pairs,
                                    int64_t pairs_cap, int64_t* n_pairs)
 {
-    if (c) { c->launches = 0; single_mode(c); }
+    if (c) { c->launches = 0; c->last_solver = 0; single_mode(c); }
     if (!rods_ok(c, n) || !n_pairs || (n > 0 && (!x || !quat)) || pairs_cap < 0 || (pairs_cap > 0 && !pairs))
         return ALENS_ERR_INVALID;
     long long cap = std::min<long long>(pairs_cap, c->max_pairs);
@@ -539,7 +549,7 @@ aLENS_status aLENS_assemble_constraints(aLENS_ctx* c, int64_t n, const double* x
                                         const double* f_nc, int64_t n_pairs, const int32_t* pairs, double* phi,
                                         double* dgeom, double* q)
 {
-    if (c) { c->launches = 0; single_mode(c); }
+    if (c) { c->launches = 0; c->last_solver = 0; single_mode(c); }
     if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
     if (n > 0 && (!x || !quat)) return ALENS_ERR_INVALID;
     if (n_pairs > 0 && (!pairs || !phi || !dgeom || !q)) return ALENS_ERR_INVALID;
@@ -564,6 +574,7 @@ static void fill_info(aLENS_ctx* c, aLENS_info* info, int64_t m, aLENS_status st
     info->residual = m > 0 ? res : 0.0;
     info->status = (int32_t)st;
     info->launches = c->launches;
+    info->solver = c->last_solver;
 }
 
 static aLENS_status solve_status(aLENS_ctx* c, int64_t m)
@@ -581,7 +592,7 @@ static aLENS_status solve_status(aLENS_ctx* c, int64_t m)
 aLENS_status aLENS_solve_lcp(aLENS_ctx* c, int64_t n, const double* quat, int64_t n_pairs, const int32_t* pairs,
                              const double* dgeom, const double* q, double* gamma, aLENS_info* info)
 {
-    if (c) { c->launches = 0; single_mode(c); }
+    if (c) { c->launches = 0; c->last_solver = 0; single_mode(c); }
     if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
     if (n > 0 && !quat) return ALENS_ERR_INVALID;
     if (n_pairs > 0 && (!pairs || !dgeom || !q || !gamma)) return ALENS_ERR_INVALID;
@@ -690,7 +701,7 @@ extern "C" {
 aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc, int32_t* pairs_out,
                         double* gamma_out, double* vel_out, aLENS_info* info)
 {
-    if (c) { c->launches = 0; single_mode(c); }
+    if (c) { c->launches = 0; c->last_solver = 0; single_mode(c); }
     if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;
     if (!c->coop_ok) return ALENS_ERR_CUDA;
     return step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
@@ -756,7 +767,7 @@ aLENS_status aLENS_brownian(aLENS_ctx* c, int64_t n, const double* quat, double 
                             const double* f_ext, double* out)
 {
     if (!rods_ok(c, n) || (n > 0 && (!quat || !out)) || !(kT >= 0.0) || step < 0) return ALENS_ERR_INVALID;
-    c->launches = 0;
+    c->launches = 0; c->last_solver = 0;
     CK(launch_brownian(c, (int)n, quat, kT, seed, (unsigned long long)step, f_ext, out));
     CK(cudaStreamSynchronize(c->stream));
     return ALENS_OK;
@@ -765,7 +776,7 @@ aLENS_status aLENS_brownian(aLENS_ctx* c, int64_t n, const double* quat, double 
 aLENS_status aLENS_random_words(aLENS_ctx* c, int64_t n, uint64_t seed, int64_t step, uint32_t* out)
 {
     if (!rods_ok(c, n) || (n > 0 && !out) || step < 0) return ALENS_ERR_INVALID;
-    c->launches = 0;
+    c->launches = 0; c->last_solver = 0;
     CK(launch_random_words(c, (int)n, seed, (unsigned long long)step, out));
     CK(cudaStreamSynchronize(c->stream));
     return ALENS_OK;
@@ -775,7 +786,7 @@ aLENS_status aLENS_run(aLENS_ctx* c, int64_t n, double* x, double* quat, const d
                        double kT, uint64_t seed, int64_t first_step, int32_t warm_start, aLENS_step_stats* stats,
                        aLENS_info* info)
 {
-    if (c) { c->launches = 0; single_mode(c); }
+    if (c) { c->launches = 0; c->last_solver = 0; single_mode(c); }
     if (!rods_ok(c, n) || (n > 0 && (!x || !quat)) || n_steps < 0 || !(kT >= 0.0) || first_step < 0)
         return ALENS_ERR_INVALID;
     if (!c->coop_ok) return ALENS_ERR_CUDA;
@@ -806,7 +817,7 @@ aLENS_status aLENS_run(aLENS_ctx* c, int64_t n, double* x, double* quat, const d
     int launches = 0;
     aLENS_status st = ALENS_OK;
     for (int64_t k = 0; k < n_steps; ++k) {
-        c->launches = 0;
+        c->launches = 0; c->last_solver = 0;
         CK(launch_brownian(c, (int)n, quat, kT, seed, (unsigned long long)(first_step + k), f_ext, c->fnc_buf));
         aLENS_info si;
         memset(&si, 0, sizeof(si));
@@ -845,7 +856,7 @@ aLENS_status aLENS_step_adjoint(aLENS_ctx* c, int64_t n, const double* x, const 
                                 const double* dL_dquat_new, double* dL_dx, double* dL_dquat, double* dL_dfnc,
                                 double* dL_deta, aLENS_info* info)
 {
-    if (c) { c->launches = 0; single_mode(c); }
+    if (c) { c->launches = 0; c->last_solver = 0; single_mode(c); }
     if (!rods_ok(c, n) || n_pairs < 0 || n_pairs > c->max_pairs) return ALENS_ERR_INVALID;
     if (n > 0 && (!x || !quat || !dL_dx || !dL_dquat)) return ALENS_ERR_INVALID;
     if (n_pairs > 0 && (!pairs || !gamma)) return ALENS_ERR_INVALID;
@@ -917,7 +928,7 @@ aLENS_status aLENS_step_batch(aLENS_ctx* c, int32_t n_systems, const aLENS_syste
                               double* x, double* quat, const double* f_nc, int32_t* pairs_out, double* gamma_out,
                               double* vel_out, aLENS_info* info)
 {
-    if (c) { c->launches = 0; single_mode(c); }
+    if (c) { c->launches = 0; c->last_solver = 0; single_mode(c); }
     if (!c || n_systems < 1 || !systems || !rod_offset) return ALENS_ERR_INVALID;
     const int64_t n = rod_offset[n_systems];
     if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;

@@ -30,7 +30,7 @@ enum Flag : int {
 };
 // 64-bit counters (Ctx::dcount)
 enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_SMEM = 6,
-                   C_QUEUE = 7, C_WALLS = 8, C_MAXRODS = 9, C_NCOUNT = 10 };
+                   C_QUEUE = 7, C_WALLS = 8, C_MAXRODS = 9, C_SMEM1 = 10, C_NCOUNT = 11 };
 
 // ------------------------------------------------------------ plain structs
 
@@ -220,6 +220,7 @@ struct SolveBufs {           // typed views into the solver workspace
     T* ax;                   // [3][np]
     T* gg[2];                // [mp][4] x 2: (delta, g, gamma_ref, 0), ping-pong
     T* U;                    // [np][6] velocity increment M D delta
+    T* U2;                   // [np][6] second increment buffer (the one-barrier solver alternates U, U2)
     T* Uref;                 // [np][6] reference velocity M D gamma_ref
     T* gref;                 // [mp] reference gradient q + D^T Uref
     T* mobr;                 // [4][np] per-rod inverse drags (batches)
@@ -282,7 +283,7 @@ struct aLENS_ctx {
     void* solve_ws;          // typed solver buffers (sized for double)
     alens::SolveBufs<double> sb64;
     alens::SolveBufs<float> sb32;
-    double* partials;        // [max_blocks][4]
+    double* partials;        // [max_blocks + 4][8]: [4][nb] block sums, or [2][4][nb] (one-barrier solver)
     int max_blocks;
     int* bstart;             // [max_blocks + 1] solver block boundaries (rod ranks)
     unsigned* bar;           // [4]
@@ -298,6 +299,8 @@ struct aLENS_ctx {
     double wait_s;
     int fault_mode;
     int solve_threads, solve_bps;
+    int solve_barriers;      // 1: one-barrier solver where its share fits (default); 2: the two-barrier kernels
+    int last_solver;         // kernel of the last single-system solve: 1 one-barrier, 2 two-barrier staged, 3 two-barrier global
     int coop_ok;
     int launches;            // kernels launched since the entry point began
     // batches (aLENS_step_batch): per-system table and per-rod system id;

@@ -14,7 +14,9 @@
 // exits.  Host code may not use the array's name as a device address, so
 // the first call on each device (with that device current) looks the
 // address up with cudaGetSymbolAddress and keeps it; make that first call
-// before any stream capture.  All calls share the array and it keeps the
+// before any stream capture.  A cudaDeviceReset unloads the module and
+// leaves the kept address stale, so the entry point is not for use on a
+// device after a reset.  All calls share the array and it keeps the
 // last call's contents: the counters the solver needs at zero are cleared on
 // every call, and two calls whose work overlaps on the GPU (on different
 // streams, or from different host threads) race on it.
@@ -38,15 +40,18 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kRodInts = align256(sizeof(int) * (kNoallocMaxRods + 1));
 constexpr size_t kPairInts = align256(sizeof(int) * kNoallocMaxPairs);
 constexpr size_t kSolveWs =
-    align256(sizeof(double) * (29 * (size_t)kNoallocMaxPairs + 19 * (size_t)kNoallocMaxRods + 104));
+    align256(sizeof(double) * (29 * (size_t)kNoallocMaxPairs + 25 * (size_t)kNoallocMaxRods + 112));
 constexpr size_t kPairDoubles = align256(sizeof(double) * kNoallocMaxPairs);
-constexpr size_t kPartials = align256(sizeof(double) * 4 * kNoallocMaxBlocks);
+constexpr size_t kPartials = align256(sizeof(double) * 8 * (kNoallocMaxBlocks + 4));
 constexpr size_t kBstart = align256(sizeof(int) * (kNoallocMaxBlocks + 1));
 constexpr int kScanTmpLen = (kNoallocMaxRods + 4095) / 4096 + 2;
 constexpr size_t kSmall = align256(16 * sizeof(unsigned)) + align256(F_NFLAGS * sizeof(int)) +
                           align256(C_NCOUNT * sizeof(unsigned long long)) + align256(kScanTmpLen * sizeof(int));
 constexpr size_t kNoallocScratchBytes =
     6 * kRodInts + 4 * kPairInts + kPairDoubles + kSolveWs + kPartials + kBstart + kSmall;
+
+// the header states the size as 5.19 MB
+static_assert(kNoallocScratchBytes > 5180000 && kNoallocScratchBytes < 5195000, "noalloc scratch size changed");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
@@ -109,6 +114,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
     c.wait_s = 5.0;
     c.scale_beta = kDefaultScaleBeta;
     c.solve_threads = 1024;
+    c.solve_barriers = 1;
     c.wall_axis = -1;
     double zperp = 4.0 * M_PI * params->viscosity * params->length / log(2.0 * params->length / params->diameter);
     c.mob.inv_perp = 1.0 / zperp;
@@ -142,7 +148,8 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
         double* b64 = (double*)c.solve_ws;
         size_t u = 0;
         auto c64 = [&](size_t cnt) { double* r = b64 + u; u = (u + cnt + 7) & ~(size_t)7; return r; };
-        c.sb64.gg[0] = c64(4 * mp); c.sb64.gg[1] = c64(4 * mp); c.sb64.U = c64(6 * np); c.sb64.Uref = c64(6 * np);
+        c.sb64.gg[0] = c64(4 * mp); c.sb64.gg[1] = c64(4 * mp); c.sb64.U = c64(6 * np); c.sb64.U2 = c64(6 * np);
+        c.sb64.Uref = c64(6 * np);
         c.sb64.gref = c64(mp);
         c.sb64.rec = c64(9 * mp); c.sb64.qe = c64(8 * mp); c.sb64.q = c64(mp); c.sb64.ax = c64(3 * np);
         c.sb64.mobr = c64(4 * np);
@@ -151,7 +158,8 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
         float* b32 = (float*)c.solve_ws;
         size_t v = 0;
         auto c32 = [&](size_t cnt) { float* r = b32 + v; v = (v + cnt + 7) & ~(size_t)7; return r; };
-        c.sb32.gg[0] = c32(4 * mp); c.sb32.gg[1] = c32(4 * mp); c.sb32.U = c32(6 * np); c.sb32.Uref = c32(6 * np);
+        c.sb32.gg[0] = c32(4 * mp); c.sb32.gg[1] = c32(4 * mp); c.sb32.U = c32(6 * np); c.sb32.U2 = c32(6 * np);
+        c.sb32.Uref = c32(6 * np);
         c.sb32.gref = c32(mp);
         c.sb32.rec = c32(9 * mp); c.sb32.qe = c32(8 * mp); c.sb32.q = c32(mp); c.sb32.ax = c32(3 * np);
         c.sb32.mobr = c32(4 * np);

@@ -199,6 +199,7 @@ struct SolveArgs {
     T* gg0;     // [m][4] (delta, g, gamma_ref, 0): written inside the kernel, plain (coherent) loads only
     T* gg1;
     T* U;       // [n][6] velocity increment M D delta
+    T* U2;      // [n][6] second increment buffer (one-barrier solver)
     T* Uref;    // [n][6] reference velocity M D gamma_ref
     T* gref;    // [m] reference gradient q + D^T Uref (blocks working from global memory)
     double* partials;
@@ -1075,6 +1076,733 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd(SolveArgs<T> a)
     }
 }
 
+// ---------------------------------------------------------------------
+// One grid barrier per iteration (staged blocks).
+//
+// The loop above exchanges two things between blocks in every iteration:
+// the velocities dU, which the constraint phase gathers, and the state of
+// constraints whose ends lie in different blocks, which the rod phase
+// gathers; each needs its own grid barrier, and the step-length sums ride
+// on the second.  Here a block also keeps a copy ("ghost") of every
+// constraint that another block owns but whose other end is one of its
+// rods, and updates it with the owner's arithmetic on the same inputs
+// (the same delta, g and alpha, the same two velocities, the same order of
+// operations), so that owner and ghost stay equal bit for bit and the rod
+// phase reads nothing but shared memory.  Only dU and the block sums cross
+// blocks, and both travel on one barrier:
+//   constraint phase k (every owned and ghost constraint):
+//       delta_k = max(-gamma_ref, delta_{k-1} - alpha_{k-1} g_{k-1}),
+//       g_k = gref + D^T dU_k, and for owned constraints the sums of
+//       s.s, s.y, y.y (s = delta_k - delta_{k-1}, y = g_k - g_{k-1}) and
+//       max |pi_k|;
+//   step decision from the sums of constraint phase k-1 (published by the
+//       last barrier, fetched into shared memory by cp.async while the
+//       constraint phase runs): alpha_k = BB(s_{k-2}, y_{k-2}), i.e. the
+//       Barzilai-Borwein step of the published method taken one iteration
+//       late (a gradient method with retards: Friedlander, Martinez, Molina
+//       & Raydan, SIAM J. Numer. Anal. 36, 1999);
+//   rod phase k: delta_{k+1} formed on the fly, dU_{k+1} = M D delta_{k+1},
+//       copied out to one of two global buffers (they alternate, so a block
+//       never overwrites velocities another block may still be reading);
+//   grid barrier (block sums in one of two buffers, alternating alike).
+// A residual below tol, 64 float32 iterations, or max_iter start a
+// reference refresh of the iterate the slots hold (the same compensated
+// passes as above, two extra barriers); the loop stops only on the residual
+// of a fresh reference, so the returned gamma (delta = 0 there) carries the
+// residual it reports, in float64 and float32 alike.
+
+// A block's share: rods [r0, r1), owned constraints [c0, c1) in slots
+// [0, nc), ghosts in slots [nc, nt).
+template <typename T>
+struct Own1 {
+    int r0, r1, c0, c1, q0, q1, nc, ng, nt, cap_r, nbp;
+    T* tot;      // [4][nbp] last barrier's block sums (cp.async target)
+    T* rec;      // [9][nt]
+    T* gref;     // [nt] q + D^T Uref
+    T* ds;       // [nt] delta
+    T* grs;      // [nt] g
+    T* gam;      // [nt] gamma_ref
+    T* ax;       // [3][cap_r]
+    T* U;        // [6][cap_r] this iteration's dU (the reference velocity during a refresh)
+    int* oth;    // [nt] rank of the slot's other end: Q for owned slots, the owner for ghosts (-1: a wall)
+    int* gid;    // [ng] constraint id of ghost slot nc + g
+    int* rowP;   // [cap_r + 1] owned ranges (constraint ids; slot = id - c0)
+    int* rowQ;   // [cap_r + 1] other-side ranges (CSR positions)
+    unsigned short* loc;    // [nt] local index of the slot's rod in this block (P owned, Q ghost), | kBil
+    unsigned short* qslot;  // [q1 - q0] slot of each other-side entry, | kBil
+    unsigned short* perm;   // [cap_r] rod order of the rod phase
+};
+constexpr unsigned kBil = 0x8000u;   // bilateral (spring) constraint: no projection
+constexpr int kMaxSlots = 0x7fff;
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Shared-memory bytes of a one-barrier block share (nt slots of which ng
+// ghosts, nr rods, nq other-side entries, nb blocks).
+__host__ __device__ inline size_t staged1_bytes(int esize, size_t nt, size_t ng, size_t nr, size_t nq, size_t nb)
+{
+    const size_t nbp = (nb + 3) & ~(size_t)3;
+    return align16(4 * nbp * esize) + align16((13 * nt + 9 * nr) * esize) +
+           align16((nt + ng + 2 * nr + 2) * sizeof(int)) + align16((nt + nq + nr) * sizeof(unsigned short));
+}
+
+template <typename T>
+__device__ void carve1(Own1<T>& o, unsigned char* base)
+{
+    const size_t nt = o.nt, R = o.cap_r;
+    o.tot = reinterpret_cast<T*>(base);
+    base += align16(4 * (size_t)o.nbp * sizeof(T));
+    T* t = reinterpret_cast<T*>(base);
+    o.rec = t; t += 9 * nt;
+    o.gref = t; t += nt;
+    o.ds = t; t += nt;
+    o.grs = t; t += nt;
+    o.gam = t; t += nt;
+    o.ax = t; t += 3 * R;
+    o.U = t; t += 6 * R;
+    base += align16((13 * nt + 9 * R) * sizeof(T));
+    int* ip = reinterpret_cast<int*>(base);
+    o.oth = ip; ip += nt;
+    o.gid = ip; ip += o.ng;
+    o.rowP = ip; ip += R + 1;
+    o.rowQ = ip; ip += R + 1;
+    base += align16((nt + o.ng + 2 * R + 2) * sizeof(int));
+    unsigned short* sp = reinterpret_cast<unsigned short*>(base);
+    o.loc = sp; sp += nt;
+    o.qslot = sp; sp += o.q1 - o.q0;
+    o.perm = sp;
+}
+
+template <typename T>
+struct Shared1 {
+    T red[32][4];
+    T alpha;
+    int kind, ng;
+};
+
+// Stage one slot (owned or ghost) of constraint c from the global arrays.
+template <typename T>
+__device__ __forceinline__ void stage_slot(const SolveArgs<T>& a, const Own1<T>& o, int t, int c, int li, int other,
+                                           unsigned bil)
+{
+    const size_t mp = a.mp, nt = o.nt;
+#pragma unroll
+    for (int w = 0; w < 9; ++w) o.rec[w * nt + t] = a.rec[w * mp + c];
+    T d, g, gr, gl;
+    ld_state(a.gg0, c, d, g, gr, gl);
+    o.ds[t] = d;
+    o.gam[t] = gr;
+    o.grs[t] = T(0);
+    o.gref[t] = T(0);
+    o.oth[t] = other;
+    o.loc[t] = (unsigned short)(li | bil);
+}
+
+template <typename T>
+__device__ void stage_in1(const SolveArgs<T>& a, Own1<T>& o, unsigned char* dyn, Shared1<T>& sh)
+{
+    const int nr = o.r1 - o.r0, nq = o.q1 - o.q0;
+    // ghosts: other-side entries of the block's rods that another block owns
+    if (threadIdx.x == 0) sh.ng = 0;
+    __syncthreads();
+    int cnt = 0;
+    for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+        const int c = a.qlist[o.q0 + k];
+        cnt += c < o.c0 || c >= o.c1;
+    }
+    if (cnt) atomicAdd(&sh.ng, cnt);
+    __syncthreads();
+    o.ng = sh.ng;
+    o.nt = o.nc + o.ng;
+    carve1(o, dyn);
+    __syncthreads();
+    if (threadIdx.x == 0) sh.ng = 0;
+    for (int li = threadIdx.x; li <= nr; li += blockDim.x) {
+        o.rowP[li] = a.rowP[o.r0 + li];
+        o.rowQ[li] = a.rowQ[o.r0 + li];
+    }
+    for (int li = threadIdx.x; li < nr; li += blockDim.x)
+        for (int w = 0; w < 3; ++w) o.ax[w * o.cap_r + li] = a.ax[w * (size_t)a.np + o.r0 + li];
+    const bool has_comp = a.comp != nullptr;
+#pragma unroll 1
+    for (int t = threadIdx.x; t < o.nc; t += blockDim.x) {
+        const int c = o.c0 + t;
+        const unsigned bil = has_comp && a.comp[c] >= T(0) ? kBil : 0u;
+        stage_slot(a, o, t, c, a.ci[c] - o.r0, a.cj[c], bil);
+    }
+    __syncthreads();   // sh.ng is 0 again before the slots are numbered
+#pragma unroll 1
+    for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+        const int c = a.qlist[o.q0 + k];
+        const unsigned bil = has_comp && a.comp[c] >= T(0) ? kBil : 0u;
+        int t;
+        if (c < o.c0 || c >= o.c1) {
+            // the slot order of ghosts does not enter any result
+            const int g = atomicAdd(&sh.ng, 1);
+            t = o.nc + g;
+            o.gid[g] = c;
+            stage_slot(a, o, t, c, a.cj[c] - o.r0, a.ci[c], bil);
+        } else {
+            t = c - o.c0;
+        }
+        o.qslot[k] = (unsigned short)(t | bil);
+    }
+    __syncthreads();
+    sort_rods(o.rowP, o.rowQ, nr, reinterpret_cast<unsigned*>(o.U), reinterpret_cast<int*>(o.U) + nr, o.perm);
+}
+
+template <typename T>
+__device__ __forceinline__ int slot_gid(const Own1<T>& o, int t)
+{
+    return t < o.nc ? o.c0 + t : o.gid[t - o.nc];
+}
+
+// Rod phase over the block's rods, every entry from shared memory (modes
+// as for phase_a: A_STEP forms delta_{k+1} with alpha and leaves dU in
+// shared memory; A_PG returns this thread's share of pi.A.pi; A_REF leaves
+// Uref = M D gamma_ref (compensated in float32) in shared memory and in
+// the global Uref).
+template <typename T, int MODE>
+__device__ __forceinline__ T rod_pass1(const SolveArgs<T>& a, const Own1<T>& o, T alpha)
+{
+    constexpr bool COMP = MODE == A_REF && sizeof(T) == 4;
+    const bool has_comp = a.comp != nullptr;
+    const size_t mp = a.mp, np = a.np, nt = o.nt;
+    T fmf = T(0);
+#pragma unroll 1
+    for (int tt = threadIdx.x; tt < o.r1 - o.r0; tt += blockDim.x) {
+        const int li = (int)o.perm[tt], i = o.r0 + li;
+        Acc<T, COMP> Fa[6];
+#pragma unroll
+        for (int w = 0; w < 6; ++w) Fa[w].init(T(0));
+        {   // owned constraints: slots [rowP[li] - c0, rowP[li + 1] - c0)
+            const int e = o.rowP[li + 1] - o.c0;
+#pragma unroll 1
+            for (int t = o.rowP[li] - o.c0; t < e; ++t) {
+                const T dv = o.ds[t], gv = o.grs[t], gr = o.gam[t];
+                T rv[6];
+#pragma unroll
+                for (int w = 0; w < 6; ++w) rv[w] = o.rec[w * nt + t];
+                const bool bil = has_comp && (o.loc[t] & kBil);
+                const T v = a_value<MODE, T>(dv, gv, gr, alpha, bil);
+                if (MODE == A_PG && bil) fmf += __ldg(&a.comp[o.c0 + t]) * v * v;   // the spring's compliance term
+#pragma unroll
+                for (int w = 0; w < 6; ++w) Fa[w].add_prod(v, rv[w]);
+                if (COMP) {   // gamma_lo and the records' low parts
+                    const int c = o.c0 + t;
+                    const T gl = gl_of_state(a.gg0, c);
+#pragma unroll
+                    for (int w = 0; w < 6; ++w) Fa[w].add_lo(v * __ldg(&a.rec_lo[w * mp + c]) + gl * rv[w]);
+                }
+            }
+        }
+        {   // constraints owned by other rods (owned or ghost slots)
+            const int e = o.rowQ[li + 1] - o.q0;
+#pragma unroll 1
+            for (int k = o.rowQ[li] - o.q0; k < e; ++k) {
+                const unsigned qs = o.qslot[k];
+                const int t = (int)(qs & kMaxSlots);
+                const T dv = o.ds[t], gv = o.grs[t], gr = o.gam[t];
+                T qv[6];
+#pragma unroll
+                for (int w = 0; w < 3; ++w) {
+                    qv[w] = o.rec[w * nt + t];
+                    qv[3 + w] = o.rec[(6 + w) * nt + t];
+                }
+                const T v = a_value<MODE, T>(dv, gv, gr, alpha, has_comp && (qs & kBil));
+#pragma unroll
+                for (int w = 0; w < 6; ++w) Fa[w].add_prod(-v, qv[w]);
+                if (COMP) {
+                    const int c = slot_gid(o, t);
+                    const T gl = gl_of_state(a.gg0, c);
+                    T ql[6];
+#pragma unroll
+                    for (int w = 0; w < 3; ++w) {
+                        ql[w] = __ldg(&a.rec_lo[w * mp + c]);
+                        ql[3 + w] = __ldg(&a.rec_lo[(6 + w) * mp + c]);
+                    }
+#pragma unroll
+                    for (int w = 0; w < 6; ++w) Fa[w].add_lo(-(v * ql[w] + gl * qv[w]));
+                }
+            }
+        }
+        T F[6];
+#pragma unroll
+        for (int w = 0; w < 6; ++w) F[w] = Fa[w].value();
+        const T p0 = o.ax[li], p1 = o.ax[o.cap_r + li], p2 = o.ax[2 * o.cap_r + li];
+        T ip = a.inv_perp, ipa = a.inv_par, ir = a.inv_rot, is = a.inv_spin;
+        if (a.mobr) {
+            ip = __ldg(&a.mobr[i]); ipa = __ldg(&a.mobr[np + i]);
+            ir = __ldg(&a.mobr[2 * np + i]); is = __ldg(&a.mobr[3 * np + i]);
+        }
+        const T pf = p0 * F[0] + p1 * F[1] + p2 * F[2];
+        const T pt = p0 * F[3] + p1 * F[4] + p2 * F[5];
+        const T cf = pf * (ipa - ip), ct = pt * (is - ir);
+        const T Uv[6] = {F[0] * ip + p0 * cf, F[1] * ip + p1 * cf, F[2] * ip + p2 * cf,
+                         F[3] * ir + p0 * ct, F[4] * ir + p1 * ct, F[5] * ir + p2 * ct};
+        if (MODE == A_PG) {
+#pragma unroll
+            for (int w = 0; w < 6; ++w) fmf += F[w] * Uv[w];
+        } else {
+#pragma unroll
+            for (int w = 0; w < 6; ++w) o.U[w * o.cap_r + li] = Uv[w];
+            if (MODE == A_REF) st_u6(a.Uref, i, Uv);
+        }
+    }
+    return fmf;
+}
+
+// The block's dU (shared [6][cap_r]) into its contiguous range of the
+// global [n][6] buffer dst, consecutive threads writing consecutive pairs.
+template <typename T>
+__device__ __forceinline__ void copy_out1(T* dst, const Own1<T>& o)
+{
+    __syncthreads();
+    const int nr = o.r1 - o.r0;
+    typename V2<T>::t* g = reinterpret_cast<typename V2<T>::t*>(dst + 6 * (size_t)o.r0);
+    for (int k = threadIdx.x; k < 3 * nr; k += blockDim.x) {
+        const int r = k / 3, w = 2 * (k - 3 * r);
+        typename V2<T>::t v;
+        v.x = o.U[w * o.cap_r + r];
+        v.y = o.U[(w + 1) * o.cap_r + r];
+        g[k] = v;
+    }
+}
+
+// The two velocities of slot t, P side first: Ui of the owner, Uj of the
+// other end (0 for a wall).  Local rods from shared memory, others from the
+// global buffer Ug.
+template <typename T>
+__device__ __forceinline__ void slot_velocities(const Own1<T>& o, int t, const T* Ug, T Ui[6], T Uj[6])
+{
+    const int li = (int)(o.loc[t] & kMaxSlots);
+    const int ro = o.oth[t];
+    T Ul[6], Uo[6];
+#pragma unroll
+    for (int w = 0; w < 6; ++w) Ul[w] = o.U[w * o.cap_r + li];
+    if (ro < 0) {
+#pragma unroll
+        for (int w = 0; w < 6; ++w) Uo[w] = T(0);
+    } else if (ro >= o.r0 && ro < o.r1) {
+#pragma unroll
+        for (int w = 0; w < 6; ++w) Uo[w] = o.U[w * o.cap_r + (ro - o.r0)];
+    } else {
+        ld_u6(Ug, ro, Uo);
+    }
+    const bool own = t < o.nc;
+#pragma unroll
+    for (int w = 0; w < 6; ++w) {
+        Ui[w] = own ? Ul[w] : Uo[w];
+        Uj[w] = own ? Uo[w] : Ul[w];
+    }
+}
+
+// Constraint phase of a step over every slot: delta_k from
+// (delta_{k-1}, g_{k-1}, alpha_{k-1}) exactly as the rod phase formed it,
+// g_k = gref + D^T dU_k (+ the spring's compliance term), and for owned
+// slots acc = (s.s, s.y, y.y, max |pi|).
+template <typename T>
+__device__ __forceinline__ void con_pass_step1(const SolveArgs<T>& a, const Own1<T>& o, T alpha, const T* Ug, T acc[4])
+{
+    const bool has_comp = a.comp != nullptr;
+    const size_t nt = o.nt;
+#pragma unroll 1
+    for (int t = threadIdx.x; t < o.nt; t += blockDim.x) {
+        T Ui[6], Uj[6], r[9];
+        slot_velocities(o, t, Ug, Ui, Uj);
+#pragma unroll
+        for (int w = 0; w < 9; ++w) r[w] = o.rec[w * nt + t];
+        const T dold = o.ds[t], gro = o.grs[t], gam = o.gam[t];
+        const int c = slot_gid(o, t);
+        const T cmp = has_comp ? __ldg(&a.comp[c]) : T(-1);
+        const bool bil = cmp >= T(0);
+        const T dm = a_value<A_STEP, T>(dold, gro, gam, alpha, bil);
+        Acc<T, false> du;
+        du.init(o.gref[t]);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            du.add_prod(r[u], Ui[u]);
+            du.add_prod(-r[u], Uj[u]);
+            du.add_prod(r[3 + u], Ui[3 + u]);
+            du.add_prod(-r[6 + u], Uj[3 + u]);
+        }
+        if (bil) du.add_prod(cmp, dm);
+        const T gr = du.value();
+        o.ds[t] = dm;
+        o.grs[t] = gr;
+        if (t < o.nc) {
+            const T pi = (bil || dm > -gam) ? gr : (gr < T(0) ? gr : T(0));
+            const T api = (pi < T(0) ? -pi : pi) * __ldg(&a.isc[c]);
+            acc[3] = api > acc[3] ? api : acc[3];
+            const T sv = dm - dold, yv = gr - gro;
+            acc[0] += sv * sv;
+            acc[1] += sv * yv;
+            acc[2] += yv * yv;
+        }
+    }
+}
+
+// Constraint phase of a refresh over every slot: gref = q + D^T Uref from
+// the split records and q with compensated sums (float32), g = gref, and
+// for owned slots acc = (pi.pi, 0, 0, max |pi|) at gamma_ref.
+template <typename T>
+__device__ __forceinline__ void con_pass_ref1(const SolveArgs<T>& a, const Own1<T>& o, T acc[4])
+{
+    constexpr bool COMP = sizeof(T) == 4;
+    const bool has_comp = a.comp != nullptr;
+    const size_t nt = o.nt, mp = a.mp;
+#pragma unroll 1
+    for (int t = threadIdx.x; t < o.nt; t += blockDim.x) {
+        T Ui[6], Uj[6], r[9];
+        slot_velocities(o, t, a.Uref, Ui, Uj);
+#pragma unroll
+        for (int w = 0; w < 9; ++w) r[w] = o.rec[w * nt + t];
+        const int c = slot_gid(o, t);
+        const T gam = o.gam[t];
+        Acc<T, COMP> du;
+        du.init(__ldg(&a.q[c]));
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            du.add_prod(r[u], Ui[u]);
+            du.add_prod(-r[u], Uj[u]);
+            du.add_prod(r[3 + u], Ui[3 + u]);
+            du.add_prod(-r[6 + u], Uj[3 + u]);
+        }
+        const T cmp = has_comp ? __ldg(&a.comp[c]) : T(-1);
+        const bool bil = cmp >= T(0);
+        if (bil) {
+            du.add_prod(cmp, gam);
+            du.add_lo(cmp * gl_of_state(a.gg0, c));
+        }
+        if (COMP) {
+            T tl = __ldg(&a.q_lo[c]);
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+                tl += __ldg(&a.rec_lo[u * mp + c]) * (Ui[u] - Uj[u]) + __ldg(&a.rec_lo[(3 + u) * mp + c]) * Ui[3 + u] -
+                      __ldg(&a.rec_lo[(6 + u) * mp + c]) * Uj[3 + u];
+            du.add_lo(tl);
+        }
+        const T gr = du.value();
+        o.gref[t] = gr;
+        o.grs[t] = gr;
+        if (t < o.nc) {
+            const T dm = o.ds[t];   // 0 after the fold
+            const T pi = (bil || dm > -gam) ? gr : (gr < T(0) ? gr : T(0));
+            const T api = (pi < T(0) ? -pi : pi) * __ldg(&a.isc[c]);
+            acc[3] = api > acc[3] ? api : acc[3];
+            acc[0] += pi * pi;
+        }
+    }
+}
+
+// Refresh, first half: every owned slot folds delta into (gamma_ref,
+// gamma_lo) as fold_delta does and publishes it in buffer 0; ghost slots
+// clear delta and take the owner's gamma_ref after the next barrier
+// (ghost_ref1).
+template <typename T>
+__device__ __forceinline__ void fold1(const SolveArgs<T>& a, const Own1<T>& o)
+{
+    const bool has_comp = a.comp != nullptr;
+#pragma unroll 1
+    for (int t = threadIdx.x; t < o.nt; t += blockDim.x) {
+        if (t < o.nc) {
+            const int c = o.c0 + t;
+            const T d = o.ds[t], gr = o.gam[t], gl = gl_of_state(a.gg0, c);
+            const bool bil = has_comp && (o.loc[t] & kBil);
+            T hi = T(0), lo = T(0);
+            if (bil || d > -gr) {
+                T s, e;
+                two_sum(gr, d, s, e);
+                const T l = gl + e;
+                hi = s + l;
+                lo = l - (hi - s);
+                if (!bil && (hi < T(0) || (hi == T(0) && lo < T(0)))) { hi = T(0); lo = T(0); }
+            }
+            o.gam[t] = hi;
+            st_ref(a.gg0, c, hi, lo);
+        }
+        o.ds[t] = T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void ghost_ref1(const SolveArgs<T>& a, const Own1<T>& o)
+{
+    for (int g = threadIdx.x; g < o.ng; g += blockDim.x) o.gam[o.nc + g] = __ldcg(&a.gg0[4 * (size_t)o.gid[g] + 2]);
+}
+
+// cp.async of the last barrier's block sums ([4][nbp] of buffer src) into
+// shared memory; the threads that issue it wait for it in tot_wait.
+template <typename T>
+__device__ __forceinline__ void tot_fetch(const Own1<T>& o, const T* src)
+{
+    const int chunks = (int)(4 * (size_t)o.nbp * sizeof(T) / 16);
+    if ((int)threadIdx.x < chunks) {
+        for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<unsigned char*>(o.tot) + 16 * (size_t)q);
+            const unsigned char* s = reinterpret_cast<const unsigned char*>(src) + 16 * (size_t)q;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(s) : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+}
+__device__ __forceinline__ void tot_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Warp w's share of the block sums: each warp's (sum, sum, sum, max) into red[w].
+template <typename T>
+__device__ __forceinline__ void warp_partial(T v[4], T (*red)[4])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) v[u] += __shfl_down_sync(0xffffffffu, v[u], o);
+        const T mx = __shfl_down_sync(0xffffffffu, v[3], o);
+        v[3] = mx > v[3] ? mx : v[3];
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) red[threadIdx.x >> 5][u] = v[u];
+    }
+}
+
+// Warp 0 after a block barrier: the block's sums over red, lane 0 stores
+// them in dst ([4][stride]).
+template <typename T>
+__device__ __forceinline__ void block_store(T (*red)[4], T* dst, int stride)
+{
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    T w[4] = {T(0), T(0), T(0), T(0)};
+    if (lane < nw) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = red[lane][u];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) w[u] += __shfl_down_sync(0xffffffffu, w[u], o);
+        const T mx = __shfl_down_sync(0xffffffffu, w[3], o);
+        w[3] = mx > w[3] ? mx : w[3];
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dst[u * stride + blockIdx.x] = w[u];
+    }
+}
+
+// One warp: the grid totals of the fetched block sums (fixed order, so
+// every block gets the same numbers); every lane returns them.
+template <typename T>
+__device__ __forceinline__ void warp_totals(const Own1<T>& o, int nb, T tot[4])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const T* row = o.tot + (size_t)u * o.nbp;
+        T w = T(0);
+        for (int b = lane; b < nb; b += 32) {
+            const T x = row[b];
+            w = u == 3 ? (x > w ? x : w) : w + x;
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            const T y = __shfl_xor_sync(0xffffffffu, w, s);
+            w = u == 3 ? (y > w ? y : w) : w + y;
+        }
+        tot[u] = w;
+    }
+}
+
+// Loop states: what the last constraint phase was (its sums are what the
+// last barrier published), and the decision taken for the next rod phase.
+enum { C_NONE1 = 0, C_STEP1 = 1, C_REF1 = 2 };
+enum { K_STEP1 = 0, K_REF1 = 1, K_STOP1 = 2 };
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ Shared1<T> sh;
+    if (a.fault == 1 && blockIdx.x == 0) return;   // test hook: this block never arrives
+    Own1<T> o;
+    o.r0 = a.bstart[blockIdx.x];
+    o.r1 = a.bstart[blockIdx.x + 1];
+    o.c0 = a.rowP[o.r0];
+    o.c1 = a.rowP[o.r1];
+    o.q0 = a.rowQ[o.r0];
+    o.q1 = a.rowQ[o.r1];
+    o.nc = o.c1 - o.c0;
+    o.cap_r = o.r1 - o.r0;
+    const int nb = (int)gridDim.x;
+    o.nbp = (nb + 3) & ~3;
+    stage_in1(a, o, dyn, sh);
+    T* part = reinterpret_cast<T*>(a.partials);   // [2][4][nbp]
+    const size_t pstride = 4 * (size_t)o.nbp;
+    unsigned epoch = 0;
+    int* s_ok = &sh.ng;   // the barrier's broadcast word (ng is not needed after staging)
+    auto barrier = [&]() { return grid_barrier(a.bar, (unsigned)nb * ++epoch, a.flags, a.wait_cycles, s_ok); };
+    const int warp = threadIdx.x >> 5;
+    // step state, kept by thread 32 (warp 1, lane 0)
+    T alpha0 = T(1), pimax = T(0);
+    int k = 0, since = 0, hist = 0;
+    bool ok = true;
+
+    // initial reference at gamma_0 and the line step alpha_0 = pi.pi / pi.A.pi
+    rod_pass1<T, A_REF>(a, o, T(0));
+    ok = barrier();
+    int pw = 0;   // block-sum buffer the next barrier publishes
+    if (ok) {
+        T v[4] = {T(0), T(0), T(0), T(0)};
+        con_pass_ref1(a, o, v);
+        __syncthreads();   // gref and g of every slot before the line step reads them
+        v[1] = rod_pass1<T, A_PG>(a, o, T(0));
+        warp_partial(v, sh.red);
+        __syncthreads();
+        if (warp == 0) block_store(sh.red, part + pw * pstride, o.nbp);
+        ok = barrier();
+    }
+    if (ok) {
+        tot_fetch(o, part + pw * pstride);
+        tot_wait();
+        __syncthreads();
+        if (warp == 1) {
+            T tot[4];
+            warp_totals(o, nb, tot);
+            if (threadIdx.x == 32) {
+                pimax = tot[3];
+                const double pap = (double)tot[1];
+                double al = (double)tot[0] / pap;
+                if (!(pap > 0.0) || !isfinite(al) || !(al > 0.0) || !isfinite((T)al)) al = 1.0;
+                alpha0 = (T)al;
+                sh.alpha = alpha0;
+                sh.kind = (!above_tol(a, pimax) || a.max_iter <= 0) ? K_STOP1 : K_STEP1;
+            }
+        }
+        __syncthreads();
+        pw ^= 1;
+    }
+    int cprev = C_NONE1;      // the constraint phase whose sums the last barrier published
+    bool rstep = false;       // the last rod phase formed a step (its delta is still to be stored)
+    T alpha_prev = T(0);
+    int db = 0;               // dU buffer the next step's rod phase writes
+    while (ok && sh.kind != K_STOP1) {
+        const int pr = pw ^ 1;   // buffer the last barrier published
+        if (cprev != C_NONE1) tot_fetch(o, part + pr * pstride);
+        T v[4] = {T(0), T(0), T(0), T(0)};
+        if (rstep) con_pass_step1(a, o, alpha_prev, db ? a.U : a.U2, v);
+        const int ccur = rstep ? C_STEP1 : C_NONE1;
+        warp_partial(v, sh.red);
+        tot_wait();
+        __syncthreads();
+        if (warp == 0) {
+            block_store(sh.red, part + pw * pstride, o.nbp);
+        } else if (warp == 1) {
+            T tot[4] = {T(0), T(0), T(0), T(0)};
+            if (cprev != C_NONE1) warp_totals(o, nb, tot);
+            if (threadIdx.x == 32) {
+                if (rstep) ++k;
+                int kind = K_STEP1;
+                T an = sh.alpha;
+                if (cprev == C_STEP1) {
+                    // sums of (s_{k-2}, y_{k-2}) and max |pi| at the iterate before the slots'
+                    pimax = tot[3];
+                    ++since;
+                    const bool below = !above_tol(a, pimax);
+                    if ((below && since >= 2) || (a.refresh > 0 && since >= a.refresh) || k >= a.max_iter) {
+                        kind = K_REF1;
+                    } else {
+                        const T ss = tot[0], sy = tot[1], yy = tot[2];
+                        an = (hist & 1) == 0 ? ss / sy : sy / yy;
+                        if (!(sy > T(0)) || !isfinite(an) || !(an > T(0))) an = alpha0;
+                        ++hist;
+                    }
+                } else if (cprev == C_REF1) {
+                    // the fresh reference's exact residual: the slots' step from it is dropped on a stop
+                    pimax = tot[3];
+                    since = 0;
+                    if (!above_tol(a, pimax) || k - 1 >= a.max_iter) {
+                        kind = K_STOP1;
+                        --k;
+                    }
+                } else if (k >= a.max_iter) {
+                    kind = K_REF1;   // the cap reached before any step's sums came back
+                }
+                sh.alpha = an;
+                sh.kind = kind;
+            }
+        }
+        __syncthreads();
+        const int kind = sh.kind;
+        if (kind == K_STOP1) break;
+        int cpub = ccur;
+        if (kind == K_REF1) {
+            fold1(a, o);
+            if (!(ok = barrier())) break;
+            ghost_ref1(a, o);
+            __syncthreads();
+            rod_pass1<T, A_REF>(a, o, T(0));
+            if (!(ok = barrier())) break;
+            T w[4] = {T(0), T(0), T(0), T(0)};
+            con_pass_ref1(a, o, w);
+            warp_partial(w, sh.red);
+            __syncthreads();
+            if (warp == 0) block_store(sh.red, part + pw * pstride, o.nbp);
+            cpub = C_REF1;
+        }
+        const T al = sh.alpha;
+        rod_pass1<T, A_STEP>(a, o, al);
+        copy_out1(db ? a.U2 : a.U, o);
+        alpha_prev = al;
+        rstep = true;
+        db ^= 1;
+        if (!(ok = barrier())) break;
+        pw ^= 1;
+        cprev = cpub;
+    }
+    if (!ok) return;
+    // every solve ends on a fresh reference: gamma = gamma_ref + gamma_lo
+    // (buffer 0) and delta = 0, so dU = 0
+    for (int t = threadIdx.x; t < o.nc; t += blockDim.x) st_dg(a.gg0, o.c0 + t, T(0), o.gref[t]);
+    {
+        typename V2<T>::t z;
+        z.x = T(0);
+        z.y = T(0);
+        typename V2<T>::t* g = reinterpret_cast<typename V2<T>::t*>(a.U + 6 * (size_t)o.r0);
+        for (int q = threadIdx.x; q < 3 * (o.r1 - o.r0); q += blockDim.x) g[q] = z;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 32) {
+        a.out[1] = (double)alpha0;
+        a.flags[F_FINAL] = 0;
+        a.flags[F_ITERS] = k;
+        a.out[0] = a.hD * (double)pimax;
+    }
+}
+
+// One warp per block b: the one-barrier kernel's shared-memory share
+// (ghosts counted from the block's other-side entries); a share whose slot
+// or rod count exceeds the 15-bit local indices does not fit.
+__global__ void k_stage_need1(int nb, int esize, const int* __restrict__ bstart, const int* __restrict__ rowP,
+                              const int* __restrict__ rowQ, const int* __restrict__ qlist,
+                              unsigned long long* __restrict__ need)
+{
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (b >= nb) return;   // uniform per warp
+    const int r0 = bstart[b], r1 = bstart[b + 1];
+    const int c0 = rowP[r0], c1 = rowP[r1], q0 = rowQ[r0], q1 = rowQ[r1];
+    int ng = 0;
+    for (int k = q0 + lane; k < q1; k += 32) {
+        const int c = qlist[k];
+        ng += c < c0 || c >= c1;
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) ng += __shfl_down_sync(0xffffffffu, ng, s);
+    if (lane == 0) {
+        const size_t nt = (size_t)(c1 - c0) + ng, nr = r1 - r0;
+        unsigned long long bytes = staged1_bytes(esize, nt, ng, nr, q1 - q0, nb);
+        if (nt > (size_t)kMaxSlots || nr > (size_t)kMaxSlots) bytes = ~0ull;
+        atomicMax(need, bytes);
+    }
+}
+
 // Batches: every cluster takes whole systems from a queue (largest first)
 // and runs the BBPGD of each on its own, with the system's own step sizes,
 // residual and stopping test.  A system's rods are the contiguous ranks
@@ -1218,7 +1946,7 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.n = n; a.m = m; a.np = (int)ctx->max_rods; a.mp = (int)ctx->max_pairs;
     a.rowP = ctx->rowP; a.rowQ = ctx->rowQ; a.qlist = ctx->qlist; a.ci = ctx->ci; a.cj = ctx->cj;
     a.rec = sb.rec; a.qe = sb.qe; a.q = sb.q; a.ax = sb.ax;
-    a.gg0 = sb.gg[0]; a.gg1 = sb.gg[1]; a.U = sb.U; a.Uref = sb.Uref; a.gref = sb.gref;
+    a.gg0 = sb.gg[0]; a.gg1 = sb.gg[1]; a.U = sb.U; a.U2 = sb.U2; a.Uref = sb.Uref; a.gref = sb.gref;
     // float32 iterations work on increments over a reference that takes
     // the iterate every kRefresh iterations (and to confirm convergence);
     // float64 needs no refresh
@@ -1261,24 +1989,51 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     const int nbw = (int)blocks + 1;
     k_partition<<<(nbw * 32 + 255) / 256, 256, 0, ctx->stream>>>(n, m, (int)blocks, ctx->rowP, ctx->rowQ, ctx->bstart);
     ++ctx->launches;
+    // counters C_SMEM, C_MAXRODS (adjacent) and C_SMEM1
     if ((e = cudaMemsetAsync(ctx->dcount + C_SMEM, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ctx->dcount + C_MAXRODS, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
+        (e = cudaMemsetAsync(ctx->dcount + C_MAXRODS, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ctx->dcount + C_SMEM1, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
         return e;
     k_stage_need<<<((int)blocks + 127) / 128, 128, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart, ctx->rowP,
                                                                   ctx->rowQ, ctx->dcount + C_SMEM,
                                                                   ctx->dcount + C_MAXRODS);
     ++ctx->launches;
-    unsigned long long need = 0, maxrods = 0;
+    if (ctx->solve_barriers == 1) {
+        k_stage_need1<<<((int)blocks * 32 + 255) / 256, 256, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart,
+                                                                            ctx->rowP, ctx->rowQ, ctx->qlist,
+                                                                            ctx->dcount + C_SMEM1);
+        ++ctx->launches;
+    }
+    unsigned long long need = 0, maxrods = 0, need1 = 0;
     if ((e = cudaMemcpyAsync(&need, ctx->dcount + C_SMEM, sizeof(need), cudaMemcpyDeviceToHost, ctx->stream)) !=
             cudaSuccess ||
         (e = cudaMemcpyAsync(&maxrods, ctx->dcount + C_MAXRODS, sizeof(maxrods), cudaMemcpyDeviceToHost,
                              ctx->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&need1, ctx->dcount + C_SMEM1, sizeof(need1), cudaMemcpyDeviceToHost, ctx->stream)) !=
+            cudaSuccess ||
         (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
         return e;
     int optin = 0;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device)) != cudaSuccess)
         return e;
     const long long budget = (long long)optin / bps - (long long)sizeof(Shared<T>) - 1024;
+    if ((e = cudaMemsetAsync(ctx->bar, 0, 4 * sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
+    if (ctx->solve_barriers == 1 && threads >= 64 && need1 > 0 && (long long)need1 <= budget) {
+        // one grid barrier per iteration: every block's share and its ghosts fit
+        const void* fn1 = (const void*)k_bbpgd1<T>;
+        if ((e = cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need1)) != cudaSuccess)
+            return e;
+        int per_sm1 = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, fn1, threads, (size_t)need1)) != cudaSuccess)
+            return e;
+        if ((long long)per_sm1 * ctx->num_sms >= blocks) {
+            void* args1[] = {&a};
+            ++ctx->launches;
+            ctx->last_solver = 1;
+            return cudaLaunchCooperativeKernel(fn1, dim3((unsigned)blocks), dim3(threads), args1, (size_t)need1,
+                                               ctx->stream);
+        }
+    }
     const bool staged = (long long)need <= budget && (long long)n / blocks < 60000;
     // global-memory blocks still take their rods in count order when the
     // order (10 bytes of scratch per rod) fits
@@ -1292,9 +2047,9 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem)) != cudaSuccess) return e;
     if ((long long)per_sm * ctx->num_sms < blocks) return cudaErrorCooperativeLaunchTooLarge;
-    if ((e = cudaMemsetAsync(ctx->bar, 0, 4 * sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
     void* args[] = {&a};
     ++ctx->launches;
+    ctx->last_solver = staged ? 2 : 3;
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, ctx->stream);
 }
 
@@ -1343,6 +2098,7 @@ static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int
     if (nclusters > ns) nclusters = ns;   // a cluster per system at most
     cfg.gridDim = dim3((unsigned)(nclusters * ctx->batch_cluster));
     ++ctx->launches;
+    ctx->last_solver = 4;
     return cudaLaunchKernelEx(&cfg, k_bbpgd_sys<T>, a, ns, (const long long*)ctx->sysoff, (const int*)ctx->sys_order,
                               ctx->dcount + C_QUEUE, ctx->sys_iters, ctx->sys_res);
 }

@@ -157,6 +157,40 @@ def test_autograd_function_matches_adjoint():
         assert float(eta.grad) == pytest.approx(ref["eta"], rel=1e-7)
 
 
+def test_autograd_backward_uses_its_forward_parameters():
+    """Two forwards on one context with different viscosities (and a
+    different dt and precision in between) before the first backward: each
+    backward gives the oracle gradient at its own forward's parameters, and
+    the context keeps the parameters it held before the backward."""
+    from paper_2109_08206_gb300.autograd import constrained_step
+    s, T = small(2, 30, 10.0, 3.0)
+    with ctx_for(s, A.FP64) as ctx:
+        outs = []
+        for eta_v in (0.7, 1.9):
+            x = dev(s.x).requires_grad_(True)
+            q = dev(s.quat).requires_grad_(True)
+            f = dev(s.f_nc).requires_grad_(True)
+            eta = torch.tensor(eta_v, dtype=torch.float64, device="cuda", requires_grad=True)
+            xn, qn = constrained_step(ctx, x, q, f, eta)
+            outs.append((eta_v, x, q, f, eta, ((xn - dev(T)) ** 2).sum()))
+        p = ctx.params
+        p.dt = 2e-3
+        p.precision = A.MIXED
+        ctx.set_params(p)
+        before = bytes(ctx.params)
+        for eta_v, x, q, f, eta, loss in outs:
+            loss.backward()
+            s2 = W.RodSystem(x=s.x, quat=s.quat, f_nc=s.f_nc, box=s.box, diameter=s.diameter, length=s.length,
+                             viscosity=eta_v, dt=s.dt, delta_c=s.delta_c)
+            ref_L, ref, _ = ADJ.loss_and_grad(s.x, s.quat, s.f_nc, O.problem_of(s2), T)
+            assert float(loss.detach()) == pytest.approx(ref_L, rel=1e-10)
+            assert rel(host(x.grad), ref["x"]) < 1e-7
+            assert rel(host(q.grad), ref["quat"]) < 1e-7
+            assert rel(host(f.grad), ref["fnc"]) < 1e-7
+            assert float(eta.grad) == pytest.approx(ref["eta"], rel=1e-7)
+            assert bytes(ctx.params) == before
+
+
 # ----------------------------------------------------- the 2e4-rod workload
 
 @pytest.fixture(scope="module")

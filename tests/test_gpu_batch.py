@@ -4,7 +4,7 @@ system by system.
 Each system of a batch is an independent periodic suspension with its own
 box and rod length; the oracle steps every system alone.  Bars as for the
 single-system step: pair lists bit-exact per system (global indices shifted
-by the system's rod offset; the 1e-9 D band of delta_c excepted), post-step
+by the system's rod offset, no mismatch excused), post-step
 centres and quaternions within 1e-6 D (float64) / 2e-5 D (mixed), U within
 1e-6 / 1e-3 relative L2.  Small systems with one or two cells per edge make
 several periodic images of one pair close (each is a separate constraint).

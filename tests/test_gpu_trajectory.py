@@ -42,6 +42,21 @@ def test_generator_words_bit_exact(seed, step):
             assert np.array_equal(got[i, 4 * h:4 * h + 4], want)
 
 
+def test_generator_first_word_block_is_published_known_answer():
+    """Rod 0, step 0, seed 0 is Philox4x32-10 at counter 0 and key 0, whose
+    output its authors publish (Salmon et al., SC'11): the GPU generator is
+    pinned to the definition itself, not only to the oracle."""
+    import json
+    from pathlib import Path
+    kat = json.loads((Path(__file__).parent / "golden" / "philox4x32_10_kat.json").read_text())
+    v = kat["vectors"][0]
+    assert all(int(w, 16) == 0 for w in v["ctr"] + v["key"])
+    s = W.tiny_system(1, 4, box=40.0)
+    with ctx_of(s) as ctx:
+        got = host(ctx.random_words(4, 0, 0)).view(np.uint32)
+    assert [int(w) for w in got[0, :4]] == [int(w, 16) for w in v["out"]]
+
+
 def test_brownian_forces_match_oracle():
     s = W.tiny_system(2, 500, box=40.0, length=4.0)
     fext = np.random.default_rng(1).standard_normal((s.n, 6))

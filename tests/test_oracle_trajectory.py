@@ -5,7 +5,9 @@ confining walls, and the first-order convergence in h of the residual
 overlaps that the linearised constraints leave (Appendix, "Temporal
 discretization": residual overlaps vanish as h -> 0 at first order).
 """
+import json
 import math
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -23,6 +25,19 @@ def test_normals_are_standard_and_independent():
     assert stats.kstest(z.ravel(), "norm").pvalue > 1e-4
     c = np.corrcoef(z.T)
     assert np.abs(c - np.eye(6)).max() < 4.0 / math.sqrt(z.shape[0])
+
+
+def test_generator_matches_published_known_answers():
+    """Philox4x32-10 against the known-answer vectors its authors publish
+    (Salmon et al., SC'11): pins word order, the hi/lo halves of the
+    products and the key schedule, which the statistics below cannot see."""
+    kat = json.loads((Path(__file__).parent / "golden" / "philox4x32_10_kat.json").read_text())
+    assert len(kat["vectors"]) == 3
+    for v in kat["vectors"]:
+        ctr = [int(w, 16) for w in v["ctr"]]
+        key = [int(w, 16) for w in v["key"]]
+        out = [int(w) for w in O.philox4x32(ctr, key)]
+        assert out == [int(w, 16) for w in v["out"]], (v, [hex(w) for w in out])
 
 
 def test_generator_words_differ_across_counters_and_seeds():

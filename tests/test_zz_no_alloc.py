@@ -4,8 +4,10 @@ It serves callers that may not allocate device memory (a memory manager
 owning the device budget, or a loop where cudaMalloc would stall other
 work): its workspace is a static device array of the library.  Checked
 against the context-based aLENS_solve_lcp on the same inputs, twice in a row
-(the shared array keeps the previous call's contents), and for its size
-limits.  The file name makes pytest collect it last.
+(the shared array keeps the previous call's contents), at its size limits
+(4096 rods and 16384 constraints, where a slip in the workspace layout would
+overrun the array), with the device's free memory unchanged across a call,
+and for the sizes it rejects.  The file name makes pytest collect it last.
 """
 import ctypes as C
 
@@ -80,4 +82,54 @@ def test_noalloc_rejects_sizes_beyond_its_limits(problem):
     gamma = torch.zeros(pairs.shape[0], dtype=torch.float64, device="cuda")
     st, _ = call_noalloc(params, big, pairs, dgeom, q, gamma)
     assert st == 2   # ALENS_ERR_CAPACITY
+    assert np.all(gamma.cpu().numpy() == 0.0)
+
+
+@pytest.fixture(scope="module")
+def largest():
+    """4096 rods and exactly 16384 constraints: the first 16384 pairs (in
+    sorted order) of a seeded suspension dense enough to have more."""
+    s = W.random_system(41, MAX_RODS, 64.0, forces="unit", tol=1e-8)
+    pb = O.problem_of(s)
+    pairs = O.find_pairs(s.x, s.quat, pb)
+    assert pairs.shape[0] > MAX_PAIRS
+    pairs = pairs[:MAX_PAIRS]
+    asm = O.assemble(s.x, s.quat, s.f_nc, pb, pairs)
+    dev = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    return s, pb, dev(s.quat), dev(pairs, torch.int32), dev(asm["dgeom"]), dev(asm["q"]), asm, pairs
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(A.FP64, 1e-8, 1e-5), (A.MIXED, 1e-6, 1e-3)])
+def test_noalloc_at_its_limits_allocates_nothing(largest, precision, tol, bar):
+    s, pb, quat, pairs, dgeom, q, asm, pairs_h = largest
+    assert quat.shape[0] == MAX_RODS and pairs.shape[0] == MAX_PAIRS
+    params = A.params_of(s, precision=precision, tol=tol, max_iter=200000)
+    with A.Context(params, s.n, MAX_PAIRS) as ctx:
+        ref, _ = ctx.solve_lcp(quat, pairs, dgeom, q)
+        ref = ref.cpu().numpy()
+    gammas = [torch.zeros(MAX_PAIRS, dtype=torch.float64, device="cuda") for _ in range(3)]
+    torch.cuda.synchronize()
+    st, _ = call_noalloc(params, quat, pairs, dgeom, q, gammas[0])   # loads whatever loads lazily
+    assert st == 0
+    for g in gammas[1:]:
+        free0 = torch.cuda.mem_get_info()[0]
+        st, info = call_noalloc(params, quat, pairs, dgeom, q, g)
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free1 == free0, (free0, free1)
+        assert st == 0 and info.status == 0 and info.residual <= tol and info.iters > 0
+        gh = g.cpu().numpy()
+        assert np.linalg.norm(gh - ref) <= bar * np.linalg.norm(ref)
+        _, r = O.gradient(s.quat, pb, pairs_h, asm["dgeom"], asm["q"], gh)
+        assert r <= tol * 1.05 + (1e-9 if precision == A.FP64 else 2e-7)
+
+
+def test_noalloc_rejects_one_pair_too_many(largest):
+    s, pb, quat, pairs, dgeom, q, asm, pairs_h = largest
+    params = A.params_of(s, precision=A.FP64, tol=1e-8)
+    more = torch.cat([pairs, pairs[-1:]])
+    d2 = torch.cat([dgeom, dgeom[-1:]])
+    q2 = torch.cat([q, q[-1:]])
+    gamma = torch.zeros(MAX_PAIRS + 1, dtype=torch.float64, device="cuda")
+    st, _ = call_noalloc(params, quat, more, d2, q2, gamma)
+    assert st == 2   # ALENS_ERR_CAPACITY, before any work is queued
     assert np.all(gamma.cpu().numpy() == 0.0)
