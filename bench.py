@@ -53,9 +53,15 @@ METRIC_GRAD = ("rod-steps/s of one step plus its adjoint (gradient of the post-s
                "FP32-mixed vs FP64 plain at residual ≤1e-5")
 
 
+METRIC_N1000 = "rod-steps/s at 1e3 rods (periodic cube of side 40), FP64 plain at residual ≤1e-8"
+METRIC_N400K = ("rod-steps/s at 4e5 rods (nematic bundle, volume fraction 0.25), FP32-mixed vs FP64 plain at "
+                "residual ≤1e-5")
+
+
 def metric_of(workload):
     return {"ensemble256": METRIC_ENSEMBLE, "n20k_grad": METRIC_GRAD,
-            "n100k_springs": METRIC_SPRINGS, "n100k_traj": METRIC_TRAJ}.get(workload, METRIC)
+            "n100k_springs": METRIC_SPRINGS, "n100k_traj": METRIC_TRAJ,
+            "n1000_box40": METRIC_N1000, "n400k_nematic": METRIC_N400K}.get(workload, METRIC)
 UNIT = "rod-steps/s"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -77,6 +83,10 @@ def parse():
                     help="diagonal scaling exponent of the BBPGD iteration (default: the library's, 0.5)")
     ap.add_argument("--barriers", type=int, default=None, choices=[1, 2],
                     help="grid barriers per BBPGD iteration (default: the library's, one where it fits)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of the headline step (fp64: the float64 step is the value and no mixed arm runs)")
+    ap.add_argument("--shape", default=None,
+                    help="solver launch shape THREADSxBLOCKS (per SM, or per cluster for a batch); skips tuning")
     return ap.parse_args()
 
 
@@ -164,24 +174,35 @@ def solve_bytes_per_iter(n, m, w):
     return m * (24 * w + 24) + n * (15 * w + 4)
 
 
-def traffic_from_profile(kernel_src: Path, shape):
-    """DRAM bytes of one BBPGD launch from the committed ncu summary, only if
-    the kernel source is unchanged since the capture (sha256 recorded there)
-    and the capture ran in the same launch shape (threads x blocks per SM)."""
-    prof = ROOT / "profiles" / "k_bbpgd_n100k_mixed.md"
-    if not prof.exists():
+def step_other_bytes(n, m, w):
+    """Algorithmic bytes of a step outside the BBPGD iterations: the
+    neighbour search and assembly, N (56 + 24) + N_c (12 + 32 + 11w + 8)
+    (rod state and keys in, pair list, records, q and Phi out), and the
+    update, N (2 x 56 + 6w) (rod state in and out, the constraint velocity)."""
+    return n * (56 + 24) + m * (12 + 32 + 11 * w + 8) + n * (2 * 56 + 6 * w)
+
+
+PROFILE_RECORD = "profiles/k_bbpgd1_n100k_mixed.json"
+
+
+def traffic_from_profile(kernel_src: Path, shape, kernel: str):
+    """DRAM bytes of one BBPGD launch from the committed ncu record
+    (``profiles/k_bbpgd1_n100k_mixed.json``), only if the solver source is
+    unchanged since the capture (its sha256 is recorded there), the capture
+    ran in the same launch shape and the same kernel ran."""
+    path = ROOT / PROFILE_RECORD
+    if not path.exists():
+        return None
+    try:
+        rec = json.loads(path.read_text())
+    except ValueError:
         return None
     sha = hashlib.sha256(kernel_src.read_bytes()).hexdigest()[:16]
-    fields = {}
-    for l in prof.read_text().splitlines():
-        k, sep, v = l.partition(":")
-        if sep and k in ("solve_cu_sha256_16", "launch_shape", "dram_bytes_per_launch"):
-            fields[k] = v.strip()
-    if len(fields) != 3 or fields["solve_cu_sha256_16"] != sha:
+    if rec.get("solve_cu_sha256_16") != sha or rec.get("kernel") != kernel:
         return None
-    if shape is None or fields["launch_shape"] != f"{shape[0]}x{shape[1]}":
+    if shape is None or rec.get("launch_shape") != f"{shape[0]}x{shape[1]}":
         return None
-    return float(fields["dram_bytes_per_launch"])
+    return float(rec["dram_bytes_per_launch"])
 
 
 def spatial_sample(s, target):
@@ -476,18 +497,24 @@ class TrajJob(SingleJob):
                               f"{K} oracle trajectory steps (Brownian forces, FISTA to {args.tol:g}), {t:.2f} s")
 
 
-def make_job(name):
+SEEDS = {"n1000_box40": 1, "n100k_phi010": 2, "n400k_nematic": 3, "n20k_phi015": 5}
+
+
+def make_job(name, sibling=False):
+    """The named workload; sibling=True draws another input of the same class
+    (every seed shifted by 1000), on which the launch shape is tuned."""
     from paper_2109_08206_gb300 import workloads as W
+    d = 1000 if sibling else 0
     if name == "n100k_traj":
-        return TrajJob(W.workload("n100k_phi010"))
+        return TrajJob(W.workload("n100k_phi010", seed=2 + d))
     if name == "n100k_springs":
-        s = W.workload("n100k_phi010", n_springs=0)
-        return SpringJob(s, W.spring_set(s, 50_000, seed=21))
+        s = W.workload("n100k_phi010", n_springs=0, seed=2 + d)
+        return SpringJob(s, W.spring_set(s, 50_000, seed=21 + d))
     if name == "ensemble256":
-        return BatchJob(W.ensemble(seed=1000, count=256))
+        return BatchJob(W.ensemble(seed=1000 + d, count=256))
     if name == "n20k_grad":
-        return GradJob(W.workload("n20k_phi015"))
-    return SingleJob(W.workload(name))
+        return GradJob(W.workload("n20k_phi015", seed=5 + d))
+    return SingleJob(W.workload(name, seed=SEEDS[name] + d))
 
 
 def oracle_step_time(s, tol, reps=1):
@@ -506,6 +533,50 @@ def cpu_cores():
         return int(os.environ.get("OMP_NUM_THREADS") or len(os.sched_getaffinity(0)))
     except Exception:
         return os.cpu_count() or 1
+
+
+def cpu_model():
+    """The host CPU as lscpu names it (model, else vendor), and nproc."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        info = {}
+        for l in out.splitlines():
+            k, _, v = l.partition(":")
+            info[k.strip()] = v.strip()
+        name = info.get("Model name") or info.get("Vendor ID")
+    except Exception:
+        pass
+    return name, os.cpu_count()
+
+
+def cpu_baseline_record(job, args):
+    """The oracle on the job's bounded CPU sample, median of 3 runs with all
+    host cores and median of 3 (1 when a run exceeds 12 s) with one thread."""
+    import oracle as O
+    reps_all = 3
+    times = []
+    sample = None
+    for _ in range(reps_all):
+        rods, t, sample = job.cpu(args)
+        times.append(t)
+    t_all = statistics.median(times)
+    before = O.set_threads(1)
+    try:
+        t1 = []
+        for k in range(3):
+            rods1, t, _ = job.cpu(args)
+            t1.append(t)
+            if t > 12.0:
+                break
+    finally:
+        O.set_threads(before)
+    model, nproc = cpu_model()
+    return {"value": rods / t_all, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": sample + f"; median of {reps_all} runs on all cores",
+            "single_thread": {"value": rods1 / statistics.median(t1), "runs": len(t1),
+                              "s_per_step": statistics.median(t1)},
+            "s_per_step": t_all, "nproc": nproc, "cpu_model": model}
 
 
 def replica_time(ms_local, pg=None, device=None):
@@ -618,18 +689,43 @@ def run_ours(args):
     def max_over_ranks(v):
         return replica_time(v, pg, dev)
 
-    # ---- untimed: the solver's launch shape (autotuned) and, for a batch,
-    # the per-system constraint counts
+    # ---- untimed: the solver's launch shape, tuned on another input of the
+    # same workload class (every seed shifted), so that the timed input is
+    # not the one the shape was picked on; for a batch, the per-system
+    # constraint counts
     import paper_2109_08206_gb300.autotune as T
-    ctx = make_ctx(A.MIXED)
+    kind = "batch" if isinstance(job, BatchJob) else "single"
+    default_shape = T.BATCH_CANDIDATES[0] if kind == "batch" else T.SINGLE_CANDIDATES[0]
+    sib = None if (args.no_tune or args.shape) else make_job(args.workload, sibling=True)
+    if args.shape:
+        default_shape = tuple(int(v) for v in args.shape.lower().split("x"))
+
+    def tune_on_sibling(precision):
+        sx, sq, sf = (torch.as_tensor(v, device=dev) for v in sib.arrays())
+        sctx = sib.context(A, precision, args.tol, stream)
+        if args.scaling is not None:
+            sctx.set_scaling(args.scaling)
+        if args.barriers is not None:
+            sctx.set_solver_schedule(args.barriers)
+        try:
+            return sib.tune(T, sctx, sx, sq, sf, precision)
+        finally:
+            sctx.close()
+
+    head = A.FP64 if args.precision == "fp64" else A.MIXED
+    wh = 8 if head == A.FP64 else 4   # bytes per working-precision value
+    if head == A.FP64:
+        args.skip_fp64 = True   # the headline is the float64 step itself
+    ctx = make_ctx(head)
+    if args.shape:
+        T.apply(ctx, kind, default_shape)
     tuned = None
-    if not args.no_tune:
-        xx, qq = x0.clone(), q0.clone()
-        shape, times = job.tune(T, ctx, xx, qq, f, A.MIXED)
-        tuned = {"shape": list(shape), "ms_solve": times}
-        del xx, qq
-    # the library's default shape: 1024 threads, as many blocks per SM as fit (one, at 64 registers)
-    shape_now = tuple(tuned["shape"]) if tuned else (1024, 1)
+    if sib is not None:
+        shape, times = tune_on_sibling(head)
+        T.apply(ctx, kind, shape)
+        tuned = {"shape": list(shape), "ms_solve": times,
+                 "tuned_on": f"{sib.name}, another seed of the same workload class"}
+    shape_now = tuple(tuned["shape"]) if tuned else default_shape
     if isinstance(job, BatchJob):
         pr = torch.empty((max_pairs, 3), dtype=torch.int32, device=dev)
         xx, qq = x0.clone(), q0.clone()
@@ -646,7 +742,7 @@ def run_ours(args):
         gpu_id = None
     clk = Clocks(gpu_id).__enter__()   # sampled across every timed region below
     t0 = time.perf_counter()
-    ms, infos, sbytes = timed(ctx, args.steps, args.warmup)
+    ms, infos, sbytes = timed(ctx, args.steps, args.warmup, w=wh)
     barrier()
     wall = time.perf_counter() - t0
     ms_step = max_over_ranks(statistics.mean(ms))
@@ -657,24 +753,54 @@ def run_ours(args):
     m = infos[-1]["n_pairs"]
     res = max(i["residual"] for i in infos)
     launches = sum(i["launches"] for i in infos)
-    b_iter = solve_bytes_per_iter(n, m, 4)
+    b_iter = solve_bytes_per_iter(n, m, wh)
     alg_bytes = statistics.mean(sbytes)
     peak, peak_kind = peaks()
     achieved = alg_bytes / (ms_solve / 1e3) / 1e9
-    traffic = traffic_from_profile(ROOT / "paper_2109_08206_gb300" / "csrc" / "solve.cu", shape_now) \
+    solver = infos[-1].get("solver")
+    tn = "double" if head == A.FP64 else "float"
+    kernel = {1: f"k_bbpgd1<{tn}>", 2: f"k_bbpgd<{tn},1>", 3: f"k_bbpgd<{tn},0>",
+              4: f"k_bbpgd_sys<{tn}>"}.get(solver, f"k_bbpgd<{tn}>")
+    traffic = traffic_from_profile(ROOT / "paper_2109_08206_gb300" / "csrc" / "solve.cu", shape_now, kernel) \
         if args.workload == "n100k_phi010" else None   # the committed capture is of this workload
+    # the whole step against the same peak: solve bytes plus the search,
+    # assembly and update bytes (the adjoint's are not counted: no step fraction for it)
+    step_bytes = alg_bytes + spc * step_other_bytes(n, m, wh)
+    step_frac = None if isinstance(job, GradJob) else step_bytes / (ms_step / 1e3) / 1e9 / peak
+
+    # ---- the library's default launch shape on the timed input (the
+    # headline runs the shape tuned on the sibling input)
+    default_run = None
+    if tuned and tuple(tuned["shape"]) != tuple(default_shape):
+        T.apply(ctx, kind, default_shape)
+        msd, infd, _ = timed(ctx, max(3, args.steps // 2), 1, w=wh)
+        T.apply(ctx, kind, shape_now)
+        msd_step = max_over_ranks(statistics.mean(msd))
+        default_run = {"shape": list(default_shape), "value": replica_value(msd_step, n * spc, ws),
+                       "ms_per_step": msd_step, "bbpgd_iters": statistics.mean(i["iters"] for i in infd),
+                       "ms_solve": statistics.mean(i["ms_solve"] for i in infd)}
 
     # ---- FP64 plain at the same residual
     fp64 = None
     if not args.skip_fp64:
         ctx64 = make_ctx(A.FP64)
-        if not args.no_tune:
-            xx, qq = x0.clone(), q0.clone()
-            job.tune(T, ctx64, xx, qq, f, A.FP64)
-            del xx, qq
+        shape64 = default_shape
+        if args.shape:
+            T.apply(ctx64, kind, default_shape)
+        if sib is not None:
+            shape64, _ = tune_on_sibling(A.FP64)
+            T.apply(ctx64, kind, shape64)
         ms64, inf64, sb64 = timed(ctx64, max(2, args.steps // 2), 1, w=8)
         ms64_step = max_over_ranks(statistics.mean(ms64))
+        ms64_solve = statistics.mean(i["ms_solve"] for i in inf64)
         fp64 = {"value": replica_value(ms64_step, n * spc, ws), "unit": UNIT, "ms_per_step": ms64_step,
+                "launch_shape": list(shape64),
+                "solver_kernel": {1: "k_bbpgd1<double>", 2: "k_bbpgd<double,1>", 3: "k_bbpgd<double,0>",
+                                  4: "k_bbpgd_sys<double>"}.get(inf64[-1].get("solver")),
+                "roofline_frac": statistics.mean(sb64) / (ms64_solve / 1e3) / 1e9 / peak,
+                "step_frac": None if isinstance(job, GradJob) else
+                (statistics.mean(sb64) + spc * step_other_bytes(n, inf64[-1]["n_pairs"], 8))
+                / (ms64_step / 1e3) / 1e9 / peak,
                 "bbpgd_iters": statistics.mean(i["iters"] for i in inf64),
                 **({"cg_iters": statistics.mean(i["cg_iters"] for i in inf64),
                     "ms_adjoint": statistics.mean(i["ms_adjoint"] for i in inf64)} if "cg_iters" in inf64[0] else {}),
@@ -700,13 +826,18 @@ def run_ours(args):
     mixed_vs_fp64 = None
     if not args.skip_fp64:
         outs = {}
+        plain = type(job) is SingleJob
         for prec in (A.MIXED, A.FP64):
             c2 = make_ctx(prec)
             xx, qq = x0.clone(), q0.clone()
             gam = torch.empty(max_pairs, dtype=torch.float64, device=dev)
-            inf = SingleJob.step(job, c2, xx, qq, f, gamma_out=gam) if isinstance(job, (GradJob, TrajJob)) \
-                else job.step(c2, xx, qq, f, gamma_out=gam)
-            outs[prec] = (xx, qq, gam[: inf.n_pairs].clone())
+            kw = {"gamma_out": gam}
+            if plain:
+                kw["pairs_out"] = torch.empty((max_pairs, 3), dtype=torch.int32, device=dev)
+            inf = SingleJob.step(job, c2, xx, qq, f, **kw) if isinstance(job, (GradJob, TrajJob)) \
+                else job.step(c2, xx, qq, f, **kw)
+            outs[prec] = (xx, qq, gam[: inf.n_pairs].clone(),
+                          kw["pairs_out"][: inf.n_pairs].clone() if plain else None)
             c2.close()
         dx = outs[A.MIXED][0] - outs[A.FP64][0]
         boxt = torch.as_tensor(job.periodic_box(), device=dev)
@@ -715,15 +846,24 @@ def run_ours(args):
         mixed_vs_fp64 = {"max_dx_over_D": float(dx.abs().max()),
                          "gamma_rel_l2": float(torch.linalg.norm(g32 - g64) / torch.linalg.norm(g64)),
                          "max_dquat": float((outs[A.MIXED][1] - outs[A.FP64][1]).abs().max())}
+        if plain and rank == 0:
+            # the float64 oracle's residual (rod diameters) of each step's
+            # gamma, on its own assembly of the same pair list
+            import oracle as O
+            s = job.s
+            pb = O.problem_of(s)
+            for prec, key in ((A.MIXED, "oracle_residual_mixed"), (A.FP64, "oracle_residual_fp64")):
+                pr_h = outs[prec][3].cpu().numpy()
+                asm = O.assemble(s.x, s.quat, s.f_nc, pb, pr_h)
+                _, r = O.gradient(s.quat, pb, pr_h, asm["dgeom"], asm["q"], outs[prec][2].cpu().numpy())
+                mixed_vs_fp64[key] = float(r)
     ctx.close()
 
     if rank != 0:
         return
     cpu = None
     if not args.skip_cpu and ws == 1:
-        rods, t_cpu, sample = job.cpu(args)
-        cpu = {"value": rods / t_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample}
-    kernel = "k_bbpgd_sys<float>" if isinstance(job, BatchJob) else "k_bbpgd<float>"
+        cpu = cpu_baseline_record(job, args)
     config = job.config(W, m)
     config.update({"tol": args.tol, "scaling_beta": 0.5 if args.scaling is None else args.scaling,
                    "l2": "flushed (256 MB write) between steps; inputs restored outside the timed region",
@@ -731,7 +871,8 @@ def run_ours(args):
     line = {
         "metric": metric_of(args.workload), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32-mixed (f64 geometry, reference passes and residual test)", "data": "synthetic",
+        "dtype": "f64" if head == A.FP64 else "f32-mixed (f64 geometry, reference passes and residual test)",
+        "data": "synthetic",
         "config": config,
         "bbpgd_iters": statistics.mean(it), "residual": res, "launch_shape": tuned,
         "solver_kernel": {0: None, 1: "one grid barrier per iteration", 2: "two barriers, shared-memory shares",
@@ -750,7 +891,9 @@ def run_ours(args):
         "fp64": fp64, "e2e": e2e, "mixed_vs_fp64": mixed_vs_fp64,
         "roofline": {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_iter": b_iter},
+                     "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_iter": b_iter,
+                     "step_frac": step_frac, "step_bytes": step_bytes},
+        "default_shape": default_run,
         "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary(), "wall_s": wall,
     }
     print(json.dumps(line), flush=True)

@@ -51,6 +51,7 @@ def lib():
         d, i64, vp = C.c_double, C.c_int64, C.c_void_p
         P = C.POINTER(Problem)
         sig = {
+            "orc_set_threads": (C.c_int, [C.c_int]),
             "orc_drag": (None, [d, d, d, vp]),
             "orc_axis": (None, [i64, vp, vp]),
             "orc_wrap": (None, [i64, vp, vp, vp]),
@@ -101,6 +102,12 @@ def problem(box, diameter=1.0, length=10.0, viscosity=1.0, dt=1e-3, delta_c=None
 def problem_of(sys) -> Problem:
     """Problem parameters of a ``workloads.RodSystem``."""
     return problem(sys.box, sys.diameter, sys.length, sys.viscosity, sys.dt, sys.delta_c)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (n <= 0 leaves them); returns
+    the count in force before the call."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def drag(eta, length, diameter):

@@ -42,6 +42,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_API __attribute__((visibility("default")))
 
@@ -68,6 +71,21 @@ static void cross3(const double* a, const double* b, double* c)
 static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 /* Drag coefficients (reading R1).  Section 3 quotes 4 pi eta L / log(2L/D). */
+/* Threads of the parallel loops (timing the CPU baseline on one core and
+ * on all of them); returns the count in force before the call.  No effect
+ * without OpenMP. */
+ORC_API int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    const int before = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return before;
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 ORC_API void orc_drag(double eta, double L, double D, double out[4])
 {
     double zperp = 4.0 * M_PI * eta * L / log(2.0 * L / D);

@@ -21,7 +21,7 @@ from pathlib import Path
 
 _CACHE = Path(__file__).resolve().parent / "_build" / "tune.json"
 
-SINGLE_CANDIDATES = ((1024, 1), (512, 2), (512, 1), (256, 4))
+SINGLE_CANDIDATES = ((1024, 1), (512, 2), (512, 1), (256, 4), (768, 1))
 BATCH_CANDIDATES = ((1024, 8), (1024, 4), (512, 4), (512, 2))
 
 
@@ -50,11 +50,17 @@ def cached(key: str):
     return tuple(e["shape"]) if e else None
 
 
-def _set(ctx, kind, shape):
+def apply(ctx, kind: str, shape):
+    """Set a launch shape ("single": threads x blocks per SM, "batch":
+    threads x blocks per cluster) on a context, e.g. one tuned on another
+    input of the same workload class."""
     if kind == "batch":
         ctx.set_batch_launch(*shape)
     else:
         ctx.set_launch(*shape)
+
+
+_set = apply
 
 
 def _tune(ctx, kind, key, run, candidates, reps):

@@ -8,10 +8,16 @@
 // iteration follows the published projected BB method (Barzilai & Borwein
 // 1988; projected form as in Dai & Fletcher 2005):
 //   gamma_{k+1} = max(0, gamma_k - alpha_k g_k),
-//   s = gamma_{k+1} - gamma_k, y = g_{k+1} - g_k (= A s),
-//   alpha_{k+1} = s.s / s.y on even k, s.y / y.y on odd k (alternating BB1/BB2),
-//   alpha_0 = pi.pi / pi.A.pi for the projected gradient pi at gamma_0,
-//   and alpha_0 again whenever s.y <= 0 or the step is not finite.
+//   s_k = gamma_{k+1} - gamma_k, y_k = g_{k+1} - g_k (= A s_k),
+//   alpha_{k+1} from the pair (s_{k-1}, y_{k-1}) of the iteration before,
+//     s.s / s.y and s.y / y.y in turn (alternating BB1/BB2): the
+//     Barzilai-Borwein step taken one iteration late, a gradient method with
+//     retards (Friedlander, Martinez, Molina & Raydan, SIAM J. Numer. Anal.
+//     36, 1999), which lets the one-barrier solver below form the step
+//     length from sums that arrive with the next barrier; every solver kernel
+//     uses it, so all of them run one method;
+//   alpha_0 = pi.pi / pi.A.pi for the projected gradient pi at gamma_0, for
+//   the first two steps and whenever s.y <= 0 or the step is not finite.
 // Stop when (h/D) max |pi_c| <= tol (pi the projected gradient) or after
 // max_iter iterations.
 //
@@ -787,6 +793,8 @@ template <typename T>
 struct StepState {
     T alpha0, pimax;   // max |pi| of the last test: the residual is (h/D) pimax
     double pp;         // pi.pi at gamma_0 (for alpha_0)
+    T pss, psy, pyy;   // the previous step's s.s, s.y, y.y (the step length lags one iteration)
+    int have, hist;    // previous sums held; BB1/BB2 alternation counter
     int iters, cur, done;
     int since;   // iterations since the last reference refresh
     __device__ __forceinline__ double residual(double hD) const { return hD * (double)pimax; }
@@ -904,6 +912,9 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
     st.alpha0 = T(1);
     st.pimax = T(0);
     st.pp = 0.0;
+    st.pss = st.psy = st.pyy = T(0);
+    st.have = 0;
+    st.hist = 0;
     st.cur = 0;
     st.since = 0;
     st.iters = 0;
@@ -959,8 +970,19 @@ __device__ __forceinline__ void solve_loop(const SolveArgs<T>& a, const Own<T>& 
                 st.cur = cur;
                 st.iters = k + 1;
                 const bool below = !above_tol(a, tot[3]);
-                T an = (k & 1) == 0 ? ss / sy : sy / yy;
-                if (!(sy > T(0)) || !isfinite(an) || !(an > T(0))) an = st.alpha0;
+                // the step length of step k + 1 from (s_{k-1}, y_{k-1}): the
+                // same one-iteration lag as the one-barrier solver, so every
+                // solver kernel runs one method (alpha_0 until a pair is held)
+                T an = st.alpha0;
+                if (st.have) {
+                    an = (st.hist & 1) == 0 ? st.pss / st.psy : st.psy / st.pyy;
+                    if (!(st.psy > T(0)) || !isfinite(an) || !(an > T(0))) an = st.alpha0;
+                    ++st.hist;
+                }
+                st.pss = ss;
+                st.psy = sy;
+                st.pyy = yy;
+                st.have = 1;
                 sh.alpha = an;
                 // float32: a residual below tol is confirmed on a fresh
                 // reference before the loop stops (the increments since the

@@ -47,21 +47,38 @@ def test_batch_solve_bytes_sum_over_systems():
 
 
 def test_roofline_traffic_only_for_the_captured_source_and_shape(tmp_path, monkeypatch):
-    # the committed ncu summary carries the kernel source's hash and the launch
-    # shape; its per-launch DRAM bytes are reported only while both match
+    # the committed ncu record carries the solver source's hash, the launch
+    # shape and the kernel; its per-launch DRAM bytes are reported only while
+    # all three match
     import hashlib
+    import json
     src = tmp_path / "solve.cu"
     src.write_text("// kernel source\n")
     sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
     prof = tmp_path / "profiles"
     prof.mkdir()
-    (prof / "k_bbpgd_n100k_mixed.md").write_text(
-        f"# summary\n\nsolve_cu_sha256_16: {sha}\nlaunch_shape: 512x2\niterations: 182\n"
-        "dram_bytes_per_launch: 66724864\n")
+    (tmp_path / bench.PROFILE_RECORD).write_text(json.dumps(
+        {"kernel": "k_bbpgd1<float>", "solve_cu_sha256_16": sha, "launch_shape": "1024x1", "iterations": 253,
+         "dram_bytes_per_launch": 44029440}))
     monkeypatch.setattr(bench, "ROOT", tmp_path)
-    assert bench.traffic_from_profile(src, (512, 2)) == 66724864.0
-    assert bench.traffic_from_profile(src, (1024, 1)) is None
-    assert bench.traffic_from_profile(src, None) is None
+    assert bench.traffic_from_profile(src, (1024, 1), "k_bbpgd1<float>") == 44029440.0
+    assert bench.traffic_from_profile(src, (512, 2), "k_bbpgd1<float>") is None
+    assert bench.traffic_from_profile(src, (1024, 1), "k_bbpgd<float,1>") is None
+    assert bench.traffic_from_profile(src, None, "k_bbpgd1<float>") is None
     src.write_text("// kernel source, changed\n")
-    assert bench.traffic_from_profile(src, (512, 2)) is None
+    assert bench.traffic_from_profile(src, (1024, 1), "k_bbpgd1<float>") is None
 
+
+def test_step_bytes_follow_the_byte_model():
+    # the whole step's algorithmic bytes outside the iterations: search and
+    # assembly N (56 + 24) + N_c (12 + 32 + 11 w + 8), update N (112 + 6 w)
+    n, m = 100_000, 358_098
+    assert bench.step_other_bytes(n, m, 4) == n * 80 + m * 96 + n * 136
+    assert bench.step_other_bytes(n, m, 8) == n * 80 + m * 140 + n * 160
+    assert bench.solve_bytes_per_iter(n, m, 4) == m * 120 + n * 64
+
+
+def test_sibling_jobs_draw_other_inputs_of_the_same_class():
+    a, b = bench.make_job("n1000_box40"), bench.make_job("n1000_box40", sibling=True)
+    assert a.n == b.n and a.s.box == b.s.box and a.s.tol == b.s.tol
+    assert not np.array_equal(a.s.x, b.s.x)
