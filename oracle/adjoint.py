@@ -1,4 +1,5 @@
-"""Adjoint of one constrained step (oracle side, dense, small systems).
+"""Adjoint of one constrained step (oracle side: dense matrices for small
+systems, scipy sparse matrices for large ones, the same formulas).
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: the tests use it to
 check the CUDA adjoint.  It shares no code with the CUDA path.
@@ -13,7 +14,8 @@ set A = {c : gamma_c > 0} (KKT: (A gamma + q)_A = 0, gamma_I = 0):
 
     u   = dL/dU                       (through the update),
     b   = D^T M u,  lambda_A solves A_AA lambda_A = b_A (minimum-norm
-          solution: lstsq; b_A lies in the range of A_AA),
+          solution: dense lstsq, or sparse MINRES from zero; b_A lies in
+          the range of A_AA),
     w   = D lambda,  nu = M (u - w),
     dL  = [direct terms of the update] + (u - w)^T dM F_tot
           + nu^T (dD gamma) - (dD lambda)^T U - lambda^T dPhi / h,
@@ -33,6 +35,8 @@ axis map p(theta) projected onto the unit sphere's tangent plane.
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sps
+import scipy.sparse.linalg as spla
 
 from . import assemble, axis, drag, find_pairs, segment_closest, solve_apgd, solve_enum, wrap
 
@@ -62,6 +66,27 @@ def _dense_D(n, pairs, dgeom):
     return D
 
 
+def _sparse_D(n, pairs, dgeom):
+    """D as a scipy sparse [6n, m] matrix: column c is (e, y_P x e) at rod i
+    and (-e, -y_Q x e) at rod j (Appendix Eq. blockdef)."""
+    m = pairs.shape[0]
+    i = pairs[:, 0].astype(np.int64)
+    j = pairs[:, 1].astype(np.int64)
+    cols = np.arange(m)
+    rows, vals, cc = [], [], []
+    for k in range(3):
+        rows += [6 * i + k, 6 * i + 3 + k, 6 * j + k, 6 * j + 3 + k]
+        vals += [dgeom[:, k], dgeom[:, 3 + k], -dgeom[:, k], -dgeom[:, 6 + k]]
+        cc += [cols] * 4
+    return sps.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cc))), shape=(6 * n, m))
+
+
+def _sparse_M(Mb):
+    """The block-diagonal mobility as a scipy sparse [6n, 6n] matrix."""
+    n = Mb.shape[0]
+    return sps.bsr_matrix((Mb, np.arange(n), np.arange(n + 1)), shape=(6 * n, 6 * n)).tocsr()
+
+
 def solve(quat, pb, pairs, dgeom, q, tol=1e-13):
     """Exact (enumeration) for up to 20 constraints, else FISTA to tol."""
     if pairs.shape[0] == 0:
@@ -73,8 +98,9 @@ def solve(quat, pb, pairs, dgeom, q, tol=1e-13):
     return g
 
 
-def forward(x, quat, fnc, pb, pairs=None, gamma=None):
-    """One step on a given (or found) pair list: U, x' (unwrapped) and theta'."""
+def forward(x, quat, fnc, pb, pairs=None, gamma=None, sparse=False):
+    """One step on a given (or found) pair list: U, x' (unwrapped) and theta'.
+    sparse=True keeps D as a scipy sparse matrix (large systems)."""
     x = np.asarray(x, dtype=np.float64)
     quat = np.asarray(quat, dtype=np.float64)
     if pairs is None:
@@ -86,8 +112,8 @@ def forward(x, quat, fnc, pb, pairs=None, gamma=None):
     p = axis(quat)
     zeta = drag(pb.viscosity, pb.length, pb.diameter)
     Mb = _mobility_blocks(p, zeta)
-    D = _dense_D(n, pairs, asm["dgeom"])
-    F = np.asarray(fnc, dtype=np.float64).reshape(n, 6) + (D @ gamma).reshape(n, 6)
+    D = _sparse_D(n, pairs, asm["dgeom"]) if sparse else _dense_D(n, pairs, asm["dgeom"])
+    F = np.asarray(fnc, dtype=np.float64).reshape(n, 6) + np.asarray(D @ gamma).reshape(n, 6)
     U = np.einsum("nij,nj->ni", Mb, F)
     h = pb.dt
     xn = x + h * U[:, :3]
@@ -116,10 +142,28 @@ def _axis_jacobian(quat):
     return J
 
 
+def _active_multiplier_sparse(D, Msp, uf, act):
+    """lambda_A of A_AA lambda_A = b_A, A_AA = D_A^T M D_A, b = D^T M u, by
+    MINRES (Paige & Saunders 1975) from zero to a relative residual of
+    1e-15: on this consistent symmetric system its iterates stay in the
+    range of A_AA, so it returns the minimum-norm solution also when A_AA is
+    singular.  (A sparse LU of A_AA gives the same multiplier to about 1e-12
+    but takes minutes at 4e4 active constraints.)"""
+    b = D.T @ (Msp @ uf)
+    DA = D[:, np.flatnonzero(act)]
+    AAA = (DA.T @ Msp @ DA).tocsr()
+    bA = b[act]
+    lam, info = spla.minres(AAA, bA, rtol=1e-15, maxiter=100 * AAA.shape[0] + 100)
+    if info != 0 or np.linalg.norm(AAA @ lam - bA) > 1e-10 * max(np.linalg.norm(bA), 1e-300):
+        lam = spla.lsqr(AAA, bA, atol=1e-15, btol=1e-15, iter_lim=100 * AAA.shape[0])[0]
+    return lam
+
+
 def step_adjoint(x, quat, fnc, pb, dL_dxn, dL_dqn=None, fw=None, active_tol=0.0):
     """Gradient of L(x', theta') for given dL/dx' [n,3] and dL/dtheta' [n,4]
     (nullable).  Returns dict: x [n,3], quat [n,4] (tangent), eta, fnc [n,6],
-    and the intermediates lambda, u."""
+    and the intermediates lambda, u.  A forward taken with sparse=True is
+    differentiated with sparse matrices throughout (the same formulas)."""
     x = np.asarray(x, dtype=np.float64)
     quat = np.asarray(quat, dtype=np.float64)
     if fw is None:
@@ -144,19 +188,26 @@ def step_adjoint(x, quat, fnc, pb, dL_dxn, dL_dqn=None, fw=None, active_tol=0.0)
         gq[:, 1:] += gv + 0.5 * h * (-g0[:, None] * om - np.cross(om, gv))
         u[:, 3:] += 0.5 * h * (-g0[:, None] * v + s[:, None] * gv - np.cross(gv, v))
     uf = u.reshape(-1)
-    Mfull = np.zeros((6 * n, 6 * n))
-    for k in range(n):
-        Mfull[6 * k:6 * k + 6, 6 * k:6 * k + 6] = Mb[k]
+    sparse = sps.issparse(D)
     m = pairs.shape[0]
     lam = np.zeros(m)
-    if m > 0:
-        b = D.T @ (Mfull @ uf)
-        act = gamma > active_tol
-        if act.any():
-            DA = D[:, act]
-            AAA = DA.T @ Mfull @ DA
-            lam[act] = np.linalg.lstsq(AAA, b[act], rcond=1e-13)[0]
-    w = (D @ lam).reshape(n, 6)
+    if sparse:
+        if m > 0:
+            act = gamma > active_tol
+            if act.any():
+                lam[act] = _active_multiplier_sparse(D, _sparse_M(Mb), uf, act)
+    else:
+        Mfull = np.zeros((6 * n, 6 * n))
+        for k in range(n):
+            Mfull[6 * k:6 * k + 6, 6 * k:6 * k + 6] = Mb[k]
+        if m > 0:
+            b = D.T @ (Mfull @ uf)
+            act = gamma > active_tol
+            if act.any():
+                DA = D[:, act]
+                AAA = DA.T @ Mfull @ DA
+                lam[act] = np.linalg.lstsq(AAA, b[act], rcond=1e-13)[0]
+    w = np.asarray(D @ lam).reshape(n, 6)
     a = u - w
     nu = np.einsum("nij,nj->ni", Mb, a)
     # mobility: d/dp of a^T M(p) F_tot, and d/d eta
@@ -171,6 +222,8 @@ def step_adjoint(x, quat, fnc, pb, dL_dxn, dL_dqn=None, fw=None, active_tol=0.0)
     xw = wrap(x, box)
     hl = 0.5 * pb.length
     for c in range(m):
+        if gamma[c] == 0.0 and lam[c] == 0.0:
+            continue   # every term of this constraint carries gamma_c or lambda_c
         i, j, code = int(pairs[c, 0]), int(pairs[c, 1]), int(pairs[c, 2])
         k = np.array([code % 3 - 1, (code // 3) % 3 - 1, code // 9 - 1], dtype=np.float64)
         dx = xw[i] - xw[j] - k * box
@@ -233,8 +286,20 @@ def step_adjoint(x, quat, fnc, pb, dL_dxn, dL_dqn=None, fw=None, active_tol=0.0)
     return {"x": gx, "quat": gq, "eta": geta, "fnc": nu, "lambda": lam, "u": u}
 
 
-def loss_and_grad(x, quat, fnc, pb, targets):
-    """The differentiation workload's loss and gradient (oracle)."""
+def loss_and_grad(x, quat, fnc, pb, targets, sparse=False, tol=1e-13):
+    """The differentiation workload's loss and gradient (oracle); sparse=True
+    for large systems (the oracle's own pair list, solve to tol and sparse
+    adjoint)."""
+    if sparse:
+        x = np.asarray(x, dtype=np.float64)
+        quat = np.asarray(quat, dtype=np.float64)
+        pairs = find_pairs(x, quat, pb)
+        asm = assemble(x, quat, fnc, pb, pairs)
+        gamma = solve(quat, pb, pairs, asm["dgeom"], asm["q"], tol=tol)
+        fw = forward(x, quat, fnc, pb, pairs=pairs, gamma=gamma, sparse=True)
+        L = centre_loss(fw["x"], targets)
+        g = step_adjoint(x, quat, fnc, pb, 2.0 * (fw["x"] - targets), fw=fw)
+        return L, g, fw
     fw = forward(x, quat, fnc, pb)
     L = centre_loss(fw["x"], targets)
     g = step_adjoint(x, quat, fnc, pb, 2.0 * (fw["x"] - targets), fw=fw)

@@ -208,11 +208,13 @@ __global__ void k_adj_rods1(int n, int np, Mob mob, double h, const double* __re
 }
 
 // b = D^T M u on the active set; CG start lambda = 0, r = b_A, p = 0, Ap = 0,
-// alpha = beta = 0.
+// alpha = beta = 0.  The CG state of constraint c is one 32-byte record
+// cgs[c] = (r, p, Ap, lambda), so that a gather by constraint id touches one
+// sector.
 __global__ void k_adj_b(int m, const int32_t* __restrict__ pairs, const double* __restrict__ dgeom,
                         const double* __restrict__ gamma, const double* __restrict__ Mu, double* __restrict__ lam,
-                        double* __restrict__ r, double* __restrict__ pv, double* __restrict__ Ap,
-                        double* __restrict__ partials, unsigned* counter, double* scal, int* iflag, double tol)
+                        double* __restrict__ cgs, double* __restrict__ partials, unsigned* counter, double* scal,
+                        int* iflag, double tol)
 {
     double acc = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
@@ -224,10 +226,10 @@ __global__ void k_adj_b(int m, const int32_t* __restrict__ pairs, const double* 
             b += d[a] * (Mu[6 * (size_t)i + a] - Mu[6 * (size_t)j + a]) + d[3 + a] * Mu[6 * (size_t)i + 3 + a] -
                  d[6 + a] * Mu[6 * (size_t)j + 3 + a];
         const double rc = gamma[c] > 0.0 ? b : 0.0;
-        r[c] = rc;
+        double2* st = reinterpret_cast<double2*>(cgs) + 2 * (size_t)c;
+        st[0] = make_double2(rc, 0.0);    // r, p
+        st[1] = make_double2(0.0, 0.0);   // Ap, lambda
         lam[c] = 0.0;
-        pv[c] = 0.0;
-        Ap[c] = 0.0;
         acc += rc * rc;
     }
     double tot;
@@ -300,10 +302,9 @@ struct CgArgs {
     const int* __restrict__ alist;
     const int* __restrict__ bk;
     const int* __restrict__ bc;
-    double* lam;
-    double* r;
-    double* pv;
-    double* Ap;
+    const T* __restrict__ pe;   // [m][8] owned-side arms per constraint (e, y_P x e, 2 pad)
+    double* cgs;         // [m][4] (r, p, Ap, lambda) per constraint
+    double* lam;         // [m] lambda, copied out of cgs when the CG ends
     T* Up;               // [n][6] rod velocities of the direction
     double* partials;    // [2][gridDim.x]: the two sums of an iteration
     unsigned* bar;       // monotone grid-barrier counter
@@ -389,6 +390,27 @@ __device__ __forceinline__ bool grid_totals4(const double* part, unsigned* bar, 
 // reaches max_iter, or when alpha_k <= 0; k is the iteration count.
 constexpr int kCgLanes = 8;
 
+// Owned-side arms in constraint order, one 8-value record per constraint
+// (e, y_P x e, two pad values), for the CG's gathers by constraint id.
+template <typename T>
+__global__ void k_cg_arms(int m, int mp, const T* __restrict__ rec, T* __restrict__ pe)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    T* o = pe + 8 * (size_t)c;
+#pragma unroll
+    for (int w = 0; w < 6; ++w) o[w] = rec[w * (size_t)mp + c];
+    o[6] = T(0);
+    o[7] = T(0);
+}
+
+__device__ __forceinline__ void ld_cgs(const double* cgs, int c, double& r, double& p, double& ap, double& lam)
+{
+    const double2* q = reinterpret_cast<const double2*>(cgs) + 2 * (size_t)c;
+    const double2 a = q[0], b = q[1];
+    r = a.x; p = a.y; ap = b.x; lam = b.y;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
 {
@@ -421,9 +443,15 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
             if (i < r1) {
                 for (int t = a.aP[i] + sub; t < a.aP[i + 1]; t += kCgLanes) {
                     const int c = a.alist[t];
-                    const T v = (T)(fma(-alpha, a.Ap[c], a.r[c]) + beta * a.pv[c]);
+                    const T* p8 = a.pe + 8 * (size_t)c;
+                    T pv6[6];
 #pragma unroll
-                    for (int w = 0; w < 6; ++w) F[w] += v * a.rec[w * mp + c];
+                    for (int w = 0; w < 6; ++w) pv6[w] = p8[w];
+                    double rc, pc, apc, lc;
+                    ld_cgs(a.cgs, c, rc, pc, apc, lc);
+                    const T v = (T)(fma(-alpha, apc, rc) + beta * pc);
+#pragma unroll
+                    for (int w = 0; w < 6; ++w) F[w] += v * pv6[w];
                 }
                 for (int t = a.aQ[i] + sub; t < a.aQ[i + 1]; t += kCgLanes) {
                     const int c = a.bc[t];
@@ -431,7 +459,9 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
                     T qv[6];
 #pragma unroll
                     for (int w = 0; w < 6; ++w) qv[w] = q8[w];
-                    const T v = (T)(fma(-alpha, a.Ap[c], a.r[c]) + beta * a.pv[c]);
+                    double rc, pc, apc, lc;
+                    ld_cgs(a.cgs, c, rc, pc, apc, lc);
+                    const T v = (T)(fma(-alpha, apc, rc) + beta * pc);
 #pragma unroll
                     for (int w = 0; w < 6; ++w) F[w] -= v * qv[w];
                 }
@@ -461,13 +491,13 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
                 s += a.rec[w * mp + c] * (ui[w] - uj[w]) + a.rec[(3 + w) * mp + c] * ui[3 + w] -
                      a.rec[(6 + w) * mp + c] * uj[3 + w];
             const double ap = (double)s;
-            const double pold = a.pv[c];
-            const double rn = fma(-alpha, a.Ap[c], a.r[c]);
+            double rold, pold, apold, lold;
+            ld_cgs(a.cgs, c, rold, pold, apold, lold);
+            const double rn = fma(-alpha, apold, rold);
             const double pn = rn + beta * pold;
-            a.lam[c] += alpha * pold;
-            a.r[c] = rn;
-            a.pv[c] = pn;
-            a.Ap[c] = ap;
+            double2* stc = reinterpret_cast<double2*>(a.cgs) + 2 * (size_t)c;
+            stc[0] = make_double2(rn, pn);
+            stc[1] = make_double2(ap, lold + alpha * pold);
             acc[0] += pn * ap;
             acc[1] += rn * ap;
             acc[2] += ap * ap;
@@ -498,6 +528,11 @@ __global__ void __launch_bounds__(1024, 1) k_cg(CgArgs<T> a)
         beta = sc[1];
         rr = sc[2];
         if (sc[3] != 0.0) break;
+    }
+    // lambda of the block's active constraints for the passes after the CG
+    for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
+        const int c = a.alist[t];
+        a.lam[c] = a.cgs[4 * (size_t)c + 3];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.scal[S_RR] = rr;
@@ -724,9 +759,10 @@ cudaError_t adjoint_reserve(aLENS_ctx* ctx)
 {
     if (ctx->adj_ws) return cudaSuccess;
     const size_t np = (size_t)ctx->max_rods, mp = (size_t)ctx->max_pairs;
-    // per rod: Ftot, U, u, Mu, nu, Up (6 each), gx, gp (3), gq (4); per constraint: lam, r, p, Ap, geo (9)
-    // (each slice is rounded up to 8 doubles: 15 slices, at most 105 doubles of padding)
-    const size_t doubles = np * (6 * 6 + 3 + 3 + 4) + mp * (4 + 9) + S_NSCAL + 128;
+    // per rod: Ftot, U, u, Mu, nu, Up (6 each), gx, gp (3), gq (4); per constraint: lam, the CG
+    // state (r, p, Ap, lambda), geo (9; the CG's owned-side arm records live there until k_adj_geo)
+    // (each slice is rounded up to 8 doubles: 13 slices, at most 91 doubles of padding)
+    const size_t doubles = np * (6 * 6 + 3 + 3 + 4) + mp * (1 + 4 + 9) + S_NSCAL + 128;
     // then the flags and the CG's active-set lists (ints): counts and row
     // pointers of the owned and other-side lists, the lists (3 mp)
     const size_t ints = I_NI + 4 * (np + 1) + 3 * mp + 64;
@@ -757,9 +793,7 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
     double* gp = take(3 * np);
     double* gq = take(4 * np);
     double* lam = take(mp);
-    double* r = take(mp);
-    double* pv = take(mp);
-    double* Ap = take(mp);
+    double* cgs = take(4 * mp);
     double* geo = take(9 * mp);
     double* scal = take(S_NSCAL);
     int* iflag = (int*)(base + o);
@@ -790,8 +824,13 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
     int iters = 0;
     double rel = 0.0;
     if (m > 0) {
-        k_adj_b<<<G, 256, 0, st>>>(m, pairs, ctx->dgeom, gamma, Mu, lam, r, pv, Ap, ctx->partials, counter, scal, iflag,
+        k_adj_b<<<G, 256, 0, st>>>(m, pairs, ctx->dgeom, gamma, Mu, lam, cgs, ctx->partials, counter, scal, iflag,
                                    tol);
+        ++ctx->launches;
+        if (mixed)
+            k_cg_arms<float><<<nblk(m, 256), 256, 0, st>>>(m, (int)mp, ctx->sb32.rec, reinterpret_cast<float*>(geo));
+        else
+            k_cg_arms<double><<<nblk(m, 256), 256, 0, st>>>(m, (int)mp, ctx->sb64.rec, geo);
         ++ctx->launches;
         // the active set as lists (the CG touches active constraints only)
         k_act_count<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowP, ctx->rowQ, ctx->qlist, gamma, cA, cB);
@@ -812,7 +851,8 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
             const SolveBufs<float>& sb = ctx->sb32;
             CgArgs<float> ca{n, m, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.qe,
                              sb.ax, (float)ctx->mob.inv_perp, (float)ctx->mob.inv_par, (float)ctx->mob.inv_rot,
-                             (float)ctx->mob.inv_spin, aP, aQ, alist, bk, bc, lam, r, pv, Ap, (float*)Upd, ctx->partials,
+                             (float)ctx->mob.inv_spin, aP, aQ, alist, bk, bc, reinterpret_cast<const float*>(geo), cgs,
+                             lam, (float*)Upd, ctx->partials,
                              ctx->bar + 2, ctx->dflags, scal, iflag, wait, fault};
             void* args[] = {&ca};
             if ((e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(1024), args, 0, st)) != cudaSuccess)
@@ -821,7 +861,7 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
             const SolveBufs<double>& sb = ctx->sb64;
             CgArgs<double> ca{n, m, (int)np, (int)mp, ctx->rowP, ctx->rowQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec,
                               sb.qe, sb.ax, ctx->mob.inv_perp, ctx->mob.inv_par, ctx->mob.inv_rot, ctx->mob.inv_spin,
-                              aP, aQ, alist, bk, bc, lam, r, pv, Ap, Upd, ctx->partials, ctx->bar + 2, ctx->dflags, scal,
+                              aP, aQ, alist, bk, bc, geo, cgs, lam, Upd, ctx->partials, ctx->bar + 2, ctx->dflags, scal,
                               iflag, wait,
                               fault};
             void* args[] = {&ca};

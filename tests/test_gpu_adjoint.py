@@ -4,10 +4,11 @@ Small systems: the CUDA gradient against the oracle's adjoint (itself pinned
 by central differences of the oracle's forward step, tests/test_oracle_adjoint.py)
 element by element — float64 to 1e-7 relative to the largest entry, mixed
 (float32 CG operator, float32 BBPGD forward) to 1e-3.  The 2e4-rod
-differentiation workload: central differences (h = 1e-6) of the CUDA
-float64 forward step's loss for sampled centre and orientation coordinates
-and the viscosity, plus agreement of the mixed gradient with the float64
-one.  Also the path through a loss on the post-step quaternions,
+differentiation workload: the oracle's sparse adjoint on its own forward
+step, element by element at the same bars; central differences (h = 1e-6)
+of the CUDA float64 forward step's loss for sampled centre and orientation
+coordinates and the viscosity, plus agreement of the mixed gradient with
+the float64 one.  Also the path through a loss on the post-step quaternions,
 free drift, determinism, invalid input and the torch.autograd wrapper.
 """
 import numpy as np
@@ -233,6 +234,35 @@ def test_n20k_gradient_against_central_differences(n20k):
         eta0 = s.viscosity
         fd = (loss_of(ctx, s, T, eta=eta0 + h) - loss_of(ctx, s, T, eta=eta0 - h)) / (2 * h)
         assert geta == pytest.approx(fd, rel=bar)
+
+
+@pytest.fixture(scope="module")
+def n20k_oracle(n20k):
+    """The float64 oracle's own step (brute-force pairs, FISTA to 1e-13) and
+    its sparse adjoint (MINRES on the active system) at 2e4 rods."""
+    s, T = n20k
+    return ADJ.loss_and_grad(s.x, s.quat, s.f_nc, O.problem_of(s), T, sparse=True, tol=1e-13)
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(A.FP64, 1e-13, 1e-7), (A.MIXED, 1e-6, 1e-3)])
+def test_n20k_gradient_against_sparse_oracle(n20k, n20k_oracle, precision, tol, bar):
+    """Element by element (relative to the largest entry) against an
+    independent gradient: the oracle's own pair list, solve and sparse
+    adjoint on the 2e4-rod differentiation workload."""
+    s, T = n20k
+    L_o, g_o, fw = n20k_oracle
+    with ctx_for(s, precision, tol=tol) as ctx:
+        gx, gq, gf, geta, info, pairs, gam = gpu_grad(ctx, s, T)
+    assert np.array_equal(pairs, fw["pairs"])
+    act_gpu, act_orc = gam > 0, fw["gamma"] > 0
+    if precision == A.FP64:
+        assert np.array_equal(act_gpu, act_orc)
+    err = {k: rel(v, g_o[k]) for k, v in (("x", gx), ("quat", gq), ("fnc", gf))}
+    print(f"\nn20k gradient vs sparse oracle ({'fp64' if precision == A.FP64 else 'mixed'}): {err}, "
+          f"eta {geta / g_o['eta'] - 1:.2e}, active {int(act_gpu.sum())} / {int(act_orc.sum())}")
+    for k, e in err.items():
+        assert e < bar, (k, e)
+    assert geta == pytest.approx(g_o["eta"], rel=bar)
 
 
 def test_n20k_mixed_gradient_close_to_fp64(n20k):

@@ -167,3 +167,52 @@ def test_no_contact_gradient_is_free_drift():
     np.testing.assert_allclose(g["x"], 2.0 * (fw["x"] - T), rtol=0, atol=1e-15)
     U = fw["U"]
     assert g["eta"] == pytest.approx(-np.sum(s.dt * 2.0 * (fw["x"] - T) * U[:, :3]) / s.viscosity, rel=1e-12)
+
+
+@pytest.mark.parametrize("seed,n,box,L", SYSTEMS)
+def test_sparse_form_equals_dense_form(seed, n, box, L):
+    """The sparse oracle adjoint (scipy sparse D and M, MINRES on the active
+    system) gives the dense one's gradient, whose central differences the
+    tests above check: the large-system oracle inherits that pin."""
+    s, T = make(seed, n, box, L)
+    pb = O.problem_of(s)
+    Ld, gd, fwd = ADJ.loss_and_grad(s.x, s.quat, s.f_nc, pb, T)
+    Ls, gs, fws = ADJ.loss_and_grad(s.x, s.quat, s.f_nc, pb, T, sparse=True)
+    assert np.array_equal(fwd["pairs"], fws["pairs"])
+    assert Ls == pytest.approx(Ld, rel=1e-13)
+    for k in ("x", "quat", "fnc", "lambda"):
+        assert rel_err(gs[k], gd[k]) < 1e-10, k
+    assert gs["eta"] == pytest.approx(gd["eta"], rel=1e-10)
+
+
+def test_sparse_form_against_central_differences():
+    """The sparse form on its own against central differences of the
+    oracle's forward step, on a system of 120 rods (larger than the dense
+    tests' and still quick)."""
+    s = W.tiny_system(377, 120, box=18.0, length=4.0)
+    s.f_nc *= 30.0
+    T = s.x + 0.01 * np.random.default_rng(9).standard_normal(s.x.shape)
+    pb = O.problem_of(s)
+    L0, g, fw0 = ADJ.loss_and_grad(s.x, s.quat, s.f_nc, pb, T, sparse=True)
+    assert (fw0["gamma"] > 0).sum() >= 20
+
+    def loss(x=None, quat=None):
+        fw = ADJ.forward(s.x if x is None else x, s.quat if quat is None else quat, s.f_nc, pb, sparse=True)
+        assert np.array_equal(fw["pairs"], fw0["pairs"])
+        assert np.array_equal(fw["gamma"] > 0, fw0["gamma"] > 0)
+        return ADJ.centre_loss(fw["x"], T)
+
+    rng = np.random.default_rng(4)
+    rods = rng.choice(np.unique(fw0["pairs"][fw0["gamma"] > 0][:, :2]), size=5, replace=False)
+    for i in rods:
+        k = int(rng.integers(3))
+        d = np.zeros_like(s.x)
+        d[i, k] = EPS
+        want = (loss(x=s.x + d) - loss(x=s.x - d)) / (2 * EPS)
+        assert g["x"][i, k] == pytest.approx(want, rel=1e-5, abs=1e-8 * np.abs(g["x"]).max())
+        v = tangent_basis(s.quat[i])[k]
+        qp, qm = s.quat.copy(), s.quat.copy()
+        qp[i] = (s.quat[i] + EPS * v) / np.linalg.norm(s.quat[i] + EPS * v)
+        qm[i] = (s.quat[i] - EPS * v) / np.linalg.norm(s.quat[i] - EPS * v)
+        want = (loss(quat=qp) - loss(quat=qm)) / (2 * EPS)
+        assert g["quat"][i] @ v == pytest.approx(want, rel=1e-5, abs=1e-8 * np.abs(g["quat"]).max())
