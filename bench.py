@@ -290,7 +290,9 @@ class BatchJob:
         s0 = self.systems[0]
         p = A.make_params(s0.box, s0.diameter, s0.length, s0.viscosity, s0.dt, s0.delta_c, tol, 1_000_000,
                           precision)
-        return A.Context(p, self.n, 12 * self.n, stream=stream)
+        ctx = A.Context(p, self.n, 12 * self.n, stream=stream)
+        ctx.set_batch_graph(True)   # the step recorded once as a CUDA graph, then replayed
+        return ctx
 
     def step(self, ctx, x, q, f, **kw):
         return ctx.step_batch(self.spec, self.off, x, q, f, **kw)
@@ -316,6 +318,7 @@ class BatchJob:
     def config(self, W, m):
         return {"workload": self.name, "systems": len(self.systems), "rods": self.n, "pairs": m,
                 "rods_per_system": [int(np.diff(self.off).min()), int(np.diff(self.off).max())],
+                "step": "one aLENS_step_batch call, replayed as a captured CUDA graph",
                 "orientation": f"nematic domains, spread {W.ENSEMBLE_SPREAD} rad about a random director each"}
 
     def cpu(self, args):

@@ -297,6 +297,30 @@ ALENS_API aLENS_status aLENS_step_batch(aLENS_ctx* ctx, int32_t n_systems, const
                                         const int64_t* rod_offset, double* x, double* quat, const double* f_nc,
                                         int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info);
 
+/* Batched steps as a captured CUDA graph (the paper has no batch mode: a
+ * batch serves many independent systems in one call).  enable = 1:
+ * aLENS_step_batch of two or more systems records its whole step - search,
+ * assembly, the per-system solver launch, update and outputs - as one CUDA
+ * graph and replays it on later calls.  A step has no host readback inside
+ * the graph: kernels sized by the constraint count are launched for the
+ * context's capacity and read the count on the device, and a step whose
+ * pairs exceed the capacity changes nothing and returns ALENS_ERR_CAPACITY
+ * with the required count (counted again outside the graph when the
+ * candidate buffer overflowed).  The graph is kept for one key: the batch
+ * tables, n, the six array pointers of the call, the parameters, the
+ * scaling exponent and the batch launch shape.  The first call with a new
+ * key runs without a graph, the second records the graph and runs it, later
+ * calls replay it; a call with another key starts over.  Steps with
+ * springs, and the fault hook, always run without a graph.  Results equal
+ * those of steps without a graph bit for bit.  enable = 0 releases the
+ * graph.  ALENS_ERR_INVALID for other values. */
+ALENS_API aLENS_status aLENS_set_batch_graph(aLENS_ctx* ctx, int32_t enable);
+
+/* Name of the CUDA runtime error behind the calling thread's last
+ * ALENS_ERR_CUDA from a context entry point ("cudaSuccess" if none);
+ * a static string. */
+ALENS_API const char* aLENS_last_cuda_error(void);
+
 /* ------------------------------------------------------------------------
  * Adjoint of aLENS_step (reverse-mode gradient of a scalar loss L(x', quat')
  * of the post-step state).  The paper does not differentiate its step; this

@@ -63,6 +63,11 @@ class AlensError(RuntimeError):
         msg = f"{where}: {STATUS.get(status, status)} ({_status_string(status)})"
         if isinstance(extra, dict) and "iters" in extra:
             msg += f" iters={extra['iters']} residual={extra['residual']:.3e} n_pairs={extra['n_pairs']}"
+        if status == 5:   # ALENS_ERR_CUDA: the runtime error behind it
+            try:
+                msg += f" [{lib().aLENS_last_cuda_error().decode()}]"
+            except Exception:
+                pass
         super().__init__(msg)
 
 
@@ -108,6 +113,8 @@ def lib():
             "aLENS_inject_fault": (i32, [vp, i32]),
             "aLENS_set_launch": (i32, [vp, i32, i32]),
             "aLENS_set_solver_schedule": (i32, [vp, i32]),
+            "aLENS_set_batch_graph": (i32, [vp, i32]),
+            "aLENS_last_cuda_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -317,6 +324,12 @@ class Context:
         if st != 0:
             raise AlensError(st, "aLENS_batch_results")
         return it, res
+
+    def set_batch_graph(self, enable: bool = True):
+        """Record aLENS_step_batch as a CUDA graph and replay it (see include/alens.h)."""
+        st = self._lib.aLENS_set_batch_graph(self._h, int(bool(enable)))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_batch_graph")
 
     def set_batch_launch(self, threads: int, cluster_blocks: int):
         st = self._lib.aLENS_set_batch_launch(self._h, int(threads), int(cluster_blocks))

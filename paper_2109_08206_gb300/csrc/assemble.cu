@@ -31,8 +31,10 @@ __global__ void k_assemble(int m, int n, int np, Geo g0, const SysGeo* __restric
                            const int* __restrict__ sysid, const int32_t* __restrict__ pairs,
                            const double* __restrict__ xw, const double* __restrict__ axis,
                            const double* __restrict__ unc, double* __restrict__ phi, double* __restrict__ dgeom,
-                           double* __restrict__ q, unsigned long long* __restrict__ counters, int* __restrict__ flags)
+                           double* __restrict__ q, unsigned long long* __restrict__ counters, int* __restrict__ flags,
+                           const unsigned long long* __restrict__ mdev)
 {
+    m = count_of(m, mdev);
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     bool active = c < m;
     bool overlap = false;
@@ -153,10 +155,10 @@ __device__ __forceinline__ void owner_other(const int32_t* pairs, const int* ran
 }
 
 __global__ void k_count_sides(int m, const int32_t* __restrict__ pairs, const int* __restrict__ rank,
-                              int* __restrict__ cntP, int* __restrict__ cntQ)
+                              int* __restrict__ cntP, int* __restrict__ cntQ, const unsigned long long* __restrict__ mdev)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m) return;
+    if (c >= count_of(m, mdev)) return;
     int ro, rq;
     bool flip;
     owner_other(pairs, rank, c, ro, rq, flip);
@@ -165,10 +167,11 @@ __global__ void k_count_sides(int m, const int32_t* __restrict__ pairs, const in
 }
 
 __global__ void k_scatter_owner(int m, const int32_t* __restrict__ pairs, const int* __restrict__ rank,
-                                const int* __restrict__ rowP, int* __restrict__ curP, int* __restrict__ perm)
+                                const int* __restrict__ rowP, int* __restrict__ curP, int* __restrict__ perm,
+                                const unsigned long long* __restrict__ mdev)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m) return;
+    if (c >= count_of(m, mdev)) return;
     int ro, rq;
     bool flip;
     owner_other(pairs, rank, c, ro, rq, flip);
@@ -228,10 +231,10 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
                              T* __restrict__ gg0, T* __restrict__ gg1, T* __restrict__ rec_lo, T* __restrict__ q_lo,
                              const double* __restrict__ comp64, T* __restrict__ compT, int np, const T* __restrict__ ax,
                              const T* __restrict__ mobr, Mob mob0, double beta, double* __restrict__ scale64,
-                             T* __restrict__ isc)
+                             T* __restrict__ isc, const unsigned long long* __restrict__ mdev)
 {
     int cc = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cc >= m) return;
+    if (cc >= count_of(m, mdev)) return;
     int c = perm[cc];
     int ro, rq;
     bool flip;
@@ -304,10 +307,11 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
 // two pad values) so that the solver's gather is one or two vector loads.
 template <typename T>
 __global__ void k_setup_qe(int m, int mp, const int* __restrict__ qlist, const T* __restrict__ rec,
-                           T* __restrict__ qe, const T* __restrict__ rec_lo, T* __restrict__ qe_lo)
+                           T* __restrict__ qe, const T* __restrict__ rec_lo, T* __restrict__ qe_lo,
+                           const unsigned long long* __restrict__ mdev)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= m) return;
+    if (k >= count_of(m, mdev)) return;
     int c = qlist[k];
     T* o = qe + 8 * (size_t)k;
 #pragma unroll
@@ -437,7 +441,7 @@ cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, 
     if (m <= 0) return cudaSuccess;
     k_assemble<<<nblk(m, 256), 256, 0, ctx->stream>>>(m, n, (int)ctx->max_rods, ctx->geo, ctx->cur_systab,
                                                       ctx->cur_sysid, pairs, ctx->xw, ctx->axis, ctx->unc, phi, dgeom, q,
-                                                      ctx->dcount, ctx->dflags);
+                                                      ctx->dcount, ctx->dflags, ctx->mdev);
     ++ctx->launches;
     return cudaGetLastError();
 }
@@ -459,11 +463,11 @@ static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
                                                   ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0], sb.gg[1],
                                                   sb.rec_lo, sb.q_lo, ctx->cur_comp, sb.comp, np, sb.ax,
                                                   ctx->cur_systab ? sb.mobr : (const T*)nullptr, ctx->mob, ctx->scale_beta,
-                                                  ctx->scale64, sb.isc);
+                                                  ctx->scale64, sb.isc, ctx->mdev);
     ++ctx->launches;
     k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
     ++ctx->launches;
-    k_setup_qe<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->qlist, sb.rec, sb.qe, sb.rec_lo, sb.qe_lo);
+    k_setup_qe<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->qlist, sb.rec, sb.qe, sb.rec_lo, sb.qe_lo, ctx->mdev);
     ++ctx->launches;
     return cudaGetLastError();
 }
@@ -492,13 +496,13 @@ cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pair
     if ((e = cudaMemsetAsync(ctx->curQ, 0, bytes, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ctx->curP, 0, bytes, st)) != cudaSuccess) return e;
     if (m > 0) {
-        k_count_sides<<<nblk(m, 256), 256, 0, st>>>(m, pairs, rank, ctx->rod_count, ctx->cntQ);
+        k_count_sides<<<nblk(m, 256), 256, 0, st>>>(m, pairs, rank, ctx->rod_count, ctx->cntQ, ctx->mdev);
         ++ctx->launches;
     }
     if ((e = exclusive_scan(ctx, ctx->rod_count, ctx->rowP, n)) != cudaSuccess) return e;
     if ((e = exclusive_scan(ctx, ctx->cntQ, ctx->rowQ, n)) != cudaSuccess) return e;
     if (m > 0) {
-        k_scatter_owner<<<nblk(m, 256), 256, 0, st>>>(m, pairs, rank, ctx->rowP, ctx->curP, ctx->perm);
+        k_scatter_owner<<<nblk(m, 256), 256, 0, st>>>(m, pairs, rank, ctx->rowP, ctx->curP, ctx->perm, ctx->mdev);
         ++ctx->launches;
         k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowP, ctx->perm);
         ++ctx->launches;

@@ -14,10 +14,16 @@ using namespace alens;
 
 namespace {
 
+// the CUDA error behind the calling thread's last ALENS_ERR_CUDA (aLENS_last_cuda_error)
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 #define CK(call)                                   \
     do {                                           \
         cudaError_t err__ = (call);                \
-        if (err__ != cudaSuccess) return ALENS_ERR_CUDA; \
+        if (err__ != cudaSuccess) {                \
+            g_last_cuda_error = err__;             \
+            return ALENS_ERR_CUDA;                 \
+        }                                          \
     } while (0)
 
 bool params_ok(const aLENS_params* p)
@@ -91,6 +97,9 @@ void free_all(aLENS_ctx* c)
                     c->row_keys, c->prev_keys, c->prev_gam};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free(c->batch_host);
     free(c->batch_off_host);
     if (c->hflags) cudaFreeHost(c->hflags);
@@ -131,10 +140,21 @@ double decode_gap(unsigned long long k)
     return v;
 }
 
+// Records a step's timing event.  While a graph is being recorded the event
+// must stay an event of the graph (a plain record during capture only orders
+// the captured work and is never recorded when the graph runs).
+cudaError_t record_event(aLENS_ctx* c, cudaEvent_t e)
+{
+    return c->mdev ? cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal) : cudaEventRecord(e, c->stream);
+}
+
 float elapsed(cudaEvent_t a, cudaEvent_t b)
 {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = -1.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        ms = -1.f;
+        cudaGetLastError();   // a timing that cannot be read is not an error of the step
+    }
     return ms;
 }
 
@@ -203,6 +223,7 @@ aLENS_status batch_tables(aLENS_ctx* c, int ns, const aLENS_system* sys, const i
         c->cur_nkeys = c->batch_keys;
         return ALENS_OK;
     }
+    ++c->tables_epoch;   // a recorded batched step no longer applies
     SysGeo* tab = (SysGeo*)calloc((size_t)ns, sizeof(SysGeo));
     long long* loff = (long long*)malloc(sizeof(long long) * (ns + 1));
     if (!tab || !loff) { free(tab); free(loff); return ALENS_ERR_NOMEM; }
@@ -282,9 +303,9 @@ aLENS_status batch_tables(aLENS_ctx* c, int ns, const aLENS_system* sys, const i
 // Runs the solver on the layout already set up; fills info.
 aLENS_status run_solver(aLENS_ctx* c, int n, int m, aLENS_info* info, cudaEvent_t e0, cudaEvent_t e1)
 {
-    CK(cudaEventRecord(e0, c->stream));
+    CK(record_event(c, e0));
     if (m > 0) CK(launch_solve(c, n, m, c->p.precision));
-    CK(cudaEventRecord(e1, c->stream));
+    CK(record_event(c, e1));
     (void)info;
     return ALENS_OK;
 }
@@ -501,7 +522,9 @@ aLENS_status aLENS_set_solver_schedule(aLENS_ctx* c, int32_t barriers)
 // candidate keys in the context and the pair total in hcount[C_PAIRS].
 // Synchronises once (twice if the candidate buffer overflowed, to count the
 // pairs exactly).
-static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const double* quat, const double* fnc)
+// The search's kernels (no host readback): pack, cell list, pair search
+// and the float64 decision.
+static aLENS_status search_kernels(aLENS_ctx* c, int n, const double* x, const double* quat, const double* fnc)
 {
     int nkeys = c->cur_nkeys;
     aLENS_status st = reset_status(c);
@@ -516,6 +539,13 @@ static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const dou
     }
     CK(launch_cell_sort(c, n));
     CK(launch_search(c, n));
+    return ALENS_OK;
+}
+
+static aLENS_status search_phase(aLENS_ctx* c, int n, const double* x, const double* quat, const double* fnc)
+{
+    aLENS_status st = search_kernels(c, n, x, quat, fnc);
+    if (st != ALENS_OK) return st;
     if ((st = read_status(c)) != ALENS_OK) return st;
     if (c->hflags[F_ERR] != 0) return (aLENS_status)c->hflags[F_ERR];
     if ((long long)c->hcount[C_CAND] > c->cand_cap) {
@@ -686,6 +716,139 @@ static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, 
     st = solve_status(c, m);
     if (opt.keep) c->prev_valid = st == ALENS_OK || st == ALENS_ERR_NOT_CONVERGED;
     fill_info(c, info, m, st);
+    if (info) {
+        info->n_pairs = mu;
+        info->ms_build = elapsed(c->ev[0], c->ev[1]);
+        info->ms_assemble = elapsed(c->ev[1], c->ev[2]);
+        info->ms_solve = elapsed(c->ev[2], c->ev[3]);
+        info->ms_update = elapsed(c->ev[3], c->ev[4]);
+    }
+    return st;
+}
+
+// A batched step without host readbacks, for recording as a CUDA graph:
+// every kernel that depends on the constraint count is launched for the
+// capacity and reads the count from the device (C_MEFF, set by the
+// capacity check; 0 after a failure, and the update then leaves the rods
+// untouched).  The caller reads the status back after the graph runs.
+static aLENS_status step_graph_body(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
+                                    int32_t* pairs_out, double* gamma_out, double* vel_out)
+{
+    const int mcap = (int)c->max_pairs;
+    c->mdev = c->dcount + C_MEFF;
+    CK(record_event(c, c->ev[0]));
+    aLENS_status st = search_kernels(c, (int)n, x, quat, f_nc);
+    if (st == ALENS_OK) {
+        CK(launch_check_capacity(c));
+        CK(launch_emit_pairs(c, (int)n, c->pairs));
+        CK(record_event(c, c->ev[1]));
+        CK(launch_assemble(c, (int)n, mcap, c->pairs, c->phi, c->dgeom, c->q64));
+        CK(launch_rank(c, (int)n));
+        CK(launch_solve_setup(c, (int)n, mcap, c->pairs, c->dgeom, c->q64, nullptr, quat, c->p.precision, c->rank));
+        st = run_solver(c, (int)n, mcap, nullptr, c->ev[2], c->ev[3]);
+    }
+    if (st == ALENS_OK) {
+        CK(launch_update(c, (int)n, mcap, x, quat, c->p.precision, vel_out, c->rank));
+        CK(record_event(c, c->ev[4]));
+        if (gamma_out) CK(launch_gamma_out(c, mcap, c->p.precision, gamma_out));
+        if (pairs_out) CK(launch_copy_pairs(c, pairs_out));
+    }
+    c->mdev = nullptr;
+    return st;
+}
+
+static void drop_graph(aLENS_ctx* c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->graph_state = 0;
+}
+
+// The key of a recorded batched step: everything its launches bake in.
+static aLENS_ctx::GraphKey graph_key(const aLENS_ctx* c, int64_t n, const double* x, const double* quat,
+                                     const double* f_nc, const int32_t* pairs_out, const double* gamma_out,
+                                     const double* vel_out)
+{
+    aLENS_ctx::GraphKey k;
+    memset(&k, 0, sizeof(k));
+    k.n = n;
+    k.ptr[0] = x; k.ptr[1] = quat; k.ptr[2] = f_nc; k.ptr[3] = pairs_out; k.ptr[4] = gamma_out; k.ptr[5] = vel_out;
+    k.p = c->p;
+    k.beta = c->scale_beta;
+    k.threads = c->batch_threads;
+    k.cluster = c->batch_cluster;
+    k.tables = c->tables_epoch;
+    return k;
+}
+
+// Replays (recording it first when needed) the graph of a batched step and
+// reads its outcome back.  Returns ALENS_ERR_NOT_IMPLEMENTED when the step
+// is to run eagerly instead (the first step of a new key).
+static aLENS_status step_batch_graph(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
+                                     int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info)
+{
+    const aLENS_ctx::GraphKey k = graph_key(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out);
+    const bool same = c->graph_state > 0 && memcmp(&k, &c->gkey, sizeof(k)) == 0;
+    if (!same) {
+        drop_graph(c);
+        c->gkey = k;
+        c->graph_state = 1;   // this key runs eagerly once (tables, attributes, allocations settle)
+        return ALENS_ERR_NOT_IMPLEMENTED;
+    }
+    if (c->graph_state == 1) {
+        c->launches = 0;
+        if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        // recording enqueues nothing: the step's launches go to a private
+        // stream for the capture, and the graph runs on the context's stream
+        cudaStream_t own = c->stream;
+        c->stream = c->cap_stream;
+        cudaError_t be = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        aLENS_status st = be == cudaSuccess ? step_graph_body(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out)
+                                            : ALENS_ERR_CUDA;
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = be == cudaSuccess ? cudaStreamEndCapture(c->stream, &g) : be;
+        c->stream = own;
+        if (st != ALENS_OK || ce != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            drop_graph(c);
+            return st != ALENS_OK ? st : ALENS_ERR_CUDA;
+        }
+        c->graph = g;
+        if (cudaGraphInstantiate(&c->gexec, g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            drop_graph(c);
+            return ALENS_ERR_CUDA;
+        }
+        c->graph_launches = c->launches;
+        c->graph_state = 2;
+    }
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    c->launches = c->graph_launches;
+    c->last_solver = 4;
+    aLENS_status st = read_status(c);
+    if (st != ALENS_OK) return st;
+    const long long mu = (long long)c->hcount[C_PAIRS];
+    if (c->hflags[F_ERR] == ALENS_ERR_CAPACITY) {
+        long long need = mu;
+        if ((long long)c->hcount[C_CAND] > c->cand_cap) {
+            // candidates overflowed: count the pairs exactly (nothing moved)
+            CK(reset_status(c) == ALENS_OK ? cudaSuccess : cudaErrorUnknown);
+            CK(launch_search_count(c, (int)n));
+            if ((st = read_status(c)) != ALENS_OK) return st;
+            need = (long long)c->hcount[C_PAIRS];
+        }
+        if (info) { memset(info, 0, sizeof(*info)); info->status = ALENS_ERR_CAPACITY; info->n_pairs = need; }
+        return ALENS_ERR_CAPACITY;
+    }
+    if (c->hflags[F_ERR] != 0) {
+        if (info) { memset(info, 0, sizeof(*info)); info->status = c->hflags[F_ERR]; info->n_pairs = mu; }
+        return (aLENS_status)c->hflags[F_ERR];
+    }
+    st = solve_status(c, mu);
+    fill_info(c, info, mu, st);
     if (info) {
         info->n_pairs = mu;
         info->ms_build = elapsed(c->ev[0], c->ev[1]);
@@ -939,10 +1102,24 @@ aLENS_status aLENS_step_batch(aLENS_ctx* c, int32_t n_systems, const aLENS_syste
     c->cur_systab = c->systab;
     c->cur_sysid = c->sysid;
     c->last_batch_n = 0;
-    st = step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
+    st = ALENS_ERR_NOT_IMPLEMENTED;
+    // a batch of one runs the single-system solver, which reads its shared-memory need back
+    const bool graphable = c->batch_graph && n > 0 && n_systems > 1 && c->sp_n == 0 && c->fault_mode == 0;
+    if (graphable) st = step_batch_graph(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
+    if (st == ALENS_ERR_NOT_IMPLEMENTED) st = step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
     if (st == ALENS_OK || st == ALENS_ERR_NOT_CONVERGED) c->last_batch_n = n_systems;
     single_mode(c);
     return st;
+}
+
+const char* aLENS_last_cuda_error(void) { return cudaGetErrorName(g_last_cuda_error); }
+
+aLENS_status aLENS_set_batch_graph(aLENS_ctx* c, int32_t enable)
+{
+    if (!c || (enable != 0 && enable != 1)) return ALENS_ERR_INVALID;
+    if (!enable) drop_graph(c);
+    c->batch_graph = enable;
+    return ALENS_OK;
 }
 
 }  // extern "C"

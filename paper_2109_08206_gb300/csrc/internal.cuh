@@ -30,7 +30,17 @@ enum Flag : int {
 };
 // 64-bit counters (Ctx::dcount)
 enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_SMEM = 6,
-                   C_QUEUE = 7, C_WALLS = 8, C_MAXRODS = 9, C_SMEM1 = 10, C_NCOUNT = 11 };
+                   C_QUEUE = 7, C_WALLS = 8, C_MAXRODS = 9, C_SMEM1 = 10, C_MEFF = 11, C_NCOUNT = 12 };
+
+// Constraint count of a launch: m itself, or, for a step that runs without
+// host readbacks (a captured graph: grids sized for the capacity m), the
+// count the device holds in *mdev, at most m.
+__device__ __forceinline__ int count_of(int m, const unsigned long long* mdev)
+{
+    if (!mdev) return m;
+    const unsigned long long v = *mdev;
+    return v < (unsigned long long)m ? (int)v : m;
+}
 
 // ------------------------------------------------------------ plain structs
 
@@ -301,6 +311,22 @@ struct aLENS_ctx {
     int solve_threads, solve_bps;
     int solve_barriers;      // 1: one-barrier solver where its share fits (default); 2: the two-barrier kernels
     int last_solver;         // kernel of the last single-system solve: 1 one-barrier, 2 two-barrier staged, 3 two-barrier global
+    // batched steps as a captured CUDA graph (aLENS_set_batch_graph)
+    const unsigned long long* mdev;   // while recording a graph: the device's constraint count (else NULL)
+    int batch_graph;         // graph mode on
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    cudaStream_t cap_stream; // the graph is recorded here (the legacy default stream cannot be captured)
+    int graph_launches;      // kernels in the graph
+    int graph_state;         // 0 nothing, 1 the key below ran eagerly once, 2 a graph of it is instantiated
+    struct GraphKey {
+        int64_t n;
+        const void* ptr[6];  // x, quat, f_nc, pairs_out, gamma_out, vel_out
+        aLENS_params p;
+        double beta;
+        int threads, cluster, tables;
+    } gkey;
+    int tables_epoch;        // bumped whenever the batch tables change
     int coop_ok;
     int launches;            // kernels launched since the entry point began
     // batches (aLENS_step_batch): per-system table and per-rod system id;
@@ -359,6 +385,8 @@ cudaError_t launch_search(aLENS_ctx* ctx, int n);
 // Exact pair count only (float64 inline), for a candidate-buffer overflow.
 cudaError_t launch_search_count(aLENS_ctx* ctx, int n);
 cudaError_t launch_emit_pairs(aLENS_ctx* ctx, int n, int32_t* pairs_out);
+cudaError_t launch_check_capacity(aLENS_ctx* ctx);
+cudaError_t launch_copy_pairs(aLENS_ctx* ctx, int32_t* pairs_out);
 
 // assemble.cu
 cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, double* phi, double* dgeom,

@@ -375,7 +375,7 @@ __global__ void k_decide(int np, Geo g0, const SysGeo* __restrict__ systab, cons
 // Pairs of rod i in (j, image) order: the kept candidates of its segment.
 __global__ void k_emit(int n, const int* __restrict__ rod_ncand, const long long* __restrict__ rod_tmpstart,
                        const int* __restrict__ rowP, const unsigned long long* __restrict__ cand,
-                       const unsigned char* __restrict__ keep, int32_t* __restrict__ out)
+                       const unsigned char* __restrict__ keep, int32_t* __restrict__ out, long long cap)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -383,6 +383,7 @@ __global__ void k_emit(int n, const int* __restrict__ rod_ncand, const long long
     long long s = rod_tmpstart[i];
     long long o = rowP[i];
     for (int u = 0; u < c; ++u) {
+        if (o >= cap) break;   // more pairs than the output holds (a step without readbacks reports CAPACITY)
         if (!keep[s + u]) continue;
         uint32_t key = (uint32_t)cand[s + u];
         out[3 * o + 0] = i;
@@ -457,9 +458,45 @@ cudaError_t launch_emit_pairs(aLENS_ctx* ctx, int n, int32_t* pairs_out)
     if (e != cudaSuccess) return e;
     if (n > 0) {
         k_emit<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, ctx->rod_ncand, ctx->rod_tmpstart, ctx->rowP, ctx->cand,
-                                                      ctx->keep, pairs_out);
+                                                      ctx->keep, pairs_out, ctx->max_pairs);
         ++ctx->launches;
     }
+    return cudaGetLastError();
+}
+
+// The step's capacity test on the device: the kept pairs fit the constraint
+// arrays and every candidate fit its buffer, else ALENS_ERR_CAPACITY.
+// C_MEFF is the constraint count the later kernels of the step take (0
+// after a failure, so that they do nothing).
+__global__ void k_check_capacity(long long max_pairs, long long cand_cap, unsigned long long* counters, int* flags)
+{
+    if (threadIdx.x != 0) return;
+    const unsigned long long mu = counters[C_PAIRS];
+    const bool over = mu > (unsigned long long)max_pairs || counters[C_CAND] > (unsigned long long)cand_cap;
+    if (over) atomicCAS(&flags[F_ERR], 0, ALENS_ERR_CAPACITY);
+    counters[C_MEFF] = (over || flags[F_ERR] != 0) ? 0ull : mu;
+}
+
+cudaError_t launch_check_capacity(aLENS_ctx* ctx)
+{
+    k_check_capacity<<<1, 32, 0, ctx->stream>>>(ctx->max_pairs, ctx->cand_cap, ctx->dcount, ctx->dflags);
+    ++ctx->launches;
+    return cudaGetLastError();
+}
+
+// The step's pair list to the caller: *mdev triples (i, j, image).
+__global__ void k_copy_pairs(long long cap, const unsigned long long* __restrict__ mdev, const int32_t* __restrict__ src,
+                             int32_t* __restrict__ dst)
+{
+    const long long m = (long long)count_of((int)cap, mdev);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 3 * m; k += (long long)gridDim.x * blockDim.x)
+        dst[k] = src[k];
+}
+
+cudaError_t launch_copy_pairs(aLENS_ctx* ctx, int32_t* pairs_out)
+{
+    k_copy_pairs<<<ctx->num_sms * 4, 256, 0, ctx->stream>>>(ctx->max_pairs, ctx->mdev, ctx->pairs, pairs_out);
+    ++ctx->launches;
     return cudaGetLastError();
 }
 

@@ -1919,10 +1919,11 @@ __global__ void k_sys_order(int ns, const long long* __restrict__ sysoff, const 
 // gamma back in the caller's pair order.
 template <typename T>
 __global__ void k_gamma_out(int m, const int* __restrict__ flags, const int* __restrict__ perm, const T* gg0,
-                            const T* gg1, const double* __restrict__ scale64, double* __restrict__ out)
+                            const T* gg1, const double* __restrict__ scale64, double* __restrict__ out,
+                            const unsigned long long* __restrict__ mdev)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m) return;
+    if (c >= count_of(m, mdev)) return;
     if (flags[F_SOLVE_ERR] != 0) return;
     const T* g = flags[F_FINAL] == 0 ? gg0 : gg1;
     // sigma_c (gamma_ref + gamma_lo + delta): the scaled iterate mapped back
@@ -2106,8 +2107,17 @@ static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int
     const long long sort_bytes = 10 * (long long)a.sort_cap;
     a.sort_ns = cap > 0 && sort_bytes <= 64 * 1024;
     const size_t smem = a.sort_ns ? (size_t)sort_bytes : 0;
-    if ((e = cudaFuncSetAttribute(k_bbpgd_sys<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
+    // the attribute is the largest dynamic shared memory a launch may ask
+    // for: raised when a batch needs more, never lowered, so that no call is
+    // made when nothing changes (a batched step may be recorded as a graph)
+    static size_t smem_set[64];
+    const int dv = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
+    if (smem > smem_set[dv]) {
+        if ((e = cudaFuncSetAttribute(k_bbpgd_sys<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        smem_set[dv] = smem;
+    }
     cfg.blockDim = dim3((unsigned)ctx->batch_threads);
     cfg.gridDim = dim3((unsigned)ctx->batch_cluster);
     cfg.dynamicSmemBytes = smem;
@@ -2139,10 +2149,10 @@ cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma
     int b = (m + 255) / 256;
     if (precision == ALENS_MIXED) {
         k_gamma_out<float><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->perm, ctx->sb32.gg[0], ctx->sb32.gg[1],
-                                                       ctx->scale64, gamma_out);
+                                                       ctx->scale64, gamma_out, ctx->mdev);
     } else {
         k_gamma_out<double><<<b, 256, 0, ctx->stream>>>(m, ctx->dflags, ctx->perm, ctx->sb64.gg[0], ctx->sb64.gg[1],
-                                                        ctx->scale64, gamma_out);
+                                                        ctx->scale64, gamma_out, ctx->mdev);
     }
     ++ctx->launches;
     return cudaGetLastError();

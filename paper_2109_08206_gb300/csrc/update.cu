@@ -13,11 +13,13 @@ __global__ void k_update(int n, int np, bool have_uc, Geo g0, const SysGeo* __re
                          const int* __restrict__ sysid, const int* __restrict__ flags,
                          const double* __restrict__ xw, const double* __restrict__ unc, const T* __restrict__ Uref,
                          const T* __restrict__ dU, const int* __restrict__ rank, double* __restrict__ x,
-                         double* __restrict__ quat, double* __restrict__ vel_out)
+                         double* __restrict__ quat, double* __restrict__ vel_out,
+                         const unsigned long long* __restrict__ mdev)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (flags[F_ERR] != 0 || flags[F_SOLVE_ERR] != 0) return;   // leave the state untouched after a failure
+    if (mdev) have_uc = *mdev > 0;   // a step without readbacks: the device's constraint count
     const Geo& g = geo_of(g0, systab, sysid, i);
     double U[6];
     const int r = rank ? rank[i] : i;   // the solver's position of rod i
@@ -59,11 +61,11 @@ cudaError_t launch_update(aLENS_ctx* ctx, int n, int m, double* x, double* quat,
     int np = (int)ctx->max_rods;
     if (precision == ALENS_MIXED) {
         k_update<float><<<b, 256, 0, ctx->stream>>>(n, np, m > 0, ctx->geo, ctx->cur_systab, ctx->cur_sysid, ctx->dflags, ctx->xw, ctx->unc, ctx->sb32.Uref, ctx->sb32.U, rank, x, quat,
-                                                    vel_out);
+                                                    vel_out, ctx->mdev);
         ++ctx->launches;
     } else {
         k_update<double><<<b, 256, 0, ctx->stream>>>(n, np, m > 0, ctx->geo, ctx->cur_systab, ctx->cur_sysid, ctx->dflags, ctx->xw, ctx->unc, ctx->sb64.Uref, ctx->sb64.U, rank, x, quat,
-                                                     vel_out);
+                                                     vel_out, ctx->mdev);
         ++ctx->launches;
     }
     return cudaGetLastError();

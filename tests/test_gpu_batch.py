@@ -228,3 +228,68 @@ def test_autotune_batch_picks_and_caches():
         assert info.status == 0
         assert T.apply_cached(ctx, "batch", A.MIXED, int(off[-1]), info.n_pairs, len(systems))
 
+
+
+@pytest.mark.parametrize("precision,tol", [(A.FP64, 1e-10), (A.MIXED, 1e-6)])
+def test_batch_graph_replay_equals_eager_steps(precision, tol):
+    """aLENS_set_batch_graph: four steps of the small batch from one state;
+    the first runs without a graph, the second records the graph, the last
+    two replay it.  Every output equals that of steps without a graph bit
+    for bit, the step's counters come back, and a context that changes its
+    buffers starts over without a graph."""
+    systems = small_batch()
+    off, x, quat, fnc, spec = W.batch_arrays(systems)
+    n = int(off[-1])
+
+    def steps(graph):
+        out = []
+        with batch_ctx(systems, precision, tol) as ctx:
+            if graph:
+                ctx.set_batch_graph(True)
+            xd, qd, fd = dev(x), dev(quat), dev(fnc)
+            pr = torch.empty((ctx.max_pairs, 3), dtype=torch.int32, device="cuda")
+            gam = torch.empty(ctx.max_pairs, dtype=torch.float64, device="cuda")
+            vel = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+            for k in range(4):
+                xd.copy_(dev(x)); qd.copy_(dev(quat))
+                info = ctx.step_batch(spec, off, xd, qd, fd, pairs_out=pr, gamma_out=gam, vel_out=vel)
+                m = info.n_pairs
+                its, res = ctx.batch_results(len(systems))
+                out.append((host(xd), host(qd), host(pr)[:m], host(gam)[:m], host(vel), info.as_dict(), its, res))
+            if graph:
+                # new buffers: another key, so this step runs without the graph and still matches
+                x2, q2 = dev(x), dev(quat)
+                info = ctx.step_batch(spec, off, x2, q2, fd)
+                assert np.array_equal(host(x2), out[0][0]) and info.n_pairs == out[0][5]["n_pairs"]
+        return out
+
+    eager, graph = steps(False), steps(True)
+    for k in range(4):
+        for a, b in zip(eager[k][:5], graph[k][:5]):
+            assert np.array_equal(a, b), k
+        ie, ig = eager[k][5], graph[k][5]
+        for f in ("n_pairs", "n_overlap", "iters", "status", "residual", "min_gap"):
+            assert ie[f] == ig[f], (k, f)
+        assert np.array_equal(eager[k][6], graph[k][6]) and np.array_equal(eager[k][7], graph[k][7])
+        assert ig["ms_solve"] > 0.0 and ig["solver"] == 4
+    assert graph[3][5]["launches"] == graph[2][5]["launches"]
+
+
+def test_batch_graph_capacity_leaves_the_state_untouched():
+    """A replayed graph whose pairs exceed the capacity moves no rod and
+    reports CAPACITY with the required count, like a step without a graph."""
+    systems = small_batch()
+    off, x, quat, fnc, spec = W.batch_arrays(systems)
+    n = int(off[-1])
+    with batch_ctx(systems, A.FP64, 1e-10) as big:
+        need = big.step_batch(spec, off, dev(x), dev(quat), dev(fnc)).n_pairs
+    s0 = systems[0]
+    p = A.make_params(s0.box, s0.diameter, s0.length, s0.viscosity, s0.dt, s0.delta_c, 1e-10, 400000, A.FP64)
+    with A.Context(p, n, need - 1) as ctx:
+        ctx.set_batch_graph(True)
+        xd, qd, fd = dev(x), dev(quat), dev(fnc)
+        for k in range(3):   # eager, recorded, replayed
+            with pytest.raises(A.AlensError) as e:
+                ctx.step_batch(spec, off, xd, qd, fd)
+            assert e.value.status == 2 and e.value.extra["n_pairs"] == need, k
+            assert np.array_equal(host(xd), x) and np.array_equal(host(qd), quat)
