@@ -726,7 +726,7 @@ def run_ours(args):
     if sib is not None:
         shape, times = tune_on_sibling(head)
         T.apply(ctx, kind, shape)
-        tuned = {"shape": list(shape), "ms_solve": times,
+        tuned = {"shape": list(shape), "cost": times, "cost_unit": T.cost_unit(kind),
                  "tuned_on": f"{sib.name}, another seed of the same workload class"}
     shape_now = tuple(tuned["shape"]) if tuned else default_shape
     if isinstance(job, BatchJob):

@@ -392,7 +392,7 @@ ALENS_API aLENS_status aLENS_set_scaling(aLENS_ctx* ctx, double beta);
 ALENS_API aLENS_status aLENS_inject_fault(aLENS_ctx* ctx, int32_t mode);
 
 /* Launch shape of the solver kernel: threads per block (multiple of 32,
- * <= 1024; default 1024) and blocks per SM (0 = as many as fit).  For tuning. */
+ * <= 1024; default 768) and blocks per SM (0 = one).  For tuning. */
 ALENS_API aLENS_status aLENS_set_launch(aLENS_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 
 /* Grid-wide synchronisations per BBPGD iteration (Appendix "Implementation":

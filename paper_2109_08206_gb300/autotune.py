@@ -3,7 +3,13 @@
 The solver's launch shape changes only how the work is spread, never what is
 computed (each candidate runs the same BBPGD to the same tolerance), so the
 tuner times the solve phase of one real step per candidate and keeps the
-fastest.  Results are cached in ``_build/tune.json`` per workload class:
+cheapest.  For a single system the score is the solve time per BBPGD
+iteration: the shape also sets the order of the float32 block sums, and the
+Barzilai-Borwein iteration count reacts to that order by tens of per cent in
+either direction without any trend, so a whole-solve time would mostly rank
+the luck of that count.  A batch scores its whole solve time, in which the
+counts of hundreds of systems average out.  Results are cached in
+``_build/tune.json`` per workload class:
 kind (single system or batch), precision, and the bucketed ratios that set
 the per-iteration work - constraints per rod (N_c/N, half-octave buckets) and
 rods per system (octave buckets).  ``apply_cached`` sets a cached shape on a
@@ -21,7 +27,8 @@ from pathlib import Path
 
 _CACHE = Path(__file__).resolve().parent / "_build" / "tune.json"
 
-SINGLE_CANDIDATES = ((1024, 1), (512, 2), (512, 1), (256, 4), (768, 1))
+SINGLE_CANDIDATES = ((768, 1), (1024, 1), (512, 1), (512, 2), (256, 4))
+TIE = 0.01   # a candidate must beat an earlier one by this fraction to be preferred
 BATCH_CANDIDATES = ((1024, 8), (1024, 4), (512, 4), (512, 2))
 
 
@@ -38,9 +45,9 @@ def _load() -> dict:
         return {}
 
 
-def _store(key: str, shape, ms: dict):
+def _store(key: str, shape, cost: dict):
     d = _load()
-    d[key] = {"shape": list(shape), "ms_solve": ms}
+    d[key] = {"shape": list(shape), "cost": cost, "unit": cost_unit(key.split(":")[0])}
     _CACHE.parent.mkdir(parents=True, exist_ok=True)
     _CACHE.write_text(json.dumps(d, indent=1, sort_keys=True))
 
@@ -63,6 +70,16 @@ def apply(ctx, kind: str, shape):
 _set = apply
 
 
+def cost_unit(kind: str) -> str:
+    return "ms per batched solve" if kind == "batch" else "us per BBPGD iteration"
+
+
+def _cost(kind: str, info) -> float:
+    if kind == "batch":
+        return info.ms_solve
+    return 1e3 * info.ms_solve / max(info.iters, 1)
+
+
 def _tune(ctx, kind, key, run, candidates, reps):
     times = {}
     for shape in candidates:
@@ -72,9 +89,12 @@ def _tune(ctx, kind, key, run, candidates, reps):
             info = run()
             if info.status not in (0, 3):   # OK or NOT_CONVERGED: the timing is valid
                 break
-            best = min(best, info.ms_solve)
+            best = min(best, _cost(kind, info))
         times[f"{shape[0]}x{shape[1]}"] = best
-    shape = min(candidates, key=lambda s: times[f"{s[0]}x{s[1]}"])
+    # the first candidate within TIE of the best: timing noise between
+    # near-equal shapes does not flip the pick
+    best = min(times.values())
+    shape = next(s for s in candidates if times[f"{s[0]}x{s[1]}"] <= best * (1.0 + TIE))
     _set(ctx, kind, shape)
     _store(key, shape, times)
     return shape, times
@@ -82,7 +102,8 @@ def _tune(ctx, kind, key, run, candidates, reps):
 
 def tune_single(ctx, x, quat, f_nc, precision: int, candidates=SINGLE_CANDIDATES, reps: int = 2):
     """Time aLENS_step's solve for each (threads, blocks per SM); x and quat
-    are restored before every step.  Returns (best shape, {shape: ms})."""
+    are restored before every step.  Returns (best shape, {shape: us per
+    iteration})."""
     x0, q0 = x.clone(), quat.clone()
 
     def run():
@@ -100,7 +121,8 @@ def tune_single(ctx, x, quat, f_nc, precision: int, candidates=SINGLE_CANDIDATES
 
 def tune_batch(ctx, systems, rod_offset, x, quat, f_nc, precision: int, candidates=BATCH_CANDIDATES,
                reps: int = 2):
-    """Time aLENS_step_batch's solve for each (threads, blocks per cluster)."""
+    """Time aLENS_step_batch's solve for each (threads, blocks per cluster).
+    Returns (best shape, {shape: ms per solve})."""
     x0, q0 = x.clone(), quat.clone()
 
     def run():

@@ -6,8 +6,10 @@
 // blockdef: q = Phi/h + D^T M F_nc.
 //
 // k_assemble: one thread per pair; float64 closest points, Phi, the 9 values
-// (e, y_P x e, y_Q x e) and q.  Overlap count and minimum gap are reduced per
-// warp before one atomic each.
+// (e, y_P x e, y_Q x e) and q, with fused multiply-adds and one reciprocal
+// for the normal (the FP64 pipe bounds the kernel; the keep/drop decision
+// upstream rounds unfused, like the oracle).  Overlap count and minimum gap
+// are reduced per warp before one atomic each.
 //
 // Solver layout (k_setup_*): constraint-major records in the solver's
 // working precision, the P-side CSR (pairs sorted by i make each rod's
@@ -58,18 +60,18 @@ __global__ void k_assemble(int m, int n, int np, Geo g0, const SysGeo* __restric
                 p[a] = axis[a * (size_t)np + i];
                 qv[a] = axis[a * (size_t)np + j];
             }
-            double s, t;
-            double dist = segment_closest<double>(dx, p, qv, g.half, kParallelDet64, s, t);
-            double yP[3], yQ[3], r[3], e[3];
+            double s, t, r[3];
+            const double dist = segment_closest<double, true>(dx, p, qv, g.half, kParallelDet64, s, t, r);
+            double yP[3], yQ[3], e[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 yP[a] = s * p[a];
                 yQ[a] = t * qv[a];
-                r[a] = dx[a] + yP[a] - yQ[a];
             }
             if (dist > 0.0) {
+                const double inv = 1.0 / dist;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) e[a] = r[a] / dist;
+                for (int a = 0; a < 3; ++a) e[a] = r[a] * inv;
             } else {
                 // centrelines touch: normal of the two axes, turned towards P;
                 // collinear axes: along the axis, towards P; coincident: e_x
@@ -90,8 +92,10 @@ __global__ void k_assemble(int m, int n, int np, Geo g0, const SysGeo* __restric
                     }
                 }
             }
-            double ta[3] = {yP[1] * e[2] - yP[2] * e[1], yP[2] * e[0] - yP[0] * e[2], yP[0] * e[1] - yP[1] * e[0]};
-            double tb[3] = {yQ[1] * e[2] - yQ[2] * e[1], yQ[2] * e[0] - yQ[0] * e[2], yQ[0] * e[1] - yQ[1] * e[0]};
+            const double ta[3] = {fma(yP[1], e[2], -(yP[2] * e[1])), fma(yP[2], e[0], -(yP[0] * e[2])),
+                                  fma(yP[0], e[1], -(yP[1] * e[0]))};
+            const double tb[3] = {fma(yQ[1], e[2], -(yQ[2] * e[1])), fma(yQ[2], e[0], -(yQ[0] * e[2])),
+                                  fma(yQ[0], e[1], -(yQ[1] * e[0]))};
             double* dg = dgeom + 9 * (size_t)c;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -103,8 +107,9 @@ __global__ void k_assemble(int m, int n, int np, Geo g0, const SysGeo* __restric
             double dtu = 0.0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                dtu += e[a] * (unc[a * (size_t)np + i] - unc[a * (size_t)np + j]);
-                dtu += ta[a] * unc[(3 + a) * (size_t)np + i] - tb[a] * unc[(3 + a) * (size_t)np + j];
+                dtu = fma(e[a], unc[a * (size_t)np + i] - unc[a * (size_t)np + j], dtu);
+                dtu = fma(ta[a], unc[(3 + a) * (size_t)np + i], dtu);
+                dtu = fma(-tb[a], unc[(3 + a) * (size_t)np + j], dtu);
             }
             phi[c] = ph;
             q[c] = ph / g.dt + dtu;

@@ -71,6 +71,20 @@ int make_geo(const aLENS_params* p, Geo* g, Mob* mob)
     g->rcut_screen2 = (float)((g->rcut + margin) * (g->rcut + margin));
     double dmax = p->diameter + p->delta_c + margin;
     g->screen_d2 = (float)(dmax * dmax);
+    // keep side of the float32 screen: the float closest points are points
+    // of the two segments (clamped to half_f, at most one float ulp past the
+    // ends), so their exact distance bounds the pair's minimum distance from
+    // above; the float evaluation of that distance is off by at most
+    // sqrt(3) (4 u B + 2 (L/2) u + 200 u) with u = 2^-24 and B the power of
+    // two above the box (positions and the image shift rounded to float, the
+    // axes rounded, a few float operations on values below 2^5 + L/2).  Twice
+    // that, plus 1e-5 D, below D + delta_c keeps the pair without float64.
+    double B = 1.0;
+    while (B < maxbox) B *= 2.0;
+    const double u = 1.0 / 16777216.0;
+    const double kmargin = 2.0 * sqrt(3.0) * (4.0 * u * B + p->length * u + 200.0 * u) + 1e-5 * p->diameter;
+    const double dkeep = p->diameter + p->delta_c - kmargin;
+    g->keep_d2 = dkeep > 0.0 ? (float)(dkeep * dkeep) : 0.0f;
     g->half_f = (float)(0.5 * p->length);
     double zperp = 4.0 * M_PI * p->viscosity * p->length / log(2.0 * p->length / p->diameter);
     mob->inv_perp = 1.0 / zperp;
@@ -89,7 +103,7 @@ cudaError_t dmalloc(P** ptr, size_t bytes)
 void free_all(aLENS_ctx* c)
 {
     void* ptrs[] = {c->xw, c->axis, c->unc, c->pos32, c->ax32, c->cellkey, c->sorted_id, c->spos32, c->sax32,
-                    c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand, c->keep,
+                    c->cell_count, c->cell_start, c->cell_cursor, c->rod_count, c->rod_ncand, c->rod_tmpstart, c->cand,
                     c->rowP, c->rowQ, c->cntQ, c->curQ, c->qlist, c->perm, c->rank, c->curP, c->ci, c->cj, c->pairs, c->phi, c->dgeom,
                     c->q64, c->scale64, c->solve_ws, c->partials, c->bstart, c->bar, c->dflags, c->dcount, c->scan_tmp,
                     c->systab, c->sysid, c->sysoff, c->sys_order, c->sys_iters, c->sys_res, c->adj_ws,
@@ -349,7 +363,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     c->stream = (cudaStream_t)cuda_stream;
     c->wait_s = 5.0;
     c->scale_beta = kDefaultScaleBeta;
-    c->solve_threads = 1024;
+    c->solve_threads = 768;   // the lowest time per iteration of 512, 768 and 1024 at 1e5 rods on 152 SMs
     c->solve_bps = 0;
     c->solve_barriers = 1;
     c->batch_threads = 1024;
@@ -386,7 +400,6 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->rod_tmpstart, np * sizeof(long long)) == cudaSuccess;
     c->cand_cap = 2 * (long long)mp + 4096;
     ok &= dmalloc(&c->cand, (size_t)c->cand_cap * sizeof(unsigned long long)) == cudaSuccess;
-    ok &= dmalloc(&c->keep, (size_t)c->cand_cap) == cudaSuccess;
     ok &= dmalloc(&c->rowP, (np + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->rowQ, (np + 1) * sizeof(int)) == cudaSuccess;
     ok &= dmalloc(&c->cntQ, (np + 1) * sizeof(int)) == cudaSuccess;

@@ -54,6 +54,7 @@ struct Geo {                 // everything the geometry kernels need
     float boxf[3];
     float rcut_screen2;      // (rcut + margin)^2 for the float pre-screen
     float screen_d2;         // (D + delta_c + margin)^2 for the float segment screen
+    float keep_d2;           // (D + delta_c - keep margin)^2: below it the float distance keeps the pair
     float half_f;            // L/2 in float
 };
 
@@ -118,26 +119,41 @@ __device__ __forceinline__ T clampv(T v, T lo, T hi)
     return v < lo ? lo : (v > hi ? hi : v);
 }
 
+// a b + c rounded once (FUSED) or twice.  The float64 keep/drop decision
+// rounds twice, like the oracle it must match bit for bit; the assembly of
+// Phi, D and q, which matches within tolerances, fuses.
+template <bool FUSED, typename T>
+__device__ __forceinline__ T madd(T a, T b, T c)
+{
+    if constexpr (FUSED) return fma(a, b, c);
+    else return a * b + c;
+}
+
+template <bool FUSED, typename T>
+__device__ __forceinline__ T dot3(const T u[3], const T v[3])
+{
+    if constexpr (FUSED) return fma(u[2], v[2], fma(u[1], v[1], u[0] * v[0]));
+    else return u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+}
+
 // Closest points of two segments {x_P + s p} and {x_Q + t q}, |s|,|t| <= hl,
 // given dx = x_P - x_Q.  Clamped-projection method: take the unconstrained
 // optimum s of the two infinite lines, clamp it, project onto Q for t; if
 // that t leaves Q, clamp t and re-project onto P.  Parallel segments
 // (det <= eps a c) whose projections overlap take s at the middle of the
-// overlap and t as its clamped projection.  Returns |dx + s p - t q|.
-template <typename T>
+// overlap and t as its clamped projection.  Leaves r = dx + s p - t q and
+// returns |r|.
+template <typename T, bool FUSED = false>
 __device__ __forceinline__ T segment_closest(const T dx[3], const T p[3], const T q[3], T hl, T det_eps, T& s_out,
-                                             T& t_out)
+                                             T& t_out, T r_out[3] = nullptr)
 {
-    T a = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
-    T b = p[0] * q[0] + p[1] * q[1] + p[2] * q[2];
-    T c = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
-    T d = p[0] * dx[0] + p[1] * dx[1] + p[2] * dx[2];
-    T e = q[0] * dx[0] + q[1] * dx[1] + q[2] * dx[2];
-    T det = a * c - b * b;
+    const T a = dot3<FUSED>(p, p), b = dot3<FUSED>(p, q), c = dot3<FUSED>(q, q);
+    const T d = dot3<FUSED>(p, dx), e = dot3<FUSED>(q, dx);
+    const T det = madd<FUSED>(a, c, -(b * b));
     T s, t;
     bool done = false;
     if (det > det_eps * a * c) {
-        s = clampv((b * e - c * d) / det, -hl, hl);
+        s = clampv(madd<FUSED>(b, e, -(c * d)) / det, -hl, hl);
     } else {
         // projections of Q's ends onto P's axis
         T e1 = (-b * hl - d) / a, e2 = (b * hl - d) / a;
@@ -145,28 +161,35 @@ __device__ __forceinline__ T segment_closest(const T dx[3], const T p[3], const 
         T olo = lo < -hl ? -hl : lo, ohi = hi > hl ? hl : hi;
         if (olo <= ohi) {
             s = T(0.5) * (olo + ohi);
-            t = clampv((b * s + e) / c, -hl, hl);
+            t = clampv(madd<FUSED>(b, s, e) / c, -hl, hl);
             done = true;
         } else {
             s = hi < -hl ? -hl : hl;   // P's end nearest to Q's projection
         }
     }
     if (!done) {
-        t = (b * s + e) / c;
+        t = madd<FUSED>(b, s, e) / c;
         if (t < -hl) {
             t = -hl;
-            s = clampv((b * t - d) / a, -hl, hl);
+            s = clampv(madd<FUSED>(b, t, -d) / a, -hl, hl);
         } else if (t > hl) {
             t = hl;
-            s = clampv((b * t - d) / a, -hl, hl);
+            s = clampv(madd<FUSED>(b, t, -d) / a, -hl, hl);
         }
     }
-    T r0 = dx[0] + s * p[0] - t * q[0];
-    T r1 = dx[1] + s * p[1] - t * q[1];
-    T r2 = dx[2] + s * p[2] - t * q[2];
+    T r[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if constexpr (FUSED) r[k] = fma(-t, q[k], fma(s, p[k], dx[k]));
+        else r[k] = dx[k] + s * p[k] - t * q[k];
+    }
     s_out = s;
     t_out = t;
-    return sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+    if (r_out) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r_out[k] = r[k];
+    }
+    return sqrt(dot3<FUSED>(r, r));
 }
 
 // ------------------------------------------------------------ scoped atomics
@@ -271,8 +294,7 @@ struct aLENS_ctx {
     int* rod_count;          // [np + 1] kept pairs per rod (i < j side)
     int* rod_ncand;          // [np] screened candidates per rod
     long long* rod_tmpstart; // [np] start of the rod's candidate segment
-    unsigned long long* cand;// [cand_cap] candidate keys (i << 32 | j << 5 | image)
-    unsigned char* keep;     // [cand_cap] float64 decision per candidate
+    unsigned long long* cand;// [cand_cap] candidate keys (i << 32 | undecided << 31 | j << 5 | image)
     long long cand_cap;
     int* rowP;               // [np + 1]
     int* rowQ;               // [np + 1]

@@ -10,9 +10,11 @@
 // Pipeline: k_pack (wrap centres, rod axis R(theta) e_z, cell key, M F_nc)
 // -> counting sort by cell key -> k_search (one warp per rod, rods visited
 // in cell order; lanes stride over the 27 neighbour cells; a float32 screen
-// with a safety margin, then the float64 keep/drop decision; warp-aggregated
-// appends into a per-rod list in shared memory, sorted there by (j, image))
-// -> scan of per-rod counts -> k_emit (pairs in (i, j, image) order).
+// that drops or keeps a candidate when its float distance is clear of
+// D + delta_c by proven margins and flags the rest; warp-aggregated appends
+// into a per-rod list in shared memory, sorted there by (j, image)) ->
+// k_decide (the float64 keep/drop decision of the flagged candidates) ->
+// scan of per-rod counts -> k_emit (pairs in (i, j, image) order).
 #include "internal.cuh"
 
 namespace alens {
@@ -144,22 +146,36 @@ __global__ void k_cell_gather(int n, const int* __restrict__ sorted_id, const fl
     sax32[k] = ax32[i];
 }
 
-// Float32 screen of one candidate.  Returns false only when the pair is
-// certainly farther apart than delta_c: the clamped closest-point pair below
-// is always a valid point pair of the two (float-rounded) segments, and away
-// from near-parallel axes it is the optimum up to rounding, so its squared
-// distance exceeds (D + delta_c + margin)^2 only if the float64 gap exceeds
-// delta_c.  Unit axes are taken as unit (a = c = 1); near-parallel pairs
-// (1 - (p.q)^2 <= 1e-4) always go on to the float64 decision.
-__device__ __forceinline__ bool screen32(const float4& pi, const float4& ai, const float4& pj, const float4& aj,
-                                         float sx, float sy, float sz, const Geo& g)
+// Float32 screen of one candidate: kScreenDrop when the pair is certainly
+// farther apart than delta_c, kScreenKeep when it is certainly closer, and
+// kScreenDecide for the float64 decision otherwise.  The clamped
+// closest-point pair below is always a valid point pair of the two
+// segments.  Drop: away from near-parallel axes it is the optimum up to
+// rounding, so its squared distance exceeds (D + delta_c + margin)^2 only if
+// the float64 gap exceeds delta_c.  Keep: its exact distance bounds the
+// pair's minimum from above, and its float distance is within the keep
+// margin of that exact distance (make_geo), so a float distance below
+// D + delta_c - margin means a gap below delta_c.  Unit axes are taken as
+// unit (a = c = 1); near-parallel pairs (1 - (p.q)^2 <= 1e-4) always go on
+// to the float64 decision.
+enum { kScreenDrop = 0, kScreenKeep = 1, kScreenDecide = 2 };
+
+// Low word of a candidate key: j << 5 | image code (j < 2^26), with bit 31
+// set while the float64 decision is pending; kDropped marks a candidate that
+// decision dropped.
+constexpr uint32_t kUndecided = 0x80000000u;
+constexpr uint32_t kKeyMask = 0x7fffffffu;
+constexpr uint32_t kDropped = 0xffffffffu;
+
+__device__ __forceinline__ int screen32(const float4& pi, const float4& ai, const float4& pj, const float4& aj,
+                                        float sx, float sy, float sz, const Geo& g)
 {
     float dx[3] = {pi.x - pj.x - sx, pi.y - pj.y - sy, pi.z - pj.z - sz};
     float r2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
-    if (!(r2 < g.rcut_screen2)) return false;
+    if (!(r2 < g.rcut_screen2)) return kScreenDrop;
     float b = ai.x * aj.x + ai.y * aj.y + ai.z * aj.z;
     float det = 1.0f - b * b;
-    if (det <= kParallelDet32) return true;
+    if (det <= kParallelDet32) return kScreenDecide;
     float d = ai.x * dx[0] + ai.y * dx[1] + ai.z * dx[2];
     float e = aj.x * dx[0] + aj.y * dx[1] + aj.z * dx[2];
     const float hl = g.half_f;
@@ -172,7 +188,9 @@ __device__ __forceinline__ bool screen32(const float4& pi, const float4& ai, con
     float r0 = dx[0] + s * ai.x - t * aj.x;
     float r1 = dx[1] + s * ai.y - t * aj.y;
     float r2b = dx[2] + s * ai.z - t * aj.z;
-    return r0 * r0 + r1 * r1 + r2b * r2b < g.screen_d2;
+    const float d2 = r0 * r0 + r1 * r1 + r2b * r2b;
+    if (d2 < g.keep_d2) return kScreenKeep;
+    return d2 < g.screen_d2 ? kScreenDecide : kScreenDrop;
 }
 
 // Float64 keep/drop decision of pair (i, j) at image shift k: surface gap
@@ -209,21 +227,24 @@ __device__ __forceinline__ void decode_cell(uint32_t key, int bits, int cc[3])
 // cut to the suffix of ids above i;
 // the warp then walks the concatenated candidates in full chunks of 32, each
 // lane finding its cell by a binary search over the prefix of the counts;
-// candidates j > i that pass the float32 screen are appended to a per-warp
-// list in shared memory with a warp ballot, sorted there by (j, image) with a
-// bitonic network, and written to the candidate buffer as 64-bit keys
-// (i << 32 | j << 5 | image).  COUNT_ONLY: decide in float64 inline and only
-// count the kept pairs (used when the candidate buffer overflows).
+// candidates j > i that the float32 screen keeps or cannot settle are
+// appended to a per-warp list in shared memory with a warp ballot, sorted
+// there by (j, image) with a bitonic network, and written to the candidate
+// buffer as 64-bit keys (i << 32 | kUndecided? | j << 5 | image); their count
+// goes to rod_count and the total, and k_decide takes the float64 decision
+// of the flagged few.  COUNT_ONLY: decide in float64 inline and only count
+// the kept pairs (used when the candidate buffer overflows).
 template <bool COUNT_ONLY>
 __global__ void __launch_bounds__(kSearchWarps * 32)
 k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __restrict__ sysid,
          const int* __restrict__ sorted_id, const float4* __restrict__ spos32,
          const float4* __restrict__ sax32, const uint32_t* __restrict__ cellkey, const double* __restrict__ xw,
          const double* __restrict__ axis, const int* __restrict__ cell_start, int* __restrict__ rod_ncand,
-         long long* __restrict__ rod_tmpstart, unsigned long long* __restrict__ cand, long long cand_cap,
-         unsigned long long* __restrict__ counters, int* __restrict__ flags)
+         int* __restrict__ rod_count, long long* __restrict__ rod_tmpstart, unsigned long long* __restrict__ cand,
+         long long cand_cap, unsigned long long* __restrict__ counters, int* __restrict__ flags)
 {
     __shared__ uint32_t list[COUNT_ONLY ? 1 : kSearchWarps][COUNT_ONLY ? 1 : kPairsPerRodCap];
+    __shared__ uint32_t ring[kSearchWarps][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x * kSearchWarps + warp;
     if (k >= n) return;   // uniform per warp
@@ -235,9 +256,11 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
     int cc[3];
     decode_cell(cellkey[i] - key_base, g.bits, cc);
     // the 27 neighbour cells, one per lane: each with the periodic image
-    // shift that brings it next to i's cell, its rod range and its image code
+    // shift that brings it next to i's cell (as a code and as a float
+    // offset), its rod range and its image code
     int cbeg = 0, ccnt = 0;
     uint32_t ccode = 0;
+    float csx = 0.0f, csy = 0.0f, csz = 0.0f;
     if (lane < 27) {
         const int d[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
         int c[3], sh[3];
@@ -249,6 +272,9 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
             else if (c[a] >= g.nc[a]) { c[a] -= g.nc[a]; sh[a] = 1; }
         }
         ccode = (uint32_t)((sh[0] + 1) + 3 * (sh[1] + 1) + 9 * (sh[2] + 1));
+        csx = (float)sh[0] * g.boxf[0];
+        csy = (float)sh[1] * g.boxf[1];
+        csz = (float)sh[2] * g.boxf[2];
         const uint32_t key = key_base + morton3(c[0], c[1], c[2]);
         int b = cell_start[key], e = cell_start[key + 1];
         // a cell's ids ascend (k_cell_sort_ids): the candidates j > i are a
@@ -271,38 +297,73 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     int cnt = 0;
-    // the candidates of all 27 cells in full chunks of 32 lanes
-    for (int base = 0; base < total; base += 32) {
-        const int t = base + lane;
-        int lo = 0, hi = 26;   // smallest o with incl[o] > t
+    // Two passes over the candidates of all 27 cells.  A: full chunks of 32
+    // lanes test the centre distance alone (the screen's first test, about
+    // one candidate in seven passes) and queue the passes, m | code << 26,
+    // in a per-warp ring.  B: every 32 queued candidates (and the rest at
+    // the end) take the whole float32 screen with all lanes busy.
+    uint32_t* Q = ring[warp];
+    int qh = 0, qn = 0;   // warp-uniform ring head and length (qn < 32 before each chunk)
+    for (int base = 0; base < total || qn > 0;) {
+        if (base < total) {
+            const int t = base + lane;
+            int lo = 0, hi = 26;   // smallest o with incl[o] > t
 #pragma unroll
-        for (int step = 0; step < 5; ++step) {
-            const int mid = (lo + hi) >> 1;
-            const int im = __shfl_sync(0xffffffffu, incl, mid);
-            if (im > t) hi = mid;
-            else lo = mid + 1;
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                const int im = __shfl_sync(0xffffffffu, incl, mid);
+                if (im > t) hi = mid;
+                else lo = mid + 1;
+            }
+            const int o = lo < 26 ? lo : 26;
+            const int ob = __shfl_sync(0xffffffffu, cbeg, o);
+            const int oc = __shfl_sync(0xffffffffu, ccnt, o);
+            const int oi = __shfl_sync(0xffffffffu, incl, o);
+            const uint32_t code = __shfl_sync(0xffffffffu, ccode, o);
+            const float sx = __shfl_sync(0xffffffffu, csx, o);
+            const float sy = __shfl_sync(0xffffffffu, csy, o);
+            const float sz = __shfl_sync(0xffffffffu, csz, o);
+            bool near = false;
+            int m = 0;
+            if (t < total) {
+                m = ob + (t - (oi - oc));
+                const float4 pj = spos32[m];
+                const float dx = pi.x - pj.x - sx, dy = pi.y - pj.y - sy, dz = pi.z - pj.z - sz;
+                near = dx * dx + dy * dy + dz * dz < g.rcut_screen2;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, near);
+            if (near) Q[(qh + qn + __popc(bal & ((1u << lane) - 1u))) & 63] = (uint32_t)m | (code << 26);
+            qn += __popc(bal);
+            base += 32;
+            __syncwarp();
         }
-        const int o = lo < 26 ? lo : 26;
-        const int ob = __shfl_sync(0xffffffffu, cbeg, o);
-        const int oc = __shfl_sync(0xffffffffu, ccnt, o);
-        const int oi = __shfl_sync(0xffffffffu, incl, o);
-        const uint32_t code = __shfl_sync(0xffffffffu, ccode, o);
-        bool keep = false;
-        int j = 0;
-        if (t < total) {
-            const int m = ob + (t - (oi - oc));
-            const int s0 = (int)(code % 3u) - 1, s1 = (int)((code / 3u) % 3u) - 1, s2 = (int)(code / 9u) - 1;
-            j = sorted_id[m];
-            keep = j > i && screen32(pi, ai, spos32[m], sax32[m], (float)s0 * g.boxf[0], (float)s1 * g.boxf[1],
-                                     (float)s2 * g.boxf[2], g);
-            if (COUNT_ONLY && keep) keep = decide64(i, j, s0, s1, s2, np, xw, axis, g);
+        if (qn >= 32 || (base >= total && qn > 0)) {
+            const int take = qn < 32 ? qn : 32;
+            const uint32_t e = lane < take ? Q[(qh + lane) & 63] : 0u;
+            qh = (qh + take) & 63;
+            qn -= take;
+            __syncwarp();   // read before the next chunk reuses the slots
+            bool keep = false;
+            int j = 0, sc = kScreenDrop;
+            const uint32_t code = e >> 26;
+            if (lane < take) {
+                const int m = (int)(e & 0x3ffffffu);
+                const int s0 = (int)(code % 3u) - 1, s1 = (int)((code / 3u) % 3u) - 1, s2 = (int)(code / 9u) - 1;
+                sc = screen32(pi, ai, spos32[m], sax32[m], (float)s0 * g.boxf[0], (float)s1 * g.boxf[1],
+                              (float)s2 * g.boxf[2], g);
+                keep = sc != kScreenDrop;
+                if (keep) j = sorted_id[m];
+                // counting decides in float64 here; the listing pass leaves it to k_decide
+                if (COUNT_ONLY && sc == kScreenDecide) keep = decide64(i, j, s0, s1, s2, np, xw, axis, g);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (!COUNT_ONLY && keep) {
+                const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                if (pos < kPairsPerRodCap)
+                    L[pos] = ((uint32_t)j << 5) | code | (sc == kScreenDecide ? kUndecided : 0u);
+            }
+            cnt += __popc(bal);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (!COUNT_ONLY && keep) {
-            const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-            if (pos < kPairsPerRodCap) L[pos] = ((uint32_t)j << 5) | code;
-        }
-        cnt += __popc(bal);
     }
     if (COUNT_ONLY) {
         if (lane == 0) atomicAdd(&counters[C_PAIRS], (unsigned long long)cnt);
@@ -316,7 +377,7 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
     // bitonic sort of L[0..cnt) padded to a power of two
     int P = 1;
     while (P < cnt) P <<= 1;
-    for (int u = cnt + lane; u < P; u += 32) L[u] = 0xffffffffu;
+    for (int u = cnt + lane; u < P; u += 32) L[u] = kKeyMask;
     __syncwarp();
     for (int size = 2; size <= P; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -325,7 +386,7 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
                 int hi = lo + stride;
                 bool up = (lo & size) == 0;
                 uint32_t a = L[lo], b = L[hi];
-                if ((a > b) == up) { L[lo] = b; L[hi] = a; }
+                if (((a & kKeyMask) > (b & kKeyMask)) == up) { L[lo] = b; L[hi] = a; }
             }
             __syncwarp();
         }
@@ -333,7 +394,9 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
     long long start = 0;
     if (lane == 0) {
         start = (long long)atomicAdd(&counters[C_CAND], (unsigned long long)cnt);
+        atomicAdd(&counters[C_PAIRS], (unsigned long long)cnt);
         rod_ncand[i] = cnt;
+        rod_count[i] = cnt;
         rod_tmpstart[i] = start;
     }
     start = __shfl_sync(0xffffffffu, start, 0);
@@ -342,40 +405,74 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
         if (start + u < cand_cap) cand[start + u] = hi | L[u];
 }
 
-// Float64 decision of every candidate (grid-stride, full warps): keep flag,
-// per-rod kept count and the total.
-__global__ void k_decide(int np, Geo g0, const SysGeo* __restrict__ systab, const int* __restrict__ sysid,
-                         const unsigned long long* counters_ro,
-                         const unsigned long long* __restrict__ cand, long long cand_cap,
-                         const double* __restrict__ xw, const double* __restrict__ axis,
-                         unsigned char* __restrict__ keep, int* __restrict__ rod_count,
-                         unsigned long long* counters)
+// Float64 decision of the candidates the float32 screen left undecided.  A
+// few per cent of the candidates carry the flag and the FP64 pipe executes a
+// warp instruction at full cost however few lanes are active, so each block
+// first gathers the flagged candidates of a chunk of kDecideChunk keys into
+// a list in shared memory (warp ballots) and then decides that list with
+// full warps: a kept candidate loses its flag, a dropped one becomes
+// kDropped and leaves its rod's count and the total.  Chunks go to blocks
+// round robin; the list holds a whole chunk, so any flagged fraction fits.
+constexpr int kDecideThreads = 256;
+constexpr int kDecideChunk = 8 * kDecideThreads;
+
+__global__ void __launch_bounds__(kDecideThreads)
+k_decide(int np, Geo g0, const SysGeo* __restrict__ systab, const int* __restrict__ sysid,
+         const unsigned long long* counters_ro, unsigned long long* __restrict__ cand, long long cand_cap,
+         const double* __restrict__ xw, const double* __restrict__ axis, int* __restrict__ rod_count,
+         unsigned long long* counters)
 {
+    __shared__ int list[kDecideChunk];
+    __shared__ int nlist;
     long long total = (long long)counters_ro[C_CAND];
     if (total > cand_cap) total = cand_cap;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k0 = (long long)blockIdx.x * blockDim.x; k0 < total; k0 += stride) {
-        long long k = k0 + threadIdx.x;
-        bool kp = false;
-        if (k < total) {
-            unsigned long long key = cand[k];
-            int i = (int)(key >> 32);
-            int j = (int)((key >> 5) & 0x7ffffffu);
-            int code = (int)(key & 31u);
-            kp = decide64(i, j, code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1, np, xw, axis,
-                          geo_of(g0, systab, sysid, i));
-            keep[k] = kp ? 1 : 0;
-            if (kp) atomicAdd(&rod_count[i], 1);
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * kDecideChunk; base < total;
+         base += (long long)gridDim.x * kDecideChunk) {
+        if (threadIdx.x == 0) nlist = 0;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kDecideChunk / kDecideThreads; ++r) {
+            const int off = r * kDecideThreads + threadIdx.x;
+            const bool f = base + off < total && ((uint32_t)cand[base + off] & kUndecided);
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            int at = 0;
+            if (lane == 0 && bal) at = atomicAdd(&nlist, __popc(bal));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (f) list[at + __popc(bal & ((1u << lane) - 1u))] = off;
         }
-        unsigned bal = __ballot_sync(0xffffffffu, kp);
-        if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&counters[C_PAIRS], (unsigned long long)__popc(bal));
+        __syncthreads();
+        const int nl = nlist;
+        for (int u0 = threadIdx.x - lane; u0 < nl; u0 += kDecideThreads) {   // whole warps
+            const int u = u0 + lane;
+            bool drop = false;
+            if (u < nl) {
+                const long long k = base + list[u];
+                const unsigned long long key = cand[k];
+                const uint32_t lo = (uint32_t)key;
+                const int i = (int)(key >> 32);
+                const int j = (int)((lo & kKeyMask) >> 5);
+                const int code = (int)(lo & 31u);
+                const bool kp = decide64(i, j, code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1, np, xw, axis,
+                                         geo_of(g0, systab, sysid, i));
+                cand[k] = (key & 0xffffffff00000000ull) | (kp ? (lo & kKeyMask) : kDropped);
+                if (!kp) {
+                    atomicSub(&rod_count[i], 1);
+                    drop = true;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, drop);
+            if (lane == 0 && bal) atomicAdd(&counters[C_PAIRS], 0ull - (unsigned long long)__popc(bal));
+        }
+        __syncthreads();   // the list is rebuilt for the next chunk
     }
 }
 
-// Pairs of rod i in (j, image) order: the kept candidates of its segment.
+// Pairs of rod i in (j, image) order: its segment of the candidate buffer
+// less the candidates k_decide dropped.
 __global__ void k_emit(int n, const int* __restrict__ rod_ncand, const long long* __restrict__ rod_tmpstart,
                        const int* __restrict__ rowP, const unsigned long long* __restrict__ cand,
-                       const unsigned char* __restrict__ keep, int32_t* __restrict__ out, long long cap)
+                       int32_t* __restrict__ out, long long cap)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -384,8 +481,8 @@ __global__ void k_emit(int n, const int* __restrict__ rod_ncand, const long long
     long long o = rowP[i];
     for (int u = 0; u < c; ++u) {
         if (o >= cap) break;   // more pairs than the output holds (a step without readbacks reports CAPACITY)
-        if (!keep[s + u]) continue;
-        uint32_t key = (uint32_t)cand[s + u];
+        const uint32_t key = (uint32_t)cand[s + u];
+        if (key == kDropped) continue;
         out[3 * o + 0] = i;
         out[3 * o + 1] = (int32_t)(key >> 5);
         out[3 * o + 2] = (int32_t)(key & 31u);
@@ -430,13 +527,12 @@ cudaError_t launch_search(aLENS_ctx* ctx, int n)
     if (n <= 0) return cudaSuccess;
     k_search<false><<<nblk(n, kSearchWarps), kSearchWarps * 32, 0, ctx->stream>>>(
         n, (int)ctx->max_rods, ctx->geo, ctx->cur_systab, ctx->cur_sysid, ctx->sorted_id, ctx->spos32, ctx->sax32,
-        ctx->cellkey, ctx->xw, ctx->axis, ctx->cell_start, ctx->rod_ncand, ctx->rod_tmpstart, ctx->cand, ctx->cand_cap,
-        ctx->dcount, ctx->dflags);
+        ctx->cellkey, ctx->xw, ctx->axis, ctx->cell_start, ctx->rod_ncand, ctx->rod_count, ctx->rod_tmpstart, ctx->cand,
+        ctx->cand_cap, ctx->dcount, ctx->dflags);
     ++ctx->launches;
-    k_decide<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>((int)ctx->max_rods, ctx->geo, ctx->cur_systab, ctx->cur_sysid,
-                                                         ctx->dcount, ctx->cand,
-                                                         ctx->cand_cap, ctx->xw, ctx->axis, ctx->keep,
-                                                         ctx->rod_count, ctx->dcount);
+    k_decide<<<ctx->num_sms, kDecideThreads, 0, ctx->stream>>>((int)ctx->max_rods, ctx->geo, ctx->cur_systab,
+                                                        ctx->cur_sysid, ctx->dcount, ctx->cand, ctx->cand_cap,
+                                                        ctx->xw, ctx->axis, ctx->rod_count, ctx->dcount);
     ++ctx->launches;
     return cudaGetLastError();
 }
@@ -446,8 +542,8 @@ cudaError_t launch_search_count(aLENS_ctx* ctx, int n)
     if (n <= 0) return cudaSuccess;
     k_search<true><<<nblk(n, kSearchWarps), kSearchWarps * 32, 0, ctx->stream>>>(
         n, (int)ctx->max_rods, ctx->geo, ctx->cur_systab, ctx->cur_sysid, ctx->sorted_id, ctx->spos32, ctx->sax32,
-        ctx->cellkey, ctx->xw, ctx->axis, ctx->cell_start, ctx->rod_ncand, ctx->rod_tmpstart, ctx->cand, ctx->cand_cap,
-        ctx->dcount, ctx->dflags);
+        ctx->cellkey, ctx->xw, ctx->axis, ctx->cell_start, ctx->rod_ncand, ctx->rod_count, ctx->rod_tmpstart, ctx->cand,
+        ctx->cand_cap, ctx->dcount, ctx->dflags);
     ++ctx->launches;
     return cudaGetLastError();
 }
@@ -458,7 +554,7 @@ cudaError_t launch_emit_pairs(aLENS_ctx* ctx, int n, int32_t* pairs_out)
     if (e != cudaSuccess) return e;
     if (n > 0) {
         k_emit<<<nblk(n, 256), 256, 0, ctx->stream>>>(n, ctx->rod_ncand, ctx->rod_tmpstart, ctx->rowP, ctx->cand,
-                                                      ctx->keep, pairs_out, ctx->max_pairs);
+                                                      pairs_out, ctx->max_pairs);
         ++ctx->launches;
     }
     return cudaGetLastError();

@@ -1198,6 +1198,7 @@ __device__ void carve1(Own1<T>& o, unsigned char* base)
 template <typename T>
 struct Shared1 {
     T red[32][4];
+    T tot[4];   // grid totals of the last barrier's block sums (warps 1-4, one each)
     T alpha;
     int kind, ng;
 };
@@ -1611,27 +1612,36 @@ __device__ __forceinline__ void block_store(T (*red)[4], T* dst, int stride)
     }
 }
 
-// One warp: the grid totals of the fetched block sums (fixed order, so
-// every block gets the same numbers); every lane returns them.
+// One warp: the grid total of row u of the fetched block sums (sums for
+// u < 3, the maximum for u = 3), in a fixed order, so every block gets the
+// same numbers; every lane returns it.
 template <typename T>
-__device__ __forceinline__ void warp_totals(const Own1<T>& o, int nb, T tot[4])
+__device__ __forceinline__ T row_total(const Own1<T>& o, int nb, int u)
 {
     const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const T* row = o.tot + (size_t)u * o.nbp;
-        T w = T(0);
-        for (int b = lane; b < nb; b += 32) {
-            const T x = row[b];
-            w = u == 3 ? (x > w ? x : w) : w + x;
-        }
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-            const T y = __shfl_xor_sync(0xffffffffu, w, s);
-            w = u == 3 ? (y > w ? y : w) : w + y;
-        }
-        tot[u] = w;
+    const T* row = o.tot + (size_t)u * o.nbp;
+    T w = T(0);
+    for (int b = lane; b < nb; b += 32) {
+        const T x = row[b];
+        w = u == 3 ? (x > w ? x : w) : w + x;
     }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const T y = __shfl_xor_sync(0xffffffffu, w, s);
+        w = u == 3 ? (y > w ? y : w) : w + y;
+    }
+    return w;
+}
+
+// The four totals, one warp each: warps 1-4 store them in shared memory and
+// meet on a named barrier (warp 0 meanwhile stores the block's own sums).
+template <typename T>
+__device__ __forceinline__ void warps_totals(const Own1<T>& o, int nb, T* tot)
+{
+    const int u = (int)(threadIdx.x >> 5) - 1;
+    const T w = row_total(o, nb, u);
+    if ((threadIdx.x & 31) == 0) tot[u] = w;
+    asm volatile("bar.sync 1, 128;\n" ::: "memory");
 }
 
 // Loop states: what the last constraint phase was (its sums are what the
@@ -1686,9 +1696,9 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
         tot_fetch(o, part + pw * pstride);
         tot_wait();
         __syncthreads();
-        if (warp == 1) {
-            T tot[4];
-            warp_totals(o, nb, tot);
+        if (warp >= 1 && warp <= 4) {
+            warps_totals(o, nb, sh.tot);
+            const T* tot = sh.tot;
             if (threadIdx.x == 32) {
                 pimax = tot[3];
                 const double pap = (double)tot[1];
@@ -1717,9 +1727,9 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
         __syncthreads();
         if (warp == 0) {
             block_store(sh.red, part + pw * pstride, o.nbp);
-        } else if (warp == 1) {
-            T tot[4] = {T(0), T(0), T(0), T(0)};
-            if (cprev != C_NONE1) warp_totals(o, nb, tot);
+        } else if (warp <= 4) {
+            if (cprev != C_NONE1) warps_totals(o, nb, sh.tot);
+            const T* tot = sh.tot;
             if (threadIdx.x == 32) {
                 if (rstep) ++k;
                 int kind = K_STEP1;
@@ -2041,7 +2051,8 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
         return e;
     const long long budget = (long long)optin / bps - (long long)sizeof(Shared<T>) - 1024;
     if ((e = cudaMemsetAsync(ctx->bar, 0, 4 * sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
-    if (ctx->solve_barriers == 1 && threads >= 64 && need1 > 0 && (long long)need1 <= budget) {
+    // (warps 1-4 form the step decision: at least 160 threads)
+    if (ctx->solve_barriers == 1 && threads >= 256 && need1 > 0 && (long long)need1 <= budget) {
         // one grid barrier per iteration: every block's share and its ghosts fit
         const void* fn1 = (const void*)k_bbpgd1<T>;
         if ((e = cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need1)) != cudaSuccess)
