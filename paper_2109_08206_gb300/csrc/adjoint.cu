@@ -824,6 +824,7 @@ cudaError_t launch_adjoint(aLENS_ctx* ctx, int n, int m, const double* quat, con
     int iters = 0;
     double rel = 0.0;
     if (m > 0) {
+        if ((e = launch_setup_qe(ctx)) != cudaSuccess) return e;   // the CG reads the forward step's qe
         k_adj_b<<<G, 256, 0, st>>>(m, pairs, ctx->dgeom, gamma, Mu, lam, cgs, ctx->partials, counter, scal, iflag,
                                    tol);
         ++ctx->launches;

@@ -472,7 +472,27 @@ static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     ++ctx->launches;
     k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
     ++ctx->launches;
-    k_setup_qe<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->qlist, sb.rec, sb.qe, sb.rec_lo, sb.qe_lo, ctx->mdev);
+    ctx->qe_pending = 1;   // written by launch_setup_qe where a solver or the adjoint reads it
+    ctx->qe_m = m;
+    ctx->qe_prec = sizeof(T) == 4 ? ALENS_MIXED : ALENS_FP64;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_qe(aLENS_ctx* ctx)
+{
+    if (!ctx->qe_pending) return cudaSuccess;
+    ctx->qe_pending = 0;
+    const int m = ctx->qe_m, mp = (int)ctx->max_pairs;
+    if (m <= 0) return cudaSuccess;
+    if (ctx->qe_prec == ALENS_MIXED) {
+        const SolveBufs<float>& sb = ctx->sb32;
+        k_setup_qe<float><<<nblk(m, 256), 256, 0, ctx->stream>>>(m, mp, ctx->qlist, sb.rec, sb.qe, sb.rec_lo, sb.qe_lo,
+                                                                  ctx->mdev);
+    } else {
+        const SolveBufs<double>& sb = ctx->sb64;
+        k_setup_qe<double><<<nblk(m, 256), 256, 0, ctx->stream>>>(m, mp, ctx->qlist, sb.rec, sb.qe, sb.rec_lo,
+                                                                   sb.qe_lo, ctx->mdev);
+    }
     ++ctx->launches;
     return cudaGetLastError();
 }
@@ -495,6 +515,8 @@ cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pair
 {
     cudaStream_t st = ctx->stream;
     cudaError_t e;
+    ctx->qe_pending = 0;
+    ctx->zero_start = gamma_in == nullptr;
     size_t bytes = sizeof(int) * ((size_t)n + 1);
     if ((e = cudaMemsetAsync(ctx->rod_count, 0, bytes, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ctx->cntQ, 0, bytes, st)) != cudaSuccess) return e;

@@ -333,6 +333,9 @@ struct aLENS_ctx {
     int solve_threads, solve_bps;
     int solve_barriers;      // 1: one-barrier solver where its share fits (default); 2: the two-barrier kernels
     int last_solver;         // kernel of the last single-system solve: 1 one-barrier, 2 two-barrier staged, 3 two-barrier global
+    int zero_start;          // the last setup started from gamma = 0 (no caller gamma)
+    int qe_pending;          // the last setup's CSR-ordered other-side copies (qe) are still to be written
+    int qe_m, qe_prec;       // ... for this many constraints in this precision
     // batched steps as a captured CUDA graph (aLENS_set_batch_graph)
     const unsigned long long* mdev;   // while recording a graph: the device's constraint count (else NULL)
     int batch_graph;         // graph mode on
@@ -425,6 +428,10 @@ cudaError_t launch_rank(aLENS_ctx* ctx, int n);
 
 // solve.cu
 cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision);
+// The other-side copies qe of the last setup, if still pending: the
+// global-memory solvers and the adjoint read them, the one-barrier solver
+// does not.
+cudaError_t launch_setup_qe(aLENS_ctx* ctx);
 cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma_out);
 
 // Springs: rows mu .. mu + nb of the internal constraint list (pairs, phi,

@@ -223,6 +223,7 @@ struct SolveArgs {
     T pi_tol;      // stopping threshold on max |pi| (float32: see above)
     int max_iter;
     int refresh;   // refresh the reference every this many iterations (0: never)
+    int zero_start;   // gamma_0 = 0 (the one-barrier solver's initial reference needs no rod pass)
     int sort_ns;   // global-memory blocks sort their rods (shared memory for the order was given)
     int sort_cap;  // rods the order's scratch holds (a larger share keeps the rank order)
     long long wait_cycles;
@@ -1392,6 +1393,20 @@ __device__ __forceinline__ void copy_out1(T* dst, const Own1<T>& o)
     }
 }
 
+// Uref = 0 for the block's rods: shared memory and its rows of the global
+// Uref (the velocity the step reports if gamma_0 already meets the tolerance).
+template <typename T>
+__device__ __forceinline__ void zero_uref1(const SolveArgs<T>& a, const Own1<T>& o)
+{
+    const int nr = o.r1 - o.r0;
+    for (int k = threadIdx.x; k < 6 * o.cap_r; k += blockDim.x) o.U[k] = T(0);
+    typename V2<T>::t z;
+    z.x = T(0);
+    z.y = T(0);
+    typename V2<T>::t* g = reinterpret_cast<typename V2<T>::t*>(a.Uref + 6 * (size_t)o.r0);
+    for (int k = threadIdx.x; k < 3 * nr; k += blockDim.x) g[k] = z;
+}
+
 // The two velocities of slot t, P side first: Ui of the owner, Uj of the
 // other end (0 for a wall).  Local rods from shared memory, others from the
 // global buffer Ug.
@@ -1467,8 +1482,10 @@ __device__ __forceinline__ void con_pass_step1(const SolveArgs<T>& a, const Own1
 
 // Constraint phase of a refresh over every slot: gref = q + D^T Uref from
 // the split records and q with compensated sums (float32), g = gref, and
-// for owned slots acc = (pi.pi, 0, 0, max |pi|) at gamma_ref.
-template <typename T>
+// for owned slots acc = (pi.pi, 0, 0, max |pi|) at gamma_ref.  ZERO: Uref
+// is 0 (gamma_ref = 0), so no velocity is read and the records' products
+// (all zero) are left out of the sums.
+template <typename T, bool ZERO = false>
 __device__ __forceinline__ void con_pass_ref1(const SolveArgs<T>& a, const Own1<T>& o, T acc[4])
 {
     constexpr bool COMP = sizeof(T) == 4;
@@ -1477,19 +1494,23 @@ __device__ __forceinline__ void con_pass_ref1(const SolveArgs<T>& a, const Own1<
 #pragma unroll 1
     for (int t = threadIdx.x; t < o.nt; t += blockDim.x) {
         T Ui[6], Uj[6], r[9];
-        slot_velocities(o, t, a.Uref, Ui, Uj);
+        if (!ZERO) {
+            slot_velocities(o, t, a.Uref, Ui, Uj);
 #pragma unroll
-        for (int w = 0; w < 9; ++w) r[w] = o.rec[w * nt + t];
+            for (int w = 0; w < 9; ++w) r[w] = o.rec[w * nt + t];
+        }
         const int c = slot_gid(o, t);
         const T gam = o.gam[t];
         Acc<T, COMP> du;
         du.init(__ldg(&a.q[c]));
+        if (!ZERO) {
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            du.add_prod(r[u], Ui[u]);
-            du.add_prod(-r[u], Uj[u]);
-            du.add_prod(r[3 + u], Ui[3 + u]);
-            du.add_prod(-r[6 + u], Uj[3 + u]);
+            for (int u = 0; u < 3; ++u) {
+                du.add_prod(r[u], Ui[u]);
+                du.add_prod(-r[u], Uj[u]);
+                du.add_prod(r[3 + u], Ui[3 + u]);
+                du.add_prod(-r[6 + u], Uj[3 + u]);
+            }
         }
         const T cmp = has_comp ? __ldg(&a.comp[c]) : T(-1);
         const bool bil = cmp >= T(0);
@@ -1499,10 +1520,12 @@ __device__ __forceinline__ void con_pass_ref1(const SolveArgs<T>& a, const Own1<
         }
         if (COMP) {
             T tl = __ldg(&a.q_lo[c]);
+            if (!ZERO) {
 #pragma unroll
-            for (int u = 0; u < 3; ++u)
-                tl += __ldg(&a.rec_lo[u * mp + c]) * (Ui[u] - Uj[u]) + __ldg(&a.rec_lo[(3 + u) * mp + c]) * Ui[3 + u] -
-                      __ldg(&a.rec_lo[(6 + u) * mp + c]) * Uj[3 + u];
+                for (int u = 0; u < 3; ++u)
+                    tl += __ldg(&a.rec_lo[u * mp + c]) * (Ui[u] - Uj[u]) +
+                          __ldg(&a.rec_lo[(3 + u) * mp + c]) * Ui[3 + u] - __ldg(&a.rec_lo[(6 + u) * mp + c]) * Uj[3 + u];
+            }
             du.add_lo(tl);
         }
         const T gr = du.value();
@@ -1678,13 +1701,21 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
     int k = 0, since = 0, hist = 0;
     bool ok = true;
 
-    // initial reference at gamma_0 and the line step alpha_0 = pi.pi / pi.A.pi
-    rod_pass1<T, A_REF>(a, o, T(0));
-    ok = barrier();
+    // initial reference at gamma_0 and the line step alpha_0 = pi.pi / pi.A.pi;
+    // from gamma_0 = 0, Uref = M D gamma_0 = 0 needs no rod pass and no
+    // other block's velocities
+    if (a.zero_start) {
+        zero_uref1(a, o);
+        __syncthreads();
+    } else {
+        rod_pass1<T, A_REF>(a, o, T(0));
+        ok = barrier();
+    }
     int pw = 0;   // block-sum buffer the next barrier publishes
     if (ok) {
         T v[4] = {T(0), T(0), T(0), T(0)};
-        con_pass_ref1(a, o, v);
+        if (a.zero_start) con_pass_ref1<T, true>(a, o, v);
+        else con_pass_ref1(a, o, v);
         __syncthreads();   // gref and g of every slot before the line step reads them
         v[1] = rod_pass1<T, A_PG>(a, o, T(0));
         warp_partial(v, sh.red);
@@ -1998,6 +2029,7 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.fault = 0;
     a.sort_ns = 0;
     a.sort_cap = 0;
+    a.zero_start = ctx->zero_start;
     a.bstart = ctx->bstart;
     return a;
 }
@@ -2068,6 +2100,7 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
                                                ctx->stream);
         }
     }
+    if ((e = launch_setup_qe(ctx)) != cudaSuccess) return e;   // the two-barrier kernels read qe
     const bool staged = (long long)need <= budget && (long long)n / blocks < 60000;
     // global-memory blocks still take their rods in count order when the
     // order (10 bytes of scratch per rod) fits
@@ -2095,6 +2128,7 @@ static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int
     ctx->fault_mode = 0;
     const int ns = ctx->batch_n;
     cudaError_t e;
+    if ((e = launch_setup_qe(ctx)) != cudaSuccess) return e;   // the per-system solver reads qe
     k_sys_order<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(ns, ctx->sysoff, ctx->rowP, ctx->sys_order);
     ++ctx->launches;
     if ((e = cudaMemsetAsync(ctx->dcount + C_QUEUE, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
