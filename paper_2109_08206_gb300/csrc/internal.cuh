@@ -13,7 +13,7 @@ namespace alens {
 
 // ---------------------------------------------------------------- constants
 
-constexpr int kSearchWarps = 4;          // warps per block of the neighbour search
+constexpr int kSearchWarps = 8;          // warps per block of the neighbour search
 constexpr int kPairsPerRodCap = 512;     // per-rod (i < j) list held in shared memory
 constexpr double kParallelDet64 = 1e-12; // a c - b^2 below this (relative) = parallel
 constexpr float kParallelDet32 = 1e-4f;  // float screen: below this go straight to float64

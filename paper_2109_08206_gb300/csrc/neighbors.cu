@@ -166,6 +166,7 @@ enum { kScreenDrop = 0, kScreenKeep = 1, kScreenDecide = 2 };
 constexpr uint32_t kUndecided = 0x80000000u;
 constexpr uint32_t kKeyMask = 0x7fffffffu;
 constexpr uint32_t kDropped = 0xffffffffu;
+constexpr int kCandPiece = 384;   // candidates a search warp lists in shared memory at a time (multiple of 32)
 
 __device__ __forceinline__ int screen32(const float4& pi, const float4& ai, const float4& pj, const float4& aj,
                                         float sx, float sy, float sz, const Geo& g)
@@ -221,35 +222,26 @@ __device__ __forceinline__ void decode_cell(uint32_t key, int bits, int cc[3])
     }
 }
 
-// One warp per rod i (rods taken in cell order for locality of the candidate
-// loads).  Lanes 0-26 fetch the rod ranges of the 27 neighbour cells at once
-// (each cell with the periodic image shift that brings it next to i's cell),
-// cut to the suffix of ids above i;
-// the warp then walks the concatenated candidates in full chunks of 32, each
-// lane finding its cell by a binary search over the prefix of the counts;
-// candidates j > i that the float32 screen keeps or cannot settle are
-// appended to a per-warp list in shared memory with a warp ballot, sorted
-// there by (j, image) with a bitonic network, and written to the candidate
-// buffer as 64-bit keys (i << 32 | kUndecided? | j << 5 | image); their count
-// goes to rod_count and the total, and k_decide takes the float64 decision
-// of the flagged few.  COUNT_ONLY: decide in float64 inline and only count
-// the kept pairs (used when the candidate buffer overflows).
+// The candidate pairs (i, j > i) of the rod at cell-sorted position k, for
+// one warp.  Lanes 0-26 fetch the rod ranges of the 27 neighbour cells at
+// once (each cell with the periodic image shift that brings it next to i's
+// cell), cut to the suffix of ids above i; the warp walks the concatenated
+// candidates in two passes (below); the candidates j > i that the float32
+// screen keeps or cannot settle go to L with a warp ballot and are sorted
+// there by (j, image) with a bitonic network.  Returns their count and,
+// unless COUNT_ONLY, leaves their keys (j << 5 | image, bit 31 while the
+// float64 decision is pending) sorted in L; COUNT_ONLY takes that decision
+// inline.  Q, E and T are the warp's ring [64], candidate list [kCandPiece]
+// and image offsets [27] in shared memory.
 template <bool COUNT_ONLY>
-__global__ void __launch_bounds__(kSearchWarps * 32)
-k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __restrict__ sysid,
-         const int* __restrict__ sorted_id, const float4* __restrict__ spos32,
-         const float4* __restrict__ sax32, const uint32_t* __restrict__ cellkey, const double* __restrict__ xw,
-         const double* __restrict__ axis, const int* __restrict__ cell_start, int* __restrict__ rod_ncand,
-         int* __restrict__ rod_count, long long* __restrict__ rod_tmpstart, unsigned long long* __restrict__ cand,
-         long long cand_cap, unsigned long long* __restrict__ counters, int* __restrict__ flags)
+__device__ __forceinline__ int search_rod(int k, int i, int np, const Geo& g0, const SysGeo* __restrict__ systab,
+                                          const int* __restrict__ sysid, const int* __restrict__ sorted_id,
+                                          const float4* __restrict__ spos32, const float4* __restrict__ sax32,
+                                          const uint32_t* __restrict__ cellkey, const double* __restrict__ xw,
+                                          const double* __restrict__ axis, const int* __restrict__ cell_start,
+                                          int* __restrict__ flags, uint32_t* L, uint32_t* Q, uint32_t* E, float4* T)
 {
-    __shared__ uint32_t list[COUNT_ONLY ? 1 : kSearchWarps][COUNT_ONLY ? 1 : kPairsPerRodCap];
-    __shared__ uint32_t ring[kSearchWarps][64];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.x * kSearchWarps + warp;
-    if (k >= n) return;   // uniform per warp
-    uint32_t* L = list[COUNT_ONLY ? 0 : warp];
-    const int i = sorted_id[k];
+    const int lane = threadIdx.x & 31;
     const float4 pi = spos32[k], ai = sax32[k];
     const Geo& g = geo_of(g0, systab, sysid, i);
     const uint32_t key_base = systab ? (uint32_t)systab[sysid[i]].key_base : 0u;
@@ -296,45 +288,40 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
         if (lane >= o) incl += y;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - ccnt;   // this lane's cell: candidates [excl, incl)
+    if (lane < 27) T[ccode] = make_float4(csx, csy, csz, 0.0f);   // equal codes, equal offsets
     int cnt = 0;
-    // Two passes over the candidates of all 27 cells.  A: full chunks of 32
-    // lanes test the centre distance alone (the screen's first test, about
-    // one candidate in seven passes) and queue the passes, m | code << 26,
-    // in a per-warp ring.  B: every 32 queued candidates (and the rest at
-    // the end) take the whole float32 screen with all lanes busy.
-    uint32_t* Q = ring[warp];
+    // Two passes over the candidates of all 27 cells.  A: the candidates,
+    // listed in shared memory kCandPiece at a time as m | code << 26 (each
+    // cell's lane writes its part of the piece), are tested in chunks of 32
+    // lanes for the centre distance alone (the screen's first test, about
+    // one candidate in seven passes) and the passes are queued in a per-warp
+    // ring.  B: every 32 queued candidates (and the rest at the end) take the
+    // whole float32 screen with all lanes busy.
     int qh = 0, qn = 0;   // warp-uniform ring head and length (qn < 32 before each chunk)
-    for (int base = 0; base < total || qn > 0;) {
+    for (int pb = 0, base = 0; base < total || qn > 0;) {
         if (base < total) {
-            const int t = base + lane;
-            int lo = 0, hi = 26;   // smallest o with incl[o] > t
-#pragma unroll
-            for (int step = 0; step < 5; ++step) {
-                const int mid = (lo + hi) >> 1;
-                const int im = __shfl_sync(0xffffffffu, incl, mid);
-                if (im > t) hi = mid;
-                else lo = mid + 1;
+            if (base == pb) {   // list the next piece [pb, pb + kCandPiece)
+                __syncwarp();   // the last piece's entries are read
+                const int u0 = max(pb - excl, 0), u1 = min(incl, pb + kCandPiece) - excl;
+                for (int u = u0; u < u1; ++u) E[excl + u - pb] = (uint32_t)(cbeg + u) | (ccode << 26);
+                __syncwarp();
             }
-            const int o = lo < 26 ? lo : 26;
-            const int ob = __shfl_sync(0xffffffffu, cbeg, o);
-            const int oc = __shfl_sync(0xffffffffu, ccnt, o);
-            const int oi = __shfl_sync(0xffffffffu, incl, o);
-            const uint32_t code = __shfl_sync(0xffffffffu, ccode, o);
-            const float sx = __shfl_sync(0xffffffffu, csx, o);
-            const float sy = __shfl_sync(0xffffffffu, csy, o);
-            const float sz = __shfl_sync(0xffffffffu, csz, o);
+            const int t = base + lane;
             bool near = false;
-            int m = 0;
+            uint32_t e = 0u;
             if (t < total) {
-                m = ob + (t - (oi - oc));
-                const float4 pj = spos32[m];
-                const float dx = pi.x - pj.x - sx, dy = pi.y - pj.y - sy, dz = pi.z - pj.z - sz;
+                e = E[t - pb];
+                const float4 sft = T[e >> 26];
+                const float4 pj = spos32[e & 0x3ffffffu];
+                const float dx = pi.x - pj.x - sft.x, dy = pi.y - pj.y - sft.y, dz = pi.z - pj.z - sft.z;
                 near = dx * dx + dy * dy + dz * dz < g.rcut_screen2;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, near);
-            if (near) Q[(qh + qn + __popc(bal & ((1u << lane) - 1u))) & 63] = (uint32_t)m | (code << 26);
+            if (near) Q[(qh + qn + __popc(bal & ((1u << lane) - 1u))) & 63] = e;
             qn += __popc(bal);
             base += 32;
+            if (base >= pb + kCandPiece) pb += kCandPiece;
             __syncwarp();
         }
         if (qn >= 32 || (base >= total && qn > 0)) {
@@ -365,10 +352,7 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
             cnt += __popc(bal);
         }
     }
-    if (COUNT_ONLY) {
-        if (lane == 0) atomicAdd(&counters[C_PAIRS], (unsigned long long)cnt);
-        return;
-    }
+    if (COUNT_ONLY) return cnt;
     __syncwarp();
     if (cnt > kPairsPerRodCap) {
         if (lane == 0 && atomicCAS(&flags[F_ERR], 0, ALENS_ERR_CAPACITY) == 0) flags[F_ERR_ROD] = i;
@@ -391,15 +375,62 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
             __syncwarp();
         }
     }
-    long long start = 0;
+    return cnt;
+}
+
+// One warp per rod i (rods taken in cell order for locality of the candidate
+// loads), search_rod finding its pairs; they are written to the candidate
+// buffer as 64-bit keys (i << 32 | kUndecided? | j << 5 | image), their
+// count to rod_count and the total, and k_decide takes the float64 decision
+// of the flagged few.  The candidate buffer and the pair total take one
+// atomic per block (per rod they would queue on one L2 address): thread 0
+// reserves the block's candidates and hands each warp its start; the
+// block's warps past n only join that count.  COUNT_ONLY: only the total
+// (used when the candidate buffer overflows).
+template <bool COUNT_ONLY>
+__global__ void __launch_bounds__(kSearchWarps * 32)
+k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __restrict__ sysid,
+         const int* __restrict__ sorted_id, const float4* __restrict__ spos32,
+         const float4* __restrict__ sax32, const uint32_t* __restrict__ cellkey, const double* __restrict__ xw,
+         const double* __restrict__ axis, const int* __restrict__ cell_start, int* __restrict__ rod_ncand,
+         int* __restrict__ rod_count, long long* __restrict__ rod_tmpstart, unsigned long long* __restrict__ cand,
+         long long cand_cap, unsigned long long* __restrict__ counters, int* __restrict__ flags)
+{
+    __shared__ uint32_t list[COUNT_ONLY ? 1 : kSearchWarps][COUNT_ONLY ? 1 : kPairsPerRodCap];
+    __shared__ uint32_t ring[kSearchWarps][64];
+    __shared__ uint32_t elist[kSearchWarps][kCandPiece];
+    __shared__ float4 Tsh[kSearchWarps][27];
+    __shared__ int wcnt[kSearchWarps];
+    __shared__ long long wstart[kSearchWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * kSearchWarps + warp;
+    uint32_t* L = list[COUNT_ONLY ? 0 : warp];
+    int i = 0, cnt = 0;
+    if (k < n) {   // uniform per warp
+        i = sorted_id[k];
+        cnt = search_rod<COUNT_ONLY>(k, i, np, g0, systab, sysid, sorted_id, spos32, sax32, cellkey, xw, axis,
+                                     cell_start, flags, L, ring[warp], elist[warp], Tsh[warp]);
+    }
+    if (lane == 0) wcnt[warp] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < kSearchWarps; ++w) tot += wcnt[w];
+        long long st = COUNT_ONLY || tot == 0 ? 0 : (long long)atomicAdd(&counters[C_CAND], (unsigned long long)tot);
+        if (tot) atomicAdd(&counters[C_PAIRS], (unsigned long long)tot);
+        for (int w = 0; w < kSearchWarps; ++w) {
+            wstart[w] = st;
+            st += wcnt[w];
+        }
+    }
+    __syncthreads();
+    if (COUNT_ONLY || k >= n) return;
+    const long long start = wstart[warp];
     if (lane == 0) {
-        start = (long long)atomicAdd(&counters[C_CAND], (unsigned long long)cnt);
-        atomicAdd(&counters[C_PAIRS], (unsigned long long)cnt);
         rod_ncand[i] = cnt;
         rod_count[i] = cnt;
         rod_tmpstart[i] = start;
     }
-    start = __shfl_sync(0xffffffffu, start, 0);
     const unsigned long long hi = (unsigned long long)(unsigned)i << 32;
     for (int u = lane; u < cnt; u += 32)
         if (start + u < cand_cap) cand[start + u] = hi | L[u];
