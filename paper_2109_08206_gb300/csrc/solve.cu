@@ -1216,7 +1216,7 @@ __device__ __forceinline__ void stage_slot(const SolveArgs<T>& a, const Own1<T>&
     ld_state(a.gg0, c, d, g, gr, gl);
     o.ds[t] = d;
     o.gam[t] = gr;
-    o.grs[t] = T(0);
+    o.grs[t] = gl;   // gamma_lo until the first reference pass replaces it by g
     o.gref[t] = T(0);
     o.oth[t] = other;
     o.loc[t] = (unsigned short)(li | bil);
@@ -1312,9 +1312,9 @@ __device__ __forceinline__ T rod_pass1(const SolveArgs<T>& a, const Own1<T>& o, 
                 if (MODE == A_PG && bil) fmf += __ldg(&a.comp[o.c0 + t]) * v * v;   // the spring's compliance term
 #pragma unroll
                 for (int w = 0; w < 6; ++w) Fa[w].add_prod(v, rv[w]);
-                if (COMP) {   // gamma_lo and the records' low parts
+                if (COMP) {   // gamma_lo (held in grs during a reference pass) and the records' low parts
                     const int c = o.c0 + t;
-                    const T gl = gl_of_state(a.gg0, c);
+                    const T gl = gv;
 #pragma unroll
                     for (int w = 0; w < 6; ++w) Fa[w].add_lo(v * __ldg(&a.rec_lo[w * mp + c]) + gl * rv[w]);
                 }
@@ -1338,7 +1338,7 @@ __device__ __forceinline__ T rod_pass1(const SolveArgs<T>& a, const Own1<T>& o, 
                 for (int w = 0; w < 6; ++w) Fa[w].add_prod(-v, qv[w]);
                 if (COMP) {
                     const int c = slot_gid(o, t);
-                    const T gl = gl_of_state(a.gg0, c);
+                    const T gl = gv;
                     T ql[6];
 #pragma unroll
                     for (int w = 0; w < 3; ++w) {
@@ -1516,7 +1516,7 @@ __device__ __forceinline__ void con_pass_ref1(const SolveArgs<T>& a, const Own1<
         const bool bil = cmp >= T(0);
         if (bil) {
             du.add_prod(cmp, gam);
-            du.add_lo(cmp * gl_of_state(a.gg0, c));
+            du.add_lo(cmp * o.grs[t]);   // gamma_lo, before g takes its place below
         }
         if (COMP) {
             T tl = __ldg(&a.q_lo[c]);
@@ -1541,40 +1541,36 @@ __device__ __forceinline__ void con_pass_ref1(const SolveArgs<T>& a, const Own1<
     }
 }
 
-// Refresh, first half: every owned slot folds delta into (gamma_ref,
-// gamma_lo) as fold_delta does and publishes it in buffer 0; ghost slots
-// clear delta and take the owner's gamma_ref after the next barrier
-// (ghost_ref1).
+// Refresh, first half: every slot folds delta into (gamma_ref, gamma_lo)
+// as fold_delta does, from the previous reference's gamma_lo in gprev;
+// ghosts repeat their owner's arithmetic on the same inputs, so both hold
+// the same reference without waiting for each other.  gamma_ref goes to
+// gam, gamma_lo to grs (the reference passes' low part, until the constraint
+// pass replaces it by g), and owned slots publish (gamma_ref, gamma_lo) in
+// gnew, the other state buffer (ghosts are still reading gprev).
 template <typename T>
-__device__ __forceinline__ void fold1(const SolveArgs<T>& a, const Own1<T>& o)
+__device__ __forceinline__ void fold1(const SolveArgs<T>& a, const Own1<T>& o, const T* gprev, T* gnew)
 {
     const bool has_comp = a.comp != nullptr;
 #pragma unroll 1
     for (int t = threadIdx.x; t < o.nt; t += blockDim.x) {
-        if (t < o.nc) {
-            const int c = o.c0 + t;
-            const T d = o.ds[t], gr = o.gam[t], gl = gl_of_state(a.gg0, c);
-            const bool bil = has_comp && (o.loc[t] & kBil);
-            T hi = T(0), lo = T(0);
-            if (bil || d > -gr) {
-                T s, e;
-                two_sum(gr, d, s, e);
-                const T l = gl + e;
-                hi = s + l;
-                lo = l - (hi - s);
-                if (!bil && (hi < T(0) || (hi == T(0) && lo < T(0)))) { hi = T(0); lo = T(0); }
-            }
-            o.gam[t] = hi;
-            st_ref(a.gg0, c, hi, lo);
+        const int c = slot_gid(o, t);
+        const T d = o.ds[t], gr = o.gam[t], gl = gl_of_state(gprev, c);
+        const bool bil = has_comp && (o.loc[t] & kBil);
+        T hi = T(0), lo = T(0);
+        if (bil || d > -gr) {
+            T s, e;
+            two_sum(gr, d, s, e);
+            const T l = gl + e;
+            hi = s + l;
+            lo = l - (hi - s);
+            if (!bil && (hi < T(0) || (hi == T(0) && lo < T(0)))) { hi = T(0); lo = T(0); }
         }
+        o.gam[t] = hi;
+        o.grs[t] = lo;
         o.ds[t] = T(0);
+        if (t < o.nc) st_ref(gnew, c, hi, lo);
     }
-}
-
-template <typename T>
-__device__ __forceinline__ void ghost_ref1(const SolveArgs<T>& a, const Own1<T>& o)
-{
-    for (int g = threadIdx.x; g < o.ng; g += blockDim.x) o.gam[o.nc + g] = __ldcg(&a.gg0[4 * (size_t)o.gid[g] + 2]);
 }
 
 // cp.async of the last barrier's block sums ([4][nbp] of buffer src) into
@@ -1747,6 +1743,7 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
     bool rstep = false;       // the last rod phase formed a step (its delta is still to be stored)
     T alpha_prev = T(0);
     int db = 0;               // dU buffer the next step's rod phase writes
+    int nref = 0;             // refreshes taken: the reference lives in state buffer nref & 1
     while (ok && sh.kind != K_STOP1) {
         const int pr = pw ^ 1;   // buffer the last barrier published
         if (cprev != C_NONE1) tot_fetch(o, part + pr * pstride);
@@ -1798,9 +1795,8 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
         if (kind == K_STOP1) break;
         int cpub = ccur;
         if (kind == K_REF1) {
-            fold1(a, o);
-            if (!(ok = barrier())) break;
-            ghost_ref1(a, o);
+            fold1(a, o, nref & 1 ? a.gg1 : a.gg0, nref & 1 ? a.gg0 : a.gg1);
+            ++nref;
             __syncthreads();
             rod_pass1<T, A_REF>(a, o, T(0));
             if (!(ok = barrier())) break;
@@ -1823,8 +1819,9 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
     }
     if (!ok) return;
     // every solve ends on a fresh reference: gamma = gamma_ref + gamma_lo
-    // (buffer 0) and delta = 0, so dU = 0
-    for (int t = threadIdx.x; t < o.nc; t += blockDim.x) st_dg(a.gg0, o.c0 + t, T(0), o.gref[t]);
+    // (state buffer nref & 1) and delta = 0, so dU = 0
+    T* gfin = nref & 1 ? a.gg1 : a.gg0;
+    for (int t = threadIdx.x; t < o.nc; t += blockDim.x) st_dg(gfin, o.c0 + t, T(0), o.gref[t]);
     {
         typename V2<T>::t z;
         z.x = T(0);
@@ -1834,7 +1831,7 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
     }
     if (blockIdx.x == 0 && threadIdx.x == 32) {
         a.out[1] = (double)alpha0;
-        a.flags[F_FINAL] = 0;
+        a.flags[F_FINAL] = nref & 1;
         a.flags[F_ITERS] = k;
         a.out[0] = a.hD * (double)pimax;
     }
