@@ -348,6 +348,60 @@ def test_float32_screen_boundary():
     assert (near & (gaps < dc)).sum() >= 20 and (near & (gaps >= dc)).sum() >= 20
 
 
+def test_float32_keep_band():
+    """The neighbour search also keeps a candidate on its float32
+    closest-point distance alone when that distance is below D + delta_c by
+    the keep margin 2 sqrt(3) (4 u B + L u + 200 u) + 1e-5 D (u = 2^-24, B
+    the power of two above the box; 2.7e-4 D at box 200): the float closest
+    points are points of the two segments, so their exact distance bounds
+    the minimum from above, and the float evaluation errs by at most half
+    the margin.  Pairs at general angles with float64 gaps on both sides of
+    delta_c - margin and of delta_c, in interior, end-to-side and end-to-end
+    closest-point configurations, rotated at random and placed near the box
+    edge, where float32 rounding is largest: the list must equal the
+    oracle's exactly (Appendix "Implementation": a pair is a constraint iff
+    its gap is below delta_c)."""
+    rng = np.random.default_rng(31)
+    L, D, dc = 10.0, 1.0, 1.0
+    box = 200.0
+    u, B = 2.0 ** -24, 256.0
+    kmargin = 2.0 * math.sqrt(3.0) * (4.0 * u * B + L * u + 200.0 * u) + 1e-5 * D
+    xs, axes = [], []
+    for ang in (0.05, 0.3, 0.9, 1.5707):
+        for eps in (-2 * kmargin, -1.2 * kmargin, -kmargin - 1e-6, -kmargin + 1e-6, -0.8 * kmargin, -0.5 * kmargin,
+                    -1e-5, -1e-7, 1e-7, 1e-5, 0.5 * kmargin, 2 * kmargin):
+            for kind in range(3):
+                R = _rotation(rng)
+                p = np.array([0.0, 0.0, 1.0])
+                q = np.array([math.sin(ang), 0.0, math.cos(ang)])
+                h = D + dc + eps
+                if kind == 0:     # interior closest points, separation along y
+                    cq = np.array([0.0, h, 0.0])
+                elif kind == 1:   # Q's lower end against the middle of P's side
+                    cq = np.array([0.0, h, 0.0]) + 0.5 * L * q
+                else:             # Q's lower end against P's upper end
+                    cq = np.array([0.0, h, 0.5 * L]) + 0.5 * L * q
+                o = box - rng.uniform(0.0, 12.0, 3)   # near the far corner
+                xs += [o, o + R @ cq]
+                axes += [R @ p, R @ q]
+    x = np.array(xs)
+    s = W.RodSystem(x=x - box * np.floor(x / box), quat=W.quat_from_axis(np.array(axes)),
+                    f_nc=np.zeros((x.shape[0], 6)), box=(box, box, box), tol=1e-10)
+    pb = O.problem_of(s)
+    ref = O.find_pairs(s.x, s.quat, pb)
+    with make_ctx(s) as ctx:
+        got = host(ctx.build_neighbors(dev(s.x), dev(s.quat)))
+    assert compare_pairs(got, ref, s) == 0
+    # the constructed pairs straddle the keep threshold and delta_c
+    built = np.arange(0, x.shape[0], 2)
+    cand = np.stack([built, built + 1, np.full(built.shape, 13)], 1).astype(np.int32)
+    shift = np.round((s.x[built] - s.x[built + 1]) / box).astype(int)
+    cand[:, 2] = (shift[:, 0] + 1) + 3 * (shift[:, 1] + 1) + 9 * (shift[:, 2] + 1)
+    gaps = O.pair_gaps(s.x, s.quat, pb, cand)
+    assert (gaps < dc - kmargin).sum() >= 20 and ((gaps > dc - kmargin) & (gaps < dc)).sum() >= 20
+    assert (gaps >= dc).sum() >= 20
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_empty_and_isolated_rods():
