@@ -309,14 +309,24 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
 }
 
 // Other-side arms in CSR order, one 8-value record per entry (e, arm x e,
-// two pad values) so that the solver's gather is one or two vector loads.
+// two pad values) so that the solver's gather is one or two vector loads;
+// and the same record of each constraint's owner side in owner order (the
+// global-memory rod phase walks a rod's owned constraints from lanes that
+// hold unrelated rods, so six scalar columns would cost six sectors).
 template <typename T>
 __global__ void k_setup_qe(int m, int mp, const int* __restrict__ qlist, const T* __restrict__ rec,
                            T* __restrict__ qe, const T* __restrict__ rec_lo, T* __restrict__ qe_lo,
-                           const unsigned long long* __restrict__ mdev)
+                           T* __restrict__ pe, const unsigned long long* __restrict__ mdev)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count_of(m, mdev)) return;
+    if (pe) {   // constraint k's owner side as one record: the global rod phase reads it whole
+        T* o = pe + 8 * (size_t)k;
+#pragma unroll
+        for (int u = 0; u < 6; ++u) o[u] = rec[u * (size_t)mp + k];
+        o[6] = T(0);
+        o[7] = T(0);
+    }
     int c = qlist[k];
     T* o = qe + 8 * (size_t)k;
 #pragma unroll
@@ -487,11 +497,11 @@ cudaError_t launch_setup_qe(aLENS_ctx* ctx)
     if (ctx->qe_prec == ALENS_MIXED) {
         const SolveBufs<float>& sb = ctx->sb32;
         k_setup_qe<float><<<nblk(m, 256), 256, 0, ctx->stream>>>(m, mp, ctx->qlist, sb.rec, sb.qe, sb.rec_lo, sb.qe_lo,
-                                                                  ctx->mdev);
+                                                                  sb.pe, ctx->mdev);
     } else {
         const SolveBufs<double>& sb = ctx->sb64;
         k_setup_qe<double><<<nblk(m, 256), 256, 0, ctx->stream>>>(m, mp, ctx->qlist, sb.rec, sb.qe, sb.rec_lo,
-                                                                   sb.qe_lo, ctx->mdev);
+                                                                   sb.qe_lo, sb.pe, ctx->mdev);
     }
     ++ctx->launches;
     return cudaGetLastError();

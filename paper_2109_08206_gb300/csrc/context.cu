@@ -447,6 +447,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         s.mobr = carve64(4 * np);
         s.comp = carve64(mp);
         s.isc = carve64(mp);
+        s.pe = nullptr;   // the float64 rod phase reads rec (its arithmetic bounds it)
         float* fb = (float*)c->solve_ws;
         size_t f = 0;
         auto carve32 = [&](size_t cnt) { float* r = fb + f; f = (f + cnt + 7) & ~(size_t)7; return r; };
@@ -458,7 +459,9 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         t.mobr = carve32(4 * np);
         t.comp = carve32(mp);
         t.isc = carve32(mp);
-        // the float32 views use at most half of the workspace: room for the low parts
+        t.pe = carve32(8 * mp);
+        // the float32 views use at most half of the workspace: room for the
+        // owner-side records and the low parts (55 mp + 25 np of 58 mp + 50 np)
         t.rec_lo = carve32(9 * mp); t.qe_lo = carve32(8 * mp); t.q_lo = carve32(mp);
     }
     if (cudaMemsetAsync(c->cell_cursor, 0, ((size_t)c->max_keys + 1) * sizeof(int), c->stream) != cudaSuccess ||

@@ -249,6 +249,7 @@ template <typename T>
 struct SolveBufs {           // typed views into the solver workspace
     T* rec;                  // [9][mp]  e, y_P x e, y_Q x e
     T* qe;                   // [mp][8]  per Q-side entry: e, y_Q x e, 2 pad (CSR order)
+    T* pe;                   // [mp][8]  per constraint: e, y_P x e, 2 pad (owner order; null: read rec)
     T* q;                    // [mp]
     T* ax;                   // [3][np]
     T* gg[2];                // [mp][4] x 2: (delta, g, gamma_ref, 0), ping-pong

@@ -217,6 +217,7 @@ struct SolveArgs {
     const T* __restrict__ comp;   // [mp] per constraint: < 0 collision, >= 0 spring compliance 1/(h kappa); NULL: all collisions
     const T* __restrict__ rec_lo; // float32: low parts of rec, qe and q for the reference passes (else NULL)
     const T* __restrict__ qe_lo;
+    const T* __restrict__ pe;   // [mp][8] owner-side records (null: read rec)
     const T* __restrict__ q_lo;
     const T* __restrict__ isc;    // [mp] 1/sigma_c of the diagonal scaling (1 when unscaled)
     double hD, tol;
@@ -403,8 +404,12 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
                             for (int w = 0; w < 6; ++w) rv[u][w] = o.rec[w * o.cap_c + lc];
                         } else {
                             ld_state(gc, c + u, dv[u], gv[u], rv_[u], gl[u]);
+                            if (sizeof(T) == 4 && a.pe) {   // float64 is bound by its arithmetic instead
+                                ld_arm(a.pe, c + u, rv[u]);
+                            } else {
 #pragma unroll
-                            for (int w = 0; w < 6; ++w) rv[u][w] = a.rec[w * mp + c + u];
+                                for (int w = 0; w < 6; ++w) rv[u][w] = a.rec[w * mp + c + u];
+                            }
                         }
                     }
                 }
@@ -414,8 +419,9 @@ __device__ __forceinline__ T phase_a(const SolveArgs<T>& a, const Own<T>& o, int
                         const T cmp = comp_of(a, c + u);
                         const T v = a_value<MODE, T>(dv[u], gv[u], rv_[u], alpha, cmp >= T(0));
                         if (MODE == A_PG && cmp >= T(0)) fmf += cmp * v * v;   // the spring's compliance term
-                        // staged: phase B forms delta_{k+1} again from the same values
-                        if (MODE == A_STEP && !ST) gn[4 * (size_t)(c + u)] = v;
+                        // phase B forms delta_{k+1} again from the same values (staged
+                        // blocks, float32); float64, bound by its arithmetic, stores it
+                        if (MODE == A_STEP && !ST && sizeof(T) == 8) gn[4 * (size_t)(c + u)] = v;
 #pragma unroll
                         for (int w = 0; w < 6; ++w) Fa[w].add_prod(v, rv[u][w]);
                         if (MODE == A_REF && COMP) {   // gamma_lo and the records' low parts
@@ -588,11 +594,18 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
 #pragma unroll
             for (int w = 0; w < 9; ++w) r[w] = a.rec[w * mp + c];
             base = MODE == B_STEP ? a.gref[c] : a.q[c];
-            T gdummy, gl;
-            ld_state(gnew, c, dm, gdummy, gam, gl);
-            if (MODE == B_STEP) {
-                T g2, gl2;
-                ld_state(gold, c, dold, gro, g2, gl2);
+            T gl;
+            if (MODE == B_STEP && sizeof(T) == 4) {
+                // delta_{k+1} as the rod phase formed it (same inputs, same rounding)
+                ld_state(gold, c, dold, gro, gam, gl);
+                dm = a_value<A_STEP, T>(dold, gro, gam, alpha, comp_of(a, c) >= T(0));
+            } else {
+                T gdummy;
+                ld_state(gnew, c, dm, gdummy, gam, gl);
+                if (MODE == B_STEP) {
+                    T g2, gl2;
+                    ld_state(gold, c, dold, gro, g2, gl2);
+                }
             }
         }
         Acc<T, COMP> du;
@@ -639,6 +652,8 @@ __device__ __forceinline__ void phase_b(const SolveArgs<T>& a, const Own<T>& o, 
             // the state other blocks read in the next rod phase: in a step,
             // only that of constraints whose other rod is another block's
             if (MODE != B_STEP || xstate) st_dg(gnew, c, dm, gr);
+        } else if (MODE == B_STEP && sizeof(T) == 4) {
+            st_dg(gnew, c, dm, gr);
         } else {
             gnew[4 * (size_t)c + 1] = gr;
         }
@@ -2018,6 +2033,7 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.inv_rot = (T)ctx->mob.inv_rot; a.inv_spin = (T)ctx->mob.inv_spin;
     a.mobr = ctx->cur_systab ? sb.mobr : nullptr;
     a.rec_lo = sb.rec_lo; a.qe_lo = sb.qe_lo; a.q_lo = sb.q_lo;
+    a.pe = sb.pe;
     a.isc = sb.isc;
     a.comp = ctx->cur_comp ? sb.comp : nullptr;
     a.hD = ctx->p.dt / ctx->p.diameter; a.tol = ctx->p.tol; a.max_iter = ctx->p.max_iter;

@@ -357,10 +357,10 @@ def test_float32_keep_band():
     the minimum from above, and the float evaluation errs by at most half
     the margin.  Pairs at general angles with float64 gaps on both sides of
     delta_c - margin and of delta_c, in interior, end-to-side and end-to-end
-    closest-point configurations, rotated at random and placed near the box
-    edge, where float32 rounding is largest: the list must equal the
-    oracle's exactly (Appendix "Implementation": a pair is a constraint iff
-    its gap is below delta_c)."""
+    closest-point configurations, rotated at random and placed at
+    coordinates in the box edge's binade, where float32 rounding is largest:
+    the list must equal the oracle's exactly (Appendix "Implementation": a
+    pair is a constraint iff its gap is below delta_c)."""
     rng = np.random.default_rng(31)
     L, D, dc = 10.0, 1.0, 1.0
     box = 200.0
@@ -381,7 +381,9 @@ def test_float32_keep_band():
                     cq = np.array([0.0, h, 0.0]) + 0.5 * L * q
                 else:             # Q's lower end against P's upper end
                     cq = np.array([0.0, h, 0.5 * L]) + 0.5 * L * q
-                o = box - rng.uniform(0.0, 12.0, 3)   # near the far corner
+                # coordinates in [130, 200): the binade of the box edge, where
+                # float32 rounding is largest
+                o = box - rng.uniform(0.0, 70.0, 3)
                 xs += [o, o + R @ cq]
                 axes += [R @ p, R @ q]
     x = np.array(xs)
@@ -389,7 +391,7 @@ def test_float32_keep_band():
                     f_nc=np.zeros((x.shape[0], 6)), box=(box, box, box), tol=1e-10)
     pb = O.problem_of(s)
     ref = O.find_pairs(s.x, s.quat, pb)
-    with make_ctx(s) as ctx:
+    with make_ctx(s, max_pairs=100_000) as ctx:
         got = host(ctx.build_neighbors(dev(s.x), dev(s.quat)))
     assert compare_pairs(got, ref, s) == 0
     # the constructed pairs straddle the keep threshold and delta_c
