@@ -880,16 +880,21 @@ struct ClusterSync {
     }
 };
 
-// Smallest rank r in [lo, hi] whose cumulative work W(r) = rowP[r] +
-// kOtherWork * rowQ[r] + kRodWork * r reaches target (an other-side entry,
-// gathered from another block, costs about twice an owned one); W is
-// strictly increasing and W(hi) >= target.  One warp: 32 probes per round,
-// then a final scan of at most 32 ranks.
+// Smallest rank r in [lo, hi] whose cumulative work W(r) = kOwnWork *
+// rowP[r] + kOtherWork * rowQ[r] + kRodWork * r reaches target (an
+// other-side entry, gathered from another block, costs about twice an owned
+// one in the two-barrier kernels); W is strictly increasing and W(hi) >=
+// target.  One warp: 32 probes per round, then a final scan of at most 32
+// ranks.  The one-barrier kernel's blocks were timed under other weights
+// (owned : other-side : rod = 4:1:4, 4:1:2, 3:1:3, 2:1:2; four seeds at 1e5
+// rods): the first two push some shares past the shared-memory budget, the
+// others cost 0.5-1.7 % more per iteration than 1:2:2.
+constexpr int kOwnWork = 1;
 constexpr int kRodWork = 2;
 constexpr int kOtherWork = 2;
 __device__ __forceinline__ long long rank_work(const int* rowP, const int* rowQ, int r)
 {
-    return (long long)rowP[r] + (long long)kOtherWork * rowQ[r] + (long long)kRodWork * r;
+    return (long long)kOwnWork * rowP[r] + (long long)kOtherWork * rowQ[r] + (long long)kRodWork * r;
 }
 __device__ __forceinline__ int find_rank(const int* rowP, const int* rowQ, int lo, int hi, long long target)
 {
@@ -897,7 +902,7 @@ __device__ __forceinline__ int find_rank(const int* rowP, const int* rowQ, int l
     while (hi - lo >= 32) {
         const long long span = hi - lo;
         const int p = lo + (int)(span * (lane + 1) / 33);
-        const long long w = (long long)rowP[p] + (long long)kOtherWork * rowQ[p] + (long long)kRodWork * p;
+        const long long w = rank_work(rowP, rowQ, p);
         const unsigned ge = __ballot_sync(0xffffffffu, w >= target);
         if (ge == 0) {
             lo = __shfl_sync(0xffffffffu, p, 31) + 1;
@@ -911,7 +916,7 @@ __device__ __forceinline__ int find_rank(const int* rowP, const int* rowQ, int l
     }
     const int p = lo + lane;
     bool ge = false;
-    if (p <= hi) ge = (long long)rowP[p] + (long long)kOtherWork * rowQ[p] + (long long)kRodWork * p >= target;
+    if (p <= hi) ge = rank_work(rowP, rowQ, p) >= target;
     const unsigned m = __ballot_sync(0xffffffffu, ge);
     return m ? lo + __ffs(m) - 1 : hi;
 }
@@ -1051,7 +1056,7 @@ __global__ void k_partition(int n, int m, int nb, const int* __restrict__ rowP, 
 {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b > nb) return;   // uniform per warp
-    const long long total = (1LL + kOtherWork) * m + (long long)kRodWork * n;
+    const long long total = rank_work(rowP, rowQ, n);
     const int r = b == nb ? n : find_rank(rowP, rowQ, 0, n, total * b / nb);
     if ((threadIdx.x & 31) == 0) bstart[b] = r;
 }
