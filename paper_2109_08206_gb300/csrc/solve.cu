@@ -2123,7 +2123,7 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     // global-memory blocks still take their rods in count order when the
     // order (10 bytes of scratch per rod) fits
     const long long sort_bytes = 10 * (long long)maxrods;
-    a.sort_ns = !staged && maxrods > 0 && maxrods < 65536 && sort_bytes <= budget;
+    a.sort_ns = sizeof(T) == 8 && !staged && maxrods > 0 && maxrods < 65536 && sort_bytes <= budget;
     a.sort_cap = (int)maxrods;
     const size_t smem = staged ? (size_t)need : (a.sort_ns ? (size_t)sort_bytes : 0);
     const void* fn = staged ? (const void*)k_bbpgd<T, true> : (const void*)k_bbpgd<T, false>;
@@ -2168,7 +2168,7 @@ static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int
     const long long cap = 2 * ((max_sys + ctx->batch_cluster - 1) / ctx->batch_cluster);
     a.sort_cap = (int)(cap < 65535 ? cap : 65535);
     const long long sort_bytes = 10 * (long long)a.sort_cap;
-    a.sort_ns = cap > 0 && sort_bytes <= 64 * 1024;
+    a.sort_ns = sizeof(T) == 8 && cap > 0 && sort_bytes <= 64 * 1024;
     const size_t smem = a.sort_ns ? (size_t)sort_bytes : 0;
     // the attribute is the largest dynamic shared memory a launch may ask
     // for: raised when a batch needs more, never lowered, so that no call is
