@@ -15,6 +15,8 @@
 // into a per-rod list in shared memory, sorted there by (j, image)) ->
 // k_decide (the float64 keep/drop decision of the flagged candidates) ->
 // scan of per-rod counts -> k_emit (pairs in (i, j, image) order).
+#include <climits>
+
 #include "internal.cuh"
 
 namespace alens {
@@ -90,10 +92,11 @@ __global__ void k_cell_scatter(int n, const uint32_t* __restrict__ cellkey, cons
 
 // Rods of each cell in ascending id, so that the cell-sorted order (which the
 // solver also uses to number rods) does not depend on the atomics above.
-// One warp per cell: the cell's ids (distinct) are staged in shared memory
-// and each goes to its rank, the count of smaller ids in the cell.  A cell
-// longer than kSortCap (none in the benchmark workloads) is sorted in place
-// by lane 0.
+// One warp per cell: the cell's ids (distinct) are staged in shared memory;
+// up to 32 go to their ranks (the count of smaller ids), longer cells (the
+// dense nematic domains hold a few hundred) through a bitonic network,
+// len log^2 len work instead of len^2.  A cell longer than kSortCap (none in
+// the benchmark workloads) is sorted in place by lane 0.
 constexpr int kSortCap = 256;
 constexpr int kSortWarps = 4;
 __global__ void __launch_bounds__(kSortWarps * 32)
@@ -117,23 +120,32 @@ k_cell_sort_ids(int nkeys, const int* __restrict__ cell_start, int* __restrict__
     }
     int* sv = buf[warp];
     for (int u = lane; u < len; u += 32) sv[u] = sorted_id[b + u];
-    __syncwarp();
-    int rk[kSortCap / 32], xv[kSortCap / 32];
-#pragma unroll
-    for (int q = 0; q < kSortCap / 32; ++q) {
-        const int u = lane + 32 * q;
-        rk[q] = -1;
-        if (u < len) {
-            const int x = sv[u];
-            int r = 0;
-            for (int t = 0; t < len; ++t) r += sv[t] < x;
-            rk[q] = r;
-            xv[q] = x;
+    if (len > 32) {
+        // bitonic network over the cell's ids padded to a power of two
+        int P = 64;
+        while (P < len) P <<= 1;
+        for (int u = len + lane; u < P; u += 32) sv[u] = INT_MAX;
+        __syncwarp();
+        for (int size = 2; size <= P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = lane; t < (P >> 1); t += 32) {
+                    const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const int x = sv[lo], y = sv[hi];
+                    if ((x > y) == up) { sv[lo] = y; sv[hi] = x; }
+                }
+                __syncwarp();
+            }
         }
+        for (int u = lane; u < len; u += 32) sorted_id[b + u] = sv[u];
+        return;
     }
-#pragma unroll
-    for (int q = 0; q < kSortCap / 32; ++q)
-        if (rk[q] >= 0) sorted_id[b + rk[q]] = xv[q];
+    __syncwarp();
+    // up to 32 ids: each goes to its rank, the count of smaller ids
+    const int x = lane < len ? sv[lane] : 0;
+    int r = 0;
+    for (int t = 0; t < len; ++t) r += sv[t] < x;
+    if (lane < len) sorted_id[b + r] = x;
 }
 
 __global__ void k_cell_gather(int n, const int* __restrict__ sorted_id, const float4* __restrict__ pos32,
