@@ -1,6 +1,7 @@
 // Exclusive prefix sum of int32 counts (CSR row pointers, cell starts).
-// Three launches: per-tile totals, one block scanning the tile totals, then
-// per-tile scans offset by their tile's prefix.  Deterministic.
+// Two launches: per-tile totals, then per-tile scans, each block adding the
+// totals of the tiles before it (a few thousand at most) for its offset.
+// Integer sums: exact and deterministic.
 #include "internal.cuh"
 
 namespace alens {
@@ -53,29 +54,18 @@ __global__ void k_tile_sums(const int* __restrict__ in, int n, int* __restrict__
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-__global__ void k_scan_sums(int* sums, int ntiles)
-{
-    __shared__ int smem[64];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < ntiles; base += blockDim.x) {
-        int idx = base + threadIdx.x;
-        int v = idx < ntiles ? sums[idx] : 0;
-        int total;
-        int ex = block_exclusive_scan(v, smem, total);
-        int c = carry;
-        if (idx < ntiles) sums[idx] = c + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry = c + total;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) sums[ntiles] = carry;
-}
-
 __global__ void k_tile_scan(const int* __restrict__ in, int n, const int* __restrict__ sums, int* __restrict__ out)
 {
     __shared__ int smem[64];
+    __shared__ int pre;
+    if (threadIdx.x < 32) {   // this tile's offset: the totals of the tiles before it
+        int a = 0;
+        for (int t = threadIdx.x; t < (int)blockIdx.x; t += 32) a += sums[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (threadIdx.x == 0) pre = a;
+    }
+    __syncthreads();
     long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
     int v[kScanItems];
     int acc = 0;
@@ -85,13 +75,13 @@ __global__ void k_tile_scan(const int* __restrict__ in, int n, const int* __rest
         acc += v[k];
     }
     int total;
-    int ex = block_exclusive_scan(acc, smem, total) + sums[blockIdx.x];
+    int ex = block_exclusive_scan(acc, smem, total) + pre;
     for (int k = 0; k < kScanItems; ++k) {
         long long idx = base + k;
         if (idx < n) out[idx] = ex;
         ex += v[k];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[gridDim.x];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = pre + total;
 }
 
 // k_tile_sums sums a tile in strided order and k_tile_scan scans it in
@@ -101,8 +91,6 @@ cudaError_t exclusive_scan(aLENS_ctx* ctx, const int* counts, int* out, int n)
     int ntiles = n > 0 ? (n + kScanTile - 1) / kScanTile : 1;
     if (ntiles + 1 > ctx->scan_tmp_len) return cudaErrorInvalidValue;
     k_tile_sums<<<ntiles, kScanThreads, 0, ctx->stream>>>(counts, n, ctx->scan_tmp);
-    ++ctx->launches;
-    k_scan_sums<<<1, 1024, 0, ctx->stream>>>(ctx->scan_tmp, ntiles);
     ++ctx->launches;
     k_tile_scan<<<ntiles, kScanThreads, 0, ctx->stream>>>(counts, n, ctx->scan_tmp, out);
     ++ctx->launches;
