@@ -373,6 +373,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) { free(c); return ALENS_ERR_CUDA; }
     c->num_sms = prop.multiProcessorCount;
+    c->smem_optin = (int)prop.sharedMemPerBlockOptin;
     int clk = 0;
     cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, c->device);
     c->clock_khz = clk > 0 ? clk : 2.1e6;

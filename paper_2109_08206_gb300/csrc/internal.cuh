@@ -333,6 +333,10 @@ struct aLENS_ctx {
     int fault_mode;
     int solve_threads, solve_bps;
     int solve_barriers;      // 1: one-barrier solver where its share fits (default); 2: the two-barrier kernels
+    int smem_optin;          // the device's opt-in shared memory per block (bytes)
+    int attr1_set[2];        // the one-barrier kernel's dynamic shared-memory limit is set (float, double)
+    int occ1_key[2];         // launch shape (threads * 64 + blocks per SM) whose occupancy was checked ...
+    int occ1_ok[2];          // ... and whether that many blocks per SM fit at the full budget
     int last_solver;         // kernel of the last single-system solve: 1 one-barrier, 2 two-barrier staged, 3 two-barrier global
     int zero_start;          // the last setup started from gamma = 0 (no caller gamma)
     int qe_pending;          // the last setup's CSR-ordered other-side copies (qe) are still to be written

@@ -107,6 +107,7 @@ extern "C" aLENS_status aLENS_solve_lcp_noalloc(const aLENS_params* params, int6
     if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return ALENS_ERR_CUDA;
     if (!prop.cooperativeLaunch) return ALENS_ERR_CUDA;
     c.num_sms = prop.multiProcessorCount;
+    c.smem_optin = (int)prop.sharedMemPerBlockOptin;
     int clk = 0;
     cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
     c.clock_khz = clk > 0 ? clk : 2.1e6;

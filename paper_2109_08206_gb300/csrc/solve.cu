@@ -2072,10 +2072,9 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     const int nbw = (int)blocks + 1;
     k_partition<<<(nbw * 32 + 255) / 256, 256, 0, ctx->stream>>>(n, m, (int)blocks, ctx->rowP, ctx->rowQ, ctx->bstart);
     ++ctx->launches;
-    // counters C_SMEM, C_MAXRODS (adjacent) and C_SMEM1
+    // counters C_SMEM, and C_MAXRODS and C_SMEM1 (adjacent)
     if ((e = cudaMemsetAsync(ctx->dcount + C_SMEM, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ctx->dcount + C_MAXRODS, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ctx->dcount + C_SMEM1, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
+        (e = cudaMemsetAsync(ctx->dcount + C_MAXRODS, 0, 2 * sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
         return e;
     k_stage_need<<<((int)blocks + 127) / 128, 128, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart, ctx->rowP,
                                                                   ctx->rowQ, ctx->dcount + C_SMEM,
@@ -2087,30 +2086,42 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
                                                                             ctx->dcount + C_SMEM1);
         ++ctx->launches;
     }
-    unsigned long long need = 0, maxrods = 0, need1 = 0;
-    if ((e = cudaMemcpyAsync(&need, ctx->dcount + C_SMEM, sizeof(need), cudaMemcpyDeviceToHost, ctx->stream)) !=
-            cudaSuccess ||
-        (e = cudaMemcpyAsync(&maxrods, ctx->dcount + C_MAXRODS, sizeof(maxrods), cudaMemcpyDeviceToHost,
-                             ctx->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&need1, ctx->dcount + C_SMEM1, sizeof(need1), cudaMemcpyDeviceToHost, ctx->stream)) !=
-            cudaSuccess ||
+    // one readback of the counters C_SMEM .. C_SMEM1 (into the pinned host status
+    // buffer; the allocation-free entry point has none and reads into the stack)
+    unsigned long long local[C_SMEM1 - C_SMEM + 1];
+    unsigned long long* hb = ctx->hcount ? ctx->hcount + C_SMEM : local;
+    if ((e = cudaMemcpyAsync(hb, ctx->dcount + C_SMEM, (C_SMEM1 - C_SMEM + 1) * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
         return e;
-    int optin = 0;
-    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device)) != cudaSuccess)
-        return e;
+    const unsigned long long need = hb[0], maxrods = hb[C_MAXRODS - C_SMEM], need1 = hb[C_SMEM1 - C_SMEM];
+    const int optin = ctx->smem_optin;
     const long long budget = (long long)optin / bps - (long long)sizeof(Shared<T>) - 1024;
     if ((e = cudaMemsetAsync(ctx->bar, 0, 4 * sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
     // (warps 1-4 form the step decision: at least 160 threads)
     if (ctx->solve_barriers == 1 && threads >= 256 && need1 > 0 && (long long)need1 <= budget) {
         // one grid barrier per iteration: every block's share and its ghosts fit
         const void* fn1 = (const void*)k_bbpgd1<T>;
-        if ((e = cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need1)) != cudaSuccess)
-            return e;
-        int per_sm1 = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, fn1, threads, (size_t)need1)) != cudaSuccess)
-            return e;
-        if ((long long)per_sm1 * ctx->num_sms >= blocks) {
+        const int ti = sizeof(T) == 4 ? 0 : 1;
+        const long long budget1 = (long long)optin - (long long)sizeof(Shared1<T>) - 1024;   // one block per SM
+        if (!ctx->attr1_set[ti]) {
+            // the limit for the largest budget once; a launch asks for its own need
+            if ((e = cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget1)) !=
+                cudaSuccess)
+                return e;
+            ctx->attr1_set[ti] = 1;
+        }
+        // occupancy only falls as shared memory grows: checked once per shape at the full budget
+        const int key = threads * 64 + bps;
+        if (ctx->occ1_key[ti] != key) {
+            int per_sm1 = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, fn1, threads, (size_t)budget)) !=
+                cudaSuccess)
+                return e;
+            ctx->occ1_ok[ti] = per_sm1 >= bps;
+            ctx->occ1_key[ti] = key;
+        }
+        if (ctx->occ1_ok[ti] && (long long)bps * ctx->num_sms >= blocks) {
             void* args1[] = {&a};
             ++ctx->launches;
             ctx->last_solver = 1;
