@@ -234,7 +234,10 @@ def ensemble_sample(systems, target, seed=7):
 
 
 class SingleJob:
-    """One system stepped by aLENS_step."""
+    """One system stepped by aLENS_step (recorded once as a CUDA graph and
+    replayed, where the step runs the one-barrier solver)."""
+
+    graph = True
 
     def __init__(self, s):
         self.s = s
@@ -243,7 +246,10 @@ class SingleJob:
 
     def context(self, A, precision, tol, stream):
         p = A.params_of(self.s, precision=precision, tol=tol, max_iter=1_000_000)
-        return A.Context(p, self.n, 12 * self.n, stream=stream)
+        ctx = A.Context(p, self.n, 12 * self.n, stream=stream)
+        if self.graph:
+            ctx.set_step_graph(True)
+        return ctx
 
     def step(self, ctx, x, q, f, **kw):
         return ctx.step(x, q, f, **kw)
@@ -263,9 +269,12 @@ class SingleJob:
 
     def config(self, W, m):
         s = self.s
-        return {"workload": s.name, "rods": self.n, "pairs": m, "box": round(float(s.box[0]), 3),
-                "volume_fraction": round(self.n * W.rod_volume(s.diameter, s.length) / float(np.prod(s.box)), 4),
-                "springs": s.meta.get("springs")}
+        c = {"workload": s.name, "rods": self.n, "pairs": m, "box": round(float(s.box[0]), 3),
+             "volume_fraction": round(self.n * W.rod_volume(s.diameter, s.length) / float(np.prod(s.box)), 4),
+             "springs": s.meta.get("springs")}
+        if self.graph:
+            c["step"] = "one aLENS_step call, replayed as a captured CUDA graph where it runs the one-barrier solver"
+        return c
 
     def cpu(self, args):
         sub, a = spatial_sample(self.s, args.sample_rods)
@@ -346,6 +355,8 @@ class GradJob(SingleJob):
     """One step and its adjoint (aLENS_step + aLENS_step_adjoint) for the loss
     sum |x' - target|^2 of the differentiation workload."""
 
+    graph = False
+
     class Out:
         def __init__(self, d):
             self.d = d
@@ -415,6 +426,8 @@ class SpringJob(SingleJob):
     """The 1e5-rod suspension with its 50,000 crosslinkers as bilateral
     spring constraints (aLENS_set_springs) instead of explicit forces."""
 
+    graph = False
+
     def __init__(self, s, springs):
         super().__init__(s)
         self.sp = springs
@@ -458,6 +471,8 @@ class TrajJob(SingleJob):
     """A Brownian trajectory of the 1e5-rod suspension: every timed call is
     aLENS_run over `steps_per_call` steps (kT = 1, Brownian forces drawn on
     the device, the workload's own forces held as f_ext, warm start)."""
+
+    graph = False
 
     steps_per_call = 10
 

@@ -316,6 +316,26 @@ ALENS_API aLENS_status aLENS_step_batch(aLENS_ctx* ctx, int32_t n_systems, const
  * graph.  ALENS_ERR_INVALID for other values. */
 ALENS_API aLENS_status aLENS_set_batch_graph(aLENS_ctx* ctx, int32_t enable);
 
+/* CUDA-graph mode for aLENS_step (single systems; Appendix "Implementation":
+ * the step's kernels, recorded once and replayed, with no host round trip
+ * inside the step).  enable = 1: the first call with a new key (n, the six
+ * array pointers, parameters, scaling exponent, solver launch shape and
+ * schedule) runs without a graph; if that step ran the one-barrier solver
+ * (aLENS_info.solver = 1), the second call records the step and runs it,
+ * and later calls replay it.  In the recorded step the solver is launched
+ * with the whole shared-memory budget of its launch shape and checks on the
+ * device that every block's share fits; when one does not (the pairs moved
+ * into a denser arrangement), nothing moves and the call runs the step
+ * without a graph, as do all later calls with that key.  Kernels sized by
+ * the constraint count are launched for the context's capacity and read the
+ * count on the device; a step whose pairs exceed the capacity changes
+ * nothing and returns ALENS_ERR_CAPACITY with the required count.  Steps
+ * with springs or walls, and the timeout test hook, always run without a
+ * graph.  Results equal those of steps without a graph bit for bit.  The
+ * graph slot is shared with aLENS_set_batch_graph (one key per context).
+ * enable = 0 releases the graph.  ALENS_ERR_INVALID for other values. */
+ALENS_API aLENS_status aLENS_set_step_graph(aLENS_ctx* ctx, int32_t enable);
+
 /* Name of the CUDA runtime error behind the calling thread's last
  * ALENS_ERR_CUDA from a context entry point ("cudaSuccess" if none);
  * a static string. */
@@ -387,8 +407,11 @@ ALENS_API aLENS_status aLENS_set_scaling(aLENS_ctx* ctx, double beta);
 /* Test hook: mode 1 makes one thread block of the next solver launch (the
  * BBPGD of a step or solve, or the CG of aLENS_step_adjoint) leave before
  * its first grid-wide arrival, so that the other blocks' bounded waits run
- * out and the call returns ALENS_ERR_TIMEOUT.  The hook clears itself after
- * one launch.  mode 0 disables it. */
+ * out and the call returns ALENS_ERR_TIMEOUT.  mode 2 makes the next
+ * recorded single-system step (aLENS_set_step_graph) find its shares too
+ * big for its launch, so that the call falls back to a step without a
+ * graph.  The hook clears itself after one launch or recording.  mode 0
+ * disables it. */
 ALENS_API aLENS_status aLENS_inject_fault(aLENS_ctx* ctx, int32_t mode);
 
 /* Launch shape of the solver kernel: threads per block (multiple of 32,

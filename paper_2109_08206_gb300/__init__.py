@@ -114,6 +114,7 @@ def lib():
             "aLENS_set_launch": (i32, [vp, i32, i32]),
             "aLENS_set_solver_schedule": (i32, [vp, i32]),
             "aLENS_set_batch_graph": (i32, [vp, i32]),
+            "aLENS_set_step_graph": (i32, [vp, i32]),
             "aLENS_last_cuda_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -330,6 +331,12 @@ class Context:
         st = self._lib.aLENS_set_batch_graph(self._h, int(bool(enable)))
         if st != 0:
             raise AlensError(st, "aLENS_set_batch_graph")
+
+    def set_step_graph(self, enable: bool = True):
+        """Record aLENS_step as a CUDA graph and replay it (see include/alens.h)."""
+        st = self._lib.aLENS_set_step_graph(self._h, int(bool(enable)))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_step_graph")
 
     def set_batch_launch(self, threads: int, cluster_blocks: int):
         st = self._lib.aLENS_set_batch_launch(self._h, int(threads), int(cluster_blocks))

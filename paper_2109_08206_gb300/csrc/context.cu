@@ -515,7 +515,7 @@ aLENS_status aLENS_set_scaling(aLENS_ctx* c, double beta)
 
 aLENS_status aLENS_inject_fault(aLENS_ctx* c, int32_t mode)
 {
-    if (!c || mode < 0 || mode > 1) return ALENS_ERR_INVALID;
+    if (!c || mode < 0 || mode > 2) return ALENS_ERR_INVALID;
     c->fault_mode = mode;
     return ALENS_OK;
 }
@@ -749,7 +749,7 @@ static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, 
 // capacity check; 0 after a failure, and the update then leaves the rods
 // untouched).  The caller reads the status back after the graph runs.
 static aLENS_status step_graph_body(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
-                                    int32_t* pairs_out, double* gamma_out, double* vel_out)
+                                    int32_t* pairs_out, double* gamma_out, double* vel_out, bool single)
 {
     const int mcap = (int)c->max_pairs;
     c->mdev = c->dcount + C_MEFF;
@@ -762,7 +762,13 @@ static aLENS_status step_graph_body(aLENS_ctx* c, int64_t n, double* x, double* 
         CK(launch_assemble(c, (int)n, mcap, c->pairs, c->phi, c->dgeom, c->q64));
         CK(launch_rank(c, (int)n));
         CK(launch_solve_setup(c, (int)n, mcap, c->pairs, c->dgeom, c->q64, nullptr, quat, c->p.precision, c->rank));
-        st = run_solver(c, (int)n, mcap, nullptr, c->ev[2], c->ev[3]);
+        if (single) {
+            CK(record_event(c, c->ev[2]));
+            CK(launch_solve_graph1(c, (int)n, mcap, c->p.precision));
+            CK(record_event(c, c->ev[3]));
+        } else {
+            st = run_solver(c, (int)n, mcap, nullptr, c->ev[2], c->ev[3]);
+        }
     }
     if (st == ALENS_OK) {
         CK(launch_update(c, (int)n, mcap, x, quat, c->p.precision, vel_out, c->rank));
@@ -797,54 +803,59 @@ static aLENS_ctx::GraphKey graph_key(const aLENS_ctx* c, int64_t n, const double
     k.threads = c->batch_threads;
     k.cluster = c->batch_cluster;
     k.tables = c->tables_epoch;
+    k.kind = 1;
     return k;
 }
 
-// Replays (recording it first when needed) the graph of a batched step and
-// reads its outcome back.  Returns ALENS_ERR_NOT_IMPLEMENTED when the step
-// is to run eagerly instead (the first step of a new key).
-static aLENS_status step_batch_graph(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
-                                     int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info)
+// The key of a recorded single-system step.
+static aLENS_ctx::GraphKey single_key(const aLENS_ctx* c, int64_t n, const double* x, const double* quat,
+                                      const double* f_nc, const int32_t* pairs_out, const double* gamma_out,
+                                      const double* vel_out)
 {
-    const aLENS_ctx::GraphKey k = graph_key(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out);
-    const bool same = c->graph_state > 0 && memcmp(&k, &c->gkey, sizeof(k)) == 0;
-    if (!same) {
+    aLENS_ctx::GraphKey k = graph_key(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out);
+    k.threads = c->solve_threads;
+    k.cluster = c->solve_bps;
+    k.tables = 0;
+    k.kind = 2;
+    k.barriers = c->solve_barriers;
+    return k;
+}
+
+// Records the step of the current key on a private stream (recording enqueues
+// nothing: the graph runs on the context's stream) and instantiates it.
+static aLENS_status record_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
+                                int32_t* pairs_out, double* gamma_out, double* vel_out, bool single)
+{
+    c->launches = 0;
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t own = c->stream;
+    c->stream = c->cap_stream;
+    cudaError_t be = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    aLENS_status st = be == cudaSuccess ? step_graph_body(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, single)
+                                        : ALENS_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = be == cudaSuccess ? cudaStreamEndCapture(c->stream, &g) : be;
+    c->stream = own;
+    if (st != ALENS_OK || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
         drop_graph(c);
-        c->gkey = k;
-        c->graph_state = 1;   // this key runs eagerly once (tables, attributes, allocations settle)
-        return ALENS_ERR_NOT_IMPLEMENTED;
+        return st != ALENS_OK ? st : ALENS_ERR_CUDA;
     }
-    if (c->graph_state == 1) {
-        c->launches = 0;
-        if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-        // recording enqueues nothing: the step's launches go to a private
-        // stream for the capture, and the graph runs on the context's stream
-        cudaStream_t own = c->stream;
-        c->stream = c->cap_stream;
-        cudaError_t be = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-        aLENS_status st = be == cudaSuccess ? step_graph_body(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out)
-                                            : ALENS_ERR_CUDA;
-        cudaGraph_t g = nullptr;
-        const cudaError_t ce = be == cudaSuccess ? cudaStreamEndCapture(c->stream, &g) : be;
-        c->stream = own;
-        if (st != ALENS_OK || ce != cudaSuccess || !g) {
-            if (g) cudaGraphDestroy(g);
-            cudaGetLastError();
-            drop_graph(c);
-            return st != ALENS_OK ? st : ALENS_ERR_CUDA;
-        }
-        c->graph = g;
-        if (cudaGraphInstantiate(&c->gexec, g, 0) != cudaSuccess) {
-            cudaGetLastError();
-            drop_graph(c);
-            return ALENS_ERR_CUDA;
-        }
-        c->graph_launches = c->launches;
-        c->graph_state = 2;
+    c->graph = g;
+    if (cudaGraphInstantiate(&c->gexec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        drop_graph(c);
+        return ALENS_ERR_CUDA;
     }
-    CK(cudaGraphLaunch(c->gexec, c->stream));
-    c->launches = c->graph_launches;
-    c->last_solver = 4;
+    c->graph_launches = c->launches;
+    c->graph_state = 2;
+    return ALENS_OK;
+}
+
+// The outcome of a replayed step, read back after the graph ran.
+static aLENS_status graph_outcome(aLENS_ctx* c, int64_t n, aLENS_info* info)
+{
     aLENS_status st = read_status(c);
     if (st != ALENS_OK) return st;
     const long long mu = (long long)c->hcount[C_PAIRS];
@@ -876,6 +887,70 @@ static aLENS_status step_batch_graph(aLENS_ctx* c, int64_t n, double* x, double*
     return st;
 }
 
+// Replays (recording it first when needed) the graph of a batched step and
+// reads its outcome back.  Returns ALENS_ERR_NOT_IMPLEMENTED when the step
+// is to run eagerly instead (the first step of a new key).
+static aLENS_status step_batch_graph(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
+                                     int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info)
+{
+    const aLENS_ctx::GraphKey k = graph_key(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out);
+    const bool same = c->graph_state > 0 && memcmp(&k, &c->gkey, sizeof(k)) == 0;
+    if (!same) {
+        drop_graph(c);
+        c->gkey = k;
+        c->graph_state = 1;   // this key runs eagerly once (tables, attributes, allocations settle)
+        return ALENS_ERR_NOT_IMPLEMENTED;
+    }
+    if (c->graph_state == 1) {
+        const aLENS_status rs = record_step(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, false);
+        if (rs != ALENS_OK) return rs;
+    }
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    c->launches = c->graph_launches;
+    c->last_solver = 4;
+    return graph_outcome(c, n, info);
+}
+
+// The same for a single-system step: the first step of a key runs eagerly
+// (ALENS_ERR_NOT_IMPLEMENTED), and a key whose eager step did not run the
+// one-barrier solver, or whose replay found a share too big for the
+// recorded launch (kSolveRedo: nothing moved), stays eager.
+static aLENS_status step_single_graph(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
+                                      int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info)
+{
+    const aLENS_ctx::GraphKey k = single_key(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out);
+    const bool same = c->graph_state > 0 && memcmp(&k, &c->gkey, sizeof(k)) == 0;
+    if (!same) {
+        drop_graph(c);
+        c->gkey = k;
+        c->graph_state = 1;
+        return ALENS_ERR_NOT_IMPLEMENTED;
+    }
+    if (c->graph_state == 3) return ALENS_ERR_NOT_IMPLEMENTED;
+    if (c->graph_state == 1) {
+        bool ok = false;
+        CK(graph1_possible(c, c->p.precision, ok));
+        if (!ok) {
+            c->graph_state = 3;
+            return ALENS_ERR_NOT_IMPLEMENTED;
+        }
+        const aLENS_status rs = record_step(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, true);
+        if (rs != ALENS_OK) return rs;
+    }
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    c->launches = c->graph_launches;
+    c->last_solver = 1;
+    CK(cudaMemcpyAsync(c->hflags, c->dflags, sizeof(int) * F_NFLAGS, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->hflags[F_SOLVE_ERR] == kSolveRedo) {
+        drop_graph(c);
+        c->gkey = k;
+        c->graph_state = 3;
+        return ALENS_ERR_NOT_IMPLEMENTED;
+    }
+    return graph_outcome(c, n, info);
+}
+
 extern "C" {
 
 aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc, int32_t* pairs_out,
@@ -884,7 +959,16 @@ aLENS_status aLENS_step(aLENS_ctx* c, int64_t n, double* x, double* quat, const 
     if (c) { c->launches = 0; c->last_solver = 0; single_mode(c); }
     if (!rods_ok(c, n) || (n > 0 && (!x || !quat))) return ALENS_ERR_INVALID;
     if (!c->coop_ok) return ALENS_ERR_CUDA;
-    return step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
+    // graph mode: plain steps (no springs, walls or bounded-wait test hook)
+    const bool graphable = c->step_graph && n > 0 && c->sp_n == 0 && c->wall_axis < 0 && c->fault_mode != 1;
+    aLENS_status st = ALENS_ERR_NOT_IMPLEMENTED;
+    if (graphable) st = step_single_graph(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
+    if (st != ALENS_ERR_NOT_IMPLEMENTED) return st;
+    c->launches = 0;
+    st = step_impl(c, n, x, quat, f_nc, pairs_out, gamma_out, vel_out, info);
+    // a key whose eager step did not run the one-barrier solver stays eager
+    if (graphable && c->graph_state == 1 && c->last_solver != 1) c->graph_state = 3;
+    return st;
 }
 
 aLENS_status aLENS_set_springs(aLENS_ctx* c, int64_t n_springs, const int32_t* ends, const double* arms,
@@ -1136,6 +1220,14 @@ aLENS_status aLENS_set_batch_graph(aLENS_ctx* c, int32_t enable)
     if (!c || (enable != 0 && enable != 1)) return ALENS_ERR_INVALID;
     if (!enable) drop_graph(c);
     c->batch_graph = enable;
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_set_step_graph(aLENS_ctx* c, int32_t enable)
+{
+    if (!c || (enable != 0 && enable != 1)) return ALENS_ERR_INVALID;
+    if (!enable) drop_graph(c);
+    c->step_graph = enable;
     return ALENS_OK;
 }
 

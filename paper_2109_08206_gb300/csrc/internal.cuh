@@ -23,11 +23,14 @@ constexpr int kMaxMortonBits = 7;        // at most 128 cells per edge
 enum Flag : int {
     F_ERR = 0,        // first error code seen by any kernel (aLENS_status)
     F_ERR_ROD = 1,    // offending rod / pair index for INVALID or per-rod overflow
-    F_SOLVE_ERR = 2,  // solver kernel: ALENS_ERR_TIMEOUT when a grid wait ran out
+    F_SOLVE_ERR = 2,  // solver kernel: ALENS_ERR_TIMEOUT when a grid wait ran out, kSolveRedo (below)
     F_FINAL = 3,      // solver kernel: buffer index that holds the final gamma
     F_ITERS = 4,      // solver kernel: iterations taken
     F_NFLAGS = 16
 };
+// F_SOLVE_ERR of a recorded single-system step whose shares did not fit the
+// shared memory it was launched with: nothing moved, the host steps eagerly
+constexpr int kSolveRedo = 1 << 20;
 // 64-bit counters (Ctx::dcount)
 enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_SMEM = 6,
                    C_QUEUE = 7, C_WALLS = 8, C_MAXRODS = 9, C_SMEM1 = 10, C_MEFF = 11, C_NCOUNT = 12 };
@@ -343,18 +346,21 @@ struct aLENS_ctx {
     int qe_m, qe_prec;       // ... for this many constraints in this precision
     // batched steps as a captured CUDA graph (aLENS_set_batch_graph)
     const unsigned long long* mdev;   // while recording a graph: the device's constraint count (else NULL)
-    int batch_graph;         // graph mode on
+    int batch_graph;         // graph mode on (batched steps)
+    int step_graph;          // graph mode on (single-system steps, aLENS_set_step_graph)
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
     cudaStream_t cap_stream; // the graph is recorded here (the legacy default stream cannot be captured)
     int graph_launches;      // kernels in the graph
-    int graph_state;         // 0 nothing, 1 the key below ran eagerly once, 2 a graph of it is instantiated
+    int graph_state;         // 0 nothing, 1 the key below ran eagerly once, 2 a graph of it is instantiated,
+                             // 3 the key stays eager (its solver reads back, or a recorded step redid)
     struct GraphKey {
         int64_t n;
         const void* ptr[6];  // x, quat, f_nc, pairs_out, gamma_out, vel_out
         aLENS_params p;
         double beta;
         int threads, cluster, tables;
+        int kind, barriers;  // 1 batched step, 2 single-system step; the solver schedule
     } gkey;
     int tables_epoch;        // bumped whenever the batch tables change
     int coop_ok;
@@ -437,6 +443,11 @@ cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision);
 // global-memory solvers and the adjoint read them, the one-barrier solver
 // does not.
 cudaError_t launch_setup_qe(aLENS_ctx* ctx);
+// The single-system solve of a step recorded as a graph (no readback; the
+// kernel checks on the device that its shares fit and otherwise flags
+// kSolveRedo), and whether the context's launch shape allows it.
+cudaError_t launch_solve_graph1(aLENS_ctx* ctx, int n, int m, int precision);
+cudaError_t graph1_possible(aLENS_ctx* ctx, int precision, bool& ok);
 cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma_out);
 
 // Springs: rows mu .. mu + nb of the internal constraint list (pairs, phi,

@@ -229,6 +229,11 @@ struct SolveArgs {
     int sort_cap;  // rods the order's scratch holds (a larger share keeps the rank order)
     long long wait_cycles;
     int fault;
+    // a step recorded as a graph: the one-barrier kernel was launched with
+    // fit_cap bytes of shared memory and reads its shares' need here (null:
+    // the need was checked on the host)
+    const unsigned long long* need1_dev;
+    long long fit_cap;
     const int* __restrict__ bstart;   // [gridDim.x + 1] rod-rank boundaries of the blocks
 };
 
@@ -1693,6 +1698,15 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ Shared1<T> sh;
+    if (a.need1_dev) {
+        // recorded step: every block reads the same need, so either all run
+        // or all leave before their first barrier and ask for an eager step
+        const unsigned long long need = *a.need1_dev;
+        if (need == 0 || need > (unsigned long long)a.fit_cap) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[F_SOLVE_ERR] = kSolveRedo;
+            return;
+        }
+    }
     if (a.fault == 1 && blockIdx.x == 0) return;   // test hook: this block never arrives
     Own1<T> o;
     o.r0 = a.bstart[blockIdx.x];
@@ -2045,6 +2059,8 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.pi_tol = pi_threshold<T>(a.hD, a.tol);
     a.wait_cycles = (long long)(ctx->wait_s * ctx->clock_khz * 1e3);
     a.fault = 0;
+    a.need1_dev = nullptr;
+    a.fit_cap = 0;
     a.sort_ns = 0;
     a.sort_cap = 0;
     a.zero_start = ctx->zero_start;
@@ -2215,6 +2231,87 @@ cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision)
     if (precision == ALENS_MIXED)
         return per_system ? solve_batch_typed<float>(ctx, ctx->sb32, n, m) : solve_typed<float>(ctx, ctx->sb32, n, m);
     return per_system ? solve_batch_typed<double>(ctx, ctx->sb64, n, m) : solve_typed<double>(ctx, ctx->sb64, n, m);
+}
+
+// The single-system solve of a step recorded as a CUDA graph: no readback.
+// The one-barrier kernel is launched with the full shared-memory budget of
+// the launch shape, and its blocks check the need of the shares (computed
+// on the device by k_stage_need1) against it: a share that does not fit
+// makes every block leave before its first barrier with kSolveRedo in
+// F_SOLVE_ERR, the update and the outputs then leave everything untouched,
+// and the caller runs the step eagerly.  graph1_possible says whether the
+// launch shape can take this path at all.
+template <typename T>
+static long long graph1_budget(const aLENS_ctx* ctx)
+{
+    const int bps = ctx->solve_bps > 0 ? ctx->solve_bps : 1;
+    return (long long)ctx->smem_optin / bps - (long long)sizeof(Shared<T>) - 1024;
+}
+
+template <typename T>
+static cudaError_t graph1_check(aLENS_ctx* ctx, bool& ok)
+{
+    ok = false;
+    const int threads = ctx->solve_threads, bps = ctx->solve_bps > 0 ? ctx->solve_bps : 1;
+    if (ctx->solve_barriers != 1 || threads < 256) return cudaSuccess;
+    const void* fn1 = (const void*)k_bbpgd1<T>;
+    const int ti = sizeof(T) == 4 ? 0 : 1;
+    const long long budget1 = (long long)ctx->smem_optin - (long long)sizeof(Shared1<T>) - 1024;
+    cudaError_t e;
+    if (!ctx->attr1_set[ti]) {
+        if ((e = cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget1)) != cudaSuccess)
+            return e;
+        ctx->attr1_set[ti] = 1;
+    }
+    int per_sm1 = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, fn1, threads, (size_t)graph1_budget<T>(ctx))) !=
+        cudaSuccess)
+        return e;
+    ok = per_sm1 >= bps;
+    return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t solve_graph1_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m)
+{
+    SolveArgs<T> a = make_args(ctx, sb, n, m);
+    const bool force_redo = ctx->fault_mode == 2;   // test hook: the recorded need never fits
+    ctx->fault_mode = 0;
+    const int threads = ctx->solve_threads;
+    const int bps = ctx->solve_bps > 0 ? ctx->solve_bps : 1;
+    long long want = ((long long)n + 31) / 32;
+    long long blocks = (long long)bps * ctx->num_sms;
+    if (want < blocks) blocks = want < 1 ? 1 : want;
+    if (blocks > ctx->max_blocks) blocks = ctx->max_blocks;
+    const long long budget = graph1_budget<T>(ctx);
+    a.need1_dev = ctx->dcount + C_SMEM1;
+    a.fit_cap = force_redo ? 0 : budget;
+    cudaError_t e;
+    const int nbw = (int)blocks + 1;
+    k_partition<<<(nbw * 32 + 255) / 256, 256, 0, ctx->stream>>>(n, m, (int)blocks, ctx->rowP, ctx->rowQ, ctx->bstart);
+    ++ctx->launches;
+    if ((e = cudaMemsetAsync(ctx->dcount + C_SMEM1, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess) return e;
+    k_stage_need1<<<((int)blocks * 32 + 255) / 256, 256, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart,
+                                                                        ctx->rowP, ctx->rowQ, ctx->qlist,
+                                                                        ctx->dcount + C_SMEM1);
+    ++ctx->launches;
+    if ((e = cudaMemsetAsync(ctx->bar, 0, 4 * sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
+    void* args1[] = {&a};
+    ++ctx->launches;
+    ctx->last_solver = 1;
+    return cudaLaunchCooperativeKernel((const void*)k_bbpgd1<T>, dim3((unsigned)blocks), dim3(threads), args1,
+                                       (size_t)budget, ctx->stream);
+}
+
+cudaError_t graph1_possible(aLENS_ctx* ctx, int precision, bool& ok)
+{
+    return precision == ALENS_MIXED ? graph1_check<float>(ctx, ok) : graph1_check<double>(ctx, ok);
+}
+
+cudaError_t launch_solve_graph1(aLENS_ctx* ctx, int n, int m, int precision)
+{
+    return precision == ALENS_MIXED ? solve_graph1_typed<float>(ctx, ctx->sb32, n, m)
+                                    : solve_graph1_typed<double>(ctx, ctx->sb64, n, m);
 }
 
 cudaError_t launch_gamma_out(aLENS_ctx* ctx, int m, int precision, double* gamma_out)
