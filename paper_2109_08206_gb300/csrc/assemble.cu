@@ -19,6 +19,8 @@
 // contiguously.
 #include <float.h>
 
+#include <climits>
+
 #include "internal.cuh"
 
 namespace alens {
@@ -184,12 +186,32 @@ __global__ void k_scatter_owner(int m, const int32_t* __restrict__ pairs, const 
 }
 
 // Ascending order inside every CSR segment (segments are short), so that
-// the layout does not depend on the order of the atomics above.
+// the layout does not depend on the order of the atomics above.  A segment
+// of up to kSegRegs entries is loaded at once and each entry stored at its
+// rank (the entries are distinct constraint ids); a longer one is sorted in
+// place.
+constexpr int kSegRegs = 16;
 __global__ void k_sort_segments(int n, const int* __restrict__ row, int* __restrict__ list)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int b = row[r], e = row[r + 1];
+    if (e - b <= kSegRegs) {
+        const int len = e - b;
+        int v[kSegRegs];
+#pragma unroll
+        for (int u = 0; u < kSegRegs; ++u) v[u] = u < len ? list[b + u] : INT_MAX;
+#pragma unroll
+        for (int u = 0; u < kSegRegs; ++u) {
+            if (u < len) {
+                int k = 0;
+#pragma unroll
+                for (int t = 0; t < kSegRegs; ++t) k += v[t] < v[u];
+                list[b + k] = v[u];
+            }
+        }
+        return;
+    }
     for (int u = b + 1; u < e; ++u) {
         int v = list[u];
         int w = u - 1;
@@ -279,7 +301,9 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
         }
     }
     scale64[cc] = sig;
-    isc[cc] = (T)(1.0 / sig);
+    // sig is a float value: for float, 1/sig in float is (T)(1.0 / sig)
+    // (double rounding is innocuous for a quotient at 53 >= 2 * 24 + 2 bits)
+    isc[cc] = sizeof(T) == 4 ? (T)__fdiv_rn(1.0f, (float)sig) : (T)(1.0 / sig);
 #pragma unroll
     for (int u = 0; u < 9; ++u) {
         const double rs = r[u] * sig;

@@ -59,6 +59,7 @@ int make_geo(const aLENS_params* p, Geo* g, Mob* mob)
         if (nc < 1) nc = 1;
         g->nc[k] = nc;
         g->cs[k] = p->box[k] / nc;
+        g->inv_cs[k] = 1.0 / g->cs[k];
         if (p->box[k] > maxbox) maxbox = p->box[k];
         if (nc > maxnc) maxnc = nc;
     }
@@ -264,7 +265,7 @@ aLENS_status batch_tables(aLENS_ctx* c, int ns, const aLENS_system* sys, const i
         c->sys_res = nullptr; c->max_systems = 0;
         if (dmalloc(&c->systab, sizeof(SysGeo) * ns) != cudaSuccess ||
             dmalloc(&c->sysoff, sizeof(long long) * (ns + 1)) != cudaSuccess ||
-            dmalloc(&c->sys_order, sizeof(int) * ns) != cudaSuccess ||
+            dmalloc(&c->sys_order, sizeof(int) * sys_queue_ints(ns)) != cudaSuccess ||
             dmalloc(&c->sys_iters, sizeof(int) * ns) != cudaSuccess ||
             dmalloc(&c->sys_res, sizeof(double) * ns) != cudaSuccess) {
             cudaGetLastError();

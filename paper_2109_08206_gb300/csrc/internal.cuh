@@ -31,6 +31,11 @@ enum Flag : int {
 // F_SOLVE_ERR of a recorded single-system step whose shares did not fit the
 // shared memory it was launched with: nothing moved, the host steps eagerly
 constexpr int kSolveRedo = 1 << 20;
+// The batched solver's pairs (two clusters on one system): at most kMaxPairs
+// per launch, each of at most kPairBlocks blocks (two clusters of 8)
+constexpr int kMaxPairs = 16;
+constexpr int kPairBlocks = 16;
+inline size_t sys_queue_ints(int ns) { return (size_t)ns + 2 * ((size_t)ns + kMaxPairs) + 1 + kMaxPairs; }
 // 64-bit counters (Ctx::dcount)
 enum Count : int { C_PAIRS = 0, C_OVERLAP = 1, C_MINGAP = 2, C_CAND = 3, C_RESID = 4, C_ALPHA0 = 5, C_SMEM = 6,
                    C_QUEUE = 7, C_WALLS = 8, C_MAXRODS = 9, C_SMEM1 = 10, C_MEFF = 11, C_NCOUNT = 12 };
@@ -50,6 +55,7 @@ __device__ __forceinline__ int count_of(int m, const unsigned long long* mdev)
 struct Geo {                 // everything the geometry kernels need
     double box[3];
     double cs[3];            // cell edge per axis (>= L + D + delta_c)
+    double inv_cs[3];        // 1 / cs (cell_index's first guess)
     int nc[3];               // cells per axis
     int bits;                // Morton bits per axis
     double diameter, length, half, delta_c, dt;
@@ -102,9 +108,29 @@ __host__ __device__ inline uint32_t morton3(int cx, int cy, int cz)
 // Wrap one coordinate into [0, b).
 __device__ __forceinline__ double wrap_coord(double v, double b)
 {
-    double w = __dsub_rn(v, __dmul_rn(b, floor(__ddiv_rn(v, b))));
+    // v - b floor(v / b).  For v in [-b, 2b) the floor of the rounded
+    // quotient is -1, 0 or 1 on the same sides of -b, 0, b and 2b as v: the
+    // double just below b (2b) divided by b rounds to a double below 1 (2),
+    // since b's unit in the last place is at least 2^-53 b.  Those cases
+    // need no division and give the same bits (v - b is exact on [b, 2b]).
+    double w;
+    if (v >= 0.0 && v < b) w = __dadd_rn(v, 0.0);   // + 0.0: -0 becomes +0, as v - b * 0 does
+    else if (v < 0.0 && v >= -b) w = __dadd_rn(v, b);
+    else if (v >= b && v < 2.0 * b) w = __dsub_rn(v, b);
+    else w = __dsub_rn(v, __dmul_rn(b, floor(__ddiv_rn(v, b))));
     if (!(w < b) || w < 0.0) w = 0.0;
     return w;
+}
+
+// (int)(w / cs) for a wrapped coordinate w >= 0: the product with 1 / cs is
+// within about 1e-12 of the rounded quotient (fewer than 2^10 cells), so its
+// floor is the quotient's unless it lies within 1e-9 of an integer, where
+// the division decides.
+__device__ __forceinline__ int cell_index(double w, double cs, double inv_cs)
+{
+    const double q = __dmul_rn(w, inv_cs), f = floor(q), r = q - f;
+    if (r > 1e-9 && r < 1.0 - 1e-9) return (int)f;
+    return (int)__ddiv_rn(w, cs);
 }
 
 // Rod axis R(theta) e_z of a quaternion (s, a, b, c).
@@ -378,7 +404,9 @@ struct aLENS_ctx {
     int batch_keys;          // their cell keys
     void* batch_host;        // host copy of the last aLENS_system array (to skip re-uploads)
     int64_t* batch_off_host; // host copy of the last rod offsets
-    int* sys_order;          // [max_systems] queue order of the per-system solver
+    int* sys_order;          // [max_systems] queue order of the per-system solver, then the
+                             // queue entries [2 (max_systems + kMaxPairs)], their count and
+                             // the pairs' barrier counters [kMaxPairs] (sys_queue_ints ints)
     int* sys_iters;          // [max_systems] iterations of each system's solve
     double* sys_res;         // [max_systems] final residual of each system
     int last_batch_n;        // systems of the last completed aLENS_step_batch (0: none)

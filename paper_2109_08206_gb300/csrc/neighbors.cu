@@ -46,7 +46,7 @@ __global__ void k_pack(int n, int np, const double* __restrict__ x, const double
         double v = x[3 * (size_t)i + k];
         bad |= !isfinite(v);
         w[k] = wrap_coord(v, g.box[k]);
-        int ck = (int)(w[k] / g.cs[k]);
+        int ck = cell_index(w[k], g.cs[k], g.inv_cs[k]);
         cc[k] = ck < 0 ? 0 : (ck >= g.nc[k] ? g.nc[k] - 1 : ck);
         xw[k * (size_t)np + i] = w[k];
         axis[k * (size_t)np + i] = p[k];
@@ -97,7 +97,7 @@ __global__ void k_cell_scatter(int n, const uint32_t* __restrict__ cellkey, cons
 // dense nematic domains hold a few hundred) through a bitonic network,
 // len log^2 len work instead of len^2.  A cell longer than kSortCap (none in
 // the benchmark workloads) is sorted in place by lane 0.
-constexpr int kSortCap = 256;
+constexpr int kSortCap = 1024;
 constexpr int kSortWarps = 4;
 __global__ void __launch_bounds__(kSortWarps * 32)
 k_cell_sort_ids(int nkeys, const int* __restrict__ cell_start, int* __restrict__ sorted_id)

@@ -827,7 +827,7 @@ struct Shared {
     T bc[4];
     T part[4];   // this block's partial (cluster solver: read by the cluster's blocks)
     T alpha;
-    int done, ok, kind, cur, sys;
+    int done, ok, kind, cur, sys, pair;
 };
 
 // Synchronisation of the blocks that share one problem.
@@ -882,6 +882,36 @@ struct ClusterSync {
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < 4; ++u) tot[u] = sh.bc[u];
+    }
+};
+
+// Batches: a cluster alone, or two clusters on one system (a pair).  A pair
+// synchronises its blocks like the grid solver, on a bounded barrier over a
+// counter of its own, with the block sums in global memory; a cluster alone
+// uses the hardware cluster barrier and distributed shared memory.
+template <typename T>
+struct BatchSync {
+    unsigned* bar;       // the pair's arrival counter (null: a cluster alone)
+    int* flags;
+    long long wait_cycles;
+    T* partials;         // the pair's [4][nb] block sums
+    unsigned nb, epoch;  // the pair's blocks, barriers passed
+    int rank;            // this block's rank in the pair
+    template <typename SH>
+    __device__ __forceinline__ bool barrier(SH& sh)
+    {
+        if (bar) return grid_barrier(bar, nb * ++epoch, flags, wait_cycles, &sh.ok);
+        cg::this_cluster().sync();
+        return true;
+    }
+    template <typename SH>
+    __device__ __forceinline__ T* slot(SH& sh) { return bar ? partials + rank : sh.part; }
+    __device__ __forceinline__ int stride() const { return bar ? (int)nb : 1; }
+    template <typename SH>
+    __device__ __forceinline__ void total(SH& sh, T tot[4])
+    {
+        if (bar) grid_total(partials, (int)nb, sh.bc, tot);
+        else ClusterSync().total(sh, tot);
     }
 };
 
@@ -1902,33 +1932,44 @@ __global__ void k_stage_need1(int nb, int esize, const int* __restrict__ bstart,
 // residual and stopping test.  A system's rods are the contiguous ranks
 // [sysoff[s], sysoff[s+1]) and its constraints the contiguous owner-major
 // range they own, so each block of the cluster takes a work-balanced share
-// of them exactly as the grid solver does.  The final state is left in
-// buffer 0; per-system iterations and residuals are written out, and the
-// largest of each into the step's counters.
+// of them exactly as the grid solver does.  The queue's entries (qent:
+// system, pair code) list the largest systems twice: the two clusters that
+// take them solve the system together as one group of twice the blocks (a
+// pair; code = 2 * pair + member), so that no single system's solve outlasts
+// the rest of the queue.  Which systems are paired depends only on the
+// systems and the launch, so every step computes the same numbers.  The
+// final state is left in buffer 0; per-system iterations and residuals are
+// written out, and the largest of each into the step's counters.
 template <typename T>
 __global__ void __launch_bounds__(1024, 1)
-k_bbpgd_sys(SolveArgs<T> a, int ns, const long long* __restrict__ sysoff, const int* __restrict__ order,
-            unsigned long long* __restrict__ queue, int* __restrict__ sys_iters, double* __restrict__ sys_res)
+k_bbpgd_sys(SolveArgs<T> a, const long long* __restrict__ sysoff, const int* __restrict__ qent,
+            const int* __restrict__ qn, unsigned* __restrict__ pair_bar, unsigned long long* __restrict__ queue,
+            int* __restrict__ sys_iters, double* __restrict__ sys_res)
 {
     extern __shared__ __align__(16) unsigned char dyn[];   // rod order scratch (when a.sort_ns)
     __shared__ Shared<T> sh;
     __shared__ int bounds[2];
     cg::cluster_group cl = cg::this_cluster();
     const int crank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
+    const int nq = *qn;
     for (;;) {
         if (crank == 0 && threadIdx.x == 0) {
             const unsigned long long k = atomicAdd(queue, 1ull);
-            sh.sys = k < (unsigned long long)ns ? order[k] : -1;
+            sh.sys = k < (unsigned long long)nq ? qent[2 * k] : -1;
+            sh.pair = k < (unsigned long long)nq ? qent[2 * k + 1] : -1;
         }
         cl.sync();
         const int s = *cl.map_shared_rank(&sh.sys, 0);
-        cl.sync();   // every block has the id before block 0 takes the next one
+        const int pc = *cl.map_shared_rank(&sh.pair, 0);
+        cl.sync();   // every block has the entry before block 0 takes the next one
         if (s < 0) break;
+        const int member = pc >= 0 ? (pc & 1) : 0;
+        const int gs = pc >= 0 ? 2 * cs : cs, grank = member * cs + crank;   // the group's blocks, this one's rank
         const int R0 = (int)sysoff[s], R1 = (int)sysoff[s + 1];
         if (threadIdx.x < 64) {   // warp w finds end w of this block's share
-            const int w = threadIdx.x >> 5, k = crank + w;
+            const int w = threadIdx.x >> 5, k = grank + w;
             const long long W0 = rank_work(a.rowP, a.rowQ, R0), W1 = rank_work(a.rowP, a.rowQ, R1);
-            const int r = k == 0 ? R0 : (k == cs ? R1 : find_rank(a.rowP, a.rowQ, R0, R1, W0 + (W1 - W0) * k / cs));
+            const int r = k == 0 ? R0 : (k == gs ? R1 : find_rank(a.rowP, a.rowQ, R0, R1, W0 + (W1 - W0) * k / gs));
             if ((threadIdx.x & 31) == 0) bounds[w] = r;
         }
         __syncthreads();
@@ -1950,7 +1991,14 @@ k_bbpgd_sys(SolveArgs<T> a, int ns, const long long* __restrict__ sysoff, const 
         o.cap_c = o.c1 - o.c0;
         o.cap_r = o.r1 - o.r0;
         o.cap_q = o.q1 - o.q0;
-        ClusterSync sy;
+        BatchSync<T> sy;
+        sy.bar = pc >= 0 ? pair_bar + (pc >> 1) : nullptr;
+        sy.flags = a.flags;
+        sy.wait_cycles = a.wait_cycles;
+        sy.partials = reinterpret_cast<T*>(a.partials) + (pc >= 0 ? (size_t)(pc >> 1) * 4 * kPairBlocks : 0);
+        sy.nb = (unsigned)gs;
+        sy.epoch = 0;
+        sy.rank = grank;
         StepState<T> st;
         solve_loop<T, false>(a, o, sh, sy, st);
         if (sh.cur == 1) {
@@ -1961,7 +2009,7 @@ k_bbpgd_sys(SolveArgs<T> a, int ns, const long long* __restrict__ sysoff, const 
                 st_ref(a.gg0, c, gr, gl);
             }
         }
-        if (crank == 0 && threadIdx.x == 0) {
+        if (grank == 0 && threadIdx.x == 0) {
             sys_iters[s] = st.iters;
             const double res = st.residual(a.hD);
             sys_res[s] = res;
@@ -1986,6 +2034,41 @@ __global__ void k_sys_order(int ns, const long long* __restrict__ sysoff, const 
         pos += mt > ms || (mt == ms && t < s);
     }
     order[pos] = s;
+}
+
+// The queue of the per-system solver: the first K systems of the order are
+// paired (listed twice), the others listed once.  A system is paired if it
+// is among the nclusters / 4 largest, holds at least 4096 constraints per
+// block of one cluster (below that the pair's grid-style barriers cost more
+// than the extra blocks save) and more than half of one cluster's mean
+// share of the batch's constraints.  One block; also zeroes the pairs'
+// barrier counters.
+__global__ void k_sys_queue(int ns, const long long* __restrict__ sysoff, const int* __restrict__ rowP,
+                            const int* __restrict__ order, int nclusters, int cs, int* __restrict__ qent,
+                            int* __restrict__ qn, unsigned* __restrict__ pair_bar)
+{
+    __shared__ int npair;
+    if (threadIdx.x == 0) {
+        const long long total = (long long)rowP[sysoff[ns]] - rowP[sysoff[0]];
+        const int cap = nclusters / 4 < kMaxPairs ? nclusters / 4 : kMaxPairs;
+        int k = 0;
+        while (k < cap && k < ns) {
+            const int sy = order[k];
+            const long long m = (long long)rowP[sysoff[sy + 1]] - rowP[sysoff[sy]];
+            if (m < 4096LL * cs || 2LL * nclusters * m <= total) break;
+            ++k;
+        }
+        npair = k;
+        *qn = ns + k;
+    }
+    __syncthreads();
+    const int K = npair;
+    for (int t = threadIdx.x; t < kMaxPairs; t += blockDim.x) pair_bar[t] = 0u;
+    for (int e = threadIdx.x; e < ns + K; e += blockDim.x) {
+        const bool paired = e < 2 * K;   // entry e = 2 * pair + member
+        qent[2 * e] = paired ? order[e >> 1] : order[e - K];
+        qent[2 * e + 1] = paired ? e : -1;
+    }
 }
 
 // gamma back in the caller's pair order.
@@ -2174,10 +2257,6 @@ static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int
     const int ns = ctx->batch_n;
     cudaError_t e;
     if ((e = launch_setup_qe(ctx)) != cudaSuccess) return e;   // the per-system solver reads qe
-    k_sys_order<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(ns, ctx->sysoff, ctx->rowP, ctx->sys_order);
-    ++ctx->launches;
-    if ((e = cudaMemsetAsync(ctx->dcount + C_QUEUE, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
-        return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -2217,12 +2296,23 @@ static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int
     int nclusters = 0;
     if ((e = cudaOccupancyMaxActiveClusters(&nclusters, k_bbpgd_sys<T>, &cfg)) != cudaSuccess) return e;
     if (nclusters < 1) return cudaErrorInvalidConfiguration;
-    if (nclusters > ns) nclusters = ns;   // a cluster per system at most
+    // a cluster per queue entry at most (every system, and the pairs' second entries)
+    const int max_pairs = nclusters / 4 < kMaxPairs ? nclusters / 4 : kMaxPairs;
+    if (nclusters > ns + max_pairs) nclusters = ns + max_pairs;
+    int* qent = ctx->sys_order + ns;
+    int* qn = qent + 2 * ((size_t)ns + kMaxPairs);
+    unsigned* pair_bar = reinterpret_cast<unsigned*>(qn + 1);
+    k_sys_order<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(ns, ctx->sysoff, ctx->rowP, ctx->sys_order);
+    k_sys_queue<<<1, 256, 0, ctx->stream>>>(ns, ctx->sysoff, ctx->rowP, ctx->sys_order, nclusters, ctx->batch_cluster,
+                                            qent, qn, pair_bar);
+    ctx->launches += 2;
+    if ((e = cudaMemsetAsync(ctx->dcount + C_QUEUE, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
+        return e;
     cfg.gridDim = dim3((unsigned)(nclusters * ctx->batch_cluster));
     ++ctx->launches;
     ctx->last_solver = 4;
-    return cudaLaunchKernelEx(&cfg, k_bbpgd_sys<T>, a, ns, (const long long*)ctx->sysoff, (const int*)ctx->sys_order,
-                              ctx->dcount + C_QUEUE, ctx->sys_iters, ctx->sys_res);
+    return cudaLaunchKernelEx(&cfg, k_bbpgd_sys<T>, a, (const long long*)ctx->sysoff, (const int*)qent,
+                              (const int*)qn, pair_bar, ctx->dcount + C_QUEUE, ctx->sys_iters, ctx->sys_res);
 }
 
 cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision)
