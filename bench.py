@@ -294,6 +294,7 @@ class BatchJob:
         self.n = int(self.off[-1])
         self.name = f"ensemble{len(systems)}"
         self.ms = None   # per-system constraint counts (set by the first step with pairs_out)
+        self.tables = None
 
     def context(self, A, precision, tol, stream):
         s0 = self.systems[0]
@@ -304,7 +305,10 @@ class BatchJob:
         return ctx
 
     def step(self, ctx, x, q, f, **kw):
-        return ctx.step_batch(self.spec, self.off, x, q, f, **kw)
+        if self.tables is None:   # the C tables of the batch, built once
+            import paper_2109_08206_gb300 as A
+            self.tables = A.BatchSpec(self.spec, self.off)
+        return ctx.step_batch(self.tables, None, x, q, f, **kw)
 
     def tune(self, T, ctx, x, q, f, precision):
         return T.tune_batch(ctx, self.spec, self.off, x, q, f, precision)

@@ -385,6 +385,19 @@ ALENS_API aLENS_status aLENS_step_adjoint(aLENS_ctx* ctx, int64_t n, const doubl
  * are those of its info.  Synchronises the context's stream. */
 ALENS_API aLENS_status aLENS_batch_results(aLENS_ctx* ctx, int32_t n_systems, int32_t* iters, double* residual);
 
+/* Blocks that solved each system in the last aLENS_step_batch: one
+ * cluster's blocks (aLENS_set_batch_launch), or twice as many for a system
+ * that two clusters solved together.  The per-system solver pairs clusters
+ * on the largest systems (at most a quarter of its clusters' count, each
+ * with at least 4096 constraints per block of one cluster and more than
+ * half of one cluster's mean share of the batch's constraints), so that no
+ * single system's solve outlasts the rest of the queue; the choice depends
+ * only on the systems and the launch shape.  blocks is a HOST array of
+ * n_systems entries; n_systems must equal that call's.  For a batch of one
+ * system the entry is 0 (the single-system solver ran).  Synchronises the
+ * context's stream. */
+ALENS_API aLENS_status aLENS_batch_groups(aLENS_ctx* ctx, int32_t n_systems, int32_t* blocks);
+
 /* Launch shape of the per-system solver of aLENS_step_batch: threads per
  * block (multiple of 32, <= 1024; default 1024) and blocks per cluster
  * (1, 2, 4 or 8; default 8).  For tuning. */

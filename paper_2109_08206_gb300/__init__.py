@@ -100,6 +100,7 @@ def lib():
             "aLENS_step": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, IP]),
             "aLENS_step_batch": (i32, [vp, i32, C.POINTER(System), C.POINTER(i64), vp, vp, vp, vp, vp, vp, IP]),
             "aLENS_batch_results": (i32, [vp, i32, vp, vp]),
+            "aLENS_batch_groups": (i32, [vp, i32, vp]),
             "aLENS_step_adjoint": (i32, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp,
                                          C.POINTER(d), IP]),
             "aLENS_set_batch_launch": (i32, [vp, i32, i32]),
@@ -164,6 +165,22 @@ def _ptr(t, dtype, shape_tail=None):
     if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
         raise ValueError(f"expected shape [*, {shape_tail}], got {tuple(t.shape)}")
     return C.c_void_p(t.data_ptr())
+
+
+class BatchSpec:
+    """The C tables of a batch (aLENS_system array and rod offsets), built
+    once for repeated Context.step_batch calls on the same systems."""
+
+    def __init__(self, systems, rod_offset):
+        ns = len(systems)
+        if len(rod_offset) != ns + 1:
+            raise ValueError("rod_offset needs n_systems + 1 entries")
+        self.n_systems = ns
+        self.tab = (System * ns)()
+        for s, (box, length) in enumerate(systems):
+            b = box if hasattr(box, "__len__") else (box, box, box)
+            self.tab[s] = System((C.c_double * 3)(*[float(v) for v in b]), float(length))
+        self.off = (C.c_int64 * (ns + 1))(*[int(v) for v in rod_offset])
 
 
 class Context:
@@ -297,15 +314,13 @@ class Context:
 
         ``systems``: sequence of (box, length) with box a 3-sequence or a scalar;
         ``rod_offset``: n_systems + 1 integers, system s owning rods
-        [rod_offset[s], rod_offset[s+1]).  Returns Info (aggregated over the batch).
+        [rod_offset[s], rod_offset[s+1]).  Or ``systems`` = a BatchSpec of
+        both (``rod_offset`` then ignored), which saves rebuilding the C
+        tables on every call.  Returns Info (aggregated over the batch).
         """
         import torch
-        ns = len(systems)
-        tab = (System * ns)()
-        for s, (box, length) in enumerate(systems):
-            b = box if hasattr(box, "__len__") else (box, box, box)
-            tab[s] = System((C.c_double * 3)(*[float(v) for v in b]), float(length))
-        off = (C.c_int64 * (ns + 1))(*[int(v) for v in rod_offset])
+        spec = systems if isinstance(systems, BatchSpec) else BatchSpec(systems, rod_offset)
+        ns, tab, off = spec.n_systems, spec.tab, spec.off
         info = Info()
         st = self._lib.aLENS_step_batch(self._h, ns, tab, off, _ptr(x, torch.float64, (3,)),
                                         _ptr(quat, torch.float64, (4,)), _ptr(f_nc, torch.float64, (6,)),
@@ -325,6 +340,15 @@ class Context:
         if st != 0:
             raise AlensError(st, "aLENS_batch_results")
         return it, res
+
+    def batch_groups(self, n_systems: int):
+        """Blocks that solved each system of the last step_batch (int32 [S])."""
+        import numpy as np
+        b = np.zeros(n_systems, dtype=np.int32)
+        st = self._lib.aLENS_batch_groups(self._h, int(n_systems), b.ctypes.data_as(C.c_void_p))
+        if st != 0:
+            raise AlensError(st, "aLENS_batch_groups")
+        return b
 
     def set_batch_graph(self, enable: bool = True):
         """Record aLENS_step_batch as a CUDA graph and replay it (see include/alens.h)."""

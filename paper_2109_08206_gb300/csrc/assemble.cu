@@ -486,17 +486,23 @@ cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, 
 }
 
 template <typename T>
+static cudaError_t setup_rods_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, const double* quat,
+                                    const int* rank)
+{
+    if (n > 0) {
+        k_setup_rods<T><<<nblk(n, 256), 256, 0, ctx->stream>>>(n, (int)ctx->max_rods, quat, rank, ctx->cur_systab,
+                                                                ctx->cur_sysid, sb.ax, sb.mobr);
+        ++ctx->launches;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
 static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m, const int32_t* pairs,
-                               const double* dgeom, const double* q, const double* gamma_in, const double* quat,
-                               const int* rank)
+                               const double* dgeom, const double* q, const double* gamma_in, const int* rank)
 {
     int mp = (int)ctx->max_pairs, np = (int)ctx->max_rods;
     cudaStream_t st = ctx->stream;
-    if (n > 0) {
-        k_setup_rods<T><<<nblk(n, 256), 256, 0, st>>>(n, np, quat, rank, ctx->cur_systab, ctx->cur_sysid, sb.ax,
-                                                       sb.mobr);
-        ++ctx->launches;
-    }
     if (m <= 0) return cudaGetLastError();
     k_setup_fill<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->perm, pairs, rank, dgeom, q, gamma_in, ctx->rowQ,
                                                   ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0], sb.gg[1],
@@ -543,14 +549,14 @@ cudaError_t launch_solve_setup_check(aLENS_ctx* ctx, int n, int m, const int32_t
 
 // Owner-major constraint layout over rod ranks, the Q-side CSR, and the
 // typed solver buffers.  The pair list must have passed the check.
-cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* dgeom,
-                               const double* q, const double* gamma_in, const double* quat, int precision,
-                               const int* rank)
+// The solver's layout from the pair list alone (no assembled values): the
+// owner-major CSR (rowP, perm in ascending order per rod), the Q-side
+// counts and offsets (rowQ) and the rods' axes and drags in rank order.
+cudaError_t launch_solve_layout(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* quat,
+                                int precision, const int* rank)
 {
     cudaStream_t st = ctx->stream;
     cudaError_t e;
-    ctx->qe_pending = 0;
-    ctx->zero_start = gamma_in == nullptr;
     size_t bytes = sizeof(int) * ((size_t)n + 1);
     if ((e = cudaMemsetAsync(ctx->rod_count, 0, bytes, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ctx->cntQ, 0, bytes, st)) != cudaSuccess) return e;
@@ -568,9 +574,28 @@ cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pair
         k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowP, ctx->perm);
         ++ctx->launches;
     }
-    if (precision == ALENS_MIXED)
-        return setup_typed<float>(ctx, ctx->sb32, n, m, pairs, dgeom, q, gamma_in, quat, rank);
-    return setup_typed<double>(ctx, ctx->sb64, n, m, pairs, dgeom, q, gamma_in, quat, rank);
+    if (precision == ALENS_MIXED) return setup_rods_typed<float>(ctx, ctx->sb32, n, quat, rank);
+    return setup_rods_typed<double>(ctx, ctx->sb64, n, quat, rank);
+}
+
+// The records, q and the starting state from the assembled values, on the
+// layout of launch_solve_layout.
+cudaError_t launch_solve_fill(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* dgeom,
+                              const double* q, const double* gamma_in, int precision, const int* rank)
+{
+    ctx->qe_pending = 0;
+    ctx->zero_start = gamma_in == nullptr;
+    if (precision == ALENS_MIXED) return setup_typed<float>(ctx, ctx->sb32, n, m, pairs, dgeom, q, gamma_in, rank);
+    return setup_typed<double>(ctx, ctx->sb64, n, m, pairs, dgeom, q, gamma_in, rank);
+}
+
+cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* dgeom,
+                               const double* q, const double* gamma_in, const double* quat, int precision,
+                               const int* rank)
+{
+    cudaError_t e = launch_solve_layout(ctx, n, m, pairs, quat, precision, rank);
+    if (e != cudaSuccess) return e;
+    return launch_solve_fill(ctx, n, m, pairs, dgeom, q, gamma_in, precision, rank);
 }
 
 }  // namespace alens

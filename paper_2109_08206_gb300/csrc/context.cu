@@ -115,6 +115,9 @@ void free_all(aLENS_ctx* c)
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     free(c->batch_host);
     free(c->batch_off_host);
     if (c->hflags) cudaFreeHost(c->hflags);
@@ -266,7 +269,7 @@ aLENS_status batch_tables(aLENS_ctx* c, int ns, const aLENS_system* sys, const i
         if (dmalloc(&c->systab, sizeof(SysGeo) * ns) != cudaSuccess ||
             dmalloc(&c->sysoff, sizeof(long long) * (ns + 1)) != cudaSuccess ||
             dmalloc(&c->sys_order, sizeof(int) * sys_queue_ints(ns)) != cudaSuccess ||
-            dmalloc(&c->sys_iters, sizeof(int) * ns) != cudaSuccess ||
+            dmalloc(&c->sys_iters, 2 * sizeof(int) * ns) != cudaSuccess ||   // iterations, then blocks
             dmalloc(&c->sys_res, sizeof(double) * ns) != cudaSuccess) {
             cudaGetLastError();
             st = ALENS_ERR_NOMEM;
@@ -430,6 +433,9 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= cudaMallocHost((void**)&c->hflags, F_NFLAGS * sizeof(int)) == cudaSuccess;
     ok &= cudaMallocHost((void**)&c->hcount, C_NCOUNT * sizeof(unsigned long long)) == cudaSuccess;
     for (int k = 0; k < 8 && ok; ++k) ok &= cudaEventCreate(&c->ev[k]) == cudaSuccess;
+    ok &= cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
+    ok &= cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok &= cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -680,6 +686,33 @@ struct StepOpts {
     bool keep = false;
 };
 
+// The launch helpers enqueue on ctx->stream: while a StreamSwap lives, that
+// is stream s.
+struct StreamSwap {
+    aLENS_ctx* c;
+    cudaStream_t own;
+    StreamSwap(aLENS_ctx* c_, cudaStream_t s) : c(c_), own(c_->stream) { c->stream = s; }
+    ~StreamSwap() { c->stream = own; }
+};
+
+// The solver layout (ranks, owner-major CSR, Q-side offsets, the rods' axes
+// and drags) needs the pair list but none of the assembled values, so it
+// runs on the side stream while the assembly, bound by the FP64 pipe, runs
+// on the step's stream; the step's stream waits for ev_join before the
+// records are filled.  Same kernels and arguments as in sequence.
+static aLENS_status fork_layout(aLENS_ctx* c, int n, int m, const double* quat)
+{
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    {
+        StreamSwap on(c, c->side);
+        CK(launch_rank(c, n));
+        CK(launch_solve_layout(c, n, m, c->pairs, quat, c->p.precision, c->rank));
+    }
+    CK(cudaEventRecord(c->ev_join, c->side));
+    return ALENS_OK;
+}
+
 static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, const double* f_nc,
                               int32_t* pairs_out, double* gamma_out, double* vel_out, aLENS_info* info,
                               StepOpts opt = StepOpts(), int64_t* walls_out = nullptr)
@@ -701,6 +734,9 @@ static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, 
     }
     CK(launch_emit_pairs(c, (int)n, c->pairs));
     CK(cudaEventRecord(c->ev[1], c->stream));
+    // walls and springs append constraints after the assembly: then the layout follows it
+    const bool beside = !walls && c->sp_n == 0;
+    if (beside && (st = fork_layout(c, (int)n, (int)m, quat)) != ALENS_OK) return st;
     CK(launch_assemble(c, (int)n, (int)mu, c->pairs, c->phi, c->dgeom, c->q64));
     if (walls) CK(launch_emit_walls(c, (int)n, (int)mu));
     if (c->sp_n > 0) {
@@ -717,8 +753,13 @@ static aLENS_status step_impl(aLENS_ctx* c, int64_t n, double* x, double* quat, 
         CK(launch_warm(c, (int)m, (int)mu, (int)mw, c->gin_buf));
         gin = c->gin_buf;
     }
-    CK(launch_rank(c, (int)n));
-    CK(launch_solve_setup(c, (int)n, (int)m, c->pairs, c->dgeom, c->q64, gin, quat, c->p.precision, c->rank));
+    if (beside) {
+        CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    } else {
+        CK(launch_rank(c, (int)n));
+        CK(launch_solve_layout(c, (int)n, (int)m, c->pairs, quat, c->p.precision, c->rank));
+    }
+    CK(launch_solve_fill(c, (int)n, (int)m, c->pairs, c->dgeom, c->q64, gin, c->p.precision, c->rank));
     if ((st = run_solver(c, (int)n, (int)m, info, c->ev[2], c->ev[3])) != ALENS_OK) return st;
     c->cur_comp = nullptr;
     CK(launch_update(c, (int)n, (int)m, x, quat, c->p.precision, vel_out, c->rank));
@@ -760,9 +801,12 @@ static aLENS_status step_graph_body(aLENS_ctx* c, int64_t n, double* x, double* 
         CK(launch_check_capacity(c));
         CK(launch_emit_pairs(c, (int)n, c->pairs));
         CK(record_event(c, c->ev[1]));
+        st = fork_layout(c, (int)n, mcap, quat);
+    }
+    if (st == ALENS_OK) {
         CK(launch_assemble(c, (int)n, mcap, c->pairs, c->phi, c->dgeom, c->q64));
-        CK(launch_rank(c, (int)n));
-        CK(launch_solve_setup(c, (int)n, mcap, c->pairs, c->dgeom, c->q64, nullptr, quat, c->p.precision, c->rank));
+        CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        CK(launch_solve_fill(c, (int)n, mcap, c->pairs, c->dgeom, c->q64, nullptr, c->p.precision, c->rank));
         if (single) {
             CK(record_event(c, c->ev[2]));
             CK(launch_solve_graph1(c, (int)n, mcap, c->p.precision));
@@ -1185,6 +1229,19 @@ aLENS_status aLENS_batch_results(aLENS_ctx* c, int32_t n_systems, int32_t* iters
     if (iters) CK(cudaMemcpyAsync(iters, c->sys_iters, sizeof(int32_t) * n_systems, cudaMemcpyDeviceToHost, c->stream));
     if (residual)
         CK(cudaMemcpyAsync(residual, c->sys_res, sizeof(double) * n_systems, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ALENS_OK;
+}
+
+aLENS_status aLENS_batch_groups(aLENS_ctx* c, int32_t n_systems, int32_t* blocks)
+{
+    if (!c || !blocks || n_systems < 1 || n_systems != c->last_batch_n) return ALENS_ERR_INVALID;
+    if (n_systems == 1) {
+        blocks[0] = 0;
+        return ALENS_OK;
+    }
+    CK(cudaMemcpyAsync(blocks, c->sys_iters + c->max_systems, sizeof(int32_t) * n_systems, cudaMemcpyDeviceToHost,
+                       c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return ALENS_OK;
 }

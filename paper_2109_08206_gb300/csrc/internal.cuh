@@ -377,6 +377,8 @@ struct aLENS_ctx {
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
     cudaStream_t cap_stream; // the graph is recorded here (the legacy default stream cannot be captured)
+    cudaStream_t side;       // the solver layout's kernels, beside the assembly (non-blocking)
+    cudaEvent_t ev_fork, ev_join;  // side waits for ev_fork; the step's stream for ev_join
     int graph_launches;      // kernels in the graph
     int graph_state;         // 0 nothing, 1 the key below ran eagerly once, 2 a graph of it is instantiated,
                              // 3 the key stays eager (its solver reads back, or a recorded step redid)
@@ -407,7 +409,7 @@ struct aLENS_ctx {
     int* sys_order;          // [max_systems] queue order of the per-system solver, then the
                              // queue entries [2 (max_systems + kMaxPairs)], their count and
                              // the pairs' barrier counters [kMaxPairs] (sys_queue_ints ints)
-    int* sys_iters;          // [max_systems] iterations of each system's solve
+    int* sys_iters;          // [2][max_systems] iterations of each system's solve, then the blocks that solved it
     double* sys_res;         // [max_systems] final residual of each system
     int last_batch_n;        // systems of the last completed aLENS_step_batch (0: none)
     void* adj_ws;            // adjoint workspace (allocated by the first aLENS_step_adjoint)
@@ -459,6 +461,13 @@ cudaError_t launch_assemble(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, 
 // the P and Q sides; launch_solve_setup must follow only if no error flag was raised.
 cudaError_t launch_solve_setup_check(aLENS_ctx* ctx, int n, int m, const int32_t* pairs);
 // rank (nullable): solver position of each rod (identity when NULL).
+// launch_solve_setup = launch_solve_layout (from the pair list alone) then
+// launch_solve_fill (from the assembled values); a step may run the layout
+// beside the assembly.
+cudaError_t launch_solve_layout(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* quat,
+                                int precision, const int* rank);
+cudaError_t launch_solve_fill(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* dgeom,
+                              const double* q, const double* gamma_in, int precision, const int* rank);
 cudaError_t launch_solve_setup(aLENS_ctx* ctx, int n, int m, const int32_t* pairs, const double* dgeom,
                                const double* q, const double* gamma_in, const double* quat, int precision,
                                const int* rank);

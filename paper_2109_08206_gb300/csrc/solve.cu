@@ -1944,7 +1944,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024, 1)
 k_bbpgd_sys(SolveArgs<T> a, const long long* __restrict__ sysoff, const int* __restrict__ qent,
             const int* __restrict__ qn, unsigned* __restrict__ pair_bar, unsigned long long* __restrict__ queue,
-            int* __restrict__ sys_iters, double* __restrict__ sys_res)
+            int* __restrict__ sys_iters, int* __restrict__ sys_blocks, double* __restrict__ sys_res)
 {
     extern __shared__ __align__(16) unsigned char dyn[];   // rod order scratch (when a.sort_ns)
     __shared__ Shared<T> sh;
@@ -2011,6 +2011,7 @@ k_bbpgd_sys(SolveArgs<T> a, const long long* __restrict__ sysoff, const int* __r
         }
         if (grank == 0 && threadIdx.x == 0) {
             sys_iters[s] = st.iters;
+            sys_blocks[s] = gs;
             const double res = st.residual(a.hD);
             sys_res[s] = res;
             atomicMax(&a.flags[F_ITERS], st.iters);
@@ -2312,7 +2313,8 @@ static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int
     ++ctx->launches;
     ctx->last_solver = 4;
     return cudaLaunchKernelEx(&cfg, k_bbpgd_sys<T>, a, (const long long*)ctx->sysoff, (const int*)qent,
-                              (const int*)qn, pair_bar, ctx->dcount + C_QUEUE, ctx->sys_iters, ctx->sys_res);
+                              (const int*)qn, pair_bar, ctx->dcount + C_QUEUE, ctx->sys_iters,
+                              ctx->sys_iters + ctx->max_systems, ctx->sys_res);
 }
 
 cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision)

@@ -114,6 +114,82 @@ def test_batch_matches_oracle_per_system(precision, tol, xbar, ubar):
     assert sum(p.shape[0] for p in per) == info.n_pairs > 0
 
 
+def test_prepared_tables_equal_lists():
+    """A BatchSpec built once gives the same step as the systems and offsets
+    passed as lists, bit for bit."""
+    systems = small_batch()
+    off, x, quat, fnc, spec = W.batch_arrays(systems)
+    prepared = A.BatchSpec(spec, off)
+    outs = []
+    with batch_ctx(systems, A.MIXED, 1e-6) as ctx:
+        for tables, offsets in ((spec, off), (prepared, None), (prepared, None)):
+            xd, qd = dev(x), dev(quat)
+            info = ctx.step_batch(tables, offsets, xd, qd, dev(fnc))
+            assert info.status == 0
+            outs.append((host(xd), host(qd), info.iters, info.n_pairs))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1]) and o[2:] == outs[0][2:]
+    with pytest.raises(ValueError):
+        A.BatchSpec(spec, off[:-1])
+
+
+def uneven_batch():
+    """Three systems of the ensemble's kind (nematic domains, thermal forces):
+    two of 2,000 and 1,500 rods and one of 300."""
+    out = []
+    for seed, n in ((81, 2000), (82, 1500), (83, 300)):
+        box = W.box_for_fraction(n, 1.0, 10.0, 0.1)
+        out.append(W.random_system(seed, n, box, length=10.0, nematic_spread=0.3, forces="thermal", tol=1e-8,
+                                   name=f"uneven_{n}"))
+    return out
+
+
+@pytest.mark.parametrize("precision,tol,xbar,ubar", [(A.FP64, 1e-10, 1e-6, 1e-6), (A.MIXED, 1e-6, 2e-5, 1e-3)])
+def test_paired_systems_match_oracle(precision, tol, xbar, ubar):
+    """One-block clusters: the two larger systems hold more than 4096
+    constraints each and far more than half of a cluster's mean share, so
+    two clusters solve each of them together (aLENS_batch_groups: 2 blocks),
+    and the smallest is solved by one.  Every system matches the oracle as
+    in the other batches, and a second step from the same state repeats the
+    first bit for bit (the pairing depends only on the systems and the
+    launch)."""
+    systems = uneven_batch()
+    off, x, quat, fnc, spec = W.batch_arrays(systems)
+    n = int(off[-1])
+    outs = []
+    with batch_ctx(systems, precision, tol) as ctx:
+        ctx.set_batch_launch(1024, 1)
+        pr = torch.empty((ctx.max_pairs, 3), dtype=torch.int32, device="cuda")
+        gam = torch.empty(ctx.max_pairs, dtype=torch.float64, device="cuda")
+        vel = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+        for rep in range(2):
+            xd, qd = dev(x), dev(quat)
+            info = ctx.step_batch(spec, off, xd, qd, dev(fnc), pairs_out=pr, gamma_out=gam, vel_out=vel)
+            assert info.status == 0 and info.residual <= tol
+            m = info.n_pairs
+            outs.append((host(xd), host(qd), host(pr)[:m], host(gam)[:m], host(vel)))
+            groups = ctx.batch_groups(len(systems))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    xg, qg, pairs, gamg, velg = outs[0]
+    per = split_pairs(pairs, off)
+    ms = [p.shape[0] for p in per]
+    assert ms[0] >= 4096 and ms[1] >= 4096 and ms[2] < 4096, ms
+    assert list(groups) == [2, 2, 1], (list(groups), ms)
+    for k, s in enumerate(systems):
+        lo, hi = off[k], off[k + 1]
+        pb = O.problem_of(s)
+        ref = O.step(s.x, s.quat, s.f_nc, pb, tol=1e-12)
+        compare_pairs(per[k], ref["pairs"], s)
+        assert np.abs(periodic_diff(xg[lo:hi], ref["x"], s.box)).max() <= xbar * s.diameter, s.name
+        assert np.abs(qg[lo:hi] - ref["quat"]).max() <= xbar, s.name
+        assert np.linalg.norm(velg[lo:hi] - ref["U"]) <= ubar * np.linalg.norm(ref["U"]), s.name
+        sel = (pairs[:, 0] >= lo) & (pairs[:, 0] < hi)
+        asm = O.assemble(s.x, s.quat, s.f_nc, pb, per[k])
+        _, r = O.gradient(s.quat, pb, per[k], asm["dgeom"], asm["q"], gamg[sel])
+        assert r <= tol * 1.05 + (1e-9 if precision == A.FP64 else 2e-7), s.name
+
+
 @pytest.mark.parametrize("precision", [A.FP64, A.MIXED])
 def test_batch_of_one_equals_single_step(precision):
     # one system through the batch tables (per-system geometry, per-rod drags;
