@@ -382,6 +382,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, c->device);
     c->clock_khz = clk > 0 ? clk : 2.1e6;
     c->coop_ok = prop.cooperativeLaunch;
+    c->batch_coop = -1;
     c->max_keys = 1 << (3 * geo.bits);
     c->max_blocks = c->num_sms * 8;
     size_t np = (size_t)max_rods, mp = (size_t)max_pairs;

@@ -392,6 +392,7 @@ struct aLENS_ctx {
     } gkey;
     int tables_epoch;        // bumped whenever the batch tables change
     int coop_ok;
+    int batch_coop;          // cooperative launch with clusters: -1 untried, 0 refused, 1 works
     int launches;            // kernels launched since the entry point began
     // batches (aLENS_step_batch): per-system table and per-rod system id;
     // NULL outside a batched step

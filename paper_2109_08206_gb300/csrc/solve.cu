@@ -2039,19 +2039,19 @@ __global__ void k_sys_order(int ns, const long long* __restrict__ sysoff, const 
 
 // The queue of the per-system solver: the first K systems of the order are
 // paired (listed twice), the others listed once.  A system is paired if it
-// is among the nclusters / 4 largest, holds at least 4096 constraints per
+// is among the max_pairs largest, holds at least 4096 constraints per
 // block of one cluster (below that the pair's grid-style barriers cost more
 // than the extra blocks save) and more than half of one cluster's mean
 // share of the batch's constraints.  One block; also zeroes the pairs'
 // barrier counters.
 __global__ void k_sys_queue(int ns, const long long* __restrict__ sysoff, const int* __restrict__ rowP,
-                            const int* __restrict__ order, int nclusters, int cs, int* __restrict__ qent,
-                            int* __restrict__ qn, unsigned* __restrict__ pair_bar)
+                            const int* __restrict__ order, int nclusters, int cs, int max_pairs,
+                            int* __restrict__ qent, int* __restrict__ qn, unsigned* __restrict__ pair_bar)
 {
     __shared__ int npair;
     if (threadIdx.x == 0) {
         const long long total = (long long)rowP[sysoff[ns]] - rowP[sysoff[0]];
-        const int cap = nclusters / 4 < kMaxPairs ? nclusters / 4 : kMaxPairs;
+        const int cap = max_pairs;
         int k = 0;
         while (k < cap && k < ns) {
             const int sy = order[k];
@@ -2294,27 +2294,49 @@ static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int
     cfg.stream = ctx->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int nclusters = 0;
-    if ((e = cudaOccupancyMaxActiveClusters(&nclusters, k_bbpgd_sys<T>, &cfg)) != cudaSuccess) return e;
-    if (nclusters < 1) return cudaErrorInvalidConfiguration;
-    // a cluster per queue entry at most (every system, and the pairs' second entries)
-    const int max_pairs = nclusters / 4 < kMaxPairs ? nclusters / 4 : kMaxPairs;
-    if (nclusters > ns + max_pairs) nclusters = ns + max_pairs;
+    int max_active = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(&max_active, k_bbpgd_sys<T>, &cfg)) != cudaSuccess) return e;
+    if (max_active < 1) return cudaErrorInvalidConfiguration;
     int* qent = ctx->sys_order + ns;
     int* qn = qent + 2 * ((size_t)ns + kMaxPairs);
     unsigned* pair_bar = reinterpret_cast<unsigned*>(qn + 1);
     k_sys_order<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(ns, ctx->sysoff, ctx->rowP, ctx->sys_order);
-    k_sys_queue<<<1, 256, 0, ctx->stream>>>(ns, ctx->sysoff, ctx->rowP, ctx->sys_order, nclusters, ctx->batch_cluster,
-                                            qent, qn, pair_bar);
-    ctx->launches += 2;
-    if ((e = cudaMemsetAsync(ctx->dcount + C_QUEUE, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
-        return e;
-    cfg.gridDim = dim3((unsigned)(nclusters * ctx->batch_cluster));
+    ++ctx->launches;
+    // Pairs wait for each other, so they need every cluster resident at
+    // once: a cooperative launch (tried by the first batched solve of the
+    // context; without it the solver runs without pairs).
+    cudaLaunchAttribute attr2[2] = {attr[0], {}};
+    attr2[1].id = cudaLaunchAttributeCooperative;
+    attr2[1].val.cooperative = 1;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int cap = max_active / 4 < kMaxPairs ? max_active / 4 : kMaxPairs;
+        const int max_pairs = ctx->batch_coop != 0 ? cap : 0;
+        // a cluster per queue entry at most (every system, and the pairs' second entries)
+        const int nclusters = max_active < ns + max_pairs ? max_active : ns + max_pairs;
+        k_sys_queue<<<1, 256, 0, ctx->stream>>>(ns, ctx->sysoff, ctx->rowP, ctx->sys_order, nclusters,
+                                                ctx->batch_cluster, max_pairs, qent, qn, pair_bar);
+        ++ctx->launches;
+        if ((e = cudaMemsetAsync(ctx->dcount + C_QUEUE, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess)
+            return e;
+        cfg.gridDim = dim3((unsigned)(nclusters * ctx->batch_cluster));
+        cfg.attrs = max_pairs > 0 ? attr2 : attr;
+        cfg.numAttrs = max_pairs > 0 ? 2 : 1;
+        e = cudaLaunchKernelEx(&cfg, k_bbpgd_sys<T>, a, (const long long*)ctx->sysoff, (const int*)qent,
+                               (const int*)qn, pair_bar, ctx->dcount + C_QUEUE, ctx->sys_iters,
+                               ctx->sys_iters + ctx->max_systems, ctx->sys_res);
+        if (e == cudaSuccess) {
+            if (max_pairs > 0) ctx->batch_coop = 1;
+            break;
+        }
+        // a refused cooperative cluster launch enqueued nothing: queue again without pairs
+        if (max_pairs == 0 || ctx->batch_coop == 1) return e;
+        cudaGetLastError();
+        ctx->batch_coop = 0;
+    }
+    if (e != cudaSuccess) return e;
     ++ctx->launches;
     ctx->last_solver = 4;
-    return cudaLaunchKernelEx(&cfg, k_bbpgd_sys<T>, a, (const long long*)ctx->sysoff, (const int*)qent,
-                              (const int*)qn, pair_bar, ctx->dcount + C_QUEUE, ctx->sys_iters,
-                              ctx->sys_iters + ctx->max_systems, ctx->sys_res);
+    return cudaSuccess;
 }
 
 cudaError_t launch_solve(aLENS_ctx* ctx, int n, int m, int precision)
