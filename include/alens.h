@@ -420,11 +420,15 @@ ALENS_API aLENS_status aLENS_set_scaling(aLENS_ctx* ctx, double beta);
 /* Test hook: mode 1 makes one thread block of the next solver launch (the
  * BBPGD of a step or solve, or the CG of aLENS_step_adjoint) leave before
  * its first grid-wide arrival, so that the other blocks' bounded waits run
- * out and the call returns ALENS_ERR_TIMEOUT.  mode 2 makes the next
+ * out and the call returns ALENS_ERR_TIMEOUT; in the batched solver, the
+ * second cluster of every pair (aLENS_batch_groups) skips its system, so
+ * that the first cluster's bounded waits run out.  mode 2 makes the next
  * recorded single-system step (aLENS_set_step_graph) find its shares too
  * big for its launch, so that the call falls back to a step without a
- * graph.  The hook clears itself after one launch or recording.  mode 0
- * disables it. */
+ * graph.  These clear themselves after one launch or recording; mode 0
+ * disables them.  mode 3 makes the context's batched solver run as on a
+ * device that refuses a cooperative launch with clusters: every system is
+ * solved by one cluster from then on (drops a recorded batched step). */
 ALENS_API aLENS_status aLENS_inject_fault(aLENS_ctx* ctx, int32_t mode);
 
 /* Launch shape of the solver kernel: threads per block (multiple of 32,

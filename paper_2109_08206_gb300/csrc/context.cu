@@ -521,9 +521,16 @@ aLENS_status aLENS_set_scaling(aLENS_ctx* c, double beta)
     return ALENS_OK;
 }
 
+static void drop_graph(aLENS_ctx* c);
+
 aLENS_status aLENS_inject_fault(aLENS_ctx* c, int32_t mode)
 {
-    if (!c || mode < 0 || mode > 2) return ALENS_ERR_INVALID;
+    if (!c || mode < 0 || mode > 3) return ALENS_ERR_INVALID;
+    if (mode == 3) {   // as after a refused cooperative cluster launch: no pairs from now on
+        c->batch_coop = 0;
+        drop_graph(c);
+        return ALENS_OK;
+    }
     c->fault_mode = mode;
     return ALENS_OK;
 }

@@ -1964,6 +1964,10 @@ k_bbpgd_sys(SolveArgs<T> a, const long long* __restrict__ sysoff, const int* __r
         cl.sync();   // every block has the entry before block 0 takes the next one
         if (s < 0) break;
         const int member = pc >= 0 ? (pc & 1) : 0;
+        if (a.fault == 1 && member == 1) {   // test hook: a pair's second cluster never arrives
+            __syncthreads();
+            continue;
+        }
         const int gs = pc >= 0 ? 2 * cs : cs, grank = member * cs + crank;   // the group's blocks, this one's rank
         const int R0 = (int)sysoff[s], R1 = (int)sysoff[s + 1];
         if (threadIdx.x < 64) {   // warp w finds end w of this block's share
@@ -2254,6 +2258,7 @@ template <typename T>
 static cudaError_t solve_batch_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int m)
 {
     SolveArgs<T> a = make_args(ctx, sb, n, m);
+    a.fault = ctx->fault_mode == 1 ? 1 : 0;
     ctx->fault_mode = 0;
     const int ns = ctx->batch_n;
     cudaError_t e;

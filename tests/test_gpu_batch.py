@@ -190,6 +190,52 @@ def test_paired_systems_match_oracle(precision, tol, xbar, ubar):
         assert r <= tol * 1.05 + (1e-9 if precision == A.FP64 else 2e-7), s.name
 
 
+def test_pairs_off_without_cooperative_cluster_launch():
+    """The test hook that makes the context run as on a device refusing a
+    cooperative launch with clusters: the same uneven batch is solved with
+    one cluster per system (aLENS_batch_groups: 1 block each), still to the
+    oracle's answer."""
+    systems = uneven_batch()
+    off, x, quat, fnc, spec = W.batch_arrays(systems)
+    n = int(off[-1])
+    tol = 1e-6
+    with batch_ctx(systems, A.MIXED, tol) as ctx:
+        ctx.set_batch_launch(1024, 1)
+        ctx.inject_fault(3)
+        vel = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+        xd, qd = dev(x), dev(quat)
+        info = ctx.step_batch(spec, off, xd, qd, dev(fnc), vel_out=vel)
+        assert info.status == 0 and info.residual <= tol
+        assert list(ctx.batch_groups(len(systems))) == [1, 1, 1]
+        xg, velg = host(xd), host(vel)
+    for k, s in enumerate(systems):
+        lo, hi = off[k], off[k + 1]
+        ref = O.step(s.x, s.quat, s.f_nc, O.problem_of(s), tol=1e-12)
+        assert np.abs(periodic_diff(xg[lo:hi], ref["x"], s.box)).max() <= 2e-5 * s.diameter, s.name
+        assert np.linalg.norm(velg[lo:hi] - ref["U"]) <= 1e-3 * np.linalg.norm(ref["U"]), s.name
+
+
+def test_pair_wait_times_out_and_context_recovers():
+    """The test hook that makes the second cluster of every pair skip its
+    system: the first cluster's bounded waits run out (wait limit 0.2 s), the
+    call returns TIMEOUT and moves no rod, and the next call on the same
+    context pairs and solves as before."""
+    systems = uneven_batch()
+    off, x, quat, fnc, spec = W.batch_arrays(systems)
+    with batch_ctx(systems, A.MIXED, 1e-6) as ctx:
+        ctx.set_batch_launch(1024, 1)
+        ctx.set_wait_limit(0.2)
+        ctx.inject_fault(1)
+        xd, qd = dev(x), dev(quat)
+        with pytest.raises(A.AlensError) as e:
+            ctx.step_batch(spec, off, xd, qd, dev(fnc))
+        assert e.value.status == 4
+        assert np.array_equal(host(xd), x) and np.array_equal(host(qd), quat)
+        info = ctx.step_batch(spec, off, xd, qd, dev(fnc))
+        assert info.status == 0
+        assert list(ctx.batch_groups(len(systems))) == [2, 2, 1]
+
+
 @pytest.mark.parametrize("precision", [A.FP64, A.MIXED])
 def test_batch_of_one_equals_single_step(precision):
     # one system through the batch tables (per-system geometry, per-rod drags;
