@@ -383,6 +383,9 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     c->clock_khz = clk > 0 ? clk : 2.1e6;
     c->coop_ok = prop.cooperativeLaunch;
     c->batch_coop = -1;
+    cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->device);
+    cudaDeviceGetAttribute(&c->l2_window_max, cudaDevAttrMaxAccessPolicyWindowSize, c->device);
+    cudaDeviceGetAttribute(&c->l2_persist_max, cudaDevAttrMaxPersistingL2CacheSize, c->device);
     c->max_keys = 1 << (3 * geo.bits);
     c->max_blocks = c->num_sms * 8;
     size_t np = (size_t)max_rods, mp = (size_t)max_pairs;
@@ -487,6 +490,13 @@ void aLENS_destroy(aLENS_ctx* c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->persist_set) {   // the persisting L2 set-aside back to what it was, unless changed since
+        size_t cur = 0;
+        if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess && cur == c->persist_set)
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, c->persist_prev);
+        cudaCtxResetPersistingL2Cache();
+        cudaGetLastError();
+    }
     free_all(c);
     free(c);
 }

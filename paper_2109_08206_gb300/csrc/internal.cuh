@@ -363,6 +363,11 @@ struct aLENS_ctx {
     int solve_threads, solve_bps;
     int solve_barriers;      // 1: one-barrier solver where its share fits (default); 2: the two-barrier kernels
     int smem_optin;          // the device's opt-in shared memory per block (bytes)
+    int l2_bytes;            // the device's L2 size, its largest access-policy window and
+    int l2_window_max;       // its largest persisting set-aside (bytes)
+    int l2_persist_max;
+    size_t persist_prev;     // the context's persisting set-aside before this context raised it
+    size_t persist_set;      // the set-aside this context set (0: untouched)
     int attr1_set[2];        // the one-barrier kernel's dynamic shared-memory limit is set (float, double)
     int occ1_key[2];         // launch shape (threads * 64 + blocks per SM) whose occupancy was checked ...
     int occ1_ok[2];          // ... and whether that many blocks per SM fit at the full budget
