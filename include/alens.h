@@ -336,6 +336,17 @@ ALENS_API aLENS_status aLENS_set_batch_graph(aLENS_ctx* ctx, int32_t enable);
  * enable = 0 releases the graph.  ALENS_ERR_INVALID for other values. */
 ALENS_API aLENS_status aLENS_set_step_graph(aLENS_ctx* ctx, int32_t enable);
 
+/* L2 residency of the solver's constraint states (enable = 1, the
+ * default).  Where the two-barrier solver reads its data from global memory
+ * and those data exceed the device's L2 (about 136 bytes per constraint),
+ * its launch carries an access-policy window that marks the two state
+ * buffers persisting in L2 while the records stream, and the context raises
+ * its persisting L2 set-aside to hold the states, as far as the device
+ * allows; aLENS_destroy puts the set-aside back.  Addresses only: every
+ * result is the same with enable = 0.  A launch being recorded into a CUDA
+ * graph takes no window.  INVALID for other values. */
+ALENS_API aLENS_status aLENS_set_l2_window(aLENS_ctx* ctx, int32_t enable);
+
 /* Name of the CUDA runtime error behind the calling thread's last
  * ALENS_ERR_CUDA from a context entry point ("cudaSuccess" if none);
  * a static string. */

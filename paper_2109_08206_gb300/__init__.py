@@ -116,6 +116,7 @@ def lib():
             "aLENS_set_solver_schedule": (i32, [vp, i32]),
             "aLENS_set_batch_graph": (i32, [vp, i32]),
             "aLENS_set_step_graph": (i32, [vp, i32]),
+            "aLENS_set_l2_window": (i32, [vp, i32]),
             "aLENS_last_cuda_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -130,7 +131,7 @@ def exported_symbols():
     """Names declared by include/alens.h (parsed from the header)."""
     import re
     text = (_PKG.parent / "include" / "alens.h").read_text()
-    return sorted(set(re.findall(r"\b(aLENS_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(aLENS_[a-z0-9_]+)\s*\(", text)))
 
 
 def _status_string(s: int) -> str:
@@ -361,6 +362,12 @@ class Context:
         st = self._lib.aLENS_set_step_graph(self._h, int(bool(enable)))
         if st != 0:
             raise AlensError(st, "aLENS_set_step_graph")
+
+    def set_l2_window(self, enable: bool = True):
+        """L2 residency of the global-memory solver's states (see include/alens.h)."""
+        st = self._lib.aLENS_set_l2_window(self._h, int(bool(enable)))
+        if st != 0:
+            raise AlensError(st, "aLENS_set_l2_window")
 
     def set_batch_launch(self, threads: int, cluster_blocks: int):
         st = self._lib.aLENS_set_batch_launch(self._h, int(threads), int(cluster_blocks))

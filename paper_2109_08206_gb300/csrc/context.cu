@@ -1307,4 +1307,11 @@ aLENS_status aLENS_set_step_graph(aLENS_ctx* c, int32_t enable)
     return ALENS_OK;
 }
 
+aLENS_status aLENS_set_l2_window(aLENS_ctx* c, int32_t enable)
+{
+    if (!c || (enable != 0 && enable != 1)) return ALENS_ERR_INVALID;
+    c->l2_window_off = !enable;
+    return ALENS_OK;
+}
+
 }  // extern "C"

@@ -368,6 +368,7 @@ struct aLENS_ctx {
     int l2_persist_max;
     size_t persist_prev;     // the context's persisting set-aside before this context raised it
     size_t persist_set;      // the set-aside this context set (0: untouched)
+    int l2_window_off;       // aLENS_set_l2_window(ctx, 0)
     int attr1_set[2];        // the one-barrier kernel's dynamic shared-memory limit is set (float, double)
     int occ1_key[2];         // launch shape (threads * 64 + blocks per SM) whose occupancy was checked ...
     int occ1_ok[2];          // ... and whether that many blocks per SM fit at the full budget

@@ -2169,7 +2169,8 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
 template <typename T>
 static bool state_window(aLENS_ctx* ctx, const T* gg0, const T* gg1, int m, cudaAccessPolicyWindow& w)
 {
-    if (ctx->l2_window_max <= 0 || ctx->l2_persist_max <= 0 || (long long)m * 136 <= (long long)ctx->l2_bytes)
+    if (ctx->l2_window_off || ctx->l2_window_max <= 0 || ctx->l2_persist_max <= 0 ||
+        (long long)m * 136 <= (long long)ctx->l2_bytes)
         return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
