@@ -457,7 +457,8 @@ k_search(int n, int np, Geo g0, const SysGeo* __restrict__ systab, const int* __
 // kDropped and leaves its rod's count and the total.  Chunks go to blocks
 // round robin; the list holds a whole chunk, so any flagged fraction fits.
 constexpr int kDecideThreads = 256;
-constexpr int kDecideChunk = 8 * kDecideThreads;
+constexpr int kDecideChunk = 4 * kDecideThreads;
+constexpr int kDecideBlocksPerSM = 4;   // about 6e5 candidates decided in one round of chunks
 
 __global__ void __launch_bounds__(kDecideThreads)
 k_decide(int np, Geo g0, const SysGeo* __restrict__ systab, const int* __restrict__ sysid,
@@ -573,7 +574,7 @@ cudaError_t launch_search(aLENS_ctx* ctx, int n)
         ctx->cellkey, ctx->xw, ctx->axis, ctx->cell_start, ctx->rod_ncand, ctx->rod_count, ctx->rod_tmpstart, ctx->cand,
         ctx->cand_cap, ctx->dcount, ctx->dflags);
     ++ctx->launches;
-    k_decide<<<ctx->num_sms, kDecideThreads, 0, ctx->stream>>>((int)ctx->max_rods, ctx->geo, ctx->cur_systab,
+    k_decide<<<ctx->num_sms * kDecideBlocksPerSM, kDecideThreads, 0, ctx->stream>>>((int)ctx->max_rods, ctx->geo, ctx->cur_systab,
                                                         ctx->cur_sysid, ctx->dcount, ctx->cand, ctx->cand_cap,
                                                         ctx->xw, ctx->axis, ctx->rod_count, ctx->dcount);
     ++ctx->launches;

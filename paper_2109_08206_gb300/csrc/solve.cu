@@ -1901,25 +1901,32 @@ __global__ void __launch_bounds__(1024, 1) k_bbpgd1(SolveArgs<T> a)
     }
 }
 
-// One warp per block b: the one-barrier kernel's shared-memory share
-// (ghosts counted from the block's other-side entries); a share whose slot
-// or rod count exceeds the 15-bit local indices does not fit.
-__global__ void k_stage_need1(int nb, int esize, const int* __restrict__ bstart, const int* __restrict__ rowP,
-                              const int* __restrict__ rowQ, const int* __restrict__ qlist,
-                              unsigned long long* __restrict__ need)
+// One thread block per solver block b (kNeedThreads threads): the
+// one-barrier kernel's shared-memory share (ghosts counted from the block's
+// other-side entries); a share whose slot or rod count exceeds the 15-bit
+// local indices does not fit.
+constexpr int kNeedThreads = 256;
+__global__ void __launch_bounds__(kNeedThreads)
+k_stage_need1(int nb, int esize, const int* __restrict__ bstart, const int* __restrict__ rowP,
+              const int* __restrict__ rowQ, const int* __restrict__ qlist, unsigned long long* __restrict__ need)
 {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (b >= nb) return;   // uniform per warp
+    __shared__ int wsum[kNeedThreads / 32];
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (b >= nb) return;   // uniform per block
     const int r0 = bstart[b], r1 = bstart[b + 1];
     const int c0 = rowP[r0], c1 = rowP[r1], q0 = rowQ[r0], q1 = rowQ[r1];
     int ng = 0;
-    for (int k = q0 + lane; k < q1; k += 32) {
+    for (int k = q0 + (int)threadIdx.x; k < q1; k += kNeedThreads) {
         const int c = qlist[k];
         ng += c < c0 || c >= c1;
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) ng += __shfl_down_sync(0xffffffffu, ng, s);
-    if (lane == 0) {
+    if (lane == 0) wsum[warp] = ng;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ng = 0;
+        for (int w = 0; w < kNeedThreads / 32; ++w) ng += wsum[w];
         const size_t nt = (size_t)(c1 - c0) + ng, nr = r1 - r0;
         unsigned long long bytes = staged1_bytes(esize, nt, ng, nr, q1 - q0, nb);
         if (nt > (size_t)kMaxSlots || nr > (size_t)kMaxSlots) bytes = ~0ull;
@@ -2233,9 +2240,9 @@ static cudaError_t solve_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
                                                                   ctx->dcount + C_MAXRODS);
     ++ctx->launches;
     if (ctx->solve_barriers == 1) {
-        k_stage_need1<<<((int)blocks * 32 + 255) / 256, 256, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart,
-                                                                            ctx->rowP, ctx->rowQ, ctx->qlist,
-                                                                            ctx->dcount + C_SMEM1);
+        k_stage_need1<<<(int)blocks, kNeedThreads, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart,
+                                                                      ctx->rowP, ctx->rowQ, ctx->qlist,
+                                                                      ctx->dcount + C_SMEM1);
         ++ctx->launches;
     }
     // one readback of the counters C_SMEM .. C_SMEM1 (into the pinned host status
@@ -2474,9 +2481,9 @@ static cudaError_t solve_graph1_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, in
     k_partition<<<(nbw * 32 + 255) / 256, 256, 0, ctx->stream>>>(n, m, (int)blocks, ctx->rowP, ctx->rowQ, ctx->bstart);
     ++ctx->launches;
     if ((e = cudaMemsetAsync(ctx->dcount + C_SMEM1, 0, sizeof(unsigned long long), ctx->stream)) != cudaSuccess) return e;
-    k_stage_need1<<<((int)blocks * 32 + 255) / 256, 256, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart,
-                                                                        ctx->rowP, ctx->rowQ, ctx->qlist,
-                                                                        ctx->dcount + C_SMEM1);
+    k_stage_need1<<<(int)blocks, kNeedThreads, 0, ctx->stream>>>((int)blocks, (int)sizeof(T), ctx->bstart,
+                                                                  ctx->rowP, ctx->rowQ, ctx->qlist,
+                                                                  ctx->dcount + C_SMEM1);
     ++ctx->launches;
     if ((e = cudaMemsetAsync(ctx->bar, 0, 4 * sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
     void* args1[] = {&a};
