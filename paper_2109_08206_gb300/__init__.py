@@ -14,7 +14,7 @@ from __future__ import annotations
 import ctypes as C
 from pathlib import Path
 
-__all__ = ["build", "lib", "Params", "Info", "System", "Context", "AlensError", "FP64", "MIXED", "STATUS"]
+__all__ = ["build", "lib", "Params", "Info", "System", "Context", "BatchSpec", "AlensError", "FP64", "MIXED", "STATUS"]
 
 _PKG = Path(__file__).resolve().parent
 _LIB_PATH = _PKG / "_build" / "libalens.so"
