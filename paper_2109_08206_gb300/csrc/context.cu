@@ -491,10 +491,14 @@ void aLENS_destroy(aLENS_ctx* c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     if (c->persist_set) {   // the persisting L2 set-aside back to what it was, unless changed since
+        int dev = -1;
+        const bool other = cudaGetDevice(&dev) == cudaSuccess && dev != c->device;
+        if (other) cudaSetDevice(c->device);   // the limit belongs to the context's device
         size_t cur = 0;
         if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess && cur == c->persist_set)
             cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, c->persist_prev);
         cudaCtxResetPersistingL2Cache();
+        if (other) cudaSetDevice(dev);
         cudaGetLastError();
     }
     free_all(c);
