@@ -258,7 +258,8 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
                              T* __restrict__ gg0, T* __restrict__ gg1, T* __restrict__ rec_lo, T* __restrict__ q_lo,
                              const double* __restrict__ comp64, T* __restrict__ compT, int np, const T* __restrict__ ax,
                              const T* __restrict__ mobr, Mob mob0, double beta, double* __restrict__ scale64,
-                             T* __restrict__ isc, const unsigned long long* __restrict__ mdev)
+                             T* __restrict__ isc, T* __restrict__ lop, T* __restrict__ loq,
+                             const unsigned long long* __restrict__ mdev)
 {
     int cc = blockIdx.x * blockDim.x + threadIdx.x;
     if (cc >= count_of(m, mdev)) return;
@@ -304,12 +305,26 @@ __global__ void k_setup_fill(int m, int mp, const int* __restrict__ perm, const 
     // sig is a float value: for float, 1/sig in float is (T)(1.0 / sig)
     // (double rounding is innocuous for a quotient at 53 >= 2 * 24 + 2 bits)
     isc[cc] = sizeof(T) == 4 ? (T)__fdiv_rn(1.0f, (float)sig) : (T)(1.0 / sig);
+    T lo[9];
 #pragma unroll
     for (int u = 0; u < 9; ++u) {
         const double rs = r[u] * sig;
         const T hi = (T)rs;
         rec[u * (size_t)mp + cc] = hi;
-        if (rec_lo) rec_lo[u * (size_t)mp + cc] = (T)(rs - (double)hi);   // float32: the rounding error
+        lo[u] = sizeof(T) == 4 ? (T)(rs - (double)hi) : T(0);   // float32: the rounding error
+        if (rec_lo) rec_lo[u * (size_t)mp + cc] = lo[u];
+    }
+    if (lop) {   // the same low parts as one row per side (the one-barrier reference passes gather them)
+        T* p = lop + 8 * (size_t)cc;
+        T* q = loq + 8 * (size_t)cc;
+#pragma unroll
+        for (int u = 0; u < 6; ++u) p[u] = lo[u];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            q[u] = lo[u];
+            q[3 + u] = lo[6 + u];
+        }
+        p[6] = p[7] = q[6] = q[7] = T(0);
     }
     const double qs = q64[c] * sig;
     const T qh = (T)qs;
@@ -508,7 +523,7 @@ static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
                                                   ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0], sb.gg[1],
                                                   sb.rec_lo, sb.q_lo, ctx->cur_comp, sb.comp, np, sb.ax,
                                                   ctx->cur_systab ? sb.mobr : (const T*)nullptr, ctx->mob, ctx->scale_beta,
-                                                  ctx->scale64, sb.isc, ctx->mdev);
+                                                  ctx->scale64, sb.isc, sb.lop, sb.loq, ctx->mdev);
     ++ctx->launches;
     k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
     ++ctx->launches;

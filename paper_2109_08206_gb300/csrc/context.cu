@@ -426,7 +426,7 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
     ok &= dmalloc(&c->scale64, mp * sizeof(double)) == cudaSuccess;
     // solver buffers, sized for float64; the float32 views alias the same memory
     // every slice starts on a 64-byte boundary (vector loads): 8 elements of slack each
-    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 18 * np + mp + 4 * np + mp + mp + 8 * 14;
+    size_t solve_elems = 9 * mp + 8 * mp + mp + 3 * np + 8 * mp + 18 * np + mp + 4 * np + mp + mp + 8 * 14 + 8 * mp;
     ok &= dmalloc((char**)&c->solve_ws, solve_elems * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->partials, ((size_t)c->max_blocks + 4) * 8 * sizeof(double)) == cudaSuccess;
     ok &= dmalloc(&c->bstart, ((size_t)c->max_blocks + 1) * sizeof(int)) == cudaSuccess;
@@ -460,6 +460,8 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         s.comp = carve64(mp);
         s.isc = carve64(mp);
         s.pe = nullptr;   // the float64 rod phase reads rec (its arithmetic bounds it)
+        s.lop = nullptr;
+        s.loq = nullptr;
         float* fb = (float*)c->solve_ws;
         size_t f = 0;
         auto carve32 = [&](size_t cnt) { float* r = fb + f; f = (f + cnt + 7) & ~(size_t)7; return r; };
@@ -472,9 +474,11 @@ aLENS_status aLENS_create(const aLENS_params* params, int64_t max_rods, int64_t 
         t.comp = carve32(mp);
         t.isc = carve32(mp);
         t.pe = carve32(8 * mp);
-        // the float32 views use at most half of the workspace: room for the
-        // owner-side records and the low parts (55 mp + 25 np of 58 mp + 50 np)
+        // the float32 views use at most 71 mp + 25 np of the workspace's
+        // 74 mp + 50 np floats: room for the owner-side records, the low
+        // parts and their rows
         t.rec_lo = carve32(9 * mp); t.qe_lo = carve32(8 * mp); t.q_lo = carve32(mp);
+        t.lop = carve32(8 * mp); t.loq = carve32(8 * mp);
     }
     if (cudaMemsetAsync(c->cell_cursor, 0, ((size_t)c->max_keys + 1) * sizeof(int), c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {

@@ -292,6 +292,8 @@ struct SolveBufs {           // typed views into the solver workspace
     T* rec_lo;               // [9][mp]
     T* qe_lo;                // [mp][8]
     T* q_lo;                 // [mp]
+    T* lop;                  // [mp][8] rec_lo of the owner side (e, y_P x e, 2 pad) as one row
+    T* loq;                  // [mp][8] rec_lo of the other side (e, y_Q x e, 2 pad) (null: read rec_lo)
     T* comp;                 // [mp] < 0 collision, >= 0 spring compliance 1/(h kappa) (solver order)
     T* isc;                  // [mp] 1 / sigma_c: the constraint's scaling undone (solver order)
 };

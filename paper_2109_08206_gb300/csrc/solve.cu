@@ -219,6 +219,8 @@ struct SolveArgs {
     const T* __restrict__ qe_lo;
     const T* __restrict__ pe;   // [mp][8] owner-side records (null: read rec)
     const T* __restrict__ q_lo;
+    const T* __restrict__ lop;    // [mp][8] float32: rec_lo rows, owner side / other side (null: read rec_lo)
+    const T* __restrict__ loq;
     const T* __restrict__ isc;    // [mp] 1/sigma_c of the diagonal scaling (1 when unscaled)
     double hD, tol;
     T pi_tol;      // stopping threshold on max |pi| (float32: see above)
@@ -1341,6 +1343,26 @@ __device__ __forceinline__ int slot_gid(const Own1<T>& o, int t)
 // shared memory; A_PG returns this thread's share of pi.A.pi; A_REF leaves
 // Uref = M D gamma_ref (compensated in float32) in shared memory and in
 // the global Uref).
+// The six low parts of one side of constraint c: e's, then the arm's (rec_lo
+// rows 0-2 and 3-5 for the owner, 0-2 and 6-8 for the other side, arm0 = 3
+// or 6), from the side's 32-byte row when there is one.
+template <typename T>
+__device__ __forceinline__ void lo_side(const T* rows, const T* rec_lo, size_t mp, int c, int arm0, T out[6])
+{
+    if (sizeof(T) == 4 && rows) {
+        const float4* r = reinterpret_cast<const float4*>(rows + 8 * (size_t)c);
+        const float4 x = __ldg(r), y = __ldg(r + 1);
+        out[0] = (T)x.x; out[1] = (T)x.y; out[2] = (T)x.z;
+        out[3] = (T)x.w; out[4] = (T)y.x; out[5] = (T)y.y;
+        return;
+    }
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+        out[w] = __ldg(&rec_lo[w * mp + c]);
+        out[3 + w] = __ldg(&rec_lo[(arm0 + w) * mp + c]);
+    }
+}
+
 template <typename T, int MODE>
 __device__ __forceinline__ T rod_pass1(const SolveArgs<T>& a, const Own1<T>& o, T alpha)
 {
@@ -1370,8 +1392,10 @@ __device__ __forceinline__ T rod_pass1(const SolveArgs<T>& a, const Own1<T>& o, 
                 if (COMP) {   // gamma_lo (held in grs during a reference pass) and the records' low parts
                     const int c = o.c0 + t;
                     const T gl = gv;
+                    T rl[6];
+                    lo_side(a.lop, a.rec_lo, mp, c, 3, rl);
 #pragma unroll
-                    for (int w = 0; w < 6; ++w) Fa[w].add_lo(v * __ldg(&a.rec_lo[w * mp + c]) + gl * rv[w]);
+                    for (int w = 0; w < 6; ++w) Fa[w].add_lo(v * rl[w] + gl * rv[w]);
                 }
             }
         }
@@ -1395,11 +1419,7 @@ __device__ __forceinline__ T rod_pass1(const SolveArgs<T>& a, const Own1<T>& o, 
                     const int c = slot_gid(o, t);
                     const T gl = gv;
                     T ql[6];
-#pragma unroll
-                    for (int w = 0; w < 3; ++w) {
-                        ql[w] = __ldg(&a.rec_lo[w * mp + c]);
-                        ql[3 + w] = __ldg(&a.rec_lo[(6 + w) * mp + c]);
-                    }
+                    lo_side(a.loq, a.rec_lo, mp, c, 6, ql);
 #pragma unroll
                     for (int w = 0; w < 6; ++w) Fa[w].add_lo(-(v * ql[w] + gl * qv[w]));
                 }
@@ -2147,6 +2167,7 @@ static SolveArgs<T> make_args(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, int
     a.inv_rot = (T)ctx->mob.inv_rot; a.inv_spin = (T)ctx->mob.inv_spin;
     a.mobr = ctx->cur_systab ? sb.mobr : nullptr;
     a.rec_lo = sb.rec_lo; a.qe_lo = sb.qe_lo; a.q_lo = sb.q_lo;
+    a.lop = sb.lop; a.loq = sb.loq;
     a.pe = sb.pe;
     a.isc = sb.isc;
     a.comp = ctx->cur_comp ? sb.comp : nullptr;
