@@ -1596,10 +1596,12 @@ __device__ __forceinline__ void con_pass_ref1(const SolveArgs<T>& a, const Own1<
         if (COMP) {
             T tl = __ldg(&a.q_lo[c]);
             if (!ZERO) {
+                T lp[6], lq[6];   // (e, y_P x e) and (e, y_Q x e) low parts
+                lo_side(a.lop, a.rec_lo, mp, c, 3, lp);
+                lo_side(a.loq, a.rec_lo, mp, c, 6, lq);
 #pragma unroll
                 for (int u = 0; u < 3; ++u)
-                    tl += __ldg(&a.rec_lo[u * mp + c]) * (Ui[u] - Uj[u]) +
-                          __ldg(&a.rec_lo[(3 + u) * mp + c]) * Ui[3 + u] - __ldg(&a.rec_lo[(6 + u) * mp + c]) * Uj[3 + u];
+                    tl += lp[u] * (Ui[u] - Uj[u]) + lp[3 + u] * Ui[3 + u] - lq[3 + u] * Uj[3 + u];
             }
             du.add_lo(tl);
         }
