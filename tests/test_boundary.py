@@ -59,3 +59,18 @@ def test_product_path_does_not_touch_the_oracle():
             list((ROOT / "paper_2109_08206_gb300" / "csrc").glob("*")) + [ROOT / "include" / "alens.h"]:
         t = p.read_text()
         assert "import oracle" not in t and "from oracle" not in t and "alens_oracle" not in t, p
+
+
+def test_batch_tables_are_laid_out_like_the_header():
+    """BatchSpec (host-side marshalling of aLENS_step_batch's tables): one
+    aLENS_system per system, scalar boxes widened to three edges, rod
+    offsets as int64; a rod_offset of the wrong length is refused before
+    any call."""
+    systems = [((10.0, 11.0, 12.0), 3.0), (20.0, 4.5)]
+    spec = A.BatchSpec(systems, [0, 5, 9])
+    assert spec.n_systems == 2
+    assert list(spec.tab[0].box) == [10.0, 11.0, 12.0] and spec.tab[0].length == 3.0
+    assert list(spec.tab[1].box) == [20.0, 20.0, 20.0] and spec.tab[1].length == 4.5
+    assert list(spec.off) == [0, 5, 9]
+    with pytest.raises(ValueError):
+        A.BatchSpec(systems, [0, 5])
