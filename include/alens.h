@@ -279,7 +279,9 @@ ALENS_API aLENS_status aLENS_run(aLENS_ctx* ctx, int64_t n, double* x, double* q
  * Every system's constraint problem is solved by its own BBPGD run (its own
  * step sizes, residual and stopping test), all of them in one launch of the
  * per-system solver (thread-block clusters taking systems from a queue,
- * largest first); a batch of one system uses the solver of aLENS_step.
+ * largest first; the largest systems of an uneven batch are solved by two
+ * clusters together, see aLENS_batch_groups); a batch of one system uses
+ * the solver of aLENS_step.
  * info aggregates the batch: pair, overlap and launch counts summed,
  * iterations and residual the largest over the systems (so the call
  * returns OK only when every system met the tolerance), minimum gap over
