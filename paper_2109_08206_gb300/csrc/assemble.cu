@@ -519,11 +519,14 @@ static cudaError_t setup_typed(aLENS_ctx* ctx, const SolveBufs<T>& sb, int n, in
     int mp = (int)ctx->max_pairs, np = (int)ctx->max_rods;
     cudaStream_t st = ctx->stream;
     if (m <= 0) return cudaGetLastError();
+    // the low-part rows serve the single-system one-barrier solver only
+    const bool batch = ctx->cur_systab != nullptr && ctx->batch_n > 1;
     k_setup_fill<T><<<nblk(m, 256), 256, 0, st>>>(m, mp, ctx->perm, pairs, rank, dgeom, q, gamma_in, ctx->rowQ,
                                                   ctx->curQ, ctx->qlist, ctx->ci, ctx->cj, sb.rec, sb.q, sb.gg[0], sb.gg[1],
                                                   sb.rec_lo, sb.q_lo, ctx->cur_comp, sb.comp, np, sb.ax,
                                                   ctx->cur_systab ? sb.mobr : (const T*)nullptr, ctx->mob, ctx->scale_beta,
-                                                  ctx->scale64, sb.isc, sb.lop, sb.loq, ctx->mdev);
+                                                  ctx->scale64, sb.isc, batch ? (T*)nullptr : sb.lop,
+                                                  batch ? (T*)nullptr : sb.loq, ctx->mdev);
     ++ctx->launches;
     k_sort_segments<<<nblk(n, 128), 128, 0, st>>>(n, ctx->rowQ, ctx->qlist);
     ++ctx->launches;
